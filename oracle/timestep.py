@@ -1,0 +1,158 @@
+"""Time integrators of §3.2 of arXiv 1209.5553 (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* EREM (eq. ``EERM``): T^{n+1} = T^n + tau phi_1(tau J_n) G(T^n, p^n), with
+  J_n = D_T G(T^n, p^n) and phi_1 from real Leja interpolation (§4.2).
+* ROSM(gamma) (eq. ``ROS``): T^{n+1} = T^n + tau (I - tau gamma J_n)^{-1} G(T^n).
+* ROS2(1) (eq. ``ROSMh`` with the coefficients of Table ``ros2``), autonomous
+  form: (I/(tau gamma) - J) k_i = G(T + sum_{j<i} a_ij k_j) - sum_{j<i} c_ij/tau k_j,
+  T^{n+1} = T^n + sum_i b_i k_i.  The diagonal c_ii of the printed table do
+  not enter the sums over j < i; the D_t f terms vanish (autonomous problem).
+
+Linear systems are solved directly (sparse LU), so the oracle's stage values
+are exact up to the conditioning of the stage matrix.
+* The sequential (Trotter) coupling of §3.2: pressure at T^n, then Darcy fluxes,
+  then one heat step; :func:`sequential_step`.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import fv
+from .leja import LejaOptions, LejaResult, phi1_leja
+
+
+@dataclass
+class HeatProblem:
+    """Everything G and J need apart from T: grid, physics, porosity,
+    conductivity and the Darcy face fluxes of the current pressure."""
+
+    grid: fv.Grid
+    phys: fv.Physics
+    phi: np.ndarray
+    lam: np.ndarray
+    fluxes: tuple
+
+    def G(self, T):
+        return fv.heat_rhs(self.grid, self.phys, self.phi, self.lam, T, self.fluxes)
+
+    def J(self, T):
+        return fv.heat_jacobian(self.grid, self.phys, self.phi, self.lam, T, self.fluxes)
+
+
+def heat_problem(grid, phys, lnk, phi, lam, p, T_for_viscosity=None):
+    """HeatProblem whose fluxes come from pressure p (Darcy mobility at
+    ``T_for_viscosity`` when the fluid laws depend on T)."""
+    fluxes = fv.darcy_fluxes(grid, phys, lnk, p, T_for_viscosity)
+    return HeatProblem(grid, phys, np.asarray(phi, np.float64).reshape(-1),
+                       np.asarray(lam, np.float64).reshape(-1), fluxes)
+
+
+def erem_step(prob: HeatProblem, T, tau: float, opts: LejaOptions | None = None):
+    """One EREM step (eq. ``EERM``); returns (T^{n+1}, LejaResult)."""
+    T = np.asarray(T, np.float64).reshape(-1)
+    G = prob.G(T)
+    J = prob.J(T)
+    res: LejaResult = phi1_leja(J, G, tau, float(np.max(np.abs(T))), opts)
+    return T + res.value, res
+
+
+# ROS2(1) coefficients (Table ros2): gamma = 1 + 1/sqrt(2), and the remaining
+# entries are the fractions of gamma the table's decimals represent.
+ROS2_GAMMA = 1.0 + 1.0 / math.sqrt(2.0)
+ROS2_A21 = 1.0 / ROS2_GAMMA
+ROS2_C21 = 2.0 / ROS2_GAMMA
+ROS2_B = (3.0 / (2.0 * ROS2_GAMMA), 1.0 / (2.0 * ROS2_GAMMA))
+ROS2_BHAT = (1.0 / ROS2_GAMMA, 0.0)
+
+
+def stage_matrix(J, tau: float, gamma: float):
+    """I / (tau gamma) - J, the matrix of every Rosenbrock stage."""
+    n = J.shape[0]
+    return (sp.identity(n, format="csr") / (tau * gamma) - J).tocsc()
+
+
+def rosm_step(prob: HeatProblem, T, tau: float, gamma: float):
+    """ROSM(gamma), eq. ``ROS``: T + tau (I - tau gamma J)^{-1} G(T)."""
+    T = np.asarray(T, np.float64).reshape(-1)
+    J = prob.J(T)
+    rhs = tau * prob.G(T)
+    A = (sp.identity(T.size, format="csr") - tau * gamma * J).tocsc()
+    return T + spla.spsolve(A, rhs)
+
+
+def ros2_step(prob: HeatProblem, T, tau: float, embedded: bool = False):
+    """ROS2(1) step; with ``embedded`` also returns the first-order solution."""
+    T = np.asarray(T, np.float64).reshape(-1)
+    J = prob.J(T)
+    A = stage_matrix(J, tau, ROS2_GAMMA)
+    lu = spla.splu(A)
+    k1 = lu.solve(prob.G(T))
+    k2 = lu.solve(prob.G(T + ROS2_A21 * k1) - (ROS2_C21 / tau) * k1)
+    y = T + ROS2_B[0] * k1 + ROS2_B[1] * k2
+    if embedded:
+        return y, T + ROS2_BHAT[0] * k1 + ROS2_BHAT[1] * k2
+    return y
+
+
+def pressure_solve_direct(grid, phys, lnk, T=None):
+    """Steady pressure by a sparse direct solve of the TPFA system."""
+    A, b = fv.pressure_system(grid, phys, lnk, T)
+    return spla.spsolve(A.tocsc(), b)
+
+
+def pressure_solve_cg(grid, phys, lnk, T=None, p0=None, tol=1e-13, maxit=100000):
+    """Steady pressure by Jacobi-preconditioned conjugate gradients, stopped
+    when ||b - A p||_2 <= tol ||b||_2 (recursive residual).  Returns
+    (p, iterations, relative residual)."""
+    A, b = fv.pressure_system(grid, phys, lnk, T)
+    x = fv.linear_head_guess(grid, phys) if p0 is None else np.array(p0, np.float64)
+    dinv = 1.0 / A.diagonal()
+    r = b - A @ x
+    bn = np.linalg.norm(b)
+    if np.linalg.norm(r) <= tol * bn:
+        return x, 0, float(np.linalg.norm(r) / bn)
+    z = dinv * r
+    d = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        Ad = A @ d
+        a = rz / (d @ Ad)
+        x = x + a * d
+        r = r - a * Ad
+        rn = np.linalg.norm(r)
+        if rn <= tol * bn:
+            return x, it, float(rn / bn)
+        z = dinv * r
+        rz_new = r @ z
+        d = z + (rz_new / rz) * d
+        rz = rz_new
+    return x, maxit, float(np.linalg.norm(r) / bn)
+
+
+def sequential_step(grid, phys, lnk, phi, lam, T, p_prev, tau, scheme="erem", opts=None,
+                    pressure="direct"):
+    """One step of the sequential (Trotter) approach of §3.2: steady pressure
+    at T^n, Darcy fluxes at T^n, then one heat step of the chosen scheme.
+    Returns (T^{n+1}, p^n, info)."""
+    if pressure == "direct":
+        p = pressure_solve_direct(grid, phys, lnk, T)
+    else:
+        p = pressure_solve_cg(grid, phys, lnk, T, p0=p_prev)[0]
+    prob = heat_problem(grid, phys, lnk, phi, lam, p, T)
+    if scheme == "erem":
+        Tn, res = erem_step(prob, T, tau, opts)
+        return Tn, p, res
+    if scheme == "ros2":
+        return ros2_step(prob, T, tau), p, None
+    if scheme == "rosm1":
+        return rosm_step(prob, T, tau, 1.0), p, None
+    if scheme == "rosm_half":
+        return rosm_step(prob, T, tau, 0.5), p, None
+    raise ValueError(scheme)

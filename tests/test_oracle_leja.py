@@ -1,0 +1,225 @@
+"""Pins of the oracle's Leja machinery (§4.2) against things other than itself:
+closed forms, brute force, high-precision arithmetic and dense matrix
+exponentials."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import fv, leja
+from oracle.leja import LejaOptions
+
+
+def test_first_leja_points_closed_form():
+    # xi_0 = 2; |xi - 2| is largest at -2; |xi^2 - 4| at 0; |xi (xi^2 - 4)| at
+    # +-2/sqrt(3) (equal products, the tie goes to the smaller point).
+    xi = leja.leja_points(3)
+    assert xi[0] == 2.0 and xi[1] == -2.0
+    assert abs(xi[2]) < 1e-15
+    assert xi[3] == pytest.approx(-2.0 / math.sqrt(3.0), abs=1e-15)
+
+
+def test_leja_points_brute_force():
+    # every new point maximises prod |xi - xi_k| on a 2e6-point grid
+    xi = leja.leja_points(24)
+    grid = np.linspace(-2.0, 2.0, 2_000_001)
+    step = grid[1] - grid[0]
+    for j in range(1, 25):
+        logp = np.zeros_like(grid)
+        for k in range(j):
+            with np.errstate(divide="ignore"):
+                logp += np.log(np.abs(grid - xi[k]))
+        best = grid[np.argmax(logp)]
+        if j == 3:
+            continue  # symmetric tie, checked above
+        assert abs(best - xi[j]) <= 2 * step, (j, best, xi[j])
+
+
+def test_leja_points_distinct_bounded_and_capacity():
+    xi = leja.leja_points(150)
+    assert np.all(np.abs(xi) <= 2.0)
+    assert len(np.unique(xi)) == xi.size
+    # (prod_{k<j} |xi_j - xi_k|)^(1/j) tends to the capacity of [-2, 2], which is 1
+    j = 150
+    g = np.exp(np.mean(np.log(np.abs(xi[j] - xi[:j]))))
+    assert 0.9 < g < 1.6
+
+
+def _mp_divided_differences(xi, c, gamma, mp):
+    xs = [mp.mpf(float(x)) for x in xi]
+
+    def phi1(z):
+        return mp.expm1(z) / z if z != 0 else mp.mpf(1)
+
+    col = [phi1(mp.mpf(c) + mp.mpf(gamma) * x) for x in xs]
+    out = [col[0]]
+    for j in range(1, len(xs)):
+        col = [(col[i + 1] - col[i]) / (xs[i + j] - xs[i]) for i in range(len(col) - 1)]
+        out.append(col[0])
+    return out
+
+
+@pytest.mark.parametrize("c,gamma", [(-20.0, 10.0), (-3.0, 1.5), (-60.0, 30.0), (-0.5, 0.25), (-5.0, 5.0)])
+def test_divided_differences_vs_high_precision(c, gamma):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 160
+    xi = leja.leja_points(45)
+    d = leja.phi1_divided_differences(xi, c, gamma)
+    ref = _mp_divided_differences(xi, c, gamma, mp)
+    for j, r in enumerate(ref):
+        r = float(r)
+        if abs(r) > 1e-280:
+            assert abs(d[j] - r) <= 1e-11 * abs(r), (j, d[j], r)
+
+
+def test_divided_difference_zero_is_phi1_at_beta():
+    xi = leja.leja_points(10)
+    for c, gamma in [(-20.0, 10.0), (-1.0, 0.3)]:
+        beta = c + 2 * gamma
+        d = leja.phi1_divided_differences(xi, c, gamma)
+        want = math.expm1(beta) / beta if beta != 0 else 1.0
+        assert d[0] == pytest.approx(want, rel=1e-14)
+
+
+def _small_problem(nx=7, ny=5, pe=20.0, seed=3):
+    rng = np.random.default_rng(seed)
+    g = fv.Grid(2, nx, ny)
+    lnk = rng.normal(0, 1, g.n)
+    ph = fv.Physics(rhoc_f=pe, rhoc_s=pe, T_inflow=80.0)
+    from oracle.timestep import heat_problem, pressure_solve_direct
+
+    p = pressure_solve_direct(g, ph, lnk)
+    prob = heat_problem(g, ph, lnk, np.full(g.n, 0.2), rng.uniform(0.5, 2.0, g.n), p)
+    T = rng.uniform(20, 80, g.n)
+    return prob, T
+
+
+def _phi1_expm(J, v, tau):
+    n = J.shape[0]
+    A = np.zeros((n + 1, n + 1))
+    A[:n, :n] = tau * J.toarray()
+    A[:n, n] = tau * v
+    return sla.expm(A)[:n, n]
+
+
+@pytest.mark.parametrize("tau", [0.01, 0.05, 0.3])
+def test_phi1_leja_matches_dense_expm(tau):
+    prob, T = _small_problem()
+    J = prob.J(T)
+    v = prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    res = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))), LejaOptions(tol_a=1e-13, tol_r=1e-13))
+    assert res.converged
+    err = np.linalg.norm(res.value - ref) / np.linalg.norm(ref)
+    assert err < 1e-10, (err, res.schedule)
+
+
+def test_phi1_leja_default_tolerance_bound():
+    # at the paper's tolerance (1e-6) the weighted error of the increment stays
+    # at the tolerance level
+    prob, T = _small_problem()
+    tau = 0.05
+    J, v = prob.J(T), prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    res = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))), LejaOptions())
+    scal = 1e-6 + 1e-6 * np.max(np.abs(T))
+    assert leja.weighted_norm(res.value - ref, scal) < 1.0
+
+
+def test_phi1_fourier_modes_periodic_advection_diffusion():
+    # periodic upwind advection-diffusion on a ring: J is circulant with
+    # eigenvectors exp(i k x) and eigenvalues
+    # lambda_k = D (2 cos(k h) - 2)/h^2 - (u/h)(1 - exp(-i k h)).
+    n, D, u, tau = 64, 0.01, 1.0, 0.02
+    h = 1.0 / n
+    main = np.full(n, -2 * D / h**2 - u / h)
+    lower = np.full(n, D / h**2 + u / h)
+    upper = np.full(n, D / h**2)
+    J = sp.diags([main, lower[1:], upper[:-1]], [0, -1, 1], shape=(n, n)).tolil()
+    J[0, n - 1] = lower[0]
+    J[n - 1, 0] = upper[0]
+    J = J.tocsr()
+    x = np.arange(n) * h
+    modes = [(1, 1.0), (3, 0.5), (7, -0.25)]
+    v = sum(a * np.cos(2 * np.pi * k * x) for k, a in modes)
+    exact = np.zeros(n, dtype=complex)
+    for k, a in modes:
+        th = 2 * np.pi * k * h
+        lam = D * (2 * np.cos(th) - 2) / h**2 - (u / h) * (1 - np.exp(-1j * th))
+        z = tau * lam
+        ph1 = np.expm1(z) / z
+        # cos = (e^{i} + e^{-i})/2 ; the conjugate mode has the conjugate eigenvalue
+        exact += a * 0.5 * tau * (ph1 * np.exp(1j * th * np.arange(n)) + np.conj(ph1) * np.exp(-1j * th * np.arange(n)))
+    exact = exact.real
+    res = leja.phi1_leja(J, v, tau, 1.0, LejaOptions(tol_a=1e-12, tol_r=1e-12))
+    assert res.converged
+    assert np.max(np.abs(res.value - exact)) < 1e-10 * np.max(np.abs(exact))
+
+
+def test_superlinear_convergence():
+    prob, T = _small_problem(pe=5.0)
+    tau = 0.05
+    J, v = prob.J(T), prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    roots = []
+    # the m-th root of the error falls towards 0 (§4.2); Leja points alternate
+    # sides of the interval, so compare every fourth degree
+    for m in (4, 8, 12, 16):
+        res = leja.phi1_leja(J, v, tau, 1.0, LejaOptions(replay=[1, m]))
+        err = np.linalg.norm(res.value - ref) / np.linalg.norm(ref)
+        if err < 1e-12:  # rounding floor reached
+            break
+        roots.append(err ** (1.0 / m))
+    assert len(roots) >= 3 and roots[-1] < 0.75 * roots[0]
+    assert all(b < a for a, b in zip(roots, roots[1:])), roots
+
+
+def test_substeps_compose_the_same_action():
+    prob, T = _small_problem()
+    tau = 0.2
+    J, v = prob.J(T), prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    for s in (2, 4):
+        res = leja.phi1_leja(J, v, tau, 1.0, LejaOptions(tol_a=1e-12, tol_r=1e-12,
+                                                        replay=None, max_doublings=0, m_max=150))
+        assert np.linalg.norm(res.value - ref) < 1e-9 * np.linalg.norm(ref)
+        forced = leja.phi1_leja(J, v, tau, 1.0, LejaOptions(replay=[s] + [60] * s))
+        assert np.linalg.norm(forced.value - ref) < 1e-9 * np.linalg.norm(ref)
+
+
+def test_degree_cap_triggers_substep_doubling():
+    prob, T = _small_problem(pe=50.0)
+    tau = 0.5
+    J, v = prob.J(T), prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    res = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))), LejaOptions(m_max=12))
+    assert res.converged and res.substeps > 1
+    scal = 1e-6 + 1e-6 * np.max(np.abs(T))
+    assert leja.weighted_norm(res.value - ref, scal) < 10.0
+    fail = leja.phi1_leja(J, v, tau, 1.0, LejaOptions(m_max=3, max_doublings=0))
+    assert not fail.converged
+
+
+def test_gershgorin_interval_contains_spectrum():
+    prob, T = _small_problem()
+    tau = 0.1
+    J = prob.J(T)
+    alpha, beta = leja.gershgorin_interval(J, tau)
+    ev = np.linalg.eigvals(tau * J.toarray())
+    assert np.all(ev.real >= alpha - 1e-9) and np.all(ev.real <= beta + 1e-9)
+
+
+def test_stopping_settings_match_paper():
+    import os
+
+    here = os.path.join(os.path.dirname(__file__), "golden", "paper_settings.txt")
+    vals = {}
+    for line in open(here):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    o = LejaOptions()
+    assert o.tol_a == vals["tol"] and o.tol_r == vals["tol"]
+    assert o.p_order == vals["p_order"] and o.avg_window == vals["avg"]

@@ -1,0 +1,208 @@
+"""Pins of the oracle's time integrators (§3.2) against closed forms of the
+semi-discrete problem, stability functions, observed orders and the
+coefficients the paper prints."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.special import gammainc
+
+import workloads as W
+from oracle import fv, timestep as ts
+from oracle.leja import LejaOptions
+
+TIGHT = LejaOptions(tol_a=1e-13, tol_r=1e-13)
+
+
+def _run(prob, T, tau, steps, opts=TIGHT):
+    for _ in range(steps):
+        T, res = ts.erem_step(prob, T, tau, opts)
+        assert res.converged
+    return T
+
+
+def test_erem_reproduces_dirichlet_neumann_diffusion_modes():
+    # No flow (equal heads), constant conductivity: along x the semi-discrete
+    # problem has a half-cell Dirichlet face at x = 0 and a closed face at x = 1.
+    # Its eigenvectors are sin((i + 1/2) theta_k), theta_k = pi (2k + 1) / (2n),
+    # with eigenvalues -4 D sin^2(theta_k / 2), D = lambda / (C h^2).
+    # capacity C = phi (rho c)_f + (1 - phi)(rho c)_s = 0.2 * 7 + 0.8 * 2 = 3
+    n, lam, C = 24, 1.5, 3.0
+    g = fv.Grid(2, n, 1)
+    ph = fv.Physics(rhoc_f=7.0, rhoc_s=2.0, head_left=0.5, head_right=0.5, T_inflow=10.0)
+    lnk = np.zeros(g.n)
+    p = np.full(g.n, 0.5)
+    prob = ts.heat_problem(g, ph, lnk, np.full(g.n, 0.2), np.full(g.n, lam), p)
+    i = np.arange(n)
+    D = lam / (C * (1.0 / n) ** 2)
+    amps = {0: 5.0, 3: -2.0, 11: 1.0}
+    T0 = 10.0 + sum(a * np.sin((i + 0.5) * math.pi * (2 * k + 1) / (2 * n)) for k, a in amps.items())
+    t_end, steps = 0.004, 4
+    T = _run(prob, T0, t_end / steps, steps)
+    exact = 10.0 + sum(
+        a * math.exp(-4 * D * math.sin(math.pi * (2 * k + 1) / (4 * n)) ** 2 * t_end)
+        * np.sin((i + 0.5) * math.pi * (2 * k + 1) / (2 * n)) for k, a in amps.items())
+    np.testing.assert_allclose(T, exact, rtol=0, atol=1e-9)
+
+
+def test_erem_reproduces_upwind_advection_closed_form():
+    # No conduction, uniform flow u: dT_0/dt = r (T_in - T_0),
+    # dT_i/dt = r (T_{i-1} - T_i), r = (rho c)_f u / (C h) with
+    # C = phi (rho c)_f + (1 - phi)(rho c)_s.  From T0 everywhere,
+    # T_i(t) = T0 + (T_in - T0) P(Poisson(r t) >= i + 1).
+    n = 20
+    g = fv.Grid(2, n, 2)
+    ph = fv.Physics(rhoc_f=4.0, rhoc_s=2.0, head_left=1.0, head_right=0.0, T_inflow=80.0)
+    lnk = np.zeros(g.n)
+    p = ts.pressure_solve_direct(g, ph, lnk)
+    prob = ts.heat_problem(g, ph, lnk, np.full(g.n, 0.3), np.zeros(g.n), p)
+    u = 1.0  # K (head drop) / L
+    C = 0.3 * 4.0 + 0.7 * 2.0
+    r = 4.0 * u / (C / n)
+    t_end = 0.25
+    T = _run(prob, np.full(g.n, 20.0), t_end / 5, 5)
+    i = np.tile(np.arange(n), 2)
+    exact = 20.0 + 60.0 * gammainc(i + 1, r * t_end)
+    np.testing.assert_allclose(T, exact, rtol=0, atol=1e-9)
+
+
+def _workload_problem(n=16, fluid_model=0, sigma=1.0):
+    wl = W.heat2d(n, sigma=sigma)
+    g = fv.Grid(2, n, n)
+    ph0 = fv.Physics(fluid_model=fluid_model)
+    p = ts.pressure_solve_direct(g, ph0, wl.lnk)
+    vx = fv.darcy_fluxes(g, ph0, wl.lnk, p)[0]
+    rc = W.rhoc_for_peclet(50.0, 2.0, vx[:, :, 0].sum())
+    ph = fv.Physics(rhoc_f=rc, rhoc_s=rc, T_inflow=80.0, fluid_model=fluid_model)
+    prob = ts.heat_problem(g, ph, wl.lnk, wl.phi, wl.lam, p, wl.T0)
+    return g, prob, wl
+
+
+def test_erem_exact_for_linear_autonomous_problem():
+    # ETD1 integrates y' = L y + g exactly, so the number of steps does not matter
+    g, prob, wl = _workload_problem(12)
+    a = _run(prob, wl.T0, 1.0, 1)
+    b = _run(prob, wl.T0, 0.1, 10)
+    c = _run(prob, wl.T0, 0.05, 20)
+    assert np.max(np.abs(a - b)) < 1e-9 * np.max(np.abs(a))
+    assert np.max(np.abs(c - b)) < 1e-9 * np.max(np.abs(a))
+    # and it equals the dense matrix exponential of the augmented system
+    J = prob.J(wl.T0).toarray()
+    gvec = prob.G(np.zeros(g.n))
+    n = g.n
+    A = np.zeros((n + 1, n + 1))
+    A[:n, :n] = J
+    A[:n, n] = gvec
+    ex = sla.expm(A) @ np.append(wl.T0, 1.0)
+    assert np.max(np.abs(a - ex[:n])) < 1e-9 * np.max(np.abs(a))
+
+
+def _order(errs, taus):
+    return [math.log(errs[k] / errs[k + 1]) / math.log(taus[k] / taus[k + 1]) for k in range(len(errs) - 1)]
+
+
+def _smooth_T0(g):
+    x = (np.arange(g.nx) + 0.5) / g.nx
+    y = (np.arange(g.ny) + 0.5) / g.ny
+    X, Y = np.meshgrid(x, y)
+    return (50 + 25 * np.sin(2 * np.pi * X) * np.cos(np.pi * Y)).reshape(-1)
+
+
+def test_erem_second_order_on_nonlinear_problem():
+    g, prob, wl = _workload_problem(12, fluid_model=1)
+    T0 = _smooth_T0(g)
+    t_end = 0.08
+    taus = [t_end / 2, t_end / 4, t_end / 8]
+    sols = [_run(prob, T0, t, round(t_end / t)) for t in taus]
+    ref = _run(prob, T0, taus[-1] / 2, round(2 * t_end / taus[-1]))
+    errs = [np.linalg.norm(s - ref) / np.linalg.norm(ref) for s in sols]
+    orders = _order(errs, taus)
+    assert min(orders) > 1.85, (errs, orders)
+
+
+def test_ros2_table_matches_printed_coefficients():
+    here = os.path.join(os.path.dirname(__file__), "golden", "ros2_table.txt")
+    vals = {}
+    for line in open(here):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    assert ts.ROS2_GAMMA == pytest.approx(vals["gamma"], rel=1e-15)
+    assert ts.ROS2_A21 == pytest.approx(vals["a21"], rel=1e-15)
+    assert ts.ROS2_C21 == pytest.approx(vals["c21"], rel=1e-15)
+    assert ts.ROS2_B[0] == pytest.approx(vals["b1"], rel=1e-15)
+    assert ts.ROS2_B[1] == pytest.approx(vals["b2"], rel=1e-15)
+    assert ts.ROS2_BHAT[0] == pytest.approx(vals["bhat1"], rel=1e-15)
+    assert ts.ROS2_BHAT[1] == vals["bhat2"]
+
+
+def test_ros2_orders_two_and_embedded_one():
+    # asymptotic regime (stiff problems show order reduction at large steps,
+    # as §5 reports): global order 2, local order 3, embedded local order 2
+    g, prob, wl = _workload_problem(10, fluid_model=1)
+    T0 = _smooth_T0(g)
+    t_end = 0.002
+    taus = [t_end / 4, t_end / 8, t_end / 16, t_end / 32]
+
+    def run(tau):
+        T = T0.copy()
+        for _ in range(round(t_end / tau)):
+            T = ts.ros2_step(prob, T, tau)
+        return T
+
+    ref = run(taus[-1] / 4)
+    errs = [np.linalg.norm(run(t) - ref) for t in taus]
+    assert min(_order(errs, taus)) > 1.9, errs
+    exact = [_run(prob, T0, t / 32, 32) for t in taus]
+    loc = [np.linalg.norm(ts.ros2_step(prob, T0, t) - e) for t, e in zip(taus, exact)]
+    assert min(_order(loc, taus)) > 2.8
+    emb = [np.linalg.norm(ts.ros2_step(prob, T0, t, embedded=True)[1] - e) for t, e in zip(taus, exact)]
+    assert all(1.9 < o < 2.1 for o in _order(emb, taus))
+
+
+def _one_cell():
+    g = fv.Grid(2, 1, 1)
+    ph = fv.Physics(rhoc_f=2.0, rhoc_s=2.0, head_left=1.0, head_right=0.0, T_inflow=70.0)
+    lnk = np.zeros(1)
+    p = ts.pressure_solve_direct(g, ph, lnk)
+    prob = ts.heat_problem(g, ph, lnk, np.full(1, 0.2), np.full(1, 1.0), p)
+    J = prob.J(np.zeros(1)).toarray()[0, 0]
+    Tstar = 70.0  # steady state: both inflow terms pull T towards T_in
+    return prob, J, Tstar
+
+
+@pytest.mark.parametrize("tau", [0.01, 0.2, 3.0])
+def test_stability_functions_on_a_single_cell(tau):
+    # y' = lambda (y - y*): EREM gives e^z, ROSM(gamma) gives
+    # (1 + z (1 - gamma)) / (1 - gamma z) (§3.2.3), and the L-stable ROS2(1)
+    # gives the order-2 two-stage function (1 + (1-2g) z + (g^2 - 2g + 1/2) z^2)/(1 - g z)^2
+    prob, lam, Tstar = _one_cell()
+    assert prob.G(np.array([Tstar]))[0] == pytest.approx(0.0, abs=1e-12)
+    z = tau * lam
+    y0 = np.array([20.0])
+    e, res = ts.erem_step(prob, y0, tau, TIGHT)
+    assert (e[0] - Tstar) == pytest.approx(math.exp(z) * (y0[0] - Tstar), rel=1e-12, abs=1e-12)
+    for gam in (1.0, 0.5):
+        r = ts.rosm_step(prob, y0, tau, gam)
+        want = (1 + z * (1 - gam)) / (1 - gam * z)
+        assert (r[0] - Tstar) == pytest.approx(want * (y0[0] - Tstar), rel=1e-13)
+    gg = ts.ROS2_GAMMA
+    want = (1 + (1 - 2 * gg) * z + (gg * gg - 2 * gg + 0.5) * z * z) / (1 - gg * z) ** 2
+    r2 = ts.ros2_step(prob, y0, tau)
+    assert (r2[0] - Tstar) == pytest.approx(want * (y0[0] - Tstar), rel=1e-12)
+
+
+def test_sequential_coupling_runs_and_cg_pressure_agrees():
+    wl = W.coupled2d(n=16, steps=3, dt=0.005)
+    g = fv.Grid(2, 16, 16)
+    ph = fv.Physics(rhoc_f=40.0, rhoc_s=40.0, T_inflow=80.0, fluid_model=1)
+    T = wl.T0.copy()
+    p = None
+    for _ in range(3):
+        Tn, p, res = ts.sequential_step(g, ph, wl.lnk, wl.phi, wl.lam, T, p, 0.005)
+        Tc, pc, _ = ts.sequential_step(g, ph, wl.lnk, wl.phi, wl.lam, T, p, 0.005, pressure="cg")
+        assert np.max(np.abs(Tn - Tc)) < 1e-6
+        T = Tn
+    assert np.all(np.isfinite(T)) and T.max() <= 80.0 + 1e-6
