@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the EREM / real-Leja phi_1 path on one GB300.
+
+Workload (default): the 256^3 layered reservoir with 8 x-aligned
+high-permeability channels (contrast 1e4), Peclet 1e3, dt = 1/32, Leja
+tolerance 1e-6; one "step" is one EREM step (eq. EERM): G(T^n), the fused
+Leja terms with their device-side stopping test, and the update.  The Darcy
+field is frozen (one pressure solve in set-up), so the Jacobian and its
+Gershgorin interval are assembled once, outside the timed region.
+
+Headline: FP32-bulk Mcell-steps/s (cells x steps / device time).  Also
+reported: the plain FP64 form on the same steps (ratio and relative L2
+difference of the two results), the end-to-end rate through the C ABI with
+host buffers, the roofline of the Leja term kernel (algorithmic bytes per
+cell-term over its CUDA-event time against the measured HBM copy bandwidth),
+SM clocks sampled during the timed region, and the CPU oracle timed on a
+bounded slab of the same workload.
+
+With --impl reference the CPU oracle itself is timed (each step one oracle
+EREM step on a 256 x 256 x 16 slab of the workload, all its channels kept).
+Under torchrun every rank runs an independent replica on its own GPU (the
+single-grid path is not sharded): value = all ranks' cell-steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "EREM Mcell-steps/s at 256³ FP32-bulk vs FP64 at ≤1e-5 rel err; HBM GB/s vs peak"
+UNIT = "Mcell-steps/s"
+# algorithmic bytes per cell per Leja term of the fused term kernel (3D):
+# 7 coefficients, q_{m-1} read, q_m written, P read and written (FP64)
+BYTES_PER_CELL_TERM = {"fp32_bulk": 7 * 4 + 4 + 4 + 16, "fp64": 7 * 8 + 8 + 8 + 16}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="grid cells per direction")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--slab", type=int, default=16, help="z planes of the oracle's sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(precision: str, n_cells: int):
+    """Bytes per Leja-term launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"leja_term_{precision}_traffic.md")
+    src = os.path.join(ROOT, "paper_1209_5553_gb300", "csrc", "kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernels.cu sha256[:16]") != sha:
+            return None
+        return float(vals["dram bytes per cell-term"]) * n_cells
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+def make_workload(n):
+    import workloads as W
+
+    return W.channels3d(n)
+
+
+def linear_head(n, nx, head_left, head_right):
+    """Pressure initial guess: the head interpolated linearly in x."""
+    x = (np.arange(nx) + 0.5) / nx
+    ramp = head_left + (head_right - head_left) * x
+    return np.broadcast_to(ramp, (n // nx, nx)).reshape(-1).copy()
+
+
+def gpu_context(E, torch, wl, precision, dev):
+    """Context with the workload's state set: GPU pressure solve, velocity
+    scaling (largest face speed 1), heat capacity for Pe = 1e3."""
+    n = wl.n
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    ctx = E.Context(3, wl.nx, wl.ny, wl.nz, physics=E.Physics(1.0, 1.0, wl.head_drop, 0.0,
+                                                             wl.T_inflow, 0),
+                    precision=precision)
+    lnk = t(wl.lnk)
+    p = t(linear_head(n, wl.nx, wl.head_drop, 0.0))
+    st = ctx.pressure_solve(lnk, None, p, tol=1e-10, maxit=200000)
+    import workloads as W
+
+    rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), 1.0)
+    head = wl.head_drop / st.vmax
+    ctx.set_physics(E.Physics(rc, rc, head, 0.0, wl.T_inflow, 0))
+    p = t(linear_head(n, wl.nx, head, 0.0))
+    st2 = ctx.pressure_solve(lnk, None, p, tol=1e-10, maxit=200000)
+    T = t(wl.T0)
+    ctx.set_state(T, p, lnk, t(wl.phi), t(wl.lam), wl.dt)
+    return ctx, T, {"pressure_iters": [st.lin_iters, st2.lin_iters], "vmax_unscaled": st.vmax,
+                    "rhoc": rc, "head_left": head}
+
+
+def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=False):
+    ctx, T, info = gpu_context(E, torch, wl, precision, dev)
+    opts = E.leja_opts(tol=wl.tol, time_terms=True)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.erem_step(T, wl.dt, opts=opts)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(dev.index if dev.index is not None else 0) if sample_clocks else None
+    if sampler:
+        sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    degrees, t_terms, n_terms, launches = [], 0.0, 0, 0
+    t0.record(stream)
+    for _ in range(steps):
+        st = ctx.erem_step(T, wl.dt, opts=opts)
+        degrees.append(st.schedule)
+        t_terms += st.t_terms_ms
+        n_terms += st.n_terms_timed
+        launches += st.launches
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = t0.elapsed_time(t1)
+    barrier(world)
+    out = {"ms": ms, "degrees": degrees, "t_terms_ms": t_terms, "n_terms": n_terms,
+           "launches": launches, "T": T.cpu().numpy(), "clocks": clocks, "info": info,
+           "alpha": st.alpha, "beta": st.beta}
+    ctx.close()
+    return out
+
+
+def run_e2e(E, torch, wl, steps, warmup, dev):
+    """Same steps through the C ABI with a pinned host T: the library copies
+    T to the device and the result back inside every call."""
+    ctx, Td, _ = gpu_context(E, torch, wl, "fp32_bulk", dev)
+    T = torch.empty(wl.n, dtype=torch.float64).pin_memory()
+    T.copy_(Td.cpu())
+    opts = E.leja_opts(tol=wl.tol)
+    for _ in range(warmup):
+        ctx.erem_step(T, wl.dt, opts=opts)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        ctx.erem_step(T, wl.dt, opts=opts)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t
+    ctx.close()
+    return sec
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample: a 16-plane z slab holding channels
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, nz_s):
+    from oracle import fv, timestep as ts
+    import workloads as W
+
+    n = wl.nx
+    lnk = wl.lnk.reshape(wl.nz, wl.ny, wl.nx)
+    chan = np.isclose(lnk, np.log(1e4)).sum(axis=(1, 2))
+    starts = list(range(0, wl.nz - nz_s + 1, nz_s))
+    z0 = max(starts, key=lambda z: chan[z:z + nz_s].sum())
+    sl = slice(z0, z0 + nz_s)
+    f = lambda a: np.ascontiguousarray(a.reshape(wl.nz, wl.ny, wl.nx)[sl]).reshape(-1)
+    g = fv.Grid(3, n, wl.ny, nz_s, 1.0, 1.0, nz_s / wl.nz)
+    base = fv.Physics(head_left=wl.head_drop, head_right=0.0, T_inflow=wl.T_inflow)
+    slnk = f(wl.lnk)
+    p, _, _ = ts.pressure_solve_cg(g, base, slnk, tol=1e-10)
+    vx, vy, vz = fv.darcy_fluxes(g, base, slnk, p)
+    a = g.face_area
+    vmax = max(np.abs(vx).max() / a[0], np.abs(vy).max() / a[1], np.abs(vz).max() / a[2])
+    rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), 1.0)
+    phys = fv.Physics(rc, rc, wl.head_drop / vmax, 0.0, wl.T_inflow, 0)
+    prob = ts.heat_problem(g, phys, slnk, f(wl.phi), f(wl.lam), p / vmax)
+    return prob, f(wl.T0), g.n, f"z-slab {n}x{wl.ny}x{nz_s} (planes {z0}..{z0 + nz_s - 1}) of the {wl.nx}^3 workload"
+
+
+def time_oracle(wl, nz_s, steps, warmup=0):
+    from oracle import timestep as ts
+    from oracle.leja import LejaOptions
+
+    prob, T, ncell, desc = oracle_sample(wl, nz_s)
+    opts = LejaOptions(tol_a=wl.tol, tol_r=wl.tol)
+    for _ in range(warmup):
+        T, _ = ts.erem_step(prob, T, wl.dt, opts)
+    t = time.perf_counter()
+    for _ in range(steps):
+        T, _ = ts.erem_step(prob, T, wl.dt, opts)
+    sec = time.perf_counter() - t
+    return ncell * steps / sec / 1e6, sec, ncell, desc
+
+
+def oracle_threads():
+    # numpy elementwise work and scipy's sparse products run on one thread
+    return 1
+
+
+# ---------------------------------------------------------------------------
+def main_reference(args):
+    rank, world, _ = dist_info()
+    if world > 1 and rank != 0:
+        return
+    wl = make_workload(args.n)
+    value, sec, ncell, desc = time_oracle(wl, args.slab, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"channels3d_{args.n}", "sample": desc, "dt": wl.dt, "tol": wl.tol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} oracle EREM steps on the {desc}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(args):
+    rank, world, local = dist_info()
+    import torch
+
+    import paper_1209_5553_gb300 as E
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist_init(world, "nccl")
+    wl = make_workload(args.n)
+    N = wl.n
+    K, Wu = args.steps, args.warmup
+
+    r32 = run_gpu(E, torch, wl, "fp32_bulk", K, Wu, dev, world, sample_clocks=(rank == 0))
+    ms = max_over_ranks(r32["ms"], world, dev)
+    value = world * N * K / (ms / 1e3) / 1e6
+    peak, peak_kind = measured_peaks()
+    b32 = BYTES_PER_CELL_TERM["fp32_bulk"]
+    achieved = b32 * N * r32["n_terms"] / (r32["t_terms_ms"] / 1e3) / 1e9 if r32["n_terms"] else None
+    traffic = recorded_traffic("fp32_bulk", N)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wu,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"channels3d_{args.n}", "grid": [args.n] * 3, "cells": N,
+                   "dt": wl.dt, "tol": wl.tol, "peclet": wl.peclet,
+                   "precision": "fp32_bulk: FP32 stencil and Leja vectors; FP64 divided differences, "
+                                "interval, running sum and error estimate",
+                   "l2": "inputs larger than L2 (coefficients + vectors ~1.3 GB per term)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "clocks": r32["clocks"],
+        "gpu_launches": r32["launches"],
+        "leja": {"degrees_per_step": [s[1:] if s[0] == 1 else s for s in r32["degrees"]],
+                 "terms_timed": r32["n_terms"], "alpha": r32["alpha"], "beta": r32["beta"]},
+        "roofline": {"kernel": "k_leja_term<float,4,3>", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_cell_term": b32,
+                     "term_ms_avg": r32["t_terms_ms"] / max(r32["n_terms"], 1)},
+        "setup": r32["info"],
+    }
+    if not args.no_fp64:
+        r64 = run_gpu(E, torch, wl, "fp64", K, Wu, dev, world)
+        ms64 = max_over_ranks(r64["ms"], world, dev)
+        b64 = BYTES_PER_CELL_TERM["fp64"]
+        ach64 = b64 * N * r64["n_terms"] / (r64["t_terms_ms"] / 1e3) / 1e9 if r64["n_terms"] else None
+        rel = float(np.linalg.norm(r32["T"] - r64["T"]) / np.linalg.norm(r64["T"]))
+        line["fp64"] = {"value": world * N * K / (ms64 / 1e3) / 1e6, "ms_per_step": ms64 / K,
+                        "achieved_gbs": ach64, "algorithmic_bytes_per_cell_term": b64,
+                        "term_ms_avg": r64["t_terms_ms"] / max(r64["n_terms"], 1),
+                        "degrees_per_step": [s[1:] if s[0] == 1 else s for s in r64["degrees"]]}
+        line["speedup_fp32_bulk_vs_fp64"] = ms64 / ms
+        line["rel_l2_fp32_bulk_vs_fp64"] = rel
+    if not args.no_e2e:
+        sec = run_e2e(E, torch, wl, K, Wu, dev)
+        sec = max_over_ranks(sec, world, dev)
+        line["e2e"] = {"value": world * N * K / sec / 1e6, "unit": UNIT,
+                       "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sec, ncell, desc = time_oracle(wl, args.slab, args.cpu_steps)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                                "sample": f"{args.cpu_steps} oracle EREM steps on the {desc} "
+                                          f"({sec:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main(a)

@@ -1,0 +1,225 @@
+/*
+ * erem.h - C ABI of the GB300 (sm_103a) library for the Exponential
+ * Rosenbrock-Euler method (EREM) with real Leja interpolation of phi_1,
+ * applied to heat transport by Darcy flow in heterogeneous porous media
+ * (Tambue, Berre, Nordbotten, arXiv 1209.5553).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  A uniform Cartesian grid of nx x ny (x nz) cells on
+ *   [0,lx] x [0,ly] (x [0,lz]) (paper §3.1, structured mesh).  Cell-centred
+ *   arrays have N = nx*ny*nz FP64 entries, contiguous, x fastest:
+ *   i = ix + nx*(iy + ny*iz).  In 2D set dim = 2 and nz = 1 (unit thickness).
+ * Boundary set-up.  x = 0: Dirichlet pressure head_left and Dirichlet
+ *   temperature T_inflow (conduction through the half cell, inflow value for
+ *   upwinding).  x = 1: Dirichlet pressure head_right; the face carries the
+ *   boundary cell's temperature outwards and no conduction.  All other faces
+ *   are closed (no flow, no heat flux).
+ * Pointers.  Every array argument may be a device pointer (cudaMalloc, torch
+ *   CUDA tensor) or a host pointer (pageable or pinned).  Host arrays are
+ *   staged through buffers owned by the context; copies are enqueued on the
+ *   given stream and the call returns after they complete.  The caller owns
+ *   all arrays; the library never keeps a caller pointer after a call.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *   default stream).  Every call enqueues its work on that stream and
+ *   returns after it has finished (the Leja stopping test and the linear
+ *   solvers read small control blocks back to the host).
+ * Errors.  Every entry point returns an erem_status; nothing is thrown
+ *   across the ABI.  erem_last_error() gives a message for the last failure
+ *   of a context.  Arguments are checked on the host (sizes, dt > 0,
+ *   tolerances > 0, NULL pointers); non-finite input values, negative
+ *   conductivities and porosities outside [0,1] are detected by the set-up
+ *   kernels and reported as EREM_ENONFINITE / EREM_EINVAL.  A failing call
+ *   leaves its in/out arrays unchanged.
+ * Threads.  A context may be used by one host thread at a time; separate
+ *   contexts are independent.
+ */
+#ifndef EREM_H
+#define EREM_H
+
+#if defined(__GNUC__)
+#define EREM_API __attribute__((visibility("default")))
+#else
+#define EREM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EREM_OK = 0,
+  EREM_EINVAL = 1,     /* bad argument, or physically invalid input field    */
+  EREM_ENOMEM = 2,     /* device or pinned host allocation failed            */
+  EREM_ENOTCONV = 3,   /* Leja interpolation or linear solver did not converge */
+  EREM_ETIMEOUT = 4,   /* a bounded device-side wait gave up (reserved)      */
+  EREM_ENONFINITE = 5, /* NaN or Inf in an input or an intermediate result   */
+  EREM_ECUDA = 6       /* CUDA runtime error (message in erem_last_error)    */
+} erem_status;
+
+/* Arithmetic of the Leja vectors and stencil sweeps.  EREM_FP64: everything
+ * in FP64.  EREM_FP32_BULK: the Jacobian coefficients and the Newton vectors
+ * q_m are FP32; divided differences, the spectral interval, the running sum
+ * P_m, the error estimate and all linear-solver arithmetic stay FP64. */
+typedef enum { EREM_FP64 = 0, EREM_FP32_BULK = 1 } erem_precision;
+
+/* Rosenbrock-type schemes of §3.2: ROSM(1) and ROSM(1/2) (eq. ROS with
+ * gamma = 1 and 1/2) and the two-stage ROS2(1) (eq. ROSMh, Table ros2). */
+typedef enum { EREM_ROSM1 = 0, EREM_ROSM_HALF = 1, EREM_ROS2 = 2 } erem_rosm_scheme;
+
+typedef struct {
+  int dim;          /* 2 or 3                                  */
+  int nx, ny, nz;   /* cells per direction (nz = 1 in 2D)      */
+  double lx, ly, lz; /* domain lengths (lz ignored in 2D)      */
+} erem_grid;
+
+/* Constants of the local-equilibrium heat model (§2 with he -> infinity):
+ * volumetric capacity C = phi*rhoc_f + (1-phi)*rhoc_s, advective face flux
+ * rhoc_f * v_sigma * X(T).  fluid_model = 0: X = T and constant fluid
+ * properties.  fluid_model = 1: rho(T)/rho_0 = 1 - 3e-4 (T - 20) and
+ * mu(T)/mu_0 = exp(-0.02 (T - 20)); the pressure equation uses the mass
+ * mobility K rho/mu, the Darcy flux K/mu, and X = (rho/rho_0) T. */
+typedef struct {
+  double rhoc_f, rhoc_s;
+  double head_left, head_right; /* Dirichlet pressure at x = 0 and x = 1 */
+  double T_inflow;              /* Dirichlet temperature at x = 0        */
+  int fluid_model;
+} erem_physics;
+
+/* Options of the real Leja phi_1 evaluation (§4.2).  Start from
+ * erem_default_leja_opts(); a zero tol_a, tol_r, p_order, m_max or avg_window
+ * takes its default, max_doublings is used as given (0 = never split). */
+typedef struct {
+  double tol_a, tol_r;  /* scal = tol_a + tol_r * ||T^n||_inf  (default 1e-6) */
+  int p_order;          /* stop when 10^p * mean(e) < 1 (default 2)           */
+  int m_max;            /* largest degree before the step is split (150)      */
+  int max_doublings;    /* substep doublings before EREM_ENOTCONV (0..6)      */
+  int avg_window;       /* number of estimates averaged (5)                   */
+  const int* replay;    /* host array [s, m_1..m_s] forcing the substep count
+                           and the degrees, or NULL for the stopping rule     */
+  int n_replay;         /* entries in replay (1 + s)                          */
+  int time_terms;       /* nonzero: time every Leja term with CUDA events     */
+} erem_leja_opts;
+
+typedef struct {
+  int substeps;         /* s: substeps of the last phi_1 evaluation           */
+  int degree_total;     /* sum of the degrees over the substeps               */
+  int degrees[64];      /* degree m_k of substep k                            */
+  double alpha, beta;   /* Gershgorin interval of dt*J                        */
+  double err_est;       /* mean error estimate at the last stop              */
+  int lin_iters;        /* linear-solver iterations (pressure / stages)       */
+  double lin_resid;     /* final relative residual of the linear solver      */
+  double flux_in;       /* pressure_solve: net Darcy inflow through x = 0     */
+  double vmax;          /* pressure_solve: largest |face flux| / face area    */
+  double t_ms;          /* wall time of the call, milliseconds                */
+  double t_terms_ms;    /* time_terms: summed device time of the Leja terms   */
+  int n_terms_timed;    /* time_terms: number of terms in t_terms_ms          */
+  int launches;         /* CUDA kernels this call launched                    */
+} erem_stats;
+
+typedef struct erem_ctx erem_ctx;
+
+/* Fill *opts with the defaults: tol 1e-6 (§5), p = 2 (§4.2: the order of
+ * EREM), m_max = 150, 6 doublings, average of 5 estimates (§4.2). */
+EREM_API void erem_default_leja_opts(erem_leja_opts* opts);
+
+/* Create a context for one grid: validates the grid, allocates every device
+ * buffer the other calls need (no allocation happens per step; staging
+ * buffers for host pointers and linear-solver vectors are allocated on their
+ * first use) and builds the Leja point table.  The current CUDA device at
+ * this call is the context's device.  *out receives the context, or NULL on
+ * failure.  Errors: EINVAL (bad grid or physics), ENOMEM, ECUDA. */
+EREM_API erem_status erem_create(const erem_grid* grid, const erem_physics* phys,
+                        erem_precision prec, erem_ctx** out);
+
+/* Free every resource of the context (NULL is ignored). */
+EREM_API erem_status erem_destroy(erem_ctx* ctx);
+
+/* Replace the physics constants (used after a pressure solve has given the
+ * velocity scale of a workload).  Takes effect at the next erem_set_state /
+ * erem_step / rosm_step. */
+EREM_API erem_status erem_set_physics(erem_ctx* ctx, const erem_physics* phys);
+
+/* Steady pressure (§2, eq. masscon4 without storage terms; the paper's
+ * initial state is the steady pressure, §5), discretized with the TPFA
+ * harmonic transmissibilities of §3.1 and solved with Jacobi-preconditioned
+ * conjugate gradients in FP64.
+ *   lnk  [N]  ln K per cell
+ *   T    [N]  temperature for the fluid laws (may be NULL: T = 20)
+ *   p    [N]  in: initial guess; out: solution
+ *   tol       stop when ||b - A p||_2 <= tol ||b||_2 (recursive residual)
+ *   maxit     iteration limit; EREM_ENOTCONV (p holds the last iterate)
+ * stats (may be NULL): lin_iters, lin_resid, flux_in, vmax, t_ms. */
+EREM_API erem_status pressure_solve(erem_ctx* ctx, const double* lnk, const double* T,
+                           double* p, double tol, int maxit, erem_stats* stats,
+                           void* stream);
+
+/* Set the state that phi1_apply uses: stores copies of the fields,
+ * assembles the Darcy face fluxes from p (eq. darcy with TPFA), the
+ * Jacobian J = D_T G(T, p) of the heat right-hand side (eq. linear; the
+ * finite-volume fluxes of §3.1 with upwind advection) and the Gershgorin
+ * interval [alpha, beta] of dt*J (§4.2).
+ *   T, p, lnk, phi, lambda [N]; dt > 0.
+ * Errors: EINVAL, ENONFINITE, ECUDA. */
+EREM_API erem_status erem_set_state(erem_ctx* ctx, const double* T, const double* p,
+                           const double* lnk, const double* phi,
+                           const double* lambda, double dt, void* stream);
+
+/* out = dt * phi_1(dt * J) v for the J and dt of the last erem_set_state
+ * (or erem_step), by real Leja interpolation in Newton form (§4.2, eqs.
+ * lejaa, div, newt) with the weighted error estimate and the stopping test
+ * 10^p mean(||e||) < 1 of §4.2; when m_max terms do not meet the test the
+ * step is split into s = 2, 4, ... substeps (§4.2).
+ *   v [N] input vector, out [N] result (may alias v).
+ * opts may be NULL (defaults).  stats (may be NULL): substeps, degrees,
+ * alpha, beta, err_est, t_ms, t_terms_ms.
+ * Errors: EINVAL (no state yet), ENOTCONV (out unchanged), ENONFINITE. */
+EREM_API erem_status phi1_apply(erem_ctx* ctx, const double* v, double* out,
+                       const erem_leja_opts* opts, erem_stats* stats,
+                       void* stream);
+
+/* One EREM step (eq. EERM):
+ *   T <- T + dt * phi_1(dt * J_n) G(T, p),   J_n = D_T G(T, p).
+ * p, lnk, phi, lambda: the fields of this step, or all NULL to keep the
+ * fields of the previous call (with fluid_model = 0 and an unchanged dt the
+ * Jacobian and the divided differences are then reused).  With
+ * fluid_model = 1, J_n and the Darcy fluxes are re-evaluated at T every step.
+ *   T [N] in/out.  Errors as phi1_apply; on error T is unchanged. */
+EREM_API erem_status erem_step(erem_ctx* ctx, double* T, const double* p,
+                      const double* lnk, const double* phi,
+                      const double* lambda, double dt,
+                      const erem_leja_opts* opts, erem_stats* stats,
+                      void* stream);
+
+/* One Rosenbrock-type step (§3.2): ROSM(gamma) (eq. ROS)
+ *   T <- T + dt (I - dt gamma J_n)^{-1} G(T)
+ * or ROS2(1) (eq. ROSMh with Table ros2, autonomous form).  Every stage
+ * system (I/(dt gamma) - J_n) k = r is solved by Jacobi-preconditioned
+ * BiCGSTAB in FP64 to ||r - A k||_2 <= lin_tol ||r||_2 (maxit iterations).
+ * Fields as erem_step.  Errors: EINVAL, ENOTCONV, ENONFINITE, ECUDA. */
+EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
+                      const double* lnk, const double* phi,
+                      const double* lambda, double dt,
+                      erem_rosm_scheme scheme, double lin_tol, int maxit,
+                      erem_stats* stats, void* stream);
+
+/* Message of the last failing call on ctx ("" if none; a static message if
+ * ctx is NULL).  The pointer stays valid until the next call on ctx. */
+EREM_API const char* erem_last_error(const erem_ctx* ctx);
+
+/* Host-only helpers (no GPU needed) that expose the FP64 scalar side of the
+ * Leja method; the device path uses the same routines.
+ * erem_leja_points: xi_0..xi_M on [-2, 2] (eq. lejaa with xi_0 = 2, ties to
+ *   the smaller point); returns 0, or -1 for M < 0 or M > 4096.
+ * erem_phi1_divided_differences: d_j = phi_1[xi_0..xi_j] of
+ *   xi -> phi_1(c + gamma xi), j = 0..M, the first column of
+ *   phi_1(c I + gamma L_hat) (§4.2); returns 0, or -1 on bad arguments. */
+EREM_API int erem_leja_points(int M, double* xi);
+EREM_API int erem_phi1_divided_differences(int M, const double* xi, double c,
+                                  double gamma, double* d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EREM_H */

@@ -1,0 +1,311 @@
+"""Python binding of the GB300 EREM library (``liberem.so``, C ABI in include/erem.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels and host C++ code.  The functions below carry the names of the
+C entry points and take torch tensors (CUDA or CPU) or numpy arrays of FP64
+values, contiguous, x fastest; CPU arrays are staged by the library.  The
+library must have been built (``__graft_entry__.build()`` or
+``python paper_1209_5553_gb300/build.py``); importing this package without it
+raises ImportError.  There is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liberem.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+    )
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes (erem_status)
+EREM_OK, EREM_EINVAL, EREM_ENOMEM, EREM_ENOTCONV, EREM_ETIMEOUT, EREM_ENONFINITE, EREM_ECUDA = range(7)
+STATUS_NAMES = {0: "EREM_OK", 1: "EREM_EINVAL", 2: "EREM_ENOMEM", 3: "EREM_ENOTCONV",
+                4: "EREM_ETIMEOUT", 5: "EREM_ENONFINITE", 6: "EREM_ECUDA"}
+EREM_FP64, EREM_FP32_BULK = 0, 1
+EREM_ROSM1, EREM_ROSM_HALF, EREM_ROS2 = 0, 1, 2
+
+
+class erem_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("lz", ctypes.c_double)]
+
+
+class erem_physics(ctypes.Structure):
+    _fields_ = [("rhoc_f", ctypes.c_double), ("rhoc_s", ctypes.c_double),
+                ("head_left", ctypes.c_double), ("head_right", ctypes.c_double),
+                ("T_inflow", ctypes.c_double), ("fluid_model", ctypes.c_int)]
+
+
+class erem_leja_opts(ctypes.Structure):
+    _fields_ = [("tol_a", ctypes.c_double), ("tol_r", ctypes.c_double),
+                ("p_order", ctypes.c_int), ("m_max", ctypes.c_int),
+                ("max_doublings", ctypes.c_int), ("avg_window", ctypes.c_int),
+                ("replay", ctypes.POINTER(ctypes.c_int)), ("n_replay", ctypes.c_int),
+                ("time_terms", ctypes.c_int)]
+
+
+class erem_stats(ctypes.Structure):
+    _fields_ = [("substeps", ctypes.c_int), ("degree_total", ctypes.c_int),
+                ("degrees", ctypes.c_int * 64), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("err_est", ctypes.c_double),
+                ("lin_iters", ctypes.c_int), ("lin_resid", ctypes.c_double),
+                ("flux_in", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("t_ms", ctypes.c_double), ("t_terms_ms", ctypes.c_double),
+                ("n_terms_timed", ctypes.c_int), ("launches", ctypes.c_int)]
+
+    @property
+    def schedule(self):
+        return [self.substeps] + [self.degrees[k] for k in range(self.substeps)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_sigs = {
+    "erem_default_leja_opts": (None, [ctypes.POINTER(erem_leja_opts)]),
+    "erem_create": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics), _I,
+                         ctypes.POINTER(_P)]),
+    "erem_destroy": (_I, [_P]),
+    "erem_set_physics": (_I, [_P, ctypes.POINTER(erem_physics)]),
+    "pressure_solve": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
+    "erem_set_state": (_I, [_P, _P, _P, _P, _P, _P, _D, _P]),
+    "phi1_apply": (_I, [_P, _P, _P, ctypes.POINTER(erem_leja_opts), ctypes.POINTER(erem_stats), _P]),
+    "erem_step": (_I, [_P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(erem_leja_opts),
+                       ctypes.POINTER(erem_stats), _P]),
+    "rosm_step": (_I, [_P, _P, _P, _P, _P, _P, _D, _I, _D, _I, ctypes.POINTER(erem_stats), _P]),
+    "erem_last_error": (ctypes.c_char_p, [_P]),
+    "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
+    "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+class EremError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _ptr(x, n: int | None):
+    """Raw pointer of an FP64 contiguous array (torch tensor or numpy array)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy arrays must be contiguous float64")
+        if n is not None and x.size != n:
+            raise ValueError(f"array has {x.size} entries, expected {n}")
+        return x.ctypes.data
+    import torch
+
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        if n is not None and x.numel() != n:
+            raise ValueError(f"tensor has {x.numel()} entries, expected {n}")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def leja_opts(tol=1e-6, tol_a=None, tol_r=None, p_order=2, m_max=150, max_doublings=6,
+              avg_window=5, replay=None, time_terms=False):
+    """erem_leja_opts with the given fields (replay = [s, m_1..m_s] or None)."""
+    o = erem_leja_opts()
+    erem_default_leja_opts(o)
+    o.tol_a = tol if tol_a is None else tol_a
+    o.tol_r = tol if tol_r is None else tol_r
+    o.p_order, o.m_max, o.max_doublings, o.avg_window = p_order, m_max, max_doublings, avg_window
+    o.time_terms = 1 if time_terms else 0
+    if replay is not None:
+        arr = (ctypes.c_int * len(replay))(*[int(v) for v in replay])
+        o._replay_keep = arr  # keep alive with the struct
+        o.replay = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int))
+        o.n_replay = len(replay)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# C entry points under their own names
+# ---------------------------------------------------------------------------
+def erem_default_leja_opts(opts: erem_leja_opts) -> None:
+    _lib.erem_default_leja_opts(ctypes.byref(opts))
+
+
+def erem_create(grid: erem_grid, phys: erem_physics, precision: int = EREM_FP64):
+    h = _P()
+    st = _lib.erem_create(ctypes.byref(grid), ctypes.byref(phys), int(precision), ctypes.byref(h))
+    if st != EREM_OK:
+        raise EremError(st, "erem_create failed")
+    return h
+
+
+def erem_destroy(ctx) -> None:
+    _lib.erem_destroy(ctx)
+
+
+def erem_last_error(ctx) -> str:
+    r = _lib.erem_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def _check(ctx, st):
+    if st != EREM_OK:
+        raise EremError(st, erem_last_error(ctx))
+
+
+def erem_set_physics(ctx, phys: erem_physics) -> None:
+    _check(ctx, _lib.erem_set_physics(ctx, ctypes.byref(phys)))
+
+
+def pressure_solve(ctx, n, lnk, T, p, tol=1e-10, maxit=100000, stream=None) -> erem_stats:
+    st = erem_stats()
+    _check(ctx, _lib.pressure_solve(ctx, _ptr(lnk, n), _ptr(T, n), _ptr(p, n), float(tol),
+                                    int(maxit), ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def erem_set_state(ctx, n, T, p, lnk, phi, lam, dt, stream=None) -> None:
+    _check(ctx, _lib.erem_set_state(ctx, _ptr(T, n), _ptr(p, n), _ptr(lnk, n), _ptr(phi, n),
+                                    _ptr(lam, n), float(dt), _stream(stream)))
+
+
+def phi1_apply(ctx, n, v, out, opts: erem_leja_opts | None = None, stream=None) -> erem_stats:
+    st = erem_stats()
+    _check(ctx, _lib.phi1_apply(ctx, _ptr(v, n), _ptr(out, n),
+                                ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def erem_step(ctx, n, T, dt, p=None, lnk=None, phi=None, lam=None,
+              opts: erem_leja_opts | None = None, stream=None) -> erem_stats:
+    st = erem_stats()
+    _check(ctx, _lib.erem_step(ctx, _ptr(T, n), _ptr(p, n), _ptr(lnk, n), _ptr(phi, n),
+                               _ptr(lam, n), float(dt),
+                               ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def rosm_step(ctx, n, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
+              lin_tol=1e-10, maxit=10000, stream=None) -> erem_stats:
+    st = erem_stats()
+    _check(ctx, _lib.rosm_step(ctx, _ptr(T, n), _ptr(p, n), _ptr(lnk, n), _ptr(phi, n),
+                               _ptr(lam, n), float(dt), int(scheme), float(lin_tol), int(maxit),
+                               ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def erem_leja_points(M: int) -> np.ndarray:
+    out = np.zeros(M + 1)
+    if _lib.erem_leja_points(int(M), out.ctypes.data_as(ctypes.POINTER(_D))) != 0:
+        raise ValueError("bad M")
+    return out
+
+
+def erem_phi1_divided_differences(xi, c: float, gamma: float) -> np.ndarray:
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    out = np.zeros(xi.size)
+    if _lib.erem_phi1_divided_differences(xi.size - 1, xi.ctypes.data_as(ctypes.POINTER(_D)),
+                                          float(c), float(gamma),
+                                          out.ctypes.data_as(ctypes.POINTER(_D))) != 0:
+        raise ValueError("bad arguments")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+@dataclass
+class Physics:
+    rhoc_f: float = 1.0
+    rhoc_s: float = 1.0
+    head_left: float = 1.0
+    head_right: float = 0.0
+    T_inflow: float = 80.0
+    fluid_model: int = 0
+
+    def c(self) -> erem_physics:
+        return erem_physics(self.rhoc_f, self.rhoc_s, self.head_left, self.head_right,
+                            self.T_inflow, self.fluid_model)
+
+
+class Context:
+    """Owns one erem_ctx; methods forward to the C entry points."""
+
+    def __init__(self, dim, nx, ny, nz=1, physics: Physics | None = None, precision="fp64",
+                 lx=1.0, ly=1.0, lz=1.0):
+        prec = {"fp64": EREM_FP64, "fp32_bulk": EREM_FP32_BULK}[precision] \
+            if isinstance(precision, str) else int(precision)
+        self.n = nx * ny * nz
+        self.grid = erem_grid(dim, nx, ny, nz, lx, ly, lz)
+        self.physics = physics or Physics()
+        self._h = erem_create(self.grid, self.physics.c(), prec)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            erem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_physics(self, physics: Physics):
+        self.physics = physics
+        erem_set_physics(self._h, physics.c())
+
+    def pressure_solve(self, lnk, T, p, tol=1e-10, maxit=100000, stream=None):
+        return pressure_solve(self._h, self.n, lnk, T, p, tol, maxit, stream)
+
+    def set_state(self, T, p, lnk, phi, lam, dt, stream=None):
+        erem_set_state(self._h, self.n, T, p, lnk, phi, lam, dt, stream)
+
+    def phi1_apply(self, v, out, opts=None, stream=None):
+        return phi1_apply(self._h, self.n, v, out, opts, stream)
+
+    def erem_step(self, T, dt, p=None, lnk=None, phi=None, lam=None, opts=None, stream=None):
+        return erem_step(self._h, self.n, T, dt, p, lnk, phi, lam, opts, stream)
+
+    def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
+                  lin_tol=1e-10, maxit=10000, stream=None):
+        return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)

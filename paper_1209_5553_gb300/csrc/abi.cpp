@@ -1,0 +1,731 @@
+// C ABI of the EREM library (declared in include/erem.h): contexts, pointer
+// staging, and the host loops that drive the device kernels.
+//
+// The Leja loop (§4.2) runs without a host round trip per term: each term
+// kernel's last block evaluates the stopping test on the device and raises
+// `done`; later term kernels of the same chunk see it and return at once.
+// The host launches a chunk of terms (sized from the previous degree), then
+// reads the control block once.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <string>
+
+#include "erem_internal.h"
+
+using namespace erem;
+
+namespace {
+
+const char* const kNullCtxMsg = "erem: NULL context";
+
+erem_status fail(erem_ctx* c, erem_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define EREM_CUDA(ctx, call)                                                         \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      return fail((ctx), EREM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                \
+  } while (0)
+
+#define EREM_TRY(expr)              \
+  do {                              \
+    erem_status st_ = (expr);       \
+    if (st_ != EREM_OK) return st_; \
+  } while (0)
+
+erem_status check_launch(erem_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, EREM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return EREM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+erem_status dalloc(erem_ctx* c, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, EREM_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  if (cudaMemset(*p, 0, bytes) != cudaSuccess) return fail(c, EREM_ECUDA, "cudaMemset failed");
+  return EREM_OK;
+}
+
+template <typename T>
+erem_status dalloc_t(erem_ctx* c, T** p, size_t count) {
+  return dalloc(c, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+// Device pointer for a caller array of N doubles: the pointer itself when it
+// is device memory, else a context staging buffer (filled when copy_in).
+erem_status resolve(erem_ctx* c, int slot, const double* ptr, bool copy_in, cudaStream_t s,
+                    double** out) {
+  if (!ptr) return fail(c, EREM_EINVAL, "NULL array argument");
+  if (is_device_ptr(ptr)) {
+    *out = const_cast<double*>(ptr);
+    return EREM_OK;
+  }
+  if (!c->stage[slot]) EREM_TRY(dalloc_t(c, &c->stage[slot], (size_t)c->N));
+  if (copy_in)
+    EREM_CUDA(c, cudaMemcpyAsync(c->stage[slot], ptr, (size_t)c->N * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+  *out = c->stage[slot];
+  return EREM_OK;
+}
+
+erem_status ensure_krylov(erem_ctx* c) {
+  if (c->kv[0]) return EREM_OK;
+  for (int k = 0; k < 12; ++k) EREM_TRY(dalloc_t(c, &c->kv[k], (size_t)c->Np));
+  return EREM_OK;
+}
+
+erem_status read_ctrl(erem_ctx* c, cudaStream_t s) {
+  EREM_CUDA(c, cudaMemcpyAsync(c->ctrl_h, c->ctrl, offsetof(Ctrl, e), cudaMemcpyDeviceToHost, s));
+  EREM_CUDA(c, cudaStreamSynchronize(s));
+  return EREM_OK;
+}
+
+erem_status check_flags(erem_ctx* c) {
+  if (c->ctrl_h->flags & FLAG_NONFINITE)
+    return fail(c, EREM_ENONFINITE, "non-finite value in an input field or its derived coefficients");
+  if (c->ctrl_h->flags & FLAG_BAD_INPUT)
+    return fail(c, EREM_EINVAL, "negative conductivity, porosity outside [0,1] or non-positive capacity");
+  return EREM_OK;
+}
+
+erem_status ensure_leja(erem_ctx* c, int M) {
+  if (M <= c->xi_cap) return EREM_OK;
+  if (M > kMaxTerms) return fail(c, EREM_EINVAL, "m_max above " + std::to_string(kMaxTerms));
+  int cap = std::max(M, 2 * c->xi_cap);
+  cap = std::min(cap, kMaxTerms);
+  leja_table(cap, &c->xi_host);
+  if (c->xi_dev) cudaFree(c->xi_dev);
+  c->xi_dev = nullptr;
+  EREM_TRY(dalloc_t(c, &c->xi_dev, (size_t)cap + 1));
+  EREM_CUDA(c, cudaMemcpy(c->xi_dev, c->xi_host.data(), (cap + 1) * sizeof(double),
+                          cudaMemcpyHostToDevice));
+  c->xi_cap = cap;
+  return EREM_OK;
+}
+
+void focal_map(erem_ctx* c) {
+  c->cfoc = 0.5 * (c->alpha + c->beta);
+  double g = 0.25 * (c->beta - c->alpha);
+  const double floor = 1e-8 * std::max(1.0, std::fabs(c->cfoc));
+  c->gam = std::max(g, floor);
+}
+
+// Divided differences of level S (interval / S) with at least M+1 entries,
+// on the device in dd_dev.
+erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s) {
+  DDEntry& e = c->dd_cache[S];
+  const double cc = c->cfoc / S, gg = c->gam / S;
+  if (e.M < M || e.c != cc || e.gamma != gg) {
+    e.c = cc;
+    e.gamma = gg;
+    e.M = M;
+    e.d.assign(M + 1, 0.0);
+    if (divided_differences(M, c->xi_host.data(), cc, gg, e.d.data()) != 0)
+      return fail(c, EREM_EINVAL, "divided differences: bad interval");
+    for (double v : e.d)
+      if (!std::isfinite(v)) return fail(c, EREM_ENONFINITE, "non-finite divided difference");
+    c->dd_tag_S = -1;
+  }
+  if (c->dd_tag_S != S || c->dd_tag_M != e.M) {
+    std::memcpy(c->dd_h, e.d.data(), (e.M + 1) * sizeof(double));
+    EREM_CUDA(c, cudaMemcpyAsync(c->dd_dev, c->dd_h, (e.M + 1) * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+    c->dd_tag_S = S;
+    c->dd_tag_M = e.M;
+  }
+  return EREM_OK;
+}
+
+struct Opts {
+  double tol_a = 1e-6, tol_r = 1e-6;
+  int p_order = 2, m_max = 150, max_doublings = 6, avg_window = 5;
+  std::vector<int> replay;
+  bool time_terms = false;
+};
+
+erem_status parse_opts(erem_ctx* c, const erem_leja_opts* o, Opts* out) {
+  Opts r;
+  if (o) {
+    if (o->tol_a != 0.0) r.tol_a = o->tol_a;
+    if (o->tol_r != 0.0) r.tol_r = o->tol_r;
+    if (o->p_order != 0) r.p_order = o->p_order;
+    if (o->m_max != 0) r.m_max = o->m_max;
+    r.max_doublings = o->max_doublings;
+    if (o->avg_window != 0) r.avg_window = o->avg_window;
+    r.time_terms = o->time_terms != 0;
+    if (o->replay) {
+      if (o->n_replay < 2) return fail(c, EREM_EINVAL, "replay needs [s, m_1..m_s]");
+      const int S = o->replay[0];
+      if (S < 1 || S > 64 || o->n_replay != 1 + S)
+        return fail(c, EREM_EINVAL, "replay: s must be 1..64 and n_replay = 1 + s");
+      for (int k = 1; k <= S; ++k)
+        if (o->replay[k] < 1 || o->replay[k] > kMaxTerms)
+          return fail(c, EREM_EINVAL, "replay degree out of range");
+      r.replay.assign(o->replay, o->replay + o->n_replay);
+    }
+  }
+  if (!(r.tol_a >= 0.0) || !(r.tol_r >= 0.0) || r.tol_a + r.tol_r <= 0.0)
+    return fail(c, EREM_EINVAL, "tolerances must be >= 0 with tol_a + tol_r > 0");
+  if (r.m_max < 1 || r.m_max > kMaxTerms) return fail(c, EREM_EINVAL, "m_max out of range");
+  if (r.avg_window < 1 || r.p_order < 0 || r.p_order > 30 || r.max_doublings < 0 ||
+      r.max_doublings > 6)
+    return fail(c, EREM_EINVAL, "bad avg_window, p_order or max_doublings (0..6)");
+  *out = r;
+  return EREM_OK;
+}
+
+erem_status ensure_events(erem_ctx* c, int n) {
+  while ((int)c->ev.size() < 2 * n) {
+    cudaEvent_t e;
+    EREM_CUDA(c, cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  return EREM_OK;
+}
+
+// out (unpadded, device) = base + dt phi_1(dt J) src, with src and base padded
+// device vectors (base may be null).  J, dt, alpha, beta and the Leja copy of
+// J must be current.
+erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double* out,
+                     const Opts& o, erem_stats* st, cudaStream_t s) {
+  const bool replay = !o.replay.empty();
+  int mcap = o.m_max;
+  if (replay)
+    for (size_t k = 1; k < o.replay.size(); ++k) mcap = std::max(mcap, o.replay[k]);
+  EREM_TRY(ensure_leja(c, mcap));
+  const double cg = c->cfoc / c->gam;  // the same for every substep level
+  int n_attempts = replay ? 1 : o.max_doublings + 1;
+  int degrees[64];
+  double t_terms = 0.0;
+  int n_timed = 0;
+  if (o.time_terms) EREM_TRY(ensure_events(c, mcap + 1));
+  for (int a = 0; a < n_attempts; ++a) {
+    const int S = replay ? o.replay[0] : (1 << a);
+    const double delta = c->dt / S;
+    // a short table first; the full one when a substep needs more terms
+    int M_avail = replay ? mcap : std::min(mcap, std::max(48, 2 * c->last_degree + 8));
+    EREM_TRY(prepare_dd(c, S, M_avail, s));
+    bool ok = true;
+    for (int k = 0; k < S; ++k) {
+      const double* u = src;
+      if (k > 0) {
+        launch_japply_add(c, c->w, src, c->u, s);
+        u = c->u;
+      }
+      StopParams sp{};
+      sp.delta = delta;
+      sp.ncells = (double)c->N;
+      sp.pow10 = std::pow(10.0, o.p_order);
+      sp.tol_a = o.tol_a;
+      sp.tol_r = o.tol_r;
+      sp.window = o.avg_window;
+      sp.m_max = replay ? o.replay[1 + k] : o.m_max;
+      sp.replay = replay ? 1 : 0;
+      const double d0 = c->dd_cache[S].d[0];
+      launch_leja_init(c, u, d0, sp, s);
+      int m = 1, qin = 0, degree = 0;
+      const int forced = replay ? o.replay[1 + k] : 0;
+      int chunk = forced ? forced : std::max(4, c->last_degree + 2);
+      while (true) {
+        const int end = forced ? forced : std::min(M_avail, m + chunk - 1);
+        for (int mm = m; mm <= end; ++mm) {
+          if (o.time_terms) cudaEventRecord(c->ev[2 * mm], s);
+          launch_leja_term(c, mm, qin, cg, s);
+          if (o.time_terms) cudaEventRecord(c->ev[2 * mm + 1], s);
+          qin ^= 1;
+        }
+        EREM_TRY(check_launch(c, "leja term"));
+        EREM_TRY(read_ctrl(c, s));
+        EREM_TRY(check_flags(c));
+        const Ctrl& h = *c->ctrl_h;
+        if (h.nonfinite) return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate");
+        if (forced) {
+          degree = forced;
+          break;
+        }
+        if (h.done && !h.fail) {
+          degree = h.degree;
+          break;
+        }
+        if (h.fail || end >= o.m_max) {
+          ok = false;
+          break;
+        }
+        if (end >= M_avail) {  // table exhausted below m_max: extend it
+          M_avail = mcap;
+          EREM_TRY(prepare_dd(c, S, M_avail, s));
+        }
+        m = end + 1;
+        chunk = 8;
+      }
+      if (!ok) break;
+      if (o.time_terms) {
+        for (int mm = 1; mm <= degree; ++mm) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, c->ev[2 * mm], c->ev[2 * mm + 1]) == cudaSuccess) {
+            t_terms += ms;
+            ++n_timed;
+          }
+        }
+      }
+      degrees[k] = degree;
+      c->last_degree = degree;
+      if (st) st->err_est = c->ctrl_h->err;
+      if (k + 1 < S) launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
+    }
+    if (!ok) continue;
+    launch_finish(c, out, base, S > 1 ? c->w : nullptr, c->P, delta, s);
+    EREM_TRY(check_launch(c, "finish"));
+    if (st) {
+      st->substeps = S;
+      st->degree_total = 0;
+      for (int k = 0; k < 64; ++k) st->degrees[k] = k < S ? degrees[k] : 0;
+      for (int k = 0; k < S; ++k) st->degree_total += degrees[k];
+      st->t_terms_ms = t_terms;
+      st->n_terms_timed = n_timed;
+    }
+    return EREM_OK;
+  }
+  return fail(c, EREM_ENOTCONV,
+              "Leja interpolation did not meet the stopping test within m_max terms after " +
+                  std::to_string(o.max_doublings) + " substep doublings");
+}
+
+// Assemble face fluxes (if fields changed or the fluid laws depend on T),
+// the cell form of J, G(T^n) and ||T^n||_inf; read alpha, beta back.
+erem_status assemble(erem_ctx* c, bool faces, cudaStream_t s) {
+  if (faces) launch_faces(c, s);
+  launch_cellJ(c, s);
+  launch_rhs(c, c->Tn, c->vrhs, 1, s);
+  EREM_TRY(check_launch(c, "assembly"));
+  EREM_TRY(read_ctrl(c, s));
+  EREM_TRY(check_flags(c));
+  c->alpha = c->dt * c->ctrl_h->gmin;
+  c->beta = c->dt * c->ctrl_h->gmax;
+  if (!std::isfinite(c->alpha) || !std::isfinite(c->beta))
+    return fail(c, EREM_ENONFINITE, "non-finite spectral interval");
+  focal_map(c);
+  return EREM_OK;
+}
+
+erem_status clear_flags(erem_ctx* c, cudaStream_t s) {
+  EREM_CUDA(c, cudaMemsetAsync(&c->ctrl->flags, 0, sizeof(int), s));
+  return EREM_OK;
+}
+
+erem_status load_fields(erem_ctx* c, const double* p, const double* lnk, const double* phi,
+                        const double* lam, cudaStream_t s) {
+  double *dp, *dk, *dphi, *dl;
+  EREM_TRY(resolve(c, 1, p, true, s, &dp));
+  EREM_TRY(resolve(c, 2, lnk, true, s, &dk));
+  EREM_TRY(resolve(c, 3, phi, true, s, &dphi));
+  EREM_TRY(resolve(c, 4, lam, true, s, &dl));
+  launch_pack(c, dp, c->p, s);
+  launch_pack(c, dk, c->lnk, s);
+  launch_pack(c, dphi, c->phi, s);
+  launch_pack(c, dl, c->lam, s);
+  return check_launch(c, "pack fields");
+}
+
+// Shared front half of erem_step / rosm_step: T^n into the context, fields,
+// assembly when needed, G(T^n) into vrhs.  *Tdev receives T's device view.
+erem_status prepare_step(erem_ctx* c, double* T, const double* p, const double* lnk,
+                         const double* phi, const double* lam, double dt, bool need_interval,
+                         cudaStream_t s, double** Tdev) {
+  if (!T) return fail(c, EREM_EINVAL, "T is NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, EREM_EINVAL, "dt must be finite and > 0");
+  const int nnull = (p == nullptr) + (lnk == nullptr) + (phi == nullptr) + (lam == nullptr);
+  if (nnull != 0 && nnull != 4)
+    return fail(c, EREM_EINVAL, "pass all of p, lnk, phi, lambda or none of them");
+  const bool fields = nnull == 0;
+  if (!fields && !c->have_state)
+    return fail(c, EREM_EINVAL, "no stored fields: pass p, lnk, phi, lambda (or call erem_set_state)");
+  EREM_TRY(clear_flags(c, s));
+  EREM_TRY(resolve(c, 0, T, true, s, Tdev));
+  launch_pack(c, *Tdev, c->Tn, s);
+  if (fields) EREM_TRY(load_fields(c, p, lnk, phi, lam, s));
+  const bool tdep = c->phys.fluid_model != 0;
+  const double old_dt = c->dt;
+  c->dt = dt;
+  if (fields || tdep || !c->have_state) {
+    EREM_TRY(assemble(c, fields || tdep, s));
+    c->jl_valid = false;
+    c->have_state = true;
+  } else {
+    launch_rhs(c, c->Tn, c->vrhs, 1, s);
+    EREM_TRY(check_launch(c, "rhs"));
+    if (dt != old_dt) {
+      c->alpha = dt * c->ctrl_h->gmin;
+      c->beta = dt * c->ctrl_h->gmax;
+      focal_map(c);
+      c->jl_valid = false;
+    }
+  }
+  if (need_interval && !c->jl_valid) {
+    launch_scale_jl(c, c->dt / c->gam, s);
+    EREM_TRY(check_launch(c, "scale"));
+    c->jl_valid = true;
+    c->dd_cache.clear();
+    c->dd_tag_S = -1;
+  }
+  return EREM_OK;
+}
+
+erem_status finish_staged(erem_ctx* c, double* host_T, const double* dev_T, cudaStream_t s) {
+  if (dev_T != host_T)
+    EREM_CUDA(c, cudaMemcpyAsync(host_T, dev_T, (size_t)c->N * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+  EREM_CUDA(c, cudaStreamSynchronize(s));
+  return EREM_OK;
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+void fill_interval(const erem_ctx* c, erem_stats* st) {
+  if (!st) return;
+  st->alpha = c->alpha;
+  st->beta = c->beta;
+}
+
+// BiCGSTAB solve of (sigma I - J) x = b (b padded); x in kv[0].
+erem_status bicg_solve(erem_ctx* c, const double* b, double sigma, double tol, int maxit,
+                       cudaStream_t s, int* iters, double* resid) {
+  launch_bicg_init(c, b, sigma, tol, s);
+  int it = 0;
+  while (true) {
+    EREM_TRY(read_ctrl(c, s));
+    if (c->ctrl_h->lin_done || it >= maxit) break;
+    const int n = std::min(8, maxit - it);
+    for (int k = 0; k < n; ++k) launch_bicg_iter(c, sigma, s);
+    EREM_TRY(check_launch(c, "bicgstab"));
+    it += n;
+  }
+  const Ctrl& h = *c->ctrl_h;
+  *iters = h.lin_it;
+  *resid = h.lin[K_BB] > 0 ? std::sqrt(h.lin[K_RR] / h.lin[K_BB]) : 0.0;
+  if (h.lin_break && !(h.lin[K_RR] <= h.lin[K_TOL2]))
+    return fail(c, EREM_ENOTCONV, "BiCGSTAB breakdown");
+  if (!h.lin_done) return fail(c, EREM_ENOTCONV, "BiCGSTAB did not converge within maxit");
+  return EREM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void erem_default_leja_opts(erem_leja_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol_a = 1e-6;
+  o->tol_r = 1e-6;
+  o->p_order = 2;
+  o->m_max = 150;
+  o->max_doublings = 6;
+  o->avg_window = 5;
+}
+
+erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_precision prec,
+                        erem_ctx** out) {
+  if (!out) return EREM_EINVAL;
+  *out = nullptr;
+  if (!grid || !phys) return EREM_EINVAL;
+  const erem_grid g = *grid;
+  if ((g.dim != 2 && g.dim != 3) || g.nx < 1 || g.ny < 1 || g.nz < 1 || (g.dim == 2 && g.nz != 1))
+    return EREM_EINVAL;
+  if (!(g.lx > 0) || !(g.ly > 0) || (g.dim == 3 && !(g.lz > 0))) return EREM_EINVAL;
+  if (prec != EREM_FP64 && prec != EREM_FP32_BULK) return EREM_EINVAL;
+  if (!(phys->rhoc_f >= 0) || !(phys->rhoc_s >= 0) || !std::isfinite(phys->head_left) ||
+      !std::isfinite(phys->head_right) || !std::isfinite(phys->T_inflow) ||
+      (phys->fluid_model != 0 && phys->fluid_model != 1))
+    return EREM_EINVAL;
+  const long long px = ((long long)g.nx + 3) / 4 * 4;
+  const long long Np = px * g.ny * g.nz;
+  if (Np >= (1LL << 31) - 1024) return EREM_EINVAL;
+  erem_ctx* c = new erem_ctx();
+  c->grid = g;
+  c->phys = *phys;
+  c->prec = prec;
+  c->dim = g.dim;
+  c->nx = g.nx;
+  c->ny = g.ny;
+  c->nz = g.nz;
+  c->px = (int)px;
+  c->N = (long long)g.nx * g.ny * g.nz;
+  c->Np = Np;
+  c->hx = g.lx / g.nx;
+  c->hy = g.ly / g.ny;
+  c->hz = g.dim == 3 ? g.lz / g.nz : 1.0;
+  c->vol = c->hx * c->hy * c->hz;
+  c->ax = c->hy * c->hz;
+  c->ay = c->hx * c->hz;
+  c->az = c->hx * c->hy;
+  auto bail = [&](erem_status st) {
+    erem_destroy(c);
+    return st;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bail(EREM_ECUDA);
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return bail(EREM_ECUDA);
+  c->red_blocks = c->sm_count * 8;
+  const size_t np = (size_t)Np, nf = (size_t)g.ny * g.nz;
+  const size_t esz = prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
+  erem_status st = EREM_OK;
+  auto A = [&](double** p, size_t n) {
+    if (st == EREM_OK) st = dalloc_t(c, p, n);
+  };
+  A(&c->lnk, np); A(&c->phi, np); A(&c->lam, np); A(&c->p, np);
+  A(&c->Lx, np); A(&c->Ly, np); A(&c->Fx, np); A(&c->Fy, np); A(&c->icap, np);
+  A(&c->LD0, nf); A(&c->F0, nf);
+  if (g.dim == 3) { A(&c->Lz, np); A(&c->Fz, np); }
+  const int nc = g.dim == 3 ? 7 : 5;
+  for (int k = 0; k < nc; ++k) {
+    A(&c->jc[k], np);
+    if (st == EREM_OK) st = dalloc(c, &c->jl[k], np * esz);
+  }
+  A(&c->Tn, np); A(&c->vrhs, np); A(&c->vin, np); A(&c->w, np); A(&c->u, np); A(&c->P, np);
+  for (int k = 0; k < 2; ++k)
+    if (st == EREM_OK) st = dalloc(c, &c->q[k], np * esz);
+  A(&c->red_part, (size_t)c->red_blocks * kRedSlots);
+  A(&c->dd_dev, (size_t)kMaxTerms + 2);
+  if (st == EREM_OK) st = dalloc(c, (void**)&c->red_cnt, sizeof(unsigned) * 4);
+  if (st == EREM_OK) st = dalloc(c, (void**)&c->ctrl, sizeof(Ctrl));
+  if (st != EREM_OK) return bail(st);
+  if (cudaMallocHost((void**)&c->ctrl_h, sizeof(Ctrl)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->dd_h, sizeof(double) * (kMaxTerms + 2)) != cudaSuccess)
+    return bail(EREM_ENOMEM);
+  std::memset(c->ctrl_h, 0, sizeof(Ctrl));
+  if (ensure_leja(c, 160) != EREM_OK) return bail(EREM_ECUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(EREM_ECUDA);
+  *out = c;
+  return EREM_OK;
+}
+
+erem_status erem_destroy(erem_ctx* c) {
+  if (!c) return EREM_OK;
+  double* dp[] = {c->lnk, c->phi, c->lam, c->p, c->Lx, c->Ly, c->Lz, c->Fx, c->Fy, c->Fz,
+                  c->icap, c->LD0, c->F0, c->Tn, c->vrhs, c->vin, c->w, c->u, c->P,
+                  c->red_part, c->xi_dev, c->dd_dev};
+  for (double* p : dp)
+    if (p) cudaFree(p);
+  for (int k = 0; k < 7; ++k) {
+    if (c->jc[k]) cudaFree(c->jc[k]);
+    if (c->jl[k]) cudaFree(c->jl[k]);
+  }
+  for (int k = 0; k < 2; ++k)
+    if (c->q[k]) cudaFree(c->q[k]);
+  for (double* p : c->kv)
+    if (p) cudaFree(p);
+  for (double* p : c->stage)
+    if (p) cudaFree(p);
+  if (c->red_cnt) cudaFree(c->red_cnt);
+  if (c->ctrl) cudaFree(c->ctrl);
+  if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
+  if (c->dd_h) cudaFreeHost(c->dd_h);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+  return EREM_OK;
+}
+
+erem_status erem_set_physics(erem_ctx* c, const erem_physics* phys) {
+  if (!c) return EREM_EINVAL;
+  if (!phys || !(phys->rhoc_f >= 0) || !(phys->rhoc_s >= 0) ||
+      (phys->fluid_model != 0 && phys->fluid_model != 1))
+    return fail(c, EREM_EINVAL, "bad physics");
+  c->phys = *phys;
+  c->have_state = false;  // the stored J no longer matches
+  return EREM_OK;
+}
+
+const char* erem_last_error(const erem_ctx* c) { return c ? c->err.c_str() : kNullCtxMsg; }
+
+erem_status pressure_solve(erem_ctx* c, const double* lnk, const double* T, double* p, double tol,
+                           int maxit, erem_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!lnk || !p) return fail(c, EREM_EINVAL, "lnk and p must not be NULL");
+  if (!(tol > 0.0) || maxit < 0) return fail(c, EREM_EINVAL, "tol must be > 0 and maxit >= 0");
+  EREM_TRY(ensure_krylov(c));
+  EREM_TRY(clear_flags(c, s));
+  double *dk, *dT = nullptr, *dp;
+  EREM_TRY(resolve(c, 5, lnk, true, s, &dk));
+  if (T) EREM_TRY(resolve(c, 6, T, true, s, &dT));
+  EREM_TRY(resolve(c, 7, p, true, s, &dp));
+  launch_pres_faces(c, dk, dT, s);
+  launch_pack(c, dp, c->kv[0], s);
+  launch_cg_init(c, tol, s);
+  EREM_TRY(check_launch(c, "pressure set-up"));
+  EREM_TRY(read_ctrl(c, s));
+  EREM_TRY(check_flags(c));
+  int k = 0;
+  while (!c->ctrl_h->lin_done && k < maxit) {
+    const int n = std::min(32, maxit - k);
+    for (int j = 0; j < n; ++j) launch_cg_iter(c, k + j, s);
+    EREM_TRY(check_launch(c, "cg"));
+    k += n;
+    EREM_TRY(read_ctrl(c, s));
+  }
+  const Ctrl h = *c->ctrl_h;
+  const double resid = h.lin[K_BB] > 0 ? std::sqrt(h.lin[K_RR] / h.lin[K_BB]) : 0.0;
+  launch_finish(c, dp, c->kv[0], nullptr, c->kv[0], 0.0, s);
+  launch_pres_post(c, dk, dT, s);
+  EREM_TRY(check_launch(c, "pressure post"));
+  EREM_TRY(finish_staged(c, p, dp, s));
+  EREM_TRY(read_ctrl(c, s));
+  if (st) {
+    st->lin_iters = h.lin_it;
+    st->lin_resid = resid;
+    st->flux_in = c->ctrl_h->flux_in;
+    st->vmax = c->ctrl_h->vmax;
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  if (h.lin_break && !(h.lin[K_RR] <= h.lin[K_TOL2]))
+    return fail(c, EREM_ENOTCONV, "CG breakdown (matrix not positive definite?)");
+  if (!h.lin_done) return fail(c, EREM_ENOTCONV, "CG did not converge within maxit");
+  return EREM_OK;
+}
+
+erem_status erem_set_state(erem_ctx* c, const double* T, const double* p, const double* lnk,
+                           const double* phi, const double* lam, double dt, void* stream) {
+  if (!c) return EREM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!T || !p || !lnk || !phi || !lam) return fail(c, EREM_EINVAL, "NULL field");
+  double* Td;
+  c->have_state = false;
+  EREM_TRY(prepare_step(c, const_cast<double*>(T), p, lnk, phi, lam, dt, true, s, &Td));
+  EREM_CUDA(c, cudaStreamSynchronize(s));
+  return EREM_OK;
+}
+
+erem_status phi1_apply(erem_ctx* c, const double* v, double* out, const erem_leja_opts* opts,
+                       erem_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->have_state || !c->jl_valid) return fail(c, EREM_EINVAL, "phi1_apply before erem_set_state");
+  if (!v || !out) return fail(c, EREM_EINVAL, "NULL vector");
+  Opts o;
+  EREM_TRY(parse_opts(c, opts, &o));
+  EREM_TRY(clear_flags(c, s));
+  double *dv, *dout;
+  EREM_TRY(resolve(c, 5, v, true, s, &dv));
+  launch_pack(c, dv, c->vin, s);
+  EREM_TRY(resolve(c, 6, out, false, s, &dout));
+  EREM_TRY(run_phi1(c, c->vin, nullptr, dout, o, st, s));
+  EREM_TRY(finish_staged(c, out, dout, s));
+  fill_interval(c, st);
+  if (st) {
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  return EREM_OK;
+}
+
+erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk,
+                      const double* phi, const double* lam, double dt, const erem_leja_opts* opts,
+                      erem_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  Opts o;
+  EREM_TRY(parse_opts(c, opts, &o));
+  double* Td = nullptr;
+  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td));
+  EREM_TRY(run_phi1(c, c->vrhs, c->Tn, Td, o, st, s));
+  EREM_TRY(finish_staged(c, T, Td, s));
+  fill_interval(c, st);
+  if (st) {
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  return EREM_OK;
+}
+
+erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk,
+                      const double* phi, const double* lam, double dt, erem_rosm_scheme scheme,
+                      double lin_tol, int maxit, erem_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (scheme != EREM_ROSM1 && scheme != EREM_ROSM_HALF && scheme != EREM_ROS2)
+    return fail(c, EREM_EINVAL, "unknown Rosenbrock scheme");
+  if (!(lin_tol > 0.0) || maxit < 1) return fail(c, EREM_EINVAL, "lin_tol > 0 and maxit >= 1");
+  EREM_TRY(ensure_krylov(c));
+  double* Td = nullptr;
+  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, false, s, &Td));
+  int it_total = 0, it = 0;
+  double res = 0.0, r = 0.0;
+  if (scheme == EREM_ROS2) {
+    // ROS2(1), Table ros2: gamma = 1 + 1/sqrt(2), a21 = 1/gamma, c21 = 2/gamma,
+    // b = (3/(2 gamma), 1/(2 gamma)); stage matrix I/(dt gamma) - J.
+    const double gam = 1.0 + 1.0 / std::sqrt(2.0);
+    const double a21 = 1.0 / gam, c21 = 2.0 / gam, b1 = 3.0 / (2.0 * gam), b2 = 1.0 / (2.0 * gam);
+    const double sigma = 1.0 / (dt * gam);
+    double* k1 = c->kv[10];
+    double* Y = c->kv[11];
+    EREM_TRY(bicg_solve(c, c->vrhs, sigma, lin_tol, maxit, s, &it, &r));
+    it_total += it;
+    res = std::max(res, r);
+    launch_lincomb(c, k1, 1.0, c->kv[0], 0.0, c->kv[0], s);
+    launch_lincomb(c, Y, 1.0, c->Tn, a21, k1, s);
+    launch_rhs(c, Y, c->vin, 0, s);
+    launch_lincomb(c, c->vin, 1.0, c->vin, -c21 / dt, k1, s);
+    EREM_TRY(check_launch(c, "ros2 stage"));
+    EREM_TRY(bicg_solve(c, c->vin, sigma, lin_tol, maxit, s, &it, &r));
+    it_total += it;
+    res = std::max(res, r);
+    // T^{n+1} = T^n + b1 k1 + b2 k2
+    launch_lincomb(c, c->u, b1, k1, b2, c->kv[0], s);
+    launch_finish(c, Td, c->Tn, nullptr, c->u, 1.0, s);
+  } else {
+    // ROSM(gamma), eq. ROS: (I/(dt gamma) - J) k = G, T^{n+1} = T^n + k / gamma
+    const double gam = scheme == EREM_ROSM1 ? 1.0 : 0.5;
+    EREM_TRY(bicg_solve(c, c->vrhs, 1.0 / (dt * gam), lin_tol, maxit, s, &it, &r));
+    it_total += it;
+    res = r;
+    launch_finish(c, Td, c->Tn, nullptr, c->kv[0], 1.0 / gam, s);
+  }
+  EREM_TRY(check_launch(c, "rosm finish"));
+  EREM_TRY(read_ctrl(c, s));
+  EREM_TRY(check_flags(c));
+  EREM_TRY(finish_staged(c, T, Td, s));
+  if (st) {
+    fill_interval(c, st);
+    st->lin_iters = it_total;
+    st->lin_resid = res;
+    st->substeps = 0;
+    st->degree_total = 0;
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  return EREM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Internal declarations of the EREM library: the context, the device
+// control block and the kernel launchers (defined in kernels.cu, driven by
+// abi.cpp).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/erem.h"
+
+namespace erem {
+
+constexpr int kThreads = 256;      // threads per block of every kernel
+constexpr int kMaxTerms = 4096;    // largest Leja degree a context accepts
+constexpr int kRedSlots = 4;       // reduction values per block
+
+// Bits of Ctrl::flags raised by the set-up kernels.
+enum : int { FLAG_NONFINITE = 1, FLAG_BAD_INPUT = 2 };
+
+// Parameters of the Leja stopping test of one substep (§4.2).
+struct StopParams {
+  double delta;    // substep length dt / s
+  double ncells;   // N, the number of real cells
+  double pow10;    // 10^p
+  double tol_a, tol_r;
+  int window;      // estimates averaged
+  int m_max;       // degree at which the substep fails
+  int replay;      // nonzero: never stop, the host sets the degree
+  int pad;
+};
+
+// Krylov scalars kept on the device (indices into Ctrl::lin).
+enum : int {
+  K_RZ = 0, K_RR, K_BB, K_ALPHA, K_BETA, K_DAD, K_RHO, K_RHO_PREV, K_OMEGA, K_SS, K_TOL2,
+  K_NLIN = 16
+};
+
+// Device control block: written by the last block of a reducing kernel,
+// read by later kernels and, in small pieces, by the host.
+struct Ctrl {
+  int done;        // Leja substep finished (stop, failure or non-finite)
+  int degree;      // degree m at which the stopping test passed
+  int fail;        // m_max reached without passing
+  int nonfinite;   // non-finite estimate met
+  int m_last;      // last term evaluated
+  int flags;       // FLAG_* from the set-up kernels
+  int lin_done;    // linear solver converged (or broke down)
+  int lin_it;      // linear solver iterations
+  int lin_break;   // linear solver breakdown
+  int pad0;
+  double err;      // mean error estimate at the last term
+  double yinf;     // ||T^n||_inf of the current state
+  double gmin, gmax;   // Gershgorin bounds of J (before the factor dt)
+  double flux_in, vmax;
+  StopParams sp;
+  double lin[K_NLIN];
+  double e[kMaxTerms + 2];  // error estimates e_1 .. e_m of the substep
+};
+
+struct DDEntry {
+  double c = 0, gamma = 0;
+  int M = -1;
+  std::vector<double> d;
+};
+
+}  // namespace erem
+
+struct erem_ctx {
+  erem_grid grid{};
+  erem_physics phys{};
+  erem_precision prec{};
+  int dim = 2, nx = 1, ny = 1, nz = 1, px = 4;
+  long long N = 0, Np = 0;   // real and padded cell counts
+  double hx = 1, hy = 1, hz = 1, vol = 1, ax = 1, ay = 1, az = 1;
+  int device = 0, sm_count = 1, red_blocks = 1;
+  std::string err;
+
+  // stored fields (padded, FP64)
+  double *lnk = nullptr, *phi = nullptr, *lam = nullptr, *p = nullptr;
+  // face form: conduction and (rho c)_f * Darcy flux through the + faces,
+  // inverse capacity, and the x = 0 faces (ny*nz entries)
+  double *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;
+  double *Fx = nullptr, *Fy = nullptr, *Fz = nullptr;
+  double *icap = nullptr, *LD0 = nullptr, *F0 = nullptr;
+  // cell form of J (FP64): D, W, E, S, N, B, T
+  double* jc[7] = {};
+  // Leja copy of J scaled by dt / gamma, in the precision of the context
+  void* jl[7] = {};
+  // vectors
+  double *Tn = nullptr, *vrhs = nullptr, *vin = nullptr, *w = nullptr, *u = nullptr, *P = nullptr;
+  void* q[2] = {};
+  // linear solvers (allocated on first use)
+  double* kv[12] = {};
+  // staging for host pointers (allocated on first use)
+  double* stage[8] = {};
+  // reductions and control
+  double* red_part = nullptr;
+  unsigned* red_cnt = nullptr;
+  erem::Ctrl* ctrl = nullptr;       // device
+  erem::Ctrl* ctrl_h = nullptr;     // pinned host mirror
+  double* xi_dev = nullptr;         // Leja points on the device
+  double* dd_dev = nullptr;         // divided differences of the active substep level
+  double* dd_h = nullptr;           // pinned staging of dd
+  int xi_cap = 0;
+  int dd_tag_S = -1, dd_tag_M = -1;
+  std::vector<double> xi_host;
+  std::map<int, erem::DDEntry> dd_cache;  // substep count -> table
+
+  // state
+  bool have_state = false;
+  bool jl_valid = false;
+  double dt = 0, alpha = 0, beta = 0;
+  double cfoc = 0, gam = 0;   // c and gamma of [alpha, beta]
+  int last_degree = 0;
+
+  // kernels launched since the current ABI call began
+  mutable long long launches = 0;
+
+  // timing
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t ev_call[2] = {nullptr, nullptr};
+};
+
+namespace erem {
+
+// ---------------------------------------------------------------------------
+// launchers (kernels.cu)
+// ---------------------------------------------------------------------------
+int grid_for(const erem_ctx* c, long long items);
+
+void launch_pack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s);
+void launch_finish(const erem_ctx* c, double* out, const double* base, const double* w,
+                   const double* P, double delta, cudaStream_t s);
+void launch_faces(const erem_ctx* c, cudaStream_t s);
+void launch_cellJ(const erem_ctx* c, cudaStream_t s);
+void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s);
+void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cudaStream_t s);
+void launch_japply_add(const erem_ctx* c, const double* x, const double* v, double* out,
+                       cudaStream_t s);
+void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
+                      cudaStream_t s);
+void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
+void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,
+                 cudaStream_t s);
+void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,
+                    const double* y, cudaStream_t s);
+
+// pressure (CG)
+void launch_pres_faces(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s);
+void launch_cg_init(const erem_ctx* c, double tol, cudaStream_t s);
+void launch_cg_iter(const erem_ctx* c, int k, cudaStream_t s);
+void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s);
+
+// stage solver (BiCGSTAB) for (sigma I - J) x = b
+void launch_bicg_init(const erem_ctx* c, const double* b, double sigma, double tol,
+                      cudaStream_t s);
+void launch_bicg_iter(const erem_ctx* c, double sigma, cudaStream_t s);
+
+// host scalar side (leja_host.cpp)
+void leja_table(int M, std::vector<double>* out);
+int divided_differences(int M, const double* xi, double c, double gamma, double* d);
+
+}  // namespace erem

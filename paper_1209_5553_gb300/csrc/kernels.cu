@@ -1,0 +1,1246 @@
+// Device kernels of the EREM library for sm_103a (GB300).
+//
+// Data layout: every cell-centred device array is padded along x to a pitch
+// px (a multiple of 4 cells), index ip = ix + px*(iy + ny*iz).  Pad cells
+// hold 0 in every array and 0 coefficients, so the Leja sweep can load and
+// store whole 128-bit vectors without a ragged-edge branch; they stay 0
+// through every kernel.  Arrays that come straight from the caller (ABI
+// inputs) are unpadded, index i = ix + nx*(iy + ny*iz).
+//
+// Reductions are deterministic: each block writes one partial per value,
+// the last block to finish (atomic ticket) sums the partials in block order
+// and writes the result into the control block.  Min/max reductions are
+// exact in any order.
+#include <cstdint>
+
+#include "erem_internal.h"
+
+namespace erem {
+namespace {
+
+constexpr int NT = kThreads;
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide reduction; the result is valid in thread 0.  `op` 0 = sum,
+// 1 = min, 2 = max.  Safe to call repeatedly (syncs before reusing smem).
+template <int OP>
+__device__ double block_reduce(double v, double* sh) {
+  v = OP == 0 ? warp_sum(v) : (OP == 1 ? warp_min(v) : warp_max(v));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (NT / 32) ? sh[threadIdx.x]
+                                       : (OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY));
+    w = OP == 0 ? warp_sum(w) : (OP == 1 ? warp_min(w) : warp_max(w));
+    v = w;
+  }
+  return v;
+}
+
+// Publish this block's partials; returns true in every thread of the last
+// block to arrive.  part has kRedSlots doubles per block.
+__device__ bool publish_partials(double* part, unsigned* cnt, const double* vals, int nv) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nv; ++k) part[blockIdx.x * kRedSlots + k] = vals[k];
+    __threadfence();
+    const unsigned t = atomicAdd(cnt, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Sum (or min/max) of partial k over all blocks, in block order; thread 0.
+template <int OP>
+__device__ double gather_partials(const double* part, int k, double* sh) {
+  double v = OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY);
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
+    const double x = __ldcg(part + b * kRedSlots + k);
+    v = OP == 0 ? v + x : (OP == 1 ? fmin(v, x) : fmax(v, x));
+  }
+  return block_reduce<OP>(v, sh);
+}
+
+struct Geo {
+  int nx, ny, nz, px, dim;
+  int N, Np;
+  int plane;  // px * ny
+};
+
+__device__ __forceinline__ void cell_of(int i, const Geo& g, int& ix, int& iy, int& iz, int& ip) {
+  const int r = i / g.nx;
+  ix = i - r * g.nx;
+  iy = r % g.ny;
+  iz = r / g.ny;
+  ip = ix + g.px * r;
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// Fluid laws (fluid_model = 1): rho/rho0 = 1 - 3e-4 (T - 20),
+// mu/mu0 = exp(-0.02 (T - 20)); X = rho/rho0 * T and its T-derivative.
+__device__ __forceinline__ double rho_rel(double T, int fm) { return fm ? 1.0 - 3e-4 * (T - 20.0) : 1.0; }
+__device__ __forceinline__ double mu_rel(double T, int fm) { return fm ? exp(-0.02 * (T - 20.0)) : 1.0; }
+__device__ __forceinline__ double Xof(double T, int fm) { return rho_rel(T, fm) * T; }
+__device__ __forceinline__ double dXof(double T, int fm) { return fm ? rho_rel(T, fm) - 3e-4 * T : 1.0; }
+
+// two-point harmonic transmissibility |s| ki kj / (ki d + kj d), uniform d
+__device__ __forceinline__ double harm(double area, double d, double ki, double kj) {
+  const double den = ki * d + kj * d;
+  return den != 0.0 ? area * ki * kj / den : 0.0;
+}
+
+struct Phys {
+  double rhoc_f, rhoc_s, head_left, head_right, T_in;
+  int fm;
+  double hx, hy, hz, vol, ax, ay, az;
+};
+
+// ---------------------------------------------------------------------------
+// layout conversion
+// ---------------------------------------------------------------------------
+__global__ void k_pack(const double* __restrict__ src, double* __restrict__ dst, Geo g,
+                       int* flags) {
+  int bad = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double v = src[i];
+    bad |= !finite(v);
+    dst[ip] = v;
+  }
+  if (bad && flags) atomicOr(flags, FLAG_NONFINITE);
+}
+
+// out[i] = base[ip] + w[ip] + delta * P[ip]   (base, w may be null)
+__global__ void k_finish(double* __restrict__ out, const double* __restrict__ base,
+                         const double* __restrict__ w, const double* __restrict__ P, double delta,
+                         Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    double v = delta * P[ip];
+    if (w) v += w[ip];
+    if (base) v += base[ip];
+    out[i] = v;
+  }
+}
+
+// w = (first ? 0 : w) + delta * P over padded arrays
+__global__ void k_axpy(double* __restrict__ w, const double* __restrict__ P, double delta,
+                       int first, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
+    w[i] = first ? delta * P[i] : w[i] + delta * P[i];
+}
+
+__global__ void k_lincomb(double* __restrict__ out, double a, const double* __restrict__ x,
+                          double b, const double* __restrict__ y, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
+    out[i] = a * x[i] + b * y[i];
+}
+
+// ---------------------------------------------------------------------------
+// face form of the heat operator (§3.1): conduction transmissibilities and
+// (rho c)_f * Darcy fluxes through the + faces of every cell, the x = 0
+// faces, and 1 / (C |Omega|).
+// ---------------------------------------------------------------------------
+struct FaceOut {
+  double *Lx, *Ly, *Lz, *Fx, *Fy, *Fz, *icap, *LD0, *F0;
+};
+struct FieldIn {
+  const double *lnk, *phi, *lam, *p, *T;  // padded
+};
+
+__global__ void k_faces(FieldIn in, FaceOut o, Geo g, Phys ph, int* flags) {
+  int bad = 0, inval = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double Ti = in.T[ip];
+    const double mi = exp(in.lnk[ip]) / mu_rel(Ti, ph.fm);
+    const double li = in.lam[ip];
+    const double pi = in.p[ip];
+    const double phi = in.phi[ip];
+    bad |= !finite(mi) | !finite(li) | !finite(pi) | !finite(phi) | !finite(Ti);
+    inval |= (li < 0.0) | (phi < 0.0) | (phi > 1.0);
+    // + x face
+    if (ix < g.nx - 1) {
+      const int j = ip + 1;
+      const double mj = exp(in.lnk[j]) / mu_rel(in.T[j], ph.fm);
+      o.Lx[ip] = harm(ph.ax, 0.5 * ph.hx, li, in.lam[j]);
+      o.Fx[ip] = ph.rhoc_f * harm(ph.ax, 0.5 * ph.hx, mi, mj) * (pi - in.p[j]);
+    } else {  // x = 1: Dirichlet pressure, outflow face without conduction
+      o.Lx[ip] = 0.0;
+      o.Fx[ip] = ph.rhoc_f * (ph.ax * mi / (0.5 * ph.hx)) * (pi - ph.head_right);
+    }
+    // + y face
+    if (iy < g.ny - 1) {
+      const int j = ip + g.px;
+      const double mj = exp(in.lnk[j]) / mu_rel(in.T[j], ph.fm);
+      o.Ly[ip] = harm(ph.ay, 0.5 * ph.hy, li, in.lam[j]);
+      o.Fy[ip] = ph.rhoc_f * harm(ph.ay, 0.5 * ph.hy, mi, mj) * (pi - in.p[j]);
+    } else {
+      o.Ly[ip] = 0.0;
+      o.Fy[ip] = 0.0;
+    }
+    if (g.dim == 3) {
+      if (iz < g.nz - 1) {
+        const int j = ip + g.plane;
+        const double mj = exp(in.lnk[j]) / mu_rel(in.T[j], ph.fm);
+        o.Lz[ip] = harm(ph.az, 0.5 * ph.hz, li, in.lam[j]);
+        o.Fz[ip] = ph.rhoc_f * harm(ph.az, 0.5 * ph.hz, mi, mj) * (pi - in.p[j]);
+      } else {
+        o.Lz[ip] = 0.0;
+        o.Fz[ip] = 0.0;
+      }
+    }
+    if (ix == 0) {  // x = 0: Dirichlet pressure and temperature
+      const int r = iy + g.ny * iz;
+      o.LD0[r] = ph.ax * li / (0.5 * ph.hx);
+      o.F0[r] = ph.rhoc_f * (ph.ax * mi / (0.5 * ph.hx)) * (ph.head_left - pi);
+    }
+    const double C = phi * ph.rhoc_f + (1.0 - phi) * ph.rhoc_s;
+    inval |= !(C > 0.0);
+    o.icap[ip] = 1.0 / (C * ph.vol);
+  }
+  if (bad) atomicOr(flags, FLAG_NONFINITE);
+  if (inval) atomicOr(flags, FLAG_BAD_INPUT);
+}
+
+// ---------------------------------------------------------------------------
+// cell form of J = D_T G (eq. linear): per cell the diagonal and the six
+// neighbour couplings, from the derivative of every face flux; plus the
+// Gershgorin bounds min(J_ii - R_i), max(J_ii + R_i) (§4.2).
+// ---------------------------------------------------------------------------
+struct FaceIn {
+  const double *Lx, *Ly, *Lz, *Fx, *Fy, *Fz, *icap, *LD0, *F0;
+};
+struct JOut {
+  double* c[7];  // D W E S N B T
+};
+
+__global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, Phys ph,
+                        double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  double gmin = INFINITY, gmax = -INFINITY;
+  int bad = 0;
+  const int fm = ph.fm;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double dXi = dXof(T[ip], fm);
+    double D = 0.0, W = 0.0, E = 0.0, S = 0.0, Nn = 0.0, B = 0.0, Tt = 0.0;
+    // + x face
+    {
+      const double F = f.Fx[ip];
+      if (ix < g.nx - 1) {
+        D -= f.Lx[ip] + (F >= 0.0 ? F * dXi : 0.0);
+        E = f.Lx[ip] + (F < 0.0 ? -F * dXof(T[ip + 1], fm) : 0.0);
+      } else {
+        D -= F * dXi;  // outflow face carries X_i for either sign
+      }
+    }
+    // - x face
+    if (ix > 0) {
+      const double F = f.Fx[ip - 1];
+      D -= f.Lx[ip - 1] + (F < 0.0 ? -F * dXi : 0.0);
+      W = f.Lx[ip - 1] + (F >= 0.0 ? F * dXof(T[ip - 1], fm) : 0.0);
+    } else {
+      const int r = iy + g.ny * iz;
+      const double F = f.F0[r];
+      D -= f.LD0[r] + (F > 0.0 ? 0.0 : -F * dXi);
+    }
+    // +- y faces
+    if (iy < g.ny - 1) {
+      const double F = f.Fy[ip];
+      D -= f.Ly[ip] + (F >= 0.0 ? F * dXi : 0.0);
+      Nn = f.Ly[ip] + (F < 0.0 ? -F * dXof(T[ip + g.px], fm) : 0.0);
+    }
+    if (iy > 0) {
+      const double F = f.Fy[ip - g.px];
+      D -= f.Ly[ip - g.px] + (F < 0.0 ? -F * dXi : 0.0);
+      S = f.Ly[ip - g.px] + (F >= 0.0 ? F * dXof(T[ip - g.px], fm) : 0.0);
+    }
+    if (g.dim == 3) {
+      if (iz < g.nz - 1) {
+        const double F = f.Fz[ip];
+        D -= f.Lz[ip] + (F >= 0.0 ? F * dXi : 0.0);
+        Tt = f.Lz[ip] + (F < 0.0 ? -F * dXof(T[ip + g.plane], fm) : 0.0);
+      }
+      if (iz > 0) {
+        const double F = f.Fz[ip - g.plane];
+        D -= f.Lz[ip - g.plane] + (F < 0.0 ? -F * dXi : 0.0);
+        B = f.Lz[ip - g.plane] + (F >= 0.0 ? F * dXof(T[ip - g.plane], fm) : 0.0);
+      }
+    }
+    const double ic = f.icap[ip];
+    D *= ic; W *= ic; E *= ic; S *= ic; Nn *= ic; B *= ic; Tt *= ic;
+    o.c[0][ip] = D; o.c[1][ip] = W; o.c[2][ip] = E; o.c[3][ip] = S; o.c[4][ip] = Nn;
+    if (g.dim == 3) { o.c[5][ip] = B; o.c[6][ip] = Tt; }
+    const double R = fabs(W) + fabs(E) + fabs(S) + fabs(Nn) + fabs(B) + fabs(Tt);
+    bad |= !finite(D) | !finite(R);
+    gmin = fmin(gmin, D - R);
+    gmax = fmax(gmax, D + R);
+  }
+  if (bad) atomicOr(&ctrl->flags, FLAG_NONFINITE);
+  const double bmin = block_reduce<1>(gmin, sh);
+  const double bmax = block_reduce<2>(gmax, sh);
+  double vals[2] = {bmin, bmax};
+  if (publish_partials(part, cnt, vals, 2)) {
+    const double a = gather_partials<1>(part, 0, sh);
+    const double b = gather_partials<2>(part, 1, sh);
+    if (threadIdx.x == 0) {
+      ctrl->gmin = a;
+      ctrl->gmax = b;
+      *cnt = 0;
+    }
+  }
+}
+
+// Leja copy of J: jl_k = (Tq)(sc * jc_k), all padded cells.
+template <typename Tq>
+__global__ void k_scale_jl(JOut jc, Tq* __restrict__ o0, Tq* __restrict__ o1,
+                           Tq* __restrict__ o2, Tq* __restrict__ o3, Tq* __restrict__ o4,
+                           Tq* __restrict__ o5, Tq* __restrict__ o6, double sc, int Np, int dim) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
+    o0[i] = (Tq)(sc * jc.c[0][i]);
+    o1[i] = (Tq)(sc * jc.c[1][i]);
+    o2[i] = (Tq)(sc * jc.c[2][i]);
+    o3[i] = (Tq)(sc * jc.c[3][i]);
+    o4[i] = (Tq)(sc * jc.c[4][i]);
+    if (dim == 3) {
+      o5[i] = (Tq)(sc * jc.c[5][i]);
+      o6[i] = (Tq)(sc * jc.c[6][i]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// heat right-hand side G(T) (eq. spaceheat2): conductive and upwind
+// advective fluxes into each cell (§3.1) over its capacity.
+// ---------------------------------------------------------------------------
+__global__ void k_rhs(FaceIn f, const double* __restrict__ T, double* __restrict__ G, Geo g,
+                      Phys ph, int set_yinf, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  const int fm = ph.fm;
+  double tmax = 0.0;
+  int bad = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double Ti = T[ip];
+    const double Xi = Xof(Ti, fm);
+    double in = 0.0;
+    {  // + x face
+      const double F = f.Fx[ip];
+      if (ix < g.nx - 1) {
+        const double Tj = T[ip + 1];
+        in -= f.Lx[ip] * (Ti - Tj) + F * (F >= 0.0 ? Xi : Xof(Tj, fm));
+      } else {
+        in -= F * Xi;
+      }
+    }
+    if (ix > 0) {  // - x face, flux in +x direction enters cell i
+      const double F = f.Fx[ip - 1];
+      const double Tj = T[ip - 1];
+      in += f.Lx[ip - 1] * (Tj - Ti) + F * (F >= 0.0 ? Xof(Tj, fm) : Xi);
+    } else {
+      const int r = iy + g.ny * iz;
+      const double F = f.F0[r];
+      in += f.LD0[r] * (ph.T_in - Ti) + F * (F > 0.0 ? Xof(ph.T_in, fm) : Xi);
+    }
+    if (iy < g.ny - 1) {
+      const double F = f.Fy[ip];
+      const double Tj = T[ip + g.px];
+      in -= f.Ly[ip] * (Ti - Tj) + F * (F >= 0.0 ? Xi : Xof(Tj, fm));
+    }
+    if (iy > 0) {
+      const double F = f.Fy[ip - g.px];
+      const double Tj = T[ip - g.px];
+      in += f.Ly[ip - g.px] * (Tj - Ti) + F * (F >= 0.0 ? Xof(Tj, fm) : Xi);
+    }
+    if (g.dim == 3) {
+      if (iz < g.nz - 1) {
+        const double F = f.Fz[ip];
+        const double Tj = T[ip + g.plane];
+        in -= f.Lz[ip] * (Ti - Tj) + F * (F >= 0.0 ? Xi : Xof(Tj, fm));
+      }
+      if (iz > 0) {
+        const double F = f.Fz[ip - g.plane];
+        const double Tj = T[ip - g.plane];
+        in += f.Lz[ip - g.plane] * (Tj - Ti) + F * (F >= 0.0 ? Xof(Tj, fm) : Xi);
+      }
+    }
+    const double Gi = f.icap[ip] * in;
+    G[ip] = Gi;
+    bad |= !finite(Gi) | !finite(Ti);
+    tmax = fmax(tmax, fabs(Ti));
+  }
+  if (bad) atomicOr(&ctrl->flags, FLAG_NONFINITE);
+  if (!set_yinf) return;
+  const double bmax = block_reduce<2>(tmax, sh);
+  double vals[1] = {bmax};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double a = gather_partials<2>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      ctrl->yinf = a;
+      *cnt = 0;
+    }
+  }
+}
+
+// (J x)_i from the FP64 cell form, one cell
+struct JIn {
+  const double* c[7];
+};
+__device__ __forceinline__ double japply_cell(const JIn& J, const double* __restrict__ x, int ip,
+                                              int ix, int iy, int iz, const Geo& g) {
+  double a = J.c[0][ip] * x[ip];
+  if (ix > 0) a += J.c[1][ip] * x[ip - 1];
+  if (ix < g.nx - 1) a += J.c[2][ip] * x[ip + 1];
+  if (iy > 0) a += J.c[3][ip] * x[ip - g.px];
+  if (iy < g.ny - 1) a += J.c[4][ip] * x[ip + g.px];
+  if (g.dim == 3) {
+    if (iz > 0) a += J.c[5][ip] * x[ip - g.plane];
+    if (iz < g.nz - 1) a += J.c[6][ip] * x[ip + g.plane];
+  }
+  return a;
+}
+
+// out = J x + v (the right-hand side J w_k + v of a later substep)
+__global__ void k_japply_add(JIn J, const double* __restrict__ x, const double* __restrict__ v,
+                             double* __restrict__ out, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    out[ip] = japply_cell(J, x, ip, ix, iy, iz, g) + v[ip];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Leja recurrence (eq. newt)
+// ---------------------------------------------------------------------------
+template <typename Tq, int VEC> struct VecT;
+template <> struct VecT<float, 4> { using V = float4; };
+template <> struct VecT<double, 2> { using V = double2; };
+
+template <typename Tq, int VEC>
+__device__ __forceinline__ void ldv(Tq (&r)[VEC], const Tq* p) {
+  using V = typename VecT<Tq, VEC>::V;
+  const V v = *reinterpret_cast<const V*>(p);
+  const Tq* s = reinterpret_cast<const Tq*>(&v);
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) r[k] = s[k];
+}
+template <typename Tq, int VEC>
+__device__ __forceinline__ void ldv_stream(Tq (&r)[VEC], const Tq* p) {
+  using V = typename VecT<Tq, VEC>::V;
+  const V v = __ldcs(reinterpret_cast<const V*>(p));
+  const Tq* s = reinterpret_cast<const Tq*>(&v);
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) r[k] = s[k];
+}
+template <typename Tq, int VEC>
+__device__ __forceinline__ void stv(Tq* p, const Tq (&r)[VEC]) {
+  using V = typename VecT<Tq, VEC>::V;
+  V v;
+  Tq* d = reinterpret_cast<Tq*>(&v);
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) d[k] = r[k];
+  *reinterpret_cast<V*>(p) = v;
+}
+// VEC doubles of P, streamed (read once, written once per term)
+template <int VEC>
+__device__ __forceinline__ void ldP(double (&r)[VEC], const double* p) {
+#pragma unroll
+  for (int k = 0; k < VEC; k += 2) {
+    const double2 v = __ldcs(reinterpret_cast<const double2*>(p + k));
+    r[k] = v.x;
+    r[k + 1] = v.y;
+  }
+}
+template <int VEC>
+__device__ __forceinline__ void stP(double* p, const double (&r)[VEC]) {
+#pragma unroll
+  for (int k = 0; k < VEC; k += 2) __stcs(reinterpret_cast<double2*>(p + k), make_double2(r[k], r[k + 1]));
+}
+
+// q_0 = u (in the Leja precision), P_0 = d_0 u; block 0 arms the control block.
+template <typename Tq>
+__global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
+                            double* __restrict__ P, double d0, int Np, StopParams sp, Ctrl* ctrl) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->done = 0;
+    ctrl->degree = 0;
+    ctrl->fail = 0;
+    ctrl->nonfinite = 0;
+    ctrl->m_last = 0;
+    ctrl->err = 0.0;
+    ctrl->sp = sp;
+  }
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
+    const double x = u[i];
+    q0[i] = (Tq)x;
+    P[i] = d0 * x;
+  }
+}
+
+template <typename Tq>
+struct LejaCoef {
+  const Tq* c[7];  // D W E S N B T, scaled by dt / gamma
+};
+
+// Stopping test of §4.2 on the estimate of term m (thread 0 of the last block).
+__device__ void stop_test(Ctrl* c, int m, double dm, double S) {
+  const StopParams sp = c->sp;
+  const double scal = sp.tol_a + sp.tol_r * c->yinf;
+  const double e = fabs(sp.delta * dm) / scal * sqrt(S / sp.ncells);
+  c->e[m] = e;
+  c->m_last = m;
+  if (!isfinite(e)) {
+    c->nonfinite = 1;
+    c->done = 1;
+    return;
+  }
+  const int lo = max(1, m - sp.window + 1);
+  double mean = 0.0;
+  for (int k = lo; k <= m; ++k) mean += c->e[k];
+  mean /= (double)(m - lo + 1);
+  c->err = mean;
+  if (sp.replay) return;
+  if (sp.pow10 * mean < 1.0) {
+    c->done = 1;
+    c->degree = m;
+  } else if (m >= sp.m_max) {
+    c->fail = 1;
+    c->done = 1;
+  }
+}
+
+// One Leja term, fused: q_m = (dt J / gamma - (c/gamma + xi_{m-1})) q_{m-1}
+// (the stencil apply), P += d_m q_m, and the partial sum of q_m^2 for the
+// error estimate; the last block runs the stopping test.  Each thread owns
+// VEC consecutive cells along x.
+template <typename Tq, int VEC, int DIM>
+__global__ void __launch_bounds__(NT)
+k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
+            LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi, const double* __restrict__ dd,
+            double cg, int m, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->done) return;
+  const Tq sh_m = (Tq)(cg + xi[m - 1]);
+  const double dm = dd[m];
+  double acc = 0.0;
+  const int nvec = g.Np / VEC;
+  const int vrow = g.px / VEC;
+  for (int t = blockIdx.x * NT + threadIdx.x; t < nvec; t += gridDim.x * NT) {
+    const int row = t / vrow;
+    const int ix = (t - row * vrow) * VEC;
+    const int iy = row % g.ny;
+    const int iz = row / g.ny;
+    const int i = row * g.px + ix;
+    Tq qc[VEC], qs[VEC], qn[VEC], qb[VEC], qt[VEC];
+    ldv<Tq, VEC>(qc, qi + i);
+    ldv<Tq, VEC>(qs, qi + i - (iy > 0 ? g.px : 0));
+    ldv<Tq, VEC>(qn, qi + i + (iy < g.ny - 1 ? g.px : 0));
+    if (DIM == 3) {
+      ldv<Tq, VEC>(qb, qi + i - (iz > 0 ? g.plane : 0));
+      ldv<Tq, VEC>(qt, qi + i + (iz < g.nz - 1 ? g.plane : 0));
+    }
+    const Tq ql = ix > 0 ? qi[i - 1] : Tq(0);
+    const Tq qr = ix + VEC < g.px ? qi[i + VEC] : Tq(0);
+    Tq cD[VEC], cW[VEC], cE[VEC], cS[VEC], cN[VEC], cB[VEC], cT[VEC];
+    ldv_stream<Tq, VEC>(cD, cf.c[0] + i);
+    ldv_stream<Tq, VEC>(cW, cf.c[1] + i);
+    ldv_stream<Tq, VEC>(cE, cf.c[2] + i);
+    ldv_stream<Tq, VEC>(cS, cf.c[3] + i);
+    ldv_stream<Tq, VEC>(cN, cf.c[4] + i);
+    if (DIM == 3) {
+      ldv_stream<Tq, VEC>(cB, cf.c[5] + i);
+      ldv_stream<Tq, VEC>(cT, cf.c[6] + i);
+    }
+    double p[VEC];
+    ldP<VEC>(p, P + i);
+    Tq out[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const Tq west = k == 0 ? ql : qc[k - 1];
+      const Tq east = k == VEC - 1 ? qr : qc[k + 1];
+      Tq a = (cD[k] - sh_m) * qc[k];
+      a = fma(cW[k], west, a);
+      a = fma(cE[k], east, a);
+      a = fma(cS[k], qs[k], a);
+      a = fma(cN[k], qn[k], a);
+      if (DIM == 3) {
+        a = fma(cB[k], qb[k], a);
+        a = fma(cT[k], qt[k], a);
+      }
+      out[k] = a;
+      const double ad = (double)a;
+      p[k] = fma(dm, ad, p[k]);
+      acc = fma(ad, ad, acc);
+    }
+    stv<Tq, VEC>(qo + i, out);
+    stP<VEC>(P + i, p);
+  }
+  const double bs = block_reduce<0>(acc, sh);
+  double vals[1] = {bs};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double S = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      stop_test(ctrl, m, dm, S);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pressure: TPFA mass-mobility transmissibilities and Jacobi-PCG
+// ---------------------------------------------------------------------------
+struct PresArr {
+  double *x, *r, *z, *d0, *d1, *Ad, *Ux, *Uy, *Uz, *diag, *b;
+};
+
+__global__ void k_pres_faces(const double* __restrict__ lnk, const double* __restrict__ T,
+                             PresArr a, Geo g, Phys ph, int* flags) {
+  int bad = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double Ti = T ? T[i] : 20.0;
+    const double mi = exp(lnk[i]) * rho_rel(Ti, ph.fm) / mu_rel(Ti, ph.fm);
+    bad |= !finite(mi);
+    double dg = 0.0, bb = 0.0;
+    auto mob = [&](int j) {
+      const double Tj = T ? T[j] : 20.0;
+      return exp(lnk[j]) * rho_rel(Tj, ph.fm) / mu_rel(Tj, ph.fm);
+    };
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    if (ix < g.nx - 1) ux = harm(ph.ax, 0.5 * ph.hx, mi, mob(i + 1));
+    if (iy < g.ny - 1) uy = harm(ph.ay, 0.5 * ph.hy, mi, mob(i + g.nx));
+    if (g.dim == 3 && iz < g.nz - 1) uz = harm(ph.az, 0.5 * ph.hz, mi, mob(i + g.nx * g.ny));
+    a.Ux[ip] = ux;
+    a.Uy[ip] = uy;
+    if (g.dim == 3) a.Uz[ip] = uz;
+    dg += ux + uy + uz;
+    if (ix > 0) dg += harm(ph.ax, 0.5 * ph.hx, mob(i - 1), mi);
+    if (iy > 0) dg += harm(ph.ay, 0.5 * ph.hy, mob(i - g.nx), mi);
+    if (g.dim == 3 && iz > 0) dg += harm(ph.az, 0.5 * ph.hz, mob(i - g.nx * g.ny), mi);
+    const double uD = ph.ax * mi / (0.5 * ph.hx);
+    if (ix == 0) { dg += uD; bb += uD * ph.head_left; }
+    if (ix == g.nx - 1) { dg += uD; bb += uD * ph.head_right; }
+    a.diag[ip] = dg;
+    a.b[ip] = bb;
+  }
+  if (bad) atomicOr(flags, FLAG_NONFINITE);
+}
+
+__device__ __forceinline__ double pres_apply(const PresArr& a, const double* __restrict__ x, int ip,
+                                             int ix, int iy, int iz, const Geo& g) {
+  double v = a.diag[ip] * x[ip];
+  if (ix < g.nx - 1) v -= a.Ux[ip] * x[ip + 1];
+  if (ix > 0) v -= a.Ux[ip - 1] * x[ip - 1];
+  if (iy < g.ny - 1) v -= a.Uy[ip] * x[ip + g.px];
+  if (iy > 0) v -= a.Uy[ip - g.px] * x[ip - g.px];
+  if (g.dim == 3) {
+    if (iz < g.nz - 1) v -= a.Uz[ip] * x[ip + g.plane];
+    if (iz > 0) v -= a.Uz[ip - g.plane] * x[ip - g.plane];
+  }
+  return v;
+}
+
+// r = b - A x, z = r / diag, d_old = 0; rz, rr, bb
+__global__ void k_cg_init(PresArr a, Geo g, double tol, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double r = a.b[ip] - pres_apply(a, a.x, ip, ix, iy, iz, g);
+    const double z = r / a.diag[ip];
+    a.r[ip] = r;
+    a.z[ip] = z;
+    a.d0[ip] = 0.0;
+    rz += r * z;
+    rr += r * r;
+    bb += a.b[ip] * a.b[ip];
+  }
+  double vals[3];
+  vals[0] = block_reduce<0>(rz, sh);
+  vals[1] = block_reduce<0>(rr, sh);
+  vals[2] = block_reduce<0>(bb, sh);
+  if (publish_partials(part, cnt, vals, 3)) {
+    const double a0 = gather_partials<0>(part, 0, sh);
+    const double a1 = gather_partials<0>(part, 1, sh);
+    const double a2 = gather_partials<0>(part, 2, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin[K_RZ] = a0;
+      ctrl->lin[K_RR] = a1;
+      ctrl->lin[K_BB] = a2;
+      ctrl->lin[K_BETA] = 0.0;
+      ctrl->lin[K_TOL2] = tol * tol * a2;
+      ctrl->lin_it = 0;
+      ctrl->lin_break = 0;
+      ctrl->lin_done = (a1 <= tol * tol * a2) ? 1 : 0;
+    }
+  }
+}
+
+// d_new = z + beta d_old; Ad = A d_new; (d, Ad) -> alpha
+__global__ void k_cg_dir(PresArr a, const double* __restrict__ dold, double* __restrict__ dnew,
+                         Geo g, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double beta = ctrl->lin[K_BETA];
+  double dad = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    auto dn = [&](int j) { return a.z[j] + beta * dold[j]; };
+    const double di = dn(ip);
+    double v = a.diag[ip] * di;
+    if (ix < g.nx - 1) v -= a.Ux[ip] * dn(ip + 1);
+    if (ix > 0) v -= a.Ux[ip - 1] * dn(ip - 1);
+    if (iy < g.ny - 1) v -= a.Uy[ip] * dn(ip + g.px);
+    if (iy > 0) v -= a.Uy[ip - g.px] * dn(ip - g.px);
+    if (g.dim == 3) {
+      if (iz < g.nz - 1) v -= a.Uz[ip] * dn(ip + g.plane);
+      if (iz > 0) v -= a.Uz[ip - g.plane] * dn(ip - g.plane);
+    }
+    dnew[ip] = di;
+    a.Ad[ip] = v;
+    dad += di * v;
+  }
+  double vals[1] = {block_reduce<0>(dad, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin[K_DAD] = s;
+      if (!(s > 0.0) || !isfinite(s)) {
+        ctrl->lin_break = 1;
+        ctrl->lin_done = 1;
+      } else {
+        ctrl->lin[K_ALPHA] = ctrl->lin[K_RZ] / s;
+      }
+    }
+  }
+}
+
+// x += alpha d, r -= alpha Ad, z = r / diag; rz_new, rr -> beta, convergence
+__global__ void k_cg_upd(PresArr a, const double* __restrict__ d, Geo g, double* part,
+                         unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double alpha = ctrl->lin[K_ALPHA];
+  double rz = 0.0, rr = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    a.x[ip] += alpha * d[ip];
+    const double r = a.r[ip] - alpha * a.Ad[ip];
+    const double z = r / a.diag[ip];
+    a.r[ip] = r;
+    a.z[ip] = z;
+    rz += r * z;
+    rr += r * r;
+  }
+  double vals[2] = {block_reduce<0>(rz, sh), 0.0};
+  vals[1] = block_reduce<0>(rr, sh);
+  if (publish_partials(part, cnt, vals, 2)) {
+    const double s0 = gather_partials<0>(part, 0, sh);
+    const double s1 = gather_partials<0>(part, 1, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin_it += 1;
+      ctrl->lin[K_BETA] = s0 / ctrl->lin[K_RZ];
+      ctrl->lin[K_RZ] = s0;
+      ctrl->lin[K_RR] = s1;
+      if (s1 <= ctrl->lin[K_TOL2]) ctrl->lin_done = 1;
+      if (!isfinite(s1)) { ctrl->lin_break = 1; ctrl->lin_done = 1; }
+    }
+  }
+}
+
+// net Darcy inflow through x = 0 and the largest face speed |v| / |sigma|
+__global__ void k_pres_post(const double* __restrict__ lnk, const double* __restrict__ T,
+                            const double* __restrict__ x, Geo g, Phys ph, double* part,
+                            unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  double fin = 0.0, vmax = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    auto mob = [&](int j) {
+      const double Tj = T ? T[j] : 20.0;
+      return exp(lnk[j]) / mu_rel(Tj, ph.fm);
+    };
+    const double mi = mob(i);
+    const double pi = x[ip];
+    if (ix == 0) {
+      const double v = (ph.ax * mi / (0.5 * ph.hx)) * (ph.head_left - pi);
+      fin += v;
+      vmax = fmax(vmax, fabs(v) / ph.ax);
+    }
+    if (ix < g.nx - 1) {
+      const double v = harm(ph.ax, 0.5 * ph.hx, mi, mob(i + 1)) * (pi - x[ip + 1]);
+      vmax = fmax(vmax, fabs(v) / ph.ax);
+    } else {
+      const double v = (ph.ax * mi / (0.5 * ph.hx)) * (pi - ph.head_right);
+      vmax = fmax(vmax, fabs(v) / ph.ax);
+    }
+    if (iy < g.ny - 1) {
+      const double v = harm(ph.ay, 0.5 * ph.hy, mi, mob(i + g.nx)) * (pi - x[ip + g.px]);
+      vmax = fmax(vmax, fabs(v) / ph.ay);
+    }
+    if (g.dim == 3 && iz < g.nz - 1) {
+      const double v = harm(ph.az, 0.5 * ph.hz, mi, mob(i + g.nx * g.ny)) * (pi - x[ip + g.plane]);
+      vmax = fmax(vmax, fabs(v) / ph.az);
+    }
+  }
+  double vals[2] = {block_reduce<0>(fin, sh), 0.0};
+  vals[1] = block_reduce<2>(vmax, sh);
+  if (publish_partials(part, cnt, vals, 2)) {
+    const double s0 = gather_partials<0>(part, 0, sh);
+    const double s1 = gather_partials<2>(part, 1, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->flux_in = s0;
+      ctrl->vmax = s1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BiCGSTAB with Jacobi preconditioning for (sigma I - J) x = b, FP64
+// ---------------------------------------------------------------------------
+struct BiArr {
+  double *x, *r, *rh, *p, *v, *y, *s, *z, *t, *dA;
+};
+
+__device__ __forceinline__ double stage_apply(const JIn& J, double sigma, const double* __restrict__ x,
+                                              int ip, int ix, int iy, int iz, const Geo& g) {
+  return sigma * x[ip] - japply_cell(J, x, ip, ix, iy, iz, g);
+}
+
+__global__ void k_bicg_init(JIn J, BiArr a, const double* __restrict__ b, double sigma, double tol,
+                            Geo g, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  double bb = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double bi = b[ip];
+    a.x[ip] = 0.0;
+    a.r[ip] = bi;
+    a.rh[ip] = bi;
+    a.p[ip] = 0.0;
+    a.v[ip] = 0.0;
+    a.dA[ip] = sigma - J.c[0][ip];
+    bb += bi * bi;
+  }
+  double vals[1] = {block_reduce<0>(bb, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin[K_BB] = s;
+      ctrl->lin[K_RHO] = s;
+      ctrl->lin[K_RHO_PREV] = 1.0;
+      ctrl->lin[K_ALPHA] = 1.0;
+      ctrl->lin[K_OMEGA] = 1.0;
+      ctrl->lin[K_RR] = s;
+      ctrl->lin[K_TOL2] = tol * tol * s;
+      ctrl->lin_it = 0;
+      ctrl->lin_break = 0;
+      ctrl->lin_done = (s == 0.0) ? 1 : 0;
+    }
+  }
+}
+
+// p = r + beta (p - omega v); y = p / diag(A)
+__global__ void k_bicg_p(BiArr a, Geo g, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double* L = ctrl->lin;
+  const double beta = (L[K_RHO] / L[K_RHO_PREV]) * (L[K_ALPHA] / L[K_OMEGA]);
+  const double omega = L[K_OMEGA];
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double pn = a.r[ip] + beta * (a.p[ip] - omega * a.v[ip]);
+    a.p[ip] = pn;
+    a.y[ip] = pn / a.dA[ip];
+  }
+}
+
+// v = A y; alpha = rho / (rh, v)
+__global__ void k_bicg_v(JIn J, BiArr a, double sigma, Geo g, double* part, unsigned* cnt,
+                         Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  double rv = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double v = stage_apply(J, sigma, a.y, ip, ix, iy, iz, g);
+    a.v[ip] = v;
+    rv += a.rh[ip] * v;
+  }
+  double vals[1] = {block_reduce<0>(rv, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      if (s == 0.0 || !isfinite(s)) {
+        ctrl->lin_break = 1;
+        ctrl->lin_done = 1;
+      } else {
+        ctrl->lin[K_ALPHA] = ctrl->lin[K_RHO] / s;
+      }
+    }
+  }
+}
+
+// s = r - alpha v; x += alpha y; z = s / diag(A); ||s||^2 -> early exit
+__global__ void k_bicg_s(BiArr a, Geo g, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double alpha = ctrl->lin[K_ALPHA];
+  double ss = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double s = a.r[ip] - alpha * a.v[ip];
+    a.s[ip] = s;
+    a.x[ip] += alpha * a.y[ip];
+    a.z[ip] = s / a.dA[ip];
+    ss += s * s;
+  }
+  double vals[1] = {block_reduce<0>(ss, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin[K_SS] = s;
+      if (s <= ctrl->lin[K_TOL2]) {
+        ctrl->lin[K_RR] = s;
+        ctrl->lin_it += 1;
+        ctrl->lin_done = 1;
+      }
+    }
+  }
+}
+
+// t = A z; omega = (t, s) / (t, t); x += omega z; r = s - omega t; new rho
+__global__ void k_bicg_t(JIn J, BiArr a, double sigma, Geo g, double* part, unsigned* cnt,
+                         Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  double ts = 0.0, tt = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double t = stage_apply(J, sigma, a.z, ip, ix, iy, iz, g);
+    a.t[ip] = t;
+    ts += t * a.s[ip];
+    tt += t * t;
+  }
+  double vals[2] = {block_reduce<0>(ts, sh), 0.0};
+  vals[1] = block_reduce<0>(tt, sh);
+  if (publish_partials(part, cnt, vals, 2)) {
+    const double s0 = gather_partials<0>(part, 0, sh);
+    const double s1 = gather_partials<0>(part, 1, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      if (s1 == 0.0 || !isfinite(s1) || s0 == 0.0) {
+        ctrl->lin_break = 1;
+        ctrl->lin_done = 1;
+      } else {
+        ctrl->lin[K_OMEGA] = s0 / s1;
+      }
+    }
+  }
+}
+
+__global__ void k_bicg_r(BiArr a, Geo g, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double omega = ctrl->lin[K_OMEGA];
+  double rho = 0.0, rr = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    a.x[ip] += omega * a.z[ip];
+    const double r = a.s[ip] - omega * a.t[ip];
+    a.r[ip] = r;
+    rho += a.rh[ip] * r;
+    rr += r * r;
+  }
+  double vals[2] = {block_reduce<0>(rho, sh), 0.0};
+  vals[1] = block_reduce<0>(rr, sh);
+  if (publish_partials(part, cnt, vals, 2)) {
+    const double s0 = gather_partials<0>(part, 0, sh);
+    const double s1 = gather_partials<0>(part, 1, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin_it += 1;
+      ctrl->lin[K_RHO_PREV] = ctrl->lin[K_RHO];
+      ctrl->lin[K_RHO] = s0;
+      ctrl->lin[K_RR] = s1;
+      if (s1 <= ctrl->lin[K_TOL2]) ctrl->lin_done = 1;
+      else if (s0 == 0.0 || !isfinite(s1)) {
+        ctrl->lin_break = 1;
+        ctrl->lin_done = 1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side argument packing
+// ---------------------------------------------------------------------------
+Geo geo_of(const erem_ctx* c) {
+  Geo g;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.nz = c->nz;
+  g.px = c->px;
+  g.dim = c->dim;
+  g.N = (int)c->N;
+  g.Np = (int)c->Np;
+  g.plane = c->px * c->ny;
+  return g;
+}
+
+Phys phys_of(const erem_ctx* c) {
+  Phys p;
+  p.rhoc_f = c->phys.rhoc_f;
+  p.rhoc_s = c->phys.rhoc_s;
+  p.head_left = c->phys.head_left;
+  p.head_right = c->phys.head_right;
+  p.T_in = c->phys.T_inflow;
+  p.fm = c->phys.fluid_model;
+  p.hx = c->hx;
+  p.hy = c->hy;
+  p.hz = c->hz;
+  p.vol = c->vol;
+  p.ax = c->ax;
+  p.ay = c->ay;
+  p.az = c->az;
+  return p;
+}
+
+FaceIn face_in(const erem_ctx* c) {
+  return FaceIn{c->Lx, c->Ly, c->Lz, c->Fx, c->Fy, c->Fz, c->icap, c->LD0, c->F0};
+}
+JIn jin(const erem_ctx* c) {
+  JIn j;
+  for (int k = 0; k < 7; ++k) j.c[k] = c->jc[k];
+  return j;
+}
+PresArr pres_arr(const erem_ctx* c) {
+  return PresArr{c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->kv[5],
+                 c->kv[6], c->kv[7], c->kv[8], c->kv[9], c->kv[10]};
+}
+BiArr bi_arr(const erem_ctx* c) {
+  return BiArr{c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4],
+               c->kv[5], c->kv[6], c->kv[7], c->kv[8], c->kv[9]};
+}
+
+int blocks_cells(const erem_ctx* c) { return grid_for(c, c->N); }
+int blocks_padded(const erem_ctx* c) { return grid_for(c, c->Np); }
+
+}  // namespace
+
+int grid_for(const erem_ctx* c, long long items) {
+  long long b = (items + NT - 1) / NT;
+  if (b < 1) b = 1;
+  if (b > c->red_blocks) b = c->red_blocks;
+  return (int)b;
+}
+
+void launch_pack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s) {
+  ++c->launches;
+  k_pack<<<blocks_cells(c), NT, 0, s>>>(src, dst, geo_of(c), &c->ctrl->flags);
+}
+
+void launch_finish(const erem_ctx* c, double* out, const double* base, const double* w,
+                   const double* P, double delta, cudaStream_t s) {
+  ++c->launches;
+  k_finish<<<blocks_cells(c), NT, 0, s>>>(out, base, w, P, delta, geo_of(c));
+}
+
+void launch_faces(const erem_ctx* c, cudaStream_t s) {
+  FieldIn in{c->lnk, c->phi, c->lam, c->p, c->Tn};
+  FaceOut o{c->Lx, c->Ly, c->Lz, c->Fx, c->Fy, c->Fz, c->icap, c->LD0, c->F0};
+  ++c->launches;
+  k_faces<<<blocks_cells(c), NT, 0, s>>>(in, o, geo_of(c), phys_of(c), &c->ctrl->flags);
+}
+
+void launch_cellJ(const erem_ctx* c, cudaStream_t s) {
+  JOut o;
+  for (int k = 0; k < 7; ++k) o.c[k] = c->jc[k];
+  ++c->launches;
+  k_cellJ<<<blocks_cells(c), NT, 0, s>>>(face_in(c), c->Tn, o, geo_of(c), phys_of(c), c->red_part,
+                                         c->red_cnt, c->ctrl);
+}
+
+void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s) {
+  JOut jc;
+  for (int k = 0; k < 7; ++k) jc.c[k] = c->jc[k];
+  if (c->prec == EREM_FP32_BULK) {
+    float* o[7];
+    for (int k = 0; k < 7; ++k) o[k] = (float*)c->jl[k];
+    ++c->launches;
+    k_scale_jl<float><<<blocks_padded(c), NT, 0, s>>>(jc, o[0], o[1], o[2], o[3], o[4], o[5], o[6],
+                                                       sc, (int)c->Np, c->dim);
+  } else {
+    double* o[7];
+    for (int k = 0; k < 7; ++k) o[k] = (double*)c->jl[k];
+    ++c->launches;
+    k_scale_jl<double><<<blocks_padded(c), NT, 0, s>>>(jc, o[0], o[1], o[2], o[3], o[4], o[5], o[6],
+                                                        sc, (int)c->Np, c->dim);
+  }
+}
+
+void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cudaStream_t s) {
+  ++c->launches;
+  k_rhs<<<blocks_cells(c), NT, 0, s>>>(face_in(c), T, G, geo_of(c), phys_of(c), set_yinf,
+                                       c->red_part, c->red_cnt, c->ctrl);
+}
+
+void launch_japply_add(const erem_ctx* c, const double* x, const double* v, double* out,
+                       cudaStream_t s) {
+  ++c->launches;
+  k_japply_add<<<blocks_cells(c), NT, 0, s>>>(jin(c), x, v, out, geo_of(c));
+}
+
+void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
+                      cudaStream_t s) {
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_leja_init<float><<<blocks_padded(c), NT, 0, s>>>(u, (float*)c->q[0], c->P, d0, (int)c->Np, sp,
+                                                       c->ctrl);
+  else
+    k_leja_init<double><<<blocks_padded(c), NT, 0, s>>>(u, (double*)c->q[0], c->P, d0, (int)c->Np,
+                                                        sp, c->ctrl);
+}
+
+void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
+  const Geo g = geo_of(c);
+  if (c->prec == EREM_FP32_BULK) {
+    LejaCoef<float> cf;
+    for (int k = 0; k < 7; ++k) cf.c[k] = (const float*)c->jl[k];
+    const float* qi = (const float*)c->q[qin];
+    float* qo = (float*)c->q[qin ^ 1];
+    const int nb = grid_for(c, c->Np / 4);
+    ++c->launches;
+    if (c->dim == 3)
+      k_leja_term<float, 4, 3><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
+                                                 c->red_part, c->red_cnt, c->ctrl);
+    else
+      k_leja_term<float, 4, 2><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
+                                                 c->red_part, c->red_cnt, c->ctrl);
+  } else {
+    LejaCoef<double> cf;
+    for (int k = 0; k < 7; ++k) cf.c[k] = (const double*)c->jl[k];
+    const double* qi = (const double*)c->q[qin];
+    double* qo = (double*)c->q[qin ^ 1];
+    const int nb = grid_for(c, c->Np / 2);
+    ++c->launches;
+    if (c->dim == 3)
+      k_leja_term<double, 2, 3><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
+                                                  c->red_part, c->red_cnt, c->ctrl);
+    else
+      k_leja_term<double, 2, 2><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
+                                                  c->red_part, c->red_cnt, c->ctrl);
+  }
+}
+
+void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,
+                 cudaStream_t s) {
+  ++c->launches;
+  k_axpy<<<blocks_padded(c), NT, 0, s>>>(w, P, delta, first, (int)c->Np);
+}
+
+void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,
+                    const double* y, cudaStream_t s) {
+  ++c->launches;
+  k_lincomb<<<blocks_padded(c), NT, 0, s>>>(out, a, x, b, y, (int)c->Np);
+}
+
+void launch_pres_faces(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {
+  ++c->launches;
+  k_pres_faces<<<blocks_cells(c), NT, 0, s>>>(lnk, T, pres_arr(c), geo_of(c), phys_of(c),
+                                              &c->ctrl->flags);
+}
+
+void launch_cg_init(const erem_ctx* c, double tol, cudaStream_t s) {
+  ++c->launches;
+  k_cg_init<<<blocks_cells(c), NT, 0, s>>>(pres_arr(c), geo_of(c), tol, c->red_part, c->red_cnt,
+                                           c->ctrl);
+}
+
+void launch_cg_iter(const erem_ctx* c, int k, cudaStream_t s) {
+  PresArr a = pres_arr(c);
+  const double* dold = (k & 1) ? a.d1 : a.d0;
+  double* dnew = (k & 1) ? a.d0 : a.d1;
+  const int nb = blocks_cells(c);
+  ++c->launches;
+  k_cg_dir<<<nb, NT, 0, s>>>(a, dold, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_cg_upd<<<nb, NT, 0, s>>>(a, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+}
+
+void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {
+  ++c->launches;
+  k_pres_post<<<blocks_cells(c), NT, 0, s>>>(lnk, T, c->kv[0], geo_of(c), phys_of(c), c->red_part,
+                                             c->red_cnt, c->ctrl);
+}
+
+void launch_bicg_init(const erem_ctx* c, const double* b, double sigma, double tol,
+                      cudaStream_t s) {
+  ++c->launches;
+  k_bicg_init<<<blocks_cells(c), NT, 0, s>>>(jin(c), bi_arr(c), b, sigma, tol, geo_of(c),
+                                             c->red_part, c->red_cnt, c->ctrl);
+}
+
+void launch_bicg_iter(const erem_ctx* c, double sigma, cudaStream_t s) {
+  const int nb = blocks_cells(c);
+  const Geo g = geo_of(c);
+  BiArr a = bi_arr(c);
+  ++c->launches;
+  k_bicg_p<<<nb, NT, 0, s>>>(a, g, c->ctrl);
+  ++c->launches;
+  k_bicg_v<<<nb, NT, 0, s>>>(jin(c), a, sigma, g, c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_bicg_s<<<nb, NT, 0, s>>>(a, g, c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_bicg_t<<<nb, NT, 0, s>>>(jin(c), a, sigma, g, c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_bicg_r<<<nb, NT, 0, s>>>(a, g, c->red_part, c->red_cnt, c->ctrl);
+}
+
+}  // namespace erem

@@ -1,0 +1,188 @@
+// Host FP64 scalar side of the real Leja method (arXiv 1209.5553, §4.2):
+// the Leja point table (eq. lejaa) and the divided differences of phi_1
+// (the matrix-function route of §4.2).  Both are small, sequential
+// computations that run once per context (points) or once per spectral
+// interval and substep count (divided differences).
+#include <algorithm>
+#include <cmath>
+#include <limits>
+#include <mutex>
+#include <vector>
+
+#include "erem_internal.h"
+
+namespace erem {
+namespace {
+
+// sum_k log|x - p_k| and its first two derivatives in x.
+struct LogProd {
+  const std::vector<double>& p;
+  double value(double x) const {
+    double s = 0.0;
+    for (double pk : p) s += std::log(std::fabs(x - pk));
+    return s;
+  }
+  void derivs(double x, double* d1, double* d2) const {
+    double a = 0.0, b = 0.0;
+    for (double pk : p) {
+      const double r = 1.0 / (x - pk);
+      a += r;
+      b -= r * r;
+    }
+    *d1 = a;
+    *d2 = b;
+  }
+};
+
+// Maximiser of the log-product strictly inside (lo, hi), two consecutive
+// points.  The log-product is concave there and its derivative runs from
+// +inf to -inf, so Newton's method on the derivative, kept inside a
+// bisection bracket, converges to its single root.
+double gap_argmax(const LogProd& f, double lo, double hi) {
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; ++it) {
+    double g, h;
+    f.derivs(x, &g, &h);
+    if (g > 0.0) lo = x; else hi = x;
+    double xn = x - g / h;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (std::fabs(xn - x) <= 4.0 * std::numeric_limits<double>::epsilon() * std::fabs(x) ||
+        xn == x || hi - lo <= std::numeric_limits<double>::denorm_min()) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  return x;
+}
+
+std::mutex g_leja_mu;
+std::vector<double> g_leja;  // process-wide table, extended on demand
+
+void extend_leja(int M) {
+  if ((int)g_leja.size() >= M + 1) return;
+  if (g_leja.empty()) g_leja.push_back(2.0);        // xi_0 = beta -> 2
+  if (M >= 1 && g_leja.size() < 2) g_leja.push_back(-2.0);  // farthest from 2
+  std::vector<double> sorted(g_leja);
+  std::sort(sorted.begin(), sorted.end());
+  while ((int)g_leja.size() < M + 1) {
+    LogProd f{g_leja};
+    double best_x = 0.0, best_v = -INFINITY;
+    std::vector<std::pair<double, double>> cand;
+    cand.reserve(sorted.size());
+    for (size_t k = 0; k + 1 < sorted.size(); ++k) {
+      const double x = gap_argmax(f, sorted[k], sorted[k + 1]);
+      const double v = f.value(x);
+      cand.emplace_back(x, v);
+      if (v > best_v) { best_v = v; best_x = x; }
+    }
+    // equal products (to 1e-12 relative) go to the smaller point
+    const double tol = 1e-12 * std::max(1.0, std::fabs(best_v));
+    for (auto& c : cand)
+      if (c.second >= best_v - tol && c.first < best_x) best_x = c.first;
+    g_leja.push_back(best_x);
+    sorted.insert(std::upper_bound(sorted.begin(), sorted.end(), best_x), best_x);
+  }
+}
+
+}  // namespace
+
+void leja_table(int M, std::vector<double>* out) {
+  std::lock_guard<std::mutex> lk(g_leja_mu);
+  extend_leja(M);
+  out->assign(g_leja.begin(), g_leja.begin() + M + 1);
+}
+
+// Divided differences d_j = phi_1[xi_0..xi_j] of xi -> phi_1(c + gamma xi).
+//
+// phi_1(z) is the divided difference exp[0, z], so phi_1[z_0..z_j] =
+// exp[0, z_0, .., z_j], an entry of the exponential of the lower bidiagonal
+// matrix with diagonal (0, z_0, .., z_M) and ones below it (the Opitz form
+// that §4.2 uses).  Scaling row/column k by gamma^(k-1) turns the divided
+// differences in z into divided differences in xi: with subdiagonal
+// (1, gamma, .., gamma) the entry (j+1, 0) of the exponential is d_j.
+//
+// exp(W) = exp(W / 2^s)^(2^s).  W / 2^s has norm <= 1/2 and at most
+// 16 rows per squaring level (n / 2^s <= 16), and its exponential is taken
+// from 64 Taylor terms built by repeated right-multiplication with the
+// bidiagonal matrix (each power is banded).  Every entry of exp(W / 2^s) is
+// non-negative (W has a non-negative off-diagonal), so the squarings
+// add terms of one sign and keep relative accuracy even for the tiny
+// entries far below the diagonal.
+int divided_differences(int M, const double* xi, double c, double gamma, double* d) {
+  if (M < 0 || !xi || !d || !std::isfinite(c) || !std::isfinite(gamma) || gamma <= 0.0) return -1;
+  const int n = M + 2;
+  std::vector<double> diag(n), sub(n, 0.0);  // sub[k] = W(k, k-1)
+  diag[0] = 0.0;
+  for (int k = 1; k < n; ++k) {
+    diag[k] = c + gamma * xi[k - 1];
+    sub[k] = (k == 1) ? 1.0 : gamma;
+  }
+  double norm = 0.0;  // ||W||_1: column k holds diag[k] and sub[k+1]
+  for (int k = 0; k < n; ++k) norm = std::max(norm, std::fabs(diag[k]) + (k + 1 < n ? sub[k + 1] : 0.0));
+  int s = 0;
+  while (norm / std::ldexp(1.0, s) > 0.5) ++s;
+  while ((double)n / std::ldexp(1.0, s) > 16.0) ++s;
+  const double scale = std::ldexp(1.0, -s);
+  for (int k = 0; k < n; ++k) { diag[k] *= scale; sub[k] *= scale; }
+
+  // E = sum_{k=0}^{64} B^k / k!, lower triangular, row-major n x n.
+  std::vector<double> E((size_t)n * n, 0.0), Tk((size_t)n * n, 0.0), Tn((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) { E[(size_t)i * n + i] = 1.0; Tk[(size_t)i * n + i] = 1.0; }
+  const int K = 64;
+  for (int k = 0; k < K; ++k) {
+    const int band = std::min(k, n - 1);       // Tk is zero below band k
+    const int nb = std::min(k + 1, n - 1);
+    const double inv = 1.0 / (double)(k + 1);
+    for (int i = 0; i < n; ++i) {
+      const int j0 = std::max(0, i - nb);
+      for (int j = j0; j <= i; ++j) {
+        // (Tk B)(i, j) = Tk(i, j) B(j, j) + Tk(i, j+1) B(j+1, j)
+        double v = 0.0;
+        if (i - j <= band) v += Tk[(size_t)i * n + j] * diag[j];
+        if (j + 1 <= i && i - (j + 1) <= band) v += Tk[(size_t)i * n + j + 1] * sub[j + 1];
+        Tn[(size_t)i * n + j] = v * inv;
+      }
+    }
+    std::swap(Tk, Tn);
+    for (int i = 0; i < n; ++i)
+      for (int j = std::max(0, i - nb); j <= i; ++j) E[(size_t)i * n + j] += Tk[(size_t)i * n + j];
+  }
+  // s - 1 full squarings of the lower triangle, the last one only for column 0
+  std::vector<double> F((size_t)n * n, 0.0);
+  for (int sq = 0; sq + 1 < s; ++sq) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double acc = 0.0;
+        for (int l = j; l <= i; ++l) acc += E[(size_t)i * n + l] * E[(size_t)l * n + j];
+        F[(size_t)i * n + j] = acc;
+      }
+    std::swap(E, F);
+  }
+  for (int j = 0; j <= M; ++j) {
+    const int i = j + 1;
+    if (s == 0) {
+      d[j] = E[(size_t)i * n];
+    } else {
+      double acc = 0.0;
+      for (int l = 0; l <= i; ++l) acc += E[(size_t)i * n + l] * E[(size_t)l * n];
+      d[j] = acc;
+    }
+  }
+  return 0;
+}
+
+}  // namespace erem
+
+extern "C" int erem_leja_points(int M, double* xi) {
+  if (M < 0 || M > 4096 || !xi) return -1;
+  std::vector<double> t;
+  erem::leja_table(M, &t);
+  std::copy(t.begin(), t.end(), xi);
+  return 0;
+}
+
+extern "C" int erem_phi1_divided_differences(int M, const double* xi, double c, double gamma,
+                                             double* d) {
+  return erem::divided_differences(M, xi, c, gamma, d);
+}

@@ -1,0 +1,105 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every entry
+point declared in include/erem.h, and its host-side FP64 scalar routines
+(Leja points, divided differences) agree with the oracle and with
+high-precision arithmetic.  No CUDA computation runs here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import leja
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def E():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1209_5553_gb300 as E
+
+    return E
+
+
+def _declared_functions():
+    src = ""
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src += open(os.path.join(ROOT, "include", f)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"EREM_API\s+[\w\s\*]+?\b(\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ("erem_create", "erem_destroy", "pressure_solve", "erem_set_state", "phi1_apply",
+                 "erem_step", "rosm_step", "erem_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(E):
+    lib = ctypes.CDLL(E.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert set(_declared_functions()) == set(E.EXPORTED)
+
+
+def test_struct_layouts_match_header(E):
+    # sizes of the ABI structs as the C compiler lays them out
+    assert ctypes.sizeof(E.erem_grid) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(E.erem_physics) == 5 * 8 + 8
+    assert ctypes.sizeof(E.erem_stats) % 8 == 0
+
+
+def test_default_options(E):
+    o = E.erem_leja_opts()
+    E.erem_default_leja_opts(o)
+    assert (o.tol_a, o.tol_r, o.p_order, o.m_max, o.max_doublings, o.avg_window) == \
+        (1e-6, 1e-6, 2, 150, 6, 5)
+
+
+def test_null_context_error_message(E):
+    assert E.erem_last_error(None) != ""
+
+
+def test_create_rejects_bad_grids_without_touching_the_gpu(E):
+    for dims in [(4, 8, 8, 1), (2, 0, 8, 1), (2, 8, 8, 3), (3, 8, 8, 0)]:
+        g = E.erem_grid(*dims, 1.0, 1.0, 1.0)
+        with pytest.raises(E.EremError) as ei:
+            E.erem_create(g, E.Physics().c(), E.EREM_FP64)
+        assert ei.value.status == E.EREM_EINVAL
+
+
+def test_host_leja_points_match_oracle(E):
+    a = E.erem_leja_points(200)
+    b = leja.leja_points(200)
+    assert np.max(np.abs(a - b)) < 1e-14
+
+
+@pytest.mark.parametrize("c,gamma", [(-20.0, 10.0), (-3.0, 1.5), (-60.0, 30.0), (-0.5, 0.25),
+                                     (-200.0, 100.0), (-1e-6, 1e-8)])
+def test_host_divided_differences_match_oracle(E, c, gamma):
+    xi = leja.leja_points(150)
+    a = E.erem_phi1_divided_differences(xi, c, gamma)
+    b = leja.phi1_divided_differences(xi, c, gamma)
+    m = np.abs(b) > 1e-280
+    assert np.max(np.abs(a[m] - b[m]) / np.abs(b[m])) < 1e-12
+
+
+def test_host_divided_differences_vs_high_precision(E):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 160
+    xi = leja.leja_points(40)
+    c, gamma = -12.5, 6.0
+    d = E.erem_phi1_divided_differences(xi, c, gamma)
+    xs = [mp.mpf(float(x)) for x in xi]
+    col = [mp.expm1(mp.mpf(c) + gamma * x) / (mp.mpf(c) + gamma * x) for x in xs]
+    ref = [col[0]]
+    for j in range(1, len(xs)):
+        col = [(col[i + 1] - col[i]) / (xs[i + j] - xs[i]) for i in range(len(col) - 1)]
+        ref.append(col[0])
+    for j, r in enumerate(ref):
+        assert abs(d[j] - float(r)) <= 1e-11 * abs(float(r))
