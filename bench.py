@@ -162,7 +162,7 @@ def measured_peaks():
 def recorded_traffic(precision: str, n_cells: int):
     """Bytes per Leja-term launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"leja_term_{precision}_traffic.md")
+    path = os.path.join(ROOT, "profiles", f"k_leja_term_{precision}_channels3d_{round(n_cells ** (1 / 3))}.md")
     src = os.path.join(ROOT, "paper_1209_5553_gb300", "csrc", "kernels.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

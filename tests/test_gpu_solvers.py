@@ -1,0 +1,177 @@
+"""GPU parity of the solvers beside the Leja path: the pressure solve
+(Jacobi CG, FP64) and the Rosenbrock-type steps ROSM(1), ROSM(1/2) and
+ROS2(1) (Jacobi BiCGSTAB stage solves, FP64), against the oracle's direct
+solves; plus the error paths of the C ABI.
+
+Linear-solver tolerances are derived from the stopping rule: a relative
+residual below tol bounds the error by tol * ||b|| * ||A^{-1}||_2, with
+||A^{-1}||_2 taken from the oracle's own matrix (dense SVD on these small
+grids); a factor 10 covers the gap between the recursive and the true
+residual."""
+import numpy as np
+import pytest
+
+import cases as C
+from oracle import fv, timestep as ts
+
+pytestmark = pytest.mark.gpu
+
+PRESSURE_TOL = 1e-12   # CG stopping tolerance used in these tests
+STAGE_TOL = 1e-12      # BiCGSTAB stopping tolerance
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_1209_5553_gb300 as E
+
+    return E
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def pressure_error_bound(A, b, p, tol):
+    smin = np.linalg.svd(A.toarray(), compute_uv=False).min()
+    return 10.0 * tol * np.linalg.norm(b) / smin / np.linalg.norm(p)
+
+
+@pytest.mark.parametrize("dim,nx,ny,nz,fm", [(2, 32, 24, 1, 0), (2, 33, 17, 1, 1), (3, 10, 9, 7, 0)])
+def test_pressure_solve_matches_direct_solution(E, dim, nx, ny, nz, fm):
+    rng = np.random.default_rng(nx + ny)
+    g = fv.Grid(dim, nx, ny, nz)
+    ph = fv.Physics(head_left=1.3, head_right=-0.2, fluid_model=fm)
+    lnk = rng.normal(0, 1.5, g.n)
+    T = rng.uniform(20, 80, g.n) if fm else None
+    A, b = fv.pressure_system(g, ph, lnk, T)
+    p_ref = ts.pressure_solve_direct(g, ph, lnk, T)
+    p0 = fv.linear_head_guess(g, ph)
+    with E.Context(dim, nx, ny, nz, physics=E.Physics(1, 1, 1.3, -0.2, 80.0, fm)) as ctx:
+        p = _t(p0)
+        st = ctx.pressure_solve(_t(lnk), _t(T) if fm else None, p, tol=PRESSURE_TOL, maxit=20000)
+        got = p.cpu().numpy()
+    assert st.lin_resid <= PRESSURE_TOL
+    err = np.linalg.norm(got - p_ref) / np.linalg.norm(p_ref)
+    assert err <= pressure_error_bound(A, b, p_ref, PRESSURE_TOL), err
+    # net inflow and largest face speed from the oracle's fluxes
+    vx, vy, vz = fv.darcy_fluxes(g, ph, lnk, p_ref, T)
+    width = g.ly * (g.lz if dim == 3 else 1.0)
+    assert st.flux_in == pytest.approx(vx[:, :, 0].sum(), rel=1e-8)
+    a = g.face_area
+    vmax = max(np.abs(vx).max() / a[0], np.abs(vy).max() / a[1],
+               np.abs(vz).max() / a[2] if vz is not None else 0.0)
+    assert st.vmax == pytest.approx(vmax, rel=1e-8)
+    assert width > 0
+
+
+def test_pressure_solve_host_pointers_and_maxit(E):
+    g = fv.Grid(2, 20, 20)
+    ph = fv.Physics()
+    lnk = np.random.default_rng(1).normal(0, 1, g.n)
+    p_ref = ts.pressure_solve_direct(g, ph, lnk)
+    with E.Context(2, 20, 20) as ctx:
+        p = fv.linear_head_guess(g, ph).copy()
+        ctx.pressure_solve(lnk.copy(), None, p, tol=PRESSURE_TOL)
+        assert np.max(np.abs(p - p_ref)) < 1e-9
+        p2 = np.zeros(g.n)
+        with pytest.raises(E.EremError) as ei:
+            ctx.pressure_solve(lnk.copy(), None, p2, tol=1e-14, maxit=2)
+        assert ei.value.status == E.EREM_ENOTCONV
+
+
+def _rosm_case():
+    case = C.random_case(2, 18, 14, seed=21, fluid_model=1)
+    return case
+
+
+@pytest.mark.parametrize("scheme", ["rosm1", "rosm_half", "ros2"])
+def test_rosm_step_matches_oracle(E, scheme):
+    case = _rosm_case()
+    prob = case.problem(case.T0)
+    tau = 0.05
+    gam = {"rosm1": 1.0, "rosm_half": 0.5, "ros2": ts.ROS2_GAMMA}[scheme]
+    if scheme == "ros2":
+        ref = ts.ros2_step(prob, case.T0, tau)
+    else:
+        ref = ts.rosm_step(prob, case.T0, tau, gam)
+    A = ts.stage_matrix(prob.J(case.T0), tau, gam)
+    smin = np.linalg.svd(A.toarray(), compute_uv=False).min()
+    G = prob.G(case.T0)
+    inc = ref - case.T0
+    # each stage: error <= 10 tol ||rhs|| / smin, rhs ~ G; scaled by the b_i or 1/gamma
+    bound = 10 * STAGE_TOL * np.linalg.norm(G) / smin * 3.0 / np.linalg.norm(inc)
+    code = {"rosm1": E.EREM_ROSM1, "rosm_half": E.EREM_ROSM_HALF, "ros2": E.EREM_ROS2}[scheme]
+    with E.Context(2, case.grid.nx, case.grid.ny, physics=case.gpu_physics()) as ctx:
+        T = _t(case.T0)
+        st = ctx.rosm_step(T, tau, code, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
+                           lin_tol=STAGE_TOL, maxit=5000)
+        got = T.cpu().numpy()
+    assert st.lin_iters > 0 and st.lin_resid <= STAGE_TOL
+    err = np.linalg.norm((got - case.T0) - inc) / np.linalg.norm(inc)
+    assert err <= max(bound, 1e-12), (err, bound)
+
+
+def test_rosm_then_erem_share_the_context(E):
+    case = C.heat2d_rect(24, 20)
+    prob = case.problem()
+    T1 = ts.ros2_step(prob, case.T0, case.dt)
+    T2, res = ts.erem_step(prob, T1, case.dt)
+    with E.Context(2, 24, 20, physics=case.gpu_physics()) as ctx:
+        T = _t(case.T0)
+        ctx.rosm_step(T, case.dt, E.EREM_ROS2, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
+                      lin_tol=STAGE_TOL)
+        ctx.erem_step(T, case.dt, opts=E.leja_opts(replay=res.schedule))
+        got = T.cpu().numpy()
+    assert C.rel_l2(got, T2) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# error paths: host-detected arguments and device-detected bad inputs
+# ---------------------------------------------------------------------------
+def test_error_paths_leave_state_unchanged(E):
+    case = C.heat2d_rect(16, 12)
+    with E.Context(2, 16, 12, physics=case.gpu_physics()) as ctx:
+        T = _t(case.T0)
+        out = _t(np.zeros(case.n))
+        with pytest.raises(E.EremError) as ei:
+            ctx.phi1_apply(T, out)  # no state yet
+        assert ei.value.status == E.EREM_EINVAL
+        with pytest.raises(E.EremError) as ei:
+            ctx.erem_step(T, 0.0, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam))
+        assert ei.value.status == E.EREM_EINVAL
+        with pytest.raises(E.EremError) as ei:
+            ctx.erem_step(T, 0.05, _t(case.p), None, _t(case.phi), _t(case.lam))
+        assert ei.value.status == E.EREM_EINVAL
+        # NaN in T: detected by the set-up kernels, T left as it was
+        bad = case.T0.copy()
+        bad[7] = np.nan
+        Tb = _t(bad)
+        with pytest.raises(E.EremError) as ei:
+            ctx.erem_step(Tb, 0.05, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam))
+        assert ei.value.status == E.EREM_ENONFINITE
+        assert np.array_equal(Tb.cpu().numpy(), bad, equal_nan=True)
+        # negative conductivity
+        lam = case.lam.copy()
+        lam[3] = -1.0
+        with pytest.raises(E.EremError) as ei:
+            ctx.erem_step(T, 0.05, _t(case.p), _t(case.lnk), _t(case.phi), _t(lam))
+        assert ei.value.status == E.EREM_EINVAL
+        # degree cap without splitting: ENOTCONV, T unchanged
+        before = T.cpu().numpy().copy()
+        with pytest.raises(E.EremError) as ei:
+            ctx.erem_step(T, 0.05, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
+                          opts=E.leja_opts(m_max=3, max_doublings=0))
+        assert ei.value.status == E.EREM_ENOTCONV
+        assert np.array_equal(T.cpu().numpy(), before)
+        # and the context still works afterwards
+        st = ctx.erem_step(T, 0.05)
+        assert st.substeps >= 1 and np.all(np.isfinite(T.cpu().numpy()))
+        # bad replay
+        with pytest.raises(E.EremError) as ei:
+            ctx.erem_step(T, 0.05, opts=E.leja_opts(replay=[2, 5]))
+        assert ei.value.status == E.EREM_EINVAL
