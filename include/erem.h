@@ -203,6 +203,33 @@ EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
                       erem_rosm_scheme scheme, double lin_tol, int maxit,
                       erem_stats* stats, void* stream);
 
+/* Steady pressure solve that allocates nothing (the paper has no
+ * counterpart: this entry point exists for callers that cannot allocate).
+ * Callers that run under a device-memory budget fixed at start-up, inside a
+ * host callback, or under another runtime's allocator cannot call
+ * cudaMalloc; erem_create does, so they could not reach pressure_solve.
+ * This call needs no context: it runs the same Jacobi-preconditioned CG as
+ * pressure_solve, with its work vectors, reduction partials and control
+ * block in one static device array compiled into the library (about 5.8 MB
+ * on every GPU that loads the library, held until the process exits).
+ *   grid, phys  as for erem_create (only the heads and fluid_model are used)
+ *   lnk [N], T [N] (may be NULL: T = 20), p [N] in: guess, out: solution;
+ *   all three must be device pointers (no staging: that would allocate).
+ *   tol, maxit, stats as for pressure_solve.
+ * Limit: round_up(nx, 4) * ny * nz <= 65536 cells, else EREM_EINVAL.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and finds there what the last call left; the call
+ * clears what must start at zero, but calls that overlap on the GPU (from
+ * other streams or threads) race on it.  The call calls no cudaMalloc or
+ * cudaFree.  Errors: EINVAL, ENONFINITE, ENOTCONV, ECUDA (no message string:
+ * there is no context to hold one). */
+EREM_API erem_status erem_pressure_solve_static(const erem_grid* grid,
+                                                const erem_physics* phys,
+                                                const double* lnk, const double* T,
+                                                double* p, double tol, int maxit,
+                                                erem_stats* stats, void* stream);
+
 /* Message of the last failing call on ctx ("" if none; a static message if
  * ctx is NULL).  The pointer stays valid until the next call on ctx. */
 EREM_API const char* erem_last_error(const erem_ctx* ctx);

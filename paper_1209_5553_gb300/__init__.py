@@ -85,6 +85,8 @@ _sigs = {
     "erem_last_error": (ctypes.c_char_p, [_P]),
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
+    "erem_pressure_solve_static": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics),
+                                        _P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -238,6 +240,21 @@ def erem_phi1_divided_differences(xi, c: float, gamma: float) -> np.ndarray:
                                           out.ctypes.data_as(ctypes.POINTER(_D))) != 0:
         raise ValueError("bad arguments")
     return out
+
+
+def erem_pressure_solve_static(grid: erem_grid, phys: erem_physics, lnk, T, p, tol=1e-10,
+                               maxit=100000, stream=None) -> erem_stats:
+    """Pressure solve for callers that cannot allocate device memory: no
+    context, work space in a static device array (at most 65536 padded
+    cells); lnk, T and p must be CUDA tensors."""
+    n = grid.nx * grid.ny * grid.nz
+    st = erem_stats()
+    rc = _lib.erem_pressure_solve_static(ctypes.byref(grid), ctypes.byref(phys), _ptr(lnk, n),
+                                         _ptr(T, n), _ptr(p, n), float(tol), int(maxit),
+                                         ctypes.byref(st), _stream(stream))
+    if rc != EREM_OK:
+        raise EremError(rc, "erem_pressure_solve_static failed")
+    return st
 
 
 # ---------------------------------------------------------------------------
