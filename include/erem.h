@@ -22,8 +22,11 @@
  *   all arrays; the library never keeps a caller pointer after a call.
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
  *   default stream).  Every call enqueues its work on that stream and
- *   returns after it has finished (the Leja stopping test and the linear
- *   solvers read small control blocks back to the host).
+ *   returns once its result is determined (the Leja stopping test and the
+ *   linear solvers read small control blocks back to the host): stats and
+ *   host output arrays are complete on return; device output arrays are
+ *   complete in stream order (the call's last kernel may still be running,
+ *   so synchronise the stream or put dependent work on it).
  * Errors.  Every entry point returns an erem_status; nothing is thrown
  *   across the ABI.  erem_last_error() gives a message for the last failure
  *   of a context.  Arguments are checked on the host (sizes, dt > 0,
@@ -112,9 +115,10 @@ typedef struct {
   double flux_in;       /* pressure_solve: net Darcy inflow through x = 0     */
   double vmax;          /* pressure_solve: largest |face flux| / face area    */
   double t_ms;          /* wall time of the call, milliseconds                */
-  double t_terms_ms;    /* time_terms: summed device time of the Leja terms   */
-  int n_terms_timed;    /* time_terms: number of terms in t_terms_ms          */
+  double t_terms_ms;    /* time_terms: summed device time of the Leja kernels */
+  int n_terms_timed;    /* time_terms: Leja terms those launches computed     */
   int launches;         /* CUDA kernels this call launched                    */
+  int n_launches_timed; /* time_terms: Leja kernel launches in t_terms_ms     */
 } erem_stats;
 
 typedef struct erem_ctx erem_ctx;

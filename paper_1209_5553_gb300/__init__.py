@@ -60,7 +60,8 @@ class erem_stats(ctypes.Structure):
                 ("lin_iters", ctypes.c_int), ("lin_resid", ctypes.c_double),
                 ("flux_in", ctypes.c_double), ("vmax", ctypes.c_double),
                 ("t_ms", ctypes.c_double), ("t_terms_ms", ctypes.c_double),
-                ("n_terms_timed", ctypes.c_int), ("launches", ctypes.c_int)]
+                ("n_terms_timed", ctypes.c_int), ("launches", ctypes.c_int),
+                ("n_launches_timed", ctypes.c_int)]
 
     @property
     def schedule(self):

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -100,6 +101,8 @@ erem_status read_ctrl(erem_ctx* c, cudaStream_t s) {
 }
 
 erem_status check_flags(erem_ctx* c) {
+  if (c->ctrl_h->flags & FLAG_TIMEOUT)
+    return fail(c, EREM_ETIMEOUT, "a two-term Leja pass gave up waiting for a slice (bounded wait)");
   if (c->ctrl_h->flags & FLAG_NONFINITE)
     return fail(c, EREM_ENONFINITE, "non-finite value in an input field or its derived coefficients");
   if (c->ctrl_h->flags & FLAG_BAD_INPUT)
@@ -204,9 +207,12 @@ erem_status ensure_events(erem_ctx* c, int n) {
 
 // out (unpadded, device) = base + dt phi_1(dt J) src, with src and base padded
 // device vectors (base may be null).  J, dt, alpha, beta and the Leja copy of
-// J must be current.
+// J must be current.  With fused_T (linear fluid model) the first substep is
+// started by the fused kernel that computes src = J T + b and base = T^n from
+// the caller's T itself.
 erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double* out,
-                     const Opts& o, erem_stats* st, cudaStream_t s) {
+                     const Opts& o, erem_stats* st, cudaStream_t s,
+                     const double* fused_T = nullptr) {
   const bool replay = !o.replay.empty();
   int mcap = o.m_max;
   if (replay)
@@ -216,7 +222,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
   int n_attempts = replay ? 1 : o.max_doublings + 1;
   int degrees[64];
   double t_terms = 0.0;
-  int n_timed = 0;
+  int n_timed = 0, n_launch_timed = 0;
   if (o.time_terms) EREM_TRY(ensure_events(c, mcap + 1));
   for (int a = 0; a < n_attempts; ++a) {
     const int S = replay ? o.replay[0] : (1 << a);
@@ -241,17 +247,28 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       sp.m_max = replay ? o.replay[1 + k] : o.m_max;
       sp.replay = replay ? 1 : 0;
       const double d0 = c->dd_cache[S].d[0];
-      launch_leja_init(c, u, d0, sp, s);
+      if (fused_T && a == 0 && k == 0)
+        launch_step_init(c, fused_T, d0, sp, s);  // also writes src = G(T) and T^n
+      else
+        launch_leja_init(c, u, d0, sp, s);
       int m = 1, qin = 0, degree = 0;
       const int forced = replay ? o.replay[1 + k] : 0;
       int chunk = forced ? forced : std::max(4, c->last_degree + 2);
+      // launches of this substep: first term, terms computed, output buffer
+      struct Launch { int m, nterms, qout; };
+      std::vector<Launch> launches;
       while (true) {
         const int end = forced ? forced : std::min(M_avail, m + chunk - 1);
-        for (int mm = m; mm <= end; ++mm) {
-          if (o.time_terms) cudaEventRecord(c->ev[2 * mm], s);
-          launch_leja_term(c, mm, qin, cg, s);
-          if (o.time_terms) cudaEventRecord(c->ev[2 * mm + 1], s);
+        int mm = m;
+        while (mm <= end) {
+          const int nt = (c->use_pairs && mm + 1 <= end) ? 2 : 1;
+          if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size()], s);
+          if (nt == 2) launch_leja_pair(c, mm, qin, cg, s);
+          else launch_leja_term(c, mm, qin, cg, s);
+          if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size() + 1], s);
+          launches.push_back(Launch{mm, nt, qin ^ 1});
           qin ^= 1;
+          mm += nt;
         }
         EREM_TRY(check_launch(c, "leja term"));
         EREM_TRY(read_ctrl(c, s));
@@ -264,6 +281,11 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
         }
         if (h.done && !h.fail) {
           degree = h.degree;
+          if (h.overshoot) {  // the pair that met the test at its first term
+            for (const Launch& l : launches)
+              if (l.m == degree && l.nterms == 2)
+                launch_unstep(c, l.qout, c->dd_cache[S].d[degree + 1], s);
+          }
           break;
         }
         if (h.fail || end >= o.m_max) {
@@ -279,11 +301,13 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       }
       if (!ok) break;
       if (o.time_terms) {
-        for (int mm = 1; mm <= degree; ++mm) {
+        for (size_t j = 0; j < launches.size(); ++j) {
+          if (launches[j].m > degree) break;  // returned at once: the test had passed
           float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, c->ev[2 * mm], c->ev[2 * mm + 1]) == cudaSuccess) {
+          if (cudaEventElapsedTime(&ms, c->ev[2 * j], c->ev[2 * j + 1]) == cudaSuccess) {
             t_terms += ms;
-            ++n_timed;
+            n_timed += launches[j].nterms;
+            ++n_launch_timed;
           }
         }
       }
@@ -293,7 +317,9 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       if (k + 1 < S) launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
     }
     if (!ok) continue;
-    launch_finish(c, out, base, S > 1 ? c->w : nullptr, c->P, delta, s);
+    // fused start: T^n is the caller's array itself, updated in place
+    launch_finish(c, out, fused_T ? nullptr : base, S > 1 ? c->w : nullptr, c->P, delta, s,
+                  fused_T ? 1 : 0);
     EREM_TRY(check_launch(c, "finish"));
     if (st) {
       st->substeps = S;
@@ -302,6 +328,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       for (int k = 0; k < S; ++k) st->degree_total += degrees[k];
       st->t_terms_ms = t_terms;
       st->n_terms_timed = n_timed;
+      st->n_launches_timed = n_launch_timed;
     }
     return EREM_OK;
   }
@@ -312,10 +339,10 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
 
 // Assemble face fluxes (if fields changed or the fluid laws depend on T),
 // the cell form of J, G(T^n) and ||T^n||_inf; read alpha, beta back.
-erem_status assemble(erem_ctx* c, bool faces, cudaStream_t s) {
+erem_status assemble(erem_ctx* c, bool faces, bool rhs, cudaStream_t s) {
   if (faces) launch_faces(c, s);
   launch_cellJ(c, s);
-  launch_rhs(c, c->Tn, c->vrhs, 1, s);
+  if (rhs) launch_rhs(c, c->Tn, c->vrhs, 1, s);
   EREM_TRY(check_launch(c, "assembly"));
   EREM_TRY(read_ctrl(c, s));
   EREM_TRY(check_flags(c));
@@ -350,7 +377,7 @@ erem_status load_fields(erem_ctx* c, const double* p, const double* lnk, const d
 // assembly when needed, G(T^n) into vrhs.  *Tdev receives T's device view.
 erem_status prepare_step(erem_ctx* c, double* T, const double* p, const double* lnk,
                          const double* phi, const double* lam, double dt, bool need_interval,
-                         cudaStream_t s, double** Tdev) {
+                         cudaStream_t s, double** Tdev, bool fused = false) {
   if (!T) return fail(c, EREM_EINVAL, "T is NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, EREM_EINVAL, "dt must be finite and > 0");
   const int nnull = (p == nullptr) + (lnk == nullptr) + (phi == nullptr) + (lam == nullptr);
@@ -361,17 +388,20 @@ erem_status prepare_step(erem_ctx* c, double* T, const double* p, const double* 
     return fail(c, EREM_EINVAL, "no stored fields: pass p, lnk, phi, lambda (or call erem_set_state)");
   EREM_TRY(clear_flags(c, s));
   EREM_TRY(resolve(c, 0, T, true, s, Tdev));
-  launch_pack(c, *Tdev, c->Tn, s);
-  if (fields) EREM_TRY(load_fields(c, p, lnk, phi, lam, s));
   const bool tdep = c->phys.fluid_model != 0;
+  // the fused first kernel of run_phi1 computes G(T) and T^n itself
+  const bool rhs_here = !(fused && !tdep);
+  const bool assemble_now = fields || tdep || !c->have_state;
+  if (rhs_here || assemble_now) launch_pack(c, *Tdev, c->Tn, s);
+  if (fields) EREM_TRY(load_fields(c, p, lnk, phi, lam, s));
   const double old_dt = c->dt;
   c->dt = dt;
-  if (fields || tdep || !c->have_state) {
-    EREM_TRY(assemble(c, fields || tdep, s));
+  if (assemble_now) {
+    EREM_TRY(assemble(c, fields || tdep, rhs_here, s));
     c->jl_valid = false;
     c->have_state = true;
   } else {
-    launch_rhs(c, c->Tn, c->vrhs, 1, s);
+    if (rhs_here) launch_rhs(c, c->Tn, c->vrhs, 1, s);
     EREM_TRY(check_launch(c, "rhs"));
     if (dt != old_dt) {
       c->alpha = dt * c->ctrl_h->gmin;
@@ -390,11 +420,14 @@ erem_status prepare_step(erem_ctx* c, double* T, const double* p, const double* 
   return EREM_OK;
 }
 
+// A host output is copied back and complete on return; a device output is
+// complete in stream order (its last kernel may still be running).
 erem_status finish_staged(erem_ctx* c, double* host_T, const double* dev_T, cudaStream_t s) {
-  if (dev_T != host_T)
+  if (dev_T != host_T) {
     EREM_CUDA(c, cudaMemcpyAsync(host_T, dev_T, (size_t)c->N * sizeof(double),
                                  cudaMemcpyDeviceToHost, s));
-  EREM_CUDA(c, cudaStreamSynchronize(s));
+    EREM_CUDA(c, cudaStreamSynchronize(s));
+  }
   return EREM_OK;
 }
 
@@ -489,6 +522,19 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     return bail(EREM_ECUDA);
   c->red_blocks = c->sm_count * 8;
+  c->wave_grid = c->sm_count;
+  int term_waves = 1;  // the one-term grid is one resident wave
+  if (const char* e = std::getenv("EREM_TERM_WAVES")) {  // tuning override
+    const int w = std::atoi(e);
+    if (w >= 1) term_waves = w;
+  }
+  c->term_grid = std::min(c->red_blocks, term_waves * c->sm_count * leja_term_blocks_per_sm(c));
+  c->use_pairs = false;  // two-term passes are opt-in (EREM_LEJA_PAIRS=1)
+  if (const char* e = std::getenv("EREM_WAVE_GRID")) {  // tuning override
+    const int z = std::atoi(e);
+    if (z >= 1) c->wave_grid = z;
+  }
+  if (const char* e = std::getenv("EREM_LEJA_PAIRS")) c->use_pairs = std::atoi(e) != 0;
   const size_t np = (size_t)Np, nf = (size_t)g.ny * g.nz;
   const size_t esz = prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
   erem_status st = EREM_OK;
@@ -497,17 +543,22 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   };
   A(&c->lnk, np); A(&c->phi, np); A(&c->lam, np); A(&c->p, np);
   A(&c->Lx, np); A(&c->Ly, np); A(&c->Fx, np); A(&c->Fy, np); A(&c->icap, np);
-  A(&c->LD0, nf); A(&c->F0, nf);
+  A(&c->LD0, nf); A(&c->F0, nf); A(&c->b0, nf);
   if (g.dim == 3) { A(&c->Lz, np); A(&c->Fz, np); }
   const int nc = g.dim == 3 ? 7 : 5;
-  for (int k = 0; k < nc; ++k) {
-    A(&c->jc[k], np);
-    if (st == EREM_OK) st = dalloc(c, &c->jl[k], np * esz);
-  }
+  for (int k = 0; k < nc; ++k) A(&c->jc[k], np);
+  if (st == EREM_OK) st = dalloc(c, &c->jl_all, (np + 128) / 128 * 128 * nc * esz);
   A(&c->Tn, np); A(&c->vrhs, np); A(&c->vin, np); A(&c->w, np); A(&c->u, np); A(&c->P, np);
   for (int k = 0; k < 2; ++k)
     if (st == EREM_OK) st = dalloc(c, &c->q[k], np * esz);
   A(&c->red_part, (size_t)c->red_blocks * kRedSlots);
+  const WaveGeoHost wg = wave_geometry(c, c->wave_grid);
+  A(&c->wave_part, (size_t)wg.n_items);
+  if (st == EREM_OK) st = dalloc(c, &c->qmid, np * esz);
+  if (st == EREM_OK) st = dalloc(c, (void**)&c->wave_ctr, 4 * sizeof(unsigned));
+  if (st == EREM_OK) st = dalloc(c, (void**)&c->wave_done, (size_t)wg.nslices * sizeof(unsigned));
+  if (st == EREM_OK) st = dalloc(c, (void**)&c->wave_bdone, (size_t)wg.nslices * sizeof(unsigned));
+  A(&c->wave_spart, 2 * (size_t)wg.nslices);
   A(&c->dd_dev, (size_t)kMaxTerms + 2);
   if (st == EREM_OK) st = dalloc(c, (void**)&c->red_cnt, sizeof(unsigned) * 4);
   if (st == EREM_OK) st = dalloc(c, (void**)&c->ctrl, sizeof(Ctrl));
@@ -525,14 +576,13 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
 erem_status erem_destroy(erem_ctx* c) {
   if (!c) return EREM_OK;
   double* dp[] = {c->lnk, c->phi, c->lam, c->p, c->Lx, c->Ly, c->Lz, c->Fx, c->Fy, c->Fz,
-                  c->icap, c->LD0, c->F0, c->Tn, c->vrhs, c->vin, c->w, c->u, c->P,
-                  c->red_part, c->xi_dev, c->dd_dev};
+                  c->icap, c->LD0, c->F0, c->b0, c->Tn, c->vrhs, c->vin, c->w, c->u, c->P,
+                  c->red_part, c->xi_dev, c->dd_dev, c->wave_part, c->wave_spart};
   for (double* p : dp)
     if (p) cudaFree(p);
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < 7; ++k)
     if (c->jc[k]) cudaFree(c->jc[k]);
-    if (c->jl[k]) cudaFree(c->jl[k]);
-  }
+  if (c->jl_all) cudaFree(c->jl_all);
   for (int k = 0; k < 2; ++k)
     if (c->q[k]) cudaFree(c->q[k]);
   for (double* p : c->kv)
@@ -540,6 +590,10 @@ erem_status erem_destroy(erem_ctx* c) {
   for (double* p : c->stage)
     if (p) cudaFree(p);
   if (c->red_cnt) cudaFree(c->red_cnt);
+  if (c->qmid) cudaFree(c->qmid);
+  if (c->wave_ctr) cudaFree(c->wave_ctr);
+  if (c->wave_done) cudaFree(c->wave_done);
+  if (c->wave_bdone) cudaFree(c->wave_bdone);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
   if (c->dd_h) cudaFreeHost(c->dd_h);
@@ -656,8 +710,9 @@ erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk
   Opts o;
   EREM_TRY(parse_opts(c, opts, &o));
   double* Td = nullptr;
-  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td));
-  EREM_TRY(run_phi1(c, c->vrhs, c->Tn, Td, o, st, s));
+  const bool fused = c->phys.fluid_model == 0;
+  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td, fused));
+  EREM_TRY(run_phi1(c, c->vrhs, c->Tn, Td, o, st, s, fused ? Td : nullptr));
   EREM_TRY(finish_staged(c, T, Td, s));
   fill_interval(c, st);
   if (st) {

@@ -18,7 +18,7 @@ constexpr int kMaxTerms = 4096;    // largest Leja degree a context accepts
 constexpr int kRedSlots = 4;       // reduction values per block
 
 // Bits of Ctrl::flags raised by the set-up kernels.
-enum : int { FLAG_NONFINITE = 1, FLAG_BAD_INPUT = 2 };
+enum : int { FLAG_NONFINITE = 1, FLAG_BAD_INPUT = 2, FLAG_TIMEOUT = 4 };
 
 // Parameters of the Leja stopping test of one substep (§4.2).
 struct StopParams {
@@ -50,7 +50,7 @@ struct Ctrl {
   int lin_done;    // linear solver converged (or broke down)
   int lin_it;      // linear solver iterations
   int lin_break;   // linear solver breakdown
-  int pad0;
+  int overshoot;   // a two-term pass added one term past the stopping degree
   double err;      // mean error estimate at the last term
   double yinf;     // ||T^n||_inf of the current state
   double gmin, gmax;   // Gershgorin bounds of J (before the factor dt)
@@ -76,6 +76,9 @@ struct erem_ctx {
   long long N = 0, Np = 0;   // real and padded cell counts
   double hx = 1, hy = 1, hz = 1, vol = 1, ax = 1, ay = 1, az = 1;
   int device = 0, sm_count = 1, red_blocks = 1;
+  bool use_pairs = true;  // two Leja terms per pass (wavefront launch)
+  int wave_grid = 1;      // persistent blocks of the two-term launch
+  int term_grid = 1;      // blocks of the one-term kernel (one resident wave)
   std::string err;
 
   // stored fields (padded, FP64)
@@ -85,13 +88,21 @@ struct erem_ctx {
   double *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;
   double *Fx = nullptr, *Fy = nullptr, *Fz = nullptr;
   double *icap = nullptr, *LD0 = nullptr, *F0 = nullptr;
+  double* b0 = nullptr;   // constant part of G at the x = 0 cells (ny*nz)
   // cell form of J (FP64): D, W, E, S, N, B, T
   double* jc[7] = {};
-  // Leja copy of J scaled by dt / gamma, in the precision of the context
-  void* jl[7] = {};
+  // Leja copy of J scaled by dt / gamma, in the precision of the context,
+  // interleaved per thread-vector (7 or 5 values per cell)
+  void* jl_all = nullptr;
   // vectors
   double *Tn = nullptr, *vrhs = nullptr, *vin = nullptr, *w = nullptr, *u = nullptr, *P = nullptr;
   void* q[2] = {};
+  void* qmid = nullptr;             // q_m of a two-term pass (Leja precision)
+  double* wave_part = nullptr;      // per-item norm partials of a two-term pass
+  unsigned* wave_ctr = nullptr;     // claim and exit counters of a two-term pass
+  unsigned* wave_done = nullptr;    // completed A items per slice
+  unsigned* wave_bdone = nullptr;   // completed B items per slice
+  double* wave_spart = nullptr;     // per-slice norm partials (A then B)
   // linear solvers (allocated on first use)
   double* kv[12] = {};
   // staging for host pointers (allocated on first use)
@@ -133,7 +144,7 @@ int grid_for(const erem_ctx* c, long long items);
 
 void launch_pack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s);
 void launch_finish(const erem_ctx* c, double* out, const double* base, const double* w,
-                   const double* P, double delta, cudaStream_t s);
+                   const double* P, double delta, cudaStream_t s, int in_place = 0);
 void launch_faces(const erem_ctx* c, cudaStream_t s);
 void launch_cellJ(const erem_ctx* c, cudaStream_t s);
 void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s);
@@ -142,7 +153,16 @@ void launch_japply_add(const erem_ctx* c, const double* x, const double* v, doub
                        cudaStream_t s);
 void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
                       cudaStream_t s);
+void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
+                      cudaStream_t s);
+int leja_term_blocks_per_sm(const erem_ctx* c);
 void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
+struct WaveGeoHost {
+  int nslices = 0, slice_cells = 0, cps = 0, chunk_vecs = 0, lag = 0, n_items = 0;
+};
+WaveGeoHost wave_geometry(const erem_ctx* c, int grid);
+void launch_leja_pair(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
+void launch_unstep(const erem_ctx* c, int qbuf, double d, cudaStream_t s);
 void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,
                  cudaStream_t s);
 void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,

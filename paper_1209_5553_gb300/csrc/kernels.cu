@@ -11,6 +11,7 @@
 // the last block to finish (atomic ticket) sums the partials in block order
 // and writes the result into the control block.  Min/max reductions are
 // exact in any order.
+#include <algorithm>
 #include <cstdint>
 
 #include "erem_internal.h"
@@ -39,47 +40,59 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Block-wide reduction; the result is valid in thread 0.  `op` 0 = sum,
-// 1 = min, 2 = max.  Safe to call repeatedly (syncs before reusing smem).
-template <int OP>
-__device__ double block_reduce(double v, double* sh) {
+// Block-wide reduction over BS threads with linear index tid; the result is
+// valid in tid 0.  OP 0 = sum, 1 = min, 2 = max.  Safe to call repeatedly
+// (syncs before reusing smem).
+template <int OP, int BS>
+__device__ double block_reduce_t(double v, double* sh, int tid) {
   v = OP == 0 ? warp_sum(v) : (OP == 1 ? warp_min(v) : warp_max(v));
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double w = threadIdx.x < (NT / 32) ? sh[threadIdx.x]
-                                       : (OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY));
+  if (tid < 32) {
+    double w = tid < (BS / 32) ? sh[tid] : (OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY));
     w = OP == 0 ? warp_sum(w) : (OP == 1 ? warp_min(w) : warp_max(w));
     v = w;
   }
   return v;
 }
+template <int OP>
+__device__ double block_reduce(double v, double* sh) {
+  return block_reduce_t<OP, NT>(v, sh, threadIdx.x);
+}
 
-// Publish this block's partials; returns true in every thread of the last
-// block to arrive.  part has kRedSlots doubles per block.
-__device__ bool publish_partials(double* part, unsigned* cnt, const double* vals, int nv) {
+// Publish this block's partials (block bid of nblocks); returns true in every
+// thread of the last block to arrive.  part has kRedSlots doubles per block.
+__device__ bool publish_partials_t(double* part, unsigned* cnt, const double* vals, int nv,
+                                   int tid, int bid, int nblocks) {
   __shared__ int s_last;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < nv; ++k) part[blockIdx.x * kRedSlots + k] = vals[k];
+  if (tid == 0) {
+    for (int k = 0; k < nv; ++k) part[bid * kRedSlots + k] = vals[k];
     __threadfence();
     const unsigned t = atomicAdd(cnt, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nblocks - 1u);
   }
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
 }
+__device__ bool publish_partials(double* part, unsigned* cnt, const double* vals, int nv) {
+  return publish_partials_t(part, cnt, vals, nv, threadIdx.x, blockIdx.x, gridDim.x);
+}
 
-// Sum (or min/max) of partial k over all blocks, in block order; thread 0.
-template <int OP>
-__device__ double gather_partials(const double* part, int k, double* sh) {
+// Sum (or min/max) of partial k over all blocks, in block order; tid 0.
+template <int OP, int BS>
+__device__ double gather_partials_t(const double* part, int k, double* sh, int tid, int nblocks) {
   double v = OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY);
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) {
+  for (int b = tid; b < nblocks; b += BS) {
     const double x = __ldcg(part + b * kRedSlots + k);
     v = OP == 0 ? v + x : (OP == 1 ? fmin(v, x) : fmax(v, x));
   }
-  return block_reduce<OP>(v, sh);
+  return block_reduce_t<OP, BS>(v, sh, tid);
+}
+template <int OP>
+__device__ double gather_partials(const double* part, int k, double* sh) {
+  return gather_partials_t<OP, NT>(part, k, sh, threadIdx.x, gridDim.x);
 }
 
 struct Geo {
@@ -133,16 +146,18 @@ __global__ void k_pack(const double* __restrict__ src, double* __restrict__ dst,
   if (bad && flags) atomicOr(flags, FLAG_NONFINITE);
 }
 
-// out[i] = base[ip] + w[ip] + delta * P[ip]   (base, w may be null)
-__global__ void k_finish(double* __restrict__ out, const double* __restrict__ base,
+// out[i] = base[ip] + w[ip] + delta * P[ip]  (base, w may be null); with
+// in_place the base is out[i] itself (the caller's unpadded array).
+__global__ void k_finish(double* out, const double* __restrict__ base,
                          const double* __restrict__ w, const double* __restrict__ P, double delta,
-                         Geo g) {
+                         int in_place, Geo g) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
     double v = delta * P[ip];
     if (w) v += w[ip];
     if (base) v += base[ip];
+    if (in_place) v += out[i];
     out[i] = v;
   }
 }
@@ -238,6 +253,7 @@ struct FaceIn {
 };
 struct JOut {
   double* c[7];  // D W E S N B T
+  double* b0;    // constant part of G at the x = 0 cells (linear fluid model)
 };
 
 __global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, Phys ph,
@@ -270,6 +286,8 @@ __global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, P
       const int r = iy + g.ny * iz;
       const double F = f.F0[r];
       D -= f.LD0[r] + (F > 0.0 ? 0.0 : -F * dXi);
+      if (o.b0)
+        o.b0[r] = f.icap[ip] * (f.LD0[r] * ph.T_in + (F > 0.0 ? F * Xof(ph.T_in, fm) : 0.0));
     }
     // +- y faces
     if (iy < g.ny - 1) {
@@ -318,21 +336,13 @@ __global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, P
   }
 }
 
-// Leja copy of J: jl_k = (Tq)(sc * jc_k), all padded cells.
-template <typename Tq>
-__global__ void k_scale_jl(JOut jc, Tq* __restrict__ o0, Tq* __restrict__ o1,
-                           Tq* __restrict__ o2, Tq* __restrict__ o3, Tq* __restrict__ o4,
-                           Tq* __restrict__ o5, Tq* __restrict__ o6, double sc, int Np, int dim) {
+// Leja copy of J: (Tq)(sc * jc_k) for every padded cell, in the warp-tile
+// interleaved layout of LejaCoef (tile of T cells).
+template <typename Tq, int T>
+__global__ void k_scale_jl(JOut jc, Tq* __restrict__ out, double sc, int Np, int nc) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
-    o0[i] = (Tq)(sc * jc.c[0][i]);
-    o1[i] = (Tq)(sc * jc.c[1][i]);
-    o2[i] = (Tq)(sc * jc.c[2][i]);
-    o3[i] = (Tq)(sc * jc.c[3][i]);
-    o4[i] = (Tq)(sc * jc.c[4][i]);
-    if (dim == 3) {
-      o5[i] = (Tq)(sc * jc.c[5][i]);
-      o6[i] = (Tq)(sc * jc.c[6][i]);
-    }
+    const size_t base = (size_t)(i / T) * nc * T + (i % T);
+    for (int k = 0; k < nc; ++k) out[base + (size_t)k * T] = (Tq)(sc * jc.c[k][i]);
   }
 }
 
@@ -438,6 +448,64 @@ __global__ void k_japply_add(JIn J, const double* __restrict__ x, const double* 
   }
 }
 
+// First kernel of an EREM step with the linear fluid model, where G is
+// affine in T: G = J T + b exactly (b non-zero only at the x = 0 cells).
+// One pass reads the caller's T (unpadded, left in place for the final
+// update), writes v = G(T^n) (FP64), q_0 = v in the Leja precision and
+// P_0 = d_0 v, reduces ||T^n||_inf for the error scale, and arms the
+// control block of the first substep.  This replaces the face-form G (about
+// 40 FP64 instructions per cell on GB300's slow FP64 pipe) by 8.
+template <typename Tq>
+__global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
+                            double* __restrict__ G, Tq* __restrict__ q0,
+                            double* __restrict__ P, double d0, Geo g, StopParams sp,
+                            double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->done = 0;
+    ctrl->degree = 0;
+    ctrl->fail = 0;
+    ctrl->nonfinite = 0;
+    ctrl->m_last = 0;
+    ctrl->overshoot = 0;
+    ctrl->err = 0.0;
+    ctrl->sp = sp;
+  }
+  const int sx = 1, sy = g.nx, sz = g.nx * g.ny;
+  double tmax = 0.0;
+  int bad = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double Ti = T[i];
+    double a = J.c[0][ip] * Ti;
+    if (ix > 0) a = fma(J.c[1][ip], T[i - sx], a);
+    if (ix < g.nx - 1) a = fma(J.c[2][ip], T[i + sx], a);
+    if (iy > 0) a = fma(J.c[3][ip], T[i - sy], a);
+    if (iy < g.ny - 1) a = fma(J.c[4][ip], T[i + sy], a);
+    if (g.dim == 3) {
+      if (iz > 0) a = fma(J.c[5][ip], T[i - sz], a);
+      if (iz < g.nz - 1) a = fma(J.c[6][ip], T[i + sz], a);
+    }
+    if (ix == 0) a += b0[iy + g.ny * iz];
+    G[ip] = a;
+    q0[ip] = (Tq)a;
+    P[ip] = d0 * a;
+    bad |= !finite(a);
+    tmax = fmax(tmax, fabs(Ti));
+  }
+  if (bad) atomicOr(&ctrl->flags, FLAG_NONFINITE);
+  const double bmax = block_reduce<2>(tmax, sh);
+  double vals[1] = {bmax};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double a = gather_partials<2>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      ctrl->yinf = a;
+      *cnt = 0;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Newton-Leja recurrence (eq. newt)
 // ---------------------------------------------------------------------------
@@ -486,6 +554,19 @@ __device__ __forceinline__ void stP(double* p, const double (&r)[VEC]) {
   for (int k = 0; k < VEC; k += 2) __stcs(reinterpret_cast<double2*>(p + k), make_double2(r[k], r[k + 1]));
 }
 
+// float -> double, exact, built from the bit fields with integer
+// instructions (the FP64 pipe of GB300 is the scarce unit in the FP32-bulk
+// sweep).  Zeros, subnormals, infinities and NaNs take the hardware
+// conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned lo = u << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // q_0 = u (in the Leja precision), P_0 = d_0 u; block 0 arms the control block.
 template <typename Tq>
 __global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
@@ -496,6 +577,7 @@ __global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
     ctrl->fail = 0;
     ctrl->nonfinite = 0;
     ctrl->m_last = 0;
+    ctrl->overshoot = 0;
     ctrl->err = 0.0;
     ctrl->sp = sp;
   }
@@ -506,10 +588,21 @@ __global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
   }
 }
 
+// The Leja copy of J is interleaved per warp tile of T = 32 VEC cells: the
+// tile's NC coefficient arrays D W E S N (B T) follow one another, T values
+// each.  A warp whose lanes own 32 consecutive VEC-cell vectors reads each
+// coefficient as one contiguous 512-byte run, and the NC runs of a tile are
+// adjacent in memory (one stream instead of NC).  c[k] points at coefficient
+// k of tile 0; the vector starting at cell i reads c[k] + leja_off(i).
 template <typename Tq>
 struct LejaCoef {
-  const Tq* c[7];  // D W E S N B T, scaled by dt / gamma
+  const Tq* c[7];
+  int nc;
 };
+template <int T>
+__device__ __forceinline__ size_t leja_off(int i, int nc) {
+  return (size_t)i + (size_t)(i / T) * (size_t)(nc - 1) * T;
+}
 
 // Stopping test of §4.2 on the estimate of term m (thread 0 of the last block).
 __device__ void stop_test(Ctrl* c, int m, double dm, double S) {
@@ -571,18 +664,19 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
     const Tq ql = ix > 0 ? qi[i - 1] : Tq(0);
     const Tq qr = ix + VEC < g.px ? qi[i + VEC] : Tq(0);
     Tq cD[VEC], cW[VEC], cE[VEC], cS[VEC], cN[VEC], cB[VEC], cT[VEC];
-    ldv_stream<Tq, VEC>(cD, cf.c[0] + i);
-    ldv_stream<Tq, VEC>(cW, cf.c[1] + i);
-    ldv_stream<Tq, VEC>(cE, cf.c[2] + i);
-    ldv_stream<Tq, VEC>(cS, cf.c[3] + i);
-    ldv_stream<Tq, VEC>(cN, cf.c[4] + i);
+    ldv_stream<Tq, VEC>(cD, cf.c[0] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cW, cf.c[1] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cE, cf.c[2] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cS, cf.c[3] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cN, cf.c[4] + leja_off<32 * VEC>(i, cf.nc));
     if (DIM == 3) {
-      ldv_stream<Tq, VEC>(cB, cf.c[5] + i);
-      ldv_stream<Tq, VEC>(cT, cf.c[6] + i);
+      ldv_stream<Tq, VEC>(cB, cf.c[5] + leja_off<32 * VEC>(i, cf.nc));
+      ldv_stream<Tq, VEC>(cT, cf.c[6] + leja_off<32 * VEC>(i, cf.nc));
     }
     double p[VEC];
     ldP<VEC>(p, P + i);
     Tq out[VEC];
+    Tq sq = Tq(0);
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
       const Tq west = k == 0 ? ql : qc[k - 1];
@@ -597,10 +691,17 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
         a = fma(cT[k], qt[k], a);
       }
       out[k] = a;
-      const double ad = (double)a;
-      p[k] = fma(dm, ad, p[k]);
-      acc = fma(ad, ad, acc);
+      if constexpr (sizeof(Tq) == 4) {
+        // FP64 running sum; the squares of the VEC FP32 values are summed in
+        // FP32 and enter the FP64 norm accumulator once per thread-vector
+        p[k] = fma(dm, f2d_exact(a), p[k]);
+        sq = fmaf(a, a, sq);
+      } else {
+        p[k] = fma(dm, a, p[k]);
+        acc = fma(a, a, acc);
+      }
     }
+    if constexpr (sizeof(Tq) == 4) acc += (double)sq;
     stv<Tq, VEC>(qo + i, out);
     stP<VEC>(P + i, p);
   }
@@ -613,6 +714,323 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
       stop_test(ctrl, m, dm, S);
     }
   }
+}
+
+// Two Leja terms per pass (m and m+1), as one streaming "wavefront" launch.
+//
+// The grid is cut into slices along its outermost dimension (z-planes in 3D,
+// y-rows in 2D) and each slice into chunks.  Work items are claimed from an
+// atomic counter in a fixed order: A(s) computes q_m on slice s from q_{m-1}
+// and stores it in a scratch vector; B(s - L), L slices behind, computes
+// q_{m+1} from q_m, adds d_m q_m + d_{m+1} q_{m+1} to P and stores q_{m+1}.
+// B(s) needs A(s-1), A(s), A(s+1); those items come earlier in the claim
+// order, so they are held by running blocks and will finish (B waits for
+// them with a bounded spin; no item ever waits on a later one).  With the
+// lag L, B re-reads the coefficients and q_m a few slices after A brought
+// them in, from L2: per pair of terms HBM sees the coefficients once, q_{m-1}
+// once, q_m written back once, P read and written once and q_{m+1} written.
+// Every access is the vectorised streaming stencil of k_leja_term.
+//
+// Norm partials are kept per item and summed in item order by the last block
+// to leave, which also runs the two stopping tests and resets the counters.
+// When the test passes at term m, P holds d_{m+1} q_{m+1} too many; the host
+// removes it with k_unstep before P is used.
+struct WaveGeo {
+  int nslices;       // slices along the march dimension
+  int slice_cells;   // padded cells per slice
+  int cps;           // chunks per slice
+  int chunk_vecs;    // thread-vectors per chunk (last chunk of a slice may be shorter)
+  int lag;           // L
+  int n_items;       // 2 * nslices * cps
+};
+
+constexpr long long kWaveSpinLimit = 400000000LL;  // cycles (about 0.2 s) before giving up
+
+// L2 eviction priorities (createpolicy + .L2::cache_hint): the A phase
+// keeps the coefficients and q_m in L2 for the B phase (evict_last); the B
+// phase reads them for the last time (evict_first).
+__device__ __forceinline__ unsigned long long l2_policy_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_hint(const float4* a, unsigned long long pol) {
+  float4 r;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(a), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ double2 ld_hint(const double2* a, unsigned long long pol) {
+  double2 r;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+               : "=d"(r.x), "=d"(r.y)
+               : "l"(a), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ void st_hint(float4* a, float4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(a), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_hint(double2* a, double2 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y),
+               "l"(pol)
+               : "memory");
+}
+
+template <typename Tq, int VEC, int DIM>
+__device__ __forceinline__ void stencil_vec(const Tq* __restrict__ q, const LejaCoef<Tq>& cf, const Geo& g,
+                                            int i, int ix, int iy, int iz, Tq shift, bool l2_only,
+                                            unsigned long long cpol, Tq (&out)[VEC]) {
+  Tq qc[VEC], qs[VEC], qn[VEC], qb[VEC], qt[VEC];
+  auto ld = [&](Tq (&r)[VEC], const Tq* p) {
+    using V = typename VecT<Tq, VEC>::V;
+    const V v = l2_only ? __ldcg(reinterpret_cast<const V*>(p)) : *reinterpret_cast<const V*>(p);
+    const Tq* s = reinterpret_cast<const Tq*>(&v);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) r[k] = s[k];
+  };
+  ld(qc, q + i);
+  ld(qs, q + i - (iy > 0 ? g.px : 0));
+  ld(qn, q + i + (iy < g.ny - 1 ? g.px : 0));
+  if (DIM == 3) {
+    ld(qb, q + i - (iz > 0 ? g.plane : 0));
+    ld(qt, q + i + (iz < g.nz - 1 ? g.plane : 0));
+  }
+  const Tq ql = ix > 0 ? (l2_only ? __ldcg(q + i - 1) : q[i - 1]) : Tq(0);
+  const Tq qr = ix + VEC < g.px ? (l2_only ? __ldcg(q + i + VEC) : q[i + VEC]) : Tq(0);
+  constexpr int NC = DIM == 3 ? 7 : 5;
+  Tq c[7][VEC];
+  using V = typename VecT<Tq, VEC>::V;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const V v = ld_hint(reinterpret_cast<const V*>(cf.c[k] + leja_off<32 * VEC>(i, cf.nc)), cpol);
+    const Tq* s = reinterpret_cast<const Tq*>(&v);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) c[k][j] = s[j];
+  }
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) {
+    const Tq west = k == 0 ? ql : qc[k - 1];
+    const Tq east = k == VEC - 1 ? qr : qc[k + 1];
+    Tq a = (c[0][k] - shift) * qc[k];
+    a = fma(c[1][k], west, a);
+    a = fma(c[2][k], east, a);
+    a = fma(c[3][k], qs[k], a);
+    a = fma(c[4][k], qn[k], a);
+    if (DIM == 3) {
+      a = fma(c[5][k], qb[k], a);
+      a = fma(c[6][k], qt[k], a);
+    }
+    out[k] = a;
+  }
+}
+
+template <typename Tq>
+__device__ __forceinline__ double to_f64(Tq v) {
+  if constexpr (sizeof(Tq) == 4) return f2d_exact(v);
+  else return v;
+}
+
+// Warps, not blocks, claim the work items, so nothing in the march needs a
+// block-wide barrier.  An item is WAVE_U thread-vectors per lane of one warp.
+// The norm partial of every item goes to ipart; the last warp to finish a
+// slice (per phase) sums that slice's items in order into spart, and the last
+// warp to leave sums the slice partials in order: the result does not depend
+// on which warp did what.
+constexpr int WAVE_U = 4;
+constexpr int WNT = 128;  // threads per block of the two-term launch
+
+__device__ __forceinline__ double warp_sum_all(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename Tq, int VEC, int DIM>
+__global__ void __launch_bounds__(WNT)
+k_leja_wave(const Tq* __restrict__ qi, Tq* __restrict__ qm, Tq* __restrict__ qo,
+            double* __restrict__ P, LejaCoef<Tq> cf, Geo g, WaveGeo w,
+            const double* __restrict__ xi, const double* __restrict__ dd, double cg, int m,
+            double* __restrict__ ipart, double* __restrict__ spart, unsigned* wctr,
+            unsigned* a_done, unsigned* b_done, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->done) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned total_warps = gridDim.x * (WNT / 32);
+  const Tq s1 = (Tq)(cg + xi[m - 1]);
+  const Tq s2 = (Tq)(cg + xi[m]);
+  const double d1 = dd[m], d2 = dd[m + 1];
+  const int vrow = g.px / VEC;
+  const int svecs = w.slice_cells / VEC;  // thread-vectors per slice
+  const int lag = w.lag, cps = w.cps, ns = w.nslices;
+  const int r1 = lag * cps;
+  const int r2 = r1 + 2 * (ns - lag) * cps;
+  const unsigned long long pol_last = l2_policy_last(), pol_first = l2_policy_first();
+  int t_next = 0;
+  if (lane == 0) t_next = (int)atomicAdd(&wctr[0], 1u);
+  t_next = __shfl_sync(0xffffffffu, t_next, 0);
+  while (true) {
+    const int t = t_next;
+    if (t >= w.n_items) break;
+    if (lane == 0) t_next = (int)atomicAdd(&wctr[0], 1u);  // claim the next item early
+    bool is_b;
+    int slice, chunk;
+    if (t < r1) {
+      is_b = false;
+      slice = t / cps;
+      chunk = t % cps;
+    } else if (t < r2) {
+      const int u = t - r1, r = u % (2 * cps);
+      is_b = r >= cps;
+      slice = lag + u / (2 * cps) - (is_b ? lag : 0);
+      chunk = is_b ? r - cps : r;
+    } else {
+      const int u = t - r2;
+      is_b = true;
+      slice = ns - lag + u / cps;
+      chunk = u % cps;
+    }
+    if (is_b) {  // q_m of slices slice-1 .. slice+1 must be complete
+      if (lane == 0) {
+        const long long t0 = clock64();
+        const int lo = max(slice - 1, 0), hi = min(slice + 1, ns - 1);
+        for (int s = lo; s <= hi; ++s) {
+          while (*(volatile unsigned*)&a_done[s] < (unsigned)cps) {
+            if ((*(volatile int*)&ctrl->flags & FLAG_TIMEOUT) || clock64() - t0 > kWaveSpinLimit) {
+              atomicOr(&ctrl->flags, FLAG_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+        __threadfence();
+      }
+      __syncwarp();
+    }
+    double acc = 0.0;
+    const int v0 = chunk * w.chunk_vecs;
+    const int v1 = min(v0 + w.chunk_vecs, svecs);
+    for (int v = v0 + lane; v < v1; v += 32) {
+      const int tv = slice * svecs + v;
+      const int row = tv / vrow;
+      const int ix = (tv - row * vrow) * VEC;
+      const int iy = row % g.ny;
+      const int iz = row / g.ny;
+      const int i = row * g.px + ix;
+      using V = typename VecT<Tq, VEC>::V;
+      Tq out[VEC];
+      if (!is_b) {
+        stencil_vec<Tq, VEC, DIM>(qi, cf, g, i, ix, iy, iz, s1, false, pol_last, out);
+        V vv;
+        Tq* dst = reinterpret_cast<Tq*>(&vv);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) dst[k] = out[k];
+        st_hint(reinterpret_cast<V*>(qm + i), vv, pol_last);
+        if constexpr (sizeof(Tq) == 4) {
+          Tq sq = Tq(0);
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) sq = fmaf(out[k], out[k], sq);
+          acc += (double)sq;
+        } else {
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) acc = fma(out[k], out[k], acc);
+        }
+      } else {
+        stencil_vec<Tq, VEC, DIM>(qm, cf, g, i, ix, iy, iz, s2, true, pol_first, out);
+        Tq own[VEC];
+        {
+          const V vv = __ldcg(reinterpret_cast<const V*>(qm + i));
+          const Tq* s = reinterpret_cast<const Tq*>(&vv);
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) own[k] = s[k];
+        }
+        double p[VEC];
+        ldP<VEC>(p, P + i);
+        Tq sq = Tq(0);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+          p[k] = fma(d1, to_f64(own[k]), p[k]);
+          p[k] = fma(d2, to_f64(out[k]), p[k]);
+          if constexpr (sizeof(Tq) == 4) sq = fmaf(out[k], out[k], sq);
+          else acc = fma(out[k], out[k], acc);
+        }
+        if constexpr (sizeof(Tq) == 4) acc += (double)sq;
+        stP<VEC>(P + i, p);
+        V vv;
+        Tq* dst = reinterpret_cast<Tq*>(&vv);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) dst[k] = out[k];
+        __stcs(reinterpret_cast<V*>(qo + i), vv);
+      }
+    }
+    acc = warp_sum_all(acc);
+    if (!is_b) __threadfence();  // this lane's q_m stores are visible GPU-wide
+    __syncwarp();
+    if (lane == 0) {
+      ipart[t] = acc;
+      __threadfence();
+      unsigned* cnt = is_b ? &b_done[slice] : &a_done[slice];
+      const unsigned prev = atomicAdd(cnt, 1u);
+      if (prev == (unsigned)cps - 1u) {  // last item of this slice and phase
+        __threadfence();
+        double s = 0.0;
+        for (int c = 0; c < cps; ++c) {
+          int it;  // item index of (phase, slice, c)
+          if (!is_b) it = slice < lag ? slice * cps + c : r1 + (slice - lag) * 2 * cps + c;
+          else it = slice < ns - lag ? r1 + slice * 2 * cps + cps + c : r2 + (slice - (ns - lag)) * cps + c;
+          s += __ldcg(ipart + it);
+        }
+        spart[(is_b ? ns : 0) + slice] = s;
+      }
+    }
+    t_next = __shfl_sync(0xffffffffu, t_next, 0);
+  }
+  // leave; the last warp to leave finishes the pass
+  unsigned last = 0;
+  if (lane == 0) {
+    __threadfence();
+    last = atomicAdd(&wctr[1], 1u) == total_warps - 1u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  double S1 = 0.0, S2 = 0.0;
+  for (int s = lane; s < ns; s += 32) {
+    S1 += __ldcg(spart + s);
+    S2 += __ldcg(spart + ns + s);
+  }
+  S1 = warp_sum_all(S1);
+  S2 = warp_sum_all(S2);
+  for (int s = lane; s < ns; s += 32) {
+    a_done[s] = 0u;
+    b_done[s] = 0u;
+  }
+  if (lane == 0) {
+    wctr[0] = 0u;
+    wctr[1] = 0u;
+    if (ctrl->flags & FLAG_TIMEOUT) {
+      ctrl->done = 1;
+    } else {
+      stop_test(ctrl, m, d1, S1);
+      if (!ctrl->done)
+        stop_test(ctrl, m + 1, d2, S2);
+      else if (ctrl->degree == m)
+        ctrl->overshoot = 1;
+    }
+  }
+}
+
+// P -= d q: removes the extra term of a pair whose first term met the test.
+template <typename Tq>
+__global__ void k_unstep(double* __restrict__ P, const Tq* __restrict__ q, double d, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
+    P[i] = fma(-d, to_f64(q[i]), P[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1087,9 +1505,9 @@ void launch_pack(const erem_ctx* c, const double* src, double* dst, cudaStream_t
 }
 
 void launch_finish(const erem_ctx* c, double* out, const double* base, const double* w,
-                   const double* P, double delta, cudaStream_t s) {
+                   const double* P, double delta, cudaStream_t s, int in_place) {
   ++c->launches;
-  k_finish<<<blocks_cells(c), NT, 0, s>>>(out, base, w, P, delta, geo_of(c));
+  k_finish<<<blocks_cells(c), NT, 0, s>>>(out, base, w, P, delta, in_place, geo_of(c));
 }
 
 void launch_faces(const erem_ctx* c, cudaStream_t s) {
@@ -1102,6 +1520,7 @@ void launch_faces(const erem_ctx* c, cudaStream_t s) {
 void launch_cellJ(const erem_ctx* c, cudaStream_t s) {
   JOut o;
   for (int k = 0; k < 7; ++k) o.c[k] = c->jc[k];
+  o.b0 = c->b0;
   ++c->launches;
   k_cellJ<<<blocks_cells(c), NT, 0, s>>>(face_in(c), c->Tn, o, geo_of(c), phys_of(c), c->red_part,
                                          c->red_cnt, c->ctrl);
@@ -1110,19 +1529,23 @@ void launch_cellJ(const erem_ctx* c, cudaStream_t s) {
 void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s) {
   JOut jc;
   for (int k = 0; k < 7; ++k) jc.c[k] = c->jc[k];
-  if (c->prec == EREM_FP32_BULK) {
-    float* o[7];
-    for (int k = 0; k < 7; ++k) o[k] = (float*)c->jl[k];
-    ++c->launches;
-    k_scale_jl<float><<<blocks_padded(c), NT, 0, s>>>(jc, o[0], o[1], o[2], o[3], o[4], o[5], o[6],
-                                                       sc, (int)c->Np, c->dim);
-  } else {
-    double* o[7];
-    for (int k = 0; k < 7; ++k) o[k] = (double*)c->jl[k];
-    ++c->launches;
-    k_scale_jl<double><<<blocks_padded(c), NT, 0, s>>>(jc, o[0], o[1], o[2], o[3], o[4], o[5], o[6],
-                                                        sc, (int)c->Np, c->dim);
-  }
+  jc.b0 = nullptr;
+  const int nc = c->dim == 3 ? 7 : 5;
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_scale_jl<float, 128><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jl_all, sc, (int)c->Np, nc);
+  else
+    k_scale_jl<double, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (double*)c->jl_all, sc, (int)c->Np, nc);
+}
+
+// Pointers of the interleaved Leja coefficients for kernels of vector width
+// VEC (tile of 32 VEC cells).
+template <typename Tq, int VEC>
+LejaCoef<Tq> leja_coef(const erem_ctx* c) {
+  LejaCoef<Tq> cf;
+  cf.nc = c->dim == 3 ? 7 : 5;
+  for (int k = 0; k < 7; ++k) cf.c[k] = (const Tq*)c->jl_all + (k < cf.nc ? k * 32 * VEC : 0);
+  return cf;
 }
 
 void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cudaStream_t s) {
@@ -1148,14 +1571,44 @@ void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopP
                                                         sp, c->ctrl);
 }
 
+void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
+                      cudaStream_t s) {
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_step_init<float><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, c->vrhs,
+                                                      (float*)c->q[0], c->P, d0, geo_of(c), sp,
+                                                      c->red_part, c->red_cnt, c->ctrl);
+  else
+    k_step_init<double><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, c->vrhs,
+                                                       (double*)c->q[0], c->P, d0, geo_of(c), sp,
+                                                       c->red_part, c->red_cnt, c->ctrl);
+}
+
+// Resident blocks per SM of the one-term kernel of this context's precision
+// and dimension (its grid-stride grid is one full wave of them).
+int leja_term_blocks_per_sm(const erem_ctx* c) {
+  int n = 0;
+  cudaError_t e;
+  if (c->prec == EREM_FP32_BULK)
+    e = c->dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<float, 4, 3>, NT, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<float, 4, 2>, NT, 0);
+  else
+    e = c->dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<double, 2, 3>, NT, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<double, 2, 2>, NT, 0);
+  if (e != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 4;
+  }
+  return n;
+}
+
 void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
   const Geo g = geo_of(c);
   if (c->prec == EREM_FP32_BULK) {
-    LejaCoef<float> cf;
-    for (int k = 0; k < 7; ++k) cf.c[k] = (const float*)c->jl[k];
+    const LejaCoef<float> cf = leja_coef<float, 4>(c);
     const float* qi = (const float*)c->q[qin];
     float* qo = (float*)c->q[qin ^ 1];
-    const int nb = grid_for(c, c->Np / 4);
+    const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
     ++c->launches;
     if (c->dim == 3)
       k_leja_term<float, 4, 3><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
@@ -1164,11 +1617,10 @@ void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t
       k_leja_term<float, 4, 2><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
                                                  c->red_part, c->red_cnt, c->ctrl);
   } else {
-    LejaCoef<double> cf;
-    for (int k = 0; k < 7; ++k) cf.c[k] = (const double*)c->jl[k];
+    const LejaCoef<double> cf = leja_coef<double, 2>(c);
     const double* qi = (const double*)c->q[qin];
     double* qo = (double*)c->q[qin ^ 1];
-    const int nb = grid_for(c, c->Np / 2);
+    const int nb = std::min(grid_for(c, c->Np / 2), c->term_grid);
     ++c->launches;
     if (c->dim == 3)
       k_leja_term<double, 2, 3><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
@@ -1177,6 +1629,68 @@ void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t
       k_leja_term<double, 2, 2><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
                                                   c->red_part, c->red_cnt, c->ctrl);
   }
+}
+
+WaveGeoHost wave_geometry(const erem_ctx* c, int grid) {
+  WaveGeoHost w;
+  const int vec = c->prec == EREM_FP32_BULK ? 4 : 2;
+  w.nslices = c->dim == 3 ? c->nz : c->ny;
+  w.slice_cells = c->dim == 3 ? c->px * c->ny : c->px;
+  const int svecs = w.slice_cells / vec;
+  w.chunk_vecs = 32 * WAVE_U;  // one warp's item
+  if (w.chunk_vecs > svecs) w.chunk_vecs = svecs;
+  w.cps = (svecs + w.chunk_vecs - 1) / w.chunk_vecs;
+  // slices in flight ~ warps / (2 cps); the lag keeps B clear of them
+  const int warps = grid * (WNT / 32);
+  const int inflight = (warps + 2 * w.cps - 1) / (2 * w.cps);
+  w.lag = 2 + (3 * inflight + 1) / 2;
+  if (w.lag > w.nslices) w.lag = w.nslices;
+  w.n_items = 2 * w.nslices * w.cps;
+  return w;
+}
+
+void launch_leja_pair(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
+  const Geo g = geo_of(c);
+  const WaveGeoHost h = wave_geometry(c, c->wave_grid);
+  WaveGeo w{h.nslices, h.slice_cells, h.cps, h.chunk_vecs, h.lag, h.n_items};
+  int grid = c->wave_grid;
+  if (grid * (WNT / 32) > h.n_items) grid = (h.n_items + WNT / 32 - 1) / (WNT / 32);
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK) {
+    const LejaCoef<float> cf = leja_coef<float, 4>(c);
+    const float* qi = (const float*)c->q[qin];
+    float* qo = (float*)c->q[qin ^ 1];
+    float* qm = (float*)c->qmid;
+    if (c->dim == 3)
+      k_leja_wave<float, 4, 3><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev, c->dd_dev,
+                                                   cg, m, c->wave_part, c->wave_spart, c->wave_ctr,
+                                                   c->wave_done, c->wave_bdone, c->ctrl);
+    else
+      k_leja_wave<float, 4, 2><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev, c->dd_dev,
+                                                   cg, m, c->wave_part, c->wave_spart, c->wave_ctr,
+                                                   c->wave_done, c->wave_bdone, c->ctrl);
+  } else {
+    const LejaCoef<double> cf = leja_coef<double, 2>(c);
+    const double* qi = (const double*)c->q[qin];
+    double* qo = (double*)c->q[qin ^ 1];
+    double* qm = (double*)c->qmid;
+    if (c->dim == 3)
+      k_leja_wave<double, 2, 3><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev,
+                                                    c->dd_dev, cg, m, c->wave_part, c->wave_spart,
+                                                    c->wave_ctr, c->wave_done, c->wave_bdone, c->ctrl);
+    else
+      k_leja_wave<double, 2, 2><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev,
+                                                    c->dd_dev, cg, m, c->wave_part, c->wave_spart,
+                                                    c->wave_ctr, c->wave_done, c->wave_bdone, c->ctrl);
+  }
+}
+
+void launch_unstep(const erem_ctx* c, int qbuf, double d, cudaStream_t s) {
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_unstep<float><<<blocks_padded(c), NT, 0, s>>>(c->P, (const float*)c->q[qbuf], d, (int)c->Np);
+  else
+    k_unstep<double><<<blocks_padded(c), NT, 0, s>>>(c->P, (const double*)c->q[qbuf], d, (int)c->Np);
 }
 
 void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,

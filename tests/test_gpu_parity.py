@@ -241,3 +241,66 @@ def test_runs_are_bitwise_deterministic(E):
             ctx.erem_step(T, case.dt)
             outs.append(T.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+def _phi1_with_env(E, case, v, tau, precision, env, opts=None):
+    import os
+
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update({k: str(val) for k, val in env.items()})
+    try:
+        with _ctx(E, case, precision) as ctx:  # tuning overrides are read at creation
+            ctx.set_state(_t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), tau)
+            out = _t(np.zeros(case.n))
+            st = ctx.phi1_apply(_t(v), out, opts)
+            return out.cpu().numpy(), st
+    finally:
+        for k_, val in old.items():
+            if val is None:
+                os.environ.pop(k_, None)
+            else:
+                os.environ[k_] = val
+
+
+@pytest.mark.parametrize("degree", [1, 2, 7, 12, 31])
+def test_two_term_passes_with_odd_and_even_degrees(E, degree):
+    # a replayed degree d runs d // 2 two-term passes and one single term when d is odd
+    case = C.random_case(3, 19, 13, 11, seed=31)
+    v, _ = _phi1_case(case, case.dt)
+    prob = case.problem(case.T0)
+    sched = [1, degree]
+    ref = leja.phi1_leja(prob.J(case.T0), v, case.dt, float(np.max(np.abs(case.T0))),
+                         LejaOptions(replay=sched))
+    got, st = _phi1_with_env(E, case, v, case.dt, "fp64", {}, E.leja_opts(replay=sched))
+    assert st.schedule == sched
+    assert C.rel_l2(got, ref.value) < FP64_TOL
+
+
+@pytest.mark.parametrize("grid", [1, 3, 7, 64])
+def test_two_term_passes_any_grid_match_single_terms(E, grid):
+    # the two-term wavefront pass gives the same result whatever the number of
+    # persistent blocks (one block walks every item in order; many blocks
+    # overlap A and B items); the single-term path is the comparison
+    case = C.random_case(3, 17, 15, 17, seed=33)
+    v, res = _phi1_case(case, case.dt)
+    for prec, tol in (("fp64", FP64_TOL), ("fp32_bulk", FP32_TOL)):
+        single, st1 = _phi1_with_env(E, case, v, case.dt, prec, {"EREM_LEJA_PAIRS": 0})
+        pair, st2 = _phi1_with_env(E, case, v, case.dt, prec,
+                                   {"EREM_LEJA_PAIRS": 1, "EREM_WAVE_GRID": grid})
+        assert C.rel_l2(pair, res.value) < tol and C.rel_l2(single, res.value) < tol
+        if prec == "fp64":
+            assert st1.schedule == st2.schedule == res.schedule
+
+
+def test_stop_inside_a_pair_removes_the_extra_term(E):
+    # free-running degrees of both parities on several seeds: the result must
+    # equal the oracle's at its own degree
+    parities = set()
+    for seed in range(6):
+        case = C.random_case(2, 23, 21, seed=40 + seed, pe=20.0 + 10 * seed)
+        v, res = _phi1_case(case, case.dt, seed=seed)
+        got, st = _phi1_with_env(E, case, v, case.dt, "fp64", {})
+        assert st.schedule == res.schedule
+        assert C.rel_l2(got, res.value) < FP64_TOL
+        parities.add(res.degrees[0] % 2)
+    assert parities == {0, 1}
