@@ -86,6 +86,14 @@ def barrier(world):
         dist.barrier()
 
 
+def aggregate(ms_local: float, cells: int, steps: int, world: int, device=None):
+    """Whole-job rate of `world` replicas that each ran `steps` steps over
+    `cells` cells: the slowest rank's time sets the job time.  Returns
+    (max ms over ranks, Mcell-steps/s of all ranks)."""
+    ms = max_over_ranks(ms_local, world, device)
+    return ms, world * cells * steps / (ms / 1e3) / 1e6
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     if world == 1:
         return x
@@ -170,7 +178,7 @@ def recorded_traffic(precision: str, n_cells: int):
         vals = {}
         for line in open(path):
             if ":" in line and line.startswith("- "):
-                k, v = line[2:].split(":", 1)
+                k, v = line[2:].split(": ", 1)
                 vals[k.strip()] = v.strip()
         if vals.get("kernels.cu sha256[:16]") != sha:
             return None
@@ -353,8 +361,7 @@ def main(args):
     K, Wu = args.steps, args.warmup
 
     r32 = run_gpu(E, torch, wl, "fp32_bulk", K, Wu, dev, world, sample_clocks=(rank == 0))
-    ms = max_over_ranks(r32["ms"], world, dev)
-    value = world * N * K / (ms / 1e3) / 1e6
+    ms, value = aggregate(r32["ms"], N, K, world, dev)
     peak, peak_kind = measured_peaks()
     b32 = BYTES_PER_CELL_TERM["fp32_bulk"]
     # one Leja launch (one term, or two terms in one pass) must move the
@@ -392,11 +399,11 @@ def main(args):
     }
     if not args.no_fp64:
         r64 = run_gpu(E, torch, wl, "fp64", K, Wu, dev, world)
-        ms64 = max_over_ranks(r64["ms"], world, dev)
+        ms64, value64 = aggregate(r64["ms"], N, K, world, dev)
         b64 = BYTES_PER_CELL_TERM["fp64"]
         ach64 = b64 * N * r64["n_leja"] / (r64["t_terms_ms"] / 1e3) / 1e9 if r64["n_leja"] else None
         rel = float(np.linalg.norm(r32["T"] - r64["T"]) / np.linalg.norm(r64["T"]))
-        line["fp64"] = {"value": world * N * K / (ms64 / 1e3) / 1e6, "ms_per_step": ms64 / K,
+        line["fp64"] = {"value": value64, "ms_per_step": ms64 / K,
                         "achieved_gbs": ach64, "algorithmic_bytes_per_cell_per_launch": b64,
                         "term_ms_avg": r64["t_terms_ms"] / max(r64["n_terms"], 1),
                         "degrees_per_step": [s[1:] if s[0] == 1 else s for s in r64["degrees"]]}
