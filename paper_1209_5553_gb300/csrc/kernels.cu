@@ -567,6 +567,106 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// The same first kernel when nx is a multiple of 4 (the caller's T then has
+// the padded layout): each thread owns four consecutive cells and moves them
+// with 128-bit loads and stores.  ||T^n||_inf and the finiteness checks use
+// integer operations on the bit patterns (for |x| the order of the bits is
+// the order of the values), so the FP64 pipe only does the 8 FMAs of G.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ bool bits_finite(unsigned long long b) {
+  return (b >> 52) != 0x7ffULL;
+}
+
+template <typename Tq, int DIM>
+__global__ void __launch_bounds__(NT)
+k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
+                double* __restrict__ G, Tq* __restrict__ q0, double* __restrict__ P, double d0,
+                Geo g, StopParams sp, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->done = 0;
+    ctrl->degree = 0;
+    ctrl->fail = 0;
+    ctrl->nonfinite = 0;
+    ctrl->m_last = 0;
+    ctrl->overshoot = 0;
+    ctrl->err = 0.0;
+    ctrl->sp = sp;
+  }
+  unsigned long long tmax = 0ULL;
+  bool bad = false;
+  const int nvec = g.Np / 4;
+  const int vrow = g.px / 4;
+  for (int t = blockIdx.x * NT + threadIdx.x; t < nvec; t += gridDim.x * NT) {
+    const int row = t / vrow;
+    const int ix = (t - row * vrow) * 4;
+    const int iy = row % g.ny;
+    const int iz = row / g.ny;
+    const int i = row * g.px + ix;
+    double tc[4], ts[4], tn[4], tb[4], tt[4];
+    ldP<4>(tc, T + i);
+    ldP<4>(ts, T + i - (iy > 0 ? g.px : 0));
+    ldP<4>(tn, T + i + (iy < g.ny - 1 ? g.px : 0));
+    if (DIM == 3) {
+      ldP<4>(tb, T + i - (iz > 0 ? g.plane : 0));
+      ldP<4>(tt, T + i + (iz < g.nz - 1 ? g.plane : 0));
+    }
+    const double tl = ix > 0 ? T[i - 1] : 0.0;
+    const double tr = ix + 4 < g.px ? T[i + 4] : 0.0;
+    constexpr int NC = DIM == 3 ? 7 : 5;
+    double c[7][4];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) ldP<4>(c[k], J.c[k] + i);
+    double a[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double west = v == 0 ? tl : tc[v - 1];
+      const double east = v == 3 ? tr : tc[v + 1];
+      double x = c[0][v] * tc[v];
+      x = fma(c[1][v], west, x);
+      x = fma(c[2][v], east, x);
+      x = fma(c[3][v], ts[v], x);
+      x = fma(c[4][v], tn[v], x);
+      if (DIM == 3) {
+        x = fma(c[5][v], tb[v], x);
+        x = fma(c[6][v], tt[v], x);
+      }
+      a[v] = x;
+    }
+    if (ix == 0) a[0] += b0[iy + g.ny * iz];
+    double p[4];
+    Tq qv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      p[v] = d0 * a[v];
+      qv[v] = (Tq)a[v];
+      const unsigned long long tb_ = abs_bits(tc[v]);
+      tmax = tmax > tb_ ? tmax : tb_;
+      bad |= !bits_finite(tb_) | !bits_finite(abs_bits(a[v]));
+    }
+    stP<4>(G + i, a);
+    stP<4>(P + i, p);
+    if constexpr (sizeof(Tq) == 4) {
+      *reinterpret_cast<float4*>(q0 + i) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+    } else {
+      *reinterpret_cast<double2*>(q0 + i) = make_double2(qv[0], qv[1]);
+      *reinterpret_cast<double2*>(q0 + i + 2) = make_double2(qv[2], qv[3]);
+    }
+  }
+  if (bad) atomicOr(&ctrl->flags, FLAG_NONFINITE);
+  const double bmax = block_reduce<2>(__longlong_as_double((long long)tmax), sh);
+  double vals[1] = {bmax};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double a = gather_partials<2>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      ctrl->yinf = a;
+      *cnt = 0;
+    }
+  }
+}
+
 // q_0 = u (in the Leja precision), P_0 = d_0 u; block 0 arms the control block.
 template <typename Tq>
 __global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
@@ -1574,6 +1674,26 @@ void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopP
 void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
                       cudaStream_t s) {
   ++c->launches;
+  if (c->px == c->nx) {  // unpadded rows: four cells per thread
+    const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
+    const Geo g = geo_of(c);
+    if (c->prec == EREM_FP32_BULK) {
+      if (c->dim == 3)
+        k_step_init_vec<float, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (float*)c->q[0], c->P,
+                                                    d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+      else
+        k_step_init_vec<float, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (float*)c->q[0], c->P,
+                                                    d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+    } else {
+      if (c->dim == 3)
+        k_step_init_vec<double, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (double*)c->q[0],
+                                                     c->P, d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+      else
+        k_step_init_vec<double, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (double*)c->q[0],
+                                                     c->P, d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+    }
+    return;
+  }
   if (c->prec == EREM_FP32_BULK)
     k_step_init<float><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, c->vrhs,
                                                       (float*)c->q[0], c->P, d0, geo_of(c), sp,
