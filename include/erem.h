@@ -249,6 +249,110 @@ EREM_API int erem_leja_points(int M, double* xi);
 EREM_API int erem_phi1_divided_differences(int M, const double* xi, double c,
                                   double gamma, double* d);
 
+/* ------------------------------------------------------------------------
+ * Batched ensembles.  The paper treats one realization at a time (§5); an
+ * ensemble of independent 2D realizations of different sizes runs here as a
+ * batch: every member takes exactly the EREM step of erem_step (fluid_model
+ * 0: fixed Darcy fluxes, so J and the divided differences are set once per
+ * member), and one run advances every member by the same number of steps.
+ *
+ * On the device every member is a small state machine (G(T^n) -> Leja terms
+ * with the stopping test of §4.2 -> substep bookkeeping -> T^{n+1}), and one
+ * launch of the batched kernel advances every active member by one pass over
+ * its own cells, so members proceed at their own Leja degrees and substep
+ * counts.  Stopping, substep doubling and the end of the run are decided on
+ * the device; a run is one launch of a CUDA graph whose conditional WHILE
+ * node repeats the kernel until every member has finished.  The loop is
+ * bounded: a run stops after steps * (sum over substep levels of
+ * 2^l (m_max + 2) + 2) iterations at most (EREM_ETIMEOUT).
+ * ------------------------------------------------------------------------ */
+typedef struct erem_ens erem_ens;
+
+/* Where each step's substep count starts.  KEEP: at the count the member's
+ * previous step passed with (the first step of a member starts at 1, or at
+ * what erem_ensemble_autotune found).  RESTART: at 1 every step, doubling
+ * on failure as erem_step does (the results then equal erem_step's). */
+typedef enum { EREM_ENS_KEEP_SUBSTEPS = 0, EREM_ENS_RESTART_SUBSTEPS = 1 } erem_ens_policy;
+
+typedef struct {
+  int substep_policy;  /* erem_ens_policy (default KEEP)                    */
+  int tile_vecs;       /* thread-vectors per thread and tile: 1, 2 or 4;
+                          0 = 2, or the value erem_ensemble_autotune chose  */
+  int blocks_per_sm;   /* 0: as many as fit (occupancy)                    */
+  int use_graph;       /* 1: one graph launch per run; 0: the host launches
+                          the kernel in batches and reads a flag between   */
+} erem_ens_config;
+
+typedef struct {
+  int status;          /* EREM_OK, EREM_ENOTCONV or EREM_ENONFINITE        */
+  int steps_done;      /* steps of the last run this member completed     */
+  int substeps;        /* substeps of its last completed step              */
+  int degree_total;    /* sum of that step's degrees                       */
+  int degrees[64];     /* degree of each substep of that step              */
+  int terms;           /* Leja terms evaluated in the last run (failed
+                          attempts included)                               */
+  int passes;          /* other passes over its cells in the last run      */
+  int attempts;        /* failed attempts (substep doublings) in the run   */
+  int pad;
+  double alpha, beta;  /* Gershgorin interval of dt*J                      */
+} erem_ens_member_stats;
+
+typedef struct {
+  double t_ms;           /* device time of the last run (CUDA events)      */
+  long long iterations;  /* launches of the batched kernel in the last run */
+  long long cells;       /* sum of the members' cells                      */
+  long long cell_terms;  /* sum over members of cells x Leja terms         */
+  long long cell_passes; /* sum over members of cells x other passes       */
+  int tile_vecs, grid, use_graph, members_failed;
+} erem_ens_run_stats;
+
+/* Create an ensemble of n_members 2D members (grids[e].dim must be 2),
+ * each with its own grid and physics (fluid_model 0).  Allocates every
+ * member's buffers (as erem_create does for each) and the batch tables.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+EREM_API erem_status erem_ensemble_create(int n_members, const erem_grid* grids,
+                                          const erem_physics* phys, erem_precision prec,
+                                          erem_ens** out);
+EREM_API erem_status erem_ensemble_destroy(erem_ens* ens);
+
+/* Member e's initial state and fields, as erem_set_state (T, p, lnk, phi,
+ * lambda of that member's size; dt > 0).  The ensemble keeps T on the
+ * device from here on.  Errors as erem_set_state. */
+EREM_API erem_status erem_ensemble_set_member(erem_ens* ens, int e, const double* T,
+                                              const double* p, const double* lnk,
+                                              const double* phi, const double* lambda,
+                                              double dt, void* stream);
+
+/* Copy member e's current temperature into T [N_e] (device or host). */
+EREM_API erem_status erem_ensemble_get_member(erem_ens* ens, int e, double* T, void* stream);
+
+/* Leja options (as for erem_step; replay and time_terms are not accepted)
+ * and batching configuration; either pointer may be NULL (defaults). */
+EREM_API erem_status erem_ensemble_configure(erem_ens* ens, const erem_leja_opts* opts,
+                                             const erem_ens_config* cfg);
+
+/* Tile-size and substep autotuner: runs probe_steps steps of the whole
+ * ensemble for each tile size (1, 2, 4 thread-vectors per thread), keeps the
+ * fastest, and restores every member's temperature afterwards.  Under the
+ * KEEP policy each member then starts at the substep count its first probe
+ * step passed with (the count erem_step would also reach, by doubling).
+ * Errors as erem_ensemble_run. */
+EREM_API erem_status erem_ensemble_autotune(erem_ens* ens, int probe_steps, void* stream);
+
+/* Advance every member by `steps` EREM steps (one graph launch).  Returns
+ * when the run is complete.  A member that fails keeps the temperature of
+ * the start of its failing step and stops; the call then returns the first
+ * failing member's status (ENOTCONV or ENONFINITE) and
+ * erem_ensemble_member_stats tells which members failed.
+ * Errors: EINVAL (a member without state), ENOTCONV, ENONFINITE, ETIMEOUT,
+ * ECUDA. */
+EREM_API erem_status erem_ensemble_run(erem_ens* ens, int steps, void* stream);
+
+EREM_API erem_status erem_ensemble_member_stats(const erem_ens* ens, int e,
+                                                erem_ens_member_stats* out);
+EREM_API erem_status erem_ensemble_run_stats(const erem_ens* ens, erem_ens_run_stats* out);
+EREM_API const char* erem_ensemble_last_error(const erem_ens* ens);
+
 #ifdef __cplusplus
 }
 #endif

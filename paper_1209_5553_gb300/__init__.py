@@ -68,6 +68,34 @@ class erem_stats(ctypes.Structure):
         return [self.substeps] + [self.degrees[k] for k in range(self.substeps)]
 
 
+EREM_ENS_KEEP_SUBSTEPS, EREM_ENS_RESTART_SUBSTEPS = 0, 1
+
+
+class erem_ens_config(ctypes.Structure):
+    _fields_ = [("substep_policy", ctypes.c_int), ("tile_vecs", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class erem_ens_member_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int),
+                ("substeps", ctypes.c_int), ("degree_total", ctypes.c_int),
+                ("degrees", ctypes.c_int * 64), ("terms", ctypes.c_int),
+                ("passes", ctypes.c_int), ("attempts", ctypes.c_int), ("pad", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+    @property
+    def schedule(self):
+        return [self.substeps] + [self.degrees[k] for k in range(self.substeps)]
+
+
+class erem_ens_run_stats(ctypes.Structure):
+    _fields_ = [("t_ms", ctypes.c_double), ("iterations", ctypes.c_longlong),
+                ("cells", ctypes.c_longlong), ("cell_terms", ctypes.c_longlong),
+                ("cell_passes", ctypes.c_longlong), ("tile_vecs", ctypes.c_int),
+                ("grid", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("members_failed", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -88,6 +116,18 @@ _sigs = {
     "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
     "erem_pressure_solve_static": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics),
                                         _P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
+    "erem_ensemble_create": (_I, [_I, ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics), _I,
+                                  ctypes.POINTER(_P)]),
+    "erem_ensemble_destroy": (_I, [_P]),
+    "erem_ensemble_set_member": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P]),
+    "erem_ensemble_get_member": (_I, [_P, _I, _P, _P]),
+    "erem_ensemble_configure": (_I, [_P, ctypes.POINTER(erem_leja_opts),
+                                     ctypes.POINTER(erem_ens_config)]),
+    "erem_ensemble_autotune": (_I, [_P, _I, _P]),
+    "erem_ensemble_run": (_I, [_P, _I, _P]),
+    "erem_ensemble_member_stats": (_I, [_P, _I, ctypes.POINTER(erem_ens_member_stats)]),
+    "erem_ensemble_run_stats": (_I, [_P, ctypes.POINTER(erem_ens_run_stats)]),
+    "erem_ensemble_last_error": (ctypes.c_char_p, [_P]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -258,6 +298,67 @@ def erem_pressure_solve_static(grid: erem_grid, phys: erem_physics, lnk, T, p, t
     return st
 
 
+def erem_ensemble_create(grids, physics, precision: int = EREM_FP64):
+    n = len(grids)
+    ga = (erem_grid * n)(*grids)
+    pa = (erem_physics * n)(*physics)
+    h = _P()
+    st = _lib.erem_ensemble_create(n, ga, pa, int(precision), ctypes.byref(h))
+    if st != EREM_OK:
+        raise EremError(st, "erem_ensemble_create failed")
+    return h
+
+
+def erem_ensemble_destroy(ens) -> None:
+    _lib.erem_ensemble_destroy(ens)
+
+
+def erem_ensemble_last_error(ens) -> str:
+    r = _lib.erem_ensemble_last_error(ens)
+    return r.decode() if r else ""
+
+
+def _echeck(ens, st):
+    if st != EREM_OK:
+        raise EremError(st, erem_ensemble_last_error(ens))
+
+
+def erem_ensemble_set_member(ens, e, n, T, p, lnk, phi, lam, dt, stream=None) -> None:
+    _echeck(ens, _lib.erem_ensemble_set_member(ens, int(e), _ptr(T, n), _ptr(p, n), _ptr(lnk, n),
+                                               _ptr(phi, n), _ptr(lam, n), float(dt),
+                                               _stream(stream)))
+
+
+def erem_ensemble_get_member(ens, e, n, T, stream=None) -> None:
+    _echeck(ens, _lib.erem_ensemble_get_member(ens, int(e), _ptr(T, n), _stream(stream)))
+
+
+def erem_ensemble_configure(ens, opts: erem_leja_opts | None = None,
+                            cfg: erem_ens_config | None = None) -> None:
+    _echeck(ens, _lib.erem_ensemble_configure(ens, ctypes.byref(opts) if opts is not None else None,
+                                              ctypes.byref(cfg) if cfg is not None else None))
+
+
+def erem_ensemble_autotune(ens, probe_steps=1, stream=None) -> None:
+    _echeck(ens, _lib.erem_ensemble_autotune(ens, int(probe_steps), _stream(stream)))
+
+
+def erem_ensemble_run(ens, steps, stream=None) -> None:
+    _echeck(ens, _lib.erem_ensemble_run(ens, int(steps), _stream(stream)))
+
+
+def erem_ensemble_member_stats(ens, e) -> erem_ens_member_stats:
+    st = erem_ens_member_stats()
+    _echeck(ens, _lib.erem_ensemble_member_stats(ens, int(e), ctypes.byref(st)))
+    return st
+
+
+def erem_ensemble_run_stats(ens) -> erem_ens_run_stats:
+    st = erem_ens_run_stats()
+    _echeck(ens, _lib.erem_ensemble_run_stats(ens, ctypes.byref(st)))
+    return st
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -327,3 +428,61 @@ class Context:
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):
         return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)
+
+
+class Ensemble:
+    """Owns one erem_ens (a batch of independent 2D members); methods
+    forward to the erem_ensemble_* entry points.  members: list of
+    (nx, ny, Physics)."""
+
+    def __init__(self, members, precision="fp64", lx=1.0, ly=1.0):
+        prec = {"fp64": EREM_FP64, "fp32_bulk": EREM_FP32_BULK}[precision] \
+            if isinstance(precision, str) else int(precision)
+        self.sizes = [nx * ny for nx, ny, _ in members]
+        grids = [erem_grid(2, nx, ny, 1, lx, ly, 1.0) for nx, ny, _ in members]
+        phys = [(ph or Physics()).c() for _, _, ph in members]
+        self._h = erem_ensemble_create(grids, phys, prec)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            erem_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def set_member(self, e, T, p, lnk, phi, lam, dt, stream=None):
+        erem_ensemble_set_member(self._h, e, self.sizes[e], T, p, lnk, phi, lam, dt, stream)
+
+    def get_member(self, e, T, stream=None):
+        erem_ensemble_get_member(self._h, e, self.sizes[e], T, stream)
+
+    def configure(self, opts=None, policy=EREM_ENS_KEEP_SUBSTEPS, tile_vecs=0, blocks_per_sm=0,
+                  use_graph=True):
+        cfg = erem_ens_config(int(policy), int(tile_vecs), int(blocks_per_sm), 1 if use_graph else 0)
+        erem_ensemble_configure(self._h, opts, cfg)
+
+    def autotune(self, probe_steps=1, stream=None):
+        erem_ensemble_autotune(self._h, probe_steps, stream)
+
+    def run(self, steps, stream=None) -> erem_ens_run_stats:
+        erem_ensemble_run(self._h, steps, stream)
+        return erem_ensemble_run_stats(self._h)
+
+    def member_stats(self, e) -> erem_ens_member_stats:
+        return erem_ensemble_member_stats(self._h, e)
+
+    def run_stats(self) -> erem_ens_run_stats:
+        return erem_ensemble_run_stats(self._h)

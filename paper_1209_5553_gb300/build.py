@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liberem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "abi.cpp", "leja_host.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "abi.cpp", "ensemble.cpp", "leja_host.cpp", "noalloc.cu"]
 HEADERS = ["erem_internal.h"]
 
 

@@ -60,6 +60,80 @@ struct Ctrl {
   double e[kMaxTerms + 2];  // error estimates e_1 .. e_m of the substep
 };
 
+// ---------------------------------------------------------------------------
+// Batched ensemble of independent 2D members (ensemble.cpp, k_ens_iter).
+//
+// Every member runs the same EREM step as a single context, as a state
+// machine: one pass over the member's tiles per iteration of the batched
+// kernel, in the phase its state names.  The last block of a member's pass
+// advances the phase; the last block of the whole launch rebuilds the list of
+// active members when one has finished and tells the graph loop whether to go
+// on.
+// ---------------------------------------------------------------------------
+enum : int {
+  ENS_INIT = 0,   // G = J T^n + b, ||T^n||_inf, first substep's q_0 and P
+  ENS_TERM,       // one Leja term and the stopping test
+  ENS_ACCUM,      // w += delta P after a substep that is not the last
+  ENS_SUBSTART,   // next substep: q_0 = G + J w, P = d_0 q_0
+  ENS_FINAL,      // T^{n+1} = T^n + w + delta P
+  ENS_RESTART,    // substeps doubled after a failure: q_0 = G, P = d_0 G
+  ENS_DONE,       // all steps of the run taken
+  ENS_FAILED      // stopped: not converged at the last level, or non-finite
+};
+enum : int { ENS_OK = 0, ENS_NOTCONV = 1, ENS_NONFINITE = 2 };
+constexpr int kEnsMaxLevels = 7;   // substeps 1, 2, .., 64
+
+struct EnsState {
+  int phase;      // ENS_*
+  int level;      // the current attempt takes 2^level substeps
+  int sub;        // substep in progress
+  int step;       // steps completed in this run
+  int target;     // steps of this run
+  int status;     // ENS_OK, ENS_NOTCONV, ENS_NONFINITE
+  int terms;      // Leja terms evaluated in this run, failed attempts included
+  int attempts;   // failed attempts (substep doublings) in this run
+  int last_S;     // substeps of the last completed step
+  int passes;     // passes of the other phases in this run
+  int last_deg[64];  // degrees of the last completed step
+  int cur_deg[64];   // degrees of the step in progress
+};
+
+struct EnsMember {
+  int nx, ny, px, Np;   // 2D geometry, padded pitch
+  int tiles;            // tiles of this member
+  int pad[3];
+  const double* jc[5];  // FP64 cell form of J: D W E S N (padded)
+  const double* b0;     // constant part of G at the x = 0 cells (ny)
+  const void* jl;       // Leja copy of J (context precision, interleaved)
+  double *T, *G, *w, *P;
+  void* q[2];
+  double* part;         // kRedSlots doubles per tile
+  unsigned* cnt;        // tile ticket
+  Ctrl* ctrl;           // stopping test state
+  EnsState* st;
+  const double* dd;     // kEnsMaxLevels tables of mmax + 1 divided differences
+  StopParams sp;        // delta of level 0 (= dt)
+  double dt, cg;        // step, c / gamma
+};
+
+struct EnsLaunch {
+  int prec;         // EREM_FP64 or EREM_FP32_BULK
+  int U;            // thread-vectors per thread in one tile
+  int grid;         // blocks
+  int n_members;
+  int nlev;         // substep levels allowed (max_doublings + 1)
+  int mmax;         // entries per divided-difference table - 1
+  int restart;      // 1: each step starts again from one substep
+  int max_iters;    // bound on loop iterations of one run
+  const EnsMember* mem;
+  const double* xi;
+  // act[0] active members, act[1] their tiles, act[2] list stale, act[3]
+  // loop goes on; then act_member[n_members], act_start[n_members + 1]
+  int* act;
+  unsigned* gcnt;   // launch ticket
+  unsigned* iters;  // iterations taken
+};
+
 struct DDEntry {
   double c = 0, gamma = 0;
   int M = -1;
@@ -178,6 +252,15 @@ void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cud
 void launch_bicg_init(const erem_ctx* c, const double* b, double sigma, double tol,
                       cudaStream_t s);
 void launch_bicg_iter(const erem_ctx* c, double sigma, cudaStream_t s);
+
+// batched ensemble
+int ens_tile_cells(int prec, int U);
+int ens_blocks_per_sm(int prec, int U);
+void launch_ens_iter(const EnsLaunch& L, cudaStream_t s);
+// Graph with one conditional WHILE node whose body is the batched kernel;
+// the kernel ends the loop.
+cudaError_t build_ens_graph(const EnsLaunch& L, cudaGraph_t* graph, cudaGraphExec_t* exec);
+void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s);
 
 // host scalar side (leja_host.cpp)
 void leja_table(int M, std::vector<double>* out);

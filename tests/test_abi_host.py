@@ -54,6 +54,37 @@ def test_struct_layouts_match_header(E):
     assert ctypes.sizeof(E.erem_stats) % 8 == 0
 
 
+def test_ensemble_struct_layouts_match_the_c_compiler(E, tmp_path):
+    # the binding's ctypes layouts against the header as gcc lays it out
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "erem.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(erem_ens_config), '
+                   'sizeof(erem_ens_member_stats), sizeof(erem_ens_run_stats), '
+                   'offsetof(erem_ens_member_stats, alpha), offsetof(erem_ens_run_stats, tile_vecs)); '
+                   'return 0; }\n')
+    exe = tmp_path / "sizes"
+    import subprocess
+
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == [ctypes.sizeof(E.erem_ens_config), ctypes.sizeof(E.erem_ens_member_stats),
+                   ctypes.sizeof(E.erem_ens_run_stats), E.erem_ens_member_stats.alpha.offset,
+                   E.erem_ens_run_stats.tile_vecs.offset]
+
+
+def test_ensemble_create_rejects_bad_members_without_touching_the_gpu(E):
+    ph = E.Physics().c()
+    g2 = E.erem_grid(2, 8, 8, 1, 1.0, 1.0, 1.0)
+    g3 = E.erem_grid(3, 8, 8, 8, 1.0, 1.0, 1.0)
+    nonlinear = E.Physics(fluid_model=1).c()
+    for grids, phys in [([g2, g3], [ph, ph]), ([g2], [nonlinear]), ([], [])]:
+        with pytest.raises(E.EremError) as ei:
+            E.erem_ensemble_create(grids, phys, E.EREM_FP32_BULK)
+        assert ei.value.status == E.EREM_EINVAL
+    assert E.erem_ensemble_last_error(None) != ""
+
+
 def test_default_options(E):
     o = E.erem_leja_opts()
     E.erem_default_leja_opts(o)

@@ -1,0 +1,237 @@
+"""Batched ensemble (erem_ensemble_*) against the oracle.
+
+Seven independent 2D members of different shapes (ragged widths, a 5 x 3
+grid, members that span several tiles) and two members whose step has to be
+split into 2 and 4 substeps at first and not later, so that the two
+substep policies take different schedules.  Every member's fields come from
+the oracle side (workloads + the oracle's direct pressure solve); member k
+draws its ln K with seed 20120925 + 4 + 1000 + k like the 512-member
+workload.
+"""
+import numpy as np
+import pytest
+
+import cases as C
+import workloads as W
+from oracle import leja, timestep as ts
+
+pytestmark = pytest.mark.gpu
+
+# (nx, ny, sigma of ln K, dt)
+SPEC = [
+    (13, 11, 0.5, 0.05),
+    (96, 50, 2.5, 0.05),
+    (37, 61, 1.5, 0.05),
+    (5, 3, 1.0, 0.05),
+    (200, 160, 2.0, 0.1),
+    (120, 100, 2.0, 0.2),
+    (64, 64, 1.0, 0.05),
+]
+STEPS = 3
+FP64_TOL = 1e-11
+FP32_TOL = 1e-5
+
+
+def _member_case(k):
+    nx, ny, sigma, dt = SPEC[k]
+    case = C.from_workload(W.heat2d_rect(nx, ny, sigma=sigma, seed=W.SEED_BASE + 4 + 1000 + k,
+                                         steps=STEPS))
+    case.dt = dt
+    return case
+
+
+@pytest.fixture(scope="module")
+def ref():
+    import torch
+
+    assert torch.cuda.is_available()
+    import paper_1209_5553_gb300 as E
+
+    members = []
+    for k in range(len(SPEC)):
+        case = _member_case(k)
+        pb = case.problem()
+        T = case.T0.copy()
+        traj, scheds = [T.copy()], []
+        for _ in range(STEPS):
+            T, res = ts.erem_step(pb, T, case.dt)
+            traj.append(T.copy())
+            scheds.append(res.schedule)
+        members.append((case, pb, traj, scheds))
+    return E, members
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _ensemble(E, members, precision, policy=None, **cfg):
+    ens = E.Ensemble([(m[0].grid.nx, m[0].grid.ny, m[0].gpu_physics()) for m in members], precision)
+    ens.configure(policy=E.EREM_ENS_RESTART_SUBSTEPS if policy is None else policy, **cfg)
+    for k, (case, _, _, _) in enumerate(members):
+        ens.set_member(k, _t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+    return ens
+
+
+def _get(ens, k):
+    import torch
+
+    out = torch.empty(ens.sizes[k], dtype=torch.float64, device="cuda")
+    ens.get_member(k, out)
+    return out.cpu().numpy()
+
+
+def test_fp64_restart_policy_matches_oracle(ref):
+    E, members = ref
+    with _ensemble(E, members, "fp64") as ens:
+        rs = ens.run(STEPS)
+        assert rs.members_failed == 0 and rs.use_graph == 1 and rs.iterations > 0
+        for k, (case, _, traj, scheds) in enumerate(members):
+            st = ens.member_stats(k)
+            assert st.status == 0 and st.steps_done == STEPS
+            assert st.schedule == scheds[-1], (k, st.schedule, scheds[-1])
+            assert C.rel_l2(_get(ens, k), traj[-1]) < FP64_TOL, k
+
+
+def test_fp64_keep_policy_matches_oracle_replay(ref):
+    # KEEP starts each step at the substep count of the previous one: step by
+    # step, the oracle replays the schedule the ensemble reports
+    E, members = ref
+    with _ensemble(E, members, "fp64", policy=E.EREM_ENS_KEEP_SUBSTEPS) as ens:
+        T = [m[0].T0.copy() for m in members]
+        for step in range(STEPS):
+            ens.run(1)
+            for k, (case, pb, traj, scheds) in enumerate(members):
+                sched = ens.member_stats(k).schedule
+                if step == 0:
+                    assert sched == scheds[0]
+                assert sched[0] >= scheds[step][0]
+                T[k], _ = ts.erem_step(pb, T[k], case.dt, leja.LejaOptions(replay=sched))
+                assert C.rel_l2(_get(ens, k), T[k]) < FP64_TOL, (k, step)
+        # the members that could go back to one substep did not
+        assert ens.member_stats(4).substeps == 2 and members[4][3][-1][0] == 1
+        assert ens.member_stats(5).substeps == 4 and members[5][3][-1][0] == 1
+        # and the schedule change stays within the Leja tolerance
+        for k, (case, _, traj, _) in enumerate(members):
+            assert C.rel_l2(_get(ens, k), traj[-1]) < FP32_TOL
+
+
+def test_fp32_bulk_matches_oracle(ref):
+    E, members = ref
+    with _ensemble(E, members, "fp32_bulk", policy=E.EREM_ENS_KEEP_SUBSTEPS) as ens:
+        ens.run(STEPS)
+        for k, (case, _, traj, _) in enumerate(members):
+            assert C.rel_l2(_get(ens, k), traj[-1]) < FP32_TOL, k
+
+
+@pytest.mark.parametrize("tile_vecs", [1, 4])
+def test_tile_sizes_match_oracle(ref, tile_vecs):
+    E, members = ref
+    with _ensemble(E, members, "fp64", tile_vecs=tile_vecs) as ens:
+        assert ens.run(STEPS).tile_vecs == tile_vecs
+        for k, (case, _, traj, scheds) in enumerate(members):
+            assert ens.member_stats(k).schedule == scheds[-1]
+            assert C.rel_l2(_get(ens, k), traj[-1]) < FP64_TOL, k
+
+
+def test_graph_and_host_driven_loop_agree_bitwise(ref):
+    E, members = ref
+    out = []
+    for graph in (True, False):
+        with _ensemble(E, members, "fp32_bulk", use_graph=graph) as ens:
+            rs = ens.run(STEPS)
+            assert rs.use_graph == (1 if graph else 0)
+            out.append(([_get(ens, k) for k in range(len(members))],
+                        [ens.member_stats(k).terms for k in range(len(members))], rs.iterations))
+    (a, ta, ia), (b, tb, ib) = out
+    assert ta == tb and ia == ib
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_runs_in_pieces_equal_one_run(ref):
+    E, members = ref
+    with _ensemble(E, members, "fp32_bulk") as one, _ensemble(E, members, "fp32_bulk") as three:
+        one.run(STEPS)
+        for _ in range(STEPS):
+            three.run(1)
+        for k in range(len(members)):
+            assert np.array_equal(_get(one, k), _get(three, k))
+
+
+def test_matches_single_context_steps(ref):
+    E, members = ref
+    with _ensemble(E, members, "fp64") as ens:
+        ens.run(STEPS)
+        for k, (case, _, _, _) in enumerate(members):
+            g = case.grid
+            with E.Context(2, g.nx, g.ny, physics=case.gpu_physics()) as ctx:
+                T = _t(case.T0)
+                ctx.set_state(T, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+                for _ in range(STEPS):
+                    ctx.erem_step(T, case.dt)
+                assert C.rel_l2(_get(ens, k), T.cpu().numpy()) < 1e-13, k
+
+
+def test_autotune_restores_state_and_learns_substeps(ref):
+    E, members = ref
+    with _ensemble(E, members, "fp32_bulk", policy=E.EREM_ENS_KEEP_SUBSTEPS) as ens:
+        before = [_get(ens, k) for k in range(len(members))]
+        ens.autotune(1)
+        for k in range(len(members)):
+            assert np.array_equal(_get(ens, k), before[k])
+        rs = ens.run(1)
+        assert rs.tile_vecs in (1, 2, 4)
+        for k, (case, _, traj, scheds) in enumerate(members):
+            st = ens.member_stats(k)
+            # started at the count doubling reached: no failed attempt
+            assert st.attempts == 0 and st.substeps == scheds[0][0]
+            assert st.terms == st.degree_total
+            assert C.rel_l2(_get(ens, k), traj[1]) < FP32_TOL
+
+
+def test_member_failure_is_isolated(ref):
+    # m_max = 40 and one doubling: each member converges or fails as the
+    # oracle with the same options does; failed members keep T^n
+    E, members = ref
+    opts_o = leja.LejaOptions(m_max=40, max_doublings=1)
+    with _ensemble(E, members, "fp64") as ens:
+        ens.configure(E.leja_opts(m_max=40, max_doublings=1), policy=E.EREM_ENS_RESTART_SUBSTEPS)
+        with pytest.raises(E.EremError) as ei:
+            ens.run(1)
+        assert ei.value.status == E.EREM_ENOTCONV
+        n_fail = 0
+        for k, (case, pb, _, _) in enumerate(members):
+            T1, res = ts.erem_step(pb, case.T0, case.dt, opts_o)
+            st = ens.member_stats(k)
+            if res.converged:
+                assert st.status == 0 and st.steps_done == 1
+                assert C.rel_l2(_get(ens, k), T1) < FP64_TOL
+            else:
+                n_fail += 1
+                assert st.status == E.EREM_ENOTCONV and st.steps_done == 0
+                assert np.array_equal(_get(ens, k), case.T0)
+        assert 0 < n_fail < len(members)
+        assert ens.run_stats().members_failed == n_fail
+
+
+def test_host_output_and_argument_errors(ref):
+    E, members = ref
+    with _ensemble(E, members[:2], "fp64") as ens:
+        ens.run(1)
+        host = np.zeros(ens.sizes[1])
+        ens.get_member(1, host)
+        assert np.array_equal(host, _get(ens, 1))
+        for bad in (lambda: ens.run(0), lambda: ens.get_member(2, host),
+                    lambda: ens.configure(E.leja_opts(replay=[1, 5]))):
+            with pytest.raises(E.EremError) as ei:
+                bad()
+            assert ei.value.status == E.EREM_EINVAL
+    case = members[0][0]
+    with E.Ensemble([(case.grid.nx, case.grid.ny, case.gpu_physics())] * 2, "fp64") as ens:
+        ens.set_member(0, _t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), 0.05)
+        with pytest.raises(E.EremError) as ei:
+            ens.run(1)  # member 1 has no state
+        assert ei.value.status == E.EREM_EINVAL
