@@ -60,9 +60,12 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--slab", type=int, default=16, help="z planes of the oracle's sample")
-    ap.add_argument("--workload", choices=["channels3d", "coupled2d"], default="channels3d",
+    ap.add_argument("--workload", choices=["channels3d", "coupled2d", "ensemble"],
+                    default="channels3d",
                     help="channels3d: the 256^3 headline; coupled2d: 1024^2 sequential "
-                         "pressure/temperature with T-dependent fluid laws")
+                         "pressure/temperature with T-dependent fluid laws; ensemble: 512 "
+                         "independent 2D members of 64^2..512^2 cells in one batched run")
+    ap.add_argument("--members", type=int, default=512, help="ensemble members")
     return ap.parse_args()
 
 
@@ -522,11 +525,204 @@ def main_coupled(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the batched ensemble: 512 independent 2D members (n ~ U{64..512}, sigma of
+# ln K ~ U[0.5, 2.5], Peclet 50, dt = 0.05); one "step" advances every member
+# by one EREM step; a run of K steps is one CUDA graph launch
+# ---------------------------------------------------------------------------
+ENS_BYTES_PER_CELL_TERM = {"fp32_bulk": 5 * 4 + 4 + 4 + 16, "fp64": 5 * 8 + 8 + 8 + 16}
+
+
+def ensemble_inputs(E, torch, dev, members):
+    """Member fields, GPU pressure solves and heat capacities (Pe = 50 from
+    each member's Darcy inflow), as host arrays."""
+    import workloads as W
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    out, cg = [], []
+    for e in range(members):
+        wl = W.ensemble_member(e, members)
+        with E.Context(2, wl.nx, wl.ny, physics=E.Physics(1.0, 1.0, wl.head_drop, 0.0,
+                                                            wl.T_inflow, 0)) as ctx:
+            p = t(linear_head(wl.n, wl.nx, wl.head_drop, 0.0))
+            st = ctx.pressure_solve(t(wl.lnk), None, p, tol=1e-10, maxit=200000)
+        rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), st.flux_in / 1.0)
+        out.append((wl, p.cpu().numpy(), E.Physics(rc, rc, wl.head_drop, 0.0, wl.T_inflow, 0)))
+        cg.append(st.lin_iters)
+    return out, cg
+
+
+def make_ensemble(E, inputs, precision, tol):
+    ens = E.Ensemble([(wl.nx, wl.ny, ph) for wl, _, ph in inputs], precision)
+    ens.configure(E.leja_opts(tol=tol), policy=E.EREM_ENS_KEEP_SUBSTEPS)
+    for e, (wl, p, _) in enumerate(inputs):
+        ens.set_member(e, wl.T0, p, wl.lnk, wl.phi, wl.lam, wl.dt)
+    return ens
+
+
+def run_ensemble(E, torch, inputs, precision, steps, warmup, dev, sample_clocks=False):
+    tol = inputs[0][0].tol
+    ens = make_ensemble(E, inputs, precision, tol)
+    t_tune = time.perf_counter()
+    ens.autotune(1)
+    t_tune = time.perf_counter() - t_tune
+    if warmup:
+        ens.run(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(dev.index if dev.index is not None else 0) if sample_clocks else None
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rs = ens.run(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    stats = [ens.member_stats(e) for e in range(len(inputs))]
+    T = [np.zeros(n) for n in ens.sizes]
+    for e in range(len(inputs)):
+        ens.get_member(e, T[e])
+    out = {"ms": ms, "run_ms": rs.t_ms, "iterations": rs.iterations, "cells": rs.cells,
+           "cell_terms": rs.cell_terms, "cell_passes": rs.cell_passes, "tile_vecs": rs.tile_vecs,
+           "grid": rs.grid, "clocks": clocks, "T": T, "tune_s": t_tune,
+           "terms": [s.terms for s in stats], "substeps": [s.substeps for s in stats],
+           "failed": rs.members_failed, "ens": ens}
+    return out
+
+
+def ensemble_e2e(E, torch, ens, inputs, steps):
+    """One run through the public API with host buffers: every member's T is
+    copied in from pinned host memory before the run and read back after."""
+    Th = [torch.from_numpy(np.ascontiguousarray(wl.T0)).pin_memory() for wl, _, _ in inputs]
+    for e in range(len(inputs)):
+        ens.set_temperature(e, Th[e])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for e in range(len(inputs)):
+        ens.set_temperature(e, Th[e])
+    ens.run(steps)
+    for e in range(len(inputs)):
+        ens.get_member(e, Th[e])
+    torch.cuda.synchronize()
+    return time.perf_counter() - t, 8 * sum(ens.sizes)
+
+
+def time_oracle_ensemble(members, n_sample):
+    """The oracle on a bounded sample: one EREM step of each of n_sample
+    members spread over the size range (the oracle's own pressure and Peclet
+    scaling, outside the timing)."""
+    from oracle import fv, timestep as ts
+    from oracle.leja import LejaOptions
+    import workloads as W
+
+    sizes, _ = W.ensemble_sizes(members)
+    order = np.argsort(sizes)
+    picks = [int(order[int(q * (members - 1))]) for q in np.linspace(0.1, 0.9, max(n_sample, 1))]
+    sec, cells = 0.0, 0
+    for e in picks:
+        wl = W.ensemble_member(e, members)
+        g = fv.Grid(2, wl.nx, wl.ny)
+        base = fv.Physics(head_left=wl.head_drop, head_right=0.0, T_inflow=wl.T_inflow)
+        p = ts.pressure_solve_direct(g, base, wl.lnk, wl.T0)
+        vx = fv.darcy_fluxes(g, base, wl.lnk, p, wl.T0)[0]
+        rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), vx[:, :, 0].sum())
+        prob = ts.heat_problem(g, fv.Physics(rc, rc, wl.head_drop, 0.0, wl.T_inflow, 0),
+                               wl.lnk, wl.phi, wl.lam, p)
+        t = time.perf_counter()
+        ts.erem_step(prob, wl.T0, wl.dt, LejaOptions(tol_a=wl.tol, tol_r=wl.tol))
+        sec += time.perf_counter() - t
+        cells += wl.n
+    desc = (f"one oracle EREM step of each of {len(picks)} members (n = "
+            f"{', '.join(str(int(sizes[e])) for e in picks)}) of the {members}-member ensemble")
+    return cells / sec / 1e6, sec, desc
+
+
+def main_ensemble(args):
+    import torch
+
+    import paper_1209_5553_gb300 as E
+
+    rank, world, local = dist_info()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist_init(world, "nccl")
+    K, Wu = args.steps, args.warmup
+    t_in = time.perf_counter()
+    inputs, cg = ensemble_inputs(E, torch, dev, args.members)
+    t_in = time.perf_counter() - t_in
+    cells = sum(wl.n for wl, _, _ in inputs)
+    r32 = run_ensemble(E, torch, inputs, "fp32_bulk", K, Wu, dev, sample_clocks=(rank == 0))
+    ms, value = aggregate(r32["ms"], cells, K, world, dev)
+    peak, peak_kind = measured_peaks()
+    b32 = ENS_BYTES_PER_CELL_TERM["fp32_bulk"]
+    achieved = b32 * r32["cell_terms"] / (r32["run_ms"] / 1e3) / 1e9
+    line = {
+        "metric": "ensemble EREM Mcell-steps/s (512 independent 2D members, 64^2..512^2, FP32-bulk)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wu,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ensemble2d_{args.members}", "members": args.members, "cells": cells,
+                   "sizes": "n ~ U{64..512} (seeded), sigma ~ U[0.5, 2.5], Pe 50, dt 0.05, tol 1e-6",
+                   "substep_policy": "keep (autotuned start)", "tile_vecs": r32["tile_vecs"],
+                   "grid": r32["grid"],
+                   "l2": "aggregate sweep 2.3 GB per term (> L2); tail iterations with few "
+                         "active members can be L2-resident",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "clocks": r32["clocks"],
+        "gpu_launches": r32["iterations"],
+        "ensemble": {"iterations": r32["iterations"], "graph_launches": 1,
+                     "cell_terms": r32["cell_terms"], "cell_passes": r32["cell_passes"],
+                     "terms_per_member_run": {"min": int(min(r32["terms"])),
+                                              "median": float(np.median(r32["terms"])),
+                                              "max": int(max(r32["terms"]))},
+                     "substeps_hist": {str(s): r32["substeps"].count(s) for s in sorted(set(r32["substeps"]))},
+                     "failed": r32["failed"], "autotune_s": r32["tune_s"], "inputs_s": t_in,
+                     "pressure_cg_iters": {"median": float(np.median(cg)), "max": int(max(cg))}},
+        "roofline": {"kernel": f"k_ens_iter<float,4,{r32['tile_vecs']}>", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_cell_term": b32,
+                     "note": "Leja-term bytes only over the whole run (the other passes, about "
+                             f"{100 * r32['cell_passes'] / max(r32['cell_terms'], 1):.1f}% of the "
+                             "cell passes, are not counted): a lower bound"},
+    }
+    if not args.no_fp64:
+        r64 = run_ensemble(E, torch, inputs, "fp64", K, Wu, dev)
+        ms64, value64 = aggregate(r64["ms"], cells, K, world, dev)
+        num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(r32["T"], r64["T"]))
+        den = sum(float(np.sum(b ** 2)) for b in r64["T"])
+        line["fp64"] = {"value": value64, "ms_per_step": ms64 / K, "tile_vecs": r64["tile_vecs"],
+                        "achieved_gbs": ENS_BYTES_PER_CELL_TERM["fp64"] * r64["cell_terms"]
+                        / (r64["run_ms"] / 1e3) / 1e9}
+        line["speedup_fp32_bulk_vs_fp64"] = ms64 / ms
+        line["rel_l2_fp32_bulk_vs_fp64"] = float(np.sqrt(num / den))
+        r64["ens"].close()
+    if not args.no_e2e:
+        sec, nbytes = ensemble_e2e(E, torch, r32["ens"], inputs, K)
+        sec = max_over_ranks(sec, world, dev)
+        line["e2e"] = {"value": world * cells * K / sec / 1e6, "unit": UNIT,
+                       "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": nbytes / K}
+    r32["ens"].close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sec, desc = time_oracle_ensemble(args.members, args.cpu_steps)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                                "sample": f"{desc} ({sec:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse_args()
     if a.impl == "reference":
         main_reference(a)
     elif a.workload == "coupled2d":
         main_coupled(a)
+    elif a.workload == "ensemble":
+        main_ensemble(a)
     else:
         main(a)

@@ -323,6 +323,12 @@ EREM_API erem_status erem_ensemble_set_member(erem_ens* ens, int e, const double
                                               const double* phi, const double* lambda,
                                               double dt, void* stream);
 
+/* Replace member e's temperature by T [N_e] (device or host), keeping its
+ * fields, Jacobian and divided differences (a restart from a saved state).
+ * Errors: EINVAL (no state yet, bad index), ECUDA. */
+EREM_API erem_status erem_ensemble_set_temperature(erem_ens* ens, int e, const double* T,
+                                                   void* stream);
+
 /* Copy member e's current temperature into T [N_e] (device or host). */
 EREM_API erem_status erem_ensemble_get_member(erem_ens* ens, int e, double* T, void* stream);
 

@@ -121,6 +121,7 @@ _sigs = {
     "erem_ensemble_destroy": (_I, [_P]),
     "erem_ensemble_set_member": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P]),
     "erem_ensemble_get_member": (_I, [_P, _I, _P, _P]),
+    "erem_ensemble_set_temperature": (_I, [_P, _I, _P, _P]),
     "erem_ensemble_configure": (_I, [_P, ctypes.POINTER(erem_leja_opts),
                                      ctypes.POINTER(erem_ens_config)]),
     "erem_ensemble_autotune": (_I, [_P, _I, _P]),
@@ -333,6 +334,10 @@ def erem_ensemble_get_member(ens, e, n, T, stream=None) -> None:
     _echeck(ens, _lib.erem_ensemble_get_member(ens, int(e), _ptr(T, n), _stream(stream)))
 
 
+def erem_ensemble_set_temperature(ens, e, n, T, stream=None) -> None:
+    _echeck(ens, _lib.erem_ensemble_set_temperature(ens, int(e), _ptr(T, n), _stream(stream)))
+
+
 def erem_ensemble_configure(ens, opts: erem_leja_opts | None = None,
                             cfg: erem_ens_config | None = None) -> None:
     _echeck(ens, _lib.erem_ensemble_configure(ens, ctypes.byref(opts) if opts is not None else None,
@@ -465,6 +470,9 @@ class Ensemble:
 
     def set_member(self, e, T, p, lnk, phi, lam, dt, stream=None):
         erem_ensemble_set_member(self._h, e, self.sizes[e], T, p, lnk, phi, lam, dt, stream)
+
+    def set_temperature(self, e, T, stream=None):
+        erem_ensemble_set_temperature(self._h, e, self.sizes[e], T, stream)
 
     def get_member(self, e, T, stream=None):
         erem_ensemble_get_member(self._h, e, self.sizes[e], T, stream)

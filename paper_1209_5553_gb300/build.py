@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "liberem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["kernels.cu", "abi.cpp", "ensemble.cpp", "leja_host.cpp", "noalloc.cu"]
-HEADERS = ["erem_internal.h"]
+HEADERS = ["erem_internal.h", "device_common.cuh", "ensemble_kernel.cuh"]
 
 
 def _cuda_home() -> str:

@@ -220,6 +220,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
   EREM_TRY(ensure_leja(c, mcap));
   const double cg = c->cfoc / c->gam;  // the same for every substep level
   int n_attempts = replay ? 1 : o.max_doublings + 1;
+  bool nonfinite_attempt = false;  // the last failed attempt had a non-finite estimate
   int degrees[64];
   double t_terms = 0.0;
   int n_timed = 0, n_launch_timed = 0;
@@ -274,7 +275,14 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
         EREM_TRY(read_ctrl(c, s));
         EREM_TRY(check_flags(c));
         const Ctrl& h = *c->ctrl_h;
-        if (h.nonfinite) return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate");
+        if (h.nonfinite) {
+          // the Newton vectors (or their squares) left the range of the Leja
+          // precision: the interpolation at this substep length failed
+          if (forced) return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate");
+          nonfinite_attempt = true;
+          ok = false;
+          break;
+        }
         if (forced) {
           degree = forced;
           break;
@@ -289,6 +297,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
           break;
         }
         if (h.fail || end >= o.m_max) {
+          nonfinite_attempt = false;
           ok = false;
           break;
         }
@@ -332,6 +341,8 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
     }
     return EREM_OK;
   }
+  if (nonfinite_attempt)
+    return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate at every substep level");
   return fail(c, EREM_ENOTCONV,
               "Leja interpolation did not meet the stopping test within m_max terms after " +
                   std::to_string(o.max_doublings) + " substep doublings");

@@ -289,33 +289,23 @@ erem_status ensure_graph(erem_ens* E, int max_iters) {
   return EREM_OK;
 }
 
-// One run: states and active list in, the loop, states out.
-erem_status run(erem_ens* E, int steps, cudaStream_t s) {
-  const long long bound = iteration_bound(E, steps);
-  E->L.max_iters = (int)bound;
-  if (E->cfg.use_graph) ENS_TRY(ensure_graph(E, (int)bound));
-  for (int e = 0; e < E->n; ++e) {
-    EnsState& st = E->st_h[e];
-    std::memset(&st, 0, sizeof(st));
-    st.phase = ENS_INIT;
-    st.level = E->cfg.substep_policy == EREM_ENS_KEEP_SUBSTEPS ? E->level_start[e] : 0;
-    st.level = std::min(st.level, E->nlev - 1);
-    st.target = steps;
-    if (E->clear_flags[e]) {
-      ENS_CUDA(E, cudaMemsetAsync(&E->ctx[e]->ctrl->flags, 0, sizeof(int), s));
-      E->clear_flags[e] = 0;
-    }
-  }
+// One pass of the batched loop over the members in `list` (their states in
+// st_h set by the caller; the states of the other members are not touched by
+// the kernel).  Adds the pass's device time and iterations to *ms, *iters.
+erem_status run_pass(erem_ens* E, const std::vector<int>& list, long long bound, cudaStream_t s,
+                     double* ms, long long* iters) {
   int* a = E->act_h;
-  a[0] = E->n;
-  a[1] = E->total_tiles;
+  int tiles = 0;
+  for (size_t k = 0; k < list.size(); ++k) {
+    a[4 + k] = list[k];
+    a[4 + E->n + k] = tiles;
+    tiles += E->tiles[list[k]];
+  }
+  a[0] = (int)list.size();
+  a[1] = tiles;
   a[2] = 0;
   a[3] = 1;
-  for (int e = 0; e < E->n; ++e) {
-    a[4 + e] = e;
-    a[4 + E->n + e] = E->tile0[e];
-  }
-  a[4 + 2 * E->n] = E->total_tiles;
+  a[4 + E->n + list.size()] = tiles;
   ENS_CUDA(E, cudaMemcpyAsync(E->st_d, E->st_h, sizeof(EnsState) * E->n, cudaMemcpyHostToDevice, s));
   ENS_CUDA(E, cudaMemcpyAsync(E->act_d, a, sizeof(int) * (2 * E->n + 5), cudaMemcpyHostToDevice, s));
   ENS_CUDA(E, cudaMemsetAsync(E->ctr_d, 0, 2 * sizeof(unsigned), s));
@@ -341,20 +331,90 @@ erem_status run(erem_ens* E, int steps, cudaStream_t s) {
   ENS_CUDA(E, cudaMemcpyAsync(E->ctr_h, E->ctr_d, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   ENS_CUDA(E, cudaMemcpyAsync(E->act_h, E->act_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   ENS_CUDA(E, cudaStreamSynchronize(s));
-  float ms = 0.f;
-  ENS_CUDA(E, cudaEventElapsedTime(&ms, E->ev[0], E->ev[1]));
+  float t = 0.f;
+  ENS_CUDA(E, cudaEventElapsedTime(&t, E->ev[0], E->ev[1]));
+  *ms += t;
+  *iters += E->ctr_h[1];
+  if (E->act_h[0] != 0)
+    return efail(E, EREM_ETIMEOUT, "the batched loop reached its iteration bound");
+  return EREM_OK;
+}
+
+// One run: every member advances `steps` steps.  A member whose Leja error
+// estimate became non-finite (the Newton vectors or their squares left the
+// range of the Leja precision; a bad state is flagged separately by the first
+// pass of its step) stops at the start of that step; it is run again, alone
+// with the other such members, from that step at the next substep level, as
+// erem_step splits a step whose interpolation failed.
+erem_status run(erem_ens* E, int steps, cudaStream_t s) {
+  const long long bound = iteration_bound(E, steps);
+  E->L.max_iters = (int)bound;
+  if (E->cfg.use_graph) ENS_TRY(ensure_graph(E, (int)bound));
+  const bool keep = E->cfg.substep_policy == EREM_ENS_KEEP_SUBSTEPS;
+  std::vector<EnsState> tot(E->n);
+  std::vector<int> list(E->n);
+  for (int e = 0; e < E->n; ++e) {
+    EnsState& st = E->st_h[e];
+    std::memset(&st, 0, sizeof(st));
+    st.phase = ENS_INIT;
+    st.level = std::min(keep ? E->level_start[e] : 0, E->nlev - 1);
+    st.target = steps;
+    std::memset(&tot[e], 0, sizeof(EnsState));
+    list[e] = e;
+    if (E->clear_flags[e]) {
+      ENS_CUDA(E, cudaMemsetAsync(&E->ctx[e]->ctrl->flags, 0, sizeof(int), s));
+      E->clear_flags[e] = 0;
+    }
+  }
+  double ms = 0.0;
+  long long iters = 0;
+  while (!list.empty()) {
+    ENS_TRY(run_pass(E, list, bound, s, &ms, &iters));
+    std::vector<int> retry;
+    for (int e : list) {
+      const EnsState& st = E->st_h[e];
+      EnsState& t = tot[e];
+      t.step += st.step;
+      t.terms += st.terms;
+      t.passes += st.passes;
+      t.attempts += st.attempts;
+      if (st.last_S > 0) {
+        t.last_S = st.last_S;
+        std::memcpy(t.last_deg, st.last_deg, sizeof(t.last_deg));
+      }
+      t.phase = st.phase;
+      t.status = st.status;
+      t.level = st.level;
+      if (st.phase == ENS_FAILED && st.status == ENS_NONFINITE && st.level + 1 < E->nlev) {
+        int flags = 0;
+        ENS_CUDA(E, cudaMemcpy(&flags, &E->ctx[e]->ctrl->flags, sizeof(int), cudaMemcpyDeviceToHost));
+        if (!(flags & FLAG_NONFINITE)) retry.push_back(e);
+      }
+    }
+    for (int e : retry) {
+      EnsState& st = E->st_h[e];
+      const int level = st.level + 1;
+      const int left = steps - tot[e].step;
+      std::memset(&st, 0, sizeof(st));
+      st.phase = ENS_INIT;
+      st.level = level;
+      st.target = left;
+      tot[e].attempts += 1;
+    }
+    list.swap(retry);
+  }
 
   erem_ens_run_stats& r = E->rs;
   std::memset(&r, 0, sizeof(r));
   r.t_ms = ms;
-  r.iterations = E->ctr_h[1];
+  r.iterations = iters;
   r.tile_vecs = E->U;
   r.grid = E->grid;
   r.use_graph = E->cfg.use_graph;
-  E->last.assign(E->st_h, E->st_h + E->n);
+  E->last = tot;
   int first_fail = -1;
   for (int e = 0; e < E->n; ++e) {
-    const EnsState& st = E->st_h[e];
+    const EnsState& st = tot[e];
     const long long N = E->ctx[e]->N;
     r.cells += N;
     r.cell_terms += N * st.terms;
@@ -370,7 +430,7 @@ erem_status run(erem_ens* E, int steps, cudaStream_t s) {
     }
   }
   if (first_fail >= 0) {
-    const EnsState& st = E->st_h[first_fail];
+    const EnsState& st = tot[first_fail];
     const std::string who = "member " + std::to_string(first_fail);
     if (st.status == ENS_NONFINITE)
       return efail(E, EREM_ENONFINITE, who + ": non-finite value in the state or the Leja estimate");
@@ -378,8 +438,6 @@ erem_status run(erem_ens* E, int steps, cudaStream_t s) {
                  who + ": Leja interpolation did not meet the stopping test within m_max terms after " +
                      std::to_string(E->max_doublings) + " substep doublings");
   }
-  if (E->act_h[0] != 0)
-    return efail(E, EREM_ETIMEOUT, "the batched loop reached its iteration bound");
   return EREM_OK;
 }
 
@@ -456,6 +514,24 @@ erem_status erem_ensemble_set_member(erem_ens* E, int e, const double* T, const 
   E->dt[e] = dt;
   E->level_start[e] = 0;
   E->clear_flags[e] = 0;
+  return EREM_OK;
+}
+
+erem_status erem_ensemble_set_temperature(erem_ens* E, int e, const double* T, void* stream) {
+  if (!E) return EREM_EINVAL;
+  ENS_TRY(check_member(E, e));
+  if (!T) return efail(E, EREM_EINVAL, "T is NULL");
+  if (!E->ready[e]) return efail(E, EREM_EINVAL, "member has no state");
+  cudaStream_t s = (cudaStream_t)stream;
+  const erem_ctx* c = E->ctx[e];
+  const double* src = T;
+  if (!is_device(T)) {
+    ENS_CUDA(E, cudaMemcpyAsync(E->stage_d, T, sizeof(double) * c->N, cudaMemcpyHostToDevice, s));
+    src = E->stage_d;
+  }
+  launch_pack(c, src, c->Tn, s);
+  ENS_CUDA(E, cudaGetLastError());
+  if (src != T) ENS_CUDA(E, cudaStreamSynchronize(s));  // the staging buffer is reused
   return EREM_OK;
 }
 

@@ -15,85 +15,11 @@
 #include <cstdint>
 
 #include "erem_internal.h"
+#include "device_common.cuh"
+#include "ensemble_kernel.cuh"
 
 namespace erem {
 namespace {
-
-constexpr int NT = kThreads;
-
-// ---------------------------------------------------------------------------
-// small device helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Block-wide reduction over BS threads with linear index tid; the result is
-// valid in tid 0.  OP 0 = sum, 1 = min, 2 = max.  Safe to call repeatedly
-// (syncs before reusing smem).
-template <int OP, int BS>
-__device__ double block_reduce_t(double v, double* sh, int tid) {
-  v = OP == 0 ? warp_sum(v) : (OP == 1 ? warp_min(v) : warp_max(v));
-  __syncthreads();
-  if ((tid & 31) == 0) sh[tid >> 5] = v;
-  __syncthreads();
-  if (tid < 32) {
-    double w = tid < (BS / 32) ? sh[tid] : (OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY));
-    w = OP == 0 ? warp_sum(w) : (OP == 1 ? warp_min(w) : warp_max(w));
-    v = w;
-  }
-  return v;
-}
-template <int OP>
-__device__ double block_reduce(double v, double* sh) {
-  return block_reduce_t<OP, NT>(v, sh, threadIdx.x);
-}
-
-// Publish this block's partials (block bid of nblocks); returns true in every
-// thread of the last block to arrive.  part has kRedSlots doubles per block.
-__device__ bool publish_partials_t(double* part, unsigned* cnt, const double* vals, int nv,
-                                   int tid, int bid, int nblocks) {
-  __shared__ int s_last;
-  if (tid == 0) {
-    for (int k = 0; k < nv; ++k) part[bid * kRedSlots + k] = vals[k];
-    __threadfence();
-    const unsigned t = atomicAdd(cnt, 1u);
-    s_last = (t == (unsigned)nblocks - 1u);
-  }
-  __syncthreads();
-  if (s_last) __threadfence();
-  return s_last != 0;
-}
-__device__ bool publish_partials(double* part, unsigned* cnt, const double* vals, int nv) {
-  return publish_partials_t(part, cnt, vals, nv, threadIdx.x, blockIdx.x, gridDim.x);
-}
-
-// Sum (or min/max) of partial k over all blocks, in block order; tid 0.
-template <int OP, int BS>
-__device__ double gather_partials_t(const double* part, int k, double* sh, int tid, int nblocks) {
-  double v = OP == 0 ? 0.0 : (OP == 1 ? INFINITY : -INFINITY);
-  for (int b = tid; b < nblocks; b += BS) {
-    const double x = __ldcg(part + b * kRedSlots + k);
-    v = OP == 0 ? v + x : (OP == 1 ? fmin(v, x) : fmax(v, x));
-  }
-  return block_reduce_t<OP, BS>(v, sh, tid);
-}
-template <int OP>
-__device__ double gather_partials(const double* part, int k, double* sh) {
-  return gather_partials_t<OP, NT>(part, k, sh, threadIdx.x, gridDim.x);
-}
 
 struct Geo {
   int nx, ny, nz, px, dim;
@@ -462,14 +388,7 @@ __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* 
                             double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctrl->done = 0;
-    ctrl->degree = 0;
-    ctrl->fail = 0;
-    ctrl->nonfinite = 0;
-    ctrl->m_last = 0;
-    ctrl->overshoot = 0;
-    ctrl->err = 0.0;
-    ctrl->sp = sp;
+    arm_ctrl(ctrl, sp);
   }
   const int sx = 1, sy = g.nx, sz = g.nx * g.ny;
   double tmax = 0.0;
@@ -509,76 +428,11 @@ __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* 
 // ---------------------------------------------------------------------------
 // Newton-Leja recurrence (eq. newt)
 // ---------------------------------------------------------------------------
-template <typename Tq, int VEC> struct VecT;
-template <> struct VecT<float, 4> { using V = float4; };
-template <> struct VecT<double, 2> { using V = double2; };
-
-template <typename Tq, int VEC>
-__device__ __forceinline__ void ldv(Tq (&r)[VEC], const Tq* p) {
-  using V = typename VecT<Tq, VEC>::V;
-  const V v = *reinterpret_cast<const V*>(p);
-  const Tq* s = reinterpret_cast<const Tq*>(&v);
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) r[k] = s[k];
-}
-template <typename Tq, int VEC>
-__device__ __forceinline__ void ldv_stream(Tq (&r)[VEC], const Tq* p) {
-  using V = typename VecT<Tq, VEC>::V;
-  const V v = __ldcs(reinterpret_cast<const V*>(p));
-  const Tq* s = reinterpret_cast<const Tq*>(&v);
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) r[k] = s[k];
-}
-template <typename Tq, int VEC>
-__device__ __forceinline__ void stv(Tq* p, const Tq (&r)[VEC]) {
-  using V = typename VecT<Tq, VEC>::V;
-  V v;
-  Tq* d = reinterpret_cast<Tq*>(&v);
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) d[k] = r[k];
-  *reinterpret_cast<V*>(p) = v;
-}
-// VEC doubles of P, streamed (read once, written once per term)
-template <int VEC>
-__device__ __forceinline__ void ldP(double (&r)[VEC], const double* p) {
-#pragma unroll
-  for (int k = 0; k < VEC; k += 2) {
-    const double2 v = __ldcs(reinterpret_cast<const double2*>(p + k));
-    r[k] = v.x;
-    r[k + 1] = v.y;
-  }
-}
-template <int VEC>
-__device__ __forceinline__ void stP(double* p, const double (&r)[VEC]) {
-#pragma unroll
-  for (int k = 0; k < VEC; k += 2) __stcs(reinterpret_cast<double2*>(p + k), make_double2(r[k], r[k + 1]));
-}
-
-// float -> double, exact, built from the bit fields with integer
-// instructions (the FP64 pipe of GB300 is the scarce unit in the FP32-bulk
-// sweep).  Zeros, subnormals, infinities and NaNs take the hardware
-// conversion.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  const unsigned lo = u << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // The same first kernel when nx is a multiple of 4 (the caller's T then has
 // the padded layout): each thread owns four consecutive cells and moves them
 // with 128-bit loads and stores.  ||T^n||_inf and the finiteness checks use
 // integer operations on the bit patterns (for |x| the order of the bits is
 // the order of the values), so the FP64 pipe only does the 8 FMAs of G.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
-}
-__device__ __forceinline__ bool bits_finite(unsigned long long b) {
-  return (b >> 52) != 0x7ffULL;
-}
-
 template <typename Tq, int DIM>
 __global__ void __launch_bounds__(NT)
 k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
@@ -586,14 +440,7 @@ k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__
                 Geo g, StopParams sp, double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctrl->done = 0;
-    ctrl->degree = 0;
-    ctrl->fail = 0;
-    ctrl->nonfinite = 0;
-    ctrl->m_last = 0;
-    ctrl->overshoot = 0;
-    ctrl->err = 0.0;
-    ctrl->sp = sp;
+    arm_ctrl(ctrl, sp);
   }
   unsigned long long tmax = 0ULL;
   bool bad = false;
@@ -672,62 +519,12 @@ template <typename Tq>
 __global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
                             double* __restrict__ P, double d0, int Np, StopParams sp, Ctrl* ctrl) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctrl->done = 0;
-    ctrl->degree = 0;
-    ctrl->fail = 0;
-    ctrl->nonfinite = 0;
-    ctrl->m_last = 0;
-    ctrl->overshoot = 0;
-    ctrl->err = 0.0;
-    ctrl->sp = sp;
+    arm_ctrl(ctrl, sp);
   }
   for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
     const double x = u[i];
     q0[i] = (Tq)x;
     P[i] = d0 * x;
-  }
-}
-
-// The Leja copy of J is interleaved per warp tile of T = 32 VEC cells: the
-// tile's NC coefficient arrays D W E S N (B T) follow one another, T values
-// each.  A warp whose lanes own 32 consecutive VEC-cell vectors reads each
-// coefficient as one contiguous 512-byte run, and the NC runs of a tile are
-// adjacent in memory (one stream instead of NC).  c[k] points at coefficient
-// k of tile 0; the vector starting at cell i reads c[k] + leja_off(i).
-template <typename Tq>
-struct LejaCoef {
-  const Tq* c[7];
-  int nc;
-};
-template <int T>
-__device__ __forceinline__ size_t leja_off(int i, int nc) {
-  return (size_t)i + (size_t)(i / T) * (size_t)(nc - 1) * T;
-}
-
-// Stopping test of §4.2 on the estimate of term m (thread 0 of the last block).
-__device__ void stop_test(Ctrl* c, int m, double dm, double S) {
-  const StopParams sp = c->sp;
-  const double scal = sp.tol_a + sp.tol_r * c->yinf;
-  const double e = fabs(sp.delta * dm) / scal * sqrt(S / sp.ncells);
-  c->e[m] = e;
-  c->m_last = m;
-  if (!isfinite(e)) {
-    c->nonfinite = 1;
-    c->done = 1;
-    return;
-  }
-  const int lo = max(1, m - sp.window + 1);
-  double mean = 0.0;
-  for (int k = lo; k <= m; ++k) mean += c->e[k];
-  mean /= (double)(m - lo + 1);
-  c->err = mean;
-  if (sp.replay) return;
-  if (sp.pow10 * mean < 1.0) {
-    c->done = 1;
-    c->degree = m;
-  } else if (m >= sp.m_max) {
-    c->fail = 1;
-    c->done = 1;
   }
 }
 
@@ -932,12 +729,6 @@ __device__ __forceinline__ void stencil_vec(const Tq* __restrict__ q, const Leja
   }
 }
 
-template <typename Tq>
-__device__ __forceinline__ double to_f64(Tq v) {
-  if constexpr (sizeof(Tq) == 4) return f2d_exact(v);
-  else return v;
-}
-
 // Warps, not blocks, claim the work items, so nothing in the march needs a
 // block-wide barrier.  An item is WAVE_U thread-vectors per lane of one warp.
 // The norm partial of every item goes to ipart; the last warp to finish a
@@ -1131,388 +922,6 @@ template <typename Tq>
 __global__ void k_unstep(double* __restrict__ P, const Tq* __restrict__ q, double d, int Np) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
     P[i] = fma(-d, to_f64(q[i]), P[i]);
-}
-
-// ---------------------------------------------------------------------------
-// Batched ensemble of independent 2D members: one launch is one iteration of
-// every active member's state machine (erem_internal.h).  Work items are
-// (member, tile) pairs of the active members, a tile being U thread-vectors
-// per thread (U NT VEC cells, row-major over the padded grid); blocks walk
-// them grid-stride.  The phase is uniform over a tile.  Per member, the block
-// that completes the member's last tile (ticket) reduces the tile partials in
-// tile order and advances the state, so results do not depend on which block
-// took which tile.
-// ---------------------------------------------------------------------------
-template <int VEC>
-__device__ __forceinline__ void ens_stencil(const EnsMember& M, const double* __restrict__ x,
-                                            int i, int row, int ix, double (&a)[VEC]) {
-  double xc[VEC], xs[VEC], xn[VEC], c[5][VEC];
-  ldP<VEC>(xc, x + i);
-  ldP<VEC>(xs, x + i - (row > 0 ? M.px : 0));
-  ldP<VEC>(xn, x + i + (row < M.ny - 1 ? M.px : 0));
-  const double xl = ix > 0 ? x[i - 1] : 0.0;
-  const double xr = ix + VEC < M.px ? x[i + VEC] : 0.0;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) ldP<VEC>(c[k], M.jc[k] + i);
-#pragma unroll
-  for (int v = 0; v < VEC; ++v) {
-    const double west = v == 0 ? xl : xc[v - 1];
-    const double east = v == VEC - 1 ? xr : xc[v + 1];
-    double y = c[0][v] * xc[v];
-    y = fma(c[1][v], west, y);
-    y = fma(c[2][v], east, y);
-    y = fma(c[3][v], xs[v], y);
-    y = fma(c[4][v], xn[v], y);
-    a[v] = y;
-  }
-}
-
-template <typename Tq, int VEC>
-__device__ __forceinline__ void ens_store_q(Tq* q, int i, const double (&a)[VEC]) {
-  Tq o[VEC];
-#pragma unroll
-  for (int v = 0; v < VEC; ++v) o[v] = (Tq)a[v];
-  stv<Tq, VEC>(q + i, o);
-}
-
-// Arm the stopping test for a new Leja substep at the state's level.
-__device__ void ens_arm(const EnsMember& M, const EnsState* st) {
-  Ctrl* c = M.ctrl;
-  c->done = 0;
-  c->degree = 0;
-  c->fail = 0;
-  c->nonfinite = 0;
-  c->m_last = 0;
-  c->overshoot = 0;
-  c->err = 0.0;
-  StopParams sp = M.sp;
-  sp.delta = M.dt / (double)(1 << st->level);
-  c->sp = sp;
-}
-
-// Advance member M after a complete pass of phase `phase` (thread 0 of the
-// member's last block).  r: the reduced value (||T^n||_inf after ENS_INIT,
-// sum of q_m^2 after ENS_TERM).  Returns 1 when the member left the active
-// set.
-__device__ int ens_advance(const EnsMember& M, const EnsLaunch& L, int phase, int m, double dm,
-                           double r) {
-  EnsState* st = M.st;
-  Ctrl* c = M.ctrl;
-  if (phase != ENS_TERM) st->passes += 1;
-  switch (phase) {
-    case ENS_INIT:
-      c->yinf = r;
-      if (__ldcg(&c->flags) & FLAG_NONFINITE) {  // raised by this pass's blocks
-        st->status = ENS_NONFINITE;
-        st->phase = ENS_FAILED;
-        return 1;
-      }
-      st->sub = 0;
-      ens_arm(M, st);
-      st->phase = ENS_TERM;
-      return 0;
-    case ENS_TERM:
-      stop_test(c, m, dm, r);
-      st->terms += 1;
-      if (c->nonfinite) {
-        st->status = ENS_NONFINITE;
-        st->phase = ENS_FAILED;
-        return 1;
-      }
-      if (!c->done) return 0;
-      if (!c->fail) {
-        st->cur_deg[st->sub] = c->degree;
-        st->phase = st->sub == (1 << st->level) - 1 ? ENS_FINAL : ENS_ACCUM;
-        return 0;
-      }
-      st->attempts += 1;
-      if (st->level + 1 < L.nlev) {
-        st->level += 1;
-        st->phase = ENS_RESTART;
-        return 0;
-      }
-      st->status = ENS_NOTCONV;
-      st->phase = ENS_FAILED;
-      return 1;
-    case ENS_ACCUM:
-      st->phase = ENS_SUBSTART;
-      return 0;
-    case ENS_SUBSTART:
-      st->sub += 1;
-      ens_arm(M, st);
-      st->phase = ENS_TERM;
-      return 0;
-    case ENS_RESTART:
-      st->sub = 0;
-      ens_arm(M, st);
-      st->phase = ENS_TERM;
-      return 0;
-    case ENS_FINAL: {
-      const int S = 1 << st->level;
-      st->last_S = S;
-      for (int k = 0; k < 64; ++k) st->last_deg[k] = k < S ? st->cur_deg[k] : 0;
-      st->step += 1;
-      if (st->step >= st->target) {
-        st->phase = ENS_DONE;
-        return 1;
-      }
-      if (L.restart) st->level = 0;
-      st->phase = ENS_INIT;
-      return 0;
-    }
-    default:
-      return 0;
-  }
-}
-
-// Block-wide exclusive scan of one int per thread; *total gets the sum.
-__device__ int block_exscan(int v, int* sm, int* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  __syncthreads();
-  if (lane == 31) sm[wid] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int k = 0; k < NT / 32; ++k) {
-      const int t = sm[k];
-      sm[k] = acc;
-      acc += t;
-    }
-    sm[NT / 32] = acc;
-  }
-  __syncthreads();
-  *total = sm[NT / 32];
-  return sm[wid] + x - v;
-}
-
-template <typename Tq, int VEC, int U>
-__global__ void __launch_bounds__(NT, 4)
-k_ens_iter(EnsLaunch L, cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double sh[NT / 32];
-  __shared__ int s_last;
-  __shared__ int s_scan[NT / 32 + 1];
-  const int n_act = L.act[0];
-  const int n_tiles = L.act[1];
-  const int* act_member = L.act + 4;
-  const int* act_start = L.act + 4 + L.n_members;
-  for (int gt = blockIdx.x; gt < n_tiles; gt += gridDim.x) {
-    // the active member owning work item gt: last k with act_start[k] <= gt
-    // (the list was written by an earlier launch: plain cached loads)
-    int lo = 0, hi = n_act - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (act_start[mid] <= gt) lo = mid;
-      else hi = mid - 1;
-    }
-    const EnsMember& M = L.mem[act_member[lo]];
-    const int t = gt - act_start[lo];
-    EnsState* st = M.st;
-    const int phase = st->phase;
-    const int level = st->level;
-    const int sub = st->sub;
-    const double* dd = M.dd + (size_t)level * (L.mmax + 1);
-    const double delta = M.dt / (double)(1 << level);
-    const int nvec = M.Np / VEC;
-    const int vrow = M.px / VEC;
-    int m = 0;
-    double dm = 0.0;
-    double acc = 0.0;                 // ENS_TERM: sum of q_m^2
-    unsigned long long tmax = 0ULL;   // ENS_INIT: ||T^n||_inf as bits
-    bool bad = false;
-    if (phase == ENS_TERM) {
-      m = M.ctrl->m_last + 1;
-      dm = dd[m];
-      const Tq shm = (Tq)(M.cg + L.xi[m - 1]);
-      const Tq* qi = (const Tq*)M.q[(m - 1) & 1];
-      Tq* qo = (Tq*)M.q[m & 1];
-      const Tq* jl = (const Tq*)M.jl;
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int v = (t * U + j) * NT + threadIdx.x;
-        if (v >= nvec) continue;
-        const int row = v / vrow;
-        const int i = v * VEC;
-        const int ix = i - row * M.px;
-        Tq qc[VEC], qs[VEC], qn[VEC];
-        ldv<Tq, VEC>(qc, qi + i);
-        ldv<Tq, VEC>(qs, qi + i - (row > 0 ? M.px : 0));
-        ldv<Tq, VEC>(qn, qi + i + (row < M.ny - 1 ? M.px : 0));
-        const Tq ql = ix > 0 ? qi[i - 1] : Tq(0);
-        const Tq qr = ix + VEC < M.px ? qi[i + VEC] : Tq(0);
-        Tq c[5][VEC];
-        const size_t off = leja_off<32 * VEC>(i, 5);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) ldv_stream<Tq, VEC>(c[k], jl + k * 32 * VEC + off);
-        double p[VEC];
-        ldP<VEC>(p, M.P + i);
-        Tq out[VEC];
-        Tq sq = Tq(0);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-          const Tq west = k == 0 ? ql : qc[k - 1];
-          const Tq east = k == VEC - 1 ? qr : qc[k + 1];
-          Tq a = (c[0][k] - shm) * qc[k];
-          a = fma(c[1][k], west, a);
-          a = fma(c[2][k], east, a);
-          a = fma(c[3][k], qs[k], a);
-          a = fma(c[4][k], qn[k], a);
-          out[k] = a;
-          if constexpr (sizeof(Tq) == 4) {
-            p[k] = fma(dm, f2d_exact(a), p[k]);
-            sq = fmaf(a, a, sq);
-          } else {
-            p[k] = fma(dm, a, p[k]);
-            acc = fma(a, a, acc);
-          }
-        }
-        if constexpr (sizeof(Tq) == 4) acc += (double)sq;
-        stv<Tq, VEC>(qo + i, out);
-        stP<VEC>(M.P + i, p);
-      }
-    } else if (phase == ENS_INIT || phase == ENS_SUBSTART) {
-      // INIT: G = J T^n + b, q_0 = G, P = d_0 G.  SUBSTART: q_0 = G + J w.
-      const double d0 = dd[0];
-      const double* x = phase == ENS_INIT ? M.T : M.w;
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int v = (t * U + j) * NT + threadIdx.x;
-        if (v >= nvec) continue;
-        const int row = v / vrow;
-        const int i = v * VEC;
-        const int ix = i - row * M.px;
-        double a[VEC];
-        ens_stencil<VEC>(M, x, i, row, ix, a);
-        if (phase == ENS_INIT) {
-          if (ix == 0) a[0] += M.b0[row];
-          double tc[VEC];
-          ldP<VEC>(tc, M.T + i);
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) {
-            const unsigned long long tb = abs_bits(tc[k]);
-            tmax = tmax > tb ? tmax : tb;
-            bad |= !bits_finite(tb) | !bits_finite(abs_bits(a[k]));
-          }
-          stP<VEC>(M.G + i, a);
-        } else {
-          double g[VEC];
-          ldP<VEC>(g, M.G + i);
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) a[k] += g[k];
-        }
-        double p[VEC];
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) p[k] = d0 * a[k];
-        stP<VEC>(M.P + i, p);
-        ens_store_q<Tq, VEC>((Tq*)M.q[0], i, a);
-      }
-    } else {
-      // cell-local phases
-      const double d0 = dd[0];
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int v = (t * U + j) * NT + threadIdx.x;
-        if (v >= nvec) continue;
-        const int i = v * VEC;
-        if (phase == ENS_RESTART) {
-          double g[VEC], p[VEC];
-          ldP<VEC>(g, M.G + i);
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) p[k] = d0 * g[k];
-          stP<VEC>(M.P + i, p);
-          ens_store_q<Tq, VEC>((Tq*)M.q[0], i, g);
-        } else {
-          double p[VEC], w[VEC];
-          ldP<VEC>(p, M.P + i);
-          if (sub > 0) ldP<VEC>(w, M.w + i);
-          double* dst = phase == ENS_ACCUM ? M.w : M.T;
-          double base[VEC];
-          if (phase == ENS_FINAL) ldP<VEC>(base, M.T + i);
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) {
-            double y = delta * p[k];
-            if (sub > 0) y += w[k];
-            if (phase == ENS_FINAL) y += base[k];
-            p[k] = y;
-          }
-          stP<VEC>(dst + i, p);
-        }
-      }
-    }
-    double bv = 0.0;
-    if (phase == ENS_INIT) bv = block_reduce<2>(__longlong_as_double((long long)tmax), sh);
-    else if (phase == ENS_TERM) bv = block_reduce<0>(acc, sh);
-    if (bad) atomicOr(&M.ctrl->flags, FLAG_NONFINITE);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      M.part[(size_t)t * kRedSlots] = bv;
-      __threadfence();
-      s_last = atomicInc(M.cnt, (unsigned)M.tiles - 1u) == (unsigned)M.tiles - 1u;
-    }
-    __syncthreads();
-    if (s_last) {  // every tile of this member's pass is done
-      __threadfence();
-      double r = 0.0;
-      if (phase == ENS_INIT) r = gather_partials_t<2, NT>(M.part, 0, sh, threadIdx.x, M.tiles);
-      else if (phase == ENS_TERM) r = gather_partials_t<0, NT>(M.part, 0, sh, threadIdx.x, M.tiles);
-      if (threadIdx.x == 0) {
-        if (ens_advance(M, L, phase, m, dm, r)) atomicExch(&L.act[2], 1);
-        __threadfence();
-      }
-    }
-    __syncthreads();
-  }
-
-  // The last block of the launch: rebuild the active list when a member
-  // left it, count the iteration and decide whether the loop goes on.
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicInc(L.gcnt, gridDim.x - 1u) == gridDim.x - 1u;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  int* act = L.act;
-  if (*(volatile int*)&act[2]) {
-    int n_off = 0, t_off = 0;
-    for (int base = 0; base < L.n_members; base += NT) {
-      const int e = base + threadIdx.x;
-      int on = 0, tl = 0;
-      if (e < L.n_members) {
-        const int ph = *(volatile int*)&L.mem[e].st->phase;
-        on = ph != ENS_DONE && ph != ENS_FAILED;
-        tl = on ? L.mem[e].tiles : 0;
-      }
-      int n_tot, t_tot;
-      const int pos = block_exscan(on, s_scan, &n_tot) + n_off;
-      const int tpos = block_exscan(tl, s_scan, &t_tot) + t_off;
-      if (on) {
-        act[4 + pos] = e;
-        act[4 + L.n_members + pos] = tpos;
-      }
-      n_off += n_tot;
-      t_off += t_tot;
-    }
-    if (threadIdx.x == 0) {
-      act[4 + L.n_members + n_off] = t_off;
-      act[0] = n_off;
-      act[1] = t_off;
-      act[2] = 0;
-    }
-  }
-  if (threadIdx.x == 0) {
-    const unsigned it = *(volatile unsigned*)L.iters + (n_act > 0 ? 1u : 0u);
-    *L.iters = it;
-    const int more = *(volatile int*)&act[0] > 0 && (long long)it < (long long)L.max_iters;
-    act[3] = more;
-    __threadfence();
-    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
-  }
 }
 
 __global__ void k_unpack(const double* __restrict__ src, double* __restrict__ dst, Geo g) {

@@ -257,6 +257,53 @@ def test_member_failure_is_isolated(ref):
         assert ens.run_stats().members_failed == n_fail
 
 
+def test_fp32_estimate_overflow_splits_the_step(ref):
+    # member 1 of the 512-member workload (190^2 cells, sigma 1.73, Pe 50):
+    # the Newton vectors q_m grow past 1.8e19 at m = 86 whatever the substep
+    # length (the scaled operator does not depend on it), so their FP32
+    # squares overflow before the oracle's 4-substep schedule (101, 72, 63,
+    # 61 terms) stops; the non-finite estimate counts as a failed attempt and
+    # the step is split further, in the ensemble and in a single context
+    E, _ = ref
+    case = C.from_workload(W.ensemble_member(1))
+    T1, res = ts.erem_step(case.problem(), case.T0, case.dt)
+    assert res.schedule[0] == 4 and res.schedule[1] > 86
+    g = case.grid
+    for policy in (E.EREM_ENS_RESTART_SUBSTEPS, E.EREM_ENS_KEEP_SUBSTEPS):
+        with E.Ensemble([(g.nx, g.ny, case.gpu_physics())], "fp32_bulk") as ens:
+            ens.configure(policy=policy)
+            ens.set_member(0, _t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
+                           case.dt)
+            ens.run(1)
+            st = ens.member_stats(0)
+            assert st.status == 0 and st.steps_done == 1 and st.substeps > 4
+            assert max(st.degrees[:st.substeps]) <= 86
+            assert C.rel_l2(_get(ens, 0), T1) < FP32_TOL
+    with E.Context(2, g.nx, g.ny, physics=case.gpu_physics(), precision="fp32_bulk") as ctx:
+        T = _t(case.T0)
+        ctx.set_state(T, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+        st = ctx.erem_step(T, case.dt)
+        assert st.substeps > 4
+        assert C.rel_l2(T.cpu().numpy(), T1) < FP32_TOL
+
+
+def test_set_temperature_restarts_from_a_saved_state(ref):
+    # save after one step, run two more, restore the saved state (from host
+    # memory for one member, device memory for the rest) and run two again
+    E, members = ref
+    with _ensemble(E, members, "fp32_bulk") as ens:
+        ens.run(1)
+        saved = [_get(ens, k) for k in range(len(members))]
+        ens.run(2)
+        after = [_get(ens, k) for k in range(len(members))]
+        for k in range(len(members)):
+            ens.set_temperature(k, saved[k] if k == 0 else _t(saved[k]))
+            assert np.array_equal(_get(ens, k), saved[k])
+        ens.run(2)
+        for k in range(len(members)):
+            assert np.array_equal(_get(ens, k), after[k])
+
+
 def test_host_output_and_argument_errors(ref):
     E, members = ref
     with _ensemble(E, members[:2], "fp64") as ens:
