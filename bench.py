@@ -174,19 +174,31 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_sources_sha():
+    """Hash of the source the Leja term kernel is built from: the shared
+    device helpers and the k_leja_term definition itself."""
+    csrc = os.path.join(ROOT, "paper_1209_5553_gb300", "csrc")
+    kern = open(os.path.join(csrc, "kernels.cu")).read()
+    start = kern.index("k_leja_term(const Tq* __restrict__ qi")
+    end = kern.index("\n}\n", start)
+    h = hashlib.sha256()
+    h.update(open(os.path.join(csrc, "device_common.cuh"), "rb").read())
+    h.update(kern[start:end].encode())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(precision: str, n_cells: int):
     """Bytes per Leja-term launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", f"k_leja_term_{precision}_channels3d_{round(n_cells ** (1 / 3))}.md")
-    src = os.path.join(ROOT, "paper_1209_5553_gb300", "csrc", "kernels.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_sources_sha()
         vals = {}
         for line in open(path):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(": ", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("kernels.cu sha256[:16]") != sha:
+        if vals.get("kernel sources sha256[:16]") != sha:
             return None
         return float(vals["dram bytes per cell-term"]) * n_cells
     except (OSError, KeyError, ValueError):
