@@ -54,6 +54,16 @@ def heat_problem(grid, phys, lnk, phi, lam, p, T_for_viscosity=None):
                        np.asarray(lam, np.float64).reshape(-1), fluxes)
 
 
+def erem_step_krylov(prob: HeatProblem, T, tau: float, opts=None):
+    """One EREM step (eq. ``EERM``) with phi_1 by the Krylov substeps of
+    ``oracle.krylov`` (§4.1); returns (T^{n+1}, KrylovResult)."""
+    from .krylov import phi1_krylov
+
+    T = np.asarray(T, np.float64).reshape(-1)
+    res = phi1_krylov(prob.J(T), prob.G(T), tau, float(np.max(np.abs(T))), opts)
+    return T + res.value, res
+
+
 def erem_step(prob: HeatProblem, T, tau: float, opts: LejaOptions | None = None):
     """One EREM step (eq. ``EERM``); returns (T^{n+1}, LejaResult)."""
     T = np.asarray(T, np.float64).reshape(-1)
