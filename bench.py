@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=256, help="grid cells per direction")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-krylov", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--slab", type=int, default=16, help="z planes of the oracle's sample")
@@ -279,6 +280,31 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
     return out
 
 
+def run_krylov(E, torch, wl, steps, warmup, dev):
+    """The same steps with phi_1 by Krylov substeps (FP64, §4.1)."""
+    ctx, T, _ = gpu_context(E, torch, wl, "fp64", dev)
+    opts = E.krylov_opts(tol=wl.tol)
+    for _ in range(warmup):
+        ctx.erem_step_krylov(T, wl.dt, opts=opts)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    subs, rej, launches = [], 0, 0
+    e0.record(stream)
+    for _ in range(steps):
+        st = ctx.erem_step_krylov(T, wl.dt, opts=opts)
+        subs.append(st.substeps)
+        rej += st.rejections
+        launches += st.launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"ms": e0.elapsed_time(e1), "substeps_per_step": subs, "rejections": rej,
+           "launches": launches, "T": T.cpu().numpy()}
+    ctx.close()
+    return out
+
+
 def run_e2e(E, torch, wl, steps, warmup, dev):
     """Same steps through the C ABI with a pinned host T: the library copies
     T to the device and the result back inside every call."""
@@ -427,6 +453,14 @@ def main(args):
                         "degrees_per_step": [s[1:] if s[0] == 1 else s for s in r64["degrees"]]}
         line["speedup_fp32_bulk_vs_fp64"] = ms64 / ms
         line["rel_l2_fp32_bulk_vs_fp64"] = rel
+        if not args.no_krylov:
+            rk = run_krylov(E, torch, wl, K, Wu, dev)
+            msk, valuek = aggregate(rk["ms"], N, K, world, dev)
+            line["krylov_fp64"] = {
+                "value": valuek, "ms_per_step": msk / K, "m": 10,
+                "substeps_per_step": rk["substeps_per_step"], "rejections": rk["rejections"],
+                "launches": rk["launches"],
+                "rel_l2_vs_leja_fp64": float(np.linalg.norm(rk["T"] - r64["T"]) / np.linalg.norm(r64["T"]))}
     if not args.no_e2e:
         sec = run_e2e(E, torch, wl, K, Wu, dev)
         sec = max_over_ranks(sec, world, dev)

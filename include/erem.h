@@ -234,6 +234,58 @@ EREM_API erem_status erem_pressure_solve_static(const erem_grid* grid,
                                                 double* p, double tol, int maxit,
                                                 erem_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Krylov (Arnoldi) phi_1, the alternative of §4.1: phi_1(tau J) v is
+ * approximated on a Krylov subspace of dimension m built by Arnoldi's
+ * algorithm with modified Gram-Schmidt (Algorithm alg:al2) as
+ * ||v|| V_{m+1} phi_1(tau Hbar_{m+1}) e_1 (eq. approphi).  The step is split
+ * into substeps of y' = J y + v (each with its own basis from J y + v) whose
+ * lengths follow a local error estimate from the first term of the expansion
+ * that eq. approphi drops; a substep is accepted when that estimate is at
+ * most 1.2 tol delta / tau, tol = (tol_a + tol_r ||T^n||_inf) sqrt(N), and
+ * the next length is 0.9 delta (tol delta / (tau err))^(1/m).  Everything
+ * runs in FP64 (the cell-form Jacobian), whatever the context's precision.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double tol_a, tol_r;  /* default 1e-6 each                                 */
+  int m;                /* Krylov dimension, 1..32 (default 10, §5)          */
+  int max_substeps;     /* substeps before EREM_ENOTCONV (default 1000)      */
+  const double* replay; /* host array: substep lengths to take instead of the
+                           error control, or NULL                            */
+  int n_replay;         /* entries in replay                                 */
+} erem_krylov_opts;
+
+typedef struct {
+  int substeps;         /* accepted substeps                                 */
+  int rejections;       /* rejected substep lengths                          */
+  int dims[64];         /* Krylov dimension of the first 64 substeps (m, or
+                           less after a breakdown: an invariant subspace)    */
+  double deltas[64];    /* their lengths                                     */
+  double err[64];       /* their local error estimates                       */
+  double t_ms;          /* wall time of the call                             */
+  int launches;         /* CUDA kernels the call launched                    */
+  int pad;
+} erem_krylov_stats;
+
+/* Defaults: tol 1e-6, m = 10, 1000 substeps, no replay. */
+EREM_API void erem_default_krylov_opts(erem_krylov_opts* opts);
+
+/* out = dt phi_1(dt J) v by Krylov substeps, for the J and dt of the last
+ * erem_set_state (as phi1_apply).  opts and stats may be NULL.
+ * Errors: EINVAL (no state, m outside 1..32), ENOTCONV (substep or rejection
+ * limit; out unchanged), ENONFINITE, ECUDA. */
+EREM_API erem_status phi1_apply_krylov(erem_ctx* ctx, const double* v, double* out,
+                                       const erem_krylov_opts* opts, erem_krylov_stats* stats,
+                                       void* stream);
+
+/* One EREM step (eq. EERM) with phi_1 by Krylov substeps; arguments and
+ * field handling as erem_step. */
+EREM_API erem_status erem_step_krylov(erem_ctx* ctx, double* T, const double* p,
+                                      const double* lnk, const double* phi,
+                                      const double* lambda, double dt,
+                                      const erem_krylov_opts* opts, erem_krylov_stats* stats,
+                                      void* stream);
+
 /* Message of the last failing call on ctx ("" if none; a static message if
  * ctx is NULL).  The pointer stays valid until the next call on ctx. */
 EREM_API const char* erem_last_error(const erem_ctx* ctx);

@@ -68,6 +68,24 @@ class erem_stats(ctypes.Structure):
         return [self.substeps] + [self.degrees[k] for k in range(self.substeps)]
 
 
+class erem_krylov_opts(ctypes.Structure):
+    _fields_ = [("tol_a", ctypes.c_double), ("tol_r", ctypes.c_double), ("m", ctypes.c_int),
+                ("max_substeps", ctypes.c_int), ("replay", ctypes.POINTER(ctypes.c_double)),
+                ("n_replay", ctypes.c_int)]
+
+
+class erem_krylov_stats(ctypes.Structure):
+    _fields_ = [("substeps", ctypes.c_int), ("rejections", ctypes.c_int),
+                ("dims", ctypes.c_int * 64), ("deltas", ctypes.c_double * 64),
+                ("err", ctypes.c_double * 64), ("t_ms", ctypes.c_double),
+                ("launches", ctypes.c_int), ("pad", ctypes.c_int)]
+
+    @property
+    def schedule(self):
+        """Substep lengths (the first 64), for replay."""
+        return [self.deltas[k] for k in range(min(self.substeps, 64))]
+
+
 EREM_ENS_KEEP_SUBSTEPS, EREM_ENS_RESTART_SUBSTEPS = 0, 1
 
 
@@ -116,6 +134,11 @@ _sigs = {
     "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
     "erem_pressure_solve_static": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics),
                                         _P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
+    "erem_default_krylov_opts": (None, [ctypes.POINTER(erem_krylov_opts)]),
+    "phi1_apply_krylov": (_I, [_P, _P, _P, ctypes.POINTER(erem_krylov_opts),
+                               ctypes.POINTER(erem_krylov_stats), _P]),
+    "erem_step_krylov": (_I, [_P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(erem_krylov_opts),
+                              ctypes.POINTER(erem_krylov_stats), _P]),
     "erem_ensemble_create": (_I, [_I, ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics), _I,
                                   ctypes.POINTER(_P)]),
     "erem_ensemble_destroy": (_I, [_P]),
@@ -299,6 +322,44 @@ def erem_pressure_solve_static(grid: erem_grid, phys: erem_physics, lnk, T, p, t
     return st
 
 
+def krylov_opts(tol=1e-6, tol_a=None, tol_r=None, m=10, max_substeps=1000, replay=None):
+    """erem_krylov_opts with the given fields (replay = substep lengths or None)."""
+    o = erem_krylov_opts()
+    _lib.erem_default_krylov_opts(ctypes.byref(o))
+    o.tol_a = tol if tol_a is None else tol_a
+    o.tol_r = tol if tol_r is None else tol_r
+    o.m, o.max_substeps = int(m), int(max_substeps)
+    if replay is not None:
+        arr = (ctypes.c_double * len(replay))(*[float(v) for v in replay])
+        o._replay_keep = arr
+        o.replay = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        o.n_replay = len(replay)
+    return o
+
+
+def erem_default_krylov_opts(opts: erem_krylov_opts) -> None:
+    _lib.erem_default_krylov_opts(ctypes.byref(opts))
+
+
+def phi1_apply_krylov(ctx, n, v, out, opts: erem_krylov_opts | None = None,
+                      stream=None) -> erem_krylov_stats:
+    st = erem_krylov_stats()
+    _check(ctx, _lib.phi1_apply_krylov(ctx, _ptr(v, n), _ptr(out, n),
+                                       ctypes.byref(opts) if opts is not None else None,
+                                       ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def erem_step_krylov(ctx, n, T, dt, p=None, lnk=None, phi=None, lam=None,
+                     opts: erem_krylov_opts | None = None, stream=None) -> erem_krylov_stats:
+    st = erem_krylov_stats()
+    _check(ctx, _lib.erem_step_krylov(ctx, _ptr(T, n), _ptr(p, n), _ptr(lnk, n), _ptr(phi, n),
+                                      _ptr(lam, n), float(dt),
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      ctypes.byref(st), _stream(stream)))
+    return st
+
+
 def erem_ensemble_create(grids, physics, precision: int = EREM_FP64):
     n = len(grids)
     ga = (erem_grid * n)(*grids)
@@ -433,6 +494,13 @@ class Context:
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):
         return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)
+
+    def phi1_apply_krylov(self, v, out, opts=None, stream=None):
+        return phi1_apply_krylov(self._h, self.n, v, out, opts, stream)
+
+    def erem_step_krylov(self, T, dt, p=None, lnk=None, phi=None, lam=None, opts=None,
+                         stream=None):
+        return erem_step_krylov(self._h, self.n, T, dt, p, lnk, phi, lam, opts, stream)
 
 
 class Ensemble:

@@ -475,6 +475,178 @@ erem_status bicg_solve(erem_ctx* c, const double* b, double sigma, double tol, i
   return EREM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Krylov phi_1 (§4.1): the basis is built on the device (kernels.cu); the
+// substep control and the small exponentials run here, one read-back of the
+// Arnoldi scalars per substep.
+// ---------------------------------------------------------------------------
+struct KrOpts {
+  double tol_a = 1e-6, tol_r = 1e-6;
+  int m = 10, max_substeps = 1000;
+  std::vector<double> replay;
+};
+
+erem_status parse_kr_opts(erem_ctx* c, const erem_krylov_opts* o, KrOpts* out) {
+  KrOpts r;
+  if (o) {
+    if (o->tol_a != 0.0) r.tol_a = o->tol_a;
+    if (o->tol_r != 0.0) r.tol_r = o->tol_r;
+    if (o->m != 0) r.m = o->m;
+    if (o->max_substeps != 0) r.max_substeps = o->max_substeps;
+    if (o->replay) {
+      if (o->n_replay < 1) return fail(c, EREM_EINVAL, "replay needs at least one substep length");
+      for (int k = 0; k < o->n_replay; ++k)
+        if (!(o->replay[k] > 0.0) || !std::isfinite(o->replay[k]))
+          return fail(c, EREM_EINVAL, "replayed substep lengths must be finite and > 0");
+      r.replay.assign(o->replay, o->replay + o->n_replay);
+    }
+  }
+  if (!(r.tol_a >= 0.0) || !(r.tol_r >= 0.0) || r.tol_a + r.tol_r <= 0.0)
+    return fail(c, EREM_EINVAL, "tolerances must be >= 0 with tol_a + tol_r > 0");
+  if (r.m < 1 || r.m > kKrMax) return fail(c, EREM_EINVAL, "Krylov dimension m must be 1..32");
+  if (r.max_substeps < 1) return fail(c, EREM_EINVAL, "max_substeps must be >= 1");
+  *out = r;
+  return EREM_OK;
+}
+
+erem_status ensure_kr(erem_ctx* c, int m) {
+  if (!c->kr_dev) {
+    EREM_TRY(dalloc(c, (void**)&c->kr_dev, sizeof(KrDev)));
+    if (cudaMallocHost((void**)&c->kr_host, sizeof(KrDev)) != cudaSuccess) {
+      cudaGetLastError();
+      c->kr_host = nullptr;
+      return fail(c, EREM_ENOMEM, "cudaMallocHost of the Krylov scalars failed");
+    }
+    for (int k = 0; k < 2; ++k) EREM_TRY(dalloc_t(c, &c->kr_w[k], (size_t)c->Np));
+    EREM_TRY(dalloc_t(c, &c->kr_r, (size_t)c->Np));
+    EREM_TRY(dalloc_t(c, &c->kr_y, (size_t)c->Np));
+  }
+  while (c->kr_cap < m + 1) {
+    EREM_TRY(dalloc_t(c, &c->kr_V[c->kr_cap], (size_t)c->Np));
+    ++c->kr_cap;
+  }
+  return EREM_OK;
+}
+
+// [phi_1, phi_2, phi_3](delta H) e_1 for the k x k Hessenberg H (row-major
+// from KrDev): the exponential of H augmented by e_1 and a shift chain.
+void kr_phis(const KrDev& K, int k, double delta, std::vector<double>* out) {
+  const int n = k + 3;
+  std::vector<double> A((size_t)n * n, 0.0), E((size_t)n * n);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) A[(size_t)i * n + j] = delta * K.H[i * kKrMax + j];
+  A[k] = 1.0;                                   // (0, k)
+  A[(size_t)k * n + k + 1] = 1.0;
+  A[(size_t)(k + 1) * n + k + 2] = 1.0;
+  expm_small(n, A.data(), E.data());
+  out->assign((size_t)3 * k, 0.0);
+  for (int q = 0; q < 3; ++q)
+    for (int i = 0; i < k; ++i) (*out)[(size_t)q * k + i] = E[(size_t)i * n + k + q];
+}
+
+// phi_1(delta Hbar_{k+1}) e_1 (eq. approphi) from the exponential of the
+// (k + 2) augmented matrix; k + 1 entries.
+void kr_phi1_hbar(const KrDev& K, int k, double delta, std::vector<double>* out) {
+  const int n = k + 2;
+  std::vector<double> A((size_t)n * n, 0.0), E((size_t)n * n);
+  for (int i = 0; i <= k; ++i)
+    for (int j = 0; j < k; ++j) A[(size_t)i * n + j] = delta * K.H[i * kKrMax + j];
+  A[k + 1] = 1.0;                               // (0, k + 1)
+  expm_small(n, A.data(), E.data());
+  out->assign(k + 1, 0.0);
+  for (int i = 0; i <= k; ++i) (*out)[i] = E[(size_t)i * n + k + 1];
+}
+
+// c->kr_y (padded) = dt phi_1(dt J) src (padded); J, dt and ||T^n||_inf
+// (in the control block) must be current.
+erem_status run_krylov(erem_ctx* c, const double* src, const KrOpts& o, erem_krylov_stats* st,
+                       cudaStream_t s) {
+  EREM_TRY(ensure_kr(c, o.m));
+  EREM_TRY(read_ctrl(c, s));
+  EREM_TRY(check_flags(c));
+  const double tau = c->dt;
+  const int m = (int)std::min<long long>(o.m, c->N);
+  const double jnorm = std::max(std::fabs(c->alpha), std::fabs(c->beta)) / tau;
+  const double btol = 1e-12 * std::max(jnorm, 1e-300);
+  const double tol = (o.tol_a + o.tol_r * c->ctrl_h->yinf) * std::sqrt((double)c->N);
+  const bool replay = !o.replay.empty();
+  EREM_CUDA(c, cudaMemsetAsync(c->kr_y, 0, sizeof(double) * c->Np, s));
+  double t = 0.0, delta = tau;
+  int nsub = 0, rej_total = 0;
+  std::vector<double> phis, coef;
+  while (replay ? nsub < (int)o.replay.size() : t < tau * (1.0 - 1e-15)) {
+    if (nsub >= o.max_substeps) return fail(c, EREM_ENOTCONV, "Krylov: substep limit reached");
+    const double* r = src;
+    if (nsub > 0) {
+      launch_japply_add(c, c->kr_y, src, c->kr_r, s);
+      r = c->kr_r;
+    }
+    launch_kr_norm0(c, r, btol, s);
+    const double* w_in = r;
+    int cur = 0;
+    for (int j = 0; j < m; ++j) {
+      launch_kr_matvec(c, w_in, c->kr_V[j], c->kr_w[cur], j, 0, s);
+      for (int i = 1; i <= j; ++i) launch_kr_orth(c, c->kr_w[cur], c->kr_V[i - 1], c->kr_V[i], i, j, 0, s);
+      launch_kr_orth(c, c->kr_w[cur], c->kr_V[j], c->kr_V[j], j + 1, j, 1, s);
+      w_in = c->kr_w[cur];
+      cur ^= 1;
+    }
+    launch_kr_matvec(c, w_in, c->kr_V[m], c->kr_w[cur], m, 1, s);  // v_{m+1}, ||J v_{m+1}||
+    EREM_TRY(check_launch(c, "arnoldi"));
+    EREM_CUDA(c, cudaMemcpyAsync(c->kr_host, c->kr_dev, sizeof(KrDev), cudaMemcpyDeviceToHost, s));
+    EREM_CUDA(c, cudaStreamSynchronize(s));
+    const KrDev& K = *c->kr_host;
+    if (!(K.beta > 0.0)) {
+      if (!std::isfinite(K.beta)) return fail(c, EREM_ENONFINITE, "Krylov: non-finite start vector");
+      break;  // J y + v = 0: y is the exact solution from here on
+    }
+    const bool happy = K.breakdown >= 0;
+    const int k = happy ? K.breakdown + 1 : m;
+    const double hnext = K.H[k * kKrMax + (k - 1)];
+    if (replay) delta = o.replay[nsub];
+    else delta = std::min(delta, tau - t);
+    int rej = 0;
+    double err = 0.0;
+    while (true) {
+      if (!happy) {
+        kr_phis(K, k, delta, &phis);
+        const double p1 = K.beta * hnext * delta * delta * std::fabs(phis[(size_t)1 * k + k - 1]);
+        const double p2 =
+            K.beta * hnext * delta * delta * delta * std::fabs(phis[(size_t)2 * k + k - 1]) * K.avnorm;
+        err = p1 > 10.0 * p2 ? p2 : (p1 > p2 ? p1 * p2 / (p1 - p2) : p1);
+        if (!std::isfinite(err)) return fail(c, EREM_ENONFINITE, "Krylov: non-finite error estimate");
+      }
+      if (replay || happy || err <= 1.2 * tol * delta / tau) break;
+      if (++rej > 50) return fail(c, EREM_ENOTCONV, "Krylov: rejection limit reached");
+      delta = 0.9 * delta * std::pow(tol * delta / (tau * err), 1.0 / k);
+    }
+    kr_phi1_hbar(K, k, delta, &coef);
+    KrComb cb{};
+    cb.n = happy ? k : k + 1;
+    for (int i = 0; i < cb.n; ++i) {
+      cb.v[i] = c->kr_V[i];
+      cb.coef[i] = delta * K.beta * coef[i];
+      if (!std::isfinite(cb.coef[i])) return fail(c, EREM_ENONFINITE, "Krylov: non-finite coefficient");
+    }
+    launch_kr_combine(c, c->kr_y, cb, s);
+    EREM_TRY(check_launch(c, "krylov combine"));
+    if (st && nsub < 64) {
+      st->dims[nsub] = k;
+      st->deltas[nsub] = delta;
+      st->err[nsub] = err;
+    }
+    rej_total += rej;
+    ++nsub;
+    t += delta;
+    delta = (happy || err == 0.0) ? tau - t : 0.9 * delta * std::pow(tol * delta / (tau * err), 1.0 / k);
+  }
+  if (st) {
+    st->substeps = nsub;
+    st->rejections = rej_total;
+  }
+  return EREM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -600,6 +772,14 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (double* p : c->stage)
     if (p) cudaFree(p);
+  for (double* p : c->kr_V)
+    if (p) cudaFree(p);
+  for (double* p : c->kr_w)
+    if (p) cudaFree(p);
+  if (c->kr_r) cudaFree(c->kr_r);
+  if (c->kr_y) cudaFree(c->kr_y);
+  if (c->kr_dev) cudaFree(c->kr_dev);
+  if (c->kr_host) cudaFreeHost(c->kr_host);
   if (c->red_cnt) cudaFree(c->red_cnt);
   if (c->qmid) cudaFree(c->qmid);
   if (c->wave_ctr) cudaFree(c->wave_ctr);
@@ -788,6 +968,65 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
     st->lin_resid = res;
     st->substeps = 0;
     st->degree_total = 0;
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  return EREM_OK;
+}
+
+void erem_default_krylov_opts(erem_krylov_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol_a = 1e-6;
+  o->tol_r = 1e-6;
+  o->m = 10;
+  o->max_substeps = 1000;
+}
+
+erem_status phi1_apply_krylov(erem_ctx* c, const double* v, double* out, const erem_krylov_opts* opts,
+                              erem_krylov_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->have_state) return fail(c, EREM_EINVAL, "phi1_apply_krylov before erem_set_state");
+  if (!v || !out) return fail(c, EREM_EINVAL, "NULL vector");
+  KrOpts o;
+  EREM_TRY(parse_kr_opts(c, opts, &o));
+  if (st) std::memset(st, 0, sizeof(*st));
+  EREM_TRY(clear_flags(c, s));
+  double *dv, *dout;
+  EREM_TRY(resolve(c, 5, v, true, s, &dv));
+  launch_pack(c, dv, c->vin, s);
+  EREM_TRY(resolve(c, 6, out, false, s, &dout));
+  EREM_TRY(run_krylov(c, c->vin, o, st, s));
+  launch_finish(c, dout, nullptr, nullptr, c->kr_y, 1.0, s);
+  EREM_TRY(check_launch(c, "krylov finish"));
+  EREM_TRY(finish_staged(c, out, dout, s));
+  if (st) {
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  return EREM_OK;
+}
+
+erem_status erem_step_krylov(erem_ctx* c, double* T, const double* p, const double* lnk,
+                             const double* phi, const double* lam, double dt,
+                             const erem_krylov_opts* opts, erem_krylov_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  KrOpts o;
+  EREM_TRY(parse_kr_opts(c, opts, &o));
+  if (st) std::memset(st, 0, sizeof(*st));
+  double* Td = nullptr;
+  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, false, s, &Td));
+  EREM_TRY(run_krylov(c, c->vrhs, o, st, s));
+  launch_finish(c, Td, c->Tn, nullptr, c->kr_y, 1.0, s);
+  EREM_TRY(check_launch(c, "krylov finish"));
+  EREM_TRY(finish_staged(c, T, Td, s));
+  if (st) {
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
   }

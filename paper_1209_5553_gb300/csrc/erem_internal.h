@@ -134,6 +134,18 @@ struct EnsLaunch {
   unsigned* iters;  // iterations taken
 };
 
+// Krylov (Arnoldi) phi_1: device scalars of one basis (kernels.cu,
+// abi.cpp).  H(i, j) is stored at H[i * kKrMax + j].
+constexpr int kKrMax = 32;   // largest Krylov dimension
+struct KrDev {
+  double H[(kKrMax + 1) * kKrMax];
+  double beta;      // ||r||_2 of the start vector
+  double avnorm;    // ||J v_{m+1}||_2
+  double btol;      // breakdown threshold on h_{j+1,j}
+  int breakdown;    // first j with h_{j+1,j} <= btol, or -1
+  int pad;
+};
+
 struct DDEntry {
   double c = 0, gamma = 0;
   int M = -1;
@@ -181,6 +193,14 @@ struct erem_ctx {
   double* kv[12] = {};
   // staging for host pointers (allocated on first use)
   double* stage[8] = {};
+  // Krylov basis and work vectors (allocated on first use)
+  double* kr_V[erem::kKrMax + 1] = {};
+  double* kr_w[2] = {};
+  double* kr_r = nullptr;
+  double* kr_y = nullptr;
+  erem::KrDev* kr_dev = nullptr;
+  erem::KrDev* kr_host = nullptr;   // pinned
+  int kr_cap = 0;                   // basis vectors allocated
   // reductions and control
   double* red_part = nullptr;
   unsigned* red_cnt = nullptr;
@@ -261,6 +281,22 @@ void launch_ens_iter(const EnsLaunch& L, cudaStream_t s);
 // the kernel ends the loop.
 cudaError_t build_ens_graph(const EnsLaunch& L, cudaGraph_t* graph, cudaGraphExec_t* exec);
 void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s);
+
+// Krylov (Arnoldi, modified Gram-Schmidt) passes, FP64
+void launch_kr_norm0(const erem_ctx* c, const double* r, double btol, cudaStream_t s);
+void launch_kr_matvec(const erem_ctx* c, const double* w_in, double* v_out, double* w_out, int j,
+                      int mode, cudaStream_t s);
+void launch_kr_orth(const erem_ctx* c, double* w, const double* vprev, const double* vi, int i,
+                    int j, int last, cudaStream_t s);
+struct KrComb {
+  const double* v[kKrMax + 1];
+  double coef[kKrMax + 1];
+  int n;
+};
+void launch_kr_combine(const erem_ctx* c, double* y, const KrComb& cb, cudaStream_t s);
+// dense exponential of a small host matrix (row-major n x n), Taylor +
+// scaling and squaring (leja_host.cpp)
+void expm_small(int n, const double* A, double* E);
 
 // host scalar side (leja_host.cpp)
 void leja_table(int M, std::vector<double>* out);

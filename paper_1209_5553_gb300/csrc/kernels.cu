@@ -933,6 +933,116 @@ __global__ void k_unpack(const double* __restrict__ src, double* __restrict__ ds
 }
 
 // ---------------------------------------------------------------------------
+// Krylov phi_1 (§4.1, Algorithm alg:al2): Arnoldi with modified Gram-Schmidt
+// in FP64 over the padded layout (pads hold 0 in every vector and 0
+// coefficients, so sums over all Np cells equal sums over the real cells).
+// The scalars h_ij, ||r|| and ||J v_{m+1}|| stay in the device block KrDev;
+// each pass reads the scalar the previous pass wrote, so a whole basis is
+// built without a host round trip.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kr_cell(int ip, const Geo& g, int& ix, int& iy, int& iz) {
+  const int row = ip / g.px;
+  ix = ip - row * g.px;
+  iy = row % g.ny;
+  iz = row / g.ny;
+}
+
+// beta = ||r||_2, arms the breakdown flag
+__global__ void k_kr_norm0(const double* __restrict__ r, Geo g, double btol, double* part,
+                           unsigned* cnt, KrDev* K) {
+  __shared__ double sh[NT / 32];
+  double acc = 0.0;
+  for (int ip = blockIdx.x * NT + threadIdx.x; ip < g.Np; ip += gridDim.x * NT) acc = fma(r[ip], r[ip], acc);
+  double vals[1] = {block_reduce<0>(acc, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      K->beta = sqrt(s);
+      K->btol = btol;
+      K->breakdown = K->beta <= 0.0 ? 0 : -1;
+    }
+  }
+}
+
+// v_j = w_in / h (h = beta for j = 0, else h_{j,j-1}); w_out = J v_j.
+// mode 0: the partial dot w_out . v_0 -> H(0, j); mode 1: ||w_out||_2 -> avnorm.
+__global__ void k_kr_matvec(JIn J, const double* __restrict__ w_in, double* __restrict__ v_out,
+                            double* __restrict__ w_out, const double* __restrict__ v0, Geo g, int j,
+                            int mode, double* part, unsigned* cnt, KrDev* K) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&K->breakdown >= 0) return;
+  const double h = j == 0 ? K->beta : K->H[j * kKrMax + (j - 1)];
+  const double s = 1.0 / h;
+  double acc = 0.0;
+  for (int ip = blockIdx.x * NT + threadIdx.x; ip < g.Np; ip += gridDim.x * NT) {
+    int ix, iy, iz;
+    kr_cell(ip, g, ix, iy, iz);
+    const double vc = s * w_in[ip];
+    v_out[ip] = vc;
+    double a = J.c[0][ip] * vc;
+    if (ix > 0) a += J.c[1][ip] * (s * w_in[ip - 1]);
+    if (ix < g.nx - 1) a += J.c[2][ip] * (s * w_in[ip + 1]);
+    if (iy > 0) a += J.c[3][ip] * (s * w_in[ip - g.px]);
+    if (iy < g.ny - 1) a += J.c[4][ip] * (s * w_in[ip + g.px]);
+    if (g.dim == 3) {
+      if (iz > 0) a += J.c[5][ip] * (s * w_in[ip - g.plane]);
+      if (iz < g.nz - 1) a += J.c[6][ip] * (s * w_in[ip + g.plane]);
+    }
+    w_out[ip] = a;
+    acc = fma(a, mode == 0 ? (j == 0 ? vc : v0[ip]) : a, acc);
+  }
+  double vals[1] = {block_reduce<0>(acc, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double d = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      if (mode == 0) K->H[j] = d;   // H(0, j)
+      else K->avnorm = sqrt(d);
+    }
+  }
+}
+
+// w -= h_{i-1,j} v_{i-1}; then the partial dot w . v_i -> H(i, j), or for
+// the last pass ||w||_2 -> h_{j+1,j} (and the breakdown test).
+__global__ void k_kr_orth(double* __restrict__ w, const double* __restrict__ vprev,
+                          const double* __restrict__ vi, Geo g, int i, int j, int last,
+                          double* part, unsigned* cnt, KrDev* K) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&K->breakdown >= 0) return;
+  const double h = K->H[(i - 1) * kKrMax + j];
+  double acc = 0.0;
+  for (int ip = blockIdx.x * NT + threadIdx.x; ip < g.Np; ip += gridDim.x * NT) {
+    const double x = w[ip] - h * vprev[ip];
+    w[ip] = x;
+    acc = fma(x, last ? x : vi[ip], acc);
+  }
+  double vals[1] = {block_reduce<0>(acc, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double d = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      if (!last) {
+        K->H[i * kKrMax + j] = d;
+      } else {
+        const double hn = sqrt(d);
+        K->H[(j + 1) * kKrMax + j] = hn;
+        if (hn <= K->btol) K->breakdown = j;
+      }
+    }
+  }
+}
+
+// y += sum_i coef_i v_i
+__global__ void k_kr_combine(double* __restrict__ y, KrComb cb, int Np) {
+  for (int ip = blockIdx.x * NT + threadIdx.x; ip < Np; ip += gridDim.x * NT) {
+    double a = y[ip];
+    for (int k = 0; k < cb.n; ++k) a = fma(cb.coef[k], cb.v[k][ip], a);
+    y[ip] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pressure: TPFA mass-mobility transmissibilities and Jacobi-PCG
 // ---------------------------------------------------------------------------
 struct PresArr {
@@ -1757,6 +1867,34 @@ cudaError_t build_ens_graph(const EnsLaunch& L, cudaGraph_t* graph, cudaGraphExe
 void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s) {
   ++c->launches;
   k_unpack<<<blocks_cells(c), NT, 0, s>>>(src, dst, geo_of(c));
+}
+
+
+// ---------------------------------------------------------------------------
+// Krylov
+// ---------------------------------------------------------------------------
+void launch_kr_norm0(const erem_ctx* c, const double* r, double btol, cudaStream_t s) {
+  ++c->launches;
+  k_kr_norm0<<<blocks_padded(c), NT, 0, s>>>(r, geo_of(c), btol, c->red_part, c->red_cnt, c->kr_dev);
+}
+
+void launch_kr_matvec(const erem_ctx* c, const double* w_in, double* v_out, double* w_out, int j,
+                      int mode, cudaStream_t s) {
+  ++c->launches;
+  k_kr_matvec<<<blocks_padded(c), NT, 0, s>>>(jin(c), w_in, v_out, w_out, c->kr_V[0], geo_of(c), j,
+                                              mode, c->red_part, c->red_cnt, c->kr_dev);
+}
+
+void launch_kr_orth(const erem_ctx* c, double* w, const double* vprev, const double* vi, int i,
+                    int j, int last, cudaStream_t s) {
+  ++c->launches;
+  k_kr_orth<<<blocks_padded(c), NT, 0, s>>>(w, vprev, vi, geo_of(c), i, j, last, c->red_part,
+                                            c->red_cnt, c->kr_dev);
+}
+
+void launch_kr_combine(const erem_ctx* c, double* y, const KrComb& cb, cudaStream_t s) {
+  ++c->launches;
+  k_kr_combine<<<blocks_padded(c), NT, 0, s>>>(y, cb, (int)c->Np);
 }
 
 }  // namespace erem

@@ -172,6 +172,44 @@ int divided_differences(int M, const double* xi, double c, double gamma, double*
   return 0;
 }
 
+// exp(A) of a small dense matrix (row-major n x n): a Taylor polynomial of
+// degree 30 of A / 2^s with ||A / 2^s||_1 <= 1/2, then s squarings.
+void expm_small(int n, const double* A, double* E) {
+  double norm = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double col = 0.0;
+    for (int i = 0; i < n; ++i) col += std::fabs(A[(size_t)i * n + j]);
+    norm = std::max(norm, col);
+  }
+  int s = 0;
+  while (norm / std::ldexp(1.0, s) > 0.5) ++s;
+  const double scale = std::ldexp(1.0, -s);
+  std::vector<double> B((size_t)n * n), T((size_t)n * n, 0.0), U((size_t)n * n);
+  for (size_t q = 0; q < B.size(); ++q) B[q] = A[q] * scale;
+  for (int i = 0; i < n; ++i) T[(size_t)i * n + i] = 1.0;
+  std::vector<double> S = T;
+  for (int k = 1; k <= 30; ++k) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double a = 0.0;
+        for (int l = 0; l < n; ++l) a += T[(size_t)i * n + l] * B[(size_t)l * n + j];
+        U[(size_t)i * n + j] = a / k;
+      }
+    T.swap(U);
+    for (size_t q = 0; q < S.size(); ++q) S[q] += T[q];
+  }
+  for (int r = 0; r < s; ++r) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double a = 0.0;
+        for (int l = 0; l < n; ++l) a += S[(size_t)i * n + l] * S[(size_t)l * n + j];
+        U[(size_t)i * n + j] = a;
+      }
+    S.swap(U);
+  }
+  std::copy(S.begin(), S.end(), E);
+}
+
 }  // namespace erem
 
 extern "C" int erem_leja_points(int M, double* xi) {
