@@ -19,6 +19,9 @@ LU solves and FFT-free arithmetic serve as library steps):
 * ``oracle.krylov``    Arnoldi / modified Gram-Schmidt (Algorithm ``alg:al2``),
                        the phi_1 approximation of eq. ``approphi`` (§4.1) with
                        error estimate and substeps
+* ``oracle.adjoint``   gradients of a temperature misfit with respect to T^0
+                       and ln K through frozen-schedule EREM steps (transposed
+                       Newton polynomial, face-flux and pressure adjoints)
 * ``oracle.timestep``  EREM (eq. ``EERM``), ROSM (eq. ``ROS``), ROS2(1)
                        (eq. ``ROSMh``, Table ``ros2``), pressure solves and the
                        sequential coupling of §3.2
@@ -28,6 +31,6 @@ other than itself: closed forms, dense matrix exponentials, high-precision
 divided differences, brute force on tiny inputs, conservation laws and the
 constants the paper prints (``tests/golden/``).
 """
-from . import fv, krylov, leja, timestep  # noqa: F401
+from . import adjoint, fv, krylov, leja, timestep  # noqa: F401
 from .fv import Grid, Physics  # noqa: F401
 from .leja import LejaOptions, LejaResult, phi1_leja  # noqa: F401
