@@ -286,6 +286,45 @@ EREM_API erem_status erem_step_krylov(erem_ctx* ctx, double* T, const double* p,
                                       const erem_krylov_opts* opts, erem_krylov_stats* stats,
                                       void* stream);
 
+/* ------------------------------------------------------------------------
+ * Adjoint of EREM steps: gradients of a function L of the temperatures with
+ * respect to T^0 and to ln K, for the linear fluid model (fixed Darcy field
+ * from one steady pressure solve).  The paper has no adjoint; each step is
+ * differentiated as the map it computes with its Leja schedule and spectral
+ * interval frozen: the Newton polynomial of §4.2 in J, whose transpose is
+ * the same polynomial in J^T (evaluated backwards by Horner's rule).  The
+ * derivative with respect to ln K runs through the upwind face fluxes and the
+ * steady pressure (one adjoint pressure solve, Jacobi CG in FP64).
+ *
+ * Use, after a forward run of erem_step on this context:
+ *   erem_adjoint_begin(ctx);
+ *   lam = dL/dT^N;  for n = N-1 .. 0: erem_adjoint_step(ctx, T^n, lam, sched_n)
+ *   (lam becomes dL/dT^n; T^n is recomputed by the caller from checkpoints,
+ *   e.g. by erem_step with the schedules replayed);
+ *   erem_adjoint_lnk(ctx, lnk, glnk, ...)  -> dL/dlnK.
+ * ------------------------------------------------------------------------ */
+
+/* Clear the accumulated derivative with respect to the face fluxes.
+ * Errors: EINVAL (no state, fluid_model != 0), ENOMEM, ECUDA. */
+EREM_API erem_status erem_adjoint_begin(erem_ctx* ctx, void* stream);
+
+/* One step backwards: lam [N] holds dL/dT^{n+1} on entry and dL/dT^n on
+ * return, for the step the context took from T [N] = T^n with the schedule
+ * [s, m_1..m_s] (erem_stats.substeps and .degrees of that step); the step's
+ * contribution to dL/dF is added to the accumulator.  The J, dt and interval
+ * are the context's current ones (those of the forward run).
+ * Errors: EINVAL (bad schedule, no state, fluid_model != 0), ENOMEM, ECUDA. */
+EREM_API erem_status erem_adjoint_step(erem_ctx* ctx, const double* T, double* lam,
+                                       const int* schedule, int n_schedule, void* stream);
+
+/* glnk [N] = dL/dlnK from the accumulated dL/dF, for lnk [N] the field of
+ * the forward run (its steady pressure must be the one given to
+ * erem_set_state).  The adjoint pressure system is solved to
+ * ||r|| <= tol ||b|| (maxit iterations); stats (may be NULL): lin_iters,
+ * lin_resid.  Errors: EINVAL, ENOTCONV, ECUDA. */
+EREM_API erem_status erem_adjoint_lnk(erem_ctx* ctx, const double* lnk, double* glnk, double tol,
+                                      int maxit, erem_stats* stats, void* stream);
+
 /* Message of the last failing call on ctx ("" if none; a static message if
  * ctx is NULL).  The pointer stays valid until the next call on ctx. */
 EREM_API const char* erem_last_error(const erem_ctx* ctx);

@@ -139,6 +139,9 @@ _sigs = {
                                ctypes.POINTER(erem_krylov_stats), _P]),
     "erem_step_krylov": (_I, [_P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(erem_krylov_opts),
                               ctypes.POINTER(erem_krylov_stats), _P]),
+    "erem_adjoint_begin": (_I, [_P, _P]),
+    "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
+    "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
     "erem_ensemble_create": (_I, [_I, ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics), _I,
                                   ctypes.POINTER(_P)]),
     "erem_ensemble_destroy": (_I, [_P]),
@@ -360,6 +363,23 @@ def erem_step_krylov(ctx, n, T, dt, p=None, lnk=None, phi=None, lam=None,
     return st
 
 
+def erem_adjoint_begin(ctx, stream=None) -> None:
+    _check(ctx, _lib.erem_adjoint_begin(ctx, _stream(stream)))
+
+
+def erem_adjoint_step(ctx, n, T, lam, schedule, stream=None) -> None:
+    arr = (ctypes.c_int * len(schedule))(*[int(v) for v in schedule])
+    _check(ctx, _lib.erem_adjoint_step(ctx, _ptr(T, n), _ptr(lam, n), arr, len(schedule),
+                                       _stream(stream)))
+
+
+def erem_adjoint_lnk(ctx, n, lnk, glnk, tol=1e-12, maxit=200000, stream=None) -> erem_stats:
+    st = erem_stats()
+    _check(ctx, _lib.erem_adjoint_lnk(ctx, _ptr(lnk, n), _ptr(glnk, n), float(tol), int(maxit),
+                                      ctypes.byref(st), _stream(stream)))
+    return st
+
+
 def erem_ensemble_create(grids, physics, precision: int = EREM_FP64):
     n = len(grids)
     ga = (erem_grid * n)(*grids)
@@ -494,6 +514,15 @@ class Context:
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):
         return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)
+
+    def adjoint_begin(self, stream=None):
+        erem_adjoint_begin(self._h, stream)
+
+    def adjoint_step(self, T, lam, schedule, stream=None):
+        erem_adjoint_step(self._h, self.n, T, lam, schedule, stream)
+
+    def adjoint_lnk(self, lnk, glnk, tol=1e-12, maxit=200000, stream=None):
+        return erem_adjoint_lnk(self._h, self.n, lnk, glnk, tol, maxit, stream)
 
     def phi1_apply_krylov(self, v, out, opts=None, stream=None):
         return phi1_apply_krylov(self._h, self.n, v, out, opts, stream)

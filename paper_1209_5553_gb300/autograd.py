@@ -1,0 +1,103 @@
+"""Temperature misfit of an EREM run as a torch.autograd.Function.
+
+Forward: the steady pressure for ln K (the library's Jacobi CG), the state of
+the heat problem, ``steps`` EREM steps (eq. ``EERM`` with real Leja phi_1,
+§4.2) from T0, and L = sum_o (T^N_o - data_o)^2 over the observation cells.
+Backward: the library's adjoint entry points (erem_adjoint_*), one step at a
+time from T^N back to T^0 with every step's Leja schedule frozen at its
+forward value; the states T^n are recomputed from checkpoints kept every
+``checkpoint`` steps by replaying those schedules, so at most ``checkpoint``
+states are held at once.  Gradients with respect to ln K and T0.
+
+Argument marshalling and step sequencing only: every step runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import Context, Physics, leja_opts
+
+
+class MisfitModel:
+    """Grid, physics and run length of the misfit (one library context).
+
+    physics: the heat-model constants and heads (fluid_model 0);
+    phi, lam: porosity and conductivity fields [N] (CUDA FP64 tensors);
+    obs: observation cells (CUDA int64), data: observed values (CUDA FP64)."""
+
+    def __init__(self, dim, nx, ny, nz, physics: Physics, phi, lam, dt, steps, obs, data,
+                 precision="fp32_bulk", checkpoint=10, tol=1e-6, pressure_tol=1e-12,
+                 replay=None):
+        if physics.fluid_model != 0:
+            raise ValueError("the adjoint needs fluid_model 0")
+        self.ctx = Context(dim, nx, ny, nz, physics=physics, precision=precision)
+        self.n = nx * ny * nz
+        self.nx = nx
+        self.physics = physics
+        self.phi, self.lam = phi, lam
+        self.dt, self.steps = float(dt), int(steps)
+        self.obs, self.data = obs, data
+        self.checkpoint = max(1, int(checkpoint))
+        self.tol, self.pressure_tol = tol, pressure_tol
+        self.replay = replay          # forced schedules (one per step), or None
+        self.schedules = []           # schedules of the last forward run
+
+    def head_guess(self, like):
+        x = (torch.arange(self.nx, dtype=torch.float64, device=like.device) + 0.5) / self.nx
+        ramp = self.physics.head_left + (self.physics.head_right - self.physics.head_left) * x
+        return ramp.repeat(self.n // self.nx).contiguous()
+
+    def close(self):
+        self.ctx.close()
+
+
+class EremMisfit(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, lnk, T0, model: MisfitModel):
+        m = model
+        lnk = lnk.detach().contiguous()
+        p = m.head_guess(lnk)
+        m.ctx.pressure_solve(lnk, None, p, tol=m.pressure_tol, maxit=1000000)
+        T = T0.detach().clone().contiguous()
+        m.ctx.set_state(T, p, lnk, m.phi, m.lam, m.dt)
+        ckpts = {0: T.clone()}
+        scheds = []
+        for n in range(m.steps):
+            opts = leja_opts(tol=m.tol) if m.replay is None else leja_opts(tol=m.tol, replay=m.replay[n])
+            st = m.ctx.erem_step(T, m.dt, opts=opts)
+            scheds.append(st.schedule)
+            if (n + 1) % m.checkpoint == 0 and n + 1 < m.steps:
+                ckpts[n + 1] = T.clone()
+        m.schedules = scheds
+        fctx.model, fctx.ckpts, fctx.scheds = m, ckpts, scheds
+        fctx.save_for_backward(lnk, T)
+        r = T[m.obs] - m.data
+        return (r * r).sum()
+
+    @staticmethod
+    def backward(fctx, gL):
+        m, ckpts, scheds = fctx.model, fctx.ckpts, fctx.scheds
+        lnk, TN = fctx.saved_tensors
+        lam = torch.zeros_like(TN)
+        lam[m.obs] = 2.0 * (TN[m.obs] - m.data) * gL
+        m.ctx.adjoint_begin()
+        starts = sorted(ckpts)
+        for a, s0 in reversed(list(enumerate(starts))):
+            s1 = starts[a + 1] if a + 1 < len(starts) else m.steps
+            states = [ckpts[s0].clone()]
+            T = states[0].clone()
+            for n in range(s0, s1 - 1):
+                m.ctx.erem_step(T, m.dt, opts=leja_opts(tol=m.tol, replay=scheds[n]))
+                states.append(T.clone())
+            for n in range(s1 - 1, s0 - 1, -1):
+                m.ctx.adjoint_step(states[n - s0], lam, scheds[n])
+        glnk = torch.zeros_like(lnk)
+        m.ctx.adjoint_lnk(lnk, glnk, tol=m.pressure_tol)
+        return glnk, lam, None
+
+
+def misfit(lnk, T0, model: MisfitModel):
+    """L(lnK, T0) with gradients through the adjoint (see EremMisfit)."""
+    return EremMisfit.apply(lnk, T0, model)

@@ -422,6 +422,7 @@ erem_status prepare_step(erem_ctx* c, double* T, const double* p, const double* 
     }
   }
   if (need_interval && !c->jl_valid) {
+    c->jlT_valid = false;
     launch_scale_jl(c, c->dt / c->gam, s);
     EREM_TRY(check_launch(c, "scale"));
     c->jl_valid = true;
@@ -647,6 +648,55 @@ erem_status run_krylov(erem_ctx* c, const double* src, const KrOpts& o, erem_kry
   return EREM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+erem_status ensure_adj(erem_ctx* c, int M, int S) {
+  const size_t np = (size_t)c->Np;
+  const size_t esz = c->prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
+  const int nc = c->dim == 3 ? 7 : 5;
+  if (!c->jlT_all) {
+    EREM_TRY(dalloc(c, &c->jlT_all, (np + 128) / 128 * 128 * nc * esz));
+    for (int k = 0; k < 2; ++k) EREM_TRY(dalloc(c, &c->adj_s[k], np * esz));
+    EREM_TRY(dalloc_t(c, &c->adj_mu, np));
+    EREM_TRY(dalloc_t(c, &c->adj_z, np));
+    EREM_TRY(dalloc_t(c, &c->adj_G, np));
+    EREM_TRY(dalloc_t(c, &c->adj_lam, np));
+    EREM_TRY(dalloc_t(c, &c->adj_gx, np));
+    EREM_TRY(dalloc_t(c, &c->adj_gy, np));
+    if (c->dim == 3) EREM_TRY(dalloc_t(c, &c->adj_gz, np));
+    EREM_TRY(dalloc_t(c, &c->adj_g0, (size_t)c->ny * c->nz));
+  }
+  if (M > c->adj_store_cap) {
+    if (c->adj_store) cudaFree(c->adj_store);
+    c->adj_store = nullptr;
+    c->adj_store_cap = 0;
+    EREM_TRY(dalloc(c, &c->adj_store, (size_t)M * np * esz));
+    c->adj_store_cap = M;
+  }
+  while ((int)c->adj_w.size() < S) {
+    double* w = nullptr;
+    EREM_TRY(dalloc_t(c, &w, np));
+    c->adj_w.push_back(w);
+  }
+  return EREM_OK;
+}
+
+erem_status adj_clear_faces(erem_ctx* c, cudaStream_t s) {
+  const size_t np = (size_t)c->Np;
+  EREM_CUDA(c, cudaMemsetAsync(c->adj_gx, 0, np * sizeof(double), s));
+  EREM_CUDA(c, cudaMemsetAsync(c->adj_gy, 0, np * sizeof(double), s));
+  if (c->adj_gz) EREM_CUDA(c, cudaMemsetAsync(c->adj_gz, 0, np * sizeof(double), s));
+  EREM_CUDA(c, cudaMemsetAsync(c->adj_g0, 0, (size_t)c->ny * c->nz * sizeof(double), s));
+  return EREM_OK;
+}
+
+erem_status adj_check(erem_ctx* c) {
+  if (!c->have_state || !c->jl_valid) return fail(c, EREM_EINVAL, "adjoint before erem_set_state");
+  if (c->phys.fluid_model != 0) return fail(c, EREM_EINVAL, "the adjoint needs fluid_model = 0");
+  return EREM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -779,6 +829,12 @@ erem_status erem_destroy(erem_ctx* c) {
   if (c->kr_r) cudaFree(c->kr_r);
   if (c->kr_y) cudaFree(c->kr_y);
   if (c->kr_dev) cudaFree(c->kr_dev);
+  void* adj[] = {c->jlT_all, c->adj_store, c->adj_s[0], c->adj_s[1], c->adj_mu, c->adj_z, c->adj_G,
+                 c->adj_lam, c->adj_gx, c->adj_gy, c->adj_gz, c->adj_g0};
+  for (void* p : adj)
+    if (p) cudaFree(p);
+  for (double* p : c->adj_w)
+    if (p) cudaFree(p);
   if (c->kr_host) cudaFreeHost(c->kr_host);
   if (c->red_cnt) cudaFree(c->red_cnt);
   if (c->qmid) cudaFree(c->qmid);
@@ -1030,6 +1086,146 @@ erem_status erem_step_krylov(erem_ctx* c, double* T, const double* p, const doub
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
   }
+  return EREM_OK;
+}
+
+erem_status erem_adjoint_begin(erem_ctx* c, void* stream) {
+  if (!c) return EREM_EINVAL;
+  EREM_TRY(adj_check(c));
+  EREM_TRY(ensure_adj(c, 1, 1));
+  return adj_clear_faces(c, (cudaStream_t)stream);
+}
+
+erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const int* sched,
+                              int ns, void* stream) {
+  if (!c) return EREM_EINVAL;
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  EREM_TRY(adj_check(c));
+  if (!T || !lam || !sched) return fail(c, EREM_EINVAL, "NULL argument");
+  const int S = ns >= 2 ? sched[0] : 0;
+  if (S < 1 || S > 64 || ns != 1 + S) return fail(c, EREM_EINVAL, "schedule must be [s, m_1..m_s], 1 <= s <= 64");
+  int M = 0;
+  for (int k = 1; k <= S; ++k) {
+    if (sched[k] < 1 || sched[k] > kMaxTerms) return fail(c, EREM_EINVAL, "schedule degree out of range");
+    M = std::max(M, sched[k]);
+  }
+  EREM_TRY(ensure_leja(c, M));
+  EREM_TRY(ensure_adj(c, M, S));
+  if (!c->jlT_valid) {
+    launch_adj_scale_jlT(c, c->dt / c->gam, s);
+    c->jlT_valid = true;
+  }
+  double *Td, *lamd;
+  EREM_TRY(resolve(c, 6, T, true, s, &Td));
+  EREM_TRY(resolve(c, 7, lam, true, s, &lamd));
+  launch_pack(c, Td, c->Tn, s);
+  launch_pack(c, lamd, c->adj_lam, s);
+  EREM_TRY(prepare_dd(c, S, M, s));
+  const std::vector<double>& d = c->dd_cache[S].d;
+  const double delta = c->dt / S;
+  const double cg = c->cfoc / c->gam;
+  const double scale = delta * delta / (c->gam / S);
+  const size_t qbytes = (size_t)c->Np * (c->prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double));
+  char* store = (char*)c->adj_store;
+  StopParams sp{};
+  sp.delta = delta;
+  sp.ncells = (double)c->N;
+  sp.pow10 = 1.0;
+  sp.tol_a = 1.0;
+  sp.tol_r = 0.0;
+  sp.window = 1;
+  sp.m_max = kMaxTerms;
+  sp.replay = 1;
+  // G = J T^n + b (the step's first kernel), then the w_k of the substeps
+  launch_step_init(c, Td, d[0], sp, s);
+  for (int k = 0; k + 1 < S; ++k) {
+    const double* u = c->vrhs;
+    if (k > 0) {
+      launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
+      u = c->u;
+    }
+    launch_leja_init(c, u, d[0], sp, s);
+    int qin = 0;
+    for (int m = 1; m <= sched[1 + k]; ++m) {
+      launch_leja_term(c, m, qin, cg, s);
+      qin ^= 1;
+    }
+    if (k == 0) launch_lincomb(c, c->adj_w[1], 0.0, c->P, delta, c->P, s);
+    else launch_lincomb(c, c->adj_w[k + 1], 1.0, c->adj_w[k], delta, c->P, s);
+  }
+  // backwards through the substeps
+  launch_lincomb(c, c->adj_mu, 1.0, c->adj_lam, 0.0, c->adj_lam, s);
+  EREM_CUDA(c, cudaMemsetAsync(c->adj_G, 0, sizeof(double) * c->Np, s));
+  for (int k = S - 1; k >= 0; --k) {
+    const double* u = c->vrhs;
+    if (k > 0) {
+      launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
+      u = c->u;
+    }
+    const int mk = sched[1 + k];
+    launch_leja_init(c, u, d[0], sp, s);
+    EREM_CUDA(c, cudaMemcpyAsync(store, c->q[0], qbytes, cudaMemcpyDeviceToDevice, s));
+    for (int m = 1; m < mk; ++m)
+      launch_leja_term_ptr(c, m, store + (size_t)(m - 1) * qbytes, store + (size_t)m * qbytes, cg, s);
+    launch_adj_start(c, c->adj_mu, d[mk], c->adj_s[0], s);
+    int cur = 0;
+    for (int j = mk - 1; j >= 0; --j) {
+      launch_adj_horner(c, c->adj_s[cur], c->adj_s[cur ^ 1], c->adj_mu, store + (size_t)j * qbytes, d[j],
+                        cg + c->xi_host[j], scale, 1, s);
+      cur ^= 1;
+    }
+    launch_adj_z(c, c->adj_s[cur], delta, c->adj_z, c->adj_G, s);
+    if (k > 0) launch_adj_face_pair(c, c->adj_z, c->adj_w[k], 1.0, s);
+    launch_adj_jT_apply(c, c->adj_z, c->adj_mu, c->adj_mu, s);
+  }
+  launch_adj_face_pair(c, c->adj_G, c->Tn, 1.0, s);
+  launch_adj_b_use(c, c->adj_G, s);
+  launch_adj_jT_apply(c, c->adj_G, c->adj_lam, c->adj_lam, s);
+  launch_unpack(c, c->adj_lam, lamd, s);
+  EREM_TRY(check_launch(c, "adjoint step"));
+  EREM_TRY(finish_staged(c, lam, lamd, s));
+  return EREM_OK;
+}
+
+erem_status erem_adjoint_lnk(erem_ctx* c, const double* lnk, double* glnk, double tol, int maxit,
+                             erem_stats* st, void* stream) {
+  if (!c) return EREM_EINVAL;
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  EREM_TRY(adj_check(c));
+  if (!c->adj_gx) return fail(c, EREM_EINVAL, "erem_adjoint_lnk before erem_adjoint_begin");
+  if (!lnk || !glnk) return fail(c, EREM_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || maxit < 0) return fail(c, EREM_EINVAL, "tol must be > 0 and maxit >= 0");
+  EREM_TRY(ensure_krylov(c));
+  double *dk, *dout;
+  EREM_TRY(resolve(c, 5, lnk, true, s, &dk));
+  launch_pres_faces(c, dk, nullptr, s);
+  launch_adj_dLdp(c, s);
+  launch_cg_init(c, tol, s);
+  EREM_TRY(check_launch(c, "adjoint pressure set-up"));
+  EREM_TRY(read_ctrl(c, s));
+  int it = 0;
+  while (!c->ctrl_h->lin_done && it < maxit) {
+    const int n = std::min(32, maxit - it);
+    for (int j = 0; j < n; ++j) launch_cg_iter(c, it + j, s);
+    EREM_TRY(check_launch(c, "adjoint cg"));
+    it += n;
+    EREM_TRY(read_ctrl(c, s));
+  }
+  const Ctrl h = *c->ctrl_h;
+  EREM_TRY(resolve(c, 6, glnk, false, s, &dout));
+  launch_adj_lnk(c, dout, s);
+  EREM_TRY(check_launch(c, "adjoint lnk"));
+  EREM_TRY(finish_staged(c, glnk, dout, s));
+  if (st) {
+    st->lin_iters = h.lin_it;
+    st->lin_resid = h.lin[K_BB] > 0 ? std::sqrt(h.lin[K_RR] / h.lin[K_BB]) : 0.0;
+    st->launches = (int)c->launches;
+  }
+  if (h.lin_break && !(h.lin[K_RR] <= h.lin[K_TOL2]))
+    return fail(c, EREM_ENOTCONV, "adjoint pressure CG breakdown");
+  if (!h.lin_done) return fail(c, EREM_ENOTCONV, "adjoint pressure CG did not converge within maxit");
   return EREM_OK;
 }
 

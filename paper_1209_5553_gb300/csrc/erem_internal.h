@@ -201,6 +201,15 @@ struct erem_ctx {
   erem::KrDev* kr_dev = nullptr;
   erem::KrDev* kr_host = nullptr;   // pinned
   int kr_cap = 0;                   // basis vectors allocated
+  // adjoint (allocated on first use)
+  void* jlT_all = nullptr;          // Leja copy of J^T, layout of jl_all
+  bool jlT_valid = false;
+  void* adj_store = nullptr;        // forward Newton vectors q_0..q_{m-1} of one substep
+  int adj_store_cap = 0;            // vectors adj_store holds
+  void* adj_s[2] = {};              // Horner values (Leja precision)
+  double *adj_mu = nullptr, *adj_z = nullptr, *adj_G = nullptr, *adj_lam = nullptr;
+  std::vector<double*> adj_w;       // w_k of the substeps of one step
+  double *adj_gx = nullptr, *adj_gy = nullptr, *adj_gz = nullptr, *adj_g0 = nullptr;
   // reductions and control
   double* red_part = nullptr;
   unsigned* red_cnt = nullptr;
@@ -251,6 +260,8 @@ void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopP
                       cudaStream_t s);
 int leja_term_blocks_per_sm(const erem_ctx* c);
 void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
+void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,
+                          cudaStream_t s);
 struct WaveGeoHost {
   int nslices = 0, slice_cells = 0, cps = 0, chunk_vecs = 0, lag = 0, n_items = 0;
 };
@@ -294,6 +305,22 @@ struct KrComb {
   int n;
 };
 void launch_kr_combine(const erem_ctx* c, double* y, const KrComb& cb, cudaStream_t s);
+// adjoint passes
+void launch_adj_scale_jlT(const erem_ctx* c, double sc, cudaStream_t s);
+void launch_adj_jT_apply(const erem_ctx* c, const double* x, const double* a, double* out,
+                         cudaStream_t s);
+void launch_adj_face_pair(const erem_ctx* c, const double* y, const double* x, double scale,
+                          cudaStream_t s);
+void launch_adj_start(const erem_ctx* c, const double* mu, double d, void* sbuf, cudaStream_t s);
+void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const double* mu,
+                       const void* q, double dj, double shift, double scale, int faces,
+                       cudaStream_t s);
+void launch_adj_z(const erem_ctx* c, const void* sbuf, double delta, double* z, double* zacc,
+                  cudaStream_t s);
+void launch_adj_b_use(const erem_ctx* c, const double* y, cudaStream_t s);
+void launch_adj_dLdp(const erem_ctx* c, cudaStream_t s);
+void launch_adj_lnk(const erem_ctx* c, double* out, cudaStream_t s);
+
 // dense exponential of a small host matrix (row-major n x n), Taylor +
 // scaling and squaring (leja_host.cpp)
 void expm_small(int n, const double* A, double* E);

@@ -1043,6 +1043,218 @@ __global__ void k_kr_combine(double* __restrict__ y, KrComb cb, int Np) {
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of frozen-schedule EREM steps (linear fluid model).  A step is the
+// Newton polynomial of §4.2 in J with its schedule and interval held; its
+// transpose is the same polynomial in J^T, evaluated here by the Horner
+// recurrence s_j = d_j mu + B_j^T s_{j+1}, B_j = (delta J - c I)/gamma -
+// xi_j I.  Every use of J on a vector x with adjoint y adds to the
+// derivative with respect to the upwind face fluxes F = (rho c)_f v:
+// (y_R / C_R - y_L / C_L) x_up on an interior face, -y x / C on the x = 1
+// face (stored in the x-face slot of the last column), y x / C on an outflow
+// x = 0 face (one value per row).
+// ---------------------------------------------------------------------------
+struct AdjFaces {
+  const double *Fx, *Fy, *Fz, *F0, *icap;
+  double *gx, *gy, *gz, *g0;
+};
+
+// Transposed Leja copy: row i of J^T holds D_i and the neighbours' couplings
+// towards i (E of the cell to the west, W of the cell to the east, ...).
+template <typename Tq, int T>
+__global__ void k_adj_scale_jlT(JOut jc, Tq* __restrict__ out, double sc, Geo g, int nc) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.Np; i += gridDim.x * NT) {
+    int ix, iy, iz;
+    const int row = i / g.px;
+    ix = i - row * g.px;
+    iy = row % g.ny;
+    iz = row / g.ny;
+    double c[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (ix < g.nx) {
+      c[0] = jc.c[0][i];
+      if (ix > 0) c[1] = jc.c[2][i - 1];
+      if (ix < g.nx - 1) c[2] = jc.c[1][i + 1];
+      if (iy > 0) c[3] = jc.c[4][i - g.px];
+      if (iy < g.ny - 1) c[4] = jc.c[3][i + g.px];
+      if (nc == 7) {
+        if (iz > 0) c[5] = jc.c[6][i - g.plane];
+        if (iz < g.nz - 1) c[6] = jc.c[5][i + g.plane];
+      }
+    }
+    const size_t base = (size_t)(i / T) * nc * T + (i % T);
+    for (int k = 0; k < nc; ++k) out[base + (size_t)k * T] = (Tq)(sc * c[k]);
+  }
+}
+
+// out = a + J^T x (FP64, over the real cells; pads keep 0)
+__global__ void k_adj_jT_apply(JIn J, const double* __restrict__ x, const double* __restrict__ a,
+                               double* __restrict__ out, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    double v = J.c[0][ip] * x[ip];
+    if (ix > 0) v += J.c[2][ip - 1] * x[ip - 1];
+    if (ix < g.nx - 1) v += J.c[1][ip + 1] * x[ip + 1];
+    if (iy > 0) v += J.c[4][ip - g.px] * x[ip - g.px];
+    if (iy < g.ny - 1) v += J.c[3][ip + g.px] * x[ip + g.px];
+    if (g.dim == 3) {
+      if (iz > 0) v += J.c[6][ip - g.plane] * x[ip - g.plane];
+      if (iz < g.nz - 1) v += J.c[5][ip + g.plane] * x[ip + g.plane];
+    }
+    out[ip] = a[ip] + v;
+  }
+}
+
+// Face-flux derivative of one use of J: y^T J x (y, x of any precision).
+template <typename Ty, typename Tx>
+__device__ __forceinline__ void adj_face_cell(const AdjFaces& f, const Ty* __restrict__ y,
+                                              const Tx* __restrict__ x, int ip, int ix, int iy,
+                                              int iz, const Geo& g, double scale) {
+  const double yc = (double)y[ip] * f.icap[ip];
+  const double xc = (double)x[ip];
+  if (ix < g.nx - 1) {
+    const double F = f.Fx[ip];
+    const double xu = F >= 0.0 ? xc : (double)x[ip + 1];
+    f.gx[ip] += scale * ((double)y[ip + 1] * f.icap[ip + 1] - yc) * xu;
+  } else {
+    f.gx[ip] += scale * (-yc * xc);
+  }
+  if (iy < g.ny - 1) {
+    const double F = f.Fy[ip];
+    const double xu = F >= 0.0 ? xc : (double)x[ip + g.px];
+    f.gy[ip] += scale * ((double)y[ip + g.px] * f.icap[ip + g.px] - yc) * xu;
+  }
+  if (g.dim == 3 && iz < g.nz - 1) {
+    const double F = f.Fz[ip];
+    const double xu = F >= 0.0 ? xc : (double)x[ip + g.plane];
+    f.gz[ip] += scale * ((double)y[ip + g.plane] * f.icap[ip + g.plane] - yc) * xu;
+  }
+  if (ix == 0) {
+    const int r = iy + g.ny * iz;
+    if (!(f.F0[r] > 0.0)) f.g0[r] += scale * yc * xc;
+  }
+}
+
+template <typename Ty, typename Tx>
+__global__ void k_adj_face_pair(AdjFaces f, const Ty* __restrict__ y, const Tx* __restrict__ x,
+                                double scale, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    adj_face_cell<Ty, Tx>(f, y, x, ip, ix, iy, iz, g, scale);
+  }
+}
+
+// One Horner step of the transposed polynomial (Leja precision):
+// s_out = d_j mu + ((delta J^T - c I)/gamma - xi_j I) s_in, and the face
+// derivative of the pair (s_in, q_j) with the factor delta^2 / gamma.
+template <typename Tq>
+__global__ void k_adj_horner(const Tq* __restrict__ s_in, Tq* __restrict__ s_out,
+                             const double* __restrict__ mu, const Tq* __restrict__ q,
+                             const Tq* __restrict__ jlT, int T_tile, int nc, double dj,
+                             double shift, double scale, int faces, AdjFaces f, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const size_t base = (size_t)(ip / T_tile) * nc * T_tile + (ip % T_tile);
+    auto cf = [&](int k) { return jlT[base + (size_t)k * T_tile]; };
+    const Tq sc = s_in[ip];
+    Tq a = (cf(0) - (Tq)shift) * sc;
+    if (ix > 0) a = fma(cf(1), s_in[ip - 1], a);
+    if (ix < g.nx - 1) a = fma(cf(2), s_in[ip + 1], a);
+    if (iy > 0) a = fma(cf(3), s_in[ip - g.px], a);
+    if (iy < g.ny - 1) a = fma(cf(4), s_in[ip + g.px], a);
+    if (g.dim == 3) {
+      if (iz > 0) a = fma(cf(5), s_in[ip - g.plane], a);
+      if (iz < g.nz - 1) a = fma(cf(6), s_in[ip + g.plane], a);
+    }
+    s_out[ip] = (Tq)(dj * mu[ip] + (double)a);
+    if (faces) adj_face_cell<Tq, Tq>(f, s_in, q, ip, ix, iy, iz, g, scale);
+  }
+}
+
+// z = delta s (FP64); zacc += z
+template <typename Tq>
+__global__ void k_adj_z(const Tq* __restrict__ s, double delta, double* __restrict__ z,
+                        double* __restrict__ zacc, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
+    const double v = delta * (double)s[i];
+    z[i] = v;
+    zacc[i] += v;
+  }
+}
+
+// s = d mu in the Leja precision (the first Horner value)
+template <typename Tq>
+__global__ void k_adj_start(const double* __restrict__ mu, double d, Tq* __restrict__ s, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) s[i] = (Tq)(d * mu[i]);
+}
+
+// the constant inflow term of G: y^T b through the x = 0 faces
+__global__ void k_adj_b_use(AdjFaces f, const double* __restrict__ y, double T_in, Geo g) {
+  const int nf = g.ny * g.nz;
+  for (int r = blockIdx.x * NT + threadIdx.x; r < nf; r += gridDim.x * NT) {
+    const int ip = g.px * r;
+    if (f.F0[r] > 0.0) f.g0[r] += y[ip] * f.icap[ip] * T_in;
+  }
+}
+
+// dL/dp from dL/dF (gathered per cell) into the right-hand side b of the
+// pressure system; x = 0 as the initial guess.
+__global__ void k_adj_dLdp(AdjFaces f, const double* __restrict__ lnk, double rc, Phys ph,
+                           double* __restrict__ b, double* __restrict__ x,
+                           const double* __restrict__ Ux, const double* __restrict__ Uy,
+                           const double* __restrict__ Uz, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    double r = 0.0;
+    if (ix < g.nx - 1) r += rc * f.gx[ip] * Ux[ip];
+    if (ix > 0) r -= rc * f.gx[ip - 1] * Ux[ip - 1];
+    if (iy < g.ny - 1) r += rc * f.gy[ip] * Uy[ip];
+    if (iy > 0) r -= rc * f.gy[ip - g.px] * Uy[ip - g.px];
+    if (g.dim == 3) {
+      if (iz < g.nz - 1) r += rc * f.gz[ip] * Uz[ip];
+      if (iz > 0) r -= rc * f.gz[ip - g.plane] * Uz[ip - g.plane];
+    }
+    const double uD = ph.ax * exp(lnk[ip]) / (0.5 * ph.hx);
+    if (ix == 0) r -= rc * f.g0[iy + g.ny * iz] * uD;
+    if (ix == g.nx - 1) r += rc * f.gx[ip] * uD;
+    b[ip] = r;
+    x[ip] = 0.0;
+  }
+}
+
+// dL/dlnK per cell from dL/dF, the pressure p and the adjoint pressure mu
+__global__ void k_adj_lnk(AdjFaces f, const double* __restrict__ lnk, const double* __restrict__ p,
+                          const double* __restrict__ mu, double rc, Phys ph,
+                          const double* __restrict__ Ux, const double* __restrict__ Uy,
+                          const double* __restrict__ Uz, double* __restrict__ out, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double kc = exp(lnk[ip]);
+    double acc = 0.0;
+    auto face = [&](const double* gf, const double* U, int L, int R, int self_is_left) {
+      const double kL = exp(lnk[L]), kR = exp(lnk[R]);
+      const double phi_s = (p[L] - p[R]) * (rc * gf[L] - (mu[L] - mu[R]));
+      acc += phi_s * U[L] * (self_is_left ? kR : kL) / (kL + kR);
+    };
+    if (ix < g.nx - 1) face(f.gx, Ux, ip, ip + 1, 1);
+    if (ix > 0) face(f.gx, Ux, ip - 1, ip, 0);
+    if (iy < g.ny - 1) face(f.gy, Uy, ip, ip + g.px, 1);
+    if (iy > 0) face(f.gy, Uy, ip - g.px, ip, 0);
+    if (g.dim == 3) {
+      if (iz < g.nz - 1) face(f.gz, Uz, ip, ip + g.plane, 1);
+      if (iz > 0) face(f.gz, Uz, ip - g.plane, ip, 0);
+    }
+    const double uD = ph.ax * kc / (0.5 * ph.hx);
+    if (ix == 0) acc += uD * (ph.head_left - p[ip]) * (rc * f.g0[iy + g.ny * iz] + mu[ip]);
+    if (ix == g.nx - 1) acc += uD * (p[ip] - ph.head_right) * (rc * f.gx[ip] - mu[ip]);
+    out[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pressure: TPFA mass-mobility transmissibilities and Jacobi-PCG
 // ---------------------------------------------------------------------------
 struct PresArr {
@@ -1660,6 +1872,33 @@ void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t
   }
 }
 
+// One Leja term with explicit input/output vectors (the adjoint's store of
+// Newton vectors); otherwise as launch_leja_term.
+void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,
+                          cudaStream_t s) {
+  const Geo g = geo_of(c);
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK) {
+    const LejaCoef<float> cf = leja_coef<float, 4>(c);
+    const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
+    if (c->dim == 3)
+      k_leja_term<float, 4, 3><<<nb, NT, 0, s>>>((const float*)qi, (float*)qo, c->P, cf, g, c->xi_dev,
+                                                 c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
+    else
+      k_leja_term<float, 4, 2><<<nb, NT, 0, s>>>((const float*)qi, (float*)qo, c->P, cf, g, c->xi_dev,
+                                                 c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
+  } else {
+    const LejaCoef<double> cf = leja_coef<double, 2>(c);
+    const int nb = std::min(grid_for(c, c->Np / 2), c->term_grid);
+    if (c->dim == 3)
+      k_leja_term<double, 2, 3><<<nb, NT, 0, s>>>((const double*)qi, (double*)qo, c->P, cf, g, c->xi_dev,
+                                                  c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
+    else
+      k_leja_term<double, 2, 2><<<nb, NT, 0, s>>>((const double*)qi, (double*)qo, c->P, cf, g, c->xi_dev,
+                                                  c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
+  }
+}
+
 WaveGeoHost wave_geometry(const erem_ctx* c, int grid) {
   WaveGeoHost w;
   const int vec = c->prec == EREM_FP32_BULK ? 4 : 2;
@@ -1895,6 +2134,93 @@ void launch_kr_orth(const erem_ctx* c, double* w, const double* vprev, const dou
 void launch_kr_combine(const erem_ctx* c, double* y, const KrComb& cb, cudaStream_t s) {
   ++c->launches;
   k_kr_combine<<<blocks_padded(c), NT, 0, s>>>(y, cb, (int)c->Np);
+}
+
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+AdjFaces adj_faces(const erem_ctx* c) {
+  return AdjFaces{c->Fx, c->Fy, c->Fz, c->F0, c->icap, c->adj_gx, c->adj_gy, c->adj_gz, c->adj_g0};
+}
+
+void launch_adj_scale_jlT(const erem_ctx* c, double sc, cudaStream_t s) {
+  JOut jc;
+  for (int k = 0; k < 7; ++k) jc.c[k] = c->jc[k];
+  jc.b0 = nullptr;
+  const int nc = c->dim == 3 ? 7 : 5;
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_adj_scale_jlT<float, 128><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jlT_all, sc, geo_of(c), nc);
+  else
+    k_adj_scale_jlT<double, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (double*)c->jlT_all, sc, geo_of(c), nc);
+}
+
+void launch_adj_jT_apply(const erem_ctx* c, const double* x, const double* a, double* out,
+                         cudaStream_t s) {
+  ++c->launches;
+  k_adj_jT_apply<<<blocks_cells(c), NT, 0, s>>>(jin(c), x, a, out, geo_of(c));
+}
+
+void launch_adj_face_pair(const erem_ctx* c, const double* y, const double* x, double scale,
+                          cudaStream_t s) {
+  ++c->launches;
+  k_adj_face_pair<double, double><<<blocks_cells(c), NT, 0, s>>>(adj_faces(c), y, x, scale, geo_of(c));
+}
+
+void launch_adj_start(const erem_ctx* c, const double* mu, double d, void* sbuf, cudaStream_t s) {
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_adj_start<float><<<blocks_padded(c), NT, 0, s>>>(mu, d, (float*)sbuf, (int)c->Np);
+  else
+    k_adj_start<double><<<blocks_padded(c), NT, 0, s>>>(mu, d, (double*)sbuf, (int)c->Np);
+}
+
+void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const double* mu,
+                       const void* q, double dj, double shift, double scale, int faces,
+                       cudaStream_t s) {
+  const int nc = c->dim == 3 ? 7 : 5;
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_adj_horner<float><<<blocks_cells(c), NT, 0, s>>>((const float*)s_in, (float*)s_out, mu,
+                                                       (const float*)q, (const float*)c->jlT_all, 128,
+                                                       nc, dj, shift, scale, faces, adj_faces(c),
+                                                       geo_of(c));
+  else
+    k_adj_horner<double><<<blocks_cells(c), NT, 0, s>>>((const double*)s_in, (double*)s_out, mu,
+                                                        (const double*)q, (const double*)c->jlT_all,
+                                                        64, nc, dj, shift, scale, faces, adj_faces(c),
+                                                        geo_of(c));
+}
+
+void launch_adj_z(const erem_ctx* c, const void* sbuf, double delta, double* z, double* zacc,
+                  cudaStream_t s) {
+  ++c->launches;
+  if (c->prec == EREM_FP32_BULK)
+    k_adj_z<float><<<blocks_padded(c), NT, 0, s>>>((const float*)sbuf, delta, z, zacc, (int)c->Np);
+  else
+    k_adj_z<double><<<blocks_padded(c), NT, 0, s>>>((const double*)sbuf, delta, z, zacc, (int)c->Np);
+}
+
+void launch_adj_b_use(const erem_ctx* c, const double* y, cudaStream_t s) {
+  ++c->launches;
+  const int nf = c->ny * c->nz;
+  k_adj_b_use<<<std::max(1, std::min(c->red_blocks, (nf + NT - 1) / NT)), NT, 0, s>>>(
+      adj_faces(c), y, c->phys.T_inflow, geo_of(c));
+}
+
+void launch_adj_dLdp(const erem_ctx* c, cudaStream_t s) {
+  const PresArr a = pres_arr(c);
+  ++c->launches;
+  k_adj_dLdp<<<blocks_cells(c), NT, 0, s>>>(adj_faces(c), c->lnk, c->phys.rhoc_f, phys_of(c), a.b, a.x,
+                                            a.Ux, a.Uy, a.Uz, geo_of(c));
+}
+
+void launch_adj_lnk(const erem_ctx* c, double* out, cudaStream_t s) {
+  const PresArr a = pres_arr(c);
+  ++c->launches;
+  k_adj_lnk<<<blocks_cells(c), NT, 0, s>>>(adj_faces(c), c->lnk, c->p, a.x, c->phys.rhoc_f, phys_of(c),
+                                           a.Ux, a.Uy, a.Uz, out, geo_of(c));
 }
 
 }  // namespace erem
