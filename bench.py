@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--slab", type=int, default=16, help="z planes of the oracle's sample")
-    ap.add_argument("--workload", choices=["channels3d", "coupled2d", "ensemble"],
+    ap.add_argument("--workload", choices=["channels3d", "coupled2d", "ensemble", "adjoint"],
                     default="channels3d",
                     help="channels3d: the 256^3 headline; coupled2d: 1024^2 sequential "
                          "pressure/temperature with T-dependent fluid laws; ensemble: 512 "
@@ -762,6 +762,81 @@ def main_ensemble(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the adjoint workload: 128^3 channels, 60 steps, gradient of a 16-cell misfit
+# with respect to ln K and T0 (forward + checkpointed adjoint, FP32-bulk)
+# ---------------------------------------------------------------------------
+def main_adjoint(args):
+    import torch
+
+    import paper_1209_5553_gb300 as E
+    import workloads as W
+    from paper_1209_5553_gb300.autograd import MisfitModel, misfit
+
+    rank, world, local = dist_info()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist_init(world, "nccl")
+    n = 128 if args.n == 256 else args.n
+    wl, obs, data = W.adjoint3d(n)
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    # heads for a largest face speed of 1 and (rho c) for Pe 1e3, from a GPU pressure solve
+    with E.Context(3, n, n, n, physics=E.Physics(1.0, 1.0, wl.head_drop, 0.0, wl.T_inflow, 0)) as ctx:
+        st = ctx.pressure_solve(t(wl.lnk), None, t(linear_head(wl.n, wl.nx, wl.head_drop, 0.0)),
+                                tol=1e-10, maxit=200000)
+    rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), 1.0)
+    phys = E.Physics(rc, rc, wl.head_drop / st.vmax, 0.0, wl.T_inflow, 0)
+    K, Wu = args.steps, args.warmup
+    runs = {}
+    for prec in ("fp32_bulk", "fp64") if not args.no_fp64 else ("fp32_bulk",):
+        m = MisfitModel(3, n, n, n, phys, t(wl.phi), t(wl.lam), wl.dt, wl.steps, t(obs, torch.int64),
+                        t(data), precision=prec, checkpoint=10)
+        lnk0, T00 = t(wl.lnk), t(wl.T0)
+
+        def grad():
+            lnk = lnk0.clone().requires_grad_(True)
+            T0 = T00.clone().requires_grad_(True)
+            L = misfit(lnk, T0, m)
+            L.backward()
+            return L.detach(), lnk.grad, T0.grad
+
+        for _ in range(Wu):
+            grad()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        for _ in range(K):
+            L, gl, gt = grad()
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        terms = sum(s[0] and sum(s[1:]) for s in m.schedules)
+        runs[prec] = {"ms_per_gradient": ms, "L": float(L), "glnk": gl.cpu().numpy(),
+                      "gT0": gt.cpu().numpy(), "leja_terms_per_run": terms}
+        m.close()
+    r = runs["fp32_bulk"]
+    cell_steps = wl.n * wl.steps
+    line = {
+        "metric": "adjoint gradient: forward + checkpointed adjoint Mcell-steps/s (128^3, 60 steps, FP32-bulk)",
+        "value": cell_steps / (r["ms_per_gradient"] / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": Wu, "ms_per_step": r["ms_per_gradient"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"adjoint3d_{n}", "cells": wl.n, "erem_steps": wl.steps,
+                   "observations": int(obs.size), "checkpoint_every": 10, "dt": wl.dt,
+                   "a 'step' here": "one gradient evaluation (forward run + adjoint run)"},
+        "adjoint": {"ms_per_gradient": r["ms_per_gradient"], "misfit": r["L"],
+                    "leja_terms_per_forward": r["leja_terms_per_run"]},
+    }
+    if "fp64" in runs:
+        q = runs["fp64"]
+        line["adjoint"]["fp64_ms_per_gradient"] = q["ms_per_gradient"]
+        line["adjoint"]["rel_l2_glnk_fp32_vs_fp64"] = float(np.linalg.norm(r["glnk"] - q["glnk"]) / np.linalg.norm(q["glnk"]))
+        line["adjoint"]["rel_l2_gT0_fp32_vs_fp64"] = float(np.linalg.norm(r["gT0"] - q["gT0"]) / np.linalg.norm(q["gT0"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse_args()
     if a.impl == "reference":
@@ -770,5 +845,7 @@ if __name__ == "__main__":
         main_coupled(a)
     elif a.workload == "ensemble":
         main_ensemble(a)
+    elif a.workload == "adjoint":
+        main_adjoint(a)
     else:
         main(a)

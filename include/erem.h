@@ -325,6 +325,16 @@ EREM_API erem_status erem_adjoint_step(erem_ctx* ctx, const double* T, double* l
 EREM_API erem_status erem_adjoint_lnk(erem_ctx* ctx, const double* lnk, double* glnk, double tol,
                                       int maxit, erem_stats* stats, void* stream);
 
+/* Hold the Gershgorin interval of J (§4.2, before the factor dt: the interval
+ * of dt J becomes [dt lo, dt hi]) at [lo, hi] for every later step of ctx
+ * instead of bounding it from the assembled J; hold = 0 releases it (lo, hi
+ * ignored).  With the Leja schedules replayed this evaluates exactly the map
+ * that erem_adjoint_step differentiates (interval and degrees frozen at the
+ * forward run's), e.g. for finite-difference checks under perturbed fields.
+ * lo and hi of a forward step are erem_stats.alpha / dt and .beta / dt.
+ * Errors: EINVAL (ctx NULL; lo or hi not finite, or lo > hi). */
+EREM_API erem_status erem_hold_interval(erem_ctx* ctx, int hold, double lo, double hi);
+
 /* Message of the last failing call on ctx ("" if none; a static message if
  * ctx is NULL).  The pointer stays valid until the next call on ctx. */
 EREM_API const char* erem_last_error(const erem_ctx* ctx);

@@ -139,6 +139,7 @@ _sigs = {
                                ctypes.POINTER(erem_krylov_stats), _P]),
     "erem_step_krylov": (_I, [_P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(erem_krylov_opts),
                               ctypes.POINTER(erem_krylov_stats), _P]),
+    "erem_hold_interval": (_I, [_P, _I, _D, _D]),
     "erem_adjoint_begin": (_I, [_P, _P]),
     "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
     "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -363,6 +364,16 @@ def erem_step_krylov(ctx, n, T, dt, p=None, lnk=None, phi=None, lam=None,
     return st
 
 
+def erem_hold_interval(ctx, interval) -> None:
+    """Hold the Gershgorin interval (lo, hi) of J for later steps; None
+    releases it."""
+    if interval is None:
+        _check(ctx, _lib.erem_hold_interval(ctx, 0, 0.0, 0.0))
+    else:
+        lo, hi = interval
+        _check(ctx, _lib.erem_hold_interval(ctx, 1, float(lo), float(hi)))
+
+
 def erem_adjoint_begin(ctx, stream=None) -> None:
     _check(ctx, _lib.erem_adjoint_begin(ctx, _stream(stream)))
 
@@ -514,6 +525,9 @@ class Context:
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):
         return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)
+
+    def hold_interval(self, interval):
+        erem_hold_interval(self._h, interval)
 
     def adjoint_begin(self, stream=None):
         erem_adjoint_begin(self._h, stream)

@@ -9,6 +9,10 @@ forward value; the states T^n are recomputed from checkpoints kept every
 ``checkpoint`` steps by replaying those schedules, so at most ``checkpoint``
 states are held at once.  Gradients with respect to ln K and T0.
 
+The adjoint differentiates the run with the interval of every step held at
+its forward value; ``interval=`` holds it (``MisfitModel.interval`` of a
+forward run) so that perturbed forwards evaluate that same map.
+
 Argument marshalling and step sequencing only: every step runs in the
 library's kernels.
 """
@@ -29,7 +33,7 @@ class MisfitModel:
 
     def __init__(self, dim, nx, ny, nz, physics: Physics, phi, lam, dt, steps, obs, data,
                  precision="fp32_bulk", checkpoint=10, tol=1e-6, pressure_tol=1e-12,
-                 replay=None):
+                 replay=None, interval=None):
         if physics.fluid_model != 0:
             raise ValueError("the adjoint needs fluid_model 0")
         self.ctx = Context(dim, nx, ny, nz, physics=physics, precision=precision)
@@ -43,6 +47,9 @@ class MisfitModel:
         self.tol, self.pressure_tol = tol, pressure_tol
         self.replay = replay          # forced schedules (one per step), or None
         self.schedules = []           # schedules of the last forward run
+        self.interval = None          # Gershgorin interval of J of the last forward run
+        if interval is not None:      # held: the map the adjoint differentiates
+            self.ctx.hold_interval(interval)
 
     def head_guess(self, like):
         x = (torch.arange(self.nx, dtype=torch.float64, device=like.device) + 0.5) / self.nx
@@ -68,6 +75,8 @@ class EremMisfit(torch.autograd.Function):
             opts = leja_opts(tol=m.tol) if m.replay is None else leja_opts(tol=m.tol, replay=m.replay[n])
             st = m.ctx.erem_step(T, m.dt, opts=opts)
             scheds.append(st.schedule)
+            if n == 0:
+                m.interval = (st.alpha / m.dt, st.beta / m.dt)
             if (n + 1) % m.checkpoint == 0 and n + 1 < m.steps:
                 ckpts[n + 1] = T.clone()
         m.schedules = scheds

@@ -125,6 +125,13 @@ erem_status ensure_leja(erem_ctx* c, int M) {
   return EREM_OK;
 }
 
+// [alpha, beta] = dt times the held bounds, else dt times the Gershgorin
+// bounds of the last assembly.
+void set_interval(erem_ctx* c) {
+  c->alpha = c->dt * (c->hold_iv ? c->hold_lo : c->ctrl_h->gmin);
+  c->beta = c->dt * (c->hold_iv ? c->hold_hi : c->ctrl_h->gmax);
+}
+
 void focal_map(erem_ctx* c) {
   c->cfoc = 0.5 * (c->alpha + c->beta);
   double g = 0.25 * (c->beta - c->alpha);
@@ -357,8 +364,7 @@ erem_status assemble(erem_ctx* c, bool faces, bool rhs, cudaStream_t s) {
   EREM_TRY(check_launch(c, "assembly"));
   EREM_TRY(read_ctrl(c, s));
   EREM_TRY(check_flags(c));
-  c->alpha = c->dt * c->ctrl_h->gmin;
-  c->beta = c->dt * c->ctrl_h->gmax;
+  set_interval(c);
   if (!std::isfinite(c->alpha) || !std::isfinite(c->beta))
     return fail(c, EREM_ENONFINITE, "non-finite spectral interval");
   focal_map(c);
@@ -382,6 +388,18 @@ erem_status load_fields(erem_ctx* c, const double* p, const double* lnk, const d
   launch_pack(c, dphi, c->phi, s);
   launch_pack(c, dl, c->lam, s);
   return check_launch(c, "pack fields");
+}
+
+// The Leja copy of J scaled by dt / gamma of the current interval; cached
+// divided differences and the adjoint's transposed copy are stale after it.
+erem_status rescale_jl(erem_ctx* c, cudaStream_t s) {
+  c->jlT_valid = false;
+  launch_scale_jl(c, c->dt / c->gam, s);
+  EREM_TRY(check_launch(c, "scale"));
+  c->jl_valid = true;
+  c->dd_cache.clear();
+  c->dd_tag_S = -1;
+  return EREM_OK;
 }
 
 // Shared front half of erem_step / rosm_step: T^n into the context, fields,
@@ -415,20 +433,12 @@ erem_status prepare_step(erem_ctx* c, double* T, const double* p, const double* 
     if (rhs_here) launch_rhs(c, c->Tn, c->vrhs, 1, s);
     EREM_TRY(check_launch(c, "rhs"));
     if (dt != old_dt) {
-      c->alpha = dt * c->ctrl_h->gmin;
-      c->beta = dt * c->ctrl_h->gmax;
+      set_interval(c);
       focal_map(c);
       c->jl_valid = false;
     }
   }
-  if (need_interval && !c->jl_valid) {
-    c->jlT_valid = false;
-    launch_scale_jl(c, c->dt / c->gam, s);
-    EREM_TRY(check_launch(c, "scale"));
-    c->jl_valid = true;
-    c->dd_cache.clear();
-    c->dd_tag_S = -1;
-  }
+  if (need_interval && !c->jl_valid) EREM_TRY(rescale_jl(c, s));
   return EREM_OK;
 }
 
@@ -1086,6 +1096,22 @@ erem_status erem_step_krylov(erem_ctx* c, double* T, const double* p, const doub
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
   }
+  return EREM_OK;
+}
+
+erem_status erem_hold_interval(erem_ctx* c, int hold, double lo, double hi) {
+  if (!c) return EREM_EINVAL;
+  if (hold && !(std::isfinite(lo) && std::isfinite(hi) && lo <= hi))
+    return fail(c, EREM_EINVAL, "held interval must be finite with lo <= hi");
+  c->hold_iv = hold != 0;
+  c->hold_lo = hold ? lo : 0.0;
+  c->hold_hi = hold ? hi : 0.0;
+  if (!c->have_state) return EREM_OK;
+  // the stored state takes the new interval at once (phi1_apply uses it)
+  set_interval(c);
+  focal_map(c);
+  EREM_TRY(rescale_jl(c, nullptr));
+  EREM_CUDA(c, cudaStreamSynchronize(nullptr));
   return EREM_OK;
 }
 

@@ -224,6 +224,8 @@ struct erem_ctx {
   std::map<int, erem::DDEntry> dd_cache;  // substep count -> table
 
   // state
+  bool hold_iv = false;              // interval held by erem_hold_interval
+  double hold_lo = 0, hold_hi = 0;    // held bounds of J (before the factor dt)
   bool have_state = false;
   bool jl_valid = false;
   double dt = 0, alpha = 0, beta = 0;

@@ -2,7 +2,8 @@
 torch.autograd.Function of ``paper_1209_5553_gb300.autograd``: against the
 oracle's adjoint (oracle/adjoint.py) with the GPU's Leja schedules frozen in
 both, against central finite differences of the GPU forward itself (h =
-1e-4, schedules replayed), and across checkpoint intervals."""
+1e-4, schedules replayed, spectral interval held), and across checkpoint
+intervals."""
 import numpy as np
 import pytest
 
@@ -37,7 +38,7 @@ def _setup(shape, steps, seed=0):
     return case, obs, data, steps
 
 
-def _model(E, case, obs, data, steps, precision, checkpoint=10, replay=None):
+def _model(E, case, obs, data, steps, precision, checkpoint=10, replay=None, interval=None):
     import torch
 
     from paper_1209_5553_gb300.autograd import MisfitModel
@@ -45,7 +46,7 @@ def _model(E, case, obs, data, steps, precision, checkpoint=10, replay=None):
     g = case.grid
     return MisfitModel(g.dim, g.nx, g.ny, g.nz, case.gpu_physics(), _t(case.phi), _t(case.lam),
                        case.dt, steps, _t(obs, torch.int64), _t(data), precision=precision,
-                       checkpoint=checkpoint, replay=replay)
+                       checkpoint=checkpoint, replay=replay, interval=interval)
 
 
 def _grads(E, case, obs, data, steps, precision, checkpoint=10, replay=None):
@@ -58,7 +59,8 @@ def _grads(E, case, obs, data, steps, precision, checkpoint=10, replay=None):
     T0 = _t(case.T0).requires_grad_(True)
     L = misfit(lnk, T0, m)
     L.backward()
-    out = (float(L.detach()), lnk.grad.cpu().numpy(), T0.grad.cpu().numpy(), list(m.schedules))
+    out = (float(L.detach()), lnk.grad.cpu().numpy(), T0.grad.cpu().numpy(), list(m.schedules),
+           m.interval)
     m.close()
     return out
 
@@ -76,7 +78,7 @@ def _oracle(case, obs, data, steps, schedules):
 @pytest.mark.parametrize("shape", [(14, 11), (6, 5, 4)])
 def test_fp64_gradients_match_oracle(E, shape):
     case, obs, data, steps = _setup(shape, 4)
-    L, glnk, gT0, sched = _grads(E, case, obs, data, steps, "fp64")
+    L, glnk, gT0, sched, _ = _grads(E, case, obs, data, steps, "fp64")
     Lo, glnk_o, gT0_o = _oracle(case, obs, data, steps, sched)
     assert abs(L - Lo) < 1e-10 * Lo
     assert C.rel_l2(gT0, gT0_o) < 1e-9
@@ -85,7 +87,7 @@ def test_fp64_gradients_match_oracle(E, shape):
 
 def test_fp32_bulk_gradients_match_oracle(E):
     case, obs, data, steps = _setup((20, 16), 5)
-    L, glnk, gT0, sched = _grads(E, case, obs, data, steps, "fp32_bulk")
+    L, glnk, gT0, sched, _ = _grads(E, case, obs, data, steps, "fp32_bulk")
     Lo, glnk_o, gT0_o = _oracle(case, obs, data, steps, sched)
     assert abs(L - Lo) < 1e-5 * Lo
     assert C.rel_l2(gT0, gT0_o) < 1e-4
@@ -97,9 +99,11 @@ def test_gradients_match_central_differences_of_the_gpu_forward(E):
 
     from paper_1209_5553_gb300.autograd import misfit
 
+    # schedules replayed and the interval held: the map the adjoint
+    # differentiates, to the O(h^2) and rounding of the differences
     case, obs, data, steps = _setup((16, 16), 6)
-    L, glnk, gT0, sched = _grads(E, case, obs, data, steps, "fp64")
-    m = _model(E, case, obs, data, steps, "fp64", replay=sched)
+    L, glnk, gT0, sched, interval = _grads(E, case, obs, data, steps, "fp64")
+    m = _model(E, case, obs, data, steps, "fp64", replay=sched, interval=interval)
     rng = np.random.default_rng(21)
     h = 1e-4
     with torch.no_grad():
@@ -109,8 +113,40 @@ def test_gradients_match_central_differences_of_the_gpu_forward(E):
             Lp = float(misfit(_t(case.lnk + h * dk), _t(case.T0 + h * dT), m))
             Lm = float(misfit(_t(case.lnk - h * dk), _t(case.T0 - h * dT), m))
             fd = (Lp - Lm) / (2 * h)
-            assert abs(fd - (glnk @ dk + gT0 @ dT)) < 1e-5 * max(abs(fd), 1e-3 * L)
+            assert abs(fd - (glnk @ dk + gT0 @ dT)) < 1e-7 * max(abs(fd), 1e-3 * L)
     m.close()
+
+
+def test_held_interval_is_the_forward_interval(E):
+    # (schedule replayed) holding the forward's own interval changes the step
+    # by rounding only; holding another one changes it, and releasing the
+    # hold restores the assembled interval
+    import torch
+
+    case, obs, data, steps = _setup((16, 12), 1)
+    g = case.grid
+    outs = []
+    with E.Context(2, g.nx, g.ny, physics=case.gpu_physics()) as ctx:
+        ctx.set_state(_t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+        st = ctx.erem_step(_t(case.T0), case.dt)
+        lo, hi = st.alpha / case.dt, st.beta / case.dt
+        for iv in (None, (lo, hi), (1.5 * lo, hi), None):
+            ctx.hold_interval(iv)
+            ctx.set_state(_t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
+                          case.dt)
+            T = _t(case.T0)
+            s2 = ctx.erem_step(T, case.dt, opts=E.leja_opts(replay=st.schedule))
+            outs.append(T.cpu().numpy())
+            if iv is not None:
+                assert abs(s2.alpha - case.dt * iv[0]) <= 1e-15 * abs(s2.alpha)
+        for bad in ((1.0, 0.0), (float("nan"), 0.0)):
+            with pytest.raises(E.EremError) as ei:
+                ctx.hold_interval(bad)
+            assert ei.value.status == E.EREM_EINVAL
+    scale = np.max(np.abs(outs[0] - case.T0))
+    assert np.max(np.abs(outs[1] - outs[0])) <= 1e-13 * scale
+    assert np.max(np.abs(outs[2] - outs[0])) > 1e-12 * scale
+    assert np.array_equal(outs[3], outs[0])
 
 
 def test_checkpoint_interval_does_not_change_the_gradients(E):

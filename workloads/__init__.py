@@ -178,3 +178,15 @@ def ensemble_member(e: int, members: int = 512) -> Workload:
     n = int(sizes[e])
     return heat2d(n, float(sigmas[e]), 0.1, SEED_BASE + 4 + 1000 + e, 30, 0.05,
                   name=f"ensemble2d_{e}")
+
+
+def adjoint3d(n: int = 128, seed: int = SEED_BASE + 5, steps: int = 60, n_obs: int = 16):
+    """The adjoint workload: the layered channel reservoir of ``channels3d`` on
+    n^3 cells (its own seed), 60 steps, and n_obs seeded observation cells
+    with synthetic observed temperatures in [20, 80].  Returns (Workload, obs,
+    data)."""
+    wl = channels3d(n, seed=seed, steps=steps)
+    rng = rng_for(seed + 1)
+    obs = np.sort(rng.choice(wl.n, size=n_obs, replace=False))
+    data = rng.uniform(20.0, 80.0, size=n_obs)
+    return wl, obs, data
