@@ -325,6 +325,19 @@ EREM_API erem_status erem_adjoint_step(erem_ctx* ctx, const double* T, double* l
 EREM_API erem_status erem_adjoint_lnk(erem_ctx* ctx, const double* lnk, double* glnk, double tol,
                                       int maxit, erem_stats* stats, void* stream);
 
+/* Preconditioner of the pressure CG (pressure_solve, erem_adjoint_lnk) for
+ * later calls on ctx.  degree 1: Jacobi (diagonal) preconditioning, plain CG
+ * in FP64.  degree 2..64: z = p(D^-1 A) D^-1 r, `degree` steps of Chebyshev
+ * iteration for A z = r on the interval [2/degree^2, 2] (D the diagonal of A,
+ * the spectrum of D^-1 A lies in (0, 2]), applied in FP32; the outer CG stays
+ * FP64 with the Polak-Ribiere beta (flexible CG), so the stopping rule and
+ * accuracy of pressure_solve are unchanged and lin_iters counts outer
+ * iterations.  Default 16.  Needs 8 FP32 vectors [N] (allocated on first use).
+ * The paper's solver is BiCGSTAB with ILU(0) (§3.2.3, §5); both are
+ * preconditioned Krylov methods for the same system.
+ * Errors: EINVAL (ctx NULL, degree outside 1..64). */
+EREM_API erem_status erem_set_pressure_precond(erem_ctx* ctx, int degree);
+
 /* Hold the Gershgorin interval of J (§4.2, before the factor dt: the interval
  * of dt J becomes [dt lo, dt hi]) at [lo, hi] for every later step of ctx
  * instead of bounding it from the assembled J; hold = 0 releases it (lo, hi

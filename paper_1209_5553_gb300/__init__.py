@@ -140,6 +140,7 @@ _sigs = {
     "erem_step_krylov": (_I, [_P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(erem_krylov_opts),
                               ctypes.POINTER(erem_krylov_stats), _P]),
     "erem_hold_interval": (_I, [_P, _I, _D, _D]),
+    "erem_set_pressure_precond": (_I, [_P, _I]),
     "erem_adjoint_begin": (_I, [_P, _P]),
     "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
     "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -374,6 +375,12 @@ def erem_hold_interval(ctx, interval) -> None:
         _check(ctx, _lib.erem_hold_interval(ctx, 1, float(lo), float(hi)))
 
 
+def erem_set_pressure_precond(ctx, degree) -> None:
+    """Pressure CG preconditioner: 1 = Jacobi, 2..64 = FP32 Chebyshev
+    polynomial of that degree (default 16)."""
+    _check(ctx, _lib.erem_set_pressure_precond(ctx, int(degree)))
+
+
 def erem_adjoint_begin(ctx, stream=None) -> None:
     _check(ctx, _lib.erem_adjoint_begin(ctx, _stream(stream)))
 
@@ -525,6 +532,9 @@ class Context:
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):
         return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)
+
+    def set_pressure_precond(self, degree):
+        erem_set_pressure_precond(self._h, degree)
 
     def hold_interval(self, interval):
         erem_hold_interval(self._h, interval)

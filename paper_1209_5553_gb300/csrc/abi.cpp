@@ -110,6 +110,65 @@ erem_status check_flags(erem_ctx* c) {
   return EREM_OK;
 }
 
+erem_status ensure_pc(erem_ctx* c) {
+  if (c->pc[0]) return EREM_OK;
+  for (int k = 0; k < 8; ++k) EREM_TRY(dalloc_t(c, &c->pc[k], (size_t)c->Np));
+  return EREM_OK;
+}
+
+// Chebyshev iteration on [2/deg^2, 2] (the spectrum of D^-1 A lies in
+// (0, 2]; the lower end trades the compression of the upper spectrum against
+// the reach towards 0, deg^2 measured best on the channel reservoirs):
+// theta, delta = centre and half-width, sigma = theta/delta, rho_0 = 1/sigma,
+// rho_j = 1/(2 sigma - rho_{j-1}); step j >= 1 adds rho_j rho_{j-1} times the
+// previous increment and 2 rho_j / delta times the scaled residual.
+PcPoly pc_poly(int deg) {
+  PcPoly P;
+  P.deg = deg;
+  const double hi = 2.0, lo = 2.0 / ((double)deg * deg);
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  P.c2[0] = 1.0 / theta;
+  for (int j = 1; j < deg; ++j) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    P.c1[j] = rn * rho;
+    P.c2[j] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return P;
+}
+
+// CG on the pressure system whose matrix and right-hand side the caller has
+// assembled into kv (initial guess in kv[0]): Jacobi-preconditioned for
+// pc_deg = 1, else flexible CG with the FP32 polynomial preconditioner.
+erem_status run_pressure_cg(erem_ctx* c, double tol, int maxit, cudaStream_t s) {
+  const bool poly = c->pc_deg > 1;
+  PcPoly P;
+  launch_cg_init(c, tol, s);
+  if (poly) {
+    EREM_TRY(ensure_pc(c));
+    P = pc_poly(c->pc_deg);
+    launch_pc_setup(c, s);
+    launch_pc_apply(c, P, s);
+  }
+  EREM_TRY(check_launch(c, "pressure CG set-up"));
+  EREM_TRY(read_ctrl(c, s));
+  EREM_TRY(check_flags(c));
+  const int chunk = poly ? std::max(2, 64 / c->pc_deg) : 32;
+  int k = 0;
+  while (!c->ctrl_h->lin_done && k < maxit) {
+    const int n = std::min(chunk, maxit - k);
+    for (int j = 0; j < n; ++j) {
+      if (poly) launch_pcg_iter(c, P, k + j, s);
+      else launch_cg_iter(c, k + j, s);
+    }
+    EREM_TRY(check_launch(c, "cg"));
+    k += n;
+    EREM_TRY(read_ctrl(c, s));
+  }
+  return EREM_OK;
+}
+
 erem_status ensure_leja(erem_ctx* c, int M) {
   if (M <= c->xi_cap) return EREM_OK;
   if (M > kMaxTerms) return fail(c, EREM_EINVAL, "m_max above " + std::to_string(kMaxTerms));
@@ -845,6 +904,8 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (double* p : c->adj_w)
     if (p) cudaFree(p);
+  for (float* p : c->pc)
+    if (p) cudaFree(p);
   if (c->kr_host) cudaFreeHost(c->kr_host);
   if (c->red_cnt) cudaFree(c->red_cnt);
   if (c->qmid) cudaFree(c->qmid);
@@ -887,18 +948,7 @@ erem_status pressure_solve(erem_ctx* c, const double* lnk, const double* T, doub
   EREM_TRY(resolve(c, 7, p, true, s, &dp));
   launch_pres_faces(c, dk, dT, s);
   launch_pack(c, dp, c->kv[0], s);
-  launch_cg_init(c, tol, s);
-  EREM_TRY(check_launch(c, "pressure set-up"));
-  EREM_TRY(read_ctrl(c, s));
-  EREM_TRY(check_flags(c));
-  int k = 0;
-  while (!c->ctrl_h->lin_done && k < maxit) {
-    const int n = std::min(32, maxit - k);
-    for (int j = 0; j < n; ++j) launch_cg_iter(c, k + j, s);
-    EREM_TRY(check_launch(c, "cg"));
-    k += n;
-    EREM_TRY(read_ctrl(c, s));
-  }
+  EREM_TRY(run_pressure_cg(c, tol, maxit, s));
   const Ctrl h = *c->ctrl_h;
   const double resid = h.lin[K_BB] > 0 ? std::sqrt(h.lin[K_RR] / h.lin[K_BB]) : 0.0;
   launch_finish(c, dp, c->kv[0], nullptr, c->kv[0], 0.0, s);
@@ -1099,6 +1149,14 @@ erem_status erem_step_krylov(erem_ctx* c, double* T, const double* p, const doub
   return EREM_OK;
 }
 
+erem_status erem_set_pressure_precond(erem_ctx* c, int degree) {
+  if (!c) return EREM_EINVAL;
+  if (degree < 1 || degree > kMaxPcDeg)
+    return fail(c, EREM_EINVAL, "preconditioner degree must be in 1.." + std::to_string(kMaxPcDeg));
+  c->pc_deg = degree;
+  return EREM_OK;
+}
+
 erem_status erem_hold_interval(erem_ctx* c, int hold, double lo, double hi) {
   if (!c) return EREM_EINVAL;
   if (hold && !(std::isfinite(lo) && std::isfinite(hi) && lo <= hi))
@@ -1228,17 +1286,8 @@ erem_status erem_adjoint_lnk(erem_ctx* c, const double* lnk, double* glnk, doubl
   EREM_TRY(resolve(c, 5, lnk, true, s, &dk));
   launch_pres_faces(c, dk, nullptr, s);
   launch_adj_dLdp(c, s);
-  launch_cg_init(c, tol, s);
   EREM_TRY(check_launch(c, "adjoint pressure set-up"));
-  EREM_TRY(read_ctrl(c, s));
-  int it = 0;
-  while (!c->ctrl_h->lin_done && it < maxit) {
-    const int n = std::min(32, maxit - it);
-    for (int j = 0; j < n; ++j) launch_cg_iter(c, it + j, s);
-    EREM_TRY(check_launch(c, "adjoint cg"));
-    it += n;
-    EREM_TRY(read_ctrl(c, s));
-  }
+  EREM_TRY(run_pressure_cg(c, tol, maxit, s));
   const Ctrl h = *c->ctrl_h;
   EREM_TRY(resolve(c, 6, glnk, false, s, &dout));
   launch_adj_lnk(c, dout, s);

@@ -15,6 +15,8 @@ namespace erem {
 
 constexpr int kThreads = 256;      // threads per block of every kernel
 constexpr int kMaxTerms = 4096;    // largest Leja degree a context accepts
+constexpr int kMaxPcDeg = 64;      // largest degree of the pressure CG's polynomial preconditioner
+constexpr int kDefaultPcDeg = 16;  // its default (1 = plain Jacobi CG)
 constexpr int kRedSlots = 4;       // reduction values per block
 
 // Bits of Ctrl::flags raised by the set-up kernels.
@@ -191,6 +193,10 @@ struct erem_ctx {
   double* wave_spart = nullptr;     // per-slice norm partials (A then B)
   // linear solvers (allocated on first use)
   double* kv[12] = {};
+  // pressure CG polynomial preconditioner: degree (1 = Jacobi), FP32 arrays
+  // dinv, Ux, Uy, Uz, r and three z buffers (allocated on first use)
+  int pc_deg = erem::kDefaultPcDeg;
+  float* pc[8] = {};
   // staging for host pointers (allocated on first use)
   double* stage[8] = {};
   // Krylov basis and work vectors (allocated on first use)
@@ -279,6 +285,16 @@ void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, d
 void launch_pres_faces(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s);
 void launch_cg_init(const erem_ctx* c, double tol, cudaStream_t s);
 void launch_cg_iter(const erem_ctx* c, int k, cudaStream_t s);
+// Chebyshev coefficients of the pressure CG's polynomial preconditioner:
+// sweep j computes z_{j+1} = z_j + c1[j] (z_j - z_{j-1}) + c2[j] (D^-1 (r - A z_j))
+// (sweep 0: z_1 = c2[0] D^-1 r)
+struct PcPoly {
+  int deg = 0;
+  double c1[kMaxPcDeg] = {}, c2[kMaxPcDeg] = {};
+};
+void launch_pc_setup(const erem_ctx* c, cudaStream_t s);
+void launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s);
+void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, int k, cudaStream_t s);
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s);
 
 // stage solver (BiCGSTAB) for (sigma I - J) x = b

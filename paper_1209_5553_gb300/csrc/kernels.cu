@@ -1347,9 +1347,12 @@ __global__ void k_cg_init(PresArr a, Geo g, double tol, double* part, unsigned* 
   }
 }
 
-// d_new = z + beta d_old; Ad = A d_new; (d, Ad) -> alpha
-__global__ void k_cg_dir(PresArr a, const double* __restrict__ dold, double* __restrict__ dnew,
-                         Geo g, double* part, unsigned* cnt, Ctrl* ctrl) {
+// d_new = z + beta d_old; Ad = A d_new; (d, Ad) -> alpha.  z is the
+// preconditioned residual: FP64 (Jacobi) or FP32 (polynomial preconditioner).
+template <typename Tz>
+__global__ void k_cg_dir(PresArr a, const Tz* __restrict__ z, const double* __restrict__ dold,
+                         double* __restrict__ dnew, Geo g, double* part, unsigned* cnt,
+                         Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (*(volatile int*)&ctrl->lin_done) return;
   const double beta = ctrl->lin[K_BETA];
@@ -1357,7 +1360,7 @@ __global__ void k_cg_dir(PresArr a, const double* __restrict__ dold, double* __r
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
-    auto dn = [&](int j) { return a.z[j] + beta * dold[j]; };
+    auto dn = [&](int j) { return (double)z[j] + beta * dold[j]; };
     const double di = dn(ip);
     double v = a.diag[ip] * di;
     if (ix < g.nx - 1) v -= a.Ux[ip] * dn(ip + 1);
@@ -1416,6 +1419,121 @@ __global__ void k_cg_upd(PresArr a, const double* __restrict__ d, Geo g, double*
       ctrl->lin_it += 1;
       ctrl->lin[K_BETA] = s0 / ctrl->lin[K_RZ];
       ctrl->lin[K_RZ] = s0;
+      ctrl->lin[K_RR] = s1;
+      if (s1 <= ctrl->lin[K_TOL2]) ctrl->lin_done = 1;
+      if (!isfinite(s1)) { ctrl->lin_break = 1; ctrl->lin_done = 1; }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Polynomial preconditioner for the pressure CG.  z = p(D^-1 A) D^-1 r is
+// `deg` steps of Chebyshev iteration for A z = r from z = 0 on the interval
+// [2/ratio, 2] that contains the spectrum of D^-1 A above its low end (D the
+// diagonal; the Gershgorin discs of D^-1 A lie in [0, 2]), so p(A) A has its
+// spectrum compressed towards 1 and the outer CG needs about deg times fewer
+// iterations.  The sweeps are stencil passes in FP32 (z, the residual copy and
+// the matrix coefficients), bound by HBM; the outer CG stays FP64 and, since
+// an FP32 polynomial is a fixed linear map only up to rounding, takes the
+// Polak-Ribiere beta = z_new.(r_new - r_old) / (z_old.r_old), with
+// r_new - r_old = -alpha A d, which is robust to it.
+// ---------------------------------------------------------------------------
+struct PcArr {
+  float *dinv, *Ux, *Uy, *Uz, *r;
+};
+
+// FP32 coefficients: 1/diag and the face couplings
+__global__ void k_pc_setup(PresArr a, PcArr p, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    p.dinv[ip] = (float)(1.0 / a.diag[ip]);
+    p.Ux[ip] = (float)a.Ux[ip];
+    p.Uy[ip] = (float)a.Uy[ip];
+    if (g.dim == 3) p.Uz[ip] = (float)a.Uz[ip];
+  }
+}
+
+// One Chebyshev step.  FIRST: z_1 = D^-1 r / theta (c2 = 1/theta) and the
+// FP32 copy of r.  Otherwise z_{j+1} = z_j + c1 (z_j - z_{j-1})
+// + c2 (D^-1 (r + N z_j) - z_j), A = D - N.  LAST: also (z, r) and (z, A d)
+// -> beta (zero on the first pass after the set-up) and (z, r) for alpha.
+template <bool FIRST, bool LAST>
+__global__ void k_pc_sweep(PresArr a, PcArr p, const float* __restrict__ zprev,
+                           const float* __restrict__ zcur, float* __restrict__ znew, float c1,
+                           float c2, Geo g, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  double rz = 0.0, zad = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    float zn;
+    if (FIRST) {
+      const float r32 = (float)a.r[ip];
+      if (!LAST) p.r[ip] = r32;
+      zn = c2 * (p.dinv[ip] * r32);
+    } else {
+      const float zc = zcur[ip];
+      const float zp = zprev ? zprev[ip] : 0.0f;   // z_0 = 0
+      float s = p.r[ip];
+      if (ix < g.nx - 1) s = fmaf(p.Ux[ip], zcur[ip + 1], s);
+      if (ix > 0) s = fmaf(p.Ux[ip - 1], zcur[ip - 1], s);
+      if (iy < g.ny - 1) s = fmaf(p.Uy[ip], zcur[ip + g.px], s);
+      if (iy > 0) s = fmaf(p.Uy[ip - g.px], zcur[ip - g.px], s);
+      if (g.dim == 3) {
+        if (iz < g.nz - 1) s = fmaf(p.Uz[ip], zcur[ip + g.plane], s);
+        if (iz > 0) s = fmaf(p.Uz[ip - g.plane], zcur[ip - g.plane], s);
+      }
+      zn = zc + c1 * (zc - zp) + c2 * fmaf(p.dinv[ip], s, -zc);
+    }
+    znew[ip] = zn;
+    if (LAST) {
+      rz += (double)zn * a.r[ip];
+      zad += (double)zn * a.Ad[ip];
+    }
+  }
+  if (!LAST) return;
+  double vals[2] = {block_reduce<0>(rz, sh), 0.0};
+  vals[1] = block_reduce<0>(zad, sh);
+  if (publish_partials(part, cnt, vals, 2)) {
+    const double s0 = gather_partials<0>(part, 0, sh);
+    const double s1 = gather_partials<0>(part, 1, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      const double beta = ctrl->lin_it == 0 ? 0.0 : -ctrl->lin[K_ALPHA] * s1 / ctrl->lin[K_RZ];
+      ctrl->lin[K_BETA] = beta;
+      ctrl->lin[K_RZ] = s0;
+      if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(beta)) {
+        ctrl->lin_break = 1;
+        ctrl->lin_done = 1;
+      }
+    }
+  }
+}
+
+// x += alpha d, r -= alpha Ad; rr -> convergence (the preconditioner's
+// sweeps follow and give z and beta)
+__global__ void k_pcg_upd(PresArr a, const double* __restrict__ d, Geo g, double* part,
+                          unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double alpha = ctrl->lin[K_ALPHA];
+  double rr = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    a.x[ip] += alpha * d[ip];
+    const double r = a.r[ip] - alpha * a.Ad[ip];
+    a.r[ip] = r;
+    rr += r * r;
+  }
+  double vals[1] = {block_reduce<0>(rr, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s1 = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin_it += 1;
       ctrl->lin[K_RR] = s1;
       if (s1 <= ctrl->lin[K_TOL2]) ctrl->lin_done = 1;
       if (!isfinite(s1)) { ctrl->lin_break = 1; ctrl->lin_done = 1; }
@@ -1991,9 +2109,64 @@ void launch_cg_iter(const erem_ctx* c, int k, cudaStream_t s) {
   double* dnew = (k & 1) ? a.d0 : a.d1;
   const int nb = blocks_cells(c);
   ++c->launches;
-  k_cg_dir<<<nb, NT, 0, s>>>(a, dold, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+  k_cg_dir<double><<<nb, NT, 0, s>>>(a, a.z, dold, dnew, geo_of(c), c->red_part, c->red_cnt,
+                                     c->ctrl);
   ++c->launches;
   k_cg_upd<<<nb, NT, 0, s>>>(a, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+}
+
+namespace {
+PcArr pc_arr(const erem_ctx* c) {
+  return PcArr{c->pc[0], c->pc[1], c->pc[2], c->pc[3], c->pc[4]};
+}
+}  // namespace
+
+// FP32 coefficients, and A d = 0 so that the first (z, A d) is defined
+void launch_pc_setup(const erem_ctx* c, cudaStream_t s) {
+  ++c->launches;
+  k_pc_setup<<<blocks_cells(c), NT, 0, s>>>(pres_arr(c), pc_arr(c), geo_of(c));
+  cudaMemsetAsync(pres_arr(c).Ad, 0, sizeof(double) * c->Np, s);
+}
+
+// The preconditioner's deg sweeps; z ends in pc[5 + (deg - 1) % 3].
+void launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s) {
+  const PresArr a = pres_arr(c);
+  const PcArr p = pc_arr(c);
+  const int nb = blocks_cells(c);
+  float* const* zb = &c->pc[5];
+  for (int j = 0; j < poly.deg; ++j) {
+    const bool last = j == poly.deg - 1;
+    float* zn = zb[j % 3];
+    const float* zc = zb[(j + 2) % 3];
+    const float* zp = j >= 2 ? zb[(j + 1) % 3] : nullptr;
+    const float c1 = (float)poly.c1[j], c2 = (float)poly.c2[j];
+    ++c->launches;
+    if (j == 0 && last)
+      k_pc_sweep<true, true><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, c1, c2, geo_of(c), c->red_part,
+                                                c->red_cnt, c->ctrl);
+    else if (j == 0)
+      k_pc_sweep<true, false><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, c1, c2, geo_of(c), c->red_part,
+                                                 c->red_cnt, c->ctrl);
+    else if (last)
+      k_pc_sweep<false, true><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, c1, c2, geo_of(c), c->red_part,
+                                                 c->red_cnt, c->ctrl);
+    else
+      k_pc_sweep<false, false><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, c1, c2, geo_of(c), c->red_part,
+                                                  c->red_cnt, c->ctrl);
+  }
+}
+
+void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, int k, cudaStream_t s) {
+  PresArr a = pres_arr(c);
+  const double* dold = (k & 1) ? a.d1 : a.d0;
+  double* dnew = (k & 1) ? a.d0 : a.d1;
+  const float* z = c->pc[5 + (poly.deg - 1) % 3];
+  const int nb = blocks_cells(c);
+  ++c->launches;
+  k_cg_dir<float><<<nb, NT, 0, s>>>(a, z, dold, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_pcg_upd<<<nb, NT, 0, s>>>(a, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+  launch_pc_apply(c, poly, s);
 }
 
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {

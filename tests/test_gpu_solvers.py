@@ -1,5 +1,6 @@
 """GPU parity of the solvers beside the Leja path: the pressure solve
-(Jacobi CG, FP64) and the Rosenbrock-type steps ROSM(1), ROSM(1/2) and
+(FP64 CG, Jacobi or with the FP32 Chebyshev polynomial preconditioner) and
+the Rosenbrock-type steps ROSM(1), ROSM(1/2) and
 ROS2(1) (Jacobi BiCGSTAB stage solves, FP64), against the oracle's direct
 solves; plus the error paths of the C ABI.
 
@@ -41,8 +42,9 @@ def pressure_error_bound(A, b, p, tol):
     return 10.0 * tol * np.linalg.norm(b) / smin / np.linalg.norm(p)
 
 
+@pytest.mark.parametrize("deg", [1, 16])
 @pytest.mark.parametrize("dim,nx,ny,nz,fm", [(2, 32, 24, 1, 0), (2, 33, 17, 1, 1), (3, 10, 9, 7, 0)])
-def test_pressure_solve_matches_direct_solution(E, dim, nx, ny, nz, fm):
+def test_pressure_solve_matches_direct_solution(E, dim, nx, ny, nz, fm, deg):
     rng = np.random.default_rng(nx + ny)
     g = fv.Grid(dim, nx, ny, nz)
     ph = fv.Physics(head_left=1.3, head_right=-0.2, fluid_model=fm)
@@ -52,6 +54,7 @@ def test_pressure_solve_matches_direct_solution(E, dim, nx, ny, nz, fm):
     p_ref = ts.pressure_solve_direct(g, ph, lnk, T)
     p0 = fv.linear_head_guess(g, ph)
     with E.Context(dim, nx, ny, nz, physics=E.Physics(1, 1, 1.3, -0.2, 80.0, fm)) as ctx:
+        ctx.set_pressure_precond(deg)
         p = _t(p0)
         st = ctx.pressure_solve(_t(lnk), _t(T) if fm else None, p, tol=PRESSURE_TOL, maxit=20000)
         got = p.cpu().numpy()
@@ -67,6 +70,36 @@ def test_pressure_solve_matches_direct_solution(E, dim, nx, ny, nz, fm):
                np.abs(vz).max() / a[2] if vz is not None else 0.0)
     assert st.vmax == pytest.approx(vmax, rel=1e-8)
     assert width > 0
+
+
+def test_polynomial_preconditioner_cuts_the_iterations(E):
+    # a heterogeneous 3D field (sigma 2): every degree reaches the direct
+    # solution within the residual bound; the outer iterations fall roughly
+    # in proportion to the degree (at least by degree / 3 up to 16; on this
+    # small grid the count levels off near 14 beyond that)
+    rng = np.random.default_rng(5)
+    g = fv.Grid(3, 24, 20, 16)
+    ph = fv.Physics(head_left=1.0, head_right=0.0, fluid_model=0)
+    lnk = rng.normal(0, 2.0, g.n)
+    A, b = fv.pressure_system(g, ph, lnk, None)
+    p_ref = ts.pressure_solve_direct(g, ph, lnk, None)
+    bound = pressure_error_bound(A, b, p_ref, PRESSURE_TOL)
+    iters = {}
+    with E.Context(3, g.nx, g.ny, g.nz, physics=E.Physics(1, 1, 1.0, 0.0, 80.0, 0)) as ctx:
+        for deg in (1, 2, 5, 16, 64):
+            ctx.set_pressure_precond(deg)
+            p = _t(np.zeros(g.n))
+            st = ctx.pressure_solve(_t(lnk), None, p, tol=PRESSURE_TOL, maxit=20000)
+            err = np.linalg.norm(p.cpu().numpy() - p_ref) / np.linalg.norm(p_ref)
+            assert st.lin_resid <= PRESSURE_TOL and err <= bound, (deg, err, bound)
+            iters[deg] = st.lin_iters
+        for bad in (0, 65):
+            with pytest.raises(E.EremError) as ei:
+                ctx.set_pressure_precond(bad)
+            assert ei.value.status == E.EREM_EINVAL
+    for deg in (2, 5, 16):
+        assert iters[deg] * deg / 3 <= iters[1], iters
+    assert iters[64] <= iters[16], iters
 
 
 def test_pressure_solve_host_pointers_and_maxit(E):
