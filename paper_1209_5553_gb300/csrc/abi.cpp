@@ -735,6 +735,15 @@ erem_status ensure_adj(erem_ctx* c, int M, int S) {
     EREM_TRY(dalloc_t(c, &c->adj_gy, np));
     if (c->dim == 3) EREM_TRY(dalloc_t(c, &c->adj_gz, np));
     EREM_TRY(dalloc_t(c, &c->adj_g0, (size_t)c->ny * c->nz));
+    if (c->prec == EREM_FP32_BULK) {
+      EREM_TRY(dalloc_t(c, &c->adj_up, np));
+      EREM_TRY(dalloc_t(c, &c->adj_icap32, np));
+      EREM_TRY(dalloc_t(c, &c->adj_mu32, np));
+      for (int k = 0; k < (c->dim == 3 ? 3 : 2); ++k) {
+        EREM_TRY(dalloc_t(c, &c->adj_g32[k], np));
+        EREM_CUDA(c, cudaMemset(c->adj_g32[k], 0, np * sizeof(float)));
+      }
+    }
   }
   if (M > c->adj_store_cap) {
     if (c->adj_store) cudaFree(c->adj_store);
@@ -757,6 +766,8 @@ erem_status adj_clear_faces(erem_ctx* c, cudaStream_t s) {
   EREM_CUDA(c, cudaMemsetAsync(c->adj_gy, 0, np * sizeof(double), s));
   if (c->adj_gz) EREM_CUDA(c, cudaMemsetAsync(c->adj_gz, 0, np * sizeof(double), s));
   EREM_CUDA(c, cudaMemsetAsync(c->adj_g0, 0, (size_t)c->ny * c->nz * sizeof(double), s));
+  for (float* g : c->adj_g32)
+    if (g) EREM_CUDA(c, cudaMemsetAsync(g, 0, np * sizeof(float), s));
   return EREM_OK;
 }
 
@@ -903,6 +914,10 @@ erem_status erem_destroy(erem_ctx* c) {
   for (void* p : adj)
     if (p) cudaFree(p);
   for (double* p : c->adj_w)
+    if (p) cudaFree(p);
+  void* adj32[] = {c->adj_up, c->adj_icap32, c->adj_mu32, c->adj_g32[0], c->adj_g32[1],
+                   c->adj_g32[2]};
+  for (void* p : adj32)
     if (p) cudaFree(p);
   for (float* p : c->pc)
     if (p) cudaFree(p);
@@ -1198,6 +1213,7 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
   EREM_TRY(ensure_adj(c, M, S));
   if (!c->jlT_valid) {
     launch_adj_scale_jlT(c, c->dt / c->gam, s);
+    if (c->prec == EREM_FP32_BULK) launch_adj_aux32(c, s);
     c->jlT_valid = true;
   }
   double *Td, *lamd;
@@ -1263,6 +1279,7 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
     if (k > 0) launch_adj_face_pair(c, c->adj_z, c->adj_w[k], 1.0, s);
     launch_adj_jT_apply(c, c->adj_z, c->adj_mu, c->adj_mu, s);
   }
+  if (c->prec == EREM_FP32_BULK) launch_adj_flush32(c, s);
   launch_adj_face_pair(c, c->adj_G, c->Tn, 1.0, s);
   launch_adj_b_use(c, c->adj_G, s);
   launch_adj_jT_apply(c, c->adj_G, c->adj_lam, c->adj_lam, s);

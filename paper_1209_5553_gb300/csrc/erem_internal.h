@@ -212,6 +212,12 @@ struct erem_ctx {
   bool jlT_valid = false;
   void* adj_store = nullptr;        // forward Newton vectors q_0..q_{m-1} of one substep
   int adj_store_cap = 0;            // vectors adj_store holds
+  // FP32-bulk Horner pass: upwind flags, FP32 capacities, FP32 mu, FP32 face
+  // sums of the current adjoint step
+  unsigned char* adj_up = nullptr;
+  float* adj_icap32 = nullptr;
+  float* adj_mu32 = nullptr;
+  float* adj_g32[3] = {};
   void* adj_s[2] = {};              // Horner values (Leja precision)
   double *adj_mu = nullptr, *adj_z = nullptr, *adj_G = nullptr, *adj_lam = nullptr;
   std::vector<double*> adj_w;       // w_k of the substeps of one step
@@ -330,6 +336,8 @@ void launch_adj_jT_apply(const erem_ctx* c, const double* x, const double* a, do
 void launch_adj_face_pair(const erem_ctx* c, const double* y, const double* x, double scale,
                           cudaStream_t s);
 void launch_adj_start(const erem_ctx* c, const double* mu, double d, void* sbuf, cudaStream_t s);
+void launch_adj_aux32(const erem_ctx* c, cudaStream_t s);
+void launch_adj_flush32(const erem_ctx* c, cudaStream_t s);
 void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const double* mu,
                        const void* q, double dj, double shift, double scale, int faces,
                        cudaStream_t s);

@@ -1172,6 +1172,105 @@ __global__ void k_adj_horner(const Tq* __restrict__ s_in, Tq* __restrict__ s_out
   }
 }
 
+// FP32-bulk form of the Horner pass.  The face derivative of a use of J
+// needs, per face, only the upwind side (one bit per face, from the signs of
+// the face fluxes), the capacities and the two vectors; it is accumulated in
+// FP32 over one adjoint step and flushed into the FP64 sums at its end.  With
+// mu, the capacities and the accumulators in FP32 the pass moves s in/out,
+// the transposed coefficients, mu, q_j, one flag byte, the capacity and the
+// three accumulators (73 B per cell in 3D) and does no FP64 arithmetic away
+// from the x = 0 column.
+struct AdjFaces32 {
+  const unsigned char* up;   // bit 0/1/2: F_x/F_y/F_z >= 0; bit 3: x = 0 face not inflowing
+  const float* icap;
+  float *gx, *gy, *gz;
+  double* g0;
+};
+
+__global__ void k_adj_aux32(const double* __restrict__ Fx, const double* __restrict__ Fy,
+                            const double* __restrict__ Fz, const double* __restrict__ F0,
+                            const double* __restrict__ icap, unsigned char* __restrict__ up,
+                            float* __restrict__ icap32, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    unsigned fl = 0;
+    if (ix < g.nx - 1 && Fx[ip] >= 0.0) fl |= 1u;
+    if (iy < g.ny - 1 && Fy[ip] >= 0.0) fl |= 2u;
+    if (g.dim == 3 && iz < g.nz - 1 && Fz[ip] >= 0.0) fl |= 4u;
+    if (ix == 0 && !(F0[iy + g.ny * iz] > 0.0)) fl |= 8u;
+    up[ip] = (unsigned char)fl;
+    icap32[ip] = (float)icap[ip];
+  }
+}
+
+template <int T_TILE>
+__global__ void k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
+                               const float* __restrict__ mu, const float* __restrict__ q,
+                               const float* __restrict__ jlT, int nc, float dj, float shift,
+                               float scale, AdjFaces32 f, Geo g) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const size_t base = (size_t)(ip / T_TILE) * nc * T_TILE + (ip % T_TILE);
+    auto cf = [&](int k) { return jlT[base + (size_t)k * T_TILE]; };
+    const float sc = s_in[ip];
+    float a = (cf(0) - shift) * sc;
+    if (ix > 0) a = fmaf(cf(1), s_in[ip - 1], a);
+    if (ix < g.nx - 1) a = fmaf(cf(2), s_in[ip + 1], a);
+    if (iy > 0) a = fmaf(cf(3), s_in[ip - g.px], a);
+    if (iy < g.ny - 1) a = fmaf(cf(4), s_in[ip + g.px], a);
+    if (g.dim == 3) {
+      if (iz > 0) a = fmaf(cf(5), s_in[ip - g.plane], a);
+      if (iz < g.nz - 1) a = fmaf(cf(6), s_in[ip + g.plane], a);
+    }
+    s_out[ip] = fmaf(dj, mu[ip], a);
+    const float yc = sc * f.icap[ip];
+    const float xc = q[ip];
+    const unsigned fl = f.up[ip];
+    if (ix < g.nx - 1) {
+      const float xu = (fl & 1u) ? xc : q[ip + 1];
+      f.gx[ip] += scale * (fmaf(s_in[ip + 1], f.icap[ip + 1], -yc) * xu);
+    } else {
+      f.gx[ip] -= scale * (yc * xc);
+    }
+    if (iy < g.ny - 1) {
+      const float xu = (fl & 2u) ? xc : q[ip + g.px];
+      f.gy[ip] += scale * (fmaf(s_in[ip + g.px], f.icap[ip + g.px], -yc) * xu);
+    }
+    if (g.dim == 3 && iz < g.nz - 1) {
+      const float xu = (fl & 4u) ? xc : q[ip + g.plane];
+      f.gz[ip] += scale * (fmaf(s_in[ip + g.plane], f.icap[ip + g.plane], -yc) * xu);
+    }
+    if (ix == 0 && (fl & 8u)) f.g0[iy + g.ny * iz] += (double)(scale * (yc * xc));
+  }
+}
+
+// the FP64 face sums += the FP32 ones of this adjoint step; FP32 sums = 0
+__global__ void k_adj_flush32(float* __restrict__ gx32, float* __restrict__ gy32,
+                              float* __restrict__ gz32, double* __restrict__ gx,
+                              double* __restrict__ gy, double* __restrict__ gz, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
+    gx[i] += (double)gx32[i];
+    gx32[i] = 0.0f;
+    gy[i] += (double)gy32[i];
+    gy32[i] = 0.0f;
+    if (gz32) {
+      gz[i] += (double)gz32[i];
+      gz32[i] = 0.0f;
+    }
+  }
+}
+
+// s = d mu in FP32 and the FP32 copy of mu
+__global__ void k_adj_start32(const double* __restrict__ mu, double d, float* __restrict__ s,
+                              float* __restrict__ mu32, int Np) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
+    s[i] = (float)(d * mu[i]);
+    mu32[i] = (float)mu[i];
+  }
+}
+
 // z = delta s (FP64); zacc += z
 template <typename Tq>
 __global__ void k_adj_z(const Tq* __restrict__ s, double delta, double* __restrict__ z,
@@ -2344,7 +2443,7 @@ void launch_adj_face_pair(const erem_ctx* c, const double* y, const double* x, d
 void launch_adj_start(const erem_ctx* c, const double* mu, double d, void* sbuf, cudaStream_t s) {
   ++c->launches;
   if (c->prec == EREM_FP32_BULK)
-    k_adj_start<float><<<blocks_padded(c), NT, 0, s>>>(mu, d, (float*)sbuf, (int)c->Np);
+    k_adj_start32<<<blocks_padded(c), NT, 0, s>>>(mu, d, (float*)sbuf, c->adj_mu32, (int)c->Np);
   else
     k_adj_start<double><<<blocks_padded(c), NT, 0, s>>>(mu, d, (double*)sbuf, (int)c->Np);
 }
@@ -2354,16 +2453,32 @@ void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const d
                        cudaStream_t s) {
   const int nc = c->dim == 3 ? 7 : 5;
   ++c->launches;
-  if (c->prec == EREM_FP32_BULK)
-    k_adj_horner<float><<<blocks_cells(c), NT, 0, s>>>((const float*)s_in, (float*)s_out, mu,
-                                                       (const float*)q, (const float*)c->jlT_all, 128,
-                                                       nc, dj, shift, scale, faces, adj_faces(c),
-                                                       geo_of(c));
-  else
+  if (c->prec == EREM_FP32_BULK) {
+    // mu is taken from its FP32 copy (written with the first Horner value)
+    (void)mu;
+    (void)faces;
+    const AdjFaces32 f{c->adj_up, c->adj_icap32, c->adj_g32[0], c->adj_g32[1], c->adj_g32[2],
+                       c->adj_g0};
+    k_adj_horner32<128><<<blocks_cells(c), NT, 0, s>>>(
+        (const float*)s_in, (float*)s_out, c->adj_mu32, (const float*)q, (const float*)c->jlT_all,
+        nc, (float)dj, (float)shift, (float)scale, f, geo_of(c));
+  } else
     k_adj_horner<double><<<blocks_cells(c), NT, 0, s>>>((const double*)s_in, (double*)s_out, mu,
                                                         (const double*)q, (const double*)c->jlT_all,
                                                         64, nc, dj, shift, scale, faces, adj_faces(c),
                                                         geo_of(c));
+}
+
+void launch_adj_aux32(const erem_ctx* c, cudaStream_t s) {
+  ++c->launches;
+  k_adj_aux32<<<blocks_cells(c), NT, 0, s>>>(c->Fx, c->Fy, c->Fz, c->F0, c->icap, c->adj_up,
+                                             c->adj_icap32, geo_of(c));
+}
+
+void launch_adj_flush32(const erem_ctx* c, cudaStream_t s) {
+  ++c->launches;
+  k_adj_flush32<<<blocks_padded(c), NT, 0, s>>>(c->adj_g32[0], c->adj_g32[1], c->adj_g32[2],
+                                                c->adj_gx, c->adj_gy, c->adj_gz, (int)c->Np);
 }
 
 void launch_adj_z(const erem_ctx* c, const void* sbuf, double delta, double* z, double* zacc,
