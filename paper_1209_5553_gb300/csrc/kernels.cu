@@ -1204,45 +1204,129 @@ __global__ void k_adj_aux32(const double* __restrict__ Fx, const double* __restr
   }
 }
 
+// Four consecutive cells of one padded row per thread (px is a multiple of
+// 4, so every row starts on a 16-byte boundary): float4 loads of the vectors,
+// coefficients, capacities and face sums, scalar loads only for the x
+// neighbours beyond the four.  Pad lanes (ix >= nx) compute nothing and store 0.
+struct Row4 {
+  int ip0, ix0, iy, iz;
+};
+__device__ __forceinline__ Row4 row4_of(int v, const Geo& g) {
+  Row4 r;
+  r.ip0 = 4 * v;
+  const int row = r.ip0 / g.px;
+  r.ix0 = r.ip0 - row * g.px;
+  r.iy = row % g.ny;
+  r.iz = row / g.ny;
+  return r;
+}
+
 template <int T_TILE>
 __global__ void k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
                                const float* __restrict__ mu, const float* __restrict__ q,
                                const float* __restrict__ jlT, int nc, float dj, float shift,
                                float scale, AdjFaces32 f, Geo g) {
-  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
-    int ix, iy, iz, ip;
-    cell_of(i, g, ix, iy, iz, ip);
-    const size_t base = (size_t)(ip / T_TILE) * nc * T_TILE + (ip % T_TILE);
-    auto cf = [&](int k) { return jlT[base + (size_t)k * T_TILE]; };
-    const float sc = s_in[ip];
-    float a = (cf(0) - shift) * sc;
-    if (ix > 0) a = fmaf(cf(1), s_in[ip - 1], a);
-    if (ix < g.nx - 1) a = fmaf(cf(2), s_in[ip + 1], a);
-    if (iy > 0) a = fmaf(cf(3), s_in[ip - g.px], a);
-    if (iy < g.ny - 1) a = fmaf(cf(4), s_in[ip + g.px], a);
+  const int nvec = g.Np / 4;
+  for (int v = blockIdx.x * NT + threadIdx.x; v < nvec; v += gridDim.x * NT) {
+    const Row4 R = row4_of(v, g);
+    const int ip0 = R.ip0;
+    const size_t base = (size_t)(ip0 / T_TILE) * nc * T_TILE + (ip0 % T_TILE);
+    float sc[4], a[4], cf[4], nb[4], m4[4];
+    ldv<float, 4>(sc, s_in + ip0);
+    const bool has_w = R.ix0 > 0, has_e = R.ix0 + 4 < g.nx;
+    const float sw = has_w ? s_in[ip0 - 1] : 0.0f;
+    const float se = has_e ? s_in[ip0 + 4] : 0.0f;
+    ldv<float, 4>(cf, jlT + base);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = (cf[j] - shift) * sc[j];
+    ldv<float, 4>(cf, jlT + base + T_TILE);       // west neighbour's coupling
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], j > 0 ? sc[j - 1] : sw, a[j]);
+    ldv<float, 4>(cf, jlT + base + 2 * T_TILE);   // east
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], j < 3 ? sc[j + 1] : se, a[j]);
+    float sn[4] = {0, 0, 0, 0}, st[4] = {0, 0, 0, 0};
+    if (R.iy > 0) {
+      ldv<float, 4>(cf, jlT + base + 3 * T_TILE);
+      ldv<float, 4>(nb, s_in + ip0 - g.px);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], nb[j], a[j]);
+    }
+    if (R.iy < g.ny - 1) {
+      ldv<float, 4>(cf, jlT + base + 4 * T_TILE);
+      ldv<float, 4>(sn, s_in + ip0 + g.px);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], sn[j], a[j]);
+    }
     if (g.dim == 3) {
-      if (iz > 0) a = fmaf(cf(5), s_in[ip - g.plane], a);
-      if (iz < g.nz - 1) a = fmaf(cf(6), s_in[ip + g.plane], a);
+      if (R.iz > 0) {
+        ldv<float, 4>(cf, jlT + base + 5 * T_TILE);
+        ldv<float, 4>(nb, s_in + ip0 - g.plane);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], nb[j], a[j]);
+      }
+      if (R.iz < g.nz - 1) {
+        ldv<float, 4>(cf, jlT + base + 6 * T_TILE);
+        ldv<float, 4>(st, s_in + ip0 + g.plane);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], st[j], a[j]);
+      }
     }
-    s_out[ip] = fmaf(dj, mu[ip], a);
-    const float yc = sc * f.icap[ip];
-    const float xc = q[ip];
-    const unsigned fl = f.up[ip];
-    if (ix < g.nx - 1) {
-      const float xu = (fl & 1u) ? xc : q[ip + 1];
-      f.gx[ip] += scale * (fmaf(s_in[ip + 1], f.icap[ip + 1], -yc) * xu);
-    } else {
-      f.gx[ip] -= scale * (yc * xc);
+    ldv<float, 4>(m4, mu + ip0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = R.ix0 + j < g.nx ? fmaf(dj, m4[j], a[j]) : 0.0f;
+    stv<float, 4>(s_out + ip0, a);
+
+    // face derivative of the pair (s_in, q_j)
+    float ic[4], x4[4], yc[4], gs[4];
+    ldv<float, 4>(ic, f.icap + ip0);
+    ldv<float, 4>(x4, q + ip0);
+    const uchar4 fl4 = *reinterpret_cast<const uchar4*>(f.up + ip0);
+    const unsigned fl[4] = {fl4.x, fl4.y, fl4.z, fl4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) yc[j] = sc[j] * ic[j];
+    const float ye = has_e ? se * f.icap[ip0 + 4] : 0.0f;
+    const float qe = has_e ? q[ip0 + 4] : 0.0f;
+    ldv<float, 4>(gs, f.gx + ip0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ix = R.ix0 + j;
+      if (ix < g.nx - 1) {
+        const float yr = j < 3 ? yc[j + 1] : ye;
+        const float xu = (fl[j] & 1u) ? x4[j] : (j < 3 ? x4[j + 1] : qe);
+        gs[j] += scale * ((yr - yc[j]) * xu);
+      } else if (ix == g.nx - 1) {
+        gs[j] -= scale * (yc[j] * x4[j]);
+      }
     }
-    if (iy < g.ny - 1) {
-      const float xu = (fl & 2u) ? xc : q[ip + g.px];
-      f.gy[ip] += scale * (fmaf(s_in[ip + g.px], f.icap[ip + g.px], -yc) * xu);
+    stv<float, 4>(f.gx + ip0, gs);
+    if (R.iy < g.ny - 1) {
+      float icn[4], xn[4];
+      ldv<float, 4>(icn, f.icap + ip0 + g.px);
+      ldv<float, 4>(xn, q + ip0 + g.px);
+      ldv<float, 4>(gs, f.gy + ip0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (R.ix0 + j < g.nx) {
+          const float xu = (fl[j] & 2u) ? x4[j] : xn[j];
+          gs[j] += scale * (fmaf(sn[j], icn[j], -yc[j]) * xu);
+        }
+      stv<float, 4>(f.gy + ip0, gs);
     }
-    if (g.dim == 3 && iz < g.nz - 1) {
-      const float xu = (fl & 4u) ? xc : q[ip + g.plane];
-      f.gz[ip] += scale * (fmaf(s_in[ip + g.plane], f.icap[ip + g.plane], -yc) * xu);
+    if (g.dim == 3 && R.iz < g.nz - 1) {
+      float icn[4], xn[4];
+      ldv<float, 4>(icn, f.icap + ip0 + g.plane);
+      ldv<float, 4>(xn, q + ip0 + g.plane);
+      ldv<float, 4>(gs, f.gz + ip0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (R.ix0 + j < g.nx) {
+          const float xu = (fl[j] & 4u) ? x4[j] : xn[j];
+          gs[j] += scale * (fmaf(st[j], icn[j], -yc[j]) * xu);
+        }
+      stv<float, 4>(f.gz + ip0, gs);
     }
-    if (ix == 0 && (fl & 8u)) f.g0[iy + g.ny * iz] += (double)(scale * (yc * xc));
+    if (R.ix0 == 0 && (fl[0] & 8u)) f.g0[R.iy + g.ny * R.iz] += (double)(scale * (yc[0] * x4[0]));
   }
 }
 
@@ -1553,10 +1637,11 @@ __global__ void k_pc_setup(PresArr a, PcArr p, Geo g) {
   }
 }
 
-// One Chebyshev step.  FIRST: z_1 = D^-1 r / theta (c2 = 1/theta) and the
-// FP32 copy of r.  Otherwise z_{j+1} = z_j + c1 (z_j - z_{j-1})
-// + c2 (D^-1 (r + N z_j) - z_j), A = D - N.  LAST: also (z, r) and (z, A d)
-// -> beta (zero on the first pass after the set-up) and (z, r) for alpha.
+// One Chebyshev step, four cells of a padded row per thread (Row4).  FIRST:
+// z_1 = D^-1 r / theta (c2 = 1/theta) and the FP32 copy of r.  Otherwise
+// z_{j+1} = z_j + c1 (z_j - z_{j-1}) + c2 (D^-1 (r + N z_j) - z_j), A = D - N.
+// LAST: also (z, r) and (z, A d) -> beta (zero on the first pass after the
+// set-up) and (z, r) for alpha.  Pad lanes store 0 and enter no sum.
 template <bool FIRST, bool LAST>
 __global__ void k_pc_sweep(PresArr a, PcArr p, const float* __restrict__ zprev,
                            const float* __restrict__ zcur, float* __restrict__ znew, float c1,
@@ -1564,32 +1649,80 @@ __global__ void k_pc_sweep(PresArr a, PcArr p, const float* __restrict__ zprev,
   __shared__ double sh[NT / 32];
   if (*(volatile int*)&ctrl->lin_done) return;
   double rz = 0.0, zad = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
-    int ix, iy, iz, ip;
-    cell_of(i, g, ix, iy, iz, ip);
-    float zn;
+  const int nvec = g.Np / 4;
+  for (int v = blockIdx.x * NT + threadIdx.x; v < nvec; v += gridDim.x * NT) {
+    const Row4 R = row4_of(v, g);
+    const int ip0 = R.ip0;
+    float zn[4], di[4];
+    ldv<float, 4>(di, p.dinv + ip0);
     if (FIRST) {
-      const float r32 = (float)a.r[ip];
-      if (!LAST) p.r[ip] = r32;
-      zn = c2 * (p.dinv[ip] * r32);
+      const double2 ra = *reinterpret_cast<const double2*>(a.r + ip0);
+      const double2 rb = *reinterpret_cast<const double2*>(a.r + ip0 + 2);
+      float r32[4] = {(float)ra.x, (float)ra.y, (float)rb.x, (float)rb.y};
+      if (!LAST) stv<float, 4>(p.r + ip0, r32);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) zn[j] = c2 * (di[j] * r32[j]);
     } else {
-      const float zc = zcur[ip];
-      const float zp = zprev ? zprev[ip] : 0.0f;   // z_0 = 0
-      float s = p.r[ip];
-      if (ix < g.nx - 1) s = fmaf(p.Ux[ip], zcur[ip + 1], s);
-      if (ix > 0) s = fmaf(p.Ux[ip - 1], zcur[ip - 1], s);
-      if (iy < g.ny - 1) s = fmaf(p.Uy[ip], zcur[ip + g.px], s);
-      if (iy > 0) s = fmaf(p.Uy[ip - g.px], zcur[ip - g.px], s);
-      if (g.dim == 3) {
-        if (iz < g.nz - 1) s = fmaf(p.Uz[ip], zcur[ip + g.plane], s);
-        if (iz > 0) s = fmaf(p.Uz[ip - g.plane], zcur[ip - g.plane], s);
+      float zc[4], zp[4] = {0, 0, 0, 0}, s[4], u[4], nb[4];
+      ldv<float, 4>(zc, zcur + ip0);
+      if (zprev) ldv<float, 4>(zp, zprev + ip0);   // z_0 = 0
+      ldv<float, 4>(s, p.r + ip0);
+      ldv<float, 4>(u, p.Ux + ip0);                 // coupling to the east neighbour
+      const bool has_w = R.ix0 > 0, has_e = R.ix0 + 4 < g.nx;
+      const float uw = has_w ? p.Ux[ip0 - 1] : 0.0f;
+      const float zw = has_w ? zcur[ip0 - 1] : 0.0f;
+      const float ze = has_e ? zcur[ip0 + 4] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int ix = R.ix0 + j;
+        if (ix < g.nx - 1) s[j] = fmaf(u[j], j < 3 ? zc[j + 1] : ze, s[j]);
+        if (ix > 0) s[j] = fmaf(j > 0 ? u[j - 1] : uw, j > 0 ? zc[j - 1] : zw, s[j]);
       }
-      zn = zc + c1 * (zc - zp) + c2 * fmaf(p.dinv[ip], s, -zc);
+      if (R.iy < g.ny - 1) {
+        ldv<float, 4>(u, p.Uy + ip0);
+        ldv<float, 4>(nb, zcur + ip0 + g.px);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[j] = fmaf(u[j], nb[j], s[j]);
+      }
+      if (R.iy > 0) {
+        ldv<float, 4>(u, p.Uy + ip0 - g.px);
+        ldv<float, 4>(nb, zcur + ip0 - g.px);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[j] = fmaf(u[j], nb[j], s[j]);
+      }
+      if (g.dim == 3) {
+        if (R.iz < g.nz - 1) {
+          ldv<float, 4>(u, p.Uz + ip0);
+          ldv<float, 4>(nb, zcur + ip0 + g.plane);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) s[j] = fmaf(u[j], nb[j], s[j]);
+        }
+        if (R.iz > 0) {
+          ldv<float, 4>(u, p.Uz + ip0 - g.plane);
+          ldv<float, 4>(nb, zcur + ip0 - g.plane);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) s[j] = fmaf(u[j], nb[j], s[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) zn[j] = zc[j] + c1 * (zc[j] - zp[j]) + c2 * fmaf(di[j], s[j], -zc[j]);
     }
-    znew[ip] = zn;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (R.ix0 + j >= g.nx) zn[j] = 0.0f;
+    stv<float, 4>(znew + ip0, zn);
     if (LAST) {
-      rz += (double)zn * a.r[ip];
-      zad += (double)zn * a.Ad[ip];
+      const double2 ra = *reinterpret_cast<const double2*>(a.r + ip0);
+      const double2 rb = *reinterpret_cast<const double2*>(a.r + ip0 + 2);
+      const double2 da = *reinterpret_cast<const double2*>(a.Ad + ip0);
+      const double2 db = *reinterpret_cast<const double2*>(a.Ad + ip0 + 2);
+      const double rr[4] = {ra.x, ra.y, rb.x, rb.y}, dd[4] = {da.x, da.y, db.x, db.y};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (R.ix0 + j < g.nx) {
+          rz += (double)zn[j] * rr[j];
+          zad += (double)zn[j] * dd[j];
+        }
     }
   }
   if (!LAST) return;
@@ -2231,7 +2364,7 @@ void launch_pc_setup(const erem_ctx* c, cudaStream_t s) {
 void launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s) {
   const PresArr a = pres_arr(c);
   const PcArr p = pc_arr(c);
-  const int nb = blocks_cells(c);
+  const int nb = grid_for(c, c->Np / 4);
   float* const* zb = &c->pc[5];
   for (int j = 0; j < poly.deg; ++j) {
     const bool last = j == poly.deg - 1;
@@ -2459,7 +2592,7 @@ void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const d
     (void)faces;
     const AdjFaces32 f{c->adj_up, c->adj_icap32, c->adj_g32[0], c->adj_g32[1], c->adj_g32[2],
                        c->adj_g0};
-    k_adj_horner32<128><<<blocks_cells(c), NT, 0, s>>>(
+    k_adj_horner32<128><<<grid_for(c, c->Np / 4), NT, 0, s>>>(
         (const float*)s_in, (float*)s_out, c->adj_mu32, (const float*)q, (const float*)c->jlT_all,
         nc, (float)dj, (float)shift, (float)scale, f, geo_of(c));
   } else
