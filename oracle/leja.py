@@ -112,6 +112,27 @@ def leja_points(M: int, tie_tol: float = 1e-12) -> np.ndarray:
     return np.array(pts)
 
 
+def fast_leja_points(M: int, tie_tol: float = 1e-12) -> np.ndarray:
+    """The fast variant of eq. ``lejaa`` (the "real fast Leja" name of §4.2;
+    the candidate rule of Baglama, Calvetti and Reichel): xi_0 = 2, xi_1 = -2,
+    and every later point is, among the midpoints of the gaps between
+    consecutive points chosen so far, the one where prod_k |xi - xi_k| is
+    largest (ties to the smaller point).  The maximisation of eq. ``lejaa``
+    over the whole interval becomes one over a finite candidate set."""
+    pts = [2.0]
+    if M >= 1:
+        pts.append(-2.0)
+    while len(pts) < M + 1:
+        P = np.array(pts)
+        s = np.sort(P)
+        cands = 0.5 * (s[:-1] + s[1:])
+        vals = [_log_product(x, P) for x in cands]
+        best = max(vals)
+        ties = [x for x, v in zip(cands, vals) if v >= best - tie_tol * max(1.0, abs(best))]
+        pts.append(float(min(ties)))
+    return np.array(pts[: M + 1])
+
+
 # --------------------------------------------------------------------------
 # step 3: divided differences by the matrix function
 # --------------------------------------------------------------------------
@@ -169,6 +190,7 @@ class LejaOptions:
     max_doublings: int = 6
     avg_window: int = 5
     replay: list | None = None  # [s, m_1, ..., m_s]
+    points: str = "exact"       # "exact" (eq. lejaa) or "fast" (midpoint candidates)
 
 
 @dataclass
@@ -186,15 +208,16 @@ class LejaResult:
         return [self.substeps] + list(self.degrees)
 
 
-_LEJA_CACHE: dict[int, np.ndarray] = {}
+_LEJA_CACHE: dict[tuple, np.ndarray] = {}
 
 
-def cached_leja_points(M: int) -> np.ndarray:
-    best = max((k for k in _LEJA_CACHE if k >= M), default=None)
+def cached_leja_points(M: int, points: str = "exact") -> np.ndarray:
+    make = {"exact": leja_points, "fast": fast_leja_points}[points]
+    best = max((k for (kind, k) in _LEJA_CACHE if kind == points and k >= M), default=None)
     if best is None:
-        _LEJA_CACHE[M] = leja_points(M)
+        _LEJA_CACHE[(points, M)] = make(M)
         best = M
-    return _LEJA_CACHE[best][: M + 1]
+    return _LEJA_CACHE[(points, best)][: M + 1]
 
 
 def weighted_norm(x, scal):
@@ -236,7 +259,7 @@ def phi1_leja(J, v, tau: float, y_inf: float, opts: LejaOptions | None = None) -
     m_cap = opts.m_max
     if opts.replay is not None:
         m_cap = max(m_cap, max(opts.replay[1:]))
-    xi = cached_leja_points(m_cap)
+    xi = cached_leja_points(m_cap, opts.points)
     attempts = [opts.replay[0]] if opts.replay is not None else [
         2**k for k in range(opts.max_doublings + 1)]
     last_err = 0.0

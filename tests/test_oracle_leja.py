@@ -223,3 +223,54 @@ def test_stopping_settings_match_paper():
     o = LejaOptions()
     assert o.tol_a == vals["tol"] and o.tol_r == vals["tol"]
     assert o.p_order == vals["p_order"] and o.avg_window == vals["avg"]
+
+
+# ---------------------------------------------------------------------------
+# the fast (midpoint-candidate) Leja points, the option behind the name of §4.2
+# ---------------------------------------------------------------------------
+def test_first_fast_leja_points_closed_form():
+    # 2, -2; the only gap midpoint is 0; then -1 and 1 tie (product 3: the
+    # smaller wins) and 1 follows (product 6 against 1.31 at -1.5); then
+    # -1.5 and 1.5 tie at 3.28 and -0.5 follows
+    assert list(leja.fast_leja_points(7)) == [2.0, -2.0, 0.0, -1.0, 1.0, -1.5, 1.5, -0.5]
+
+
+def test_fast_leja_points_brute_force():
+    # every new point is, over all midpoints of consecutive chosen points
+    # (enumerated afresh), one with the largest product, the smallest on ties;
+    # every point is a dyadic rational (a midpoint of midpoints of +-2)
+    xi = leja.fast_leja_points(60)
+    for j in range(2, 61):
+        s = sorted(xi[:j])
+        mids = [(a + b) / 2 for a, b in zip(s[:-1], s[1:])]
+        prods = [math.prod(abs(m - x) for x in xi[:j]) for m in mids]
+        best = max(prods)
+        winners = [m for m, p in zip(mids, prods) if p >= best * (1 - 1e-12)]
+        assert xi[j] == min(winners), j
+        assert float(xi[j] * 2**40).is_integer()
+
+
+def test_fast_leja_points_distinct_bounded_and_capacity():
+    xi = leja.fast_leja_points(150)
+    assert np.all(np.abs(xi) <= 2.0)
+    assert len(np.unique(xi)) == xi.size
+    j = 150
+    g = np.exp(np.mean(np.log(np.abs(xi[j] - xi[:j]))))
+    assert 0.9 < g < 1.6
+
+
+@pytest.mark.parametrize("tau", [0.01, 0.05, 0.3])
+def test_phi1_fast_leja_matches_dense_expm(tau):
+    prob, T = _small_problem()
+    J = prob.J(T)
+    v = prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    res = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))),
+                         LejaOptions(tol_a=1e-13, tol_r=1e-13, points="fast"))
+    assert res.converged
+    err = np.linalg.norm(res.value - ref) / np.linalg.norm(ref)
+    assert err < 1e-10, (err, res.schedule)
+    # the two point sets give the same function value through different
+    # polynomials
+    exact = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))), LejaOptions(tol_a=1e-13, tol_r=1e-13))
+    assert np.linalg.norm(res.value - exact.value) / np.linalg.norm(ref) < 2e-10
