@@ -246,8 +246,9 @@ def gpu_context(E, torch, wl, precision, dev):
                     "rhoc": rc, "head_left": head}
 
 
-def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=False):
+def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=False, points="exact"):
     ctx, T, info = gpu_context(E, torch, wl, precision, dev)
+    ctx.set_leja_points(points)
     opts = E.leja_opts(tol=wl.tol, time_terms=True)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -453,6 +454,14 @@ def main(args):
                         "degrees_per_step": [s[1:] if s[0] == 1 else s for s in r64["degrees"]]}
         line["speedup_fp32_bulk_vs_fp64"] = ms64 / ms
         line["rel_l2_fp32_bulk_vs_fp64"] = rel
+        # the same steps with the fast (midpoint-candidate) Leja points
+        rf = run_gpu(E, torch, wl, "fp32_bulk", K, Wu, dev, world, points="fast")
+        msf, valuef = aggregate(rf["ms"], N, K, world, dev)
+        line["leja_fast_fp32_bulk"] = {
+            "value": valuef, "ms_per_step": msf / K,
+            "terms_per_step": float(np.mean([sum(s[1:]) for s in rf["degrees"]])),
+            "terms_per_step_exact_points": float(np.mean([sum(s[1:]) for s in r32["degrees"]])),
+            "rel_l2_vs_exact_points": float(np.linalg.norm(rf["T"] - r32["T"]) / np.linalg.norm(r32["T"]))}
         if not args.no_krylov:
             rk = run_krylov(E, torch, wl, K, Wu, dev)
             msk, valuek = aggregate(rk["ms"], N, K, world, dev)

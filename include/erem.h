@@ -325,6 +325,19 @@ EREM_API erem_status erem_adjoint_step(erem_ctx* ctx, const double* T, double* l
 EREM_API erem_status erem_adjoint_lnk(erem_ctx* ctx, const double* lnk, double* glnk, double tol,
                                       int maxit, erem_stats* stats, void* stream);
 
+/* Point set of the Leja interpolation (§4.2) for later calls on ctx.
+ *   EREM_LEJA_EXACT (default): eq. lejaa, each point maximises
+ *     prod_k |xi - xi_k| over the whole interval (ties to the smaller point).
+ *   EREM_LEJA_FAST: the "fast" variant named in the title of §4.2 (the
+ *     candidate rule of Baglama, Calvetti and Reichel): xi_0 = 2, xi_1 = -2,
+ *     then the midpoint of a gap between consecutive chosen points with the
+ *     largest product (ties to the smaller point); the points are dyadic.
+ * The divided differences are recomputed for the new points; replayed
+ * schedules keep their meaning (degrees per substep).  The batched ensemble
+ * keeps the exact points.  Errors: EINVAL (ctx NULL, unknown kind). */
+typedef enum { EREM_LEJA_EXACT = 0, EREM_LEJA_FAST = 1 } erem_leja_kind;
+EREM_API erem_status erem_set_leja_points(erem_ctx* ctx, int kind);
+
 /* Preconditioner of the pressure CG (pressure_solve, erem_adjoint_lnk) for
  * later calls on ctx.  degree 1: Jacobi (diagonal) preconditioning, plain CG
  * in FP64.  degree 2..64: z = p(D^-1 A) D^-1 r, `degree` steps of Chebyshev
@@ -332,7 +345,7 @@ EREM_API erem_status erem_adjoint_lnk(erem_ctx* ctx, const double* lnk, double* 
  * the spectrum of D^-1 A lies in (0, 2]), applied in FP32; the outer CG stays
  * FP64 with the Polak-Ribiere beta (flexible CG), so the stopping rule and
  * accuracy of pressure_solve are unchanged and lin_iters counts outer
- * iterations.  Default 16.  Needs 8 FP32 vectors [N] (allocated on first use).
+ * iterations.  Default 32.  Needs 8 FP32 vectors [N] (allocated on first use).
  * The paper's solver is BiCGSTAB with ILU(0) (§3.2.3, §5); both are
  * preconditioned Krylov methods for the same system.
  * Errors: EINVAL (ctx NULL, degree outside 1..64). */
@@ -360,6 +373,9 @@ EREM_API const char* erem_last_error(const erem_ctx* ctx);
  *   xi -> phi_1(c + gamma xi), j = 0..M, the first column of
  *   phi_1(c I + gamma L_hat) (§4.2); returns 0, or -1 on bad arguments. */
 EREM_API int erem_leja_points(int M, double* xi);
+/* erem_fast_leja_points: the EREM_LEJA_FAST points xi_0..xi_M (see
+ *   erem_set_leja_points); returns 0, or -1 for M < 0 or M > 4096. */
+EREM_API int erem_fast_leja_points(int M, double* xi);
 EREM_API int erem_phi1_divided_differences(int M, const double* xi, double c,
                                   double gamma, double* d);
 

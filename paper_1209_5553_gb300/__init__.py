@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "EREM_OK", 1: "EREM_EINVAL", 2: "EREM_ENOMEM", 3: "EREM_ENOTC
                 4: "EREM_ETIMEOUT", 5: "EREM_ENONFINITE", 6: "EREM_ECUDA"}
 EREM_FP64, EREM_FP32_BULK = 0, 1
 EREM_ROSM1, EREM_ROSM_HALF, EREM_ROS2 = 0, 1, 2
+EREM_LEJA_EXACT, EREM_LEJA_FAST = 0, 1
 
 
 class erem_grid(ctypes.Structure):
@@ -131,6 +132,8 @@ _sigs = {
     "rosm_step": (_I, [_P, _P, _P, _P, _P, _P, _D, _I, _D, _I, ctypes.POINTER(erem_stats), _P]),
     "erem_last_error": (ctypes.c_char_p, [_P]),
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
+    "erem_fast_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
+    "erem_set_leja_points": (_I, [_P, _I]),
     "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
     "erem_pressure_solve_static": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics),
                                         _P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -302,6 +305,19 @@ def erem_leja_points(M: int) -> np.ndarray:
     return out
 
 
+def erem_fast_leja_points(M: int) -> np.ndarray:
+    out = np.zeros(M + 1)
+    if _lib.erem_fast_leja_points(int(M), out.ctypes.data_as(ctypes.POINTER(_D))) != 0:
+        raise ValueError("bad M")
+    return out
+
+
+def erem_set_leja_points(ctx, kind) -> None:
+    """EREM_LEJA_EXACT or EREM_LEJA_FAST (or "exact" / "fast")."""
+    kind = {"exact": EREM_LEJA_EXACT, "fast": EREM_LEJA_FAST}.get(kind, kind)
+    _check(ctx, _lib.erem_set_leja_points(ctx, int(kind)))
+
+
 def erem_phi1_divided_differences(xi, c: float, gamma: float) -> np.ndarray:
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     out = np.zeros(xi.size)
@@ -377,7 +393,7 @@ def erem_hold_interval(ctx, interval) -> None:
 
 def erem_set_pressure_precond(ctx, degree) -> None:
     """Pressure CG preconditioner: 1 = Jacobi, 2..64 = FP32 Chebyshev
-    polynomial of that degree (default 16)."""
+    polynomial of that degree (default 32)."""
     _check(ctx, _lib.erem_set_pressure_precond(ctx, int(degree)))
 
 
@@ -532,6 +548,9 @@ class Context:
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):
         return rosm_step(self._h, self.n, T, dt, scheme, p, lnk, phi, lam, lin_tol, maxit, stream)
+
+    def set_leja_points(self, kind):
+        erem_set_leja_points(self._h, kind)
 
     def set_pressure_precond(self, degree):
         erem_set_pressure_precond(self._h, degree)

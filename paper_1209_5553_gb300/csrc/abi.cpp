@@ -174,7 +174,8 @@ erem_status ensure_leja(erem_ctx* c, int M) {
   if (M > kMaxTerms) return fail(c, EREM_EINVAL, "m_max above " + std::to_string(kMaxTerms));
   int cap = std::max(M, 2 * c->xi_cap);
   cap = std::min(cap, kMaxTerms);
-  leja_table(cap, &c->xi_host);
+  if (c->leja_kind == EREM_LEJA_FAST) fast_leja_table(cap, &c->xi_host);
+  else leja_table(cap, &c->xi_host);
   if (c->xi_dev) cudaFree(c->xi_dev);
   c->xi_dev = nullptr;
   EREM_TRY(dalloc_t(c, &c->xi_dev, (size_t)cap + 1));
@@ -1162,6 +1163,19 @@ erem_status erem_step_krylov(erem_ctx* c, double* T, const double* p, const doub
     st->launches = (int)c->launches;
   }
   return EREM_OK;
+}
+
+erem_status erem_set_leja_points(erem_ctx* c, int kind) {
+  if (!c) return EREM_EINVAL;
+  if (kind != EREM_LEJA_EXACT && kind != EREM_LEJA_FAST)
+    return fail(c, EREM_EINVAL, "Leja point kind must be EREM_LEJA_EXACT or EREM_LEJA_FAST");
+  if (kind == c->leja_kind) return EREM_OK;
+  const int cap = c->xi_cap;
+  c->leja_kind = kind;
+  c->xi_cap = 0;            // rebuilt for the new kind
+  c->dd_cache.clear();      // divided differences belong to the points
+  c->dd_tag_S = -1;
+  return cap > 0 ? ensure_leja(c, cap) : EREM_OK;
 }
 
 erem_status erem_set_pressure_precond(erem_ctx* c, int degree) {

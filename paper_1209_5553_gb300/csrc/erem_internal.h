@@ -16,7 +16,7 @@ namespace erem {
 constexpr int kThreads = 256;      // threads per block of every kernel
 constexpr int kMaxTerms = 4096;    // largest Leja degree a context accepts
 constexpr int kMaxPcDeg = 64;      // largest degree of the pressure CG's polynomial preconditioner
-constexpr int kDefaultPcDeg = 16;  // its default (1 = plain Jacobi CG)
+constexpr int kDefaultPcDeg = 32;  // its default (1 = plain Jacobi CG)
 constexpr int kRedSlots = 4;       // reduction values per block
 
 // Bits of Ctrl::flags raised by the set-up kernels.
@@ -231,6 +231,7 @@ struct erem_ctx {
   double* dd_dev = nullptr;         // divided differences of the active substep level
   double* dd_h = nullptr;           // pinned staging of dd
   int xi_cap = 0;
+  int leja_kind = 0;   // EREM_LEJA_EXACT or EREM_LEJA_FAST
   int dd_tag_S = -1, dd_tag_M = -1;
   std::vector<double> xi_host;
   std::map<int, erem::DDEntry> dd_cache;  // substep count -> table
@@ -353,6 +354,7 @@ void expm_small(int n, const double* A, double* E);
 
 // host scalar side (leja_host.cpp)
 void leja_table(int M, std::vector<double>* out);
+void fast_leja_table(int M, std::vector<double>* out);
 int divided_differences(int M, const double* xi, double c, double gamma, double* d);
 
 }  // namespace erem

@@ -85,7 +85,60 @@ void extend_leja(int M) {
   }
 }
 
+std::mutex g_fast_mu;
+std::vector<double> g_fast;                 // fast points in the order chosen
+std::vector<double> g_fast_sorted;          // the same, sorted
+std::vector<std::pair<double, double>> g_fast_cand;  // (gap midpoint, log-product)
+
+// The fast variant: each new point is the gap midpoint with the largest
+// log-product over the points chosen so far (ties to the smaller point).
+// Adding a point adds its log-distance to every candidate and replaces the
+// candidate of the gap it splits by the midpoints of the two halves.
+void extend_fast(int M) {
+  if ((int)g_fast.size() >= M + 1) return;
+  auto logprod = [](double x) {
+    double s = 0.0;
+    for (double pk : g_fast) s += std::log(std::fabs(x - pk));
+    return s;
+  };
+  if (g_fast.empty()) {
+    g_fast = {2.0};
+    g_fast_sorted = {2.0};
+  }
+  if (M >= 1 && g_fast.size() < 2) {
+    g_fast.push_back(-2.0);
+    g_fast_sorted = {-2.0, 2.0};
+    g_fast_cand = {{0.0, logprod(0.0)}};
+  }
+  while ((int)g_fast.size() < M + 1) {
+    double best_v = -INFINITY;
+    for (auto& c : g_fast_cand) best_v = std::max(best_v, c.second);
+    const double tol = 1e-12 * std::max(1.0, std::fabs(best_v));
+    size_t pick = 0;
+    double best_x = INFINITY;
+    for (size_t i = 0; i < g_fast_cand.size(); ++i)
+      if (g_fast_cand[i].second >= best_v - tol && g_fast_cand[i].first < best_x) {
+        best_x = g_fast_cand[i].first;
+        pick = i;
+      }
+    // neighbours of the chosen midpoint in the sorted points
+    const auto hi_it = std::upper_bound(g_fast_sorted.begin(), g_fast_sorted.end(), best_x);
+    const double hi = *hi_it, lo = *(hi_it - 1);
+    g_fast.push_back(best_x);
+    g_fast_sorted.insert(hi_it, best_x);
+    g_fast_cand.erase(g_fast_cand.begin() + pick);
+    for (auto& c : g_fast_cand) c.second += std::log(std::fabs(c.first - best_x));
+    for (double m : {0.5 * (lo + best_x), 0.5 * (best_x + hi)}) g_fast_cand.emplace_back(m, logprod(m));
+  }
+}
+
 }  // namespace
+
+void fast_leja_table(int M, std::vector<double>* out) {
+  std::lock_guard<std::mutex> lk(g_fast_mu);
+  extend_fast(M);
+  out->assign(g_fast.begin(), g_fast.begin() + M + 1);
+}
 
 void leja_table(int M, std::vector<double>* out) {
   std::lock_guard<std::mutex> lk(g_leja_mu);
@@ -216,6 +269,14 @@ extern "C" int erem_leja_points(int M, double* xi) {
   if (M < 0 || M > 4096 || !xi) return -1;
   std::vector<double> t;
   erem::leja_table(M, &t);
+  std::copy(t.begin(), t.end(), xi);
+  return 0;
+}
+
+extern "C" int erem_fast_leja_points(int M, double* xi) {
+  if (M < 0 || M > 4096 || !xi) return -1;
+  std::vector<double> t;
+  erem::fast_leja_table(M, &t);
   std::copy(t.begin(), t.end(), xi);
   return 0;
 }

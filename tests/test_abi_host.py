@@ -129,6 +129,16 @@ def test_host_leja_points_match_oracle(E):
     assert np.max(np.abs(a - b)) < 1e-14
 
 
+def test_host_fast_leja_points_match_oracle(E):
+    # dyadic points: the library's incremental candidate update and the
+    # oracle's fresh enumeration choose bit-identical points
+    a = E.erem_fast_leja_points(300)
+    b = leja.fast_leja_points(300)
+    assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        E.erem_fast_leja_points(5000)
+
+
 @pytest.mark.parametrize("c,gamma", [(-20.0, 10.0), (-3.0, 1.5), (-60.0, 30.0), (-0.5, 0.25),
                                      (-200.0, 100.0), (-1e-6, 1e-8)])
 def test_host_divided_differences_match_oracle(E, c, gamma):

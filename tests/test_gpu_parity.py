@@ -304,3 +304,57 @@ def test_stop_inside_a_pair_removes_the_extra_term(E):
         assert C.rel_l2(got, res.value) < FP64_TOL
         parities.add(res.degrees[0] % 2)
     assert parities == {0, 1}
+
+
+# ---------------------------------------------------------------------------
+# fast (midpoint-candidate) Leja points
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,make", [CASES_2D[0], CASES_2D[1], CASES_3D[1], CASES_3D[2]],
+                         ids=["heat2d_64", "ragged_65x67", "box_24x20x9", "channels_32"])
+def test_erem_steps_with_fast_leja_points(E, name, make):
+    # the oracle with the same point set: FP64 replayed to 1e-11 and, free
+    # running, on the oracle's schedule; FP32-bulk to 1e-5; the point set only
+    # changes the polynomial, so exact and fast agree to the Leja tolerance
+    case = make()
+    steps = 3
+    fast = LejaOptions(points="fast")
+    T_ref, scheds = _oracle_run(case, steps, fast)
+    T_exact, _ = _oracle_run(case, steps)
+    assert C.rel_l2(T_ref - case.T0, T_exact - case.T0) < 1e-5
+    for prec, tol in (("fp64", FP64_TOL), ("fp32_bulk", FP32_TOL)):
+        for replay in ((True, False) if prec == "fp64" else (False,)):
+            with _ctx(E, case, prec) as ctx:
+                ctx.set_leja_points("fast")
+                T = _t(case.T0)
+                got_s = []
+                for k in range(steps):
+                    fields = (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam)) if k == 0 else (None,) * 4
+                    opts = E.leja_opts(replay=scheds[k]) if replay else None
+                    got_s.append(ctx.erem_step(T, case.dt, *fields, opts=opts).schedule)
+                got = T.cpu().numpy()
+            assert C.rel_l2(got, T_ref) < tol, (prec, replay)
+            if prec == "fp64" and not replay:
+                assert got_s == scheds
+
+
+def test_leja_point_kind_switches_and_errors(E):
+    # switching back to the exact points restores the exact-point result
+    # bit for bit; bad kinds are EINVAL
+    case = C.heat2d(32)
+    v = case.problem(case.T0).G(case.T0)
+    outs = {}
+    with _ctx(E, case, "fp64") as ctx:
+        ctx.set_state(_t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+        for kind in ("exact", "fast", "exact"):
+            ctx.set_leja_points(kind)
+            out = _t(np.zeros(case.n))
+            st = ctx.phi1_apply(_t(v), out)
+            outs.setdefault(kind, []).append((out.cpu().numpy(), st.schedule))
+        for bad in (2, -1):
+            with pytest.raises(E.EremError) as ei:
+                ctx.set_leja_points(bad)
+            assert ei.value.status == E.EREM_EINVAL
+    assert np.array_equal(outs["exact"][0][0], outs["exact"][1][0])
+    ref = leja.phi1_leja(case.problem(case.T0).J(case.T0), v, case.dt, float(np.max(case.T0)),
+                         LejaOptions(points="fast", replay=outs["fast"][0][1]))
+    assert C.rel_l2(outs["fast"][0][0], ref.value) < FP64_TOL
