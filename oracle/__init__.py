@@ -22,6 +22,9 @@ LU solves and FFT-free arithmetic serve as library steps):
 * ``oracle.adjoint``   gradients of a temperature misfit with respect to T^0
                        and ln K through frozen-schedule EREM steps (transposed
                        Newton polynomial, face-flux and pressure adjoints)
+* ``oracle.nonauto``   non-autonomous EREM (eq. ``nEERMg``): phi_1 and phi_2
+                       by Leja interpolation, D_t G of a time-dependent
+                       inflow temperature
 * ``oracle.timestep``  EREM (eq. ``EERM``), ROSM (eq. ``ROS``), ROS2(1)
                        (eq. ``ROSMh``, Table ``ros2``), pressure solves and the
                        sequential coupling of §3.2
@@ -31,6 +34,6 @@ other than itself: closed forms, dense matrix exponentials, high-precision
 divided differences, brute force on tiny inputs, conservation laws and the
 constants the paper prints (``tests/golden/``).
 """
-from . import adjoint, fv, krylov, leja, timestep  # noqa: F401
+from . import adjoint, fv, krylov, leja, nonauto, timestep  # noqa: F401
 from .fv import Grid, Physics  # noqa: F401
 from .leja import LejaOptions, LejaResult, phi1_leja  # noqa: F401
