@@ -119,6 +119,7 @@ typedef struct {
   int n_terms_timed;    /* time_terms: Leja terms those launches computed     */
   int launches;         /* CUDA kernels this call launched                    */
   int n_launches_timed; /* time_terms: Leja kernel launches in t_terms_ms     */
+  int degree_phi2;      /* erem_step_forced: degree of the phi_2 interpolation */
 } erem_stats;
 
 typedef struct erem_ctx erem_ctx;
@@ -201,6 +202,29 @@ EREM_API erem_status erem_step(erem_ctx* ctx, double* T, const double* p,
  * system (I/(dt gamma) - J_n) k = r is solved by Jacobi-preconditioned
  * BiCGSTAB in FP64 to ||r - A k||_2 <= lin_tol ||r||_2 (maxit iterations).
  * Fields as erem_step.  Errors: EINVAL, ENOTCONV, ENONFINITE, ECUDA. */
+/* One step of the non-autonomous EREM scheme (eq. nEERMg, §3.2) for the
+ * heat problem whose inflow temperature depends on time:
+ *   T <- T + dt phi_1(dt J) G(T, t_n) + dt^2 phi_2(dt J) D_t G(T, t_n),
+ * G(T, t_n) with the inflow temperature T_in = T_in(t_n) (instead of the
+ * physics' T_inflow) and D_t G = T_in_rate dG/dT_in, non-zero on the x = 0
+ * cells only (their Dirichlet conduction and inflowing advection, §3.1).
+ * phi_2(z) = (e^z - 1 - z)/z^2.  Both products are Leja interpolations on
+ * the interval of dt J (§4.2; the phi_2 divided differences by the same
+ * matrix-function route); the phi_2 interpolation is stopped by the same
+ * test on its increments dt^2 d_m q_m.  When m_max terms do not suffice the
+ * step is split into s pieces of length delta = dt / s: piece k adds
+ * delta phi_1(delta J)(J y_k + G + k delta D_t G) + delta^2 phi_2(delta J) D_t G,
+ * the exact flow of the linearised equation y' = J y + G + t D_t G.
+ * opts->replay, if given, is [s, m_1..m_s, m_phi2] (n_replay = s + 2).
+ * stats: as erem_step plus degree_phi2; degree_total counts both parts.
+ * Needs fluid_model = 0 (G affine in T and T_in).  Other arguments and
+ * errors as erem_step. */
+EREM_API erem_status erem_step_forced(erem_ctx* ctx, double* T, double dt, double T_in,
+                                      double T_in_rate, const double* p, const double* lnk,
+                                      const double* phi, const double* lambda,
+                                      const erem_leja_opts* opts, erem_stats* stats,
+                                      void* stream);
+
 EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
                       const double* lnk, const double* phi,
                       const double* lambda, double dt,
@@ -371,11 +395,14 @@ EREM_API const char* erem_last_error(const erem_ctx* ctx);
  *   the smaller point); returns 0, or -1 for M < 0 or M > 4096.
  * erem_phi1_divided_differences: d_j = phi_1[xi_0..xi_j] of
  *   xi -> phi_1(c + gamma xi), j = 0..M, the first column of
- *   phi_1(c I + gamma L_hat) (§4.2); returns 0, or -1 on bad arguments. */
+ *   phi_1(c I + gamma L_hat) (§4.2); returns 0, or -1 on bad arguments.
+ * erem_phi2_divided_differences: the same for phi_2 (eq. nEERMg). */
 EREM_API int erem_leja_points(int M, double* xi);
 /* erem_fast_leja_points: the EREM_LEJA_FAST points xi_0..xi_M (see
  *   erem_set_leja_points); returns 0, or -1 for M < 0 or M > 4096. */
 EREM_API int erem_fast_leja_points(int M, double* xi);
+EREM_API int erem_phi2_divided_differences(int M, const double* xi, double c, double gamma,
+                                           double* d);
 EREM_API int erem_phi1_divided_differences(int M, const double* xi, double c,
                                   double gamma, double* d);
 

@@ -62,11 +62,16 @@ class erem_stats(ctypes.Structure):
                 ("flux_in", ctypes.c_double), ("vmax", ctypes.c_double),
                 ("t_ms", ctypes.c_double), ("t_terms_ms", ctypes.c_double),
                 ("n_terms_timed", ctypes.c_int), ("launches", ctypes.c_int),
-                ("n_launches_timed", ctypes.c_int)]
+                ("n_launches_timed", ctypes.c_int), ("degree_phi2", ctypes.c_int)]
 
     @property
     def schedule(self):
         return [self.substeps] + [self.degrees[k] for k in range(self.substeps)]
+
+    @property
+    def schedule_forced(self):
+        """[s, m_1..m_s, m_phi2] of erem_step_forced (its replay format)."""
+        return self.schedule + [self.degree_phi2]
 
 
 class erem_krylov_opts(ctypes.Structure):
@@ -133,6 +138,9 @@ _sigs = {
     "erem_last_error": (ctypes.c_char_p, [_P]),
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_fast_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
+    "erem_phi2_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
+    "erem_step_forced": (_I, [_P, _P, _D, _D, _D, _P, _P, _P, _P, ctypes.POINTER(erem_leja_opts),
+                              ctypes.POINTER(erem_stats), _P]),
     "erem_set_leja_points": (_I, [_P, _I]),
     "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
     "erem_pressure_solve_static": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics),
@@ -289,6 +297,16 @@ def erem_step(ctx, n, T, dt, p=None, lnk=None, phi=None, lam=None,
     return st
 
 
+def erem_step_forced(ctx, n, T, dt, T_in, T_in_rate, p=None, lnk=None, phi=None, lam=None,
+                     opts: erem_leja_opts | None = None, stream=None) -> erem_stats:
+    st = erem_stats()
+    _check(ctx, _lib.erem_step_forced(ctx, _ptr(T, n), float(dt), float(T_in), float(T_in_rate),
+                                      _ptr(p, n), _ptr(lnk, n), _ptr(phi, n), _ptr(lam, n),
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      ctypes.byref(st), _stream(stream)))
+    return st
+
+
 def rosm_step(ctx, n, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
               lin_tol=1e-10, maxit=10000, stream=None) -> erem_stats:
     st = erem_stats()
@@ -303,6 +321,16 @@ def erem_leja_points(M: int) -> np.ndarray:
     if _lib.erem_leja_points(int(M), out.ctypes.data_as(ctypes.POINTER(_D))) != 0:
         raise ValueError("bad M")
     return out
+
+
+def erem_phi2_divided_differences(xi, c: float, gamma: float) -> np.ndarray:
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    d = np.zeros(xi.size)
+    if _lib.erem_phi2_divided_differences(xi.size - 1, xi.ctypes.data_as(ctypes.POINTER(_D)),
+                                          float(c), float(gamma),
+                                          d.ctypes.data_as(ctypes.POINTER(_D))) != 0:
+        raise ValueError("bad arguments")
+    return d
 
 
 def erem_fast_leja_points(M: int) -> np.ndarray:
@@ -544,6 +572,11 @@ class Context:
 
     def erem_step(self, T, dt, p=None, lnk=None, phi=None, lam=None, opts=None, stream=None):
         return erem_step(self._h, self.n, T, dt, p, lnk, phi, lam, opts, stream)
+
+    def erem_step_forced(self, T, dt, T_in, T_in_rate, p=None, lnk=None, phi=None, lam=None,
+                         opts=None, stream=None):
+        return erem_step_forced(self._h, self.n, T, dt, T_in, T_in_rate, p, lnk, phi, lam, opts,
+                                stream)
 
     def rosm_step(self, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
                   lin_tol=1e-10, maxit=10000, stream=None):

@@ -199,27 +199,31 @@ void focal_map(erem_ctx* c) {
   c->gam = std::max(g, floor);
 }
 
-// Divided differences of level S (interval / S) with at least M+1 entries,
-// on the device in dd_dev.
-erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s) {
-  DDEntry& e = c->dd_cache[S];
+// Divided differences of level S (interval / S) with at least M+1 entries
+// (of phi_1, or phi_2 for phi = 2), on the device in dd_dev.
+int dd_key(int S, int phi) { return 8 * S + phi; }
+DDEntry& dd_entry(erem_ctx* c, int S, int phi = 1) { return c->dd_cache[dd_key(S, phi)]; }
+
+erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1) {
+  DDEntry& e = dd_entry(c, S, phi);
+  const int key = dd_key(S, phi);
   const double cc = c->cfoc / S, gg = c->gam / S;
   if (e.M < M || e.c != cc || e.gamma != gg) {
     e.c = cc;
     e.gamma = gg;
     e.M = M;
     e.d.assign(M + 1, 0.0);
-    if (divided_differences(M, c->xi_host.data(), cc, gg, e.d.data()) != 0)
+    if (divided_differences_phi(phi, M, c->xi_host.data(), cc, gg, e.d.data()) != 0)
       return fail(c, EREM_EINVAL, "divided differences: bad interval");
     for (double v : e.d)
       if (!std::isfinite(v)) return fail(c, EREM_ENONFINITE, "non-finite divided difference");
     c->dd_tag_S = -1;
   }
-  if (c->dd_tag_S != S || c->dd_tag_M != e.M) {
+  if (c->dd_tag_S != key || c->dd_tag_M != e.M) {
     std::memcpy(c->dd_h, e.d.data(), (e.M + 1) * sizeof(double));
     EREM_CUDA(c, cudaMemcpyAsync(c->dd_dev, c->dd_h, (e.M + 1) * sizeof(double),
                                  cudaMemcpyHostToDevice, s));
-    c->dd_tag_S = S;
+    c->dd_tag_S = key;
     c->dd_tag_M = e.M;
   }
   return EREM_OK;
@@ -277,6 +281,112 @@ erem_status ensure_events(erem_ctx* c, int n) {
 // J must be current.  With fused_T (linear fluid model) the first substep is
 // started by the fused kernel that computes src = J T + b and base = T^n from
 // the caller's T itself.
+// Device time of the Leja launches of a call (time_terms).
+struct TermTiming {
+  double ms = 0.0;
+  int terms = 0, launches = 0;
+};
+
+// One Newton interpolation (§4.2) at substep level S with the table of phi
+// (prepared in dd_dev): q_0 = u (or, for the fused first kernel, G(T) from
+// fused_T), P = sum_m d_m q_m, the terms launched in chunks and stopped by
+// the device test (StopParams sp) or at the forced degree.  *degree gets m;
+// *failed is set when m_max terms do not meet the test, *nonfinite when the
+// estimate left the range of the Leja precision.
+erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int S, int phi,
+                        int* M_avail, int mcap, const StopParams& sp, int forced, const Opts& o,
+                        TermTiming* tt, int* degree, bool* failed, bool* nonfinite,
+                        cudaStream_t s) {
+  const double cg = c->cfoc / c->gam;  // the same for every substep level
+  const double d0 = dd_entry(c, S, phi).d[0];
+  *failed = *nonfinite = false;
+  if (fused_T)
+    launch_step_init(c, fused_T, d0, sp, s);  // also writes vrhs = G(T) and T^n
+  else
+    launch_leja_init(c, u, d0, sp, s);
+  int m = 1, qin = 0;
+  int chunk = forced ? forced : std::max(4, c->last_degree + 2);
+  // launches of this interpolation: first term, terms computed, output buffer
+  struct Launch { int m, nterms, qout; };
+  std::vector<Launch> launches;
+  while (true) {
+    const int end = forced ? forced : std::min(*M_avail, m + chunk - 1);
+    int mm = m;
+    while (mm <= end) {
+      const int nt = (c->use_pairs && mm + 1 <= end) ? 2 : 1;
+      if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size()], s);
+      if (nt == 2) launch_leja_pair(c, mm, qin, cg, s);
+      else launch_leja_term(c, mm, qin, cg, s);
+      if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size() + 1], s);
+      launches.push_back(Launch{mm, nt, qin ^ 1});
+      qin ^= 1;
+      mm += nt;
+    }
+    EREM_TRY(check_launch(c, "leja term"));
+    EREM_TRY(read_ctrl(c, s));
+    EREM_TRY(check_flags(c));
+    const Ctrl& h = *c->ctrl_h;
+    if (h.nonfinite) {
+      // the Newton vectors (or their squares) left the range of the Leja
+      // precision: the interpolation at this substep length failed
+      if (forced) return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate");
+      *nonfinite = *failed = true;
+      return EREM_OK;
+    }
+    if (forced) {
+      *degree = forced;
+      break;
+    }
+    if (h.done && !h.fail) {
+      *degree = h.degree;
+      if (h.overshoot) {  // the pair that met the test at its first term
+        for (const Launch& l : launches)
+          if (l.m == *degree && l.nterms == 2)
+            launch_unstep(c, l.qout, dd_entry(c, S, phi).d[*degree + 1], s);
+      }
+      break;
+    }
+    if (h.fail || end >= o.m_max) {
+      *failed = true;
+      return EREM_OK;
+    }
+    if (end >= *M_avail) {  // table exhausted below m_max: extend it
+      *M_avail = mcap;
+      EREM_TRY(prepare_dd(c, S, *M_avail, s, phi));
+    }
+    m = end + 1;
+    chunk = 8;
+  }
+  if (o.time_terms && tt) {
+    for (size_t j = 0; j < launches.size(); ++j) {
+      if (launches[j].m > *degree) break;  // returned at once: the test had passed
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[2 * j], c->ev[2 * j + 1]) == cudaSuccess) {
+        tt->ms += ms;
+        tt->terms += launches[j].nterms;
+        ++tt->launches;
+      }
+    }
+  }
+  c->last_degree = *degree;
+  return EREM_OK;
+}
+
+StopParams stop_params(const erem_ctx* c, const Opts& o, double scale, int m_max, bool replay) {
+  StopParams sp{};
+  sp.delta = scale;
+  sp.ncells = (double)c->N;
+  sp.pow10 = std::pow(10.0, o.p_order);
+  sp.tol_a = o.tol_a;
+  sp.tol_r = o.tol_r;
+  sp.window = o.avg_window;
+  sp.m_max = m_max;
+  sp.replay = replay ? 1 : 0;
+  return sp;
+}
+
+// out = base + dt phi_1(dt J) src (T^n + the EREM increment when base = T^n),
+// with substep doubling (§4.2) or the replayed schedule.
 erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double* out,
                      const Opts& o, erem_stats* st, cudaStream_t s,
                      const double* fused_T = nullptr) {
@@ -285,12 +395,10 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
   if (replay)
     for (size_t k = 1; k < o.replay.size(); ++k) mcap = std::max(mcap, o.replay[k]);
   EREM_TRY(ensure_leja(c, mcap));
-  const double cg = c->cfoc / c->gam;  // the same for every substep level
   int n_attempts = replay ? 1 : o.max_doublings + 1;
   bool nonfinite_attempt = false;  // the last failed attempt had a non-finite estimate
   int degrees[64];
-  double t_terms = 0.0;
-  int n_timed = 0, n_launch_timed = 0;
+  TermTiming tt;
   if (o.time_terms) EREM_TRY(ensure_events(c, mcap + 1));
   for (int a = 0; a < n_attempts; ++a) {
     const int S = replay ? o.replay[0] : (1 << a);
@@ -305,90 +413,18 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
         launch_japply_add(c, c->w, src, c->u, s);
         u = c->u;
       }
-      StopParams sp{};
-      sp.delta = delta;
-      sp.ncells = (double)c->N;
-      sp.pow10 = std::pow(10.0, o.p_order);
-      sp.tol_a = o.tol_a;
-      sp.tol_r = o.tol_r;
-      sp.window = o.avg_window;
-      sp.m_max = replay ? o.replay[1 + k] : o.m_max;
-      sp.replay = replay ? 1 : 0;
-      const double d0 = c->dd_cache[S].d[0];
-      if (fused_T && a == 0 && k == 0)
-        launch_step_init(c, fused_T, d0, sp, s);  // also writes src = G(T) and T^n
-      else
-        launch_leja_init(c, u, d0, sp, s);
-      int m = 1, qin = 0, degree = 0;
       const int forced = replay ? o.replay[1 + k] : 0;
-      int chunk = forced ? forced : std::max(4, c->last_degree + 2);
-      // launches of this substep: first term, terms computed, output buffer
-      struct Launch { int m, nterms, qout; };
-      std::vector<Launch> launches;
-      while (true) {
-        const int end = forced ? forced : std::min(M_avail, m + chunk - 1);
-        int mm = m;
-        while (mm <= end) {
-          const int nt = (c->use_pairs && mm + 1 <= end) ? 2 : 1;
-          if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size()], s);
-          if (nt == 2) launch_leja_pair(c, mm, qin, cg, s);
-          else launch_leja_term(c, mm, qin, cg, s);
-          if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size() + 1], s);
-          launches.push_back(Launch{mm, nt, qin ^ 1});
-          qin ^= 1;
-          mm += nt;
-        }
-        EREM_TRY(check_launch(c, "leja term"));
-        EREM_TRY(read_ctrl(c, s));
-        EREM_TRY(check_flags(c));
-        const Ctrl& h = *c->ctrl_h;
-        if (h.nonfinite) {
-          // the Newton vectors (or their squares) left the range of the Leja
-          // precision: the interpolation at this substep length failed
-          if (forced) return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate");
-          nonfinite_attempt = true;
-          ok = false;
-          break;
-        }
-        if (forced) {
-          degree = forced;
-          break;
-        }
-        if (h.done && !h.fail) {
-          degree = h.degree;
-          if (h.overshoot) {  // the pair that met the test at its first term
-            for (const Launch& l : launches)
-              if (l.m == degree && l.nterms == 2)
-                launch_unstep(c, l.qout, c->dd_cache[S].d[degree + 1], s);
-          }
-          break;
-        }
-        if (h.fail || end >= o.m_max) {
-          nonfinite_attempt = false;
-          ok = false;
-          break;
-        }
-        if (end >= M_avail) {  // table exhausted below m_max: extend it
-          M_avail = mcap;
-          EREM_TRY(prepare_dd(c, S, M_avail, s));
-        }
-        m = end + 1;
-        chunk = 8;
-      }
-      if (!ok) break;
-      if (o.time_terms) {
-        for (size_t j = 0; j < launches.size(); ++j) {
-          if (launches[j].m > degree) break;  // returned at once: the test had passed
-          float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, c->ev[2 * j], c->ev[2 * j + 1]) == cudaSuccess) {
-            t_terms += ms;
-            n_timed += launches[j].nterms;
-            ++n_launch_timed;
-          }
-        }
+      const StopParams sp = stop_params(c, o, delta, replay ? forced : o.m_max, replay);
+      int degree = 0;
+      bool failed = false, nonfinite = false;
+      EREM_TRY(leja_interp(c, u, (fused_T && a == 0 && k == 0) ? fused_T : nullptr, S, 1, &M_avail,
+                           mcap, sp, forced, o, &tt, &degree, &failed, &nonfinite, s));
+      if (failed) {
+        nonfinite_attempt = nonfinite;
+        ok = false;
+        break;
       }
       degrees[k] = degree;
-      c->last_degree = degree;
       if (st) st->err_est = c->ctrl_h->err;
       if (k + 1 < S) launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
     }
@@ -402,9 +438,95 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       st->degree_total = 0;
       for (int k = 0; k < 64; ++k) st->degrees[k] = k < S ? degrees[k] : 0;
       for (int k = 0; k < S; ++k) st->degree_total += degrees[k];
-      st->t_terms_ms = t_terms;
-      st->n_terms_timed = n_timed;
-      st->n_launches_timed = n_launch_timed;
+      st->t_terms_ms = tt.ms;
+      st->n_terms_timed = tt.terms;
+      st->n_launches_timed = tt.launches;
+    }
+    return EREM_OK;
+  }
+  if (nonfinite_attempt)
+    return fail(c, EREM_ENONFINITE, "non-finite Leja error estimate at every substep level");
+  return fail(c, EREM_ENOTCONV,
+              "Leja interpolation did not meet the stopping test within m_max terms after " +
+                  std::to_string(o.max_doublings) + " substep doublings");
+}
+
+// out = T^n + dt phi_1(dt J) vrhs + dt^2 phi_2(dt J) fin_w (eq. nEERMg) with
+// substep doubling; m2_forced is the replayed phi_2 degree (with o.replay).
+erem_status run_forced(erem_ctx* c, double* out, const Opts& o, int m2_forced, erem_stats* st,
+                       cudaStream_t s) {
+  const bool replay = !o.replay.empty();
+  int mcap = o.m_max;
+  if (replay) {
+    for (size_t k = 1; k < o.replay.size(); ++k) mcap = std::max(mcap, o.replay[k]);
+    mcap = std::max(mcap, m2_forced);
+  }
+  EREM_TRY(ensure_leja(c, mcap));
+  const int n_attempts = replay ? 1 : o.max_doublings + 1;
+  bool nonfinite_attempt = false;
+  int degrees[64];
+  TermTiming tt;
+  if (o.time_terms) EREM_TRY(ensure_events(c, mcap + 1));
+  for (int a = 0; a < n_attempts; ++a) {
+    const int S = replay ? o.replay[0] : (1 << a);
+    const double delta = c->dt / S;
+    int M1 = replay ? mcap : std::min(mcap, std::max(48, 2 * c->last_degree + 8));
+    int M2 = M1;
+    // phi_2 part, the same for every piece: fin_p2 = delta^2 phi_2(delta J) w
+    EREM_TRY(prepare_dd(c, S, M2, s, 2));
+    int deg2 = 0;
+    bool failed = false, nonfinite = false;
+    {
+      const StopParams sp = stop_params(c, o, delta * delta, replay ? m2_forced : o.m_max, replay);
+      EREM_TRY(leja_interp(c, c->fin_w, nullptr, S, 2, &M2, mcap, sp, replay ? m2_forced : 0, o,
+                           &tt, &deg2, &failed, &nonfinite, s));
+    }
+    if (failed) {
+      nonfinite_attempt = nonfinite;
+      continue;
+    }
+    launch_lincomb(c, c->fin_p2, 0.0, c->P, delta * delta, c->P, s);
+    EREM_TRY(prepare_dd(c, S, M1, s, 1));
+    bool ok = true;
+    for (int k = 0; k < S; ++k) {
+      const double* u = c->vrhs;
+      if (k > 0) {  // J y_k + G + k delta w
+        launch_japply_add(c, c->w, c->vrhs, c->u, s);
+        launch_lincomb(c, c->u, 1.0, c->u, k * delta, c->fin_w, s);
+        u = c->u;
+      }
+      const int forced = replay ? o.replay[1 + k] : 0;
+      const StopParams sp = stop_params(c, o, delta, replay ? forced : o.m_max, replay);
+      int degree = 0;
+      EREM_TRY(leja_interp(c, u, nullptr, S, 1, &M1, mcap, sp, forced, o, &tt, &degree, &failed,
+                           &nonfinite, s));
+      if (failed) {
+        nonfinite_attempt = nonfinite;
+        ok = false;
+        break;
+      }
+      degrees[k] = degree;
+      if (st) st->err_est = c->ctrl_h->err;
+      if (k + 1 < S) {  // y_{k+1} = y_k + delta P + the phi_2 increment
+        launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
+        launch_lincomb(c, c->w, 1.0, c->w, 1.0, c->fin_p2, s);
+      }
+    }
+    if (!ok) continue;
+    // the last piece's phi_2 increment, then out = T^n + y + delta P
+    if (S == 1) launch_lincomb(c, c->w, 0.0, c->fin_p2, 1.0, c->fin_p2, s);
+    else launch_lincomb(c, c->w, 1.0, c->w, 1.0, c->fin_p2, s);
+    launch_finish(c, out, c->Tn, c->w, c->P, delta, s, 0);
+    EREM_TRY(check_launch(c, "forced finish"));
+    if (st) {
+      st->substeps = S;
+      st->degree_total = deg2;
+      for (int k = 0; k < 64; ++k) st->degrees[k] = k < S ? degrees[k] : 0;
+      for (int k = 0; k < S; ++k) st->degree_total += degrees[k];
+      st->degree_phi2 = deg2;
+      st->t_terms_ms = tt.ms;
+      st->n_terms_timed = tt.terms;
+      st->n_launches_timed = tt.launches;
     }
     return EREM_OK;
   }
@@ -916,6 +1038,8 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (double* p : c->adj_w)
     if (p) cudaFree(p);
+  for (double* p : {c->fin_b, c->fin_w, c->fin_p2})
+    if (p) cudaFree(p);
   void* adj32[] = {c->adj_up, c->adj_icap32, c->adj_mu32, c->adj_g32[0], c->adj_g32[1],
                    c->adj_g32[2]};
   for (void* p : adj32)
@@ -1036,6 +1160,54 @@ erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk
   const bool fused = c->phys.fluid_model == 0;
   EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td, fused));
   EREM_TRY(run_phi1(c, c->vrhs, c->Tn, Td, o, st, s, fused ? Td : nullptr));
+  EREM_TRY(finish_staged(c, T, Td, s));
+  fill_interval(c, st);
+  if (st) {
+    st->t_ms = now_ms() - t0;
+    st->launches = (int)c->launches;
+  }
+  return EREM_OK;
+}
+
+erem_status erem_step_forced(erem_ctx* c, double* T, double dt, double T_in, double T_in_rate,
+                             const double* p, const double* lnk, const double* phi,
+                             const double* lam, const erem_leja_opts* opts, erem_stats* st,
+                             void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  c->launches = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->phys.fluid_model != 0)
+    return fail(c, EREM_EINVAL, "erem_step_forced needs fluid_model 0 (G affine in T_in)");
+  if (!std::isfinite(T_in) || !std::isfinite(T_in_rate))
+    return fail(c, EREM_EINVAL, "T_in and T_in_rate must be finite");
+  // replay [s, m_1..m_s, m_phi2]: the phi_1 part is parsed as for erem_step
+  erem_leja_opts o1{};
+  const erem_leja_opts* op = opts;
+  int m2 = 0;
+  if (opts && opts->replay) {
+    const int S = opts->n_replay >= 1 ? opts->replay[0] : 0;
+    if (S < 1 || S > 64 || opts->n_replay != S + 2)
+      return fail(c, EREM_EINVAL, "replay must be [s, m_1..m_s, m_phi2] with n_replay = s + 2");
+    m2 = opts->replay[S + 1];
+    if (m2 < 1 || m2 > kMaxTerms) return fail(c, EREM_EINVAL, "replay degree out of range");
+    o1 = *opts;
+    o1.n_replay = S + 1;
+    op = &o1;
+  }
+  Opts o;
+  EREM_TRY(parse_opts(c, op, &o));
+  if (!c->fin_b) {
+    EREM_TRY(dalloc_t(c, &c->fin_b, (size_t)c->Np));
+    EREM_TRY(dalloc_t(c, &c->fin_w, (size_t)c->Np));
+    EREM_TRY(dalloc_t(c, &c->fin_p2, (size_t)c->Np));
+  }
+  double* Td = nullptr;
+  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td, false));
+  launch_inflow_forced(c, T_in, T_in_rate, c->fin_b, c->fin_w, s);
+  launch_japply_add(c, c->Tn, c->fin_b, c->vrhs, s);  // G(T^n, t_n) = J T^n + b(T_in)
+  EREM_TRY(check_launch(c, "forced right-hand side"));
+  EREM_TRY(run_forced(c, Td, o, m2, st, s));
   EREM_TRY(finish_staged(c, T, Td, s));
   fill_interval(c, st);
   if (st) {
@@ -1236,7 +1408,7 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
   launch_pack(c, Td, c->Tn, s);
   launch_pack(c, lamd, c->adj_lam, s);
   EREM_TRY(prepare_dd(c, S, M, s));
-  const std::vector<double>& d = c->dd_cache[S].d;
+  const std::vector<double>& d = dd_entry(c, S).d;
   const double delta = c->dt / S;
   const double cg = c->cfoc / c->gam;
   const double scale = delta * delta / (c->gam / S);

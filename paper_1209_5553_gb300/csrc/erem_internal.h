@@ -212,6 +212,9 @@ struct erem_ctx {
   bool jlT_valid = false;
   void* adj_store = nullptr;        // forward Newton vectors q_0..q_{m-1} of one substep
   int adj_store_cap = 0;            // vectors adj_store holds
+  // erem_step_forced: b(T_in) and D_t G as full vectors (non-zero on the x = 0
+  // cells), and the phi_2 increment delta^2 phi_2(delta J) D_t G
+  double *fin_b = nullptr, *fin_w = nullptr, *fin_p2 = nullptr;
   // FP32-bulk Horner pass: upwind flags, FP32 capacities, FP32 mu, FP32 face
   // sums of the current adjoint step
   unsigned char* adj_up = nullptr;
@@ -267,6 +270,8 @@ void launch_faces(const erem_ctx* c, cudaStream_t s);
 void launch_cellJ(const erem_ctx* c, cudaStream_t s);
 void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s);
 void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cudaStream_t s);
+void launch_inflow_forced(const erem_ctx* c, double T_in, double rate, double* b, double* w,
+                          cudaStream_t s);
 void launch_japply_add(const erem_ctx* c, const double* x, const double* v, double* out,
                        cudaStream_t s);
 void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
@@ -353,6 +358,7 @@ void launch_adj_lnk(const erem_ctx* c, double* out, cudaStream_t s);
 void expm_small(int n, const double* A, double* E);
 
 // host scalar side (leja_host.cpp)
+int divided_differences_phi(int kphi, int M, const double* xi, double c, double gamma, double* d);
 void leja_table(int M, std::vector<double>* out);
 void fast_leja_table(int M, std::vector<double>* out);
 int divided_differences(int M, const double* xi, double c, double gamma, double* d);

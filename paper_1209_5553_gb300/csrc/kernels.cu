@@ -374,6 +374,22 @@ __global__ void k_japply_add(JIn J, const double* __restrict__ x, const double* 
   }
 }
 
+// Time-dependent inflow temperature, linear fluid model: the x = 0 cells'
+// b(T_in) = (LD0 + F0^+) T_in / C and w = D_t G = T_in_rate (LD0 + F0^+) / C
+// (Dirichlet conduction and inflowing advection of §3.1); the other cells of
+// both vectors stay 0.
+__global__ void k_inflow_forced(const double* __restrict__ icap, const double* __restrict__ LD0,
+                                const double* __restrict__ F0, double T_in, double rate,
+                                double* __restrict__ b, double* __restrict__ w, Geo g) {
+  const int nf = g.ny * g.nz;
+  for (int r = blockIdx.x * NT + threadIdx.x; r < nf; r += gridDim.x * NT) {
+    const int ip = g.px * r;
+    const double coef = icap[ip] * (LD0[r] + (F0[r] > 0.0 ? F0[r] : 0.0));
+    b[ip] = coef * T_in;
+    w[ip] = coef * rate;
+  }
+}
+
 // First kernel of an EREM step with the linear fluid model, where G is
 // affine in T: G = J T + b exactly (b non-zero only at the x = 0 cells).
 // One pass reads the caller's T (unpadded, left in place for the final
@@ -2123,6 +2139,14 @@ void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cud
   ++c->launches;
   k_rhs<<<blocks_cells(c), NT, 0, s>>>(face_in(c), T, G, geo_of(c), phys_of(c), set_yinf,
                                        c->red_part, c->red_cnt, c->ctrl);
+}
+
+void launch_inflow_forced(const erem_ctx* c, double T_in, double rate, double* b, double* w,
+                          cudaStream_t s) {
+  ++c->launches;
+  const int nf = c->ny * c->nz;
+  k_inflow_forced<<<std::max(1, std::min(c->red_blocks, (nf + NT - 1) / NT)), NT, 0, s>>>(
+      c->icap, c->LD0, c->F0, T_in, rate, b, w, geo_of(c));
 }
 
 void launch_japply_add(const erem_ctx* c, const double* x, const double* v, double* out,

@@ -162,14 +162,19 @@ void leja_table(int M, std::vector<double>* out) {
 // non-negative (W has a non-negative off-diagonal), so the squarings
 // add terms of one sign and keep relative accuracy even for the tiny
 // entries far below the diagonal.
-int divided_differences(int M, const double* xi, double c, double gamma, double* d) {
-  if (M < 0 || !xi || !d || !std::isfinite(c) || !std::isfinite(gamma) || gamma <= 0.0) return -1;
-  const int n = M + 2;
+//
+// phi_2 (and phi_k) the same way: phi_k(z) = exp[0, .., 0, z] with k zeros,
+// so the diagonal starts with k zeros, the subdiagonal with k ones, and the
+// entry (j+k, 0) is the divided difference d_j of phi_k.
+int divided_differences_phi(int kphi, int M, const double* xi, double c, double gamma, double* d) {
+  if (kphi < 1 || kphi > 4 || M < 0 || !xi || !d || !std::isfinite(c) || !std::isfinite(gamma) ||
+      gamma <= 0.0)
+    return -1;
+  const int n = M + 1 + kphi;
   std::vector<double> diag(n), sub(n, 0.0);  // sub[k] = W(k, k-1)
-  diag[0] = 0.0;
-  for (int k = 1; k < n; ++k) {
-    diag[k] = c + gamma * xi[k - 1];
-    sub[k] = (k == 1) ? 1.0 : gamma;
+  for (int k = 0; k < n; ++k) {
+    diag[k] = k < kphi ? 0.0 : c + gamma * xi[k - kphi];
+    if (k > 0) sub[k] = (k <= kphi) ? 1.0 : gamma;
   }
   double norm = 0.0;  // ||W||_1: column k holds diag[k] and sub[k+1]
   for (int k = 0; k < n; ++k) norm = std::max(norm, std::fabs(diag[k]) + (k + 1 < n ? sub[k + 1] : 0.0));
@@ -213,7 +218,7 @@ int divided_differences(int M, const double* xi, double c, double gamma, double*
     std::swap(E, F);
   }
   for (int j = 0; j <= M; ++j) {
-    const int i = j + 1;
+    const int i = j + kphi;
     if (s == 0) {
       d[j] = E[(size_t)i * n];
     } else {
@@ -223,6 +228,10 @@ int divided_differences(int M, const double* xi, double c, double gamma, double*
     }
   }
   return 0;
+}
+
+int divided_differences(int M, const double* xi, double c, double gamma, double* d) {
+  return divided_differences_phi(1, M, xi, c, gamma, d);
 }
 
 // exp(A) of a small dense matrix (row-major n x n): a Taylor polynomial of
@@ -271,6 +280,11 @@ extern "C" int erem_leja_points(int M, double* xi) {
   erem::leja_table(M, &t);
   std::copy(t.begin(), t.end(), xi);
   return 0;
+}
+
+extern "C" int erem_phi2_divided_differences(int M, const double* xi, double c, double gamma,
+                                             double* d) {
+  return erem::divided_differences_phi(2, M, xi, c, gamma, d);
 }
 
 extern "C" int erem_fast_leja_points(int M, double* xi) {

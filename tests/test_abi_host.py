@@ -129,6 +129,17 @@ def test_host_leja_points_match_oracle(E):
     assert np.max(np.abs(a - b)) < 1e-14
 
 
+@pytest.mark.parametrize("c,gamma", [(-20.0, 10.0), (-3.0, 1.5), (-60.0, 30.0), (-1e-6, 1e-8)])
+def test_host_phi2_divided_differences_match_oracle(E, c, gamma):
+    from oracle import nonauto
+
+    xi = leja.leja_points(120)
+    a = E.erem_phi2_divided_differences(xi, c, gamma)
+    b = nonauto.phi2_divided_differences(xi, c, gamma)
+    big = np.abs(b) > 1e-280
+    assert np.max(np.abs(a[big] - b[big]) / np.abs(b[big])) < 1e-11
+
+
 def test_host_fast_leja_points_match_oracle(E):
     # dyadic points: the library's incremental candidate update and the
     # oracle's fresh enumeration choose bit-identical points
