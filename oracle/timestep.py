@@ -5,6 +5,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 * EREM (eq. ``EERM``): T^{n+1} = T^n + tau phi_1(tau J_n) G(T^n, p^n), with
   J_n = D_T G(T^n, p^n) and phi_1 from real Leja interpolation (§4.2).
 * ROSM(gamma) (eq. ``ROS``): T^{n+1} = T^n + tau (I - tau gamma J_n)^{-1} G(T^n).
+* ROS3p (Table ``ros3``), the same form with three stages.
 * ROS2(1) (eq. ``ROSMh`` with the coefficients of Table ``ros2``), autonomous
   form: (I/(tau gamma) - J) k_i = G(T + sum_{j<i} a_ij k_j) - sum_{j<i} c_ij/tau k_j,
   T^{n+1} = T^n + sum_i b_i k_i.  The diagonal c_ii of the printed table do
@@ -82,6 +83,16 @@ ROS2_B = (3.0 / (2.0 * ROS2_GAMMA), 1.0 / (2.0 * ROS2_GAMMA))
 ROS2_BHAT = (1.0 / ROS2_GAMMA, 0.0)
 
 
+# ROS3p coefficients (Table ros3): gamma = (3 + sqrt 3)/6; a21 = a31 = 1/gamma,
+# a32 = 0; c21 = 1/gamma^2, c31 = 2 sqrt 3, c32 = sqrt 3; b = (2, 1/sqrt 3,
+# 1 - 1/sqrt 3).  The embedded weights are taken as printed.
+ROS3P_GAMMA = (3.0 + math.sqrt(3.0)) / 6.0
+ROS3P_A = ((1.0 / ROS3P_GAMMA,), (1.0 / ROS3P_GAMMA, 0.0))            # a21; a31, a32
+ROS3P_C = ((1.0 / ROS3P_GAMMA**2,), (2.0 * math.sqrt(3.0), math.sqrt(3.0)))  # c21; c31, c32
+ROS3P_B = (2.0, 1.0 / math.sqrt(3.0), 1.0 - 1.0 / math.sqrt(3.0))
+ROS3P_BHAT = (2.113248654051871, 1.0, 0.4226497308103742)
+
+
 def stage_matrix(J, tau: float, gamma: float):
     """I / (tau gamma) - J, the matrix of every Rosenbrock stage."""
     n = J.shape[0]
@@ -95,6 +106,67 @@ def rosm_step(prob: HeatProblem, T, tau: float, gamma: float):
     rhs = tau * prob.G(T)
     A = (sp.identity(T.size, format="csr") - tau * gamma * J).tocsc()
     return T + spla.spsolve(A, rhs)
+
+
+def ros3p_step(prob: HeatProblem, T, tau: float, embedded: bool = False):
+    """ROS3p step (eq. ``ROSMh``, Table ``ros3``, autonomous form as for
+    ROS2(1)); with ``embedded`` also returns the second-order solution."""
+    T = np.asarray(T, np.float64).reshape(-1)
+    J = prob.J(T)
+    lu = spla.splu(stage_matrix(J, tau, ROS3P_GAMMA))
+    k = [lu.solve(prob.G(T))]
+    for i in (1, 2):
+        Y = T + sum(a * kj for a, kj in zip(ROS3P_A[i - 1], k))
+        rhs = prob.G(Y) - sum((c / tau) * kj for c, kj in zip(ROS3P_C[i - 1], k))
+        k.append(lu.solve(rhs))
+    y = T + sum(b * ki for b, ki in zip(ROS3P_B, k))
+    if embedded:
+        return y, T + sum(b * ki for b, ki in zip(ROS3P_BHAT, k))
+    return y
+
+
+@dataclass
+class AdaptiveResult:
+    T: np.ndarray
+    dts: list            # accepted step lengths
+    rejected: int
+    errs: list           # scaled error of every attempt, in order
+
+
+def ros_integrate(prob: HeatProblem, T, t_end: float, dt0: float, scheme: str = "ros3p",
+                  tol_a: float = 1e-6, tol_r: float = 1e-6, max_steps: int = 100000):
+    """Adaptive Rosenbrock integration over [0, t_end] with the embedded
+    solution of eq. ``ROSMh`` and the standard error control and step-size
+    prediction (the paper points to Hairer and Wanner): err = RMS(y - y_hat)
+    / (tol_a + tol_r ||T^n||_inf) (the uniform scale of §4.2); a step is
+    accepted when err <= 1; the next length is dt min(facmax, max(0.2,
+    0.9 err^(-1/p))), p the order of the scheme (2 for ROS2(1), 3 for ROS3p),
+    with facmax = 5, or 1 right after a rejection; the last step ends at
+    t_end."""
+    step = {"ros2": ros2_step, "ros3p": ros3p_step}[scheme]
+    p = {"ros2": 2, "ros3p": 3}[scheme]
+    T = np.asarray(T, np.float64).reshape(-1).copy()
+    t, dt, facmax = 0.0, dt0, 5.0
+    dts, errs, rejected = [], [], 0
+    while t < t_end and len(dts) + rejected < max_steps:
+        h = min(dt, t_end - t)
+        y, yh = step(prob, T, h, embedded=True)
+        sc = tol_a + tol_r * float(np.max(np.abs(T)))
+        err = float(np.sqrt(np.mean((y - yh) ** 2))) / sc
+        errs.append(err)
+        pred = math.inf if err == 0.0 else 0.9 * err ** (-1.0 / p)
+        if err <= 1.0:
+            T = y
+            t = t_end if h == t_end - t else t + h
+            dts.append(h)
+            grow = min(facmax, max(0.2, pred))
+            facmax = 5.0
+        else:
+            rejected += 1
+            grow = min(1.0, max(0.2, pred))
+            facmax = 1.0
+        dt = h * grow
+    return AdaptiveResult(T, dts, rejected, errs)
 
 
 def ros2_step(prob: HeatProblem, T, tau: float, embedded: bool = False):

@@ -162,6 +162,101 @@ def test_ros2_orders_two_and_embedded_one():
     assert all(1.9 < o < 2.1 for o in _order(emb, taus))
 
 
+def test_ros3p_table_matches_printed_coefficients():
+    here = os.path.join(os.path.dirname(__file__), "golden", "ros3p_table.txt")
+    vals = {}
+    for line in open(here):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    assert ts.ROS3P_GAMMA == pytest.approx(vals["gamma"], rel=1e-15)
+    assert ts.ROS3P_A[0][0] == pytest.approx(vals["a21"], rel=1e-15)
+    assert ts.ROS3P_A[1] == pytest.approx((vals["a31"], vals["a32"]), rel=1e-15)
+    assert ts.ROS3P_C[0][0] == pytest.approx(vals["c21"], rel=1e-15)
+    assert ts.ROS3P_C[1] == pytest.approx((vals["c31"], vals["c32"]), rel=1e-15)
+    assert ts.ROS3P_B == pytest.approx((vals["b1"], vals["b2"], vals["b3"]), rel=1e-15)
+    assert ts.ROS3P_BHAT == (vals["bhat1"], vals["bhat2"], vals["bhat3"])
+    # the printed diagonal c_ii are 1/gamma (they do not enter the sums over j < i)
+    assert vals["c11"] == pytest.approx(1.0 / ts.ROS3P_GAMMA, rel=1e-14)
+
+
+def _ros3p_R(z):
+    # the scheme on y' = lam y (z = tau lam), from its defining stage
+    # equations: (1/gamma - z) k_i = z y + sum_j (z a_ij - c_ij) k_j
+    g = ts.ROS3P_GAMMA
+    k = []
+    for i in range(3):
+        s = z
+        for j in range(i):
+            s += (z * ts.ROS3P_A[i - 1][j] - ts.ROS3P_C[i - 1][j]) * k[j]
+        k.append(s / (1.0 / g - z))
+    return 1.0 + sum(b * ki for b, ki in zip(ts.ROS3P_B, k))
+
+
+def test_ros3p_stability_function_is_third_order_and_a_stable():
+    # R(z) - e^z = O(z^4) on the real line and in the complex plane; |R| <= 1
+    # on the negative real axis and the imaginary axis (A-stable, §3.2.3)
+    for z in (1e-2, -1e-2, 1e-2j, -2e-2 + 1e-2j):
+        r = _ros3p_R(z)
+        assert abs(r - np.exp(z)) < 0.5 * abs(z) ** 4, z
+        assert abs(r - np.exp(z)) > 1e-3 * abs(z) ** 4   # not fourth order
+    # A-stable but not L-stable: |R(-inf)| is about 0.73
+    assert 0.5 < abs(_ros3p_R(-1e9)) < 1.0
+    for x in np.concatenate([-np.logspace(-3, 6, 200), 1j * np.logspace(-3, 6, 200)]):
+        assert abs(_ros3p_R(x)) <= 1.0 + 1e-12, x
+
+
+def test_ros3p_orders_three_and_embedded_two():
+    g, prob, wl = _workload_problem(10, fluid_model=1)
+    T0 = _smooth_T0(g)
+    t_end = 0.002
+    taus = [t_end / 4, t_end / 8, t_end / 16, t_end / 32]
+
+    def run(tau):
+        T = T0.copy()
+        for _ in range(round(t_end / tau)):
+            T = ts.ros3p_step(prob, T, tau)
+        return T
+
+    ref = run(taus[-1] / 4)
+    errs = [np.linalg.norm(run(t) - ref) for t in taus]
+    assert min(_order(errs, taus)) > 2.8, (errs, _order(errs, taus))
+    exact = [_run(prob, T0, t / 32, 32) for t in taus]
+    emb = [np.linalg.norm(ts.ros3p_step(prob, T0, t, embedded=True)[1] - e) for t, e in zip(taus, exact)]
+    # embedded order 2: local error O(tau^3), reached from above as tau falls
+    o = _order(emb, taus)
+    assert all(2.9 < x < 3.6 for x in o) and o[-1] < o[0] and o[-1] < 3.25, o
+
+
+@pytest.mark.parametrize("scheme,p", [("ros2", 2), ("ros3p", 3)])
+def test_adaptive_rosenbrock_control(scheme, p):
+    # every run ends exactly at t_end, accepts exactly the attempts with
+    # err <= 1 and the global error falls with the tolerance.  ROS2(1): the
+    # error follows the tolerance and the accepted steps grow like
+    # tol^(-1/2).  ROS3p: on this stiff problem its embedded pair under-reports
+    # the local error at long steps (the embedded and main solutions err
+    # alike: 5e-6 estimated against 3.4e-5 true at dt = 2.5e-3), so only
+    # the monotone decrease is required
+    g, prob, wl = _workload_problem(10, fluid_model=1)
+    T0 = _smooth_T0(g)
+    t_end = 0.01
+    ref = _run(prob, T0, t_end / 400, 400)
+    runs = {tol: ts.ros_integrate(prob, T0, t_end, 1e-4, scheme, tol, tol) for tol in (1e-4, 1e-6)}
+    errs = {}
+    for tol, r in runs.items():
+        assert abs(sum(r.dts) - t_end) < 1e-15
+        assert sum(e <= 1.0 for e in r.errs) == len(r.dts) and len(r.errs) == len(r.dts) + r.rejected
+        errs[tol] = np.max(np.abs(r.T - ref)) / (1 + np.max(np.abs(ref)))
+    assert errs[1e-6] < errs[1e-4]
+    if scheme == "ros2":
+        assert all(errs[tol] < 30.0 * tol for tol in errs), errs
+        ratio = len(runs[1e-6].dts) / len(runs[1e-4].dts)
+        assert 0.5 * 100 ** (1 / p) < ratio < 2.0 * 100 ** (1 / p), ratio
+    # a too-large first step is rejected and then shrinks
+    r = ts.ros_integrate(prob, T0, t_end, t_end, scheme, 1e-8, 1e-8)
+    assert r.rejected >= 1 and r.errs[0] > 1.0 and r.dts[0] < t_end
+
+
 def _one_cell():
     g = fv.Grid(2, 1, 1)
     ph = fv.Physics(rhoc_f=2.0, rhoc_s=2.0, head_left=1.0, head_right=0.0, T_inflow=70.0)
@@ -192,6 +287,8 @@ def test_stability_functions_on_a_single_cell(tau):
     want = (1 + (1 - 2 * gg) * z + (gg * gg - 2 * gg + 0.5) * z * z) / (1 - gg * z) ** 2
     r2 = ts.ros2_step(prob, y0, tau)
     assert (r2[0] - Tstar) == pytest.approx(want * (y0[0] - Tstar), rel=1e-12)
+    r3 = ts.ros3p_step(prob, y0, tau)
+    assert (r3[0] - Tstar) == pytest.approx(_ros3p_R(z) * (y0[0] - Tstar), rel=1e-12)
 
 
 def test_sequential_coupling_runs_and_cg_pressure_agrees():
