@@ -281,6 +281,39 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
     return out
 
 
+def run_forced(E, torch, wl, steps, warmup, dev):
+    """The same workload with a time-dependent inflow temperature
+    T_in(t) = 60 + 20 sin(2 pi t) (eq. nEERMg: phi_1 and phi_2 per step),
+    FP32-bulk."""
+    import math
+
+    ctx, T, _ = gpu_context(E, torch, wl, "fp32_bulk", dev)
+    opts = E.leja_opts(tol=wl.tol)
+    tin = lambda t: 60.0 + 20.0 * math.sin(2 * math.pi * t)
+    rate = lambda t: 40.0 * math.pi * math.cos(2 * math.pi * t)
+    k = 0
+    for _ in range(warmup):
+        ctx.erem_step_forced(T, wl.dt, tin(k * wl.dt), rate(k * wl.dt), opts=opts)
+        k += 1
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    terms1, terms2 = [], []
+    e0.record(stream)
+    for _ in range(steps):
+        st = ctx.erem_step_forced(T, wl.dt, tin(k * wl.dt), rate(k * wl.dt), opts=opts)
+        terms1.append(st.degree_total - st.degree_phi2)
+        terms2.append(st.degree_phi2)
+        k += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"ms": e0.elapsed_time(e1), "phi1_terms_per_step": float(np.mean(terms1)),
+           "phi2_terms_per_step": float(np.mean(terms2))}
+    ctx.close()
+    return out
+
+
 def run_krylov(E, torch, wl, steps, warmup, dev):
     """The same steps with phi_1 by Krylov substeps (FP64, §4.1)."""
     ctx, T, _ = gpu_context(E, torch, wl, "fp64", dev)
@@ -462,6 +495,12 @@ def main(args):
             "terms_per_step": float(np.mean([sum(s[1:]) for s in rf["degrees"]])),
             "terms_per_step_exact_points": float(np.mean([sum(s[1:]) for s in r32["degrees"]])),
             "rel_l2_vs_exact_points": float(np.linalg.norm(rf["T"] - r32["T"]) / np.linalg.norm(r32["T"]))}
+        rfo = run_forced(E, torch, wl, K, Wu, dev)
+        msfo, valuefo = aggregate(rfo["ms"], N, K, world, dev)
+        line["forced_fp32_bulk"] = {
+            "value": valuefo, "ms_per_step": msfo / K, "inflow": "T_in(t) = 60 + 20 sin(2 pi t)",
+            "phi1_terms_per_step": rfo["phi1_terms_per_step"],
+            "phi2_terms_per_step": rfo["phi2_terms_per_step"]}
         if not args.no_krylov:
             rk = run_krylov(E, torch, wl, K, Wu, dev)
             msk, valuek = aggregate(rk["ms"], N, K, world, dev)
@@ -512,7 +551,8 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
         if scheme == "erem":
             s2 = ctx.erem_step(T, wl.dt, p, lnk, phi, lam, opts=opts)
         else:
-            s2 = ctx.rosm_step(T, wl.dt, E.EREM_ROS2, p, lnk, phi, lam, lin_tol=1e-10, maxit=20000)
+            code = E.EREM_ROS3P if scheme == "ros3p" else E.EREM_ROS2
+            s2 = ctx.rosm_step(T, wl.dt, code, p, lnk, phi, lam, lin_tol=1e-10, maxit=20000)
         return s1, s2
 
     for _ in range(warmup):
@@ -553,7 +593,7 @@ def main_coupled(args):
     K, Wu = args.steps, args.warmup
     runs = {}
     for key, scheme, prec in (("erem_fp32_bulk", "erem", "fp32_bulk"), ("erem_fp64", "erem", "fp64"),
-                              ("ros2_fp64", "ros2", "fp64")):
+                              ("ros2_fp64", "ros2", "fp64"), ("ros3p_fp64", "ros3p", "fp64")):
         r = run_coupled(E, torch, wl, scheme, prec, K, Wu, dev)
         ms, value = aggregate(r["ms"], wl.n, K, world, dev)
         r.update(ms=ms, value=value)

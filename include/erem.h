@@ -67,8 +67,9 @@ typedef enum {
 typedef enum { EREM_FP64 = 0, EREM_FP32_BULK = 1 } erem_precision;
 
 /* Rosenbrock-type schemes of §3.2: ROSM(1) and ROSM(1/2) (eq. ROS with
- * gamma = 1 and 1/2) and the two-stage ROS2(1) (eq. ROSMh, Table ros2). */
-typedef enum { EREM_ROSM1 = 0, EREM_ROSM_HALF = 1, EREM_ROS2 = 2 } erem_rosm_scheme;
+ * gamma = 1 and 1/2), the two-stage ROS2(1) (eq. ROSMh, Table ros2) and
+ * the three-stage ROS3p (Table ros3). */
+typedef enum { EREM_ROSM1 = 0, EREM_ROSM_HALF = 1, EREM_ROS2 = 2, EREM_ROS3P = 3 } erem_rosm_scheme;
 
 typedef struct {
   int dim;          /* 2 or 3                                  */
@@ -196,12 +197,6 @@ EREM_API erem_status erem_step(erem_ctx* ctx, double* T, const double* p,
                       const erem_leja_opts* opts, erem_stats* stats,
                       void* stream);
 
-/* One Rosenbrock-type step (§3.2): ROSM(gamma) (eq. ROS)
- *   T <- T + dt (I - dt gamma J_n)^{-1} G(T)
- * or ROS2(1) (eq. ROSMh with Table ros2, autonomous form).  Every stage
- * system (I/(dt gamma) - J_n) k = r is solved by Jacobi-preconditioned
- * BiCGSTAB in FP64 to ||r - A k||_2 <= lin_tol ||r||_2 (maxit iterations).
- * Fields as erem_step.  Errors: EINVAL, ENOTCONV, ENONFINITE, ECUDA. */
 /* One step of the non-autonomous EREM scheme (eq. nEERMg, §3.2) for the
  * heat problem whose inflow temperature depends on time:
  *   T <- T + dt phi_1(dt J) G(T, t_n) + dt^2 phi_2(dt J) D_t G(T, t_n),
@@ -225,11 +220,51 @@ EREM_API erem_status erem_step_forced(erem_ctx* ctx, double* T, double dt, doubl
                                       const erem_leja_opts* opts, erem_stats* stats,
                                       void* stream);
 
+/* One Rosenbrock-type step (§3.2): ROSM(gamma) (eq. ROS)
+ *   T <- T + dt (I - dt gamma J_n)^{-1} G(T)
+ * or the s-stage form of eq. ROSMh (autonomous: the gamma_i D_t f terms
+ * vanish; the printed diagonal c_ii do not enter the sums over j < i) with
+ * Table ros2 (ROS2(1), two stages) or Table ros3 (ROS3p, three stages):
+ *   (I/(dt gamma) - J_n) k_i = G(T + sum_{j<i} a_ij k_j) - sum_{j<i} c_ij/dt k_j,
+ *   T <- T + sum_i b_i k_i.
+ * Every stage system is solved by Jacobi-preconditioned BiCGSTAB in FP64 to
+ * ||r - A k||_2 <= lin_tol ||r||_2 (maxit iterations).  For ROS2(1) and
+ * ROS3p, stats->err_est = RMS over the cells of y - y_hat, the difference to
+ * the embedded solution (weights b_hat of the tables: orders 1 and 2).
+ * Fields as erem_step.
+ * Errors: EINVAL, ENOTCONV, ENONFINITE, ECUDA. */
 EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
                       const double* lnk, const double* phi,
                       const double* lambda, double dt,
                       erem_rosm_scheme scheme, double lin_tol, int maxit,
                       erem_stats* stats, void* stream);
+
+/* Adaptive Rosenbrock integration of the stored state (erem_set_state or the
+ * last step's fields) over [0, t_end] with ROS2(1) or ROS3p and the error
+ * control the paper points to (§3.2.3: Hairer-Wanner): each attempt of
+ * length h is one rosm_step; err = RMS(y - y_hat) / (tol_a + tol_r
+ * ||T^n||_inf); the attempt is accepted when err <= 1, else T is restored;
+ * the next length is h min(facmax, max(0.2, 0.9 err^(-1/p))) with p the
+ * scheme's order (2 or 3) and facmax = 5, or 1 right after a rejection; the
+ * last step ends at t_end.
+ *   T [N] in/out; dt0 > 0 the first length; max_attempts bounds accepted +
+ *   rejected attempts (ENOTCONV when t_end is not reached, T then holds the
+ *   state at the last accepted time, stats->t_reached).
+ *   dts (may be NULL) receives the accepted lengths (capacity max_attempts).
+ * Errors: EINVAL (scheme not ROS2/ROS3P, bad tolerances or lengths),
+ * ENOTCONV, and those of rosm_step. */
+typedef struct {
+  int accepted, rejected;
+  int lin_iters;        /* BiCGSTAB iterations over all attempts */
+  int launches;
+  double t_reached;     /* t_end unless max_attempts ran out     */
+  double dt_min, dt_max;
+  double t_ms;
+} erem_adapt_stats;
+EREM_API erem_status rosm_integrate(erem_ctx* ctx, double* T, double t_end, double dt0,
+                                    erem_rosm_scheme scheme, double tol_a, double tol_r,
+                                    double lin_tol, int maxit, int max_attempts, double* dts,
+                                    erem_adapt_stats* stats, void* stream);
 
 /* Steady pressure solve that allocates nothing (the paper has no
  * counterpart: this entry point exists for callers that cannot allocate).

@@ -142,15 +142,22 @@ def ros_integrate(prob: HeatProblem, T, t_end: float, dt0: float, scheme: str = 
     accepted when err <= 1; the next length is dt min(facmax, max(0.2,
     0.9 err^(-1/p))), p the order of the scheme (2 for ROS2(1), 3 for ROS3p),
     with facmax = 5, or 1 right after a rejection; the last step ends at
-    t_end."""
+    t_end.  ``prob`` is a HeatProblem or a function of T^n giving the
+    problem of that step (fluid laws that depend on T re-evaluated per step).
+
+    For the linear heat model the ROS3p difference y - y_hat vanishes
+    identically: there the second stage is (1 - 1/gamma) k_1 and the printed
+    b - b_hat annihilates that combination, so only nonlinear terms give
+    ROS3p an error estimate."""
     step = {"ros2": ros2_step, "ros3p": ros3p_step}[scheme]
+    prob_of = prob if callable(prob) else (lambda _T: prob)
     p = {"ros2": 2, "ros3p": 3}[scheme]
     T = np.asarray(T, np.float64).reshape(-1).copy()
     t, dt, facmax = 0.0, dt0, 5.0
     dts, errs, rejected = [], [], 0
     while t < t_end and len(dts) + rejected < max_steps:
         h = min(dt, t_end - t)
-        y, yh = step(prob, T, h, embedded=True)
+        y, yh = step(prob_of(T), T, h, embedded=True)
         sc = tol_a + tol_r * float(np.max(np.abs(T)))
         err = float(np.sqrt(np.mean((y - yh) ** 2))) / sc
         errs.append(err)

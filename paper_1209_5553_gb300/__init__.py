@@ -30,7 +30,7 @@ EREM_OK, EREM_EINVAL, EREM_ENOMEM, EREM_ENOTCONV, EREM_ETIMEOUT, EREM_ENONFINITE
 STATUS_NAMES = {0: "EREM_OK", 1: "EREM_EINVAL", 2: "EREM_ENOMEM", 3: "EREM_ENOTCONV",
                 4: "EREM_ETIMEOUT", 5: "EREM_ENONFINITE", 6: "EREM_ECUDA"}
 EREM_FP64, EREM_FP32_BULK = 0, 1
-EREM_ROSM1, EREM_ROSM_HALF, EREM_ROS2 = 0, 1, 2
+EREM_ROSM1, EREM_ROSM_HALF, EREM_ROS2, EREM_ROS3P = 0, 1, 2, 3
 EREM_LEJA_EXACT, EREM_LEJA_FAST = 0, 1
 
 
@@ -72,6 +72,12 @@ class erem_stats(ctypes.Structure):
     def schedule_forced(self):
         """[s, m_1..m_s, m_phi2] of erem_step_forced (its replay format)."""
         return self.schedule + [self.degree_phi2]
+
+
+class erem_adapt_stats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int), ("rejected", ctypes.c_int), ("lin_iters", ctypes.c_int),
+                ("launches", ctypes.c_int), ("t_reached", ctypes.c_double),
+                ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double), ("t_ms", ctypes.c_double)]
 
 
 class erem_krylov_opts(ctypes.Structure):
@@ -139,6 +145,8 @@ _sigs = {
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_fast_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_phi2_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
+    "rosm_integrate": (_I, [_P, _P, _D, _D, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_D),
+                            ctypes.POINTER(erem_adapt_stats), _P]),
     "erem_step_forced": (_I, [_P, _P, _D, _D, _D, _P, _P, _P, _P, ctypes.POINTER(erem_leja_opts),
                               ctypes.POINTER(erem_stats), _P]),
     "erem_set_leja_points": (_I, [_P, _I]),
@@ -305,6 +313,19 @@ def erem_step_forced(ctx, n, T, dt, T_in, T_in_rate, p=None, lnk=None, phi=None,
                                       ctypes.byref(opts) if opts is not None else None,
                                       ctypes.byref(st), _stream(stream)))
     return st
+
+
+def rosm_integrate(ctx, n, T, t_end, dt0, scheme=EREM_ROS2, tol_a=1e-6, tol_r=1e-6,
+                   lin_tol=1e-10, maxit=10000, max_attempts=100000, stream=None):
+    """Adaptive ROS2(1)/ROS3p over [0, t_end]; returns (erem_adapt_stats,
+    accepted step lengths)."""
+    st = erem_adapt_stats()
+    dts = np.zeros(max_attempts)
+    _check(ctx, _lib.rosm_integrate(ctx, _ptr(T, n), float(t_end), float(dt0), int(scheme),
+                                    float(tol_a), float(tol_r), float(lin_tol), int(maxit),
+                                    int(max_attempts), dts.ctypes.data_as(ctypes.POINTER(_D)),
+                                    ctypes.byref(st), _stream(stream)))
+    return st, dts[: st.accepted].copy()
 
 
 def rosm_step(ctx, n, T, dt, scheme=EREM_ROS2, p=None, lnk=None, phi=None, lam=None,
@@ -572,6 +593,11 @@ class Context:
 
     def erem_step(self, T, dt, p=None, lnk=None, phi=None, lam=None, opts=None, stream=None):
         return erem_step(self._h, self.n, T, dt, p, lnk, phi, lam, opts, stream)
+
+    def rosm_integrate(self, T, t_end, dt0, scheme=EREM_ROS2, tol_a=1e-6, tol_r=1e-6,
+                       lin_tol=1e-10, maxit=10000, max_attempts=100000, stream=None):
+        return rosm_integrate(self._h, self.n, T, t_end, dt0, scheme, tol_a, tol_r, lin_tol, maxit,
+                              max_attempts, stream)
 
     def erem_step_forced(self, T, dt, T_in, T_in_rate, p=None, lnk=None, phi=None, lam=None,
                          opts=None, stream=None):

@@ -1038,7 +1038,7 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (double* p : c->adj_w)
     if (p) cudaFree(p);
-  for (double* p : {c->fin_b, c->fin_w, c->fin_p2})
+  for (double* p : {c->fin_b, c->fin_w, c->fin_p2, c->ada_save})
     if (p) cudaFree(p);
   void* adj32[] = {c->adj_up, c->adj_icap32, c->adj_mu32, c->adj_g32[0], c->adj_g32[1],
                    c->adj_g32[2]};
@@ -1224,7 +1224,8 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
   const double t0 = now_ms();
   c->launches = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  if (scheme != EREM_ROSM1 && scheme != EREM_ROSM_HALF && scheme != EREM_ROS2)
+  if (scheme != EREM_ROSM1 && scheme != EREM_ROSM_HALF && scheme != EREM_ROS2 &&
+      scheme != EREM_ROS3P)
     return fail(c, EREM_EINVAL, "unknown Rosenbrock scheme");
   if (!(lin_tol > 0.0) || maxit < 1) return fail(c, EREM_EINVAL, "lin_tol > 0 and maxit >= 1");
   EREM_TRY(ensure_krylov(c));
@@ -1232,6 +1233,7 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
   EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, false, s, &Td));
   int it_total = 0, it = 0;
   double res = 0.0, r = 0.0;
+  bool embedded = false;
   if (scheme == EREM_ROS2) {
     // ROS2(1), Table ros2: gamma = 1 + 1/sqrt(2), a21 = 1/gamma, c21 = 2/gamma,
     // b = (3/(2 gamma), 1/(2 gamma)); stage matrix I/(dt gamma) - J.
@@ -1251,9 +1253,54 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
     EREM_TRY(bicg_solve(c, c->vin, sigma, lin_tol, maxit, s, &it, &r));
     it_total += it;
     res = std::max(res, r);
-    // T^{n+1} = T^n + b1 k1 + b2 k2
+    // T^{n+1} = T^n + b1 k1 + b2 k2; embedded y_hat = T^n + k1 / gamma
     launch_lincomb(c, c->u, b1, k1, b2, c->kv[0], s);
     launch_finish(c, Td, c->Tn, nullptr, c->u, 1.0, s);
+    launch_lincomb(c, c->vin, b1 - 1.0 / gam, k1, b2, c->kv[0], s);
+    launch_sumsq(c, c->vin, s);
+    embedded = true;
+  } else if (scheme == EREM_ROS3P) {
+    // ROS3p, Table ros3: gamma = (3 + sqrt 3)/6, a21 = a31 = 1/gamma, a32 = 0,
+    // c21 = 1/gamma^2, c31 = 2 sqrt 3, c32 = sqrt 3, b = (2, 1/sqrt 3,
+    // 1 - 1/sqrt 3); embedded weights as printed
+    const double r3 = std::sqrt(3.0);
+    const double gam = (3.0 + r3) / 6.0;
+    const double a21 = 1.0 / gam, a31 = 1.0 / gam, c21 = 1.0 / (gam * gam), c31 = 2.0 * r3,
+                 c32 = r3;
+    const double b[3] = {2.0, 1.0 / r3, 1.0 - 1.0 / r3};
+    const double bh[3] = {2.113248654051871, 1.0, 0.4226497308103742};
+    const double sigma = 1.0 / (dt * gam);
+    double* k1 = c->kv[10];
+    double* k2 = c->w;
+    double* Y = c->kv[11];
+    EREM_TRY(bicg_solve(c, c->vrhs, sigma, lin_tol, maxit, s, &it, &r));
+    it_total += it;
+    res = std::max(res, r);
+    launch_lincomb(c, k1, 1.0, c->kv[0], 0.0, c->kv[0], s);
+    launch_lincomb(c, Y, 1.0, c->Tn, a21, k1, s);
+    launch_rhs(c, Y, c->vin, 0, s);
+    launch_lincomb(c, c->vin, 1.0, c->vin, -c21 / dt, k1, s);
+    EREM_TRY(check_launch(c, "ros3p stage 2"));
+    EREM_TRY(bicg_solve(c, c->vin, sigma, lin_tol, maxit, s, &it, &r));
+    it_total += it;
+    res = std::max(res, r);
+    launch_lincomb(c, k2, 1.0, c->kv[0], 0.0, c->kv[0], s);
+    launch_lincomb(c, Y, 1.0, c->Tn, a31, k1, s);  // a32 = 0
+    launch_rhs(c, Y, c->vin, 0, s);
+    launch_lincomb(c, c->vin, 1.0, c->vin, -c31 / dt, k1, s);
+    launch_lincomb(c, c->vin, 1.0, c->vin, -c32 / dt, k2, s);
+    EREM_TRY(check_launch(c, "ros3p stage 3"));
+    EREM_TRY(bicg_solve(c, c->vin, sigma, lin_tol, maxit, s, &it, &r));
+    it_total += it;
+    res = std::max(res, r);
+    // T^{n+1} = T^n + sum b_i k_i (k3 in kv[0]); y - y_hat = sum (b_i - bh_i) k_i
+    launch_lincomb(c, c->u, b[0], k1, b[1], k2, s);
+    launch_lincomb(c, c->u, 1.0, c->u, b[2], c->kv[0], s);
+    launch_finish(c, Td, c->Tn, nullptr, c->u, 1.0, s);
+    launch_lincomb(c, c->vin, b[0] - bh[0], k1, b[1] - bh[1], k2, s);
+    launch_lincomb(c, c->vin, 1.0, c->vin, b[2] - bh[2], c->kv[0], s);
+    launch_sumsq(c, c->vin, s);
+    embedded = true;
   } else {
     // ROSM(gamma), eq. ROS: (I/(dt gamma) - J) k = G, T^{n+1} = T^n + k / gamma
     const double gam = scheme == EREM_ROSM1 ? 1.0 : 0.5;
@@ -1272,9 +1319,74 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
     st->lin_resid = res;
     st->substeps = 0;
     st->degree_total = 0;
+    st->err_est = embedded ? std::sqrt(c->ctrl_h->lin[K_EMB] / (double)c->N) : 0.0;
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
   }
+  return EREM_OK;
+}
+
+erem_status rosm_integrate(erem_ctx* c, double* T, double t_end, double dt0,
+                           erem_rosm_scheme scheme, double tol_a, double tol_r, double lin_tol,
+                           int maxit, int max_attempts, double* dts, erem_adapt_stats* ast,
+                           void* stream) {
+  if (!c) return EREM_EINVAL;
+  const double t0 = now_ms();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (scheme != EREM_ROS2 && scheme != EREM_ROS3P)
+    return fail(c, EREM_EINVAL, "rosm_integrate needs EREM_ROS2 or EREM_ROS3P");
+  if (!T) return fail(c, EREM_EINVAL, "T is NULL");
+  if (!(t_end > 0.0) || !std::isfinite(t_end) || !(dt0 > 0.0) || !std::isfinite(dt0))
+    return fail(c, EREM_EINVAL, "t_end and dt0 must be finite and > 0");
+  if (!(tol_a >= 0.0) || !(tol_r >= 0.0) || tol_a + tol_r <= 0.0)
+    return fail(c, EREM_EINVAL, "tolerances must be >= 0 with tol_a + tol_r > 0");
+  if (max_attempts < 1) return fail(c, EREM_EINVAL, "max_attempts must be >= 1");
+  if (!c->have_state) return fail(c, EREM_EINVAL, "no stored state: call erem_set_state first");
+  if (!c->ada_save) EREM_TRY(dalloc_t(c, &c->ada_save, (size_t)c->N));
+  const double order = scheme == EREM_ROS2 ? 2.0 : 3.0;
+  const size_t bytes = (size_t)c->N * sizeof(double);
+  erem_adapt_stats a{};
+  a.dt_min = INFINITY;
+  a.dt_max = 0.0;
+  int launches = 0;
+  double t = 0.0, dt = dt0, facmax = 5.0;
+  while (t < t_end && a.accepted + a.rejected < max_attempts) {
+    const bool last = dt >= t_end - t;
+    const double h = last ? t_end - t : dt;
+    EREM_CUDA(c, cudaMemcpyAsync(c->ada_save, T, bytes, cudaMemcpyDefault, s));
+    erem_stats st{};
+    EREM_TRY(rosm_step(c, T, nullptr, nullptr, nullptr, nullptr, h, scheme, lin_tol, maxit, &st,
+                       stream));
+    launches += st.launches + 1;
+    a.lin_iters += st.lin_iters;
+    const double sc = tol_a + tol_r * c->ctrl_h->yinf;  // ||T^n||_inf of this attempt
+    const double err = st.err_est / sc;
+    const double pred = err == 0.0 ? INFINITY : 0.9 * std::pow(err, -1.0 / order);
+    double grow;
+    if (err <= 1.0) {
+      if (dts) dts[a.accepted] = h;
+      ++a.accepted;
+      t = last ? t_end : t + h;
+      a.dt_min = std::min(a.dt_min, h);
+      a.dt_max = std::max(a.dt_max, h);
+      grow = std::min(facmax, std::max(0.2, pred));
+      facmax = 5.0;
+    } else {
+      ++a.rejected;
+      EREM_CUDA(c, cudaMemcpyAsync(T, c->ada_save, bytes, cudaMemcpyDefault, s));
+      ++launches;
+      grow = std::min(1.0, std::max(0.2, pred));
+      facmax = 1.0;
+    }
+    dt = h * grow;
+  }
+  EREM_CUDA(c, cudaStreamSynchronize(s));
+  a.t_reached = t;
+  a.launches = launches;
+  a.t_ms = now_ms() - t0;
+  if (ast) *ast = a;
+  if (t < t_end)
+    return fail(c, EREM_ENOTCONV, "rosm_integrate: max_attempts reached before t_end");
   return EREM_OK;
 }
 

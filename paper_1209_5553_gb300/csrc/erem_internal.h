@@ -37,6 +37,7 @@ struct StopParams {
 // Krylov scalars kept on the device (indices into Ctrl::lin).
 enum : int {
   K_RZ = 0, K_RR, K_BB, K_ALPHA, K_BETA, K_DAD, K_RHO, K_RHO_PREV, K_OMEGA, K_SS, K_TOL2,
+  K_EMB,  // sum of squares of the embedded Rosenbrock difference
   K_NLIN = 16
 };
 
@@ -215,6 +216,7 @@ struct erem_ctx {
   // erem_step_forced: b(T_in) and D_t G as full vectors (non-zero on the x = 0
   // cells), and the phi_2 increment delta^2 phi_2(delta J) D_t G
   double *fin_b = nullptr, *fin_w = nullptr, *fin_p2 = nullptr;
+  double* ada_save = nullptr;  // rosm_integrate: T before an attempt [N]
   // FP32-bulk Horner pass: upwind flags, FP32 capacities, FP32 mu, FP32 face
   // sums of the current adjoint step
   unsigned char* adj_up = nullptr;
@@ -272,6 +274,7 @@ void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s);
 void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cudaStream_t s);
 void launch_inflow_forced(const erem_ctx* c, double T_in, double rate, double* b, double* w,
                           cudaStream_t s);
+void launch_sumsq(const erem_ctx* c, const double* x, cudaStream_t s);  // -> ctrl->lin[K_EMB]
 void launch_japply_add(const erem_ctx* c, const double* x, const double* v, double* out,
                        cudaStream_t s);
 void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,

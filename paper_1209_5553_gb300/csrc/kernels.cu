@@ -1789,6 +1789,26 @@ __global__ void k_pcg_upd(PresArr a, const double* __restrict__ d, Geo g, double
   }
 }
 
+// sum over the cells of x^2 (the embedded Rosenbrock difference) -> K_EMB
+__global__ void k_sumsq(const double* __restrict__ x, Geo g, double* part, unsigned* cnt,
+                        Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  double s = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    s += x[ip] * x[ip];
+  }
+  double vals[1] = {block_reduce<0>(s, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double a = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin[K_EMB] = a;
+    }
+  }
+}
+
 // net Darcy inflow through x = 0 and the largest face speed |v| / |sigma|
 __global__ void k_pres_post(const double* __restrict__ lnk, const double* __restrict__ T,
                             const double* __restrict__ x, Geo g, Phys ph, double* part,
@@ -2139,6 +2159,11 @@ void launch_rhs(const erem_ctx* c, const double* T, double* G, int set_yinf, cud
   ++c->launches;
   k_rhs<<<blocks_cells(c), NT, 0, s>>>(face_in(c), T, G, geo_of(c), phys_of(c), set_yinf,
                                        c->red_part, c->red_cnt, c->ctrl);
+}
+
+void launch_sumsq(const erem_ctx* c, const double* x, cudaStream_t s) {
+  ++c->launches;
+  k_sumsq<<<blocks_cells(c), NT, 0, s>>>(x, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
 }
 
 void launch_inflow_forced(const erem_ctx* c, double T_in, double rate, double* b, double* w,

@@ -92,6 +92,24 @@ def test_krylov_struct_layouts_and_defaults(E, tmp_path):
     assert (o.tol_a, o.tol_r, o.m, o.max_substeps, o.n_replay) == (1e-6, 1e-6, 10, 1000, 0)
 
 
+def test_stats_struct_layouts_match_the_c_compiler(E, tmp_path):
+    src = tmp_path / "st.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "erem.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(erem_stats), '
+                   'offsetof(erem_stats, degree_phi2), sizeof(erem_adapt_stats), '
+                   'offsetof(erem_adapt_stats, t_reached), offsetof(erem_adapt_stats, t_ms)); '
+                   'return 0; }\n')
+    exe = tmp_path / "st"
+    import subprocess
+
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == [ctypes.sizeof(E.erem_stats), E.erem_stats.degree_phi2.offset,
+                   ctypes.sizeof(E.erem_adapt_stats), E.erem_adapt_stats.t_reached.offset,
+                   E.erem_adapt_stats.t_ms.offset]
+
+
 def test_ensemble_create_rejects_bad_members_without_touching_the_gpu(E):
     ph = E.Physics().c()
     g2 = E.erem_grid(2, 8, 8, 1, 1.0, 1.0, 1.0)

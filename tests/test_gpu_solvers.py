@@ -122,14 +122,17 @@ def _rosm_case():
     return case
 
 
-@pytest.mark.parametrize("scheme", ["rosm1", "rosm_half", "ros2"])
+@pytest.mark.parametrize("scheme", ["rosm1", "rosm_half", "ros2", "ros3p"])
 def test_rosm_step_matches_oracle(E, scheme):
     case = _rosm_case()
     prob = case.problem(case.T0)
     tau = 0.05
-    gam = {"rosm1": 1.0, "rosm_half": 0.5, "ros2": ts.ROS2_GAMMA}[scheme]
+    gam = {"rosm1": 1.0, "rosm_half": 0.5, "ros2": ts.ROS2_GAMMA, "ros3p": ts.ROS3P_GAMMA}[scheme]
+    emb = None
     if scheme == "ros2":
-        ref = ts.ros2_step(prob, case.T0, tau)
+        ref, emb = ts.ros2_step(prob, case.T0, tau, embedded=True)
+    elif scheme == "ros3p":
+        ref, emb = ts.ros3p_step(prob, case.T0, tau, embedded=True)
     else:
         ref = ts.rosm_step(prob, case.T0, tau, gam)
     A = ts.stage_matrix(prob.J(case.T0), tau, gam)
@@ -138,7 +141,8 @@ def test_rosm_step_matches_oracle(E, scheme):
     inc = ref - case.T0
     # each stage: error <= 10 tol ||rhs|| / smin, rhs ~ G; scaled by the b_i or 1/gamma
     bound = 10 * STAGE_TOL * np.linalg.norm(G) / smin * 3.0 / np.linalg.norm(inc)
-    code = {"rosm1": E.EREM_ROSM1, "rosm_half": E.EREM_ROSM_HALF, "ros2": E.EREM_ROS2}[scheme]
+    code = {"rosm1": E.EREM_ROSM1, "rosm_half": E.EREM_ROSM_HALF, "ros2": E.EREM_ROS2,
+            "ros3p": E.EREM_ROS3P}[scheme]
     with E.Context(2, case.grid.nx, case.grid.ny, physics=case.gpu_physics()) as ctx:
         T = _t(case.T0)
         st = ctx.rosm_step(T, tau, code, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
@@ -147,6 +151,47 @@ def test_rosm_step_matches_oracle(E, scheme):
     assert st.lin_iters > 0 and st.lin_resid <= STAGE_TOL
     err = np.linalg.norm((got - case.T0) - inc) / np.linalg.norm(inc)
     assert err <= max(bound, 1e-12), (err, bound)
+    if emb is not None:
+        # the embedded difference: RMS of y - y_hat (stage errors as above)
+        want = np.sqrt(np.mean((ref - emb) ** 2))
+        assert st.err_est == pytest.approx(want, rel=max(1e-9, 100 * bound * np.linalg.norm(inc)
+                                                          / np.linalg.norm(ref - emb)))
+    else:
+        assert st.err_est == 0.0
+
+
+@pytest.mark.parametrize("scheme", ["ros2", "ros3p"])
+def test_adaptive_rosenbrock_matches_oracle(E, scheme):
+    # the GPU controller takes the oracle's accept/reject decisions and step
+    # lengths (the error estimates differ by the stage-solve tolerance only);
+    # nonlinear fluid laws (ROS3p's estimate vanishes on the linear model),
+    # the Darcy fluxes re-evaluated at T^n every step on both sides
+    case = C.random_case(2, 16, 12, seed=23, fluid_model=1)
+    t_end, dt0, tol = 0.05, 1e-3, 1e-5
+    ref = ts.ros_integrate(lambda T: case.problem(T), case.T0, t_end, dt0, scheme, tol, tol)
+    assert ref.rejected + len(ref.dts) > 5
+    code = {"ros2": E.EREM_ROS2, "ros3p": E.EREM_ROS3P}[scheme]
+    with E.Context(2, case.grid.nx, case.grid.ny, physics=case.gpu_physics()) as ctx:
+        T = _t(case.T0)
+        ctx.set_state(T, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), dt0)
+        st, dts = ctx.rosm_integrate(T, t_end, dt0, code, tol, tol, lin_tol=1e-13, maxit=20000)
+        got = T.cpu().numpy()
+        assert st.rejected == ref.rejected and st.accepted == len(ref.dts)
+        assert np.allclose(dts, ref.dts, rtol=1e-7, atol=0)
+        assert st.t_reached == t_end and abs(dts.sum() - t_end) < 1e-15
+        # too few attempts: ENOTCONV, T at the last accepted time
+        T2 = _t(case.T0)
+        ctx.set_state(T2, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), dt0)
+        with pytest.raises(E.EremError) as ei:
+            ctx.rosm_integrate(T2, t_end, dt0, code, tol, tol, lin_tol=1e-13, max_attempts=2)
+        assert ei.value.status == E.EREM_ENOTCONV
+        for bad in (dict(scheme=E.EREM_ROSM1), dict(tol_a=0.0, tol_r=0.0), dict(dt0=-1.0)):
+            args = dict(t_end=t_end, dt0=dt0, scheme=code, tol_a=tol, tol_r=tol)
+            args.update(bad)
+            with pytest.raises(E.EremError) as ei:
+                ctx.rosm_integrate(T2, **args)
+            assert ei.value.status == E.EREM_EINVAL
+    assert C.rel_l2(got, ref.T) < 1e-8
 
 
 def test_rosm_then_erem_share_the_context(E):

@@ -9,6 +9,7 @@ import pytest
 import scipy.linalg as sla
 from scipy.special import gammainc
 
+import cases as C
 import workloads as W
 from oracle import fv, timestep as ts
 from oracle.leja import LejaOptions
@@ -252,6 +253,13 @@ def test_adaptive_rosenbrock_control(scheme, p):
         assert all(errs[tol] < 30.0 * tol for tol in errs), errs
         ratio = len(runs[1e-6].dts) / len(runs[1e-4].dts)
         assert 0.5 * 100 ** (1 / p) < ratio < 2.0 * 100 ** (1 / p), ratio
+    # the linear heat model: ROS3p's embedded difference vanishes identically
+    lin = C.random_case(2, 8, 6, seed=4, fluid_model=0)
+    pl = lin.problem(lin.T0)
+    y, yh = ts.ros3p_step(pl, lin.T0, 0.05, embedded=True)
+    assert np.max(np.abs(y - yh)) < 1e-12 * np.max(np.abs(y - lin.T0))
+    y2, yh2 = ts.ros2_step(pl, lin.T0, 0.05, embedded=True)
+    assert np.max(np.abs(y2 - yh2)) > 1e-3 * np.max(np.abs(y2 - lin.T0))
     # a too-large first step is rejected and then shrinks
     r = ts.ros_integrate(prob, T0, t_end, t_end, scheme, 1e-8, 1e-8)
     assert r.rejected >= 1 and r.errs[0] > 1.0 and r.dts[0] < t_end
