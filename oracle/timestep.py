@@ -14,7 +14,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Linear systems are solved directly (sparse LU), so the oracle's stage values
 are exact up to the conditioning of the stage matrix.
 * The sequential (Trotter) coupling of §3.2: pressure at T^n, then Darcy fluxes,
-  then one heat step; :func:`sequential_step`.
+  then one heat step; :func:`sequential_step`.  The Strang alternative of
+  §3.2 (heat tau/2, pressure, heat tau/2): :func:`strang_step`.
 """
 from __future__ import annotations
 
@@ -223,6 +224,26 @@ def pressure_solve_cg(grid, phys, lnk, T=None, p0=None, tol=1e-13, maxit=100000)
         d = z + (rz_new / rz) * d
         rz = rz_new
     return x, maxit, float(np.linalg.norm(r) / bn)
+
+
+def strang_step(grid, phys, lnk, phi, lam, T, p, tau, opts=(None, None), pressure="direct"):
+    """One Strang step of §3.2 with the steady pressure of this build: an
+    EREM heat step of tau/2 with the Darcy fluxes of the current pressure p
+    (and the viscosity at the current T), the steady pressure at the new T,
+    then a second heat step of tau/2 with it.  p is the pressure the previous
+    step ended with (for the first step, the steady pressure at T^0).  With a
+    steady (instantly relaxed) pressure the symmetric splitting does not keep
+    its formal second order: the coupling is lagged by half a step in each
+    half.  Returns (T^{n+1}, p^{n+1}, (result of each half))."""
+    prob = heat_problem(grid, phys, lnk, phi, lam, p, T)
+    Th, r1 = erem_step(prob, T, tau / 2, opts[0])
+    if pressure == "direct":
+        p1 = pressure_solve_direct(grid, phys, lnk, Th)
+    else:
+        p1 = pressure_solve_cg(grid, phys, lnk, Th, p0=p)[0]
+    prob = heat_problem(grid, phys, lnk, phi, lam, p1, Th)
+    T1, r2 = erem_step(prob, Th, tau / 2, opts[1])
+    return T1, p1, (r1, r2)
 
 
 def sequential_step(grid, phys, lnk, phi, lam, T, p_prev, tau, scheme="erem", opts=None,

@@ -299,6 +299,67 @@ def test_stability_functions_on_a_single_cell(tau):
     assert (r3[0] - Tstar) == pytest.approx(_ros3p_R(z) * (y0[0] - Tstar), rel=1e-12)
 
 
+def _strang_setup(fm, n=12):
+    wl = W.coupled2d(n=n, steps=1, dt=0.01)
+    g = fv.Grid(2, n, n)
+    base = fv.Physics(head_left=1.0, head_right=0.0, T_inflow=80.0, fluid_model=fm)
+    p0 = ts.pressure_solve_direct(g, base, wl.lnk, wl.T0)
+    U = fv.darcy_fluxes(g, base, wl.lnk, p0, wl.T0)[0][:, :, 0].sum() / g.ly
+    rc = 20.0 * 2.0 / U
+    ph = fv.Physics(rc, rc, 1.0, 0.0, 80.0, fm)
+    return wl, g, ph
+
+
+def test_strang_step_is_two_exact_half_steps_for_the_linear_model():
+    # fluid_model 0: the pressure does not depend on T, the heat problem is
+    # linear and autonomous, so the two half steps compose to the exact flow
+    # of one full step
+    wl, g, ph = _strang_setup(0)
+    p = ts.pressure_solve_direct(g, ph, wl.lnk, wl.T0)
+    T1, p1, (r1, r2) = ts.strang_step(g, ph, wl.lnk, wl.phi, wl.lam, wl.T0, p, 0.02, (TIGHT, TIGHT))
+    prob = ts.heat_problem(g, ph, wl.lnk, wl.phi, wl.lam, p, wl.T0)
+    T2, _ = ts.erem_step(prob, wl.T0, 0.02, TIGHT)
+    assert np.linalg.norm(T1 - T2) < 1e-10 * np.linalg.norm(T2 - wl.T0)
+    assert np.max(np.abs(p1 - p)) < 1e-12 * np.max(np.abs(p))
+
+
+def test_strang_step_pressure_is_steady_at_the_half_step():
+    wl, g, ph = _strang_setup(1)
+    p = ts.pressure_solve_direct(g, ph, wl.lnk, wl.T0)
+    T1, p1, (r1, r2) = ts.strang_step(g, ph, wl.lnk, wl.phi, wl.lam, wl.T0, p, 0.02)
+    prob = ts.heat_problem(g, ph, wl.lnk, wl.phi, wl.lam, p, wl.T0)
+    Th, _ = ts.erem_step(prob, wl.T0, 0.01)
+    A, b = fv.pressure_system(g, ph, wl.lnk, Th)
+    assert np.linalg.norm(A @ p1 - b) < 1e-12 * np.linalg.norm(b)
+    assert r1.converged and r2.converged
+
+
+def test_strang_and_trotter_converge_to_the_same_solution():
+    # with the steady pressure both splittings are first order here (0.85 to
+    # 1.06 measured from 4 to 32 steps); both approach the same limit
+    wl, g, ph = _strang_setup(1)
+    t_end = 0.08
+
+    def trotter(n):
+        T, p = wl.T0.copy(), None
+        for _ in range(n):
+            T, p, _ = ts.sequential_step(g, ph, wl.lnk, wl.phi, wl.lam, T, p, t_end / n, opts=TIGHT)
+        return T
+
+    def strang(n):
+        T = wl.T0.copy()
+        p = ts.pressure_solve_direct(g, ph, wl.lnk, T)
+        for _ in range(n):
+            T, p, _ = ts.strang_step(g, ph, wl.lnk, wl.phi, wl.lam, T, p, t_end / n, (TIGHT, TIGHT))
+        return T
+
+    ref = strang(128)
+    for f in (trotter, strang):
+        e = [np.linalg.norm(f(n) - ref) for n in (8, 16, 32)]
+        orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+        assert all(0.7 < o < 1.5 for o in orders), (f.__name__, e, orders)
+
+
 def test_sequential_coupling_runs_and_cg_pressure_agrees():
     wl = W.coupled2d(n=16, steps=3, dt=0.005)
     g = fv.Grid(2, 16, 16)
