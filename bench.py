@@ -547,6 +547,12 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     stream = torch.cuda.current_stream()
 
     def step():
+        if scheme == "strang":
+            st, s1 = ctx.coupled_step(T, p, lnk, phi, lam, wl.dt, E.EREM_SPLIT_STRANG,
+                                      pressure_tol=1e-10, opts=[opts, opts])
+            s1.launches += st[0].launches + st[1].launches
+            st[1].degree_total += st[0].degree_total
+            return s1, st[1]
         s1 = ctx.pressure_solve(lnk, T, p, tol=1e-10, maxit=200000)
         if scheme == "erem":
             s2 = ctx.erem_step(T, wl.dt, p, lnk, phi, lam, opts=opts)
@@ -593,7 +599,8 @@ def main_coupled(args):
     K, Wu = args.steps, args.warmup
     runs = {}
     for key, scheme, prec in (("erem_fp32_bulk", "erem", "fp32_bulk"), ("erem_fp64", "erem", "fp64"),
-                              ("ros2_fp64", "ros2", "fp64"), ("ros3p_fp64", "ros3p", "fp64")):
+                              ("ros2_fp64", "ros2", "fp64"), ("ros3p_fp64", "ros3p", "fp64"),
+                              ("erem_strang_fp32_bulk", "strang", "fp32_bulk")):
         r = run_coupled(E, torch, wl, scheme, prec, K, Wu, dev)
         ms, value = aggregate(r["ms"], wl.n, K, world, dev)
         r.update(ms=ms, value=value)

@@ -239,6 +239,30 @@ EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
                       erem_rosm_scheme scheme, double lin_tol, int maxit,
                       erem_stats* stats, void* stream);
 
+/* One step of the coupled pressure/temperature problem by operator
+ * splitting (§3.2), with the steady pressure of this library:
+ *   EREM_SPLIT_TROTTER (the paper's "sequential approach"): p <- steady
+ *     pressure at T^n (CG from the guess in p), then one EREM heat step of
+ *     dt with the Darcy fluxes of p (erem_step with the fields);
+ *   EREM_SPLIT_STRANG: an EREM heat step of dt/2 with the p given (the
+ *     pressure the previous step ended with; for the first step the steady
+ *     pressure at T^0), p <- steady pressure at the new T, a second heat step
+ *     of dt/2.  With an instantly relaxed pressure the symmetric splitting
+ *     is first order like the sequential one (the coupling lags by half a
+ *     step in each half).
+ *   T [N], p [N] in/out; lnk, phi, lambda [N].  pressure_tol, pressure_maxit
+ *   as pressure_solve.  opts: NULL or an array of one (Trotter) or two
+ *   (Strang, one per half step) Leja option structs; stats: NULL or an array
+ *   of as many erem_stats for the heat steps; pstats (may be NULL): the
+ *   pressure solve.  Errors as pressure_solve and erem_step; on an error of
+ *   the second half T holds the state after the first. */
+typedef enum { EREM_SPLIT_TROTTER = 0, EREM_SPLIT_STRANG = 1 } erem_splitting;
+EREM_API erem_status coupled_step(erem_ctx* ctx, double* T, double* p, const double* lnk,
+                                  const double* phi, const double* lambda, double dt,
+                                  erem_splitting splitting, double pressure_tol,
+                                  int pressure_maxit, const erem_leja_opts* opts,
+                                  erem_stats* stats, erem_stats* pstats, void* stream);
+
 /* Adaptive Rosenbrock integration of the stored state (erem_set_state or the
  * last step's fields) over [0, t_end] with ROS2(1) or ROS3p and the error
  * control the paper points to (§3.2.3: Hairer-Wanner): each attempt of

@@ -32,6 +32,7 @@ STATUS_NAMES = {0: "EREM_OK", 1: "EREM_EINVAL", 2: "EREM_ENOMEM", 3: "EREM_ENOTC
 EREM_FP64, EREM_FP32_BULK = 0, 1
 EREM_ROSM1, EREM_ROSM_HALF, EREM_ROS2, EREM_ROS3P = 0, 1, 2, 3
 EREM_LEJA_EXACT, EREM_LEJA_FAST = 0, 1
+EREM_SPLIT_TROTTER, EREM_SPLIT_STRANG = 0, 1
 
 
 class erem_grid(ctypes.Structure):
@@ -145,6 +146,8 @@ _sigs = {
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_fast_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_phi2_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
+    "coupled_step": (_I, [_P, _P, _P, _P, _P, _P, _D, _I, _D, _I, ctypes.POINTER(erem_leja_opts),
+                          ctypes.POINTER(erem_stats), ctypes.POINTER(erem_stats), _P]),
     "rosm_integrate": (_I, [_P, _P, _D, _D, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_D),
                             ctypes.POINTER(erem_adapt_stats), _P]),
     "erem_step_forced": (_I, [_P, _P, _D, _D, _D, _P, _P, _P, _P, ctypes.POINTER(erem_leja_opts),
@@ -313,6 +316,27 @@ def erem_step_forced(ctx, n, T, dt, T_in, T_in_rate, p=None, lnk=None, phi=None,
                                       ctypes.byref(opts) if opts is not None else None,
                                       ctypes.byref(st), _stream(stream)))
     return st
+
+
+def coupled_step(ctx, n, T, p, lnk, phi, lam, dt, splitting=EREM_SPLIT_TROTTER,
+                 pressure_tol=1e-10, pressure_maxit=200000, opts=None, stream=None):
+    """One split pressure/temperature step; opts: None or a list of one
+    (Trotter) or two (Strang) erem_leja_opts.  Returns (heat stats list,
+    pressure stats)."""
+    nh = 2 if splitting == EREM_SPLIT_STRANG else 1
+    if opts is not None:
+        if len(opts) != nh:
+            raise ValueError(f"opts needs {nh} entries")
+        arr = (erem_leja_opts * nh)(*opts)
+    st = (erem_stats * nh)()
+    pst = erem_stats()
+    _check(ctx, _lib.coupled_step(ctx, _ptr(T, n), _ptr(p, n), _ptr(lnk, n), _ptr(phi, n),
+                                  _ptr(lam, n), float(dt), int(splitting), float(pressure_tol),
+                                  int(pressure_maxit),
+                                  ctypes.cast(arr, ctypes.POINTER(erem_leja_opts)) if opts is not None
+                                  else None, ctypes.cast(st, ctypes.POINTER(erem_stats)),
+                                  ctypes.byref(pst), _stream(stream)))
+    return list(st), pst
 
 
 def rosm_integrate(ctx, n, T, t_end, dt0, scheme=EREM_ROS2, tol_a=1e-6, tol_r=1e-6,
@@ -593,6 +617,11 @@ class Context:
 
     def erem_step(self, T, dt, p=None, lnk=None, phi=None, lam=None, opts=None, stream=None):
         return erem_step(self._h, self.n, T, dt, p, lnk, phi, lam, opts, stream)
+
+    def coupled_step(self, T, p, lnk, phi, lam, dt, splitting=EREM_SPLIT_TROTTER,
+                     pressure_tol=1e-10, pressure_maxit=200000, opts=None, stream=None):
+        return coupled_step(self._h, self.n, T, p, lnk, phi, lam, dt, splitting, pressure_tol,
+                            pressure_maxit, opts, stream)
 
     def rosm_integrate(self, T, t_end, dt0, scheme=EREM_ROS2, tol_a=1e-6, tol_r=1e-6,
                        lin_tol=1e-10, maxit=10000, max_attempts=100000, stream=None):

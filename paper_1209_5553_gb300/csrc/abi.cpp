@@ -1326,6 +1326,25 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
   return EREM_OK;
 }
 
+erem_status coupled_step(erem_ctx* c, double* T, double* p, const double* lnk, const double* phi,
+                         const double* lam, double dt, erem_splitting split, double ptol,
+                         int pmaxit, const erem_leja_opts* opts, erem_stats* st,
+                         erem_stats* pst, void* stream) {
+  if (!c) return EREM_EINVAL;
+  if (split != EREM_SPLIT_TROTTER && split != EREM_SPLIT_STRANG)
+    return fail(c, EREM_EINVAL, "splitting must be EREM_SPLIT_TROTTER or EREM_SPLIT_STRANG");
+  if (!T || !p || !lnk || !phi || !lam) return fail(c, EREM_EINVAL, "NULL array argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, EREM_EINVAL, "dt must be finite and > 0");
+  if (split == EREM_SPLIT_TROTTER) {
+    EREM_TRY(pressure_solve(c, lnk, T, p, ptol, pmaxit, pst, stream));
+    return erem_step(c, T, p, lnk, phi, lam, dt, opts, st, stream);
+  }
+  EREM_TRY(erem_step(c, T, p, lnk, phi, lam, 0.5 * dt, opts, st, stream));
+  EREM_TRY(pressure_solve(c, lnk, T, p, ptol, pmaxit, pst, stream));
+  return erem_step(c, T, p, lnk, phi, lam, 0.5 * dt, opts ? opts + 1 : nullptr,
+                   st ? st + 1 : nullptr, stream);
+}
+
 erem_status rosm_integrate(erem_ctx* c, double* T, double t_end, double dt0,
                            erem_rosm_scheme scheme, double tol_a, double tol_r, double lin_tol,
                            int maxit, int max_attempts, double* dts, erem_adapt_stats* ast,

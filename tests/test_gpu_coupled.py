@@ -79,3 +79,51 @@ def test_coupled_steps_with_gpu_pressure_in_the_loop(setup):
         got = T.cpu().numpy()
     inc = np.linalg.norm(Ts[-1] - wl.T0) / np.linalg.norm(Ts[-1])
     assert C.rel_l2(got, Ts[-1]) < max(1e-11, 10 * STEPS * bound * inc), bound
+
+
+def test_coupled_step_trotter_and_strang_match_oracle(setup):
+    # the C ABI's coupled_step: Trotter against the oracle's sequential
+    # steps, Strang (heat dt/2, pressure, heat dt/2) against strang_step,
+    # each heat step replaying the oracle's schedule; the pressure CG error
+    # enters through the fluxes (bound as above)
+    E, wl, g, ph, ps, scheds, Ts = setup
+    phys = E.Physics(ph.rhoc_f, ph.rhoc_s, 1.0, 0.0, 80.0, 1)
+    T_s = wl.T0.copy()
+    p_s = ts.pressure_solve_direct(g, ph, wl.lnk, T_s)
+    s_scheds, s_T, bound = [], [], 0.0
+    for _ in range(STEPS):
+        T_s, p_s, (r1, r2) = ts.strang_step(g, ph, wl.lnk, wl.phi, wl.lam, T_s, p_s, wl.dt)
+        s_scheds.append((r1.schedule, r2.schedule))
+        A, b = fv.pressure_system(g, ph, wl.lnk, T_s)
+        smin = np.linalg.svd(A.toarray(), compute_uv=False).min()
+        bound = max(bound, 10 * CG_TOL * np.linalg.norm(b) / smin / np.linalg.norm(p_s))
+    s_T = T_s
+    fields = (_t(wl.lnk), _t(wl.phi), _t(wl.lam))
+    with E.Context(2, 24, 24, physics=phys) as ctx:
+        T = _t(wl.T0)
+        p = _t(fv.linear_head_guess(g, ph))
+        for k in range(STEPS):
+            st, pst = ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_TROTTER, pressure_tol=CG_TOL,
+                                       opts=[E.leja_opts(replay=scheds[k])])
+            assert pst.lin_resid <= CG_TOL and st[0].schedule == scheds[k]
+        got_trotter = T.cpu().numpy()
+        T = _t(wl.T0)
+        p = _t(fv.linear_head_guess(g, ph))
+        ctx.pressure_solve(fields[0], T, p, tol=CG_TOL)
+        for k in range(STEPS):
+            st, pst = ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_STRANG, pressure_tol=CG_TOL,
+                                       opts=[E.leja_opts(replay=s) for s in s_scheds[k]])
+            assert [s.schedule for s in st] == list(s_scheds[k])
+        got_strang = T.cpu().numpy()
+        p_got = p.cpu().numpy()
+        with pytest.raises(ValueError):
+            ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_STRANG, opts=[E.leja_opts()])
+        with pytest.raises(E.EremError) as ei:
+            ctx.coupled_step(T, p, *fields, wl.dt, 7)
+        assert ei.value.status == E.EREM_EINVAL
+    inc = np.linalg.norm(Ts[-1] - wl.T0) / np.linalg.norm(Ts[-1])
+    assert C.rel_l2(got_trotter, Ts[-1]) < max(1e-11, 10 * STEPS * bound * inc)
+    assert C.rel_l2(got_strang, s_T) < max(1e-11, 10 * STEPS * bound * inc)
+    assert C.rel_l2(p_got, p_s) < 10 * bound
+    # the two splittings differ at the splitting error, far above the bound
+    assert C.rel_l2(got_strang, got_trotter) > 1e3 * max(1e-11, 10 * STEPS * bound * inc)
