@@ -44,6 +44,7 @@ def test_static_pressure_solve_matches_pressure_solve(dims):
     guess = fv.linear_head_guess(g, ph)
     phys = E.Physics(1.0, 1.0, ph.head_left, ph.head_right, 80.0, fm)
     with E.Context(dim, nx, ny, nz, physics=phys) as ctx:
+        ctx.set_pressure_precond(1)   # the static solve is the Jacobi CG
         p_ref = t(guess)
         st_ref = ctx.pressure_solve(t(lnk), t(T) if fm else None, p_ref, tol=PRESSURE_TOL)
         ref = p_ref.cpu().numpy()
