@@ -148,8 +148,9 @@ EREM_API erem_status erem_set_physics(erem_ctx* ctx, const erem_physics* phys);
 
 /* Steady pressure (§2, eq. masscon4 without storage terms; the paper's
  * initial state is the steady pressure, §5), discretized with the TPFA
- * harmonic transmissibilities of §3.1 and solved with Jacobi-preconditioned
- * conjugate gradients in FP64.
+ * harmonic transmissibilities of §3.1 and solved by conjugate gradients in
+ * FP64, preconditioned by the context's choice (erem_set_pressure_precond:
+ * an FP32 Chebyshev polynomial of degree 32 by default, or Jacobi).
  *   lnk  [N]  ln K per cell
  *   T    [N]  temperature for the fluid laws (may be NULL: T = 20)
  *   p    [N]  in: initial guess; out: solution
@@ -295,8 +296,8 @@ EREM_API erem_status rosm_integrate(erem_ctx* ctx, double* T, double t_end, doub
  * Callers that run under a device-memory budget fixed at start-up, inside a
  * host callback, or under another runtime's allocator cannot call
  * cudaMalloc; erem_create does, so they could not reach pressure_solve.
- * This call needs no context: it runs the same Jacobi-preconditioned CG as
- * pressure_solve, with its work vectors, reduction partials and control
+ * This call needs no context: it runs the Jacobi-preconditioned CG of
+ * pressure_solve (erem_set_pressure_precond degree 1), with its work vectors, reduction partials and control
  * block in one static device array compiled into the library (about 5.8 MB
  * on every GPU that loads the library, held until the process exits).
  *   grid, phys  as for erem_create (only the heads and fluid_model are used)
