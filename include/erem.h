@@ -150,7 +150,7 @@ EREM_API erem_status erem_set_physics(erem_ctx* ctx, const erem_physics* phys);
  * initial state is the steady pressure, §5), discretized with the TPFA
  * harmonic transmissibilities of §3.1 and solved by conjugate gradients in
  * FP64, preconditioned by the context's choice (erem_set_pressure_precond:
- * an FP32 Chebyshev polynomial of degree 32 by default, or Jacobi).
+ * an FP32 multigrid V-cycle by default, a Chebyshev polynomial, or Jacobi).
  *   lnk  [N]  ln K per cell
  *   T    [N]  temperature for the fluid laws (may be NULL: T = 20)
  *   p    [N]  in: initial guess; out: solution
@@ -423,17 +423,27 @@ typedef enum { EREM_LEJA_EXACT = 0, EREM_LEJA_FAST = 1 } erem_leja_kind;
 EREM_API erem_status erem_set_leja_points(erem_ctx* ctx, int kind);
 
 /* Preconditioner of the pressure CG (pressure_solve, erem_adjoint_lnk) for
- * later calls on ctx.  degree 1: Jacobi (diagonal) preconditioning, plain CG
+ * later calls on ctx.  degree 0: one multigrid V-cycle (aggregates of 2 x 2
+ * (x 2) cells, Galerkin coarse operators, nu Chebyshev-Jacobi smoothing
+ * steps on [1/4, 2] before and after, the coarse correction weighted by
+ * omega, single-block CG on the coarsest level of <= 512 cells; FP32;
+ * parameters by erem_set_pressure_multigrid, default nu = 3, omega = 1.8).
+ * degree 1: Jacobi (diagonal) preconditioning, plain CG
  * in FP64.  degree 2..64: z = p(D^-1 A) D^-1 r, `degree` steps of Chebyshev
  * iteration for A z = r on the interval [2/degree^2, 2] (D the diagonal of A,
  * the spectrum of D^-1 A lies in (0, 2]), applied in FP32; the outer CG stays
  * FP64 with the Polak-Ribiere beta (flexible CG), so the stopping rule and
  * accuracy of pressure_solve are unchanged and lin_iters counts outer
- * iterations.  Default 32.  Needs 8 FP32 vectors [N] (allocated on first use).
+ * iterations.  Default 0 (multigrid).  Needs 8 FP32 vectors [N] (and the
+ * coarse levels, about N/2 more in 2D) allocated on first use.
  * The paper's solver is BiCGSTAB with ILU(0) (§3.2.3, §5); both are
  * preconditioned Krylov methods for the same system.
- * Errors: EINVAL (ctx NULL, degree outside 1..64). */
+ * Errors: EINVAL (ctx NULL, degree outside 0..64). */
 EREM_API erem_status erem_set_pressure_precond(erem_ctx* ctx, int degree);
+
+/* Multigrid parameters (degree 0 above): nu in 1..16, omega in (0, 2).
+ * Errors: EINVAL. */
+EREM_API erem_status erem_set_pressure_multigrid(erem_ctx* ctx, int nu, double omega);
 
 /* Hold the Gershgorin interval of J (§4.2, before the factor dt: the interval
  * of dt J becomes [dt lo, dt hi]) at [lo, hi] for every later step of ctx

@@ -163,6 +163,7 @@ _sigs = {
                               ctypes.POINTER(erem_krylov_stats), _P]),
     "erem_hold_interval": (_I, [_P, _I, _D, _D]),
     "erem_set_pressure_precond": (_I, [_P, _I]),
+    "erem_set_pressure_multigrid": (_I, [_P, _I, _D]),
     "erem_adjoint_begin": (_I, [_P, _P]),
     "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
     "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -465,8 +466,8 @@ def erem_hold_interval(ctx, interval) -> None:
 
 
 def erem_set_pressure_precond(ctx, degree) -> None:
-    """Pressure CG preconditioner: 1 = Jacobi, 2..64 = FP32 Chebyshev
-    polynomial of that degree (default 32)."""
+    """Pressure CG preconditioner: 0 = FP32 multigrid V-cycle (default),
+    1 = Jacobi, 2..64 = FP32 Chebyshev polynomial of that degree."""
     _check(ctx, _lib.erem_set_pressure_precond(ctx, int(degree)))
 
 
@@ -642,6 +643,9 @@ class Context:
 
     def set_pressure_precond(self, degree):
         erem_set_pressure_precond(self._h, degree)
+
+    def set_pressure_multigrid(self, nu=3, omega=1.8):
+        _check(self._h, _lib.erem_set_pressure_multigrid(self._h, int(nu), float(omega)))
 
     def hold_interval(self, interval):
         erem_hold_interval(self._h, interval)

@@ -122,10 +122,11 @@ erem_status ensure_pc(erem_ctx* c) {
 // theta, delta = centre and half-width, sigma = theta/delta, rho_0 = 1/sigma,
 // rho_j = 1/(2 sigma - rho_{j-1}); step j >= 1 adds rho_j rho_{j-1} times the
 // previous increment and 2 rho_j / delta times the scaled residual.
-PcPoly pc_poly(int deg) {
+PcPoly pc_poly(int deg, double lo = -1.0) {
   PcPoly P;
   P.deg = deg;
-  const double hi = 2.0, lo = 2.0 / ((double)deg * deg);
+  const double hi = 2.0;
+  if (lo < 0.0) lo = 2.0 / ((double)deg * deg);
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
   double rho = 1.0 / sigma;
   P.c2[0] = 1.0 / theta;
@@ -138,28 +139,60 @@ PcPoly pc_poly(int deg) {
   return P;
 }
 
+// Levels of the pressure multigrid: halve every dimension > 1 (rounding up)
+// until at most 512 cells remain (at least one coarse level).
+erem_status ensure_mg(erem_ctx* c) {
+  if (!c->pc_diag) EREM_TRY(dalloc_t(c, &c->pc_diag, (size_t)c->Np));
+  if (!c->mg.empty()) return EREM_OK;
+  int nx = c->nx, ny = c->ny, nz = c->nz;
+  while (c->mg.empty() || (long long)nx * ny * nz > 512) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = c->dim == 3 ? (nz + 1) / 2 : 1;
+    if (!c->mg.empty() && cx == nx && cy == ny && cz == nz) break;
+    nx = cx;
+    ny = cy;
+    nz = cz;
+    MgLevel m;
+    m.nx = nx;
+    m.ny = ny;
+    m.nz = nz;
+    const size_t n = (size_t)nx * ny * nz;
+    c->mg.push_back(m);
+    MgLevel& L = c->mg.back();
+    for (float** a : {&L.diag, &L.dinv, &L.Ux, &L.Uy, &L.rhs, &L.x[0], &L.x[1], &L.x[2], &L.x[3]})
+      EREM_TRY(dalloc_t(c, a, n));
+    if (c->dim == 3) EREM_TRY(dalloc_t(c, &L.Uz, n));
+  }
+  return EREM_OK;
+}
+
 // CG on the pressure system whose matrix and right-hand side the caller has
 // assembled into kv (initial guess in kv[0]): Jacobi-preconditioned for
-// pc_deg = 1, else flexible CG with the FP32 polynomial preconditioner.
+// pc_deg = 1, else flexible CG with the FP32 polynomial preconditioner
+// (pc_deg >= 2) or the multigrid V-cycle (pc_deg = 0).
 erem_status run_pressure_cg(erem_ctx* c, double tol, int maxit, cudaStream_t s) {
-  const bool poly = c->pc_deg > 1;
+  const bool prec = c->pc_deg != 1;
+  const bool mg = c->pc_deg == 0;
   PcPoly P;
+  const float* z = nullptr;
   launch_cg_init(c, tol, s);
-  if (poly) {
+  if (prec) {
     EREM_TRY(ensure_pc(c));
-    P = pc_poly(c->pc_deg);
+    if (mg) EREM_TRY(ensure_mg(c));
+    // the multigrid smoother damps the upper part [1/4, 2] of the spectrum
+    P = mg ? pc_poly(c->mg_nu, 0.25) : pc_poly(c->pc_deg);
     launch_pc_setup(c, s);
-    launch_pc_apply(c, P, s);
+    if (mg) launch_mg_setup(c, s);
+    z = launch_pc_apply(c, P, s);
   }
   EREM_TRY(check_launch(c, "pressure CG set-up"));
   EREM_TRY(read_ctrl(c, s));
   EREM_TRY(check_flags(c));
-  const int chunk = poly ? std::max(2, 64 / c->pc_deg) : 32;
+  const int chunk = mg ? 2 : (prec ? std::max(2, 64 / c->pc_deg) : 32);
   int k = 0;
   while (!c->ctrl_h->lin_done && k < maxit) {
     const int n = std::min(chunk, maxit - k);
     for (int j = 0; j < n; ++j) {
-      if (poly) launch_pcg_iter(c, P, k + j, s);
+      if (prec) launch_pcg_iter(c, P, z, k + j, s);
       else launch_cg_iter(c, k + j, s);
     }
     EREM_TRY(check_launch(c, "cg"));
@@ -1046,6 +1079,10 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (float* p : c->pc)
     if (p) cudaFree(p);
+  if (c->pc_diag) cudaFree(c->pc_diag);
+  for (MgLevel& m : c->mg)
+    for (float* p : {m.diag, m.dinv, m.Ux, m.Uy, m.Uz, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3]})
+      if (p) cudaFree(p);
   if (c->kr_host) cudaFreeHost(c->kr_host);
   if (c->red_cnt) cudaFree(c->red_cnt);
   if (c->qmid) cudaFree(c->qmid);
@@ -1483,9 +1520,18 @@ erem_status erem_set_leja_points(erem_ctx* c, int kind) {
 
 erem_status erem_set_pressure_precond(erem_ctx* c, int degree) {
   if (!c) return EREM_EINVAL;
-  if (degree < 1 || degree > kMaxPcDeg)
-    return fail(c, EREM_EINVAL, "preconditioner degree must be in 1.." + std::to_string(kMaxPcDeg));
+  if (degree < 0 || degree > kMaxPcDeg)
+    return fail(c, EREM_EINVAL, "preconditioner degree must be in 0.." + std::to_string(kMaxPcDeg));
   c->pc_deg = degree;
+  return EREM_OK;
+}
+
+erem_status erem_set_pressure_multigrid(erem_ctx* c, int nu, double omega) {
+  if (!c) return EREM_EINVAL;
+  if (nu < 1 || nu > 16 || !(omega > 0.0 && omega < 2.0))
+    return fail(c, EREM_EINVAL, "multigrid: nu in 1..16 and omega in (0, 2)");
+  c->mg_nu = nu;
+  c->mg_omega = (float)omega;
   return EREM_OK;
 }
 

@@ -16,7 +16,7 @@ namespace erem {
 constexpr int kThreads = 256;      // threads per block of every kernel
 constexpr int kMaxTerms = 4096;    // largest Leja degree a context accepts
 constexpr int kMaxPcDeg = 64;      // largest degree of the pressure CG's polynomial preconditioner
-constexpr int kDefaultPcDeg = 32;  // its default (1 = plain Jacobi CG)
+constexpr int kDefaultPcDeg = 0;   // its default: multigrid (1 = plain Jacobi CG)
 constexpr int kRedSlots = 4;       // reduction values per block
 
 // Bits of Ctrl::flags raised by the set-up kernels.
@@ -149,6 +149,15 @@ struct KrDev {
   int pad;
 };
 
+// One coarse level of the pressure multigrid: an aggregate of 2 x 2 (x 2)
+// cells of the level above; A = diag - (couplings), FP32, unpadded layout.
+struct MgLevel {
+  int nx = 0, ny = 0, nz = 0;
+  float *diag = nullptr, *dinv = nullptr, *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;
+  float* rhs = nullptr;
+  float* x[4] = {};
+};
+
 struct DDEntry {
   double c = 0, gamma = 0;
   int M = -1;
@@ -198,6 +207,12 @@ struct erem_ctx {
   // dinv, Ux, Uy, Uz, r and three z buffers (allocated on first use)
   int pc_deg = erem::kDefaultPcDeg;
   float* pc[8] = {};
+  // multigrid preconditioner (pc_deg = 0): FP32 diagonal of the fine level
+  // and the coarse levels 1..L (levels[0] is the first coarse level)
+  float* pc_diag = nullptr;
+  std::vector<erem::MgLevel> mg;
+  int mg_nu = 3;          // Chebyshev-Jacobi smoothing steps before and after
+  float mg_omega = 1.8f;  // weight of the coarse correction
   // staging for host pointers (allocated on first use)
   double* stage[8] = {};
   // Krylov basis and work vectors (allocated on first use)
@@ -308,8 +323,11 @@ struct PcPoly {
   double c1[kMaxPcDeg] = {}, c2[kMaxPcDeg] = {};
 };
 void launch_pc_setup(const erem_ctx* c, cudaStream_t s);
-void launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s);
-void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, int k, cudaStream_t s);
+// The preconditioner (Chebyshev polynomial, or the multigrid V-cycle with
+// `poly` as its smoother when pc_deg = 0); returns the buffer that holds z.
+const float* launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s);
+void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, const float* z, int k, cudaStream_t s);
+void launch_mg_setup(const erem_ctx* c, cudaStream_t s);
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s);
 
 // stage solver (BiCGSTAB) for (sigma I - J) x = b

@@ -1642,11 +1642,12 @@ struct PcArr {
 };
 
 // FP32 coefficients: 1/diag and the face couplings
-__global__ void k_pc_setup(PresArr a, PcArr p, Geo g) {
+__global__ void k_pc_setup(PresArr a, PcArr p, float* __restrict__ diag32, Geo g) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
     p.dinv[ip] = (float)(1.0 / a.diag[ip]);
+    if (diag32) diag32[ip] = (float)a.diag[ip];
     p.Ux[ip] = (float)a.Ux[ip];
     p.Uy[ip] = (float)a.Uy[ip];
     if (g.dim == 3) p.Uz[ip] = (float)a.Uz[ip];
@@ -1757,6 +1758,179 @@ __global__ void k_pc_sweep(PresArr a, PcArr p, const float* __restrict__ zprev,
         ctrl->lin_done = 1;
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid preconditioner for the pressure CG: aggregates of 2 x 2 (x 2)
+// cells, piecewise-constant prolongation P and restriction P^T, Galerkin
+// coarse operators P^T A P (again 5- or 7-point M-matrices: a coarse face
+// coupling is the sum of the fine couplings across it, a coarse diagonal the
+// sum of the children's diagonals minus twice their internal couplings),
+// Chebyshev-Jacobi smoothing in FP32, the coarse correction over-weighted by
+// omega (piecewise-constant prolongation under-corrects smooth errors), and
+// a single-block CG on the coarsest level.  One V-cycle is the
+// preconditioner of the flexible FP64 CG.
+// ---------------------------------------------------------------------------
+struct MgL {
+  float *diag, *dinv, *Ux, *Uy, *Uz;
+  Geo g;
+};
+
+// the children of coarse cell (X, Y, Z): [2X, min(2X+2, nx)) x ...
+__global__ void k_mg_coarsen(MgL f, MgL c) {
+  for (int I = blockIdx.x * NT + threadIdx.x; I < c.g.N; I += gridDim.x * NT) {
+    int X, Y, Z, IP;
+    cell_of(I, c.g, X, Y, Z, IP);
+    const int xe = min(2 * X + 2, f.g.nx), ye = min(2 * Y + 2, f.g.ny);
+    const int ze = f.g.dim == 3 ? min(2 * Z + 2, f.g.nz) : 1;
+    double dg = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int iz = (f.g.dim == 3 ? 2 * Z : 0); iz < ze; ++iz)
+      for (int iy = 2 * Y; iy < ye; ++iy)
+        for (int ix = 2 * X; ix < xe; ++ix) {
+          const int ip = ix + f.g.px * (iy + f.g.ny * iz);
+          dg += f.diag[ip];
+          if (ix + 1 < xe) dg -= 2.0 * f.Ux[ip];
+          else if (ix + 1 < f.g.nx) ux += f.Ux[ip];
+          if (iy + 1 < ye) dg -= 2.0 * f.Uy[ip];
+          else if (iy + 1 < f.g.ny) uy += f.Uy[ip];
+          if (f.g.dim == 3) {
+            if (iz + 1 < ze) dg -= 2.0 * f.Uz[ip];
+            else if (iz + 1 < f.g.nz) uz += f.Uz[ip];
+          }
+        }
+    c.diag[IP] = (float)dg;
+    c.dinv[IP] = (float)(1.0 / dg);
+    c.Ux[IP] = (float)ux;
+    c.Uy[IP] = (float)uy;
+    if (c.g.dim == 3) c.Uz[IP] = (float)uz;
+  }
+}
+
+// (N x)_i: the couplings of cell i to its neighbours applied to x
+__device__ __forceinline__ float mg_offdiag(const MgL& L, const float* __restrict__ x, int ip, int ix,
+                                            int iy, int iz) {
+  float s = 0.0f;
+  if (ix < L.g.nx - 1) s = fmaf(L.Ux[ip], x[ip + 1], s);
+  if (ix > 0) s = fmaf(L.Ux[ip - 1], x[ip - 1], s);
+  if (iy < L.g.ny - 1) s = fmaf(L.Uy[ip], x[ip + L.g.px], s);
+  if (iy > 0) s = fmaf(L.Uy[ip - L.g.px], x[ip - L.g.px], s);
+  if (L.g.dim == 3) {
+    if (iz < L.g.nz - 1) s = fmaf(L.Uz[ip], x[ip + L.g.plane], s);
+    if (iz > 0) s = fmaf(L.Uz[ip - L.g.plane], x[ip - L.g.plane], s);
+  }
+  return s;
+}
+
+// One Chebyshev-Jacobi step on a coarse level: xn = xc + c1 (xc - xp) +
+// c2 (D^-1 (rhs + N xc) - xc); xc = NULL means x = 0 (xn = c2 D^-1 rhs),
+// xp = NULL means 0.
+__global__ void k_mg_sweep(MgL L, const float* __restrict__ rhs, const float* __restrict__ xp,
+                           const float* __restrict__ xc, float* __restrict__ xn, float c1,
+                           float c2) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < L.g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, L.g, ix, iy, iz, ip);
+    if (!xc) {
+      xn[ip] = c2 * (L.dinv[ip] * rhs[ip]);
+      continue;
+    }
+    const float z = xc[ip];
+    const float zp = xp ? xp[ip] : 0.0f;
+    const float s = rhs[ip] + mg_offdiag(L, xc, ip, ix, iy, iz);
+    xn[ip] = z + c1 * (z - zp) + c2 * fmaf(L.dinv[ip], s, -z);
+  }
+}
+
+// rhs_c = P^T (rhs_f - A_f x_f)
+__global__ void k_mg_restrict(MgL f, const float* __restrict__ rhs_f, const float* __restrict__ x_f,
+                              MgL c, float* __restrict__ rhs_c) {
+  for (int I = blockIdx.x * NT + threadIdx.x; I < c.g.N; I += gridDim.x * NT) {
+    int X, Y, Z, IP;
+    cell_of(I, c.g, X, Y, Z, IP);
+    const int xe = min(2 * X + 2, f.g.nx), ye = min(2 * Y + 2, f.g.ny);
+    const int ze = f.g.dim == 3 ? min(2 * Z + 2, f.g.nz) : 1;
+    float acc = 0.0f;
+    for (int iz = (f.g.dim == 3 ? 2 * Z : 0); iz < ze; ++iz)
+      for (int iy = 2 * Y; iy < ye; ++iy)
+        for (int ix = 2 * X; ix < xe; ++ix) {
+          const int ip = ix + f.g.px * (iy + f.g.ny * iz);
+          acc += rhs_f[ip] - fmaf(f.diag[ip], x_f[ip], -mg_offdiag(f, x_f, ip, ix, iy, iz));
+        }
+    rhs_c[IP] = acc;
+  }
+}
+
+// x_f += omega P x_c
+__global__ void k_mg_prolong(MgL f, float* __restrict__ x_f, MgL c, const float* __restrict__ x_c,
+                             float omega) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < f.g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, f.g, ix, iy, iz, ip);
+    const int I = (ix >> 1) + c.g.px * ((iy >> 1) + c.g.ny * (f.g.dim == 3 ? (iz >> 1) : 0));
+    x_f[ip] = fmaf(omega, x_c[I], x_f[ip]);
+  }
+}
+
+// Coarsest level: Jacobi-preconditioned CG in one block, from x = 0, to
+// ||r|| <= rtol ||b|| or maxit iterations (N <= a few thousand cells).
+constexpr int kMgCoarseThreads = 512;
+__device__ float mg_block_sum(float v, float* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  float t = threadIdx.x < (kMgCoarseThreads / 32) ? sh[threadIdx.x] : 0.0f;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (threadIdx.x == 0) sh[32] = t;
+  __syncthreads();
+  return sh[32];
+}
+
+__global__ void __launch_bounds__(kMgCoarseThreads)
+k_mg_coarse_cg(MgL L, const float* __restrict__ b, float* __restrict__ x, float* __restrict__ r,
+               float* __restrict__ p, float* __restrict__ q, int maxit, float rtol) {
+  __shared__ float sh[33];
+  const int N = L.g.N;
+  float rz = 0.0f, bb = 0.0f;
+  for (int i = threadIdx.x; i < N; i += kMgCoarseThreads) {
+    x[i] = 0.0f;
+    r[i] = b[i];
+    p[i] = L.dinv[i] * b[i];
+    rz += r[i] * p[i];
+    bb += b[i] * b[i];
+  }
+  rz = mg_block_sum(rz, sh);
+  bb = mg_block_sum(bb, sh);
+  const float stop = rtol * rtol * bb;
+  for (int it = 0; it < maxit && bb > 0.0f; ++it) {
+    float pq = 0.0f;
+    for (int i = threadIdx.x; i < N; i += kMgCoarseThreads) {
+      int ix, iy, iz, ip;
+      cell_of(i, L.g, ix, iy, iz, ip);
+      const float v = fmaf(L.diag[ip], p[ip], -mg_offdiag(L, p, ip, ix, iy, iz));
+      q[ip] = v;
+      pq += p[ip] * v;
+    }
+    pq = mg_block_sum(pq, sh);
+    if (!(pq > 0.0f)) break;
+    const float alpha = rz / pq;
+    float rr = 0.0f, rzn = 0.0f;
+    for (int i = threadIdx.x; i < N; i += kMgCoarseThreads) {
+      x[i] = fmaf(alpha, p[i], x[i]);
+      r[i] = fmaf(-alpha, q[i], r[i]);
+      rr += r[i] * r[i];
+      rzn += r[i] * (L.dinv[i] * r[i]);
+    }
+    rr = mg_block_sum(rr, sh);
+    rzn = mg_block_sum(rzn, sh);
+    if (rr <= stop) break;
+    const float beta = rzn / rz;
+    rz = rzn;
+    for (int i = threadIdx.x; i < N; i += kMgCoarseThreads) p[i] = fmaf(beta, p[i], L.dinv[i] * r[i]);
+    __syncthreads();
   }
 }
 
@@ -2405,16 +2579,135 @@ PcArr pc_arr(const erem_ctx* c) {
 // FP32 coefficients, and A d = 0 so that the first (z, A d) is defined
 void launch_pc_setup(const erem_ctx* c, cudaStream_t s) {
   ++c->launches;
-  k_pc_setup<<<blocks_cells(c), NT, 0, s>>>(pres_arr(c), pc_arr(c), geo_of(c));
+  k_pc_setup<<<blocks_cells(c), NT, 0, s>>>(pres_arr(c), pc_arr(c), c->pc_diag, geo_of(c));
   cudaMemsetAsync(pres_arr(c).Ad, 0, sizeof(double) * c->Np, s);
 }
 
-// The preconditioner's deg sweeps; z ends in pc[5 + (deg - 1) % 3].
-void launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s) {
+namespace {
+Geo geo_level(int dim, int nx, int ny, int nz) {
+  Geo g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.px = nx;
+  g.dim = dim;
+  g.N = nx * ny * nz;
+  g.Np = g.N;
+  g.plane = nx * ny;
+  return g;
+}
+MgL mg_fine(const erem_ctx* c) {
+  return MgL{c->pc_diag, c->pc[0], c->pc[1], c->pc[2], c->pc[3], geo_of(c)};
+}
+MgL mg_level(const erem_ctx* c, int l) {
+  const MgLevel& m = c->mg[l];
+  return MgL{m.diag, m.dinv, m.Ux, m.Uy, m.Uz, geo_level(c->dim, m.nx, m.ny, m.nz)};
+}
+}  // namespace
+
+// Galerkin operators of the coarse levels, after launch_pc_setup.
+void launch_mg_setup(const erem_ctx* c, cudaStream_t s) {
+  for (size_t l = 0; l < c->mg.size(); ++l) {
+    const MgL f = l == 0 ? mg_fine(c) : mg_level(c, (int)l - 1);
+    const MgL cl = mg_level(c, (int)l);
+    ++c->launches;
+    k_mg_coarsen<<<grid_for(c, cl.g.N), NT, 0, s>>>(f, cl);
+  }
+}
+
+namespace {
+// smoothing on coarse level l: deg Chebyshev-Jacobi steps from x = 0 (pre) or
+// from x[*cur] (post); returns the buffer index holding the result
+int mg_smooth(const erem_ctx* c, int l, const PcPoly& poly, int cur, bool from_zero, cudaStream_t s) {
+  const MgL L = mg_level(c, l);
+  const MgLevel& m = c->mg[l];
+  const int nb = grid_for(c, L.g.N);
+  int prev = -1;
+  for (int j = 0; j < poly.deg; ++j) {
+    const int nxt = from_zero && j == 0 ? 0 : (cur + 1) % 3;
+    const float* xc = (from_zero && j == 0) ? nullptr : m.x[cur];
+    const float* xp = prev >= 0 ? m.x[prev] : nullptr;
+    ++c->launches;
+    k_mg_sweep<<<nb, NT, 0, s>>>(L, m.rhs, xp, xc, m.x[nxt], (float)poly.c1[j], (float)poly.c2[j]);
+    prev = (from_zero && j == 0) ? -1 : cur;
+    cur = nxt;
+  }
+  return cur;
+}
+
+// V-cycle below the fine level: the correction of coarse level l for its rhs
+// (already restricted); returns the buffer index holding it
+int mg_cycle(const erem_ctx* c, int l, const PcPoly& poly, float omega, cudaStream_t s) {
+  const MgLevel& m = c->mg[l];
+  const MgL L = mg_level(c, l);
+  if (l + 1 == (int)c->mg.size()) {
+    ++c->launches;
+    k_mg_coarse_cg<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3], 400,
+                                                   1e-5f);
+    return 0;
+  }
+  int cur = mg_smooth(c, l, poly, 0, true, s);
+  const MgL Lc = mg_level(c, l + 1);
+  ++c->launches;
+  k_mg_restrict<<<grid_for(c, Lc.g.N), NT, 0, s>>>(L, m.rhs, m.x[cur], Lc, c->mg[l + 1].rhs);
+  const int ec = mg_cycle(c, l + 1, poly, omega, s);
+  ++c->launches;
+  k_mg_prolong<<<grid_for(c, L.g.N), NT, 0, s>>>(L, m.x[cur], Lc, c->mg[l + 1].x[ec], omega);
+  return mg_smooth(c, l, poly, cur, false, s);
+}
+}  // namespace
+
+// The preconditioner.  Chebyshev (pc_deg >= 2): deg sweeps, z ends in
+// pc[5 + (deg - 1) % 3].  Multigrid (pc_deg = 0): pre-smoothing on the fine
+// level from 0, restriction, the coarse V-cycle, prolongation of its
+// correction and post-smoothing, the last sweep with the two dots.
+const float* launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s) {
   const PresArr a = pres_arr(c);
   const PcArr p = pc_arr(c);
   const int nb = grid_for(c, c->Np / 4);
   float* const* zb = &c->pc[5];
+  if (c->pc_deg == 0) {
+    const int nu = poly.deg;
+    // pre-smoothing: sweep 0 converts r to FP32 and starts from z = 0
+    for (int j = 0; j < nu; ++j) {
+      float* zn = zb[j % 3];
+      const float* zc = j >= 1 ? zb[(j + 2) % 3] : nullptr;
+      const float* zp = j >= 2 ? zb[(j + 1) % 3] : nullptr;
+      ++c->launches;
+      if (j == 0)
+        k_pc_sweep<true, false><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, (float)poly.c1[j],
+                                                   (float)poly.c2[j], geo_of(c), c->red_part,
+                                                   c->red_cnt, c->ctrl);
+      else
+        k_pc_sweep<false, false><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, (float)poly.c1[j],
+                                                    (float)poly.c2[j], geo_of(c), c->red_part,
+                                                    c->red_cnt, c->ctrl);
+    }
+    const int x0 = (nu - 1) % 3;
+    const MgL F = mg_fine(c);
+    const MgL C1 = mg_level(c, 0);
+    ++c->launches;
+    k_mg_restrict<<<grid_for(c, C1.g.N), NT, 0, s>>>(F, p.r, zb[x0], C1, c->mg[0].rhs);
+    const int ec = mg_cycle(c, 0, poly, c->mg_omega, s);
+    ++c->launches;
+    k_mg_prolong<<<blocks_cells(c), NT, 0, s>>>(F, zb[x0], C1, c->mg[0].x[ec], c->mg_omega);
+    // post-smoothing from the corrected z
+    for (int j = 0; j < nu; ++j) {
+      const int cur = (x0 + j) % 3;
+      float* zn = zb[(cur + 1) % 3];
+      const float* zp = j >= 1 ? zb[(cur + 2) % 3] : nullptr;
+      ++c->launches;
+      if (j == nu - 1)
+        k_pc_sweep<false, true><<<nb, NT, 0, s>>>(a, p, zp, zb[cur], zn, (float)poly.c1[j],
+                                                   (float)poly.c2[j], geo_of(c), c->red_part,
+                                                   c->red_cnt, c->ctrl);
+      else
+        k_pc_sweep<false, false><<<nb, NT, 0, s>>>(a, p, zp, zb[cur], zn, (float)poly.c1[j],
+                                                    (float)poly.c2[j], geo_of(c), c->red_part,
+                                                    c->red_cnt, c->ctrl);
+    }
+    return zb[(x0 + nu) % 3];
+  }
   for (int j = 0; j < poly.deg; ++j) {
     const bool last = j == poly.deg - 1;
     float* zn = zb[j % 3];
@@ -2435,19 +2728,20 @@ void launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s) {
       k_pc_sweep<false, false><<<nb, NT, 0, s>>>(a, p, zp, zc, zn, c1, c2, geo_of(c), c->red_part,
                                                   c->red_cnt, c->ctrl);
   }
+  return zb[(poly.deg - 1) % 3];
 }
 
-void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, int k, cudaStream_t s) {
+void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, const float* z, int k, cudaStream_t s) {
   PresArr a = pres_arr(c);
   const double* dold = (k & 1) ? a.d1 : a.d0;
   double* dnew = (k & 1) ? a.d0 : a.d1;
-  const float* z = c->pc[5 + (poly.deg - 1) % 3];
   const int nb = blocks_cells(c);
   ++c->launches;
   k_cg_dir<float><<<nb, NT, 0, s>>>(a, z, dold, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
   ++c->launches;
   k_pcg_upd<<<nb, NT, 0, s>>>(a, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
-  launch_pc_apply(c, poly, s);
+  (void)launch_pc_apply(c, poly, s);
+  (void)z;
 }
 
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {

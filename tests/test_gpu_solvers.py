@@ -42,7 +42,7 @@ def pressure_error_bound(A, b, p, tol):
     return 10.0 * tol * np.linalg.norm(b) / smin / np.linalg.norm(p)
 
 
-@pytest.mark.parametrize("deg", [1, 16])
+@pytest.mark.parametrize("deg", [1, 16, 0])
 @pytest.mark.parametrize("dim,nx,ny,nz,fm", [(2, 32, 24, 1, 0), (2, 33, 17, 1, 1), (3, 10, 9, 7, 0)])
 def test_pressure_solve_matches_direct_solution(E, dim, nx, ny, nz, fm, deg):
     rng = np.random.default_rng(nx + ny)
@@ -93,13 +93,52 @@ def test_polynomial_preconditioner_cuts_the_iterations(E):
             err = np.linalg.norm(p.cpu().numpy() - p_ref) / np.linalg.norm(p_ref)
             assert st.lin_resid <= PRESSURE_TOL and err <= bound, (deg, err, bound)
             iters[deg] = st.lin_iters
-        for bad in (0, 65):
+        for bad in (-1, 65):
             with pytest.raises(E.EremError) as ei:
                 ctx.set_pressure_precond(bad)
             assert ei.value.status == E.EREM_EINVAL
     for deg in (2, 5, 16):
         assert iters[deg] * deg / 3 <= iters[1], iters
     assert iters[64] <= iters[16], iters
+
+
+@pytest.mark.parametrize("dims", [(2, 96, 80, 1), (2, 67, 41, 1), (3, 40, 33, 21)])
+def test_multigrid_preconditioner(E, dims):
+    # degree 0: the multigrid V-cycle; the direct solution within the
+    # residual bound in a few tens of outer iterations on sigma = 2 fields,
+    # with a fraction of the fine-level work of the degree-32 polynomial; odd
+    # sizes coarsen with ragged aggregates
+    dim, nx, ny, nz = dims
+    rng = np.random.default_rng(nx)
+    g = fv.Grid(dim, nx, ny, nz)
+    ph = fv.Physics(head_left=1.0, head_right=0.0, fluid_model=0)
+    lnk = rng.normal(0, 2.0, g.n)
+    A, b = fv.pressure_system(g, ph, lnk, None)
+    p_ref = ts.pressure_solve_direct(g, ph, lnk, None)
+    bound = pressure_error_bound(A, b, p_ref, PRESSURE_TOL) if g.n < 6000 else None
+    iters = {}
+    with E.Context(dim, nx, ny, nz, physics=E.Physics(1, 1, 1.0, 0.0, 80.0, 0)) as ctx:
+        for deg in (32, 0):
+            ctx.set_pressure_precond(deg)
+            p = _t(np.zeros(g.n))
+            st = ctx.pressure_solve(_t(lnk), None, p, tol=PRESSURE_TOL, maxit=20000)
+            got = p.cpu().numpy()
+            assert st.lin_resid <= PRESSURE_TOL, deg
+            err = np.linalg.norm(got - p_ref) / np.linalg.norm(p_ref)
+            r = np.linalg.norm(A @ got - b) / np.linalg.norm(b)
+            assert r < 10 * PRESSURE_TOL, (deg, r)
+            if bound is not None:
+                assert err <= bound, (deg, err, bound)
+            iters[deg] = st.lin_iters
+        with pytest.raises(E.EremError) as ei:
+            ctx.set_pressure_multigrid(0, 1.8)
+        assert ei.value.status == E.EREM_EINVAL
+        with pytest.raises(E.EremError) as ei:
+            ctx.set_pressure_multigrid(3, 2.0)
+        assert ei.value.status == E.EREM_EINVAL
+    # fine-level work: 2 nu + 2 sweep-sized passes per V-cycle against 32
+    # sweeps per polynomial application
+    assert iters[0] < 40 and iters[0] * (2 * 3 + 2) < 0.5 * iters[32] * 32, iters
 
 
 def test_pressure_solve_host_pointers_and_maxit(E):
