@@ -228,7 +228,8 @@ EREM_API erem_status erem_step_forced(erem_ctx* ctx, double* T, double dt, doubl
  * Table ros2 (ROS2(1), two stages) or Table ros3 (ROS3p, three stages):
  *   (I/(dt gamma) - J_n) k_i = G(T + sum_{j<i} a_ij k_j) - sum_{j<i} c_ij/dt k_j,
  *   T <- T + sum_i b_i k_i.
- * Every stage system is solved by Jacobi-preconditioned BiCGSTAB in FP64 to
+ * Every stage system is solved by BiCGSTAB in FP64 (preconditioner:
+ * erem_set_stage_precond, a multigrid V-cycle by default) to
  * ||r - A k||_2 <= lin_tol ||r||_2 (maxit iterations).  For ROS2(1) and
  * ROS3p, stats->err_est = RMS over the cells of y - y_hat, the difference to
  * the embedded solution (weights b_hat of the tables: orders 1 and 2).
@@ -440,6 +441,16 @@ EREM_API erem_status erem_set_leja_points(erem_ctx* ctx, int kind);
  * preconditioned Krylov methods for the same system.
  * Errors: EINVAL (ctx NULL, degree outside 0..64). */
 EREM_API erem_status erem_set_pressure_precond(erem_ctx* ctx, int degree);
+
+/* Preconditioner of the Rosenbrock stage systems (sigma I - J) k = r for
+ * later rosm_step / rosm_integrate calls: 0 = Jacobi BiCGSTAB; 1 (default)
+ * = BiCGSTAB with one multigrid V-cycle as right preconditioner (aggregates
+ * of 2 x 2 (x 2) cells, a Galerkin coarse operator with one coupling per
+ * direction, two damped Jacobi sweeps (weight 0.8) before and after, 40 on
+ * the coarsest level of <= 512 cells; FP32; a fixed linear map up to
+ * rounding).  The stage tolerance and its meaning are unchanged.
+ * Errors: EINVAL. */
+EREM_API erem_status erem_set_stage_precond(erem_ctx* ctx, int kind);
 
 /* Multigrid parameters (degree 0 above): nu in 1..16, omega in (0, 2).
  * Errors: EINVAL. */

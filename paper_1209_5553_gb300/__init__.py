@@ -164,6 +164,7 @@ _sigs = {
     "erem_hold_interval": (_I, [_P, _I, _D, _D]),
     "erem_set_pressure_precond": (_I, [_P, _I]),
     "erem_set_pressure_multigrid": (_I, [_P, _I, _D]),
+    "erem_set_stage_precond": (_I, [_P, _I]),
     "erem_adjoint_begin": (_I, [_P, _P]),
     "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
     "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -643,6 +644,10 @@ class Context:
 
     def set_pressure_precond(self, degree):
         erem_set_pressure_precond(self._h, degree)
+
+    def set_stage_precond(self, kind):
+        """Rosenbrock stage solves: 0 = Jacobi BiCGSTAB, 1 = multigrid (default)."""
+        _check(self._h, _lib.erem_set_stage_precond(self._h, int(kind)))
 
     def set_pressure_multigrid(self, nu=3, omega=1.8):
         _check(self._h, _lib.erem_set_pressure_multigrid(self._h, int(nu), float(omega)))

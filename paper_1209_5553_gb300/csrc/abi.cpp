@@ -680,15 +680,52 @@ void fill_interval(const erem_ctx* c, erem_stats* st) {
 }
 
 // BiCGSTAB solve of (sigma I - J) x = b (b padded); x in kv[0].
+// Levels of the stage multigrid: the fine level, then halve every dimension
+// > 1 until at most 512 cells remain (at least one coarse level).
+erem_status ensure_smg(erem_ctx* c) {
+  if (!c->smg.empty()) return EREM_OK;
+  int nx = c->nx, ny = c->ny, nz = c->nz;
+  const int nk = c->dim == 3 ? 6 : 4;
+  auto add = [&](int ax, int ay, int az, size_t n) -> erem_status {
+    SmgLevel m;
+    m.nx = ax;
+    m.ny = ay;
+    m.nz = az;
+    c->smg.push_back(m);
+    SmgLevel& L = c->smg.back();
+    for (float** a : {&L.D, &L.Dinv, &L.rhs, &L.x[0], &L.x[1], &L.x[2]}) EREM_TRY(dalloc_t(c, a, n));
+    for (int q = 0; q < nk; ++q) EREM_TRY(dalloc_t(c, &L.c[q], n));
+    return EREM_OK;
+  };
+  EREM_TRY(add(nx, ny, nz, (size_t)c->Np));
+  while (c->smg.size() < 2 || (long long)nx * ny * nz > 512) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = c->dim == 3 ? (nz + 1) / 2 : 1;
+    if (c->smg.size() >= 2 && cx == nx && cy == ny && cz == nz) break;
+    nx = cx;
+    ny = cy;
+    nz = cz;
+    EREM_TRY(add(nx, ny, nz, (size_t)nx * ny * nz));
+  }
+  return EREM_OK;
+}
+
 erem_status bicg_solve(erem_ctx* c, const double* b, double sigma, double tol, int maxit,
                        cudaStream_t s, int* iters, double* resid) {
+  const bool mg = c->stage_precond == 1;
+  if (mg) {
+    EREM_TRY(ensure_smg(c));
+    launch_smg_setup(c, sigma, s);
+  }
   launch_bicg_init(c, b, sigma, tol, s);
   int it = 0;
   while (true) {
     EREM_TRY(read_ctrl(c, s));
     if (c->ctrl_h->lin_done || it >= maxit) break;
-    const int n = std::min(8, maxit - it);
-    for (int k = 0; k < n; ++k) launch_bicg_iter(c, sigma, s);
+    const int n = std::min(mg ? 2 : 8, maxit - it);
+    for (int k = 0; k < n; ++k) {
+      if (mg) launch_bicg_iter_mg(c, sigma, s);
+      else launch_bicg_iter(c, sigma, s);
+    }
     EREM_TRY(check_launch(c, "bicgstab"));
     it += n;
   }
@@ -1080,6 +1117,12 @@ erem_status erem_destroy(erem_ctx* c) {
   for (float* p : c->pc)
     if (p) cudaFree(p);
   if (c->pc_diag) cudaFree(c->pc_diag);
+  for (SmgLevel& m : c->smg) {
+    for (float* p : {m.D, m.Dinv, m.rhs, m.x[0], m.x[1], m.x[2]})
+      if (p) cudaFree(p);
+    for (float* p : m.c)
+      if (p) cudaFree(p);
+  }
   for (MgLevel& m : c->mg)
     for (float* p : {m.diag, m.dinv, m.Ux, m.Uy, m.Uz, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3]})
       if (p) cudaFree(p);
@@ -1523,6 +1566,14 @@ erem_status erem_set_pressure_precond(erem_ctx* c, int degree) {
   if (degree < 0 || degree > kMaxPcDeg)
     return fail(c, EREM_EINVAL, "preconditioner degree must be in 0.." + std::to_string(kMaxPcDeg));
   c->pc_deg = degree;
+  return EREM_OK;
+}
+
+erem_status erem_set_stage_precond(erem_ctx* c, int kind) {
+  if (!c) return EREM_EINVAL;
+  if (kind != 0 && kind != 1)
+    return fail(c, EREM_EINVAL, "stage preconditioner: 0 (Jacobi) or 1 (multigrid)");
+  c->stage_precond = kind;
   return EREM_OK;
 }
 

@@ -158,6 +158,19 @@ struct MgLevel {
   float* x[4] = {};
 };
 
+// One level of the multigrid preconditioner of the Rosenbrock stage systems
+// (sigma I - J, non-symmetric): A x = D x - sum_k c_k x_(neighbour k),
+// k = west, east, south, north, bottom, top; FP32.  Level 0 has the padded
+// layout of the context, coarse levels (aggregates of 2 x 2 (x 2) cells) an
+// unpadded one.
+struct SmgLevel {
+  int nx = 0, ny = 0, nz = 0;
+  float *D = nullptr, *Dinv = nullptr;
+  float* c[6] = {};
+  float* rhs = nullptr;
+  float* x[3] = {};
+};
+
 struct DDEntry {
   double c = 0, gamma = 0;
   int M = -1;
@@ -213,6 +226,9 @@ struct erem_ctx {
   std::vector<erem::MgLevel> mg;
   int mg_nu = 3;          // Chebyshev-Jacobi smoothing steps before and after
   float mg_omega = 1.8f;  // weight of the coarse correction
+  // Rosenbrock stage systems: 0 = Jacobi BiCGSTAB, 1 = multigrid-preconditioned
+  int stage_precond = 1;
+  std::vector<erem::SmgLevel> smg;   // smg[0] = the fine level
   // staging for host pointers (allocated on first use)
   double* stage[8] = {};
   // Krylov basis and work vectors (allocated on first use)
@@ -328,6 +344,10 @@ void launch_pc_setup(const erem_ctx* c, cudaStream_t s);
 const float* launch_pc_apply(const erem_ctx* c, const PcPoly& poly, cudaStream_t s);
 void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, const float* z, int k, cudaStream_t s);
 void launch_mg_setup(const erem_ctx* c, cudaStream_t s);
+// stage multigrid: operators of every level for sigma I - J; one BiCGSTAB
+// iteration with the V-cycle as right preconditioner
+void launch_smg_setup(const erem_ctx* c, double sigma, cudaStream_t s);
+void launch_bicg_iter_mg(const erem_ctx* c, double sigma, cudaStream_t s);
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s);
 
 // stage solver (BiCGSTAB) for (sigma I - J) x = b

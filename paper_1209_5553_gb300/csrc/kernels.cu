@@ -2218,6 +2218,209 @@ __global__ void k_bicg_r(BiArr a, Geo g, double* part, unsigned* cnt, Ctrl* ctrl
 }
 
 // ---------------------------------------------------------------------------
+// Multigrid preconditioner of the Rosenbrock stage systems (sigma I - J),
+// non-symmetric (upwind): the same aggregates and piecewise-constant
+// transfers as the pressure multigrid, a Galerkin coarse operator that keeps
+// one coupling per direction (a coarse coupling sums the children's
+// couplings that leave the aggregate that way, the coarse diagonal sums the
+// children's diagonals minus their couplings inside the aggregate), damped
+// Jacobi smoothing (weight 0.8, a fixed linear smoother: BiCGSTAB needs a
+// fixed preconditioner) and a fixed number of damped Jacobi sweeps on the
+// coarsest level.
+// ---------------------------------------------------------------------------
+struct MgN {
+  float *D, *Dinv;
+  float* c[6];  // west, east, south, north, bottom, top
+  Geo g;
+};
+
+__device__ __forceinline__ float smg_offdiag(const MgN& L, const float* __restrict__ x, int ip, int ix,
+                                             int iy, int iz) {
+  float s = 0.0f;
+  if (ix > 0) s = fmaf(L.c[0][ip], x[ip - 1], s);
+  if (ix < L.g.nx - 1) s = fmaf(L.c[1][ip], x[ip + 1], s);
+  if (iy > 0) s = fmaf(L.c[2][ip], x[ip - L.g.px], s);
+  if (iy < L.g.ny - 1) s = fmaf(L.c[3][ip], x[ip + L.g.px], s);
+  if (L.g.dim == 3) {
+    if (iz > 0) s = fmaf(L.c[4][ip], x[ip - L.g.plane], s);
+    if (iz < L.g.nz - 1) s = fmaf(L.c[5][ip], x[ip + L.g.plane], s);
+  }
+  return s;
+}
+
+// level 0: D = sigma - J_ii, c_k = J's coupling k (J >= 0 off the diagonal)
+__global__ void k_smg_setup(JIn J, double sigma, MgN L) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < L.g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, L.g, ix, iy, iz, ip);
+    const double d = sigma - J.c[0][ip];
+    L.D[ip] = (float)d;
+    L.Dinv[ip] = (float)(1.0 / d);
+    const int nk = L.g.dim == 3 ? 6 : 4;
+    for (int q = 0; q < nk; ++q) L.c[q][ip] = (float)J.c[q + 1][ip];
+  }
+}
+
+__global__ void k_smg_coarsen(MgN f, MgN c) {
+  for (int I = blockIdx.x * NT + threadIdx.x; I < c.g.N; I += gridDim.x * NT) {
+    int X, Y, Z, IP;
+    cell_of(I, c.g, X, Y, Z, IP);
+    const int xs = 2 * X, ys = 2 * Y, zs = f.g.dim == 3 ? 2 * Z : 0;
+    const int xe = min(xs + 2, f.g.nx), ye = min(ys + 2, f.g.ny);
+    const int ze = f.g.dim == 3 ? min(zs + 2, f.g.nz) : 1;
+    double d = 0.0, cc[6] = {0, 0, 0, 0, 0, 0};
+    for (int iz = zs; iz < ze; ++iz)
+      for (int iy = ys; iy < ye; ++iy)
+        for (int ix = xs; ix < xe; ++ix) {
+          const int ip = ix + f.g.px * (iy + f.g.ny * iz);
+          d += f.D[ip];
+          // a coupling inside the aggregate moves to the diagonal, one that
+          // leaves it to the coarse coupling of that direction
+          if (ix > 0) { if (ix - 1 >= xs) d -= f.c[0][ip]; else cc[0] += f.c[0][ip]; }
+          if (ix < f.g.nx - 1) { if (ix + 1 < xe) d -= f.c[1][ip]; else cc[1] += f.c[1][ip]; }
+          if (iy > 0) { if (iy - 1 >= ys) d -= f.c[2][ip]; else cc[2] += f.c[2][ip]; }
+          if (iy < f.g.ny - 1) { if (iy + 1 < ye) d -= f.c[3][ip]; else cc[3] += f.c[3][ip]; }
+          if (f.g.dim == 3) {
+            if (iz > 0) { if (iz - 1 >= zs) d -= f.c[4][ip]; else cc[4] += f.c[4][ip]; }
+            if (iz < f.g.nz - 1) { if (iz + 1 < ze) d -= f.c[5][ip]; else cc[5] += f.c[5][ip]; }
+          }
+        }
+    c.D[IP] = (float)d;
+    c.Dinv[IP] = (float)(1.0 / d);
+    const int nk = c.g.dim == 3 ? 6 : 4;
+    for (int q = 0; q < nk; ++q) c.c[q][IP] = (float)cc[q];
+  }
+}
+
+// damped Jacobi: xo = xi + w D^-1 (rhs - A xi); xi = NULL means 0
+__global__ void k_smg_jacobi(MgN L, const float* __restrict__ rhs, const float* __restrict__ xi,
+                             float* __restrict__ xo, float w) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < L.g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, L.g, ix, iy, iz, ip);
+    if (!xi) {
+      xo[ip] = w * L.Dinv[ip] * rhs[ip];
+      continue;
+    }
+    const float x = xi[ip];
+    const float res = rhs[ip] - fmaf(L.D[ip], x, -smg_offdiag(L, xi, ip, ix, iy, iz));
+    xo[ip] = fmaf(w * L.Dinv[ip], res, x);
+  }
+}
+
+// rhs_c = P^T (rhs_f - A_f x_f)
+__global__ void k_smg_restrict(MgN f, const float* __restrict__ rhs_f, const float* __restrict__ x_f,
+                               MgN c, float* __restrict__ rhs_c) {
+  for (int I = blockIdx.x * NT + threadIdx.x; I < c.g.N; I += gridDim.x * NT) {
+    int X, Y, Z, IP;
+    cell_of(I, c.g, X, Y, Z, IP);
+    const int xe = min(2 * X + 2, f.g.nx), ye = min(2 * Y + 2, f.g.ny);
+    const int ze = f.g.dim == 3 ? min(2 * Z + 2, f.g.nz) : 1;
+    float acc = 0.0f;
+    for (int iz = (f.g.dim == 3 ? 2 * Z : 0); iz < ze; ++iz)
+      for (int iy = 2 * Y; iy < ye; ++iy)
+        for (int ix = 2 * X; ix < xe; ++ix) {
+          const int ip = ix + f.g.px * (iy + f.g.ny * iz);
+          acc += rhs_f[ip] - fmaf(f.D[ip], x_f[ip], -smg_offdiag(f, x_f, ip, ix, iy, iz));
+        }
+    rhs_c[IP] = acc;
+  }
+}
+
+// x_f += P x_c
+__global__ void k_smg_prolong(Geo fg, float* __restrict__ x_f, Geo cg, const float* __restrict__ x_c) {
+  for (int i = blockIdx.x * NT + threadIdx.x; i < fg.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, fg, ix, iy, iz, ip);
+    x_f[ip] += x_c[(ix >> 1) + cg.px * ((iy >> 1) + cg.ny * (fg.dim == 3 ? (iz >> 1) : 0))];
+  }
+}
+
+// coarsest level (N <= a few thousand): `sweeps` damped Jacobi sweeps from 0
+// in one block, ping-ponging between x and tmp; the result ends in x
+__global__ void __launch_bounds__(512) k_smg_coarse(MgN L, const float* __restrict__ rhs,
+                                                    float* __restrict__ x, float* __restrict__ tmp,
+                                                    int sweeps, float w) {
+  const int N = L.g.N;
+  for (int i = threadIdx.x; i < N; i += 512) x[i] = w * L.Dinv[i] * rhs[i];
+  __syncthreads();
+  float* a = x;
+  float* b = tmp;
+  for (int it = 1; it < sweeps; ++it) {
+    for (int i = threadIdx.x; i < N; i += 512) {
+      int ix, iy, iz, ip;
+      cell_of(i, L.g, ix, iy, iz, ip);
+      const float res = rhs[ip] - fmaf(L.D[ip], a[ip], -smg_offdiag(L, a, ip, ix, iy, iz));
+      b[ip] = fmaf(w * L.Dinv[ip], res, a[ip]);
+    }
+    __syncthreads();
+    float* t = a;
+    a = b;
+    b = t;
+  }
+  if (a != x) {
+    for (int i = threadIdx.x; i < N; i += 512) x[i] = a[i];
+  }
+}
+
+// BiCGSTAB with the V-cycle as right preconditioner: the direction and the
+// intermediate residual go to the V-cycle in FP32, its output comes back in
+// FP64 (y, z of the Jacobi form)
+__global__ void k_bicg_p_mg(BiArr a, float* __restrict__ p32, Geo g, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double* L = ctrl->lin;
+  const double beta = (L[K_RHO] / L[K_RHO_PREV]) * (L[K_ALPHA] / L[K_OMEGA]);
+  const double omega = L[K_OMEGA];
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double pn = a.r[ip] + beta * (a.p[ip] - omega * a.v[ip]);
+    a.p[ip] = pn;
+    p32[ip] = (float)pn;
+  }
+}
+
+__global__ void k_bicg_s_mg(BiArr a, float* __restrict__ s32, Geo g, double* part, unsigned* cnt,
+                            Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (*(volatile int*)&ctrl->lin_done) return;
+  const double alpha = ctrl->lin[K_ALPHA];
+  double ss = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const double s = a.r[ip] - alpha * a.v[ip];
+    a.s[ip] = s;
+    a.x[ip] += alpha * a.y[ip];
+    s32[ip] = (float)s;
+    ss += s * s;
+  }
+  double vals[1] = {block_reduce<0>(ss, sh)};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double s = gather_partials<0>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      ctrl->lin[K_SS] = s;
+      if (s <= ctrl->lin[K_TOL2]) {
+        ctrl->lin[K_RR] = s;
+        ctrl->lin_it += 1;
+        ctrl->lin_done = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_f2d(const float* __restrict__ in, double* __restrict__ out, Geo g, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->lin_done) return;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    out[ip] = (double)in[ip];
+  }
+}
+
+
+// ---------------------------------------------------------------------------
 // host-side argument packing
 // ---------------------------------------------------------------------------
 Geo geo_of(const erem_ctx* c) {
@@ -2755,6 +2958,81 @@ void launch_bicg_init(const erem_ctx* c, const double* b, double sigma, double t
   ++c->launches;
   k_bicg_init<<<blocks_cells(c), NT, 0, s>>>(jin(c), bi_arr(c), b, sigma, tol, geo_of(c),
                                              c->red_part, c->red_cnt, c->ctrl);
+}
+
+namespace {
+MgN smg_level(const erem_ctx* c, int l) {
+  const SmgLevel& m = c->smg[l];
+  MgN L;
+  L.D = m.D;
+  L.Dinv = m.Dinv;
+  for (int q = 0; q < 6; ++q) L.c[q] = m.c[q];
+  L.g = l == 0 ? geo_of(c) : geo_level(c->dim, m.nx, m.ny, m.nz);
+  return L;
+}
+
+constexpr float kSmgW = 0.8f;       // damped Jacobi weight
+constexpr int kSmgCoarseSweeps = 40;
+
+// V-cycle on level l for smg[l].rhs: two damped Jacobi sweeps, restriction,
+// the coarser correction, prolongation, two sweeps; returns the index of the
+// buffer that holds the result
+int smg_cycle(const erem_ctx* c, int l, cudaStream_t s) {
+  const SmgLevel& m = c->smg[l];
+  const MgN L = smg_level(c, l);
+  if (l + 1 == (int)c->smg.size()) {
+    ++c->launches;
+    k_smg_coarse<<<1, 512, 0, s>>>(L, m.rhs, m.x[0], m.x[1], kSmgCoarseSweeps, kSmgW);
+    return 0;
+  }
+  const int nb = grid_for(c, L.g.N);
+  c->launches += 2;
+  k_smg_jacobi<<<nb, NT, 0, s>>>(L, m.rhs, nullptr, m.x[0], kSmgW);
+  k_smg_jacobi<<<nb, NT, 0, s>>>(L, m.rhs, m.x[0], m.x[1], kSmgW);
+  const MgN Lc = smg_level(c, l + 1);
+  ++c->launches;
+  k_smg_restrict<<<grid_for(c, Lc.g.N), NT, 0, s>>>(L, m.rhs, m.x[1], Lc, c->smg[l + 1].rhs);
+  const int ec = smg_cycle(c, l + 1, s);
+  c->launches += 3;
+  k_smg_prolong<<<nb, NT, 0, s>>>(L.g, m.x[1], Lc.g, c->smg[l + 1].x[ec]);
+  k_smg_jacobi<<<nb, NT, 0, s>>>(L, m.rhs, m.x[1], m.x[2], kSmgW);
+  k_smg_jacobi<<<nb, NT, 0, s>>>(L, m.rhs, m.x[2], m.x[0], kSmgW);
+  return 0;
+}
+}  // namespace
+
+void launch_smg_setup(const erem_ctx* c, double sigma, cudaStream_t s) {
+  const MgN L0 = smg_level(c, 0);
+  ++c->launches;
+  k_smg_setup<<<blocks_cells(c), NT, 0, s>>>(jin(c), sigma, L0);
+  for (size_t l = 1; l < c->smg.size(); ++l) {
+    const MgN cl = smg_level(c, (int)l);
+    ++c->launches;
+    k_smg_coarsen<<<grid_for(c, cl.g.N), NT, 0, s>>>(smg_level(c, (int)l - 1), cl);
+  }
+}
+
+void launch_bicg_iter_mg(const erem_ctx* c, double sigma, cudaStream_t s) {
+  const int nb = blocks_cells(c);
+  const Geo g = geo_of(c);
+  BiArr a = bi_arr(c);
+  float* rhs0 = c->smg[0].rhs;
+  ++c->launches;
+  k_bicg_p_mg<<<nb, NT, 0, s>>>(a, rhs0, g, c->ctrl);
+  int e = smg_cycle(c, 0, s);
+  ++c->launches;
+  k_f2d<<<nb, NT, 0, s>>>(c->smg[0].x[e], a.y, g, c->ctrl);
+  ++c->launches;
+  k_bicg_v<<<nb, NT, 0, s>>>(jin(c), a, sigma, g, c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_bicg_s_mg<<<nb, NT, 0, s>>>(a, rhs0, g, c->red_part, c->red_cnt, c->ctrl);
+  e = smg_cycle(c, 0, s);
+  ++c->launches;
+  k_f2d<<<nb, NT, 0, s>>>(c->smg[0].x[e], a.z, g, c->ctrl);
+  ++c->launches;
+  k_bicg_t<<<nb, NT, 0, s>>>(jin(c), a, sigma, g, c->red_part, c->red_cnt, c->ctrl);
+  ++c->launches;
+  k_bicg_r<<<nb, NT, 0, s>>>(a, g, c->red_part, c->red_cnt, c->ctrl);
 }
 
 void launch_bicg_iter(const erem_ctx* c, double sigma, cudaStream_t s) {

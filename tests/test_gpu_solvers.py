@@ -233,6 +233,34 @@ def test_adaptive_rosenbrock_matches_oracle(E, scheme):
     assert C.rel_l2(got, ref.T) < 1e-8
 
 
+@pytest.mark.parametrize("dims", [(2, 70, 52, 1, 1), (3, 20, 17, 11, 0)])
+def test_stage_multigrid_matches_jacobi_bicgstab(E, dims):
+    # the ROS2(1) and ROS3p steps with the multigrid-preconditioned stage
+    # solves equal those with Jacobi BiCGSTAB within the stage-solve bound and
+    # take several times fewer iterations
+    dim, nx, ny, nz, fm = dims
+    case = C.random_case(dim, nx, ny, nz, seed=nx, fluid_model=fm)
+    tau = 0.05
+    fields = lambda: (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam))
+    out = {}
+    with E.Context(dim, nx, ny, nz, physics=case.gpu_physics()) as ctx:
+        for scheme in (E.EREM_ROS2, E.EREM_ROS3P):
+            for kind in (0, 1):
+                ctx.set_stage_precond(kind)
+                T = _t(case.T0)
+                st = ctx.rosm_step(T, tau, scheme, *fields(), lin_tol=STAGE_TOL, maxit=20000)
+                out[(scheme, kind)] = (T.cpu().numpy(), st.lin_iters, st.err_est)
+        with pytest.raises(E.EremError) as ei:
+            ctx.set_stage_precond(2)
+        assert ei.value.status == E.EREM_EINVAL
+    for scheme in (E.EREM_ROS2, E.EREM_ROS3P):
+        (Tj, ij, ej), (Tm, im, em) = out[(scheme, 0)], out[(scheme, 1)]
+        inc = np.linalg.norm(Tj - case.T0)
+        assert np.linalg.norm(Tm - Tj) < 1e-9 * inc, scheme
+        assert em == pytest.approx(ej, rel=1e-6, abs=1e-12)
+        assert 3 * im < ij, (scheme, im, ij)
+
+
 def test_rosm_then_erem_share_the_context(E):
     case = C.heat2d_rect(24, 20)
     prob = case.problem()
