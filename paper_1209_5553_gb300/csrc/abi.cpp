@@ -140,12 +140,13 @@ PcPoly pc_poly(int deg, double lo = -1.0) {
 }
 
 // Levels of the pressure multigrid: halve every dimension > 1 (rounding up)
-// until at most 512 cells remain (at least one coarse level).
+// until at most kMgCoarsest cells remain (at least one coarse level).  A small
+// coarsest level keeps its one-block solve short (a few dozen barriers).
 erem_status ensure_mg(erem_ctx* c) {
   if (!c->pc_diag) EREM_TRY(dalloc_t(c, &c->pc_diag, (size_t)c->Np));
   if (!c->mg.empty()) return EREM_OK;
   int nx = c->nx, ny = c->ny, nz = c->nz;
-  while (c->mg.empty() || (long long)nx * ny * nz > 512) {
+  while (c->mg.empty() || (long long)nx * ny * nz > kMgCoarsest) {
     const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = c->dim == 3 ? (nz + 1) / 2 : 1;
     if (!c->mg.empty() && cx == nx && cy == ny && cz == nz) break;
     nx = cx;
@@ -681,7 +682,7 @@ void fill_interval(const erem_ctx* c, erem_stats* st) {
 
 // BiCGSTAB solve of (sigma I - J) x = b (b padded); x in kv[0].
 // Levels of the stage multigrid: the fine level, then halve every dimension
-// > 1 until at most 512 cells remain (at least one coarse level).
+// > 1 until at most kMgCoarsest cells remain (at least one coarse level).
 erem_status ensure_smg(erem_ctx* c) {
   if (!c->smg.empty()) return EREM_OK;
   int nx = c->nx, ny = c->ny, nz = c->nz;
@@ -698,7 +699,7 @@ erem_status ensure_smg(erem_ctx* c) {
     return EREM_OK;
   };
   EREM_TRY(add(nx, ny, nz, (size_t)c->Np));
-  while (c->smg.size() < 2 || (long long)nx * ny * nz > 512) {
+  while (c->smg.size() < 2 || (long long)nx * ny * nz > kMgCoarsest) {
     const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = c->dim == 3 ? (nz + 1) / 2 : 1;
     if (c->smg.size() >= 2 && cx == nx && cy == ny && cz == nz) break;
     nx = cx;

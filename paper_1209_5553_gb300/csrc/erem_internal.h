@@ -17,6 +17,7 @@ constexpr int kThreads = 256;      // threads per block of every kernel
 constexpr int kMaxTerms = 4096;    // largest Leja degree a context accepts
 constexpr int kMaxPcDeg = 64;      // largest degree of the pressure CG's polynomial preconditioner
 constexpr int kDefaultPcDeg = 0;   // its default: multigrid (1 = plain Jacobi CG)
+constexpr int kMgCoarsest = 512;   // cells of the coarsest multigrid level, at most
 constexpr int kRedSlots = 4;       // reduction values per block
 
 // Bits of Ctrl::flags raised by the set-up kernels.

@@ -1875,6 +1875,7 @@ __global__ void k_mg_prolong(MgL f, float* __restrict__ x_f, MgL c, const float*
 // Coarsest level: Jacobi-preconditioned CG in one block, from x = 0, to
 // ||r|| <= rtol ||b|| or maxit iterations (N <= a few thousand cells).
 constexpr int kMgCoarseThreads = 512;
+constexpr float kMgCoarseRtol = 1e-3f;  // the coarsest solve only needs to remove smooth error
 __device__ float mg_block_sum(float v, float* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -2846,7 +2847,7 @@ int mg_cycle(const erem_ctx* c, int l, const PcPoly& poly, float omega, cudaStre
   if (l + 1 == (int)c->mg.size()) {
     ++c->launches;
     k_mg_coarse_cg<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3], 400,
-                                                   1e-5f);
+                                                   kMgCoarseRtol);
     return 0;
   }
   int cur = mg_smooth(c, l, poly, 0, true, s);
