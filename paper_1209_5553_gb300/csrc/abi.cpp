@@ -176,7 +176,10 @@ erem_status run_pressure_cg(erem_ctx* c, double tol, int maxit, cudaStream_t s) 
   PcPoly P;
   const float* z = nullptr;
   launch_cg_init(c, tol, s);
-  if (prec) {
+  EREM_TRY(check_launch(c, "pressure CG set-up"));
+  EREM_TRY(read_ctrl(c, s));
+  EREM_TRY(check_flags(c));
+  if (prec && !c->ctrl_h->lin_done) {  // nothing to precondition when the guess solves it
     EREM_TRY(ensure_pc(c));
     if (mg) EREM_TRY(ensure_mg(c));
     // the multigrid smoother damps the upper part [1/4, 2] of the spectrum
@@ -184,10 +187,9 @@ erem_status run_pressure_cg(erem_ctx* c, double tol, int maxit, cudaStream_t s) 
     launch_pc_setup(c, s);
     if (mg) launch_mg_setup(c, s);
     z = launch_pc_apply(c, P, s);
+    EREM_TRY(check_launch(c, "pressure preconditioner set-up"));
+    EREM_TRY(read_ctrl(c, s));
   }
-  EREM_TRY(check_launch(c, "pressure CG set-up"));
-  EREM_TRY(read_ctrl(c, s));
-  EREM_TRY(check_flags(c));
   const int chunk = mg ? 2 : (prec ? std::max(2, 64 / c->pc_deg) : 32);
   int k = 0;
   while (!c->ctrl_h->lin_done && k < maxit) {
