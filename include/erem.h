@@ -442,6 +442,17 @@ EREM_API erem_status erem_set_leja_points(erem_ctx* ctx, int kind);
  * Errors: EINVAL (ctx NULL, degree outside 0..64). */
 EREM_API erem_status erem_set_pressure_precond(erem_ctx* ctx, int degree);
 
+/* Host arrays for erem_step's T.  mode 1 (default): when T is page-locked
+ * host memory mapped into the GPU's address space (cudaHostAlloc /
+ * cudaMallocHost; reached over NVLink-C2C on Grace systems), the fused
+ * linear-model path applies (fluid_model 0) and nx is a multiple of 4, a
+ * streaming kernel reads T once into the context's copy of T^n and the
+ * step's last kernel writes T^{n+1} directly: one pass each way, no staging
+ * copies; the call returns after the write is complete.  mode 0, other host
+ * memory and the other entry points: T is copied to a context buffer and
+ * back.  Errors: EINVAL. */
+EREM_API erem_status erem_set_host_access(erem_ctx* ctx, int mode);
+
 /* Preconditioner of the Rosenbrock stage systems (sigma I - J) k = r for
  * later rosm_step / rosm_integrate calls: 0 = Jacobi BiCGSTAB; 1 (default)
  * = BiCGSTAB with one multigrid V-cycle as right preconditioner (aggregates

@@ -165,6 +165,7 @@ _sigs = {
     "erem_set_pressure_precond": (_I, [_P, _I]),
     "erem_set_pressure_multigrid": (_I, [_P, _I, _D]),
     "erem_set_stage_precond": (_I, [_P, _I]),
+    "erem_set_host_access": (_I, [_P, _I]),
     "erem_adjoint_begin": (_I, [_P, _P]),
     "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
     "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -644,6 +645,11 @@ class Context:
 
     def set_pressure_precond(self, degree):
         erem_set_pressure_precond(self._h, degree)
+
+    def set_host_access(self, mode):
+        """erem_step with a pinned host T: 1 = kernels access it in place
+        (default), 0 = staged copies."""
+        _check(self._h, _lib.erem_set_host_access(self._h, int(mode)))
 
     def set_stage_precond(self, kind):
         """Rosenbrock stage solves: 0 = Jacobi BiCGSTAB, 1 = multigrid (default)."""

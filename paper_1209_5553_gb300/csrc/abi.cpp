@@ -56,6 +56,19 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory that the GPU can reach
+// directly (mapped under unified addressing; over NVLink-C2C on Grace
+// systems), or nullptr.
+double* host_mapped(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<double*>(a.devicePointer);
+}
+
 erem_status dalloc(erem_ctx* c, void** p, size_t bytes) {
   if (cudaMalloc(p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -76,7 +89,7 @@ erem_status dalloc_t(erem_ctx* c, T** p, size_t count) {
 erem_status resolve(erem_ctx* c, int slot, const double* ptr, bool copy_in, cudaStream_t s,
                     double** out) {
   if (!ptr) return fail(c, EREM_EINVAL, "NULL array argument");
-  if (is_device_ptr(ptr)) {
+  if ((slot == 0 && c->zc_active) || is_device_ptr(ptr)) {
     *out = const_cast<double*>(ptr);
     return EREM_OK;
   }
@@ -336,8 +349,8 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
   const double cg = c->cfoc / c->gam;  // the same for every substep level
   const double d0 = dd_entry(c, S, phi).d[0];
   *failed = *nonfinite = false;
-  if (fused_T)
-    launch_step_init(c, fused_T, d0, sp, s);  // also writes vrhs = G(T) and T^n
+  if (fused_T)  // also writes vrhs = G(T)
+    launch_step_init(c, fused_T, d0, sp, s);
   else
     launch_leja_init(c, u, d0, sp, s);
   int m = 1, qin = 0;
@@ -465,9 +478,13 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       if (k + 1 < S) launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
     }
     if (!ok) continue;
-    // fused start: T^n is the caller's array itself, updated in place
-    launch_finish(c, out, fused_T ? nullptr : base, S > 1 ? c->w : nullptr, c->P, delta, s,
-                  fused_T ? 1 : 0);
+    // fused start: T^n is the caller's array itself, updated in place; a host
+    // T (c->zc_out) is written once from T^n in Tn, where the fused kernel read it
+    if (c->zc_out)
+      launch_finish(c, c->zc_out, c->Tn, S > 1 ? c->w : nullptr, c->P, delta, s, 0);
+    else
+      launch_finish(c, out, fused_T ? nullptr : base, S > 1 ? c->w : nullptr, c->P, delta, s,
+                    fused_T ? 1 : 0);
     EREM_TRY(check_launch(c, "finish"));
     if (st) {
       st->substeps = S;
@@ -1241,9 +1258,30 @@ erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk
   EREM_TRY(parse_opts(c, opts, &o));
   double* Td = nullptr;
   const bool fused = c->phys.fluid_model == 0;
-  EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td, fused));
-  EREM_TRY(run_phi1(c, c->vrhs, c->Tn, Td, o, st, s, fused ? Td : nullptr));
-  EREM_TRY(finish_staged(c, T, Td, s));
+  // a page-locked host T (unpadded rows) is read once by a streaming kernel
+  // into Tn and written once by the last kernel (one pass each way over the
+  // link) instead of being staged by copies
+  double* Tz = (fused && c->host_access == 1 && c->px == c->nx && T && !is_device_ptr(T))
+                   ? host_mapped(T) : nullptr;
+  struct ZcScope {
+    erem_ctx* c;
+    ~ZcScope() {
+      c->zc_active = false;
+      c->zc_out = nullptr;
+    }
+  } zc_scope{c};
+  if (Tz) {
+    c->zc_active = true;
+    EREM_TRY(prepare_step(c, Tz, p, lnk, phi, lam, dt, true, s, &Td, fused));
+    launch_pack(c, Tz, c->Tn, s);
+    c->zc_out = Tz;
+    EREM_TRY(run_phi1(c, c->vrhs, c->Tn, c->Tn, o, st, s, c->Tn));
+    EREM_CUDA(c, cudaStreamSynchronize(s));
+  } else {
+    EREM_TRY(prepare_step(c, T, p, lnk, phi, lam, dt, true, s, &Td, fused));
+    EREM_TRY(run_phi1(c, c->vrhs, c->Tn, Td, o, st, s, fused ? Td : nullptr));
+    EREM_TRY(finish_staged(c, T, Td, s));
+  }
   fill_interval(c, st);
   if (st) {
     st->t_ms = now_ms() - t0;
@@ -1569,6 +1607,13 @@ erem_status erem_set_pressure_precond(erem_ctx* c, int degree) {
   if (degree < 0 || degree > kMaxPcDeg)
     return fail(c, EREM_EINVAL, "preconditioner degree must be in 0.." + std::to_string(kMaxPcDeg));
   c->pc_deg = degree;
+  return EREM_OK;
+}
+
+erem_status erem_set_host_access(erem_ctx* c, int mode) {
+  if (!c) return EREM_EINVAL;
+  if (mode != 0 && mode != 1) return fail(c, EREM_EINVAL, "host access: 0 (staged) or 1 (in place)");
+  c->host_access = mode;
   return EREM_OK;
 }
 

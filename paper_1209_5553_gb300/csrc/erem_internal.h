@@ -249,6 +249,11 @@ struct erem_ctx {
   // cells), and the phi_2 increment delta^2 phi_2(delta J) D_t G
   double *fin_b = nullptr, *fin_w = nullptr, *fin_p2 = nullptr;
   double* ada_save = nullptr;  // rosm_integrate: T before an attempt [N]
+  // erem_step with a pinned host T read and written in place by the kernels
+  // (the first kernel also leaves T^n in Tn); host_access = 0 stages copies
+  int host_access = 1;
+  bool zc_active = false;
+  double* zc_out = nullptr;   // the host T the last kernel writes (device address)
   // FP32-bulk Horner pass: upwind flags, FP32 capacities, FP32 mu, FP32 face
   // sums of the current adjoint step
   unsigned char* adj_up = nullptr;
@@ -312,7 +317,8 @@ void launch_japply_add(const erem_ctx* c, const double* x, const double* v, doub
 void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
                       cudaStream_t s);
 void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
-                      cudaStream_t s);
+                      cudaStream_t s,
+                      double* Tcopy = nullptr);
 int leja_term_blocks_per_sm(const erem_ctx* c);
 void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
 void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,

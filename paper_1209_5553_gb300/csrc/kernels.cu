@@ -399,7 +399,7 @@ __global__ void k_inflow_forced(const double* __restrict__ icap, const double* _
 // 40 FP64 instructions per cell on GB300's slow FP64 pipe) by 8.
 template <typename Tq>
 __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
-                            double* __restrict__ G, Tq* __restrict__ q0,
+                            double* __restrict__ Tcopy, double* __restrict__ G, Tq* __restrict__ q0,
                             double* __restrict__ P, double d0, Geo g, StopParams sp,
                             double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
@@ -426,6 +426,7 @@ __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* 
     G[ip] = a;
     q0[ip] = (Tq)a;
     P[ip] = d0 * a;
+    if (Tcopy) Tcopy[ip] = Ti;
     bad |= !finite(a);
     tmax = fmax(tmax, fabs(Ti));
   }
@@ -452,8 +453,9 @@ __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* 
 template <typename Tq, int DIM>
 __global__ void __launch_bounds__(NT)
 k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
-                double* __restrict__ G, Tq* __restrict__ q0, double* __restrict__ P, double d0,
-                Geo g, StopParams sp, double* part, unsigned* cnt, Ctrl* ctrl) {
+                double* __restrict__ Tcopy, double* __restrict__ G, Tq* __restrict__ q0,
+                double* __restrict__ P, double d0, Geo g, StopParams sp, double* part,
+                unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     arm_ctrl(ctrl, sp);
@@ -511,6 +513,7 @@ k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__
     }
     stP<4>(G + i, a);
     stP<4>(P + i, p);
+    if (Tcopy) stP<4>(Tcopy + i, tc);
     if constexpr (sizeof(Tq) == 4) {
       *reinterpret_cast<float4*>(q0 + i) = make_float4(qv[0], qv[1], qv[2], qv[3]);
     } else {
@@ -2570,34 +2573,34 @@ void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopP
 }
 
 void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
-                      cudaStream_t s) {
+                      cudaStream_t s, double* Tcopy) {
   ++c->launches;
   if (c->px == c->nx) {  // unpadded rows: four cells per thread
     const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
     const Geo g = geo_of(c);
     if (c->prec == EREM_FP32_BULK) {
       if (c->dim == 3)
-        k_step_init_vec<float, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (float*)c->q[0], c->P,
+        k_step_init_vec<float, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (float*)c->q[0], c->P,
                                                     d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
       else
-        k_step_init_vec<float, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (float*)c->q[0], c->P,
+        k_step_init_vec<float, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (float*)c->q[0], c->P,
                                                     d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
     } else {
       if (c->dim == 3)
-        k_step_init_vec<double, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (double*)c->q[0],
+        k_step_init_vec<double, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (double*)c->q[0],
                                                      c->P, d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
       else
-        k_step_init_vec<double, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, c->vrhs, (double*)c->q[0],
+        k_step_init_vec<double, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (double*)c->q[0],
                                                      c->P, d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
     }
     return;
   }
   if (c->prec == EREM_FP32_BULK)
-    k_step_init<float><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, c->vrhs,
+    k_step_init<float><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs,
                                                       (float*)c->q[0], c->P, d0, geo_of(c), sp,
                                                       c->red_part, c->red_cnt, c->ctrl);
   else
-    k_step_init<double><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, c->vrhs,
+    k_step_init<double><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs,
                                                        (double*)c->q[0], c->P, d0, geo_of(c), sp,
                                                        c->red_part, c->red_cnt, c->ctrl);
 }

@@ -358,3 +358,36 @@ def test_leja_point_kind_switches_and_errors(E):
     ref = leja.phi1_leja(case.problem(case.T0).J(case.T0), v, case.dt, float(np.max(case.T0)),
                          LejaOptions(points="fast", replay=outs["fast"][0][1]))
     assert C.rel_l2(outs["fast"][0][0], ref.value) < FP64_TOL
+
+
+@pytest.mark.parametrize("name,make", [("heat2d_64", lambda: C.heat2d(64)),
+                                       ("ragged_37x23", lambda: C.heat2d_rect(37, 23)),
+                                       ("box_24x20x9", lambda: C.random_case(3, 24, 20, 9, seed=5))])
+def test_host_T_in_place_equals_device_T(E, name, make):
+    # erem_step with T in page-locked host memory read and written in place by
+    # the kernels, staged through copies, or on the device: bitwise equal
+    import torch
+
+    case = make()
+    fields = lambda: (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam))
+    outs = []
+    for kind in ("device", "pinned_in_place", "pinned_staged", "pageable"):
+        with _ctx(E, case, "fp32_bulk") as ctx:
+            if kind == "pinned_staged":
+                ctx.set_host_access(0)
+            if kind == "device":
+                T = _t(case.T0)
+            elif kind == "pageable":
+                T = case.T0.copy()
+            else:
+                T = torch.from_numpy(case.T0.copy()).pin_memory()
+            for k in range(3):
+                ctx.erem_step(T, case.dt, *(fields() if k == 0 else (None,) * 4))
+            outs.append(T.cpu().numpy() if hasattr(T, "cpu") else T.copy())
+        if kind == "pinned_staged":
+            with _ctx(E, case, "fp32_bulk") as ctx:
+                with pytest.raises(E.EremError) as ei:
+                    ctx.set_host_access(2)
+                assert ei.value.status == E.EREM_EINVAL
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
