@@ -2947,8 +2947,8 @@ void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, const float* z, int 
   k_cg_dir<float><<<nb, NT, 0, s>>>(a, z, dold, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
   ++c->launches;
   k_pcg_upd<<<nb, NT, 0, s>>>(a, dnew, geo_of(c), c->red_part, c->red_cnt, c->ctrl);
+  // the next z lands in the same buffer (the preconditioner's sweep count is fixed)
   (void)launch_pc_apply(c, poly, s);
-  (void)z;
 }
 
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {
