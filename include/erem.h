@@ -389,6 +389,22 @@ EREM_API erem_status erem_step_krylov(erem_ctx* ctx, double* T, const double* p,
  *   erem_adjoint_lnk(ctx, lnk, glnk, ...)  -> dL/dlnK.
  * ------------------------------------------------------------------------ */
 
+/* Adjoint tape.  record = 1: reserve a device arena of at least `bytes`
+ * (kept across calls, freed with the context), clear it, and from now on let
+ * every erem_step (fluid_model 0) record what erem_adjoint_step would
+ * otherwise recompute for that step: the start of every substep after the
+ * first (FP64 [N] each) and the Newton vectors q_0..q_m of every substep (in
+ * the Leja precision).  A step that does not fit is not recorded.
+ * erem_adjoint_step uses the last record when its schedule is the step's and
+ * then releases it (last in, first out), so replaying a checkpoint segment
+ * forward with the tape on and then stepping back through it computes every
+ * Newton vector once per segment instead of twice; the gradient is bitwise
+ * the same.  record = 0: stop recording and drop the records (the arena is
+ * kept).  Bytes per step: (s - 1) 8 N' + sum_k (m_k + 1) q N' with N' the
+ * padded cell count (round_up(nx, 4) ny nz) and q = 4 (FP32-bulk) or 8.
+ * Errors: EINVAL, ENOMEM. */
+EREM_API erem_status erem_adjoint_tape(erem_ctx* ctx, size_t bytes, int record);
+
 /* Clear the accumulated derivative with respect to the face fluxes.
  * Errors: EINVAL (no state, fluid_model != 0), ENOMEM, ECUDA. */
 EREM_API erem_status erem_adjoint_begin(erem_ctx* ctx, void* stream);

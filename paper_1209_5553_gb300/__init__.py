@@ -166,6 +166,7 @@ _sigs = {
     "erem_set_pressure_multigrid": (_I, [_P, _I, _D]),
     "erem_set_stage_precond": (_I, [_P, _I]),
     "erem_set_host_access": (_I, [_P, _I]),
+    "erem_adjoint_tape": (_I, [_P, ctypes.c_size_t, _I]),
     "erem_adjoint_begin": (_I, [_P, _P]),
     "erem_adjoint_step": (_I, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), _I, _P]),
     "erem_adjoint_lnk": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -660,6 +661,11 @@ class Context:
 
     def hold_interval(self, interval):
         erem_hold_interval(self._h, interval)
+
+    def adjoint_tape(self, nbytes, record=True):
+        """Reserve the adjoint tape (bytes) and record the following
+        erem_steps (record=True), or stop recording (record=False)."""
+        _check(self._h, _lib.erem_adjoint_tape(self._h, int(nbytes), 1 if record else 0))
 
     def adjoint_begin(self, stream=None):
         erem_adjoint_begin(self._h, stream)

@@ -7,7 +7,10 @@ Backward: the library's adjoint entry points (erem_adjoint_*), one step at a
 time from T^N back to T^0 with every step's Leja schedule frozen at its
 forward value; the states T^n are recomputed from checkpoints kept every
 ``checkpoint`` steps by replaying those schedules, so at most ``checkpoint``
-states are held at once.  Gradients with respect to ln K and T0.
+states are held at once.  With ``tape`` (default) the replay of a segment
+records its Newton vectors on the device (erem_adjoint_tape) and the adjoint
+steps use them instead of computing them a second time.  Gradients with
+respect to ln K and T0.
 
 The adjoint differentiates the run with the interval of every step held at
 its forward value; ``interval=`` holds it (``MisfitModel.interval`` of a
@@ -33,12 +36,15 @@ class MisfitModel:
 
     def __init__(self, dim, nx, ny, nz, physics: Physics, phi, lam, dt, steps, obs, data,
                  precision="fp32_bulk", checkpoint=10, tol=1e-6, pressure_tol=1e-12,
-                 replay=None, interval=None):
+                 replay=None, interval=None, tape=True):
         if physics.fluid_model != 0:
             raise ValueError("the adjoint needs fluid_model 0")
         self.ctx = Context(dim, nx, ny, nz, physics=physics, precision=precision)
         self.n = nx * ny * nz
         self.nx = nx
+        self.n_padded = (nx + 3) // 4 * 4 * ny * nz
+        self.qbytes = 4 if precision == "fp32_bulk" else 8
+        self.tape = bool(tape)
         self.physics = physics
         self.phi, self.lam = phi, lam
         self.dt, self.steps = float(dt), int(steps)
@@ -55,6 +61,15 @@ class MisfitModel:
         x = (torch.arange(self.nx, dtype=torch.float64, device=like.device) + 0.5) / self.nx
         ramp = self.physics.head_left + (self.physics.head_right - self.physics.head_left) * x
         return ramp.repeat(self.n // self.nx).contiguous()
+
+    def tape_bytes(self, scheds):
+        """Device bytes the adjoint tape needs for these steps."""
+        total = 0
+        for sc in scheds:
+            s = sc[0]
+            total += (s - 1) * 8 * self.n_padded
+            total += sum(m + 1 for m in sc[1:]) * self.qbytes * self.n_padded
+        return total
 
     def close(self):
         self.ctx.close()
@@ -95,13 +110,19 @@ class EremMisfit(torch.autograd.Function):
         starts = sorted(ckpts)
         for a, s0 in reversed(list(enumerate(starts))):
             s1 = starts[a + 1] if a + 1 < len(starts) else m.steps
+            if m.tape:  # every step of the segment recorded once, consumed backwards
+                m.ctx.adjoint_tape(m.tape_bytes(scheds[s0:s1]), True)
             states = [ckpts[s0].clone()]
             T = states[0].clone()
-            for n in range(s0, s1 - 1):
+            last = s1 if m.tape else s1 - 1
+            for n in range(s0, last):
                 m.ctx.erem_step(T, m.dt, opts=leja_opts(tol=m.tol, replay=scheds[n]))
-                states.append(T.clone())
+                if n + 1 < s1:
+                    states.append(T.clone())
             for n in range(s1 - 1, s0 - 1, -1):
                 m.ctx.adjoint_step(states[n - s0], lam, scheds[n])
+            if m.tape:
+                m.ctx.adjoint_tape(0, False)
         glnk = torch.zeros_like(lnk)
         m.ctx.adjoint_lnk(lnk, glnk, tol=m.pressure_tol)
         return glnk, lam, None

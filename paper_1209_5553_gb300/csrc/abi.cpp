@@ -353,6 +353,20 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     launch_step_init(c, fused_T, d0, sp, s);
   else
     launch_leja_init(c, u, d0, sp, s);
+  // taping (phi_1 of erem_step): the terms write q_m straight into the tape,
+  // slot m of this interpolation, when the arena has room for every term
+  const size_t qbytes = (size_t)c->Np * (c->prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double));
+  char* slot0 = nullptr;
+  if (c->rec_ok && phi == 1) {
+    const size_t need = (size_t)(forced ? forced : *M_avail) + 1;
+    if (c->tape_used + need * qbytes <= c->tape_cap) {
+      slot0 = c->tape + c->tape_used;
+      c->rec.q_off.push_back(c->tape_used);
+      EREM_CUDA(c, cudaMemcpyAsync(slot0, c->q[0], qbytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+      c->rec_ok = false;
+    }
+  }
   int m = 1, qin = 0;
   int chunk = forced ? forced : std::max(4, c->last_degree + 2);
   // launches of this interpolation: first term, terms computed, output buffer
@@ -362,9 +376,12 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     const int end = forced ? forced : std::min(*M_avail, m + chunk - 1);
     int mm = m;
     while (mm <= end) {
-      const int nt = (c->use_pairs && mm + 1 <= end) ? 2 : 1;
+      const int nt = (c->use_pairs && !slot0 && mm + 1 <= end) ? 2 : 1;
       if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size()], s);
-      if (nt == 2) launch_leja_pair(c, mm, qin, cg, s);
+      if (slot0)
+        launch_leja_term_ptr(c, mm, slot0 + (size_t)(mm - 1) * qbytes, slot0 + (size_t)mm * qbytes,
+                             cg, s);
+      else if (nt == 2) launch_leja_pair(c, mm, qin, cg, s);
       else launch_leja_term(c, mm, qin, cg, s);
       if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size() + 1], s);
       launches.push_back(Launch{mm, nt, qin ^ 1});
@@ -402,6 +419,14 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     if (end >= *M_avail) {  // table exhausted below m_max: extend it
       *M_avail = mcap;
       EREM_TRY(prepare_dd(c, S, *M_avail, s, phi));
+      if (slot0 && c->tape_used + ((size_t)mcap + 1) * qbytes > c->tape_cap) {
+        // the tape cannot hold the longer interpolation: go on untaped (the
+        // remaining terms continue from the last taped slot)
+        EREM_CUDA(c, cudaMemcpyAsync(c->q[qin], slot0 + (size_t)(end)*qbytes, qbytes,
+                                     cudaMemcpyDeviceToDevice, s));
+        slot0 = nullptr;
+        c->rec_ok = false;
+      }
     }
     m = end + 1;
     chunk = 8;
@@ -418,6 +443,7 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     }
   }
   c->last_degree = *degree;
+  if (slot0) c->tape_used += ((size_t)*degree + 1) * qbytes;
   return EREM_OK;
 }
 
@@ -452,6 +478,12 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
   for (int a = 0; a < n_attempts; ++a) {
     const int S = replay ? o.replay[0] : (1 << a);
     const double delta = c->dt / S;
+    if (c->rec_try) {  // a new attempt tapes from the start of the record
+      c->tape_used = c->rec.begin;
+      c->rec.q_off.clear();
+      c->rec.w_off.clear();
+      c->rec_ok = true;
+    }
     // a short table first; the full one when a substep needs more terms
     int M_avail = replay ? mcap : std::min(mcap, std::max(48, 2 * c->last_degree + 8));
     EREM_TRY(prepare_dd(c, S, M_avail, s));
@@ -475,9 +507,35 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       }
       degrees[k] = degree;
       if (st) st->err_est = c->ctrl_h->err;
-      if (k + 1 < S) launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
+      if (k + 1 < S) {
+        launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
+        if (c->rec_ok) {  // the start of substep k+1 for the adjoint
+          const size_t wb = (size_t)c->Np * sizeof(double);
+          if (c->tape_used + wb <= c->tape_cap) {
+            EREM_CUDA(c, cudaMemcpyAsync(c->tape + c->tape_used, c->w, wb, cudaMemcpyDeviceToDevice, s));
+            c->rec.w_off.push_back(c->tape_used);
+            c->tape_used += wb;
+          } else {
+            c->rec_ok = false;
+          }
+        }
+      }
     }
     if (!ok) continue;
+    if (c->rec_try) {
+      if (c->rec_ok) {
+        c->rec.sched.assign(1, S);
+        for (int k = 0; k < S; ++k) c->rec.sched.push_back(degrees[k]);
+        c->tape_recs.push_back(c->rec);
+      } else {
+        // a step that does not fit ends the tape: records are matched to
+        // steps by order, so a gap would pair a later step with a wrong one
+        c->tape_recs.clear();
+        c->tape_used = 0;
+        c->tape_on = false;
+        c->rec_count0 = 0;
+      }
+    }
     // fused start: T^n is the caller's array itself, updated in place; a host
     // T (c->zc_out) is written once from T^n in Tn, where the fused kernel read it
     if (c->zc_out)
@@ -1128,6 +1186,7 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (double* p : c->adj_w)
     if (p) cudaFree(p);
+  if (c->tape) cudaFree(c->tape);
   for (double* p : {c->fin_b, c->fin_w, c->fin_p2, c->ada_save})
     if (p) cudaFree(p);
   void* adj32[] = {c->adj_up, c->adj_icap32, c->adj_mu32, c->adj_g32[0], c->adj_g32[1],
@@ -1258,6 +1317,21 @@ erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk
   EREM_TRY(parse_opts(c, opts, &o));
   double* Td = nullptr;
   const bool fused = c->phys.fluid_model == 0;
+  // adjoint tape: record this step (erem_adjoint_tape); a failed step leaves
+  // the tape as it was
+  struct RecScope {
+    erem_ctx* c;
+    ~RecScope() {
+      if (c->rec_try && c->tape_on && c->tape_recs.size() == c->rec_count0)
+        c->tape_used = c->rec.begin;
+      c->rec_try = false;
+      c->rec_ok = false;
+    }
+  } rec_scope{c};
+  c->rec_try = c->tape_on && c->phys.fluid_model == 0;
+  c->rec = erem_ctx::TapeRec{};
+  c->rec.begin = c->tape_used;
+  c->rec_count0 = c->tape_recs.size();
   // a page-locked host T (unpadded rows) is read once by a streaming kernel
   // into Tn and written once by the last kernel (one pass each way over the
   // link) instead of being staged by copies
@@ -1650,6 +1724,27 @@ erem_status erem_hold_interval(erem_ctx* c, int hold, double lo, double hi) {
   return EREM_OK;
 }
 
+erem_status erem_adjoint_tape(erem_ctx* c, size_t bytes, int record) {
+  if (!c) return EREM_EINVAL;
+  c->tape_recs.clear();
+  c->tape_used = 0;
+  c->tape_on = false;
+  if (!record) return EREM_OK;
+  if (bytes > c->tape_cap) {
+    if (c->tape) cudaFree(c->tape);
+    c->tape = nullptr;
+    c->tape_cap = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(&c->tape), bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->tape = nullptr;
+      return fail(c, EREM_ENOMEM, "adjoint tape: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->tape_cap = bytes;
+  }
+  c->tape_on = true;
+  return EREM_OK;
+}
+
 erem_status erem_adjoint_begin(erem_ctx* c, void* stream) {
   if (!c) return EREM_EINVAL;
   EREM_TRY(adj_check(c));
@@ -1699,47 +1794,73 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
   sp.window = 1;
   sp.m_max = kMaxTerms;
   sp.replay = 1;
-  // G = J T^n + b (the step's first kernel), then the w_k of the substeps
-  launch_step_init(c, Td, d[0], sp, s);
-  for (int k = 0; k + 1 < S; ++k) {
-    const double* u = c->vrhs;
-    if (k > 0) {
-      launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
-      u = c->u;
+  // the last taped record, if it is this step's: its substep starts and Newton
+  // vectors replace the recomputation below (the values are the same bits)
+  const erem_ctx::TapeRec* rec = nullptr;
+  if (!c->tape_recs.empty()) {
+    const erem_ctx::TapeRec& r = c->tape_recs.back();
+    if ((int)r.sched.size() == ns && std::equal(r.sched.begin(), r.sched.end(), sched)) rec = &r;
+  }
+  std::vector<const double*> wk(S, nullptr);  // w_k, k >= 1
+  if (rec) {
+    for (int k = 1; k < S; ++k) wk[k] = (const double*)(c->tape + rec->w_off[k - 1]);
+  } else {
+    // G = J T^n + b (the step's first kernel), then the w_k of the substeps
+    launch_step_init(c, Td, d[0], sp, s);
+    for (int k = 0; k + 1 < S; ++k) {
+      const double* u = c->vrhs;
+      if (k > 0) {
+        launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
+        u = c->u;
+      }
+      launch_leja_init(c, u, d[0], sp, s);
+      int qin = 0;
+      for (int m = 1; m <= sched[1 + k]; ++m) {
+        launch_leja_term(c, m, qin, cg, s);
+        qin ^= 1;
+      }
+      // the forward's own update w += delta P (k_axpy), so that these are the
+      // bits erem_step produced (and an adjoint tape recorded)
+      if (k > 0)
+        EREM_CUDA(c, cudaMemcpyAsync(c->adj_w[k + 1], c->adj_w[k], sizeof(double) * c->Np,
+                                     cudaMemcpyDeviceToDevice, s));
+      launch_axpy(c, c->adj_w[k + 1], c->P, delta, k == 0 ? 1 : 0, s);
     }
-    launch_leja_init(c, u, d[0], sp, s);
-    int qin = 0;
-    for (int m = 1; m <= sched[1 + k]; ++m) {
-      launch_leja_term(c, m, qin, cg, s);
-      qin ^= 1;
-    }
-    if (k == 0) launch_lincomb(c, c->adj_w[1], 0.0, c->P, delta, c->P, s);
-    else launch_lincomb(c, c->adj_w[k + 1], 1.0, c->adj_w[k], delta, c->P, s);
+    for (int k = 1; k < S; ++k) wk[k] = c->adj_w[k];
   }
   // backwards through the substeps
   launch_lincomb(c, c->adj_mu, 1.0, c->adj_lam, 0.0, c->adj_lam, s);
   EREM_CUDA(c, cudaMemsetAsync(c->adj_G, 0, sizeof(double) * c->Np, s));
   for (int k = S - 1; k >= 0; --k) {
-    const double* u = c->vrhs;
-    if (k > 0) {
-      launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
-      u = c->u;
-    }
     const int mk = sched[1 + k];
-    launch_leja_init(c, u, d[0], sp, s);
-    EREM_CUDA(c, cudaMemcpyAsync(store, c->q[0], qbytes, cudaMemcpyDeviceToDevice, s));
-    for (int m = 1; m < mk; ++m)
-      launch_leja_term_ptr(c, m, store + (size_t)(m - 1) * qbytes, store + (size_t)m * qbytes, cg, s);
+    const char* qk = store;
+    if (rec) {
+      qk = c->tape + rec->q_off[k];
+    } else {
+      const double* u = c->vrhs;
+      if (k > 0) {
+        launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
+        u = c->u;
+      }
+      launch_leja_init(c, u, d[0], sp, s);
+      EREM_CUDA(c, cudaMemcpyAsync(store, c->q[0], qbytes, cudaMemcpyDeviceToDevice, s));
+      for (int m = 1; m < mk; ++m)
+        launch_leja_term_ptr(c, m, store + (size_t)(m - 1) * qbytes, store + (size_t)m * qbytes, cg, s);
+    }
     launch_adj_start(c, c->adj_mu, d[mk], c->adj_s[0], s);
     int cur = 0;
     for (int j = mk - 1; j >= 0; --j) {
-      launch_adj_horner(c, c->adj_s[cur], c->adj_s[cur ^ 1], c->adj_mu, store + (size_t)j * qbytes, d[j],
+      launch_adj_horner(c, c->adj_s[cur], c->adj_s[cur ^ 1], c->adj_mu, qk + (size_t)j * qbytes, d[j],
                         cg + c->xi_host[j], scale, 1, s);
       cur ^= 1;
     }
     launch_adj_z(c, c->adj_s[cur], delta, c->adj_z, c->adj_G, s);
-    if (k > 0) launch_adj_face_pair(c, c->adj_z, c->adj_w[k], 1.0, s);
+    if (k > 0) launch_adj_face_pair(c, c->adj_z, wk[k], 1.0, s);
     launch_adj_jT_apply(c, c->adj_z, c->adj_mu, c->adj_mu, s);
+  }
+  if (rec) {  // consumed: the tape shrinks back to the record's start
+    c->tape_used = rec->begin;
+    c->tape_recs.pop_back();
   }
   if (c->prec == EREM_FP32_BULK) launch_adj_flush32(c, s);
   launch_adj_face_pair(c, c->adj_G, c->Tn, 1.0, s);

@@ -249,6 +249,25 @@ struct erem_ctx {
   // cells), and the phi_2 increment delta^2 phi_2(delta J) D_t G
   double *fin_b = nullptr, *fin_w = nullptr, *fin_p2 = nullptr;
   double* ada_save = nullptr;  // rosm_integrate: T before an attempt [N]
+  // adjoint tape: erem_step records, while tape_on, what erem_adjoint_step
+  // would otherwise recompute (the substep starts w_k and the Newton vectors
+  // q_j of every substep) into one reserved device arena; records are
+  // consumed last in, first out
+  struct TapeRec {
+    std::vector<int> sched;          // [s, m_1..m_s]
+    std::vector<size_t> w_off;       // w_1..w_{s-1} (FP64, padded)
+    std::vector<size_t> q_off;       // q_0 of each substep (Leja precision, padded)
+    size_t begin = 0;
+  };
+  char* tape = nullptr;
+  size_t tape_cap = 0, tape_used = 0;
+  bool tape_on = false;
+  std::vector<TapeRec> tape_recs;
+  // the record of the step in progress (rec_ok = false: this step is not taped)
+  TapeRec rec;
+  bool rec_try = false;   // erem_step in progress tapes (tape_on)
+  bool rec_ok = false;    // ... and its current attempt still fits
+  size_t rec_count0 = 0;  // records before the step
   // erem_step with a pinned host T read and written in place by the kernels
   // (the first kernel also leaves T^n in Tn); host_access = 0 stages copies
   int host_access = 1;

@@ -38,7 +38,8 @@ def _setup(shape, steps, seed=0):
     return case, obs, data, steps
 
 
-def _model(E, case, obs, data, steps, precision, checkpoint=10, replay=None, interval=None):
+def _model(E, case, obs, data, steps, precision, checkpoint=10, replay=None, interval=None,
+           tape=True):
     import torch
 
     from paper_1209_5553_gb300.autograd import MisfitModel
@@ -46,15 +47,15 @@ def _model(E, case, obs, data, steps, precision, checkpoint=10, replay=None, int
     g = case.grid
     return MisfitModel(g.dim, g.nx, g.ny, g.nz, case.gpu_physics(), _t(case.phi), _t(case.lam),
                        case.dt, steps, _t(obs, torch.int64), _t(data), precision=precision,
-                       checkpoint=checkpoint, replay=replay, interval=interval)
+                       checkpoint=checkpoint, replay=replay, interval=interval, tape=tape)
 
 
-def _grads(E, case, obs, data, steps, precision, checkpoint=10, replay=None):
+def _grads(E, case, obs, data, steps, precision, checkpoint=10, replay=None, tape=True):
     import torch
 
     from paper_1209_5553_gb300.autograd import misfit
 
-    m = _model(E, case, obs, data, steps, precision, checkpoint, replay)
+    m = _model(E, case, obs, data, steps, precision, checkpoint, replay, tape=tape)
     lnk = _t(case.lnk).requires_grad_(True)
     T0 = _t(case.T0).requires_grad_(True)
     L = misfit(lnk, T0, m)
@@ -155,6 +156,42 @@ def test_checkpoint_interval_does_not_change_the_gradients(E):
     b = _grads(E, case, obs, data, steps, "fp32_bulk", checkpoint=3)
     assert a[3] == b[3] and a[0] == b[0]
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("precision", ["fp32_bulk", "fp64"])
+def test_tape_gives_the_same_gradients(E, precision):
+    # the Newton vectors and substep starts recorded by the segment replay are
+    # the bits the adjoint would recompute: the gradients are bitwise equal;
+    # two steps forced to two and three substeps exercise the w_k records
+    case, obs, data, steps = _setup((18, 14), 7)
+    free = _grads(E, case, obs, data, steps, precision)[3]
+    sched = [list(s) for s in free]
+    sched[2] = [2, free[2][1] + 4, free[2][1] + 2]
+    sched[5] = [3] + [free[5][1] + 3] * 3
+    a = _grads(E, case, obs, data, steps, precision, checkpoint=3, replay=sched, tape=False)
+    b = _grads(E, case, obs, data, steps, precision, checkpoint=3, replay=sched, tape=True)
+    assert a[3] == b[3] == sched
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_tape_that_does_not_fit_falls_back(E):
+    # a tape too small for a segment records nothing; the adjoint recomputes
+    import torch
+
+    case, obs, data, steps = _setup((12, 10), 4)
+    ref = _grads(E, case, obs, data, steps, "fp32_bulk", tape=False)
+    m = _model(E, case, obs, data, steps, "fp32_bulk")
+    m.tape_bytes = lambda scheds: 1024   # far too small
+    from paper_1209_5553_gb300.autograd import misfit
+
+    lnk = _t(case.lnk).requires_grad_(True)
+    T0 = _t(case.T0).requires_grad_(True)
+    L = misfit(lnk, T0, m)
+    L.backward()
+    assert float(L.detach()) == ref[0]
+    assert np.array_equal(lnk.grad.cpu().numpy(), ref[1]) and np.array_equal(T0.grad.cpu().numpy(), ref[2])
+    m.close()
 
 
 def test_adjoint_argument_errors(E):
