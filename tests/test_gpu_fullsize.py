@@ -70,3 +70,42 @@ def test_full_size_exactness_on_the_linear_problem(full):
     one, _ = _step(E, case, "fp64", 1, 2 * case.dt, opts)
     two, _ = _step(E, case, "fp64", 2, case.dt, opts)
     assert C.rel_l2(one - case.T0, two - case.T0) < 1e-7
+
+
+@pytest.mark.timeout(1800)
+def test_full_size_fast_leja_step_matches_oracle(full):
+    # the fast (midpoint-candidate) Leja points at 256^3, FP64, the oracle's
+    # schedule with the same points replayed
+    from oracle.leja import LejaOptions
+
+    E, case, _, _ = full
+    T1, res = ts.erem_step(case.problem(), case.T0, case.dt, LejaOptions(points="fast"))
+    g = case.grid
+    with E.Context(3, g.nx, g.ny, g.nz, physics=case.gpu_physics(), precision="fp64") as ctx:
+        ctx.set_leja_points("fast")
+        T = _t(case.T0)
+        ctx.set_state(T, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+        st = ctx.erem_step(T, case.dt, opts=E.leja_opts(replay=res.schedule))
+        got = T.cpu().numpy()
+    assert st.schedule == res.schedule
+    assert C.rel_l2(got, T1) < FP64_TOL
+
+
+@pytest.mark.timeout(1800)
+def test_full_size_forced_step_matches_oracle(full):
+    # the non-autonomous step (eq. nEERMg) at 256^3 with a time-dependent
+    # inflow temperature: FP64 with the oracle's [s, m.., m_phi2] replayed,
+    # FP32-bulk free-running
+    from oracle import nonauto as NA
+
+    E, case, _, _ = full
+    T_in, rate = 70.0, 40.0
+    T1, res = NA.erem_step_forced(case.problem(), case.T0, case.dt, T_in, rate)
+    g = case.grid
+    for prec, tol, opts in (("fp64", FP64_TOL, E.leja_opts(replay=res.schedule)), ("fp32_bulk", FP32_TOL, None)):
+        with E.Context(3, g.nx, g.ny, g.nz, physics=case.gpu_physics(), precision=prec) as ctx:
+            T = _t(case.T0)
+            ctx.set_state(T, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
+            ctx.erem_step_forced(T, case.dt, T_in, rate, opts=opts)
+            got = T.cpu().numpy()
+        assert C.rel_l2(got, T1) < tol, prec
