@@ -141,6 +141,30 @@ def test_multigrid_preconditioner(E, dims):
     assert iters[0] < 40 and iters[0] * (2 * 3 + 2) < 0.5 * iters[32] * 32, iters
 
 
+@pytest.mark.parametrize("dims", [(2, 1, 1, 1), (2, 7, 1, 1), (2, 1, 9, 1), (2, 3, 2, 1),
+                                  (3, 1, 1, 5), (3, 2, 3, 2)])
+def test_multigrid_on_degenerate_grids(E, dims):
+    # single cells, single rows and tiny boxes: the multigrid levels coarsen
+    # to one cell; pressure (CG) and a ROS2(1) step (stage BiCGSTAB) against
+    # the direct solutions
+    dim, nx, ny, nz = dims
+    case = C.random_case(dim, nx, ny, nz, seed=nx * 7 + ny, fluid_model=0)
+    g = case.grid
+    ph = fv.Physics(head_left=1.0, head_right=0.0, fluid_model=0)
+    p_ref = ts.pressure_solve_direct(g, ph, case.lnk, None)
+    ref = ts.ros2_step(case.problem(case.T0), case.T0, 0.05)
+    with E.Context(dim, nx, ny, nz, physics=case.gpu_physics()) as ctx:
+        p = _t(np.zeros(g.n))
+        st = ctx.pressure_solve(_t(case.lnk), None, p, tol=PRESSURE_TOL, maxit=2000)
+        assert st.lin_resid <= PRESSURE_TOL
+        assert np.max(np.abs(p.cpu().numpy() - p_ref)) <= 1e-9 * max(1.0, np.max(np.abs(p_ref)))
+        T = _t(case.T0)
+        ctx.rosm_step(T, 0.05, E.EREM_ROS2, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam),
+                      lin_tol=STAGE_TOL, maxit=2000)
+        got = T.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-8 * max(1.0, np.max(np.abs(ref - case.T0)))
+
+
 def test_pressure_solve_host_pointers_and_maxit(E):
     g = fv.Grid(2, 20, 20)
     ph = fv.Physics()
