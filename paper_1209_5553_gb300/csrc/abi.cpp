@@ -179,6 +179,49 @@ erem_status ensure_mg(erem_ctx* c) {
   return EREM_OK;
 }
 
+// The graph of two preconditioned iterations (their kernels' arguments are
+// fixed for the context and preconditioner; the scalars live on the device).
+// Captured on a stream of the context's own, so any caller stream may replay
+// it.  Returns false when capture is not available (the caller then launches
+// the kernels itself).
+bool ensure_pcg_graph(erem_ctx* c, const PcPoly& P, const float* z) {
+  const long long key = ((long long)c->pc_deg << 40) ^ ((long long)c->mg_nu << 32) ^
+                        (long long)(c->mg_omega * 1e6f);
+  if (c->pcg_exec && c->pcg_key == key) return true;
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+  c->pcg_exec = nullptr;
+  c->pcg_graph = nullptr;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    return false;
+  }
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const long long before = c->launches;
+  launch_pcg_iter(c, P, z, 0, c->cap_stream);
+  launch_pcg_iter(c, P, z, 1, c->cap_stream);
+  c->pcg_kernels = (int)(c->launches - before);
+  c->launches = before;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(c->cap_stream, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaGraphInstantiate(&c->pcg_exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    c->pcg_exec = nullptr;
+    return false;
+  }
+  c->pcg_graph = g;
+  c->pcg_key = key;
+  return true;
+}
+
 // CG on the pressure system whose matrix and right-hand side the caller has
 // assembled into kv (initial guess in kv[0]): Jacobi-preconditioned for
 // pc_deg = 1, else flexible CG with the FP32 polynomial preconditioner
@@ -203,13 +246,22 @@ erem_status run_pressure_cg(erem_ctx* c, double tol, int maxit, cudaStream_t s) 
     EREM_TRY(check_launch(c, "pressure preconditioner set-up"));
     EREM_TRY(read_ctrl(c, s));
   }
-  const int chunk = mg ? 2 : (prec ? std::max(2, 64 / c->pc_deg) : 32);
+  int chunk = mg ? 2 : (prec ? std::max(2, 64 / c->pc_deg) : 32);
+  const bool graph = prec && !c->ctrl_h->lin_done && ensure_pcg_graph(c, P, z);
+  if (graph) chunk = (chunk + 1) / 2 * 2;  // whole even/odd pairs
   int k = 0;
   while (!c->ctrl_h->lin_done && k < maxit) {
     const int n = std::min(chunk, maxit - k);
-    for (int j = 0; j < n; ++j) {
-      if (prec) launch_pcg_iter(c, P, z, k + j, s);
-      else launch_cg_iter(c, k + j, s);
+    if (graph && n % 2 == 0) {
+      for (int j = 0; j < n; j += 2) {
+        EREM_CUDA(c, cudaGraphLaunch(c->pcg_exec, s));
+        c->launches += c->pcg_kernels;
+      }
+    } else {
+      for (int j = 0; j < n; ++j) {
+        if (prec) launch_pcg_iter(c, P, z, k + j, s);
+        else launch_cg_iter(c, k + j, s);
+      }
     }
     EREM_TRY(check_launch(c, "cg"));
     k += n;
@@ -1195,6 +1247,9 @@ erem_status erem_destroy(erem_ctx* c) {
     if (p) cudaFree(p);
   for (float* p : c->pc)
     if (p) cudaFree(p);
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->pc_diag) cudaFree(c->pc_diag);
   for (SmgLevel& m : c->smg) {
     for (float* p : {m.D, m.Dinv, m.rhs, m.x[0], m.x[1], m.x[2]})

@@ -227,6 +227,13 @@ struct erem_ctx {
   std::vector<erem::MgLevel> mg;
   int mg_nu = 3;          // Chebyshev-Jacobi smoothing steps before and after
   float mg_omega = 1.8f;  // weight of the coarse correction
+  // two preconditioned CG iterations (even, odd) captured as one CUDA graph,
+  // replayed per chunk; rebuilt when the preconditioner settings change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t pcg_graph = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  long long pcg_key = -1;
+  int pcg_kernels = 0;    // kernels in the graph (for the launch count)
   // Rosenbrock stage systems: 0 = Jacobi BiCGSTAB, 1 = multigrid-preconditioned
   int stage_precond = 1;
   std::vector<erem::SmgLevel> smg;   // smg[0] = the fine level
