@@ -188,6 +188,8 @@ bool ensure_pcg_graph(erem_ctx* c, const PcPoly& P, const float* z) {
   const long long key = ((long long)c->pc_deg << 40) ^ ((long long)c->mg_nu << 32) ^
                         (long long)(c->mg_omega * 1e6f);
   if (c->pcg_exec && c->pcg_key == key) return true;
+  if (c->bicg_exec) cudaGraphExecDestroy(c->bicg_exec);
+  if (c->bicg_graph) cudaGraphDestroy(c->bicg_graph);
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
   if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
   c->pcg_exec = nullptr;
@@ -839,6 +841,45 @@ erem_status ensure_smg(erem_ctx* c) {
   return EREM_OK;
 }
 
+// Two multigrid-preconditioned BiCGSTAB iterations as one graph (their
+// arguments are fixed for the context and sigma); false when capture is not
+// available.
+bool ensure_bicg_graph(erem_ctx* c, double sigma) {
+  if (c->bicg_exec && c->bicg_sigma == sigma) return true;
+  if (c->bicg_exec) cudaGraphExecDestroy(c->bicg_exec);
+  if (c->bicg_graph) cudaGraphDestroy(c->bicg_graph);
+  c->bicg_exec = nullptr;
+  c->bicg_graph = nullptr;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    return false;
+  }
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const long long before = c->launches;
+  launch_bicg_iter_mg(c, sigma, c->cap_stream);
+  launch_bicg_iter_mg(c, sigma, c->cap_stream);
+  c->bicg_kernels = (int)(c->launches - before);
+  c->launches = before;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(c->cap_stream, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaGraphInstantiate(&c->bicg_exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    c->bicg_exec = nullptr;
+    return false;
+  }
+  c->bicg_graph = g;
+  c->bicg_sigma = sigma;
+  return true;
+}
+
 erem_status bicg_solve(erem_ctx* c, const double* b, double sigma, double tol, int maxit,
                        cudaStream_t s, int* iters, double* resid) {
   const bool mg = c->stage_precond == 1;
@@ -847,14 +888,20 @@ erem_status bicg_solve(erem_ctx* c, const double* b, double sigma, double tol, i
     launch_smg_setup(c, sigma, s);
   }
   launch_bicg_init(c, b, sigma, tol, s);
+  const bool graph = mg && ensure_bicg_graph(c, sigma);
   int it = 0;
   while (true) {
     EREM_TRY(read_ctrl(c, s));
     if (c->ctrl_h->lin_done || it >= maxit) break;
     const int n = std::min(mg ? 2 : 8, maxit - it);
-    for (int k = 0; k < n; ++k) {
-      if (mg) launch_bicg_iter_mg(c, sigma, s);
-      else launch_bicg_iter(c, sigma, s);
+    if (graph && n == 2) {
+      EREM_CUDA(c, cudaGraphLaunch(c->bicg_exec, s));
+      c->launches += c->bicg_kernels;
+    } else {
+      for (int k = 0; k < n; ++k) {
+        if (mg) launch_bicg_iter_mg(c, sigma, s);
+        else launch_bicg_iter(c, sigma, s);
+      }
     }
     EREM_TRY(check_launch(c, "bicgstab"));
     it += n;

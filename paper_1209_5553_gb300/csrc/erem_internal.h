@@ -234,6 +234,12 @@ struct erem_ctx {
   cudaGraphExec_t pcg_exec = nullptr;
   long long pcg_key = -1;
   int pcg_kernels = 0;    // kernels in the graph (for the launch count)
+  // the same for two multigrid-preconditioned BiCGSTAB iterations of the
+  // stage systems (keyed by sigma)
+  cudaGraph_t bicg_graph = nullptr;
+  cudaGraphExec_t bicg_exec = nullptr;
+  double bicg_sigma = 0.0;
+  int bicg_kernels = 0;
   // Rosenbrock stage systems: 0 = Jacobi BiCGSTAB, 1 = multigrid-preconditioned
   int stage_precond = 1;
   std::vector<erem::SmgLevel> smg;   // smg[0] = the fine level
