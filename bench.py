@@ -851,9 +851,12 @@ def main_adjoint(args):
     phys = E.Physics(rc, rc, wl.head_drop / st.vmax, 0.0, wl.T_inflow, 0)
     K, Wu = args.steps, args.warmup
     runs = {}
-    for prec in ("fp32_bulk", "fp64") if not args.no_fp64 else ("fp32_bulk",):
+    arms = [("fp32_bulk", "segment"), ("fp32_bulk", "full")]
+    if not args.no_fp64:
+        arms.append(("fp64", "segment"))
+    for prec, tape in arms:
         m = MisfitModel(3, n, n, n, phys, t(wl.phi), t(wl.lam), wl.dt, wl.steps, t(obs, torch.int64),
-                        t(data), precision=prec, checkpoint=10)
+                        t(data), precision=prec, checkpoint=10, tape=tape)
         lnk0, T00 = t(wl.lnk), t(wl.T0)
 
         def grad():
@@ -875,7 +878,7 @@ def main_adjoint(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / K
         terms = sum(s[0] and sum(s[1:]) for s in m.schedules)
-        runs[prec] = {"ms_per_gradient": ms, "L": float(L), "glnk": gl.cpu().numpy(),
+        runs[prec if tape == "segment" else prec + "_full_tape"] = {"ms_per_gradient": ms, "L": float(L), "glnk": gl.cpu().numpy(),
                       "gT0": gt.cpu().numpy(), "leja_terms_per_run": terms}
         m.close()
     r = runs["fp32_bulk"]
@@ -891,6 +894,10 @@ def main_adjoint(args):
         "adjoint": {"ms_per_gradient": r["ms_per_gradient"], "misfit": r["L"],
                     "leja_terms_per_forward": r["leja_terms_per_run"]},
     }
+    f = runs["fp32_bulk_full_tape"]
+    line["adjoint"]["full_tape_ms_per_gradient"] = f["ms_per_gradient"]
+    line["adjoint"]["rel_l2_glnk_full_tape_vs_checkpointed"] = float(
+        np.linalg.norm(f["glnk"] - r["glnk"]) / np.linalg.norm(r["glnk"]))
     if "fp64" in runs:
         q = runs["fp64"]
         line["adjoint"]["fp64_ms_per_gradient"] = q["ms_per_gradient"]

@@ -7,10 +7,13 @@ Backward: the library's adjoint entry points (erem_adjoint_*), one step at a
 time from T^N back to T^0 with every step's Leja schedule frozen at its
 forward value; the states T^n are recomputed from checkpoints kept every
 ``checkpoint`` steps by replaying those schedules, so at most ``checkpoint``
-states are held at once.  With ``tape`` (default) the replay of a segment
-records its Newton vectors on the device (erem_adjoint_tape) and the adjoint
-steps use them instead of computing them a second time.  Gradients with
-respect to ln K and T0.
+states are held at once.  With ``tape`` (default "segment") the replay of a
+segment records its Newton vectors on the device (erem_adjoint_tape) and the
+adjoint steps use them instead of computing them a second time.  With
+``tape="full"`` the forward run itself records them and keeps every state
+(60 steps at 128^3 in FP32-bulk fill about 12 GB), so the backward pass
+replays nothing.
+Gradients with respect to ln K and T0.
 
 The adjoint differentiates the run with the interval of every step held at
 its forward value; ``interval=`` holds it (``MisfitModel.interval`` of a
@@ -44,7 +47,9 @@ class MisfitModel:
         self.nx = nx
         self.n_padded = (nx + 3) // 4 * 4 * ny * nz
         self.qbytes = 4 if precision == "fp32_bulk" else 8
-        self.tape = bool(tape)
+        self.tape = {True: "segment", False: None, None: None}.get(tape, tape)
+        if self.tape not in (None, "segment", "full"):
+            raise ValueError("tape must be 'segment', 'full' or False")
         self.physics = physics
         self.phi, self.lam = phi, lam
         self.dt, self.steps = float(dt), int(steps)
@@ -61,6 +66,15 @@ class MisfitModel:
         x = (torch.arange(self.nx, dtype=torch.float64, device=like.device) + 0.5) / self.nx
         ramp = self.physics.head_left + (self.physics.head_right - self.physics.head_left) * x
         return ramp.repeat(self.n // self.nx).contiguous()
+
+    def full_tape_reserve(self):
+        """Arena for a whole run: room for 64 Newton vectors a step (plus one
+        interpolation's look-ahead), at most half the free device memory.  A run
+        that outgrows it is not taped at all: the adjoint then recomputes every
+        step from the kept states."""
+        free, _ = torch.cuda.mem_get_info()
+        want = (self.steps + 1) * 64 * self.qbytes * self.n_padded
+        return int(min(want, 0.5 * free))
 
     def tape_bytes(self, scheds):
         """Device bytes the adjoint tape needs for these steps."""
@@ -84,6 +98,9 @@ class EremMisfit(torch.autograd.Function):
         m.ctx.pressure_solve(lnk, None, p, tol=m.pressure_tol, maxit=1000000)
         T = T0.detach().clone().contiguous()
         m.ctx.set_state(T, p, lnk, m.phi, m.lam, m.dt)
+        full = m.tape == "full"
+        if full:   # record the forward run itself
+            m.ctx.adjoint_tape(m.full_tape_reserve(), True)
         ckpts = {0: T.clone()}
         scheds = []
         for n in range(m.steps):
@@ -92,7 +109,7 @@ class EremMisfit(torch.autograd.Function):
             scheds.append(st.schedule)
             if n == 0:
                 m.interval = (st.alpha / m.dt, st.beta / m.dt)
-            if (n + 1) % m.checkpoint == 0 and n + 1 < m.steps:
+            if n + 1 < m.steps and (full or (n + 1) % m.checkpoint == 0):
                 ckpts[n + 1] = T.clone()
         m.schedules = scheds
         fctx.model, fctx.ckpts, fctx.scheds = m, ckpts, scheds
@@ -107,6 +124,13 @@ class EremMisfit(torch.autograd.Function):
         lam = torch.zeros_like(TN)
         lam[m.obs] = 2.0 * (TN[m.obs] - m.data) * gL
         m.ctx.adjoint_begin()
+        if m.tape == "full":  # every state kept and every step taped by the forward run
+            for n in range(m.steps - 1, -1, -1):
+                m.ctx.adjoint_step(ckpts[n], lam, scheds[n])
+            m.ctx.adjoint_tape(0, False)
+            glnk = torch.zeros_like(lnk)
+            m.ctx.adjoint_lnk(lnk, glnk, tol=m.pressure_tol)
+            return glnk, lam, None
         starts = sorted(ckpts)
         for a, s0 in reversed(list(enumerate(starts))):
             s1 = starts[a + 1] if a + 1 < len(starts) else m.steps

@@ -175,6 +175,50 @@ def test_tape_gives_the_same_gradients(E, precision):
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
+@pytest.mark.parametrize("precision", ["fp32_bulk", "fp64"])
+def test_full_tape_gives_the_same_gradients(E, precision):
+    # the forward run tapes every step and keeps every state; the backward pass
+    # replays nothing and its gradients are those of the recomputing adjoint
+    case, obs, data, steps = _setup((18, 14), 7)
+    free = _grads(E, case, obs, data, steps, precision)[3]
+    sched = [list(s) for s in free]
+    sched[2] = [2, free[2][1] + 4, free[2][1] + 2]
+    sched[5] = [3] + [free[5][1] + 3] * 3
+    a = _grads(E, case, obs, data, steps, precision, checkpoint=3, replay=sched, tape=False)
+    b = _grads(E, case, obs, data, steps, precision, replay=sched, tape="full")
+    assert a[3] == b[3] == sched
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_full_tape_free_run_matches_oracle(E):
+    # stopping-test forward (no replay) taped as it runs: FP64 gradients
+    # against the oracle's adjoint of the same frozen schedules
+    case, obs, data, steps = _setup((14, 11), 4)
+    L, glnk, gT0, sched, _ = _grads(E, case, obs, data, steps, "fp64", tape="full")
+    Lo, glnk_o, gT0_o = _oracle(case, obs, data, steps, sched)
+    assert abs(L - Lo) < 1e-10 * Lo
+    assert C.rel_l2(gT0, gT0_o) < 1e-9
+    assert C.rel_l2(glnk, glnk_o) < 1e-8
+
+
+def test_full_tape_that_does_not_fit_falls_back(E):
+    case, obs, data, steps = _setup((12, 10), 4)
+    ref = _grads(E, case, obs, data, steps, "fp32_bulk", tape=False, replay=None)
+    from paper_1209_5553_gb300.autograd import misfit
+
+    m = _model(E, case, obs, data, steps, "fp32_bulk", tape="full")
+    m.full_tape_reserve = lambda: 1024   # far too small: nothing is taped
+    lnk = _t(case.lnk).requires_grad_(True)
+    T0 = _t(case.T0).requires_grad_(True)
+    L = misfit(lnk, T0, m)
+    L.backward()
+    assert m.schedules == ref[3]
+    assert np.allclose(lnk.grad.cpu().numpy(), ref[1], rtol=1e-12, atol=0)
+    assert np.allclose(T0.grad.cpu().numpy(), ref[2], rtol=1e-12, atol=0)
+    m.close()
+
+
 def test_tape_that_does_not_fit_falls_back(E):
     # a tape too small for a segment records nothing; the adjoint recomputes
     import torch
