@@ -548,11 +548,12 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     ctx.set_physics(E.Physics(rc, rc, wl.head_drop, 0.0, wl.T_inflow, 1))
     opts = E.leja_opts(tol=wl.tol, time_terms=True)
     stream = torch.cuda.current_stream()
+    T_p = T.clone()  # the temperature p was solved at
 
     def step():
         if scheme == "strang":
             st, s1 = ctx.coupled_step(T, p, lnk, phi, lam, wl.dt, E.EREM_SPLIT_STRANG,
-                                      pressure_tol=1e-10, opts=[opts, opts])
+                                      pressure_tol=1e-10, opts=[opts, opts], T_p=T_p)
             s1.launches += st[0].launches + st[1].launches
             st[1].degree_total += st[0].degree_total
             return s1, st[1]

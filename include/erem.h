@@ -246,22 +246,28 @@ EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
  *   EREM_SPLIT_TROTTER (the paper's "sequential approach"): p <- steady
  *     pressure at T^n (CG from the guess in p), then one EREM heat step of
  *     dt with the Darcy fluxes of p (erem_step with the fields);
- *   EREM_SPLIT_STRANG: an EREM heat step of dt/2 with the p given (the
- *     pressure the previous step ended with; for the first step the steady
- *     pressure at T^0), p <- steady pressure at the new T, a second heat step
- *     of dt/2.  With an instantly relaxed pressure the symmetric splitting
- *     is first order like the sequential one (the coupling lags by half a
- *     step in each half).
- *   T [N], p [N] in/out; lnk, phi, lambda [N].  pressure_tol, pressure_maxit
- *   as pressure_solve.  opts: NULL or an array of one (Trotter) or two
- *   (Strang, one per half step) Leja option structs; stats: NULL or an array
- *   of as many erem_stats for the heat steps; pstats (may be NULL): the
- *   pressure solve.  Errors as pressure_solve and erem_step; on an error of
+ *   EREM_SPLIT_STRANG: an EREM heat step of dt/2 with the Darcy fluxes of
+ *     the last pressure solve (p, the pressure the previous step ended with,
+ *     with the viscosity at T_p, the temperature it was solved at; for the
+ *     first step the steady pressure at T^0 and T_p = T^0), p <- steady
+ *     pressure at the new T, a second heat step of dt/2 with its fluxes.
+ *     With an instantly relaxed pressure the symmetric splitting is first
+ *     order like the sequential one (the coupling lags by half a step in
+ *     each half).
+ *   T [N], p [N] in/out; lnk, phi, lambda [N].  T_p [N] in/out, may be NULL:
+ *     in, the temperature p was solved at (NULL: T, right for a first step
+ *     and for a pressure solved at T^n; Strang only); out, the temperature the
+ *     step's pressure was solved at (T^n for Trotter, the half-step
+ *     temperature for Strang), to be passed to the next step.
+ *   pressure_tol, pressure_maxit as pressure_solve.  opts: NULL or an array
+ *   of one (Trotter) or two (Strang, one per half step) Leja option structs;
+ *   stats: NULL or an array of as many erem_stats for the heat steps; pstats
+ *   (may be NULL): the pressure solve.  Errors as pressure_solve and erem_step; on an error of
  *   the second half T holds the state after the first. */
 typedef enum { EREM_SPLIT_TROTTER = 0, EREM_SPLIT_STRANG = 1 } erem_splitting;
-EREM_API erem_status coupled_step(erem_ctx* ctx, double* T, double* p, const double* lnk,
-                                  const double* phi, const double* lambda, double dt,
-                                  erem_splitting splitting, double pressure_tol,
+EREM_API erem_status coupled_step(erem_ctx* ctx, double* T, double* p, double* T_p,
+                                  const double* lnk, const double* phi, const double* lambda,
+                                  double dt, erem_splitting splitting, double pressure_tol,
                                   int pressure_maxit, const erem_leja_opts* opts,
                                   erem_stats* stats, erem_stats* pstats, void* stream);
 

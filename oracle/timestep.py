@@ -226,16 +226,19 @@ def pressure_solve_cg(grid, phys, lnk, T=None, p0=None, tol=1e-13, maxit=100000)
     return x, maxit, float(np.linalg.norm(r) / bn)
 
 
-def strang_step(grid, phys, lnk, phi, lam, T, p, tau, opts=(None, None), pressure="direct"):
+def strang_step(grid, phys, lnk, phi, lam, T, p, tau, opts=(None, None), pressure="direct",
+                T_p=None):
     """One Strang step of §3.2 with the steady pressure of this build: an
-    EREM heat step of tau/2 with the Darcy fluxes of the current pressure p
-    (and the viscosity at the current T), the steady pressure at the new T,
-    then a second heat step of tau/2 with it.  p is the pressure the previous
-    step ended with (for the first step, the steady pressure at T^0).  With a
-    steady (instantly relaxed) pressure the symmetric splitting does not keep
-    its formal second order: the coupling is lagged by half a step in each
-    half.  Returns (T^{n+1}, p^{n+1}, (result of each half))."""
-    prob = heat_problem(grid, phys, lnk, phi, lam, p, T)
+    EREM heat step of tau/2 with the Darcy fluxes of the last pressure
+    solve, the steady pressure at the new T, then a second heat step of tau/2
+    with the fluxes of that pressure.  The flow subproblem hands the heat
+    subproblem a velocity field, so the first half takes p with the viscosity
+    at T_p, the temperature p was solved at (the previous step's half-step
+    temperature; T_p = T for the first step, where p is the steady pressure at
+    T^0): those fluxes are divergence-free, while re-evaluating the viscosity
+    at T would not be.  Returns (T^{n+1}, p^{n+1}, T_h, (result of each
+    half)), T_h the temperature p^{n+1} was solved at (the next step's T_p)."""
+    prob = heat_problem(grid, phys, lnk, phi, lam, p, T if T_p is None else T_p)
     Th, r1 = erem_step(prob, T, tau / 2, opts[0])
     if pressure == "direct":
         p1 = pressure_solve_direct(grid, phys, lnk, Th)
@@ -243,7 +246,7 @@ def strang_step(grid, phys, lnk, phi, lam, T, p, tau, opts=(None, None), pressur
         p1 = pressure_solve_cg(grid, phys, lnk, Th, p0=p)[0]
     prob = heat_problem(grid, phys, lnk, phi, lam, p1, Th)
     T1, r2 = erem_step(prob, Th, tau / 2, opts[1])
-    return T1, p1, (r1, r2)
+    return T1, p1, Th, (r1, r2)
 
 
 def sequential_step(grid, phys, lnk, phi, lam, T, p_prev, tau, scheme="erem", opts=None,

@@ -146,7 +146,7 @@ _sigs = {
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_fast_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_phi2_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
-    "coupled_step": (_I, [_P, _P, _P, _P, _P, _P, _D, _I, _D, _I, ctypes.POINTER(erem_leja_opts),
+    "coupled_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _D, _I, _D, _I, ctypes.POINTER(erem_leja_opts),
                           ctypes.POINTER(erem_stats), ctypes.POINTER(erem_stats), _P]),
     "rosm_integrate": (_I, [_P, _P, _D, _D, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_D),
                             ctypes.POINTER(erem_adapt_stats), _P]),
@@ -323,10 +323,11 @@ def erem_step_forced(ctx, n, T, dt, T_in, T_in_rate, p=None, lnk=None, phi=None,
 
 
 def coupled_step(ctx, n, T, p, lnk, phi, lam, dt, splitting=EREM_SPLIT_TROTTER,
-                 pressure_tol=1e-10, pressure_maxit=200000, opts=None, stream=None):
+                 pressure_tol=1e-10, pressure_maxit=200000, opts=None, stream=None, T_p=None):
     """One split pressure/temperature step; opts: None or a list of one
-    (Trotter) or two (Strang) erem_leja_opts.  Returns (heat stats list,
-    pressure stats)."""
+    (Trotter) or two (Strang) erem_leja_opts; T_p: None or the temperature p
+    was solved at (updated to the one the step's pressure was solved at).
+    Returns (heat stats list, pressure stats)."""
     nh = 2 if splitting == EREM_SPLIT_STRANG else 1
     if opts is not None:
         if len(opts) != nh:
@@ -334,7 +335,7 @@ def coupled_step(ctx, n, T, p, lnk, phi, lam, dt, splitting=EREM_SPLIT_TROTTER,
         arr = (erem_leja_opts * nh)(*opts)
     st = (erem_stats * nh)()
     pst = erem_stats()
-    _check(ctx, _lib.coupled_step(ctx, _ptr(T, n), _ptr(p, n), _ptr(lnk, n), _ptr(phi, n),
+    _check(ctx, _lib.coupled_step(ctx, _ptr(T, n), _ptr(p, n), _ptr(T_p, n), _ptr(lnk, n), _ptr(phi, n),
                                   _ptr(lam, n), float(dt), int(splitting), float(pressure_tol),
                                   int(pressure_maxit),
                                   ctypes.cast(arr, ctypes.POINTER(erem_leja_opts)) if opts is not None
@@ -623,9 +624,9 @@ class Context:
         return erem_step(self._h, self.n, T, dt, p, lnk, phi, lam, opts, stream)
 
     def coupled_step(self, T, p, lnk, phi, lam, dt, splitting=EREM_SPLIT_TROTTER,
-                     pressure_tol=1e-10, pressure_maxit=200000, opts=None, stream=None):
+                     pressure_tol=1e-10, pressure_maxit=200000, opts=None, stream=None, T_p=None):
         return coupled_step(self._h, self.n, T, p, lnk, phi, lam, dt, splitting, pressure_tol,
-                            pressure_maxit, opts, stream)
+                            pressure_maxit, opts, stream, T_p)
 
     def rosm_integrate(self, T, t_end, dt0, scheme=EREM_ROS2, tol_a=1e-6, tol_r=1e-6,
                        lin_tol=1e-10, maxit=10000, max_attempts=100000, stream=None):

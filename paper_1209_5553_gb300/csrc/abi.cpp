@@ -1623,21 +1623,40 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
   return EREM_OK;
 }
 
-erem_status coupled_step(erem_ctx* c, double* T, double* p, const double* lnk, const double* phi,
-                         const double* lam, double dt, erem_splitting split, double ptol,
-                         int pmaxit, const erem_leja_opts* opts, erem_stats* st,
+erem_status coupled_step(erem_ctx* c, double* T, double* p, double* T_p, const double* lnk,
+                         const double* phi, const double* lam, double dt, erem_splitting split,
+                         double ptol, int pmaxit, const erem_leja_opts* opts, erem_stats* st,
                          erem_stats* pst, void* stream) {
   if (!c) return EREM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
   if (split != EREM_SPLIT_TROTTER && split != EREM_SPLIT_STRANG)
     return fail(c, EREM_EINVAL, "splitting must be EREM_SPLIT_TROTTER or EREM_SPLIT_STRANG");
   if (!T || !p || !lnk || !phi || !lam) return fail(c, EREM_EINVAL, "NULL array argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, EREM_EINVAL, "dt must be finite and > 0");
+  // T_p <- the temperature the pressure was just solved at
+  auto keep_Tp = [&]() -> erem_status {
+    if (T_p && T_p != T)
+      EREM_CUDA(c, cudaMemcpyAsync(T_p, T, (size_t)c->N * sizeof(double), cudaMemcpyDefault, s));
+    return EREM_OK;
+  };
   if (split == EREM_SPLIT_TROTTER) {
     EREM_TRY(pressure_solve(c, lnk, T, p, ptol, pmaxit, pst, stream));
+    EREM_TRY(keep_Tp());
     return erem_step(c, T, p, lnk, phi, lam, dt, opts, st, stream);
   }
-  EREM_TRY(erem_step(c, T, p, lnk, phi, lam, 0.5 * dt, opts, st, stream));
+  // first half: the fluxes of the last solve, the viscosity at T_p
+  if (T_p) {
+    double* dTp;
+    EREM_TRY(resolve(c, 6, T_p, true, s, &dTp));
+    launch_pack(c, dTp, c->u, s);
+    EREM_TRY(check_launch(c, "pack T_p"));
+    c->visc_u = true;
+  }
+  const erem_status e1 = erem_step(c, T, p, lnk, phi, lam, 0.5 * dt, opts, st, stream);
+  c->visc_u = false;
+  EREM_TRY(e1);
   EREM_TRY(pressure_solve(c, lnk, T, p, ptol, pmaxit, pst, stream));
+  EREM_TRY(keep_Tp());
   return erem_step(c, T, p, lnk, phi, lam, 0.5 * dt, opts ? opts + 1 : nullptr,
                    st ? st + 1 : nullptr, stream);
 }

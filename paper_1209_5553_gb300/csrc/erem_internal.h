@@ -285,6 +285,9 @@ struct erem_ctx {
   // (the first kernel also leaves T^n in Tn); host_access = 0 stages copies
   int host_access = 1;
   bool zc_active = false;
+  // the face assembly takes the viscosity's temperature from u (padded)
+  // instead of T^n: a Strang half step with the fluxes of the last solve
+  bool visc_u = false;
   double* zc_out = nullptr;   // the host T the last kernel writes (device address)
   // FP32-bulk Horner pass: upwind flags, FP32 capacities, FP32 mu, FP32 face
   // sums of the current adjoint step

@@ -113,13 +113,35 @@ struct FieldIn {
   const double *lnk, *phi, *lam, *p, *T;  // padded
 };
 
-__global__ void k_faces(FieldIn in, FaceOut o, Geo g, Phys ph, int* flags) {
+// Cell mobility, once per cell into m (padded): K rho(T)/mu(T) for the
+// pressure matrix (darcy = 0), K/mu(T) for the Darcy fluxes (darcy = 1).  The
+// face kernels below take their harmonic means from it instead of evaluating
+// the fluid laws (two FP64 exponentials) again for every face of every cell.
+__global__ void k_mobility(const double* __restrict__ lnk, const double* __restrict__ T,
+                           double* __restrict__ m, Geo g, Phys ph, int darcy, int in_padded,
+                           int* flags) {
+  int bad = 0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
+    int ix, iy, iz, ip;
+    cell_of(i, g, ix, iy, iz, ip);
+    const int j = in_padded ? ip : i;  // lnk and T in the padded or the caller's layout
+    const double Ti = T ? T[j] : 20.0;
+    const double mi = darcy ? exp(lnk[j]) / mu_rel(Ti, ph.fm)
+                            : exp(lnk[j]) * rho_rel(Ti, ph.fm) / mu_rel(Ti, ph.fm);
+    bad |= !finite(mi);
+    m[ip] = mi;
+  }
+  if (bad && flags) atomicOr(flags, FLAG_NONFINITE);
+}
+
+__global__ void k_faces(FieldIn in, const double* __restrict__ m, FaceOut o, Geo g, Phys ph,
+                        int* flags) {
   int bad = 0, inval = 0;
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
     const double Ti = in.T[ip];
-    const double mi = exp(in.lnk[ip]) / mu_rel(Ti, ph.fm);
+    const double mi = m[ip];  // K / mu(T), k_mobility
     const double li = in.lam[ip];
     const double pi = in.p[ip];
     const double phi = in.phi[ip];
@@ -128,7 +150,7 @@ __global__ void k_faces(FieldIn in, FaceOut o, Geo g, Phys ph, int* flags) {
     // + x face
     if (ix < g.nx - 1) {
       const int j = ip + 1;
-      const double mj = exp(in.lnk[j]) / mu_rel(in.T[j], ph.fm);
+      const double mj = m[j];
       o.Lx[ip] = harm(ph.ax, 0.5 * ph.hx, li, in.lam[j]);
       o.Fx[ip] = ph.rhoc_f * harm(ph.ax, 0.5 * ph.hx, mi, mj) * (pi - in.p[j]);
     } else {  // x = 1: Dirichlet pressure, outflow face without conduction
@@ -138,7 +160,7 @@ __global__ void k_faces(FieldIn in, FaceOut o, Geo g, Phys ph, int* flags) {
     // + y face
     if (iy < g.ny - 1) {
       const int j = ip + g.px;
-      const double mj = exp(in.lnk[j]) / mu_rel(in.T[j], ph.fm);
+      const double mj = m[j];
       o.Ly[ip] = harm(ph.ay, 0.5 * ph.hy, li, in.lam[j]);
       o.Fy[ip] = ph.rhoc_f * harm(ph.ay, 0.5 * ph.hy, mi, mj) * (pi - in.p[j]);
     } else {
@@ -148,7 +170,7 @@ __global__ void k_faces(FieldIn in, FaceOut o, Geo g, Phys ph, int* flags) {
     if (g.dim == 3) {
       if (iz < g.nz - 1) {
         const int j = ip + g.plane;
-        const double mj = exp(in.lnk[j]) / mu_rel(in.T[j], ph.fm);
+        const double mj = m[j];
         o.Lz[ip] = harm(ph.az, 0.5 * ph.hz, li, in.lam[j]);
         o.Fz[ip] = ph.rhoc_f * harm(ph.az, 0.5 * ph.hz, mi, mj) * (pi - in.p[j]);
       } else {
@@ -1463,38 +1485,31 @@ struct PresArr {
   double *x, *r, *z, *d0, *d1, *Ad, *Ux, *Uy, *Uz, *diag, *b;
 };
 
-__global__ void k_pres_faces(const double* __restrict__ lnk, const double* __restrict__ T,
-                             PresArr a, Geo g, Phys ph, int* flags) {
-  int bad = 0;
+// TPFA pressure matrix from the cell mobilities m: upper couplings, diagonal
+// (with the Dirichlet faces at x = 0 and x = 1) and right-hand side
+__global__ void k_pres_faces(const double* __restrict__ m, PresArr a, Geo g, Phys ph) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
-    const double Ti = T ? T[i] : 20.0;
-    const double mi = exp(lnk[i]) * rho_rel(Ti, ph.fm) / mu_rel(Ti, ph.fm);
-    bad |= !finite(mi);
+    const double mi = m[ip];
     double dg = 0.0, bb = 0.0;
-    auto mob = [&](int j) {
-      const double Tj = T ? T[j] : 20.0;
-      return exp(lnk[j]) * rho_rel(Tj, ph.fm) / mu_rel(Tj, ph.fm);
-    };
     double ux = 0.0, uy = 0.0, uz = 0.0;
-    if (ix < g.nx - 1) ux = harm(ph.ax, 0.5 * ph.hx, mi, mob(i + 1));
-    if (iy < g.ny - 1) uy = harm(ph.ay, 0.5 * ph.hy, mi, mob(i + g.nx));
-    if (g.dim == 3 && iz < g.nz - 1) uz = harm(ph.az, 0.5 * ph.hz, mi, mob(i + g.nx * g.ny));
+    if (ix < g.nx - 1) ux = harm(ph.ax, 0.5 * ph.hx, mi, m[ip + 1]);
+    if (iy < g.ny - 1) uy = harm(ph.ay, 0.5 * ph.hy, mi, m[ip + g.px]);
+    if (g.dim == 3 && iz < g.nz - 1) uz = harm(ph.az, 0.5 * ph.hz, mi, m[ip + g.plane]);
     a.Ux[ip] = ux;
     a.Uy[ip] = uy;
     if (g.dim == 3) a.Uz[ip] = uz;
     dg += ux + uy + uz;
-    if (ix > 0) dg += harm(ph.ax, 0.5 * ph.hx, mob(i - 1), mi);
-    if (iy > 0) dg += harm(ph.ay, 0.5 * ph.hy, mob(i - g.nx), mi);
-    if (g.dim == 3 && iz > 0) dg += harm(ph.az, 0.5 * ph.hz, mob(i - g.nx * g.ny), mi);
+    if (ix > 0) dg += harm(ph.ax, 0.5 * ph.hx, m[ip - 1], mi);
+    if (iy > 0) dg += harm(ph.ay, 0.5 * ph.hy, m[ip - g.px], mi);
+    if (g.dim == 3 && iz > 0) dg += harm(ph.az, 0.5 * ph.hz, m[ip - g.plane], mi);
     const double uD = ph.ax * mi / (0.5 * ph.hx);
     if (ix == 0) { dg += uD; bb += uD * ph.head_left; }
     if (ix == g.nx - 1) { dg += uD; bb += uD * ph.head_right; }
     a.diag[ip] = dg;
     a.b[ip] = bb;
   }
-  if (bad) atomicOr(flags, FLAG_NONFINITE);
 }
 
 __device__ __forceinline__ double pres_apply(const PresArr& a, const double* __restrict__ x, int ip,
@@ -1938,6 +1953,89 @@ k_mg_coarse_cg(MgL L, const float* __restrict__ b, float* __restrict__ x, float*
   }
 }
 
+// Sum over the block of two per-thread values, every thread getting both
+// totals: warp sums in `slot` (one float2 per warp), one block sync, then each
+// thread adds the warp sums itself in the same order (the same totals in every
+// thread).  Two calls in a row take different slots.
+__device__ __forceinline__ float2 mg_block_sum2(float a, float b, float2* slot) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) slot[threadIdx.x >> 5] = make_float2(a, b);
+  __syncthreads();
+  float2 t = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int w = 0; w < kMgCoarseThreads / 32; ++w) {
+    const float2 v = slot[w];
+    t.x += v.x;
+    t.y += v.y;
+  }
+  return t;
+}
+
+// Coarsest level with at most kMgCoarseThreads cells: the Jacobi-PCG of
+// k_mg_coarse_cg with one cell per thread, its coefficients, x and r in
+// registers and only the direction p in shared memory (the stencil's
+// neighbour reads); three block syncs per iteration.  The result goes to x.
+__global__ void __launch_bounds__(kMgCoarseThreads)
+k_mg_coarse_cg1(MgL L, const float* __restrict__ b, float* __restrict__ x, int maxit, float rtol) {
+  __shared__ float ps[kMgCoarseThreads];
+  __shared__ float2 slot[2][kMgCoarseThreads / 32];
+  const int N = L.g.N;
+  const bool own = (int)threadIdx.x < N;
+  int ix = 0, iy = 0, iz = 0, ip = 0;
+  float dg = 0.0f, dinv = 0.0f, cw = 0.0f, ce = 0.0f, cs = 0.0f, cn = 0.0f, cb = 0.0f, ct = 0.0f;
+  float xv = 0.0f, rv = 0.0f;
+  if (own) {
+    cell_of((int)threadIdx.x, L.g, ix, iy, iz, ip);
+    dg = L.diag[ip];
+    dinv = L.dinv[ip];
+    if (ix > 0) cw = L.Ux[ip - 1];
+    if (ix < L.g.nx - 1) ce = L.Ux[ip];
+    if (iy > 0) cs = L.Uy[ip - L.g.px];
+    if (iy < L.g.ny - 1) cn = L.Uy[ip];
+    if (L.g.dim == 3) {
+      if (iz > 0) cb = L.Uz[ip - L.g.plane];
+      if (iz < L.g.nz - 1) ct = L.Uz[ip];
+    }
+    rv = b[ip];
+    ps[ip] = dinv * rv;
+  }
+  const float2 s0 = mg_block_sum2(rv * (dinv * rv), rv * rv, slot[0]);
+  float rz = s0.x;
+  const float stop = rtol * rtol * s0.y;
+  for (int it = 0; it < maxit && s0.y > 0.0f; ++it) {
+    __syncthreads();  // p complete
+    float pv = 0.0f, v = 0.0f;
+    if (own) {
+      pv = ps[ip];
+      float o = 0.0f;
+      if (ix > 0) o = fmaf(cw, ps[ip - 1], o);
+      if (ix < L.g.nx - 1) o = fmaf(ce, ps[ip + 1], o);
+      if (iy > 0) o = fmaf(cs, ps[ip - L.g.px], o);
+      if (iy < L.g.ny - 1) o = fmaf(cn, ps[ip + L.g.px], o);
+      if (L.g.dim == 3) {
+        if (iz > 0) o = fmaf(cb, ps[ip - L.g.plane], o);
+        if (iz < L.g.nz - 1) o = fmaf(ct, ps[ip + L.g.plane], o);
+      }
+      v = fmaf(dg, pv, -o);
+    }
+    const float pq = mg_block_sum2(pv * v, 0.0f, slot[0]).x;
+    if (!(pq > 0.0f)) break;
+    const float alpha = rz / pq;
+    xv = fmaf(alpha, pv, xv);
+    rv = fmaf(-alpha, v, rv);
+    const float zv = dinv * rv;
+    const float2 s = mg_block_sum2(rv * rv, rv * zv, slot[1]);
+    if (s.x <= stop) break;
+    const float beta = s.y / rz;
+    rz = s.y;
+    if (own) ps[ip] = fmaf(beta, pv, zv);
+  }
+  if (own) x[ip] = xv;
+}
+
 // x += alpha d, r -= alpha Ad; rr -> convergence (the preconditioner's
 // sweeps follow and give z and beta)
 __global__ void k_pcg_upd(PresArr a, const double* __restrict__ d, Geo g, double* part,
@@ -1988,19 +2086,14 @@ __global__ void k_sumsq(const double* __restrict__ x, Geo g, double* part, unsig
 }
 
 // net Darcy inflow through x = 0 and the largest face speed |v| / |sigma|
-__global__ void k_pres_post(const double* __restrict__ lnk, const double* __restrict__ T,
-                            const double* __restrict__ x, Geo g, Phys ph, double* part,
-                            unsigned* cnt, Ctrl* ctrl) {
+__global__ void k_pres_post(const double* __restrict__ m, const double* __restrict__ x, Geo g,
+                            Phys ph, double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   double fin = 0.0, vmax = 0.0;
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
-    auto mob = [&](int j) {
-      const double Tj = T ? T[j] : 20.0;
-      return exp(lnk[j]) / mu_rel(Tj, ph.fm);
-    };
-    const double mi = mob(i);
+    const double mi = m[ip];
     const double pi = x[ip];
     if (ix == 0) {
       const double v = (ph.ax * mi / (0.5 * ph.hx)) * (ph.head_left - pi);
@@ -2008,18 +2101,18 @@ __global__ void k_pres_post(const double* __restrict__ lnk, const double* __rest
       vmax = fmax(vmax, fabs(v) / ph.ax);
     }
     if (ix < g.nx - 1) {
-      const double v = harm(ph.ax, 0.5 * ph.hx, mi, mob(i + 1)) * (pi - x[ip + 1]);
+      const double v = harm(ph.ax, 0.5 * ph.hx, mi, m[ip + 1]) * (pi - x[ip + 1]);
       vmax = fmax(vmax, fabs(v) / ph.ax);
     } else {
       const double v = (ph.ax * mi / (0.5 * ph.hx)) * (pi - ph.head_right);
       vmax = fmax(vmax, fabs(v) / ph.ax);
     }
     if (iy < g.ny - 1) {
-      const double v = harm(ph.ay, 0.5 * ph.hy, mi, mob(i + g.nx)) * (pi - x[ip + g.px]);
+      const double v = harm(ph.ay, 0.5 * ph.hy, mi, m[ip + g.px]) * (pi - x[ip + g.px]);
       vmax = fmax(vmax, fabs(v) / ph.ay);
     }
     if (g.dim == 3 && iz < g.nz - 1) {
-      const double v = harm(ph.az, 0.5 * ph.hz, mi, mob(i + g.nx * g.ny)) * (pi - x[ip + g.plane]);
+      const double v = harm(ph.az, 0.5 * ph.hz, mi, m[ip + g.plane]) * (pi - x[ip + g.plane]);
       vmax = fmax(vmax, fabs(v) / ph.az);
     }
   }
@@ -2367,6 +2460,56 @@ __global__ void __launch_bounds__(512) k_smg_coarse(MgN L, const float* __restri
   }
 }
 
+// Coarsest level with at most 512 cells: the damped Jacobi sweeps of
+// k_smg_coarse with one cell per thread, its coefficients and rhs in registers
+// and the iterate in shared memory (two buffers, one block sync per sweep).
+__global__ void __launch_bounds__(512) k_smg_coarse1(MgN L, const float* __restrict__ rhs,
+                                                     float* __restrict__ x, int sweeps, float w) {
+  __shared__ float xs[2][512];
+  const int N = L.g.N;
+  const bool own = (int)threadIdx.x < N;
+  int ix = 0, iy = 0, iz = 0, ip = 0;
+  float d = 0.0f, wdi = 0.0f, r = 0.0f, cw = 0.0f, ce = 0.0f, cs = 0.0f, cn = 0.0f, cb = 0.0f,
+        ct = 0.0f, xv = 0.0f;
+  if (own) {
+    cell_of((int)threadIdx.x, L.g, ix, iy, iz, ip);
+    d = L.D[ip];
+    wdi = w * L.Dinv[ip];
+    r = rhs[ip];
+    if (ix > 0) cw = L.c[0][ip];
+    if (ix < L.g.nx - 1) ce = L.c[1][ip];
+    if (iy > 0) cs = L.c[2][ip];
+    if (iy < L.g.ny - 1) cn = L.c[3][ip];
+    if (L.g.dim == 3) {
+      if (iz > 0) cb = L.c[4][ip];
+      if (iz < L.g.nz - 1) ct = L.c[5][ip];
+    }
+    xv = wdi * r;
+    xs[0][ip] = xv;
+  }
+  int cur = 0;
+  for (int it = 1; it < sweeps; ++it) {
+    __syncthreads();  // xs[cur] complete
+    if (own) {
+      const float* a = xs[cur];
+      float o = 0.0f;
+      if (ix > 0) o = fmaf(cw, a[ip - 1], o);
+      if (ix < L.g.nx - 1) o = fmaf(ce, a[ip + 1], o);
+      if (iy > 0) o = fmaf(cs, a[ip - L.g.px], o);
+      if (iy < L.g.ny - 1) o = fmaf(cn, a[ip + L.g.px], o);
+      if (L.g.dim == 3) {
+        if (iz > 0) o = fmaf(cb, a[ip - L.g.plane], o);
+        if (iz < L.g.nz - 1) o = fmaf(ct, a[ip + L.g.plane], o);
+      }
+      const float res = r - fmaf(d, xv, -o);
+      xv = fmaf(wdi, res, xv);
+      xs[cur ^ 1][ip] = xv;
+    }
+    cur ^= 1;
+  }
+  if (own) x[ip] = xv;
+}
+
 // BiCGSTAB with the V-cycle as right preconditioner: the direction and the
 // intermediate residual go to the V-cycle in FP32, its output comes back in
 // FP64 (y, z of the Jacobi form)
@@ -2498,11 +2641,15 @@ void launch_finish(const erem_ctx* c, double* out, const double* base, const dou
   k_finish<<<blocks_cells(c), NT, 0, s>>>(out, base, w, P, delta, in_place, geo_of(c));
 }
 
+// the cell mobilities K / mu(T) go to P (the Leja sum, which every step
+// initialises after the assembly); T is T^n, or u when visc_u is set
 void launch_faces(const erem_ctx* c, cudaStream_t s) {
   FieldIn in{c->lnk, c->phi, c->lam, c->p, c->Tn};
   FaceOut o{c->Lx, c->Ly, c->Lz, c->Fx, c->Fy, c->Fz, c->icap, c->LD0, c->F0};
-  ++c->launches;
-  k_faces<<<blocks_cells(c), NT, 0, s>>>(in, o, geo_of(c), phys_of(c), &c->ctrl->flags);
+  c->launches += 2;
+  k_mobility<<<blocks_cells(c), NT, 0, s>>>(c->lnk, c->visc_u ? c->u : c->Tn, c->P, geo_of(c),
+                                            phys_of(c), 1, 1, &c->ctrl->flags);
+  k_faces<<<blocks_cells(c), NT, 0, s>>>(in, c->P, o, geo_of(c), phys_of(c), &c->ctrl->flags);
 }
 
 void launch_cellJ(const erem_ctx* c, cudaStream_t s) {
@@ -2753,10 +2900,14 @@ void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, d
   k_lincomb<<<blocks_padded(c), NT, 0, s>>>(out, a, x, b, y, (int)c->Np);
 }
 
+// the cell mobilities go to kv[1] (the CG residual, which k_cg_init writes
+// afterwards; free again once the CG has converged)
 void launch_pres_faces(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {
-  ++c->launches;
-  k_pres_faces<<<blocks_cells(c), NT, 0, s>>>(lnk, T, pres_arr(c), geo_of(c), phys_of(c),
-                                              &c->ctrl->flags);
+  const PresArr a = pres_arr(c);
+  c->launches += 2;
+  k_mobility<<<blocks_cells(c), NT, 0, s>>>(lnk, T, a.r, geo_of(c), phys_of(c), 0, 0,
+                                            &c->ctrl->flags);
+  k_pres_faces<<<blocks_cells(c), NT, 0, s>>>(a.r, a, geo_of(c), phys_of(c));
 }
 
 void launch_cg_init(const erem_ctx* c, double tol, cudaStream_t s) {
@@ -2849,8 +3000,11 @@ int mg_cycle(const erem_ctx* c, int l, const PcPoly& poly, float omega, cudaStre
   const MgL L = mg_level(c, l);
   if (l + 1 == (int)c->mg.size()) {
     ++c->launches;
-    k_mg_coarse_cg<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3], 400,
-                                                   kMgCoarseRtol);
+    if (L.g.Np <= kMgCoarseThreads)
+      k_mg_coarse_cg1<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], 400, kMgCoarseRtol);
+    else
+      k_mg_coarse_cg<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3], 400,
+                                                     kMgCoarseRtol);
     return 0;
   }
   int cur = mg_smooth(c, l, poly, 0, true, s);
@@ -2952,8 +3106,10 @@ void launch_pcg_iter(const erem_ctx* c, const PcPoly& poly, const float* z, int 
 }
 
 void launch_pres_post(const erem_ctx* c, const double* lnk, const double* T, cudaStream_t s) {
-  ++c->launches;
-  k_pres_post<<<blocks_cells(c), NT, 0, s>>>(lnk, T, c->kv[0], geo_of(c), phys_of(c), c->red_part,
+  const PresArr a = pres_arr(c);
+  c->launches += 2;
+  k_mobility<<<blocks_cells(c), NT, 0, s>>>(lnk, T, a.r, geo_of(c), phys_of(c), 1, 0, nullptr);
+  k_pres_post<<<blocks_cells(c), NT, 0, s>>>(a.r, a.x, geo_of(c), phys_of(c), c->red_part,
                                              c->red_cnt, c->ctrl);
 }
 
@@ -2986,7 +3142,10 @@ int smg_cycle(const erem_ctx* c, int l, cudaStream_t s) {
   const MgN L = smg_level(c, l);
   if (l + 1 == (int)c->smg.size()) {
     ++c->launches;
-    k_smg_coarse<<<1, 512, 0, s>>>(L, m.rhs, m.x[0], m.x[1], kSmgCoarseSweeps, kSmgW);
+    if (L.g.Np <= 512)
+      k_smg_coarse1<<<1, 512, 0, s>>>(L, m.rhs, m.x[0], kSmgCoarseSweeps, kSmgW);
+    else
+      k_smg_coarse<<<1, 512, 0, s>>>(L, m.rhs, m.x[0], m.x[1], kSmgCoarseSweeps, kSmgW);
     return 0;
   }
   const int nb = grid_for(c, L.g.N);

@@ -86,13 +86,17 @@ def test_coupled_step_trotter_and_strang_match_oracle(setup):
     # steps, Strang (heat dt/2, pressure, heat dt/2) against strang_step,
     # each heat step replaying the oracle's schedule; the pressure CG error
     # enters through the fluxes (bound as above)
+    import torch
+
     E, wl, g, ph, ps, scheds, Ts = setup
     phys = E.Physics(ph.rhoc_f, ph.rhoc_s, 1.0, 0.0, 80.0, 1)
     T_s = wl.T0.copy()
     p_s = ts.pressure_solve_direct(g, ph, wl.lnk, T_s)
+    Tp_s = T_s
     s_scheds, s_T, bound = [], [], 0.0
     for _ in range(STEPS):
-        T_s, p_s, (r1, r2) = ts.strang_step(g, ph, wl.lnk, wl.phi, wl.lam, T_s, p_s, wl.dt)
+        T_s, p_s, Tp_s, (r1, r2) = ts.strang_step(g, ph, wl.lnk, wl.phi, wl.lam, T_s, p_s, wl.dt,
+                                                  T_p=Tp_s)
         s_scheds.append((r1.schedule, r2.schedule))
         A, b = fv.pressure_system(g, ph, wl.lnk, T_s)
         smin = np.linalg.svd(A.toarray(), compute_uv=False).min()
@@ -102,19 +106,23 @@ def test_coupled_step_trotter_and_strang_match_oracle(setup):
     with E.Context(2, 24, 24, physics=phys) as ctx:
         T = _t(wl.T0)
         p = _t(fv.linear_head_guess(g, ph))
+        T_p = torch.empty_like(T)
         for k in range(STEPS):
             st, pst = ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_TROTTER, pressure_tol=CG_TOL,
-                                       opts=[E.leja_opts(replay=scheds[k])])
+                                       opts=[E.leja_opts(replay=scheds[k])], T_p=T_p)
             assert pst.lin_resid <= CG_TOL and st[0].schedule == scheds[k]
         got_trotter = T.cpu().numpy()
+        got_Tp_trotter = T_p.cpu().numpy()   # T^n of the last step: its pressure's temperature
         T = _t(wl.T0)
         p = _t(fv.linear_head_guess(g, ph))
         ctx.pressure_solve(fields[0], T, p, tol=CG_TOL)
+        T_p = T.clone()                  # the pressure was solved at T^0
         for k in range(STEPS):
             st, pst = ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_STRANG, pressure_tol=CG_TOL,
-                                       opts=[E.leja_opts(replay=s) for s in s_scheds[k]])
+                                       opts=[E.leja_opts(replay=s) for s in s_scheds[k]], T_p=T_p)
             assert [s.schedule for s in st] == list(s_scheds[k])
         got_strang = T.cpu().numpy()
+        got_Tp = T_p.cpu().numpy()
         p_got = p.cpu().numpy()
         with pytest.raises(ValueError):
             ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_STRANG, opts=[E.leja_opts()])
@@ -124,6 +132,8 @@ def test_coupled_step_trotter_and_strang_match_oracle(setup):
     inc = np.linalg.norm(Ts[-1] - wl.T0) / np.linalg.norm(Ts[-1])
     assert C.rel_l2(got_trotter, Ts[-1]) < max(1e-11, 10 * STEPS * bound * inc)
     assert C.rel_l2(got_strang, s_T) < max(1e-11, 10 * STEPS * bound * inc)
+    assert C.rel_l2(got_Tp, Tp_s) < max(1e-11, 10 * STEPS * bound * inc)
+    assert C.rel_l2(got_Tp_trotter, Ts[-2]) < max(1e-11, 10 * STEPS * bound * inc)
     assert C.rel_l2(p_got, p_s) < 10 * bound
     # the two splittings differ at the splitting error, far above the bound
     assert C.rel_l2(got_strang, got_trotter) > 1e3 * max(1e-11, 10 * STEPS * bound * inc)
