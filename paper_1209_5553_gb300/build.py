@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
         else:
-            cmd = [os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden",
+            cmd = [os.environ.get("CXX", "g++"), "-O3", "-std=c++17", "-fPIC", "-fvisibility=hidden",
                    "-I", os.path.join(cuda, "include"), "-I", CSRC, "-c", path, "-o", obj]
         jobs.append(cmd)
     if jobs:

@@ -314,10 +314,21 @@ erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1) {
   if (e.M < M || e.c != cc || e.gamma != gg) {
     e.c = cc;
     e.gamma = gg;
-    e.M = M;
-    e.d.assign(M + 1, 0.0);
-    if (divided_differences_phi(phi, M, c->xi_host.data(), cc, gg, e.d.data()) != 0)
+    if (c->dd_spec.valid() && c->spec_key == key && c->spec_kind == c->leja_kind &&
+        c->spec_M >= M && c->spec_c == cc && c->spec_g == gg) {
+      // computed ahead on the host thread (the same function of the same inputs)
+      e.d = c->dd_spec.get();
+      e.M = c->spec_M;
+    } else {
+      e.M = M;
+      e.d.assign(M + 1, 0.0);
+      if (divided_differences_phi(phi, M, c->xi_host.data(), cc, gg, e.d.data()) != 0)
+        e.d.clear();
+    }
+    if (e.d.empty()) {
+      e.M = -1;
       return fail(c, EREM_EINVAL, "divided differences: bad interval");
+    }
     for (double v : e.d)
       if (!std::isfinite(v)) return fail(c, EREM_ENONFINITE, "non-finite divided difference");
     c->dd_tag_S = -1;
@@ -330,6 +341,35 @@ erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1) {
     c->dd_tag_M = e.M;
   }
   return EREM_OK;
+}
+
+// Start the phi_1 table of substep level S (M + 1 entries) on a host thread;
+// prepare_dd takes it if that level is reached with the same interval.
+void speculate_dd(erem_ctx* c, int S, int M) {
+  const int key = dd_key(S, 1);
+  const double cc = c->cfoc / S, gg = c->gam / S;
+  const DDEntry& e = dd_entry(c, S, 1);
+  if (e.M >= M && e.c == cc && e.gamma == gg) return;  // cached
+  if (c->dd_spec.valid() && c->spec_key == key && c->spec_kind == c->leja_kind &&
+      c->spec_M >= M && c->spec_c == cc && c->spec_g == gg)
+    return;  // already under way
+  if (c->dd_spec.valid()) c->dd_spec.wait();  // one table at a time
+  std::vector<double> xi(c->xi_host.begin(), c->xi_host.begin() + M + 1);
+  try {
+    c->dd_spec = std::async(std::launch::async, [xi = std::move(xi), M, cc, gg]() {
+      std::vector<double> d(M + 1, 0.0);
+      if (divided_differences_phi(1, M, xi.data(), cc, gg, d.data()) != 0) d.clear();
+      return d;
+    });
+  } catch (...) {  // no thread: prepare_dd computes the table itself
+    c->dd_spec = std::future<std::vector<double>>();
+    return;
+  }
+  c->spec_key = key;
+  c->spec_kind = c->leja_kind;
+  c->spec_M = M;
+  c->spec_c = cc;
+  c->spec_g = gg;
 }
 
 struct Opts {
@@ -541,6 +581,9 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
     // a short table first; the full one when a substep needs more terms
     int M_avail = replay ? mcap : std::min(mcap, std::max(48, 2 * c->last_degree + 8));
     EREM_TRY(prepare_dd(c, S, M_avail, s));
+    // the last step needed more substeps: the next level's table is computed
+    // on the host while this level's terms run
+    if (!replay && a + 1 < n_attempts && c->last_S > S) speculate_dd(c, 2 * S, mcap);
     bool ok = true;
     for (int k = 0; k < S; ++k) {
       const double* u = src;
@@ -576,6 +619,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       }
     }
     if (!ok) continue;
+    c->last_S = S;
     if (c->rec_try) {
       if (c->rec_ok) {
         c->rec.sched.assign(1, S);

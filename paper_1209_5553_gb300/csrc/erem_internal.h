@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <future>
 #include <map>
 #include <string>
 #include <vector>
@@ -312,6 +313,12 @@ struct erem_ctx {
   int dd_tag_S = -1, dd_tag_M = -1;
   std::vector<double> xi_host;
   std::map<int, erem::DDEntry> dd_cache;  // substep count -> table
+  // the phi_1 table of the next substep level, computed on a host thread
+  // while the GPU runs the current level (when the last step needed it)
+  std::future<std::vector<double>> dd_spec;
+  int spec_key = -1, spec_kind = -1, spec_M = -1;
+  double spec_c = 0, spec_g = 0;
+  int last_S = 1;   // substeps of the last erem_step
 
   // state
   bool hold_iv = false;              // interval held by erem_hold_interval

@@ -206,15 +206,22 @@ int divided_differences_phi(int kphi, int M, const double* xi, double c, double 
     for (int i = 0; i < n; ++i)
       for (int j = std::max(0, i - nb); j <= i; ++j) E[(size_t)i * n + j] += Tk[(size_t)i * n + j];
   }
-  // s - 1 full squarings of the lower triangle, the last one only for column 0
+  // s - 1 full squarings of the lower triangle, the last one only for column 0.
+  // Row form: row i of E E is sum_l E(i, l) (row l of E), rows read
+  // contiguously; each entry still sums its products in increasing l.
   std::vector<double> F((size_t)n * n, 0.0);
   for (int sq = 0; sq + 1 < s; ++sq) {
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j <= i; ++j) {
-        double acc = 0.0;
-        for (int l = j; l <= i; ++l) acc += E[(size_t)i * n + l] * E[(size_t)l * n + j];
-        F[(size_t)i * n + j] = acc;
+    for (int i = 0; i < n; ++i) {
+      double* __restrict__ Fi = &F[(size_t)i * n];
+      const double* __restrict__ Ei = &E[(size_t)i * n];
+      for (int j = 0; j <= i; ++j) Fi[j] = 0.0;
+      for (int l = 0; l <= i; ++l) {
+        const double a = Ei[l];
+        const double* __restrict__ El = &E[(size_t)l * n];
+#pragma GCC ivdep
+        for (int j = 0; j <= l; ++j) Fi[j] += a * El[j];
       }
+    }
     std::swap(E, F);
   }
   for (int j = 0; j <= M; ++j) {
