@@ -69,7 +69,8 @@ def parse_args():
     ap.add_argument("--members", type=int, default=512, help="ensemble members")
     ap.add_argument("--arms", default="all",
                     help="coupled2d: comma-separated subset of erem_fp32_bulk, erem_fp64, ros2_fp64, "
-                         "ros3p_fp64, erem_strang_fp32_bulk (the line needs erem_fp32_bulk)")
+                         "ros3p_fp64, erem_strang_fp32_bulk, erem_from_last_fp32_bulk (the line "
+                         "needs erem_fp32_bulk)")
     return ap.parse_args()
 
 
@@ -543,6 +544,9 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     lnk, phi, lam = t(wl.lnk), t(wl.phi), t(wl.lam)
     T = t(wl.T0)
     p = t(linear_head(wl.n, wl.nx, wl.head_drop, 0.0))
+    if scheme == "erem_from_last":  # each step starts at the last step's substep count
+        ctx.set_substep_start(E.EREM_SUBSTEPS_FROM_LAST)
+        scheme = "erem"
     st = ctx.pressure_solve(lnk, T, p, tol=1e-10, maxit=200000)
     rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), st.flux_in / 1.0)
     ctx.set_physics(E.Physics(rc, rc, wl.head_drop, 0.0, wl.T_inflow, 1))
@@ -604,7 +608,8 @@ def main_coupled(args):
     runs = {}
     arms = (("erem_fp32_bulk", "erem", "fp32_bulk"), ("erem_fp64", "erem", "fp64"),
             ("ros2_fp64", "ros2", "fp64"), ("ros3p_fp64", "ros3p", "fp64"),
-            ("erem_strang_fp32_bulk", "strang", "fp32_bulk"))
+            ("erem_strang_fp32_bulk", "strang", "fp32_bulk"),
+            ("erem_from_last_fp32_bulk", "erem_from_last", "fp32_bulk"))
     want = None if args.arms == "all" else set(args.arms.split(",")) | {"erem_fp32_bulk"}
     for key, scheme, prec in arms:
         if want is not None and key not in want:

@@ -445,6 +445,20 @@ EREM_API erem_status erem_adjoint_lnk(erem_ctx* ctx, const double* lnk, double* 
 typedef enum { EREM_LEJA_EXACT = 0, EREM_LEJA_FAST = 1 } erem_leja_kind;
 EREM_API erem_status erem_set_leja_points(erem_ctx* ctx, int kind);
 
+/* Substep count the first attempt of a step takes (phi1_apply, erem_step,
+ * the heat steps of coupled_step; not replayed steps).  §4.2 splits a step
+ * whose interpolation needs more than m_max terms and fixes only that
+ * doubling, not where it starts:
+ *   EREM_SUBSTEPS_FROM_ONE (default): every step starts at one substep;
+ *   EREM_SUBSTEPS_FROM_LAST: a step starts at the count the last step on
+ *     ctx passed with (capped at 2^max_doublings) and doubles from there, so
+ *     a run whose interval keeps needing s substeps does not repeat the
+ *     failing attempts below s every step; it never goes back down.
+ * erem_set_state restarts the count at one.  Errors: EINVAL (ctx NULL,
+ * unknown mode). */
+typedef enum { EREM_SUBSTEPS_FROM_ONE = 0, EREM_SUBSTEPS_FROM_LAST = 1 } erem_substep_start;
+EREM_API erem_status erem_set_substep_start(erem_ctx* ctx, int mode);
+
 /* Preconditioner of the pressure CG (pressure_solve, erem_adjoint_lnk) for
  * later calls on ctx.  degree 0: one multigrid V-cycle (aggregates of 2 x 2
  * (x 2) cells, Galerkin coarse operators, nu Chebyshev-Jacobi smoothing

@@ -191,6 +191,11 @@ class LejaOptions:
     avg_window: int = 5
     replay: list | None = None  # [s, m_1, ..., m_s]
     points: str = "exact"       # "exact" (eq. lejaa) or "fast" (midpoint candidates)
+    # substep count the first attempt takes (a power of two; the doubling on
+    # failure goes on from there up to 2**max_doublings).  §4.2 fixes only the
+    # doubling: 1 restarts every step from one substep, the last step's count
+    # continues where it stopped.
+    start_substeps: int = 1
 
 
 @dataclass
@@ -260,8 +265,9 @@ def phi1_leja(J, v, tau: float, y_inf: float, opts: LejaOptions | None = None) -
     if opts.replay is not None:
         m_cap = max(m_cap, max(opts.replay[1:]))
     xi = cached_leja_points(m_cap, opts.points)
+    first = min(max(1, opts.start_substeps), 2**opts.max_doublings)
     attempts = [opts.replay[0]] if opts.replay is not None else [
-        2**k for k in range(opts.max_doublings + 1)]
+        2**k for k in range(opts.max_doublings + 1) if 2**k >= first]
     last_err = 0.0
     for s in attempts:
         delta = tau / s

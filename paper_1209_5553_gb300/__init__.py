@@ -32,6 +32,7 @@ STATUS_NAMES = {0: "EREM_OK", 1: "EREM_EINVAL", 2: "EREM_ENOMEM", 3: "EREM_ENOTC
 EREM_FP64, EREM_FP32_BULK = 0, 1
 EREM_ROSM1, EREM_ROSM_HALF, EREM_ROS2, EREM_ROS3P = 0, 1, 2, 3
 EREM_LEJA_EXACT, EREM_LEJA_FAST = 0, 1
+EREM_SUBSTEPS_FROM_ONE, EREM_SUBSTEPS_FROM_LAST = 0, 1
 EREM_SPLIT_TROTTER, EREM_SPLIT_STRANG = 0, 1
 
 
@@ -153,6 +154,7 @@ _sigs = {
     "erem_step_forced": (_I, [_P, _P, _D, _D, _D, _P, _P, _P, _P, ctypes.POINTER(erem_leja_opts),
                               ctypes.POINTER(erem_stats), _P]),
     "erem_set_leja_points": (_I, [_P, _I]),
+    "erem_set_substep_start": (_I, [_P, _I]),
     "erem_phi1_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
     "erem_pressure_solve_static": (_I, [ctypes.POINTER(erem_grid), ctypes.POINTER(erem_physics),
                                         _P, _P, _P, _D, _I, ctypes.POINTER(erem_stats), _P]),
@@ -394,6 +396,12 @@ def erem_set_leja_points(ctx, kind) -> None:
     """EREM_LEJA_EXACT or EREM_LEJA_FAST (or "exact" / "fast")."""
     kind = {"exact": EREM_LEJA_EXACT, "fast": EREM_LEJA_FAST}.get(kind, kind)
     _check(ctx, _lib.erem_set_leja_points(ctx, int(kind)))
+
+
+def erem_set_substep_start(ctx, mode) -> None:
+    """EREM_SUBSTEPS_FROM_ONE or EREM_SUBSTEPS_FROM_LAST (or "one" / "last")."""
+    mode = {"one": EREM_SUBSTEPS_FROM_ONE, "last": EREM_SUBSTEPS_FROM_LAST}.get(mode, mode)
+    _check(ctx, _lib.erem_set_substep_start(ctx, int(mode)))
 
 
 def erem_phi1_divided_differences(xi, c: float, gamma: float) -> np.ndarray:
@@ -644,6 +652,9 @@ class Context:
 
     def set_leja_points(self, kind):
         erem_set_leja_points(self._h, kind)
+
+    def set_substep_start(self, mode):
+        erem_set_substep_start(self._h, mode)
 
     def set_pressure_precond(self, degree):
         erem_set_pressure_precond(self._h, degree)

@@ -565,11 +565,15 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
     for (size_t k = 1; k < o.replay.size(); ++k) mcap = std::max(mcap, o.replay[k]);
   EREM_TRY(ensure_leja(c, mcap));
   int n_attempts = replay ? 1 : o.max_doublings + 1;
+  // the first attempt: one substep, or the last step's count (at most 2^max_doublings)
+  int a0 = 0;
+  if (!replay && c->substep_start == EREM_SUBSTEPS_FROM_LAST)
+    while (a0 < o.max_doublings && (1 << a0) < c->last_S) ++a0;
   bool nonfinite_attempt = false;  // the last failed attempt had a non-finite estimate
   int degrees[64];
   TermTiming tt;
   if (o.time_terms) EREM_TRY(ensure_events(c, mcap + 1));
-  for (int a = 0; a < n_attempts; ++a) {
+  for (int a = a0; a < n_attempts; ++a) {
     const int S = replay ? o.replay[0] : (1 << a);
     const double delta = c->dt / S;
     if (c->rec_try) {  // a new attempt tapes from the start of the record
@@ -595,7 +599,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       const StopParams sp = stop_params(c, o, delta, replay ? forced : o.m_max, replay);
       int degree = 0;
       bool failed = false, nonfinite = false;
-      EREM_TRY(leja_interp(c, u, (fused_T && a == 0 && k == 0) ? fused_T : nullptr, S, 1, &M_avail,
+      EREM_TRY(leja_interp(c, u, (fused_T && a == a0 && k == 0) ? fused_T : nullptr, S, 1, &M_avail,
                            mcap, sp, forced, o, &tt, &degree, &failed, &nonfinite, s));
       if (failed) {
         nonfinite_attempt = nonfinite;
@@ -1422,6 +1426,7 @@ erem_status erem_set_state(erem_ctx* c, const double* T, const double* p, const 
   if (!T || !p || !lnk || !phi || !lam) return fail(c, EREM_EINVAL, "NULL field");
   double* Td;
   c->have_state = false;
+  c->last_S = 1;  // a new run starts from one substep
   EREM_TRY(prepare_step(c, const_cast<double*>(T), p, lnk, phi, lam, dt, true, s, &Td));
   EREM_CUDA(c, cudaStreamSynchronize(s));
   return EREM_OK;
@@ -1839,6 +1844,14 @@ erem_status erem_set_leja_points(erem_ctx* c, int kind) {
   c->dd_cache.clear();      // divided differences belong to the points
   c->dd_tag_S = -1;
   return cap > 0 ? ensure_leja(c, cap) : EREM_OK;
+}
+
+erem_status erem_set_substep_start(erem_ctx* c, int mode) {
+  if (!c) return EREM_EINVAL;
+  if (mode != EREM_SUBSTEPS_FROM_ONE && mode != EREM_SUBSTEPS_FROM_LAST)
+    return fail(c, EREM_EINVAL, "substep start must be EREM_SUBSTEPS_FROM_ONE or EREM_SUBSTEPS_FROM_LAST");
+  c->substep_start = mode;
+  return EREM_OK;
 }
 
 erem_status erem_set_pressure_precond(erem_ctx* c, int degree) {

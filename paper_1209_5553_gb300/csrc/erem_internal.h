@@ -319,6 +319,7 @@ struct erem_ctx {
   int spec_key = -1, spec_kind = -1, spec_M = -1;
   double spec_c = 0, spec_g = 0;
   int last_S = 1;   // substeps of the last erem_step
+  int substep_start = 0;   // EREM_SUBSTEPS_FROM_ONE or EREM_SUBSTEPS_FROM_LAST
 
   // state
   bool hold_iv = false;              // interval held by erem_hold_interval

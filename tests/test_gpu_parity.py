@@ -213,6 +213,39 @@ def test_degree_cap_splits_the_step_like_the_oracle(E):
     assert C.rel_l2(got, ref.value) < FP64_TOL
 
 
+def test_substeps_from_the_last_step_like_the_oracle(E):
+    # m_max = 14 makes the steps split; starting each step at the count the
+    # last one passed with takes the oracle's schedule under the same rule,
+    # and skips the failing attempts below it
+    case = C.random_case(2, 20, 16, seed=11, pe=60.0)
+    tau, steps = 0.4, 4
+    prob = case.problem(case.T0)
+    T = case.T0.copy()
+    scheds, s0 = [], 1
+    for _ in range(steps):
+        T, res = ts.erem_step(prob, T, tau, LejaOptions(m_max=14, start_substeps=s0))
+        assert res.converged
+        scheds.append(res.schedule)
+        s0 = res.substeps
+    assert scheds[0][0] > 1
+    with _ctx(E, case, "fp64") as ctx:
+        ctx.set_substep_start(E.EREM_SUBSTEPS_FROM_LAST)
+        Tg = _t(case.T0)
+        got_s = []
+        for k in range(steps):
+            fields = (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam)) if k == 0 else (None,) * 4
+            st = ctx.erem_step(Tg, tau, *fields, opts=E.leja_opts(m_max=14))
+            got_s.append(st.schedule)
+        got = Tg.cpu().numpy()
+        # erem_set_state restarts from one substep: the first step's schedule again
+        ctx.set_state(_t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), tau)
+        assert ctx.erem_step(_t(case.T0), tau, opts=E.leja_opts(m_max=14)).schedule == scheds[0]
+        with pytest.raises(E.EremError):
+            ctx.set_substep_start(2)
+    assert got_s == scheds
+    assert C.rel_l2(got, T) < FP64_TOL
+
+
 def test_host_pointers_match_device_pointers(E):
     case = C.heat2d_rect(40, 24)
     res = []

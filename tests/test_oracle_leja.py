@@ -202,6 +202,29 @@ def test_degree_cap_triggers_substep_doubling():
     assert not fail.converged
 
 
+def test_substep_start_skips_the_smaller_levels():
+    # starting at s0 substeps: the attempts below s0 are not taken, the value
+    # is still the phi_1 action within the tolerance, and a start at or above
+    # the count the doubling reaches gives the doubling's own result
+    prob, T = _small_problem(pe=50.0)
+    tau = 0.5
+    J, v = prob.J(T), prob.G(T)
+    ref = _phi1_expm(J, v, tau)
+    scal = 1e-6 + 1e-6 * np.max(np.abs(T))
+    base = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))), LejaOptions(m_max=12))
+    assert base.converged and base.substeps >= 2
+    same = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))),
+                          LejaOptions(m_max=12, start_substeps=base.substeps))
+    assert same.schedule == base.schedule and np.array_equal(same.value, base.value)
+    up = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))),
+                        LejaOptions(m_max=12, start_substeps=2 * base.substeps))
+    assert up.converged and up.substeps == 2 * base.substeps
+    assert leja.weighted_norm(up.value - ref, scal) < 10.0
+    capped = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))),
+                            LejaOptions(m_max=40, max_doublings=1, start_substeps=64))
+    assert capped.substeps == 2
+
+
 def test_gershgorin_interval_contains_spectrum():
     prob, T = _small_problem()
     tau = 0.1
