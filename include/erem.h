@@ -463,7 +463,8 @@ EREM_API erem_status erem_set_substep_start(erem_ctx* ctx, int mode);
  * later calls on ctx.  degree 0: one multigrid V-cycle (aggregates of 2 x 2
  * (x 2) cells, Galerkin coarse operators, nu Chebyshev-Jacobi smoothing
  * steps on [1/4, 2] before and after, the coarse correction weighted by
- * omega, single-block CG on the coarsest level of <= 512 cells; FP32;
+ * omega, the coarsest level of <= 512 cells solved by its inverse, formed
+ * once per solve; FP32;
  * parameters by erem_set_pressure_multigrid, default nu = 3, omega = 1.8).
  * degree 1: Jacobi (diagonal) preconditioning, plain CG
  * in FP64.  degree 2..64: z = p(D^-1 A) D^-1 r, `degree` steps of Chebyshev

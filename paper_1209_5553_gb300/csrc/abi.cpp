@@ -176,6 +176,9 @@ erem_status ensure_mg(erem_ctx* c) {
       EREM_TRY(dalloc_t(c, a, n));
     if (c->dim == 3) EREM_TRY(dalloc_t(c, &L.Uz, n));
   }
+  MgLevel& last = c->mg.back();  // at most 512 cells: its inverse, at most 1 MB
+  const size_t nc = (size_t)last.nx * last.ny * last.nz;
+  if (nc <= (size_t)kMgCoarsest) EREM_TRY(dalloc_t(c, &last.inv, nc * nc));
   return EREM_OK;
 }
 
@@ -1353,7 +1356,7 @@ erem_status erem_destroy(erem_ctx* c) {
       if (p) cudaFree(p);
   }
   for (MgLevel& m : c->mg)
-    for (float* p : {m.diag, m.dinv, m.Ux, m.Uy, m.Uz, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3]})
+    for (float* p : {m.diag, m.dinv, m.Ux, m.Uy, m.Uz, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3], m.inv})
       if (p) cudaFree(p);
   if (c->kr_host) cudaFreeHost(c->kr_host);
   if (c->red_cnt) cudaFree(c->red_cnt);

@@ -158,6 +158,7 @@ struct MgLevel {
   float *diag = nullptr, *dinv = nullptr, *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;
   float* rhs = nullptr;
   float* x[4] = {};
+  float* inv = nullptr;   // coarsest level: its operator's inverse, N x N by columns
 };
 
 // One level of the multigrid preconditioner of the Rosenbrock stage systems

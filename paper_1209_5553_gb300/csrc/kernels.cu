@@ -1977,16 +1977,15 @@ __device__ __forceinline__ float2 mg_block_sum2(float a, float b, float2* slot) 
 // Coarsest level with at most kMgCoarseThreads cells: the Jacobi-PCG of
 // k_mg_coarse_cg with one cell per thread, its coefficients, x and r in
 // registers and only the direction p in shared memory (the stencil's
-// neighbour reads); three block syncs per iteration.  The result goes to x.
-__global__ void __launch_bounds__(kMgCoarseThreads)
-k_mg_coarse_cg1(MgL L, const float* __restrict__ b, float* __restrict__ x, int maxit, float rtol) {
-  __shared__ float ps[kMgCoarseThreads];
-  __shared__ float2 slot[2][kMgCoarseThreads / 32];
+// neighbour reads); three block syncs per iteration.  rv is this thread's
+// entry of the right-hand side (0 past N); returns its entry of x.
+__device__ float mg_cg_block(const MgL& L, float rv, int maxit, float rtol, float* ps,
+                             float2 (*slot)[kMgCoarseThreads / 32]) {
   const int N = L.g.N;
   const bool own = (int)threadIdx.x < N;
   int ix = 0, iy = 0, iz = 0, ip = 0;
   float dg = 0.0f, dinv = 0.0f, cw = 0.0f, ce = 0.0f, cs = 0.0f, cn = 0.0f, cb = 0.0f, ct = 0.0f;
-  float xv = 0.0f, rv = 0.0f;
+  float xv = 0.0f;
   if (own) {
     cell_of((int)threadIdx.x, L.g, ix, iy, iz, ip);
     dg = L.diag[ip];
@@ -1999,7 +1998,6 @@ k_mg_coarse_cg1(MgL L, const float* __restrict__ b, float* __restrict__ x, int m
       if (iz > 0) cb = L.Uz[ip - L.g.plane];
       if (iz < L.g.nz - 1) ct = L.Uz[ip];
     }
-    rv = b[ip];
     ps[ip] = dinv * rv;
   }
   const float2 s0 = mg_block_sum2(rv * (dinv * rv), rv * rv, slot[0]);
@@ -2033,7 +2031,57 @@ k_mg_coarse_cg1(MgL L, const float* __restrict__ b, float* __restrict__ x, int m
     rz = s.y;
     if (own) ps[ip] = fmaf(beta, pv, zv);
   }
-  if (own) x[ip] = xv;
+  return xv;
+}
+
+// The coarsest solve of one V-cycle by the block CG (when the level has no
+// inverse); the result goes to x.
+__global__ void __launch_bounds__(kMgCoarseThreads)
+k_mg_coarse_cg1(MgL L, const float* __restrict__ b, float* __restrict__ x, int maxit, float rtol) {
+  __shared__ float ps[kMgCoarseThreads];
+  __shared__ float2 slot[2][kMgCoarseThreads / 32];
+  const bool own = (int)threadIdx.x < L.g.N;
+  const float xv = mg_cg_block(L, own ? b[threadIdx.x] : 0.0f, maxit, rtol, ps, slot);
+  if (own) x[threadIdx.x] = xv;
+}
+
+// The inverse of the coarsest operator, once per set-up: block j solves
+// A x = e_j by the block CG and writes column j (inv[j N + i] = x_i); the
+// level is unpadded, so cell index and array index agree.
+constexpr float kMgInvRtol = 1e-4f;
+constexpr int kMgInvMaxit = 1000;
+__global__ void __launch_bounds__(kMgCoarseThreads)
+k_mg_coarse_inv(MgL L, float* __restrict__ inv) {
+  __shared__ float ps[kMgCoarseThreads];
+  __shared__ float2 slot[2][kMgCoarseThreads / 32];
+  const int N = L.g.N;
+  const int j = blockIdx.x;
+  const float xv = mg_cg_block(L, (int)threadIdx.x == j ? 1.0f : 0.0f, kMgInvMaxit, kMgInvRtol, ps,
+                               slot);
+  if ((int)threadIdx.x < N) inv[(size_t)j * N + threadIdx.x] = xv;
+}
+
+// x = inv b on the coarsest level: thread i takes row i, the columns stream
+// (inv[j N + i] for consecutive i is contiguous), b staged in shared memory.
+constexpr int kMgApplyThreads = 128;
+__global__ void __launch_bounds__(kMgApplyThreads)
+k_mg_coarse_apply(const float* __restrict__ inv, const float* __restrict__ b, float* __restrict__ x,
+                  int N) {
+  __shared__ float bs[kMgCoarseThreads];
+  for (int j = threadIdx.x; j < N; j += kMgApplyThreads) bs[j] = b[j];
+  __syncthreads();
+  const int i = blockIdx.x * kMgApplyThreads + threadIdx.x;
+  if (i >= N) return;
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+  int j = 0;
+  for (; j + 4 <= N; j += 4) {
+    a0 = fmaf(inv[(size_t)j * N + i], bs[j], a0);
+    a1 = fmaf(inv[(size_t)(j + 1) * N + i], bs[j + 1], a1);
+    a2 = fmaf(inv[(size_t)(j + 2) * N + i], bs[j + 2], a2);
+    a3 = fmaf(inv[(size_t)(j + 3) * N + i], bs[j + 3], a3);
+  }
+  for (; j < N; ++j) a0 = fmaf(inv[(size_t)j * N + i], bs[j], a0);
+  x[i] = (a0 + a1) + (a2 + a3);
 }
 
 // x += alpha d, r -= alpha Ad; rr -> convergence (the preconditioner's
@@ -2963,13 +3011,20 @@ MgL mg_level(const erem_ctx* c, int l) {
 }
 }  // namespace
 
-// Galerkin operators of the coarse levels, after launch_pc_setup.
+// Galerkin operators of the coarse levels, after launch_pc_setup, and the
+// inverse of the coarsest one.
 void launch_mg_setup(const erem_ctx* c, cudaStream_t s) {
   for (size_t l = 0; l < c->mg.size(); ++l) {
     const MgL f = l == 0 ? mg_fine(c) : mg_level(c, (int)l - 1);
     const MgL cl = mg_level(c, (int)l);
     ++c->launches;
     k_mg_coarsen<<<grid_for(c, cl.g.N), NT, 0, s>>>(f, cl);
+  }
+  const MgLevel& last = c->mg.back();
+  const MgL Lc = mg_level(c, (int)c->mg.size() - 1);
+  if (last.inv && Lc.g.N <= kMgCoarseThreads && Lc.g.Np == Lc.g.N) {
+    ++c->launches;
+    k_mg_coarse_inv<<<Lc.g.N, kMgCoarseThreads, 0, s>>>(Lc, last.inv);
   }
 }
 
@@ -3000,7 +3055,10 @@ int mg_cycle(const erem_ctx* c, int l, const PcPoly& poly, float omega, cudaStre
   const MgL L = mg_level(c, l);
   if (l + 1 == (int)c->mg.size()) {
     ++c->launches;
-    if (L.g.Np <= kMgCoarseThreads)
+    if (m.inv && L.g.N <= kMgCoarseThreads && L.g.Np == L.g.N)
+      k_mg_coarse_apply<<<(L.g.N + kMgApplyThreads - 1) / kMgApplyThreads, kMgApplyThreads, 0, s>>>(
+          m.inv, m.rhs, m.x[0], L.g.N);
+    else if (L.g.N <= kMgCoarseThreads && L.g.Np == L.g.N)
       k_mg_coarse_cg1<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], 400, kMgCoarseRtol);
     else
       k_mg_coarse_cg<<<1, kMgCoarseThreads, 0, s>>>(L, m.rhs, m.x[0], m.x[1], m.x[2], m.x[3], 400,
