@@ -1269,6 +1269,13 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
     if (z >= 1) c->wave_grid = z;
   }
   if (const char* e = std::getenv("EREM_LEJA_PAIRS")) c->use_pairs = std::atoi(e) != 0;
+  if (const char* e = std::getenv("EREM_WAVE_SPIN_LIMIT")) {  // cycles, at least 1000
+    const long long v = std::atoll(e);
+    if (v >= 1000) c->wave_spin_limit = v;
+  }
+  // failure-path test of the bounded waits: the two-term launch's waits run
+  // out, the call returns EREM_ETIMEOUT
+  if (const char* e = std::getenv("EREM_WAVE_WAIT_NEVER")) c->wave_wait_never = std::atoi(e) != 0;
   const size_t np = (size_t)Np, nf = (size_t)g.ny * g.nz;
   const size_t esz = prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
   erem_status st = EREM_OK;

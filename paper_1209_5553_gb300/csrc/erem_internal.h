@@ -192,6 +192,10 @@ struct erem_ctx {
   int device = 0, sm_count = 1, red_blocks = 1;
   bool use_pairs = true;  // two Leja terms per pass (wavefront launch)
   int wave_grid = 1;      // persistent blocks of the two-term launch
+  // bounded waits of the two-term launch: the clock limit of one wait, and a
+  // test hook under which every wait targets a count nothing reaches
+  long long wave_spin_limit = 400000000LL;  // cycles, about 0.2 s
+  bool wave_wait_never = false;
   int term_grid = 1;      // blocks of the one-term kernel (one resident wave)
   std::string err;
 

@@ -680,9 +680,9 @@ struct WaveGeo {
   int chunk_vecs;    // thread-vectors per chunk (last chunk of a slice may be shorter)
   int lag;           // L
   int n_items;       // 2 * nslices * cps
+  long long spin_limit;  // clock cycles a wait may take before the pass gives up
+  unsigned wait_extra;   // 0; 1 makes every wait target a count nothing reaches (failure test)
 };
-
-constexpr long long kWaveSpinLimit = 400000000LL;  // cycles (about 0.2 s) before giving up
 
 // L2 eviction priorities (createpolicy + .L2::cache_hint): the A phase
 // keeps the coefficients and q_m in L2 for the B phase (evict_last); the B
@@ -833,8 +833,8 @@ k_leja_wave(const Tq* __restrict__ qi, Tq* __restrict__ qm, Tq* __restrict__ qo,
         const long long t0 = clock64();
         const int lo = max(slice - 1, 0), hi = min(slice + 1, ns - 1);
         for (int s = lo; s <= hi; ++s) {
-          while (*(volatile unsigned*)&a_done[s] < (unsigned)cps) {
-            if ((*(volatile int*)&ctrl->flags & FLAG_TIMEOUT) || clock64() - t0 > kWaveSpinLimit) {
+          while (*(volatile unsigned*)&a_done[s] < (unsigned)cps + w.wait_extra) {
+            if ((*(volatile int*)&ctrl->flags & FLAG_TIMEOUT) || clock64() - t0 > w.spin_limit) {
               atomicOr(&ctrl->flags, FLAG_TIMEOUT);
               break;
             }
@@ -2895,7 +2895,8 @@ WaveGeoHost wave_geometry(const erem_ctx* c, int grid) {
 void launch_leja_pair(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
   const Geo g = geo_of(c);
   const WaveGeoHost h = wave_geometry(c, c->wave_grid);
-  WaveGeo w{h.nslices, h.slice_cells, h.cps, h.chunk_vecs, h.lag, h.n_items};
+  WaveGeo w{h.nslices, h.slice_cells, h.cps, h.chunk_vecs, h.lag, h.n_items,
+            c->wave_spin_limit, c->wave_wait_never ? 1u : 0u};
   int grid = c->wave_grid;
   if (grid * (WNT / 32) > h.n_items) grid = (h.n_items + WNT / 32 - 1) / (WNT / 32);
   ++c->launches;
