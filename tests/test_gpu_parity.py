@@ -246,6 +246,31 @@ def test_substeps_from_the_last_step_like_the_oracle(E):
     assert C.rel_l2(got, T) < FP64_TOL
 
 
+def test_substeps_from_one_every_step_like_the_oracle(E):
+    # the default rule on the same steps: every step restarts at one substep
+    # (the next level's divided differences are computed on a host thread
+    # while the failing level runs); schedules and values are the oracle's
+    case = C.random_case(2, 20, 16, seed=11, pe=60.0)
+    tau, steps = 0.4, 4
+    prob = case.problem(case.T0)
+    T = case.T0.copy()
+    scheds = []
+    for _ in range(steps):
+        T, res = ts.erem_step(prob, T, tau, LejaOptions(m_max=14))
+        assert res.converged
+        scheds.append(res.schedule)
+    assert all(s[0] > 1 for s in scheds)
+    with _ctx(E, case, "fp64") as ctx:
+        Tg = _t(case.T0)
+        got_s = []
+        for k in range(steps):
+            fields = (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam)) if k == 0 else (None,) * 4
+            got_s.append(ctx.erem_step(Tg, tau, *fields, opts=E.leja_opts(m_max=14)).schedule)
+        got = Tg.cpu().numpy()
+    assert got_s == scheds
+    assert C.rel_l2(got, T) < FP64_TOL
+
+
 def test_host_pointers_match_device_pointers(E):
     case = C.heat2d_rect(40, 24)
     res = []
