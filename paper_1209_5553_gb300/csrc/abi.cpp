@@ -333,7 +333,10 @@ erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1) {
       return fail(c, EREM_EINVAL, "divided differences: bad interval");
     }
     for (double v : e.d)
-      if (!std::isfinite(v)) return fail(c, EREM_ENONFINITE, "non-finite divided difference");
+      if (!std::isfinite(v)) {
+        e.M = -1;  // not cached: a later call with this interval fails the same way
+        return fail(c, EREM_ENONFINITE, "non-finite divided difference");
+      }
     c->dd_tag_S = -1;
   }
   if (c->dd_tag_S != key || c->dd_tag_M != e.M) {
