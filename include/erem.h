@@ -258,7 +258,8 @@ EREM_API erem_status rosm_step(erem_ctx* ctx, double* T, const double* p,
  *     in, the temperature p was solved at (NULL: T, right for a first step
  *     and for a pressure solved at T^n; Strang only); out, the temperature the
  *     step's pressure was solved at (T^n for Trotter, the half-step
- *     temperature for Strang), to be passed to the next step.
+ *     temperature for Strang), to be passed to the next step; an array of
+ *     its own (EINVAL if it is T or p).
  *   pressure_tol, pressure_maxit as pressure_solve.  opts: NULL or an array
  *   of one (Trotter) or two (Strang, one per half step) Leja option structs;
  *   stats: NULL or an array of as many erem_stats for the heat steps; pstats

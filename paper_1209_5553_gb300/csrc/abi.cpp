@@ -1694,10 +1694,11 @@ erem_status coupled_step(erem_ctx* c, double* T, double* p, double* T_p, const d
   if (split != EREM_SPLIT_TROTTER && split != EREM_SPLIT_STRANG)
     return fail(c, EREM_EINVAL, "splitting must be EREM_SPLIT_TROTTER or EREM_SPLIT_STRANG");
   if (!T || !p || !lnk || !phi || !lam) return fail(c, EREM_EINVAL, "NULL array argument");
+  if (T_p == T || T_p == p) return fail(c, EREM_EINVAL, "T_p must be an array of its own");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, EREM_EINVAL, "dt must be finite and > 0");
   // T_p <- the temperature the pressure was just solved at
   auto keep_Tp = [&]() -> erem_status {
-    if (T_p && T_p != T)
+    if (T_p)
       EREM_CUDA(c, cudaMemcpyAsync(T_p, T, (size_t)c->N * sizeof(double), cudaMemcpyDefault, s));
     return EREM_OK;
   };

@@ -129,6 +129,9 @@ def test_coupled_step_trotter_and_strang_match_oracle(setup):
         with pytest.raises(E.EremError) as ei:
             ctx.coupled_step(T, p, *fields, wl.dt, 7)
         assert ei.value.status == E.EREM_EINVAL
+        with pytest.raises(E.EremError) as ei:   # T_p must not alias T
+            ctx.coupled_step(T, p, *fields, wl.dt, E.EREM_SPLIT_STRANG, T_p=T)
+        assert ei.value.status == E.EREM_EINVAL
     inc = np.linalg.norm(Ts[-1] - wl.T0) / np.linalg.norm(Ts[-1])
     assert C.rel_l2(got_trotter, Ts[-1]) < max(1e-11, 10 * STEPS * bound * inc)
     assert C.rel_l2(got_strang, s_T) < max(1e-11, 10 * STEPS * bound * inc)
