@@ -335,6 +335,29 @@ def test_strang_step_pressure_is_steady_at_the_half_step():
     assert r1.converged and r2.converged
 
 
+def test_strang_T_p_enters_only_through_the_viscosity():
+    # T_p is the temperature of the last pressure solve: it sets the viscosity
+    # of the first half's Darcy fluxes and nothing else.  With T-free fluid
+    # laws it has no effect; with the T-dependent ones it changes the fluxes
+    # and so the result, but not the half-step temperature's starting state
+    wl, g, ph0 = _strang_setup(0)
+    rng = np.random.default_rng(3)
+    Tp = wl.T0 + rng.uniform(-5.0, 5.0, wl.T0.size)
+    p = ts.pressure_solve_direct(g, ph0, wl.lnk, wl.T0)
+    a = ts.strang_step(g, ph0, wl.lnk, wl.phi, wl.lam, wl.T0, p, 0.02)
+    b = ts.strang_step(g, ph0, wl.lnk, wl.phi, wl.lam, wl.T0, p, 0.02, T_p=Tp)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    wl, g, ph1 = _strang_setup(1)
+    p = ts.pressure_solve_direct(g, ph1, wl.lnk, wl.T0)
+    a = ts.strang_step(g, ph1, wl.lnk, wl.phi, wl.lam, wl.T0, p, 0.02)
+    b = ts.strang_step(g, ph1, wl.lnk, wl.phi, wl.lam, wl.T0, p, 0.02, T_p=Tp)
+    assert not np.array_equal(a[2], b[2])
+    # the first half with T_p is the EREM step of the fluxes of p at viscosity(T_p)
+    prob = ts.heat_problem(g, ph1, wl.lnk, wl.phi, wl.lam, p, Tp)
+    Th, _ = ts.erem_step(prob, wl.T0, 0.01)
+    assert np.array_equal(Th, b[2])
+
+
 def test_strang_and_trotter_converge_to_the_same_solution():
     # with the steady pressure both splittings are first order here (0.94 to
     # 1.10 measured from 4 to 32 steps); both approach the same limit
