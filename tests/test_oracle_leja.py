@@ -297,3 +297,100 @@ def test_phi1_fast_leja_matches_dense_expm(tau):
     # polynomials
     exact = leja.phi1_leja(J, v, tau, float(np.max(np.abs(T))), LejaOptions(tol_a=1e-13, tol_r=1e-13))
     assert np.linalg.norm(res.value - exact.value) / np.linalg.norm(ref) < 2e-10
+
+
+# ---------------------------------------------------------------------------
+# the stopping rule of §4.2, pinned on a diagonal J whose Newton vectors have a
+# closed form, so the sequence of error estimates e_m is known without the
+# oracle's recurrence or its divided-difference routine
+# ---------------------------------------------------------------------------
+def _closed_form_estimates(lam, v, tau, y_inf, tol, M, mp):
+    """e_1..e_M for J = diag(lam): the interval of tau J is [tau min, tau max];
+    mode i of q_m is v_i prod_{k<m} ((tau lam_i - c)/gamma - xi_k); d_m are
+    160-digit recursive divided differences; e_m is the weighted RMS of the
+    increment tau d_m q_m with scal = tol_a + tol_r ||y||_inf (tol_a = tol_r)."""
+    alpha, beta = tau * lam.min(), tau * lam.max()
+    c, gamma = 0.5 * (alpha + beta), 0.25 * (beta - alpha)
+    xi = leja.leja_points(M)
+    d = [float(x) for x in _mp_divided_differences(xi, c, gamma, mp)]
+    z = (tau * lam - c) / gamma
+    scal = tol + tol * y_inf
+    q = np.asarray(v, np.float64).copy()
+    e = []
+    for m in range(1, M + 1):
+        q = q * (z - xi[m - 1])
+        e.append(math.sqrt(float(np.mean((tau * d[m] * q / scal) ** 2))))
+    return np.array(e)
+
+
+def _first_stop(e, window, p=2, divisor=None, first=1):
+    """First m >= first with 10^p times the mean of the last `window`
+    estimates (those that exist) below 1; `divisor` replaces the count of
+    averaged estimates (a zero-padded mean)."""
+    for m in range(first, len(e) + 1):
+        tail = e[max(0, m - window):m]
+        mean = float(np.sum(tail)) / (divisor or tail.size)
+        if 10.0**p * mean < 1.0:
+            return m
+    return None
+
+
+def _diagonal_case(n, lam_max, seed):
+    rng = np.random.default_rng(seed)
+    lam = -np.sort(rng.uniform(0.0, lam_max, n))
+    lam[0], lam[-1] = 0.0, -lam_max
+    return lam, rng.normal(0.0, 1.0, n)
+
+
+@pytest.mark.parametrize("n,lam_max,tau,y_inf,tol", [
+    (40, 50.0, 1.0, 1.0, 1e-6),    # window 4 / 5 / 6 stop at 29 / 30 / 31
+    (40, 200.0, 0.5, 80.0, 1e-8),  # tau != 1 and a state scale in scal
+    (64, 400.0, 0.25, 20.0, 3e-7),
+])
+def test_stopping_rule_degree_from_closed_form_estimates(n, lam_max, tau, y_inf, tol):
+    # §4.2: stop at the first m where 10^p (p = 2) times the mean of the last
+    # five estimates is below 1.  The case is chosen so that a window of 4 or
+    # 6, the last estimate alone, or a stop one term late each give another
+    # degree than the rule as printed.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 160
+    lam, v = _diagonal_case(n, lam_max, seed=7)
+    e = _closed_form_estimates(lam, v, tau, y_inf, tol, 90, mp)
+    want = _first_stop(e, 5)
+    assert want is not None
+    variants = {_first_stop(e, 4), _first_stop(e, 6), _first_stop(e, 1), want + 1}
+    assert want not in variants, (want, variants)
+    res = leja.phi1_leja(sp.diags(lam), v, tau, y_inf, LejaOptions(tol_a=tol, tol_r=tol))
+    assert res.converged and res.substeps == 1
+    assert res.degrees == [want]
+    # the reported estimate is that mean at the stopping degree
+    assert res.err_est == pytest.approx(float(np.mean(e[want - 5:want])), rel=1e-9)
+    # the value is the Newton sum up to that degree: tau phi_1(tau lam) v
+    # within the estimate's tolerance, mode by mode
+    exact = tau * np.array([math.expm1(tau * x) / (tau * x) if x != 0 else 1.0 for x in lam]) * v
+    scal = tol + tol * y_inf
+    assert leja.weighted_norm(res.value - exact, scal) < 1.0
+
+
+def test_stopping_rule_averages_the_estimates_that_exist_at_the_start():
+    # before five estimates exist the mean runs over e_1..e_m (§4.2 gives no
+    # minimum degree).  v is scaled so that 10^p e_1 = 2.5 and the later
+    # estimates are far smaller: the rule stops at m = 3, where the mean first
+    # drops below 10^-p; a zero-padded mean (sum / 5) would stop at m = 1, a
+    # rule that waits for five estimates at m = 5, the last estimate alone at
+    # m = 2.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 160
+    lam, v = _diagonal_case(16, 0.5, seed=3)
+    tol, tau = 1e-3, 1.0
+    e1 = _closed_form_estimates(lam, v, tau, 1.0, tol, 1, mp)[0]
+    v = v * (2.5 / (100.0 * e1))
+    e = _closed_form_estimates(lam, v, tau, 1.0, tol, 20, mp)
+    assert 100.0 * e[0] == pytest.approx(2.5, rel=1e-12) and 100.0 * e[1] < 0.4
+    want = _first_stop(e, 5)
+    assert want == 3
+    assert _first_stop(e, 5, divisor=5) == 1
+    assert _first_stop(e, 5, first=5) == 5
+    assert _first_stop(e, 1) == 2
+    res = leja.phi1_leja(sp.diags(lam), v, tau, 1.0, LejaOptions(tol_a=tol, tol_r=tol))
+    assert res.degrees == [want] and res.substeps == 1
