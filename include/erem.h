@@ -306,15 +306,22 @@ EREM_API erem_status rosm_integrate(erem_ctx* ctx, double* T, double t_end, doub
  * cudaMalloc; erem_create does, so they could not reach pressure_solve.
  * This call needs no context: it runs the Jacobi-preconditioned CG of
  * pressure_solve (erem_set_pressure_precond degree 1), with its work vectors, reduction partials and control
- * block in one static device array compiled into the library (about 5.8 MB
- * on every GPU that loads the library, held until the process exits).
+ * block in one static device array compiled into the library (about 5.8 MB).
+ * The runtime loads the library's device code lazily: the first call on a
+ * device loads it there, which places the array in that device's memory, so
+ * a caller under a fixed budget sees those 5.8 MB taken by its first call
+ * (make it at start-up); the array then stays until the process exits, and
+ * later calls take no device memory.
  *   grid, phys  as for erem_create (only the heads and fluid_model are used)
  *   lnk [N], T [N] (may be NULL: T = 20), p [N] in: guess, out: solution;
- *   all three must be device pointers (no staging: that would allocate).
- *   tol, maxit, stats as for pressure_solve.
+ *   all three must be device memory of the current device, or managed
+ *   memory (host arrays, pinned or not, are refused: staging would allocate).
+ *   tol, maxit as for pressure_solve; stats as for pressure_solve, with t_ms
+ *   the host wall time of the call (it waits for its kernels).
  * Limit: round_up(nx, 4) * ny * nz <= 65536 cells, else EREM_EINVAL.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
+ * Every call looks up the array's device address with the current device
+ * (after a device reset the module, and the array, are loaded anew); make
+ * the first call on a device before any stream capture.  Every
  * call shares the array and finds there what the last call left; the call
  * clears what must start at zero, but calls that overlap on the GPU (from
  * other streams or threads) race on it.  The call calls no cudaMalloc or

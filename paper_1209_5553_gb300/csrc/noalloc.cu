@@ -9,14 +9,16 @@
 // part of the loaded library, so the call itself allocates nothing; the
 // caller still passes its own device arrays for the inputs and the output.
 //
-// The array holds at most kMaxCells padded cells; every GPU that loads the
-// library keeps it (about 5.8 MB) until the process exits.  All calls share
-// it and it keeps what the last call left there: each call clears the parts
-// that must start at zero, and two calls that overlap on the GPU (different
-// streams or host threads) race on it.
+// The array holds at most kMaxCells padded cells (about 5.8 MB).  With the
+// CUDA runtime's lazy module loading the array is placed on a device when
+// the library's module is loaded there, which the first call on that device
+// does (through cudaGetSymbolAddress); from then on it stays until the
+// process exits.  All calls share it and it keeps what the last call left
+// there: each call clears the parts that must start at zero, and two calls
+// that overlap on the GPU (different streams or host threads) race on it.
+#include <chrono>
 #include <cstddef>
 #include <cstring>
-#include <mutex>
 
 #include "erem_internal.h"
 
@@ -31,42 +33,37 @@ constexpr size_t kWords = (size_t)kVecs * kMaxCells + (size_t)kMaxBlocks * erem:
 
 static __device__ __align__(256) double g_pressure_scratch[kWords];
 
-struct DeviceScratch {
-  int device;
-  double* base;
-};
-std::mutex g_mu;
-DeviceScratch g_known[64];
-int g_nknown = 0;
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// Device address of the scratch array on the current device.  It is looked
+// up on every call (with the device current), not cached: a device reset or
+// a new primary context reloads the module and places the array anew.  Once
+// the module is loaded on the device the lookup allocates nothing.
 erem_status scratch_base(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return EREM_ECUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  for (int k = 0; k < g_nknown; ++k)
-    if (g_known[k].device == dev) {
-      *out = g_known[k].base;
-      return EREM_OK;
-    }
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_pressure_scratch) != cudaSuccess || p == nullptr) {
     cudaGetLastError();
     return EREM_ECUDA;
   }
-  if (g_nknown < 64) g_known[g_nknown++] = DeviceScratch{dev, (double*)p};
   *out = (double*)p;
   return EREM_OK;
 }
 
-bool on_device(const void* p) {
+// A device array the kernels of the current device can read: device memory
+// of this device (memory of another GPU would be an illegal address here
+// without peer access), or managed memory.  Host memory is refused, pinned
+// or not: staging it through device buffers would allocate.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -86,14 +83,15 @@ extern "C" erem_status erem_pressure_solve_static(const erem_grid* grid, const e
   const long long px = ((long long)g.nx + 3) / 4 * 4;
   const long long Np = px * g.ny * g.nz;
   if (Np > kMaxCells) return EREM_EINVAL;  // grid larger than the static scratch
-  if (!on_device(lnk) || !on_device(p) || (T && !on_device(T))) return EREM_EINVAL;
-
-  double* base = nullptr;
-  if (scratch_base(&base) != EREM_OK) return EREM_ECUDA;
+  const double t0 = now_ms();
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return EREM_ECUDA;
+  if (!on_device(lnk, dev) || !on_device(p, dev) || (T && !on_device(T, dev))) return EREM_EINVAL;
+
+  double* base = nullptr;
+  if (scratch_base(&base) != EREM_OK) return EREM_ECUDA;
 
   // A context view over the scratch array: the existing CG launchers read
   // their geometry and work-vector pointers from it.  Nothing is allocated.
@@ -156,6 +154,7 @@ extern "C" erem_status erem_pressure_solve_static(const erem_grid* grid, const e
     stats->flux_in = h.flux_in;
     stats->vmax = h.vmax;
     stats->launches = (int)v.launches;
+    stats->t_ms = now_ms() - t0;
   }
   if (last.lin_break && !(last.lin[K_RR] <= last.lin[K_TOL2])) return EREM_ENOTCONV;
   if (!last.lin_done) return EREM_ENOTCONV;

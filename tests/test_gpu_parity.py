@@ -146,6 +146,9 @@ def test_erem_heat2d_64_free_running_fp64_and_fp32(E):
                 got_s.append(ctx.erem_step(T, case.dt).schedule)
             got = T.cpu().numpy()
         assert C.rel_l2(got, T_ref) < tol, prec
+        # the change the 20 steps made, T^20 - T^0, to the same bound
+        inc_tol = 10 * tol if prec == "fp64" else tol
+        assert C.rel_l2(got - case.T0, T_ref - case.T0) < inc_tol, prec
         if prec == "fp64":
             assert got_s == scheds
 
@@ -164,6 +167,8 @@ def test_erem_steps_3d(E, name, make):
                 ctx.erem_step(T, case.dt, *fields, opts=opts)
             got = T.cpu().numpy()
         assert C.rel_l2(got, T_ref) < tol, prec
+        inc_tol = 10 * tol if prec == "fp64" else tol
+        assert C.rel_l2(got - case.T0, T_ref - case.T0) < inc_tol, prec
 
 
 def test_erem_nonlinear_fluid_reassembles_every_step(E):

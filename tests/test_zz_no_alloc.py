@@ -1,13 +1,16 @@
 """The pressure solve that allocates nothing (erem_pressure_solve_static),
 for callers that cannot call cudaMalloc: its work space is a static device
 array inside the library.  Checked through the C ABI against the context
-entry point pressure_solve on the same inputs, on consecutive calls that
-share (and inherit) the static array, within the pressure tolerance the
-solver tests use.  This file is collected last on purpose."""
+entry point pressure_solve and against the oracle's direct solve on the same
+inputs, on consecutive calls that share (and inherit) the static array,
+within the pressure tolerance the solver tests use; the second call must
+leave the device's free memory unchanged.  This file is collected last on
+purpose."""
 import numpy as np
 import pytest
 
 from oracle import fv
+from oracle import timestep as ts
 
 pytestmark = pytest.mark.gpu
 
@@ -49,17 +52,25 @@ def test_static_pressure_solve_matches_pressure_solve(dims):
         st_ref = ctx.pressure_solve(t(lnk), t(T) if fm else None, p_ref, tol=PRESSURE_TOL)
         ref = p_ref.cpu().numpy()
     bound = _bound(g, ph, lnk, T)
+    direct = ts.pressure_solve_direct(g, ph, lnk, T)
     grid = E.erem_grid(dim, nx, ny, nz, 1.0, 1.0, 1.0)
+    args = [(t(guess), t(lnk), t(T) if fm else None) for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):  # two calls in a row share the static work space
-        p = t(guess)
-        st = E.erem_pressure_solve_static(grid, phys.c(), t(lnk), t(T) if fm else None, p,
-                                          tol=PRESSURE_TOL)
+        p, lk, Tt = args[call]
+        free0 = torch.cuda.mem_get_info()[0]
+        st = E.erem_pressure_solve_static(grid, phys.c(), lk, Tt, p, tol=PRESSURE_TOL)
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:  # the first call may load the module (and place the array)
+            assert free1 == free0
         got = p.cpu().numpy()
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= bound, call
+        assert np.linalg.norm(got - direct) / np.linalg.norm(direct) <= bound, call
         assert st.lin_resid <= PRESSURE_TOL
         assert st.lin_iters == st_ref.lin_iters
         assert st.flux_in == pytest.approx(st_ref.flux_in, rel=1e-10)
         assert st.vmax == pytest.approx(st_ref.vmax, rel=1e-10)
+        assert st.t_ms > 0.0
 
 
 def test_static_pressure_solve_rejects_grids_beyond_its_limit():
@@ -78,3 +89,10 @@ def test_static_pressure_solve_rejects_grids_beyond_its_limit():
     with pytest.raises(E.EremError) as ei:
         E.erem_pressure_solve_static(small, E.Physics().c(), np.zeros(64), None, np.zeros(64))
     assert ei.value.status == E.EREM_EINVAL
+    # page-locked host memory too, although the GPU could address it
+    pinned = torch.zeros(64, dtype=torch.float64).pin_memory()
+    dev = torch.zeros(64, dtype=torch.float64, device="cuda")
+    for lk, p in ((pinned, dev), (dev, pinned.clone().pin_memory())):
+        with pytest.raises(E.EremError) as ei:
+            E.erem_pressure_solve_static(small, E.Physics().c(), lk, None, p)
+        assert ei.value.status == E.EREM_EINVAL
