@@ -41,9 +41,8 @@ if ROOT not in sys.path:
 
 METRIC = "EREM Mcell-steps/s at 256³ FP32-bulk vs FP64 at ≤1e-5 rel err; HBM GB/s vs peak"
 UNIT = "Mcell-steps/s"
-# algorithmic bytes per cell of one Leja launch (3D): 7 coefficients, q read,
-# q written, P read and written (FP64) -- the same for the one-term kernel and
-# for the two-term pass, which reads the coefficients once for both terms
+# algorithmic bytes per cell of one Leja term (3D): 7 coefficients, q read,
+# q written, P read and written (FP64)
 BYTES_PER_CELL_TERM = {"fp32_bulk": 7 * 4 + 4 + 4 + 16, "fp64": 7 * 8 + 8 + 8 + 16}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -446,12 +445,11 @@ def main(args):
     ms, value = aggregate(r32["ms"], N, K, world, dev)
     peak, peak_kind = measured_peaks()
     b32 = BYTES_PER_CELL_TERM["fp32_bulk"]
-    # one Leja launch (one term, or two terms in one pass) must move the
-    # coefficients once, q in and out, and P in and out: 52 B per cell
+    # one Leja term must move the coefficients once, q in and out, and P in
+    # and out: 52 B per cell
     sec_leja = r32["t_terms_ms"] / 1e3
     achieved = b32 * N * r32["n_leja"] / sec_leja / 1e9 if r32["n_leja"] else None
     effective = b32 * N * r32["n_terms"] / sec_leja / 1e9 if r32["n_terms"] else None
-    pairs = r32["n_terms"] > r32["n_leja"]
     traffic = recorded_traffic("fp32_bulk", N)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wu,
@@ -467,7 +465,7 @@ def main(args):
         "gpu_launches": r32["launches"],
         "leja": {"degrees_per_step": [s[1:] if s[0] == 1 else s for s in r32["degrees"]],
                  "terms_timed": r32["n_terms"], "alpha": r32["alpha"], "beta": r32["beta"]},
-        "roofline": {"kernel": "k_leja_pair<float,3>" if pairs else "k_leja_term<float,4,3>",
+        "roofline": {"kernel": "k_leja_term<float,4,3>",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"

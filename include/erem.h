@@ -55,7 +55,7 @@ typedef enum {
   EREM_EINVAL = 1,     /* bad argument, or physically invalid input field    */
   EREM_ENOMEM = 2,     /* device or pinned host allocation failed            */
   EREM_ENOTCONV = 3,   /* Leja interpolation or linear solver did not converge */
-  EREM_ETIMEOUT = 4,   /* a bounded device-side wait gave up (reserved)      */
+  EREM_ETIMEOUT = 4,   /* an iteration bound ran out (the batched loop)      */
   EREM_ENONFINITE = 5, /* NaN or Inf in an input or an intermediate result   */
   EREM_ECUDA = 6       /* CUDA runtime error (message in erem_last_error)    */
 } erem_status;

@@ -114,8 +114,6 @@ erem_status read_ctrl(erem_ctx* c, cudaStream_t s) {
 }
 
 erem_status check_flags(erem_ctx* c) {
-  if (c->ctrl_h->flags & FLAG_TIMEOUT)
-    return fail(c, EREM_ETIMEOUT, "a two-term Leja pass gave up waiting for a slice (bounded wait)");
   if (c->ctrl_h->flags & FLAG_NONFINITE)
     return fail(c, EREM_ENONFINITE, "non-finite value in an input field or its derived coefficients");
   if (c->ctrl_h->flags & FLAG_BAD_INPUT)
@@ -469,24 +467,19 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
   }
   int m = 1, qin = 0;
   int chunk = forced ? forced : std::max(4, c->last_degree + 2);
-  // launches of this interpolation: first term, terms computed, output buffer
-  struct Launch { int m, nterms, qout; };
-  std::vector<Launch> launches;
+  // the first term of every launch of this interpolation, in order
+  std::vector<int> launches;
   while (true) {
     const int end = forced ? forced : std::min(*M_avail, m + chunk - 1);
-    int mm = m;
-    while (mm <= end) {
-      const int nt = (c->use_pairs && !slot0 && mm + 1 <= end) ? 2 : 1;
+    for (int mm = m; mm <= end; ++mm) {
       if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size()], s);
       if (slot0)
         launch_leja_term_ptr(c, mm, slot0 + (size_t)(mm - 1) * qbytes, slot0 + (size_t)mm * qbytes,
                              cg, s);
-      else if (nt == 2) launch_leja_pair(c, mm, qin, cg, s);
       else launch_leja_term(c, mm, qin, cg, s);
       if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size() + 1], s);
-      launches.push_back(Launch{mm, nt, qin ^ 1});
+      launches.push_back(mm);
       qin ^= 1;
-      mm += nt;
     }
     EREM_TRY(check_launch(c, "leja term"));
     EREM_TRY(read_ctrl(c, s));
@@ -505,11 +498,6 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     }
     if (h.done && !h.fail) {
       *degree = h.degree;
-      if (h.overshoot) {  // the pair that met the test at its first term
-        for (const Launch& l : launches)
-          if (l.m == *degree && l.nterms == 2)
-            launch_unstep(c, l.qout, dd_entry(c, S, phi).d[*degree + 1], s);
-      }
       break;
     }
     if (h.fail || end >= o.m_max) {
@@ -533,11 +521,11 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
   }
   if (o.time_terms && tt) {
     for (size_t j = 0; j < launches.size(); ++j) {
-      if (launches[j].m > *degree) break;  // returned at once: the test had passed
+      if (launches[j] > *degree) break;  // returned at once: the test had passed
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, c->ev[2 * j], c->ev[2 * j + 1]) == cudaSuccess) {
         tt->ms += ms;
-        tt->terms += launches[j].nterms;
+        tt->terms += 1;
         ++tt->launches;
       }
     }
@@ -1259,26 +1247,12 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     return bail(EREM_ECUDA);
   c->red_blocks = c->sm_count * 8;
-  c->wave_grid = c->sm_count;
   int term_waves = 1;  // the one-term grid is one resident wave
   if (const char* e = std::getenv("EREM_TERM_WAVES")) {  // tuning override
     const int w = std::atoi(e);
     if (w >= 1) term_waves = w;
   }
   c->term_grid = std::min(c->red_blocks, term_waves * c->sm_count * leja_term_blocks_per_sm(c));
-  c->use_pairs = false;  // two-term passes are opt-in (EREM_LEJA_PAIRS=1)
-  if (const char* e = std::getenv("EREM_WAVE_GRID")) {  // tuning override
-    const int z = std::atoi(e);
-    if (z >= 1) c->wave_grid = z;
-  }
-  if (const char* e = std::getenv("EREM_LEJA_PAIRS")) c->use_pairs = std::atoi(e) != 0;
-  if (const char* e = std::getenv("EREM_WAVE_SPIN_LIMIT")) {  // cycles, at least 1000
-    const long long v = std::atoll(e);
-    if (v >= 1000) c->wave_spin_limit = v;
-  }
-  // failure-path test of the bounded waits: the two-term launch's waits run
-  // out, the call returns EREM_ETIMEOUT
-  if (const char* e = std::getenv("EREM_WAVE_WAIT_NEVER")) c->wave_wait_never = std::atoi(e) != 0;
   const size_t np = (size_t)Np, nf = (size_t)g.ny * g.nz;
   const size_t esz = prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
   erem_status st = EREM_OK;
@@ -1296,13 +1270,6 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   for (int k = 0; k < 2; ++k)
     if (st == EREM_OK) st = dalloc(c, &c->q[k], np * esz);
   A(&c->red_part, (size_t)c->red_blocks * kRedSlots);
-  const WaveGeoHost wg = wave_geometry(c, c->wave_grid);
-  A(&c->wave_part, (size_t)wg.n_items);
-  if (st == EREM_OK) st = dalloc(c, &c->qmid, np * esz);
-  if (st == EREM_OK) st = dalloc(c, (void**)&c->wave_ctr, 4 * sizeof(unsigned));
-  if (st == EREM_OK) st = dalloc(c, (void**)&c->wave_done, (size_t)wg.nslices * sizeof(unsigned));
-  if (st == EREM_OK) st = dalloc(c, (void**)&c->wave_bdone, (size_t)wg.nslices * sizeof(unsigned));
-  A(&c->wave_spart, 2 * (size_t)wg.nslices);
   A(&c->dd_dev, (size_t)kMaxTerms + 2);
   if (st == EREM_OK) st = dalloc(c, (void**)&c->red_cnt, sizeof(unsigned) * 4);
   if (st == EREM_OK) st = dalloc(c, (void**)&c->ctrl, sizeof(Ctrl));
@@ -1321,7 +1288,7 @@ erem_status erem_destroy(erem_ctx* c) {
   if (!c) return EREM_OK;
   double* dp[] = {c->lnk, c->phi, c->lam, c->p, c->Lx, c->Ly, c->Lz, c->Fx, c->Fy, c->Fz,
                   c->icap, c->LD0, c->F0, c->b0, c->Tn, c->vrhs, c->vin, c->w, c->u, c->P,
-                  c->red_part, c->xi_dev, c->dd_dev, c->wave_part, c->wave_spart};
+                  c->red_part, c->xi_dev, c->dd_dev};
   for (double* p : dp)
     if (p) cudaFree(p);
   for (int k = 0; k < 7; ++k)
@@ -1370,10 +1337,6 @@ erem_status erem_destroy(erem_ctx* c) {
       if (p) cudaFree(p);
   if (c->kr_host) cudaFreeHost(c->kr_host);
   if (c->red_cnt) cudaFree(c->red_cnt);
-  if (c->qmid) cudaFree(c->qmid);
-  if (c->wave_ctr) cudaFree(c->wave_ctr);
-  if (c->wave_done) cudaFree(c->wave_done);
-  if (c->wave_bdone) cudaFree(c->wave_bdone);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
   if (c->dd_h) cudaFreeHost(c->dd_h);

@@ -60,7 +60,6 @@ __device__ void ens_arm(const EnsMember& M, const EnsState* st) {
   c->fail = 0;
   c->nonfinite = 0;
   c->m_last = 0;
-  c->overshoot = 0;
   c->err = 0.0;
   StopParams sp = M.sp;
   sp.delta = M.dt / (double)(1 << st->level);

@@ -22,7 +22,7 @@ constexpr int kMgCoarsest = 512;   // cells of the coarsest multigrid level, at 
 constexpr int kRedSlots = 4;       // reduction values per block
 
 // Bits of Ctrl::flags raised by the set-up kernels.
-enum : int { FLAG_NONFINITE = 1, FLAG_BAD_INPUT = 2, FLAG_TIMEOUT = 4 };
+enum : int { FLAG_NONFINITE = 1, FLAG_BAD_INPUT = 2 };
 
 // Parameters of the Leja stopping test of one substep (§4.2).
 struct StopParams {
@@ -55,7 +55,6 @@ struct Ctrl {
   int lin_done;    // linear solver converged (or broke down)
   int lin_it;      // linear solver iterations
   int lin_break;   // linear solver breakdown
-  int overshoot;   // a two-term pass added one term past the stopping degree
   double err;      // mean error estimate at the last term
   double yinf;     // ||T^n||_inf of the current state
   double gmin, gmax;   // Gershgorin bounds of J (before the factor dt)
@@ -190,12 +189,6 @@ struct erem_ctx {
   long long N = 0, Np = 0;   // real and padded cell counts
   double hx = 1, hy = 1, hz = 1, vol = 1, ax = 1, ay = 1, az = 1;
   int device = 0, sm_count = 1, red_blocks = 1;
-  bool use_pairs = true;  // two Leja terms per pass (wavefront launch)
-  int wave_grid = 1;      // persistent blocks of the two-term launch
-  // bounded waits of the two-term launch: the clock limit of one wait, and a
-  // test hook under which every wait targets a count nothing reaches
-  long long wave_spin_limit = 400000000LL;  // cycles, about 0.2 s
-  bool wave_wait_never = false;
   int term_grid = 1;      // blocks of the one-term kernel (one resident wave)
   std::string err;
 
@@ -215,12 +208,6 @@ struct erem_ctx {
   // vectors
   double *Tn = nullptr, *vrhs = nullptr, *vin = nullptr, *w = nullptr, *u = nullptr, *P = nullptr;
   void* q[2] = {};
-  void* qmid = nullptr;             // q_m of a two-term pass (Leja precision)
-  double* wave_part = nullptr;      // per-item norm partials of a two-term pass
-  unsigned* wave_ctr = nullptr;     // claim and exit counters of a two-term pass
-  unsigned* wave_done = nullptr;    // completed A items per slice
-  unsigned* wave_bdone = nullptr;   // completed B items per slice
-  double* wave_spart = nullptr;     // per-slice norm partials (A then B)
   // linear solvers (allocated on first use)
   double* kv[12] = {};
   // pressure CG polynomial preconditioner: degree (1 = Jacobi), FP32 arrays
@@ -371,12 +358,6 @@ int leja_term_blocks_per_sm(const erem_ctx* c);
 void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
 void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,
                           cudaStream_t s);
-struct WaveGeoHost {
-  int nslices = 0, slice_cells = 0, cps = 0, chunk_vecs = 0, lag = 0, n_items = 0;
-};
-WaveGeoHost wave_geometry(const erem_ctx* c, int grid);
-void launch_leja_pair(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
-void launch_unstep(const erem_ctx* c, int qbuf, double d, cudaStream_t s);
 void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,
                  cudaStream_t s);
 void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,

@@ -654,317 +654,6 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
   }
 }
 
-// Two Leja terms per pass (m and m+1), as one streaming "wavefront" launch.
-//
-// The grid is cut into slices along its outermost dimension (z-planes in 3D,
-// y-rows in 2D) and each slice into chunks.  Work items are claimed from an
-// atomic counter in a fixed order: A(s) computes q_m on slice s from q_{m-1}
-// and stores it in a scratch vector; B(s - L), L slices behind, computes
-// q_{m+1} from q_m, adds d_m q_m + d_{m+1} q_{m+1} to P and stores q_{m+1}.
-// B(s) needs A(s-1), A(s), A(s+1); those items come earlier in the claim
-// order, so they are held by running blocks and will finish (B waits for
-// them with a bounded spin; no item ever waits on a later one).  With the
-// lag L, B re-reads the coefficients and q_m a few slices after A brought
-// them in, from L2: per pair of terms HBM sees the coefficients once, q_{m-1}
-// once, q_m written back once, P read and written once and q_{m+1} written.
-// Every access is the vectorised streaming stencil of k_leja_term.
-//
-// Norm partials are kept per item and summed in item order by the last block
-// to leave, which also runs the two stopping tests and resets the counters.
-// When the test passes at term m, P holds d_{m+1} q_{m+1} too many; the host
-// removes it with k_unstep before P is used.
-struct WaveGeo {
-  int nslices;       // slices along the march dimension
-  int slice_cells;   // padded cells per slice
-  int cps;           // chunks per slice
-  int chunk_vecs;    // thread-vectors per chunk (last chunk of a slice may be shorter)
-  int lag;           // L
-  int n_items;       // 2 * nslices * cps
-  long long spin_limit;  // clock cycles a wait may take before the pass gives up
-  unsigned wait_extra;   // 0; 1 makes every wait target a count nothing reaches (failure test)
-};
-
-// L2 eviction priorities (createpolicy + .L2::cache_hint): the A phase
-// keeps the coefficients and q_m in L2 for the B phase (evict_last); the B
-// phase reads them for the last time (evict_first).
-__device__ __forceinline__ unsigned long long l2_policy_last() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ unsigned long long l2_policy_first() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ float4 ld_hint(const float4* a, unsigned long long pol) {
-  float4 r;
-  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-               : "l"(a), "l"(pol));
-  return r;
-}
-__device__ __forceinline__ double2 ld_hint(const double2* a, unsigned long long pol) {
-  double2 r;
-  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
-               : "=d"(r.x), "=d"(r.y)
-               : "l"(a), "l"(pol));
-  return r;
-}
-__device__ __forceinline__ void st_hint(float4* a, float4 v, unsigned long long pol) {
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(a), "f"(v.x),
-               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void st_hint(double2* a, double2 v, unsigned long long pol) {
-  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y),
-               "l"(pol)
-               : "memory");
-}
-
-template <typename Tq, int VEC, int DIM>
-__device__ __forceinline__ void stencil_vec(const Tq* __restrict__ q, const LejaCoef<Tq>& cf, const Geo& g,
-                                            int i, int ix, int iy, int iz, Tq shift, bool l2_only,
-                                            unsigned long long cpol, Tq (&out)[VEC]) {
-  Tq qc[VEC], qs[VEC], qn[VEC], qb[VEC], qt[VEC];
-  auto ld = [&](Tq (&r)[VEC], const Tq* p) {
-    using V = typename VecT<Tq, VEC>::V;
-    const V v = l2_only ? __ldcg(reinterpret_cast<const V*>(p)) : *reinterpret_cast<const V*>(p);
-    const Tq* s = reinterpret_cast<const Tq*>(&v);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) r[k] = s[k];
-  };
-  ld(qc, q + i);
-  ld(qs, q + i - (iy > 0 ? g.px : 0));
-  ld(qn, q + i + (iy < g.ny - 1 ? g.px : 0));
-  if (DIM == 3) {
-    ld(qb, q + i - (iz > 0 ? g.plane : 0));
-    ld(qt, q + i + (iz < g.nz - 1 ? g.plane : 0));
-  }
-  const Tq ql = ix > 0 ? (l2_only ? __ldcg(q + i - 1) : q[i - 1]) : Tq(0);
-  const Tq qr = ix + VEC < g.px ? (l2_only ? __ldcg(q + i + VEC) : q[i + VEC]) : Tq(0);
-  constexpr int NC = DIM == 3 ? 7 : 5;
-  Tq c[7][VEC];
-  using V = typename VecT<Tq, VEC>::V;
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const V v = ld_hint(reinterpret_cast<const V*>(cf.c[k] + leja_off<32 * VEC>(i, cf.nc)), cpol);
-    const Tq* s = reinterpret_cast<const Tq*>(&v);
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) c[k][j] = s[j];
-  }
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) {
-    const Tq west = k == 0 ? ql : qc[k - 1];
-    const Tq east = k == VEC - 1 ? qr : qc[k + 1];
-    Tq a = (c[0][k] - shift) * qc[k];
-    a = fma(c[1][k], west, a);
-    a = fma(c[2][k], east, a);
-    a = fma(c[3][k], qs[k], a);
-    a = fma(c[4][k], qn[k], a);
-    if (DIM == 3) {
-      a = fma(c[5][k], qb[k], a);
-      a = fma(c[6][k], qt[k], a);
-    }
-    out[k] = a;
-  }
-}
-
-// Warps, not blocks, claim the work items, so nothing in the march needs a
-// block-wide barrier.  An item is WAVE_U thread-vectors per lane of one warp.
-// The norm partial of every item goes to ipart; the last warp to finish a
-// slice (per phase) sums that slice's items in order into spart, and the last
-// warp to leave sums the slice partials in order: the result does not depend
-// on which warp did what.
-constexpr int WAVE_U = 4;
-constexpr int WNT = 128;  // threads per block of the two-term launch
-
-__device__ __forceinline__ double warp_sum_all(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename Tq, int VEC, int DIM>
-__global__ void __launch_bounds__(WNT)
-k_leja_wave(const Tq* __restrict__ qi, Tq* __restrict__ qm, Tq* __restrict__ qo,
-            double* __restrict__ P, LejaCoef<Tq> cf, Geo g, WaveGeo w,
-            const double* __restrict__ xi, const double* __restrict__ dd, double cg, int m,
-            double* __restrict__ ipart, double* __restrict__ spart, unsigned* wctr,
-            unsigned* a_done, unsigned* b_done, Ctrl* ctrl) {
-  if (*(volatile int*)&ctrl->done) return;
-  const int lane = threadIdx.x & 31;
-  const unsigned total_warps = gridDim.x * (WNT / 32);
-  const Tq s1 = (Tq)(cg + xi[m - 1]);
-  const Tq s2 = (Tq)(cg + xi[m]);
-  const double d1 = dd[m], d2 = dd[m + 1];
-  const int vrow = g.px / VEC;
-  const int svecs = w.slice_cells / VEC;  // thread-vectors per slice
-  const int lag = w.lag, cps = w.cps, ns = w.nslices;
-  const int r1 = lag * cps;
-  const int r2 = r1 + 2 * (ns - lag) * cps;
-  const unsigned long long pol_last = l2_policy_last(), pol_first = l2_policy_first();
-  int t_next = 0;
-  if (lane == 0) t_next = (int)atomicAdd(&wctr[0], 1u);
-  t_next = __shfl_sync(0xffffffffu, t_next, 0);
-  while (true) {
-    const int t = t_next;
-    if (t >= w.n_items) break;
-    if (lane == 0) t_next = (int)atomicAdd(&wctr[0], 1u);  // claim the next item early
-    bool is_b;
-    int slice, chunk;
-    if (t < r1) {
-      is_b = false;
-      slice = t / cps;
-      chunk = t % cps;
-    } else if (t < r2) {
-      const int u = t - r1, r = u % (2 * cps);
-      is_b = r >= cps;
-      slice = lag + u / (2 * cps) - (is_b ? lag : 0);
-      chunk = is_b ? r - cps : r;
-    } else {
-      const int u = t - r2;
-      is_b = true;
-      slice = ns - lag + u / cps;
-      chunk = u % cps;
-    }
-    if (is_b) {  // q_m of slices slice-1 .. slice+1 must be complete
-      if (lane == 0) {
-        const long long t0 = clock64();
-        const int lo = max(slice - 1, 0), hi = min(slice + 1, ns - 1);
-        for (int s = lo; s <= hi; ++s) {
-          while (*(volatile unsigned*)&a_done[s] < (unsigned)cps + w.wait_extra) {
-            if ((*(volatile int*)&ctrl->flags & FLAG_TIMEOUT) || clock64() - t0 > w.spin_limit) {
-              atomicOr(&ctrl->flags, FLAG_TIMEOUT);
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-        __threadfence();
-      }
-      __syncwarp();
-    }
-    double acc = 0.0;
-    const int v0 = chunk * w.chunk_vecs;
-    const int v1 = min(v0 + w.chunk_vecs, svecs);
-    for (int v = v0 + lane; v < v1; v += 32) {
-      const int tv = slice * svecs + v;
-      const int row = tv / vrow;
-      const int ix = (tv - row * vrow) * VEC;
-      const int iy = row % g.ny;
-      const int iz = row / g.ny;
-      const int i = row * g.px + ix;
-      using V = typename VecT<Tq, VEC>::V;
-      Tq out[VEC];
-      if (!is_b) {
-        stencil_vec<Tq, VEC, DIM>(qi, cf, g, i, ix, iy, iz, s1, false, pol_last, out);
-        V vv;
-        Tq* dst = reinterpret_cast<Tq*>(&vv);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) dst[k] = out[k];
-        st_hint(reinterpret_cast<V*>(qm + i), vv, pol_last);
-        if constexpr (sizeof(Tq) == 4) {
-          Tq sq = Tq(0);
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) sq = fmaf(out[k], out[k], sq);
-          acc += (double)sq;
-        } else {
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) acc = fma(out[k], out[k], acc);
-        }
-      } else {
-        stencil_vec<Tq, VEC, DIM>(qm, cf, g, i, ix, iy, iz, s2, true, pol_first, out);
-        Tq own[VEC];
-        {
-          const V vv = __ldcg(reinterpret_cast<const V*>(qm + i));
-          const Tq* s = reinterpret_cast<const Tq*>(&vv);
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) own[k] = s[k];
-        }
-        double p[VEC];
-        ldP<VEC>(p, P + i);
-        Tq sq = Tq(0);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-          p[k] = fma(d1, to_f64(own[k]), p[k]);
-          p[k] = fma(d2, to_f64(out[k]), p[k]);
-          if constexpr (sizeof(Tq) == 4) sq = fmaf(out[k], out[k], sq);
-          else acc = fma(out[k], out[k], acc);
-        }
-        if constexpr (sizeof(Tq) == 4) acc += (double)sq;
-        stP<VEC>(P + i, p);
-        V vv;
-        Tq* dst = reinterpret_cast<Tq*>(&vv);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) dst[k] = out[k];
-        __stcs(reinterpret_cast<V*>(qo + i), vv);
-      }
-    }
-    acc = warp_sum_all(acc);
-    if (!is_b) __threadfence();  // this lane's q_m stores are visible GPU-wide
-    __syncwarp();
-    if (lane == 0) {
-      ipart[t] = acc;
-      __threadfence();
-      unsigned* cnt = is_b ? &b_done[slice] : &a_done[slice];
-      const unsigned prev = atomicAdd(cnt, 1u);
-      if (prev == (unsigned)cps - 1u) {  // last item of this slice and phase
-        __threadfence();
-        double s = 0.0;
-        for (int c = 0; c < cps; ++c) {
-          int it;  // item index of (phase, slice, c)
-          if (!is_b) it = slice < lag ? slice * cps + c : r1 + (slice - lag) * 2 * cps + c;
-          else it = slice < ns - lag ? r1 + slice * 2 * cps + cps + c : r2 + (slice - (ns - lag)) * cps + c;
-          s += __ldcg(ipart + it);
-        }
-        spart[(is_b ? ns : 0) + slice] = s;
-      }
-    }
-    t_next = __shfl_sync(0xffffffffu, t_next, 0);
-  }
-  // leave; the last warp to leave finishes the pass
-  unsigned last = 0;
-  if (lane == 0) {
-    __threadfence();
-    last = atomicAdd(&wctr[1], 1u) == total_warps - 1u;
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (!last) return;
-  __threadfence();
-  double S1 = 0.0, S2 = 0.0;
-  for (int s = lane; s < ns; s += 32) {
-    S1 += __ldcg(spart + s);
-    S2 += __ldcg(spart + ns + s);
-  }
-  S1 = warp_sum_all(S1);
-  S2 = warp_sum_all(S2);
-  for (int s = lane; s < ns; s += 32) {
-    a_done[s] = 0u;
-    b_done[s] = 0u;
-  }
-  if (lane == 0) {
-    wctr[0] = 0u;
-    wctr[1] = 0u;
-    if (ctrl->flags & FLAG_TIMEOUT) {
-      ctrl->done = 1;
-    } else {
-      stop_test(ctrl, m, d1, S1);
-      if (!ctrl->done)
-        stop_test(ctrl, m + 1, d2, S2);
-      else if (ctrl->degree == m)
-        ctrl->overshoot = 1;
-    }
-  }
-}
-
-// P -= d q: removes the extra term of a pair whose first term met the test.
-template <typename Tq>
-__global__ void k_unstep(double* __restrict__ P, const Tq* __restrict__ q, double d, int Np) {
-  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
-    P[i] = fma(-d, to_f64(q[i]), P[i]);
-}
-
 __global__ void k_unpack(const double* __restrict__ src, double* __restrict__ dst, Geo g) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
@@ -2872,69 +2561,6 @@ void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, do
       k_leja_term<double, 2, 2><<<nb, NT, 0, s>>>((const double*)qi, (double*)qo, c->P, cf, g, c->xi_dev,
                                                   c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
   }
-}
-
-WaveGeoHost wave_geometry(const erem_ctx* c, int grid) {
-  WaveGeoHost w;
-  const int vec = c->prec == EREM_FP32_BULK ? 4 : 2;
-  w.nslices = c->dim == 3 ? c->nz : c->ny;
-  w.slice_cells = c->dim == 3 ? c->px * c->ny : c->px;
-  const int svecs = w.slice_cells / vec;
-  w.chunk_vecs = 32 * WAVE_U;  // one warp's item
-  if (w.chunk_vecs > svecs) w.chunk_vecs = svecs;
-  w.cps = (svecs + w.chunk_vecs - 1) / w.chunk_vecs;
-  // slices in flight ~ warps / (2 cps); the lag keeps B clear of them
-  const int warps = grid * (WNT / 32);
-  const int inflight = (warps + 2 * w.cps - 1) / (2 * w.cps);
-  w.lag = 2 + (3 * inflight + 1) / 2;
-  if (w.lag > w.nslices) w.lag = w.nslices;
-  w.n_items = 2 * w.nslices * w.cps;
-  return w;
-}
-
-void launch_leja_pair(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
-  const Geo g = geo_of(c);
-  const WaveGeoHost h = wave_geometry(c, c->wave_grid);
-  WaveGeo w{h.nslices, h.slice_cells, h.cps, h.chunk_vecs, h.lag, h.n_items,
-            c->wave_spin_limit, c->wave_wait_never ? 1u : 0u};
-  int grid = c->wave_grid;
-  if (grid * (WNT / 32) > h.n_items) grid = (h.n_items + WNT / 32 - 1) / (WNT / 32);
-  ++c->launches;
-  if (c->prec == EREM_FP32_BULK) {
-    const LejaCoef<float> cf = leja_coef<float, 4>(c);
-    const float* qi = (const float*)c->q[qin];
-    float* qo = (float*)c->q[qin ^ 1];
-    float* qm = (float*)c->qmid;
-    if (c->dim == 3)
-      k_leja_wave<float, 4, 3><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev, c->dd_dev,
-                                                   cg, m, c->wave_part, c->wave_spart, c->wave_ctr,
-                                                   c->wave_done, c->wave_bdone, c->ctrl);
-    else
-      k_leja_wave<float, 4, 2><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev, c->dd_dev,
-                                                   cg, m, c->wave_part, c->wave_spart, c->wave_ctr,
-                                                   c->wave_done, c->wave_bdone, c->ctrl);
-  } else {
-    const LejaCoef<double> cf = leja_coef<double, 2>(c);
-    const double* qi = (const double*)c->q[qin];
-    double* qo = (double*)c->q[qin ^ 1];
-    double* qm = (double*)c->qmid;
-    if (c->dim == 3)
-      k_leja_wave<double, 2, 3><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev,
-                                                    c->dd_dev, cg, m, c->wave_part, c->wave_spart,
-                                                    c->wave_ctr, c->wave_done, c->wave_bdone, c->ctrl);
-    else
-      k_leja_wave<double, 2, 2><<<grid, WNT, 0, s>>>(qi, qm, qo, c->P, cf, g, w, c->xi_dev,
-                                                    c->dd_dev, cg, m, c->wave_part, c->wave_spart,
-                                                    c->wave_ctr, c->wave_done, c->wave_bdone, c->ctrl);
-  }
-}
-
-void launch_unstep(const erem_ctx* c, int qbuf, double d, cudaStream_t s) {
-  ++c->launches;
-  if (c->prec == EREM_FP32_BULK)
-    k_unstep<float><<<blocks_padded(c), NT, 0, s>>>(c->P, (const float*)c->q[qbuf], d, (int)c->Np);
-  else
-    k_unstep<double><<<blocks_padded(c), NT, 0, s>>>(c->P, (const double*)c->q[qbuf], d, (int)c->Np);
 }
 
 void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,

@@ -326,8 +326,9 @@ def _phi1_with_env(E, case, v, tau, precision, env, opts=None):
 
 
 @pytest.mark.parametrize("degree", [1, 2, 7, 12, 31])
-def test_two_term_passes_with_odd_and_even_degrees(E, degree):
-    # a replayed degree d runs d // 2 two-term passes and one single term when d is odd
+def test_replayed_degrees_from_one_to_a_chunk_and_beyond(E, degree):
+    # a replayed degree runs exactly that many terms, inside one chunk of
+    # launches or across several
     case = C.random_case(3, 19, 13, 11, seed=31)
     v, _ = _phi1_case(case, case.dt)
     prob = case.problem(case.T0)
@@ -339,54 +340,7 @@ def test_two_term_passes_with_odd_and_even_degrees(E, degree):
     assert C.rel_l2(got, ref.value) < FP64_TOL
 
 
-@pytest.mark.parametrize("grid", [1, 3, 7, 64])
-def test_two_term_passes_any_grid_match_single_terms(E, grid):
-    # the two-term wavefront pass gives the same result whatever the number of
-    # persistent blocks (one block walks every item in order; many blocks
-    # overlap A and B items); the single-term path is the comparison
-    case = C.random_case(3, 17, 15, 17, seed=33)
-    v, res = _phi1_case(case, case.dt)
-    for prec, tol in (("fp64", FP64_TOL), ("fp32_bulk", FP32_TOL)):
-        single, st1 = _phi1_with_env(E, case, v, case.dt, prec, {"EREM_LEJA_PAIRS": 0})
-        pair, st2 = _phi1_with_env(E, case, v, case.dt, prec,
-                                   {"EREM_LEJA_PAIRS": 1, "EREM_WAVE_GRID": grid})
-        assert C.rel_l2(pair, res.value) < tol and C.rel_l2(single, res.value) < tol
-        if prec == "fp64":
-            assert st1.schedule == st2.schedule == res.schedule
-
-
-def test_two_term_wait_that_runs_out_returns_timeout(E):
-    # every wait of the two-term pass targets a count nothing reaches: each
-    # gives up at its clock limit, the call reports EREM_ETIMEOUT and leaves
-    # its output as it was, and the device stays usable (a fresh context then
-    # computes the oracle's value)
-    import os
-
-    case = C.random_case(3, 17, 15, 17, seed=33)
-    v, res = _phi1_case(case, case.dt)
-    env = {"EREM_LEJA_PAIRS": "1", "EREM_WAVE_WAIT_NEVER": "1", "EREM_WAVE_SPIN_LIMIT": "200000"}
-    old = {k_: os.environ.get(k_) for k_ in env}
-    os.environ.update(env)
-    try:
-        with _ctx(E, case, "fp64") as ctx:
-            ctx.set_state(_t(case.T0), _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam), case.dt)
-            out = _t(np.full(case.n, 7.0))
-            with pytest.raises(E.EremError) as ei:
-                ctx.phi1_apply(_t(v), out, E.leja_opts(replay=[1, 6]))
-            assert ei.value.status == E.EREM_ETIMEOUT
-            assert np.all(out.cpu().numpy() == 7.0)
-    finally:
-        for k_, val in old.items():
-            if val is None:
-                os.environ.pop(k_, None)
-            else:
-                os.environ[k_] = val
-    got, st = _phi1_with_env(E, case, v, case.dt, "fp64", {"EREM_LEJA_PAIRS": 1})
-    assert st.schedule == res.schedule
-    assert C.rel_l2(got, res.value) < FP64_TOL
-
-
-def test_stop_inside_a_pair_removes_the_extra_term(E):
+def test_free_running_degrees_of_both_parities(E):
     # free-running degrees of both parities on several seeds: the result must
     # equal the oracle's at its own degree
     parities = set()
