@@ -42,8 +42,22 @@ if ROOT not in sys.path:
 METRIC = "EREM Mcell-steps/s at 256³ FP32-bulk vs FP64 at ≤1e-5 rel err; HBM GB/s vs peak"
 UNIT = "Mcell-steps/s"
 # algorithmic bytes per cell of one Leja term (3D): 7 coefficients, q read,
-# q written, P read and written (FP64)
+# q written, P read and written (FP64).  The running sum is updated at odd m
+# only (both products of a pair are in registers then): odd terms move these
+# bytes, even terms 16 fewer.
 BYTES_PER_CELL_TERM = {"fp32_bulk": 7 * 4 + 4 + 4 + 16, "fp64": 7 * 8 + 8 + 8 + 16}
+P_BYTES = 16
+
+
+def term_bytes_per_cell(full_bytes: int, degrees) -> float:
+    """Algorithmic bytes per cell of all Leja terms of substeps with these
+    degrees: the odd terms (which update P) move full_bytes, the even ones
+    full_bytes - 16."""
+    total = 0
+    for m in degrees:
+        odd = (m + 1) // 2
+        total += odd * full_bytes + (m - odd) * (full_bytes - P_BYTES)
+    return float(total)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -58,6 +72,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-krylov", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the FP64 oracle's full-size first step (about a minute on the host)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the coupled 1024^2, ensemble and adjoint sub-objects of the default line")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--slab", type=int, default=16, help="z planes of the oracle's sample")
     ap.add_argument("--workload", choices=["channels3d", "coupled2d", "ensemble", "adjoint"],
@@ -180,11 +198,11 @@ def measured_peaks():
 
 def kernel_sources_sha():
     """Hash of the source the Leja term kernel is built from: the shared
-    device helpers and the k_leja_term definition itself."""
+    device helpers and the k_leja_term body and entry points."""
     csrc = os.path.join(ROOT, "paper_1209_5553_gb300", "csrc")
     kern = open(os.path.join(csrc, "kernels.cu")).read()
-    start = kern.index("k_leja_term(const Tq* __restrict__ qi")
-    end = kern.index("\n}\n", start)
+    start = kern.index("__device__ __forceinline__ void leja_term_body(")
+    end = kern.index("\n}\n", kern.index("k_leja_term1(const Tq* __restrict__ qi", start))
     h = hashlib.sha256()
     h.update(open(os.path.join(csrc, "device_common.cuh"), "rb").read())
     h.update(kern[start:end].encode())
@@ -249,11 +267,16 @@ def gpu_context(E, torch, wl, precision, dev):
                     "rhoc": rc, "head_left": head}
 
 
-def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=False, points="exact"):
+def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=False, points="exact",
+            capture_first=False):
     ctx, T, info = gpu_context(E, torch, wl, precision, dev)
     ctx.set_leja_points(points)
     opts = E.leja_opts(tol=wl.tol, time_terms=True)
     stream = torch.cuda.current_stream()
+    first = None
+    if capture_first:  # the first step from T^0, untimed, for the oracle check
+        st = ctx.erem_step(T, wl.dt, opts=opts)
+        first = {"T": T.cpu().numpy(), "schedule": st.schedule}
     for _ in range(warmup):
         ctx.erem_step(T, wl.dt, opts=opts)
     torch.cuda.synchronize()
@@ -279,7 +302,7 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
     barrier(world)
     out = {"ms": ms, "degrees": degrees, "t_terms_ms": t_terms, "n_terms": n_terms,
            "n_leja": n_leja, "launches": launches, "T": T.cpu().numpy(), "clocks": clocks, "info": info,
-           "alpha": st.alpha, "beta": st.beta}
+           "alpha": st.alpha, "beta": st.beta, "first": first}
     ctx.close()
     return out
 
@@ -362,17 +385,18 @@ def run_e2e(E, torch, wl, steps, warmup, dev):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample: a 16-plane z slab holding channels
+# CPU oracle: z slabs of the workload (each an independent problem with its
+# own pressure solve and velocity scaling) and the full-size first step
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, nz_s):
+def oracle_slab(wl, z0, nz_s):
+    """The oracle's heat problem on planes z0 .. z0+nz_s-1 of the workload
+    (the whole workload when nz_s = nz): its own pressure (Jacobi CG from the
+    linear head, where the channel family's head is exact), velocity scaled
+    to a largest face speed of 1, (rho c) for the Peclet number."""
     from oracle import fv, timestep as ts
     import workloads as W
 
     n = wl.nx
-    lnk = wl.lnk.reshape(wl.nz, wl.ny, wl.nx)
-    chan = np.isclose(lnk, np.log(1e4)).sum(axis=(1, 2))
-    starts = list(range(0, wl.nz - nz_s + 1, nz_s))
-    z0 = max(starts, key=lambda z: chan[z:z + nz_s].sum())
     sl = slice(z0, z0 + nz_s)
     f = lambda a: np.ascontiguousarray(a.reshape(wl.nz, wl.ny, wl.nx)[sl]).reshape(-1)
     g = fv.Grid(3, n, wl.ny, nz_s, 1.0, 1.0, nz_s / wl.nz)
@@ -385,14 +409,114 @@ def oracle_sample(wl, nz_s):
     rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), 1.0)
     phys = fv.Physics(rc, rc, wl.head_drop / vmax, 0.0, wl.T_inflow, 0)
     prob = ts.heat_problem(g, phys, slnk, f(wl.phi), f(wl.lam), p / vmax)
-    return prob, f(wl.T0), g.n, f"z-slab {n}x{wl.ny}x{nz_s} (planes {z0}..{z0 + nz_s - 1}) of the {wl.nx}^3 workload"
+    return prob, f(wl.T0), g.n
+
+
+def _oracle_slab_worker(n, z0, nz_s, steps, warmup, barrier, queue):
+    """One process of the all-core baseline: set up its slab, wait for the
+    others, then time `steps` oracle EREM steps."""
+    try:
+        from oracle import timestep as ts
+        from oracle.leja import LejaOptions
+
+        wl = make_workload(n)
+        prob, T, ncell = oracle_slab(wl, z0, nz_s)
+        opts = LejaOptions(tol_a=wl.tol, tol_r=wl.tol)
+        for _ in range(warmup):
+            T, _ = ts.erem_step(prob, T, wl.dt, opts)
+        barrier.wait(timeout=1800)
+        t = time.perf_counter()
+        for _ in range(steps):
+            T, _ = ts.erem_step(prob, T, wl.dt, opts)
+        queue.put((z0, ncell, time.perf_counter() - t, None))
+    except Exception as e:  # noqa: BLE001 -- reported to the parent
+        barrier.abort()
+        queue.put((z0, 0, 0.0, repr(e)))
+
+
+def host_info():
+    """Host cores, CPU model and architecture of the machine the oracle runs on."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    try:
+        nproc = len(os.sched_getaffinity(0))
+    except AttributeError:
+        nproc = os.cpu_count() or 1
+    return {"nproc": nproc, "cpu_model": model or platform.processor() or "unknown",
+            "arch": platform.machine()}
+
+
+def time_oracle_all_cores(wl, steps, warmup=0, workers=None):
+    """The oracle as it stands (numpy/scipy, one thread per process) on all
+    host cores: one spawned process per z slab of the workload, every slab an
+    independent problem; the processes set up, meet at a barrier and time
+    their steps together.  Returns (Mcell-steps/s summed over the slabs, wall
+    seconds of the slowest, processes, description)."""
+    import multiprocessing as mp
+
+    host = host_info()
+    workers = workers or max(1, min(host["nproc"], wl.nz // 4))
+    nz_s = wl.nz // workers
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"  # inherited by the spawned processes: one thread each
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_slab_worker,
+                         args=(wl.nx, k * nz_s, nz_s, steps, warmup, barrier, queue))
+             for k in range(workers)]
+    try:
+        for p in procs:
+            p.start()
+        res = [queue.get(timeout=3600) for _ in procs]
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    errs = [r[3] for r in res if r[3]]
+    if errs:
+        raise RuntimeError(f"oracle worker failed: {errs[0]}")
+    sec = max(r[2] for r in res)
+    cells = sum(r[1] for r in res)
+    desc = (f"{workers} concurrent processes, one per z-slab {wl.nx}x{wl.ny}x{nz_s} of the "
+            f"{wl.nx}^3 workload (planes 0..{workers * nz_s - 1}; each slab its own problem)")
+    return cells * steps / sec / 1e6, sec, workers, desc
 
 
 def time_oracle(wl, nz_s, steps, warmup=0):
+    """The oracle on one host thread: `steps` EREM steps on the 16-plane
+    slab of the workload that holds the most channels."""
     from oracle import timestep as ts
     from oracle.leja import LejaOptions
 
-    prob, T, ncell, desc = oracle_sample(wl, nz_s)
+    lnk = wl.lnk.reshape(wl.nz, wl.ny, wl.nx)
+    chan = np.isclose(lnk, np.log(1e4)).sum(axis=(1, 2))
+    z0 = max(range(0, wl.nz - nz_s + 1, nz_s), key=lambda z: chan[z:z + nz_s].sum())
+    prob, T, ncell = oracle_slab(wl, z0, nz_s)
     opts = LejaOptions(tol_a=wl.tol, tol_r=wl.tol)
     for _ in range(warmup):
         T, _ = ts.erem_step(prob, T, wl.dt, opts)
@@ -400,12 +524,31 @@ def time_oracle(wl, nz_s, steps, warmup=0):
     for _ in range(steps):
         T, _ = ts.erem_step(prob, T, wl.dt, opts)
     sec = time.perf_counter() - t
+    desc = f"z-slab {wl.nx}x{wl.ny}x{nz_s} (planes {z0}..{z0 + nz_s - 1}) of the {wl.nx}^3 workload"
     return ncell * steps / sec / 1e6, sec, ncell, desc
 
 
-def oracle_threads():
-    # numpy elementwise work and scipy's sparse products run on one thread
-    return 1
+def oracle_check(wl, firsts):
+    """Relative L2 errors of the GPU's first steps from T^0 against one
+    oracle EREM step of the whole workload (FP64, same inputs): on the state
+    T^1 and on the increment T^1 - T^0 the step computed."""
+    from oracle import timestep as ts
+    from oracle.leja import LejaOptions
+
+    t = time.perf_counter()
+    prob, T0, _ = oracle_slab(wl, 0, wl.nz)
+    T1, res = ts.erem_step(prob, T0, wl.dt, LejaOptions(tol_a=wl.tol, tol_r=wl.tol))
+    sec = time.perf_counter() - t
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out = {"oracle_schedule": res.schedule, "oracle_s": sec,
+           "what": "one step from T^0 of the full workload; relative L2 of the state T^1 and of "
+                   "the increment T^1 - T^0 against the FP64 oracle"}
+    for key, f in firsts.items():
+        if f is None:
+            continue
+        out[key] = {"rel_l2_state": rel(f["T"], T1), "rel_l2_increment": rel(f["T"] - T0, T1 - T0),
+                    "schedule": f["schedule"]}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -414,15 +557,16 @@ def main_reference(args):
     if world > 1 and rank != 0:
         return
     wl = make_workload(args.n)
-    value, sec, ncell, desc = time_oracle(wl, args.slab, args.steps, args.warmup)
+    value, sec, workers, desc = time_oracle_all_cores(wl, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sec / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"channels3d_{args.n}", "sample": desc, "dt": wl.dt, "tol": wl.tol},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                         "sample": f"{args.steps} oracle EREM steps on the {desc}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": f"{args.steps} oracle EREM steps in each of {desc}",
+                         "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -441,14 +585,17 @@ def main(args):
     N = wl.n
     K, Wu = args.steps, args.warmup
 
-    r32 = run_gpu(E, torch, wl, "fp32_bulk", K, Wu, dev, world, sample_clocks=(rank == 0))
+    check = rank == 0 and world == 1 and not args.no_oracle_check
+    r32 = run_gpu(E, torch, wl, "fp32_bulk", K, Wu, dev, world, sample_clocks=(rank == 0),
+                  capture_first=check)
     ms, value = aggregate(r32["ms"], N, K, world, dev)
     peak, peak_kind = measured_peaks()
     b32 = BYTES_PER_CELL_TERM["fp32_bulk"]
-    # one Leja term must move the coefficients once, q in and out, and P in
-    # and out: 52 B per cell
+    # a Leja term moves the coefficients once and q in and out; the odd terms
+    # also read and write P: 52 B per cell for odd m, 36 B for even m
     sec_leja = r32["t_terms_ms"] / 1e3
-    achieved = b32 * N * r32["n_leja"] / sec_leja / 1e9 if r32["n_leja"] else None
+    bpc = term_bytes_per_cell(b32, [m for s in r32["degrees"] for m in s[1:]])
+    achieved = bpc * N / sec_leja / 1e9 if r32["n_leja"] else None
     effective = b32 * N * r32["n_terms"] / sec_leja / 1e9 if r32["n_terms"] else None
     traffic = recorded_traffic("fp32_bulk", N)
     line = {
@@ -470,21 +617,23 @@ def main(args):
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
-                     "algorithmic_bytes_per_cell_per_launch": b32,
+                     "algorithmic_bytes_per_cell_per_launch": bpc / max(r32["n_leja"], 1),
+                     "algorithmic_bytes_per_cell": {"odd_terms": b32, "even_terms": b32 - P_BYTES},
                      "launch_ms_avg": r32["t_terms_ms"] / max(r32["n_leja"], 1),
-                     "terms_per_launch": r32["n_terms"] / max(r32["n_leja"], 1),
-                     "effective_gbs_per_term": effective,
+                     "effective_gbs_at_52_bytes_per_term": effective,
                      "term_ms_avg": r32["t_terms_ms"] / max(r32["n_terms"], 1)},
         "setup": r32["info"],
     }
     if not args.no_fp64:
-        r64 = run_gpu(E, torch, wl, "fp64", K, Wu, dev, world)
+        r64 = run_gpu(E, torch, wl, "fp64", K, Wu, dev, world, capture_first=check)
         ms64, value64 = aggregate(r64["ms"], N, K, world, dev)
         b64 = BYTES_PER_CELL_TERM["fp64"]
-        ach64 = b64 * N * r64["n_leja"] / (r64["t_terms_ms"] / 1e3) / 1e9 if r64["n_leja"] else None
+        bpc64 = term_bytes_per_cell(b64, [m for s in r64["degrees"] for m in s[1:]])
+        ach64 = bpc64 * N / (r64["t_terms_ms"] / 1e3) / 1e9 if r64["n_leja"] else None
         rel = float(np.linalg.norm(r32["T"] - r64["T"]) / np.linalg.norm(r64["T"]))
         line["fp64"] = {"value": value64, "ms_per_step": ms64 / K,
-                        "achieved_gbs": ach64, "algorithmic_bytes_per_cell_per_launch": b64,
+                        "achieved_gbs": ach64,
+                        "algorithmic_bytes_per_cell_per_launch": bpc64 / max(r64["n_leja"], 1),
                         "term_ms_avg": r64["t_terms_ms"] / max(r64["n_terms"], 1),
                         "degrees_per_step": [s[1:] if s[0] == 1 else s for s in r64["degrees"]]}
         line["speedup_fp32_bulk_vs_fp64"] = ms64 / ms
@@ -516,11 +665,25 @@ def main(args):
         sec = max_over_ranks(sec, world, dev)
         line["e2e"] = {"value": world * N * K / sec / 1e6, "unit": UNIT,
                        "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
+    if not args.no_extra:
+        # the other workloads, each with its own value, step time, dominant
+        # kernel's roofline and FP32-bulk/FP64 ratio
+        line["coupled2d"] = coupled_summary(E, torch, dev, world, K, Wu)
+        line["ensemble"] = ensemble_summary(E, torch, dev, world, Wu)
+        line["adjoint"] = adjoint_summary(E, torch, dev, world)
+    if check:
+        line["rel_l2_vs_oracle"] = oracle_check(wl, {
+            "fp32_bulk": r32["first"], "fp64": r64["first"] if not args.no_fp64 else None})
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, sec, ncell, desc = time_oracle(wl, args.slab, args.cpu_steps)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                                "sample": f"{args.cpu_steps} oracle EREM steps on the {desc} "
-                                          f"({sec:.1f} s)"}
+        v, sec, workers, desc = time_oracle_all_cores(wl, args.cpu_steps)
+        v1, sec1, _, desc1 = time_oracle(wl, args.slab, args.cpu_steps)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
+                                "sample": f"{args.cpu_steps} oracle EREM steps in each of {desc} "
+                                          f"({sec:.1f} s); the rate is summed over the processes",
+                                "host": host_info(),
+                                "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"{args.cpu_steps} oracle EREM steps on the "
+                                                            f"{desc1} ({sec1:.1f} s)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -572,22 +735,67 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    cg_it, lin_it, degrees, launches = [], [], [], 0
+    cg_it, lin_it, degrees, launches, t_terms, n_terms, scheds = [], [], [], 0, 0.0, 0, []
     e0.record(stream)
     for _ in range(steps):
         s1, s2 = step()
         cg_it.append(s1.lin_iters)
         lin_it.append(s2.lin_iters)
         degrees.append(s2.degree_total)
+        scheds.append(list(s2.degrees[:s2.substeps]))
         launches += s1.launches + s2.launches
+        t_terms += s2.t_terms_ms
+        n_terms += s2.n_terms_timed
     e1.record(stream)
     torch.cuda.synchronize()
     out = {"ms": e0.elapsed_time(e1), "cg_iters_per_step": float(np.mean(cg_it)),
            "stage_iters_per_step": float(np.mean(lin_it)),
            "leja_terms_per_step": float(np.mean(degrees)), "launches": launches,
-           "T": T.cpu().numpy(), "rhoc": rc}
+           "T": T.cpu().numpy(), "rhoc": rc, "t_terms_ms": t_terms, "n_terms": n_terms,
+           "degrees": [m for sc in scheds for m in sc]}
     ctx.close()
     return out
+
+
+def coupled_summary(E, torch, dev, world, K, Wu):
+    """The 1024^2 coupled workload for the default line: EREM FP32-bulk and
+    FP64 and ROS2 (FP64), K steps each after Wu warm-up steps."""
+    import workloads as W
+
+    wl = W.coupled2d(1024)
+    runs = {}
+    for key, scheme, prec in (("erem_fp32_bulk", "erem", "fp32_bulk"), ("erem_fp64", "erem", "fp64"),
+                              ("ros2_fp64", "ros2", "fp64")):
+        r = run_coupled(E, torch, wl, scheme, prec, K, Wu, dev)
+        ms, value = aggregate(r["ms"], wl.n, K, world, dev)
+        r.update(ms=ms, value=value)
+        runs[key] = r
+    h, d, q = runs["erem_fp32_bulk"], runs["erem_fp64"], runs["ros2_fp64"]
+    peak, kind = measured_peaks()
+    b = ENS_BYTES_PER_CELL_TERM["fp32_bulk"]  # 2D: 5 coefficients, q in/out, P in/out
+    bpc = term_bytes_per_cell(b, h["degrees"])
+    ach = bpc * wl.n / (h["t_terms_ms"] / 1e3) / 1e9 if h["n_terms"] else None
+    rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
+    return {
+        "workload": "coupled2d_1024", "cells": wl.n, "steps": K, "warmup": Wu, "unit": UNIT,
+        "value": h["value"], "ms_per_step": h["ms"] / K,
+        "what": "per step: steady FP64 pressure CG at T^n (multigrid-preconditioned, to 1e-10), "
+                "then one heat step with the T-dependent fluid laws",
+        "leja_terms_per_step": h["leja_terms_per_step"], "cg_iters_per_step": h["cg_iters_per_step"],
+        "fp64": {"value": d["value"], "ms_per_step": d["ms"] / K},
+        "speedup_fp32_bulk_vs_fp64": d["ms"] / h["ms"],
+        "rel_l2_fp32_bulk_vs_fp64": rel(h["T"], d["T"]),
+        "ros2_fp64": {"value": q["value"], "ms_per_step": q["ms"] / K,
+                      "stage_iters_per_step": q["stage_iters_per_step"],
+                      "rel_l2_vs_erem_fp64": rel(q["T"], d["T"])},
+        "roofline": {"kernel": "k_leja_term<float,4,2>", "bound": "hbm", "achieved": ach, "peak": peak,
+                     "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,
+                     "peak_source": f"{kind} hbm_gbs",
+                     "algorithmic_bytes_per_cell": {"odd_terms": b, "even_terms": b - P_BYTES},
+                     "term_ms_avg": h["t_terms_ms"] / max(h["n_terms"], 1),
+                     "note": "the 1024^2 term's working set (about 50 MB) stays in L2, so the "
+                             "achieved rate is not an HBM figure"},
+    }
 
 
 def main_coupled(args):
@@ -753,6 +961,44 @@ def time_oracle_ensemble(members, n_sample):
     return cells / sec / 1e6, sec, desc
 
 
+def ensemble_summary(E, torch, dev, world, Wu, members=512, steps=30):
+    """The 512-member ensemble for the default line: one graph launch of the
+    workload's 30 EREM steps per precision, after Wu warm-up steps."""
+    t_in = time.perf_counter()
+    inputs, _ = ensemble_inputs(E, torch, dev, members)
+    t_in = time.perf_counter() - t_in
+    cells = sum(wl.n for wl, _, _ in inputs)
+    peak, kind = measured_peaks()
+    out = {"workload": f"ensemble2d_{members}", "members": members, "cells": cells, "steps": steps,
+           "warmup": Wu, "unit": UNIT, "inputs_s": t_in}
+    Ts = {}
+    for prec in ("fp32_bulk", "fp64"):
+        r = run_ensemble(E, torch, inputs, prec, steps, Wu, dev)
+        ms, value = aggregate(r["ms"], cells, steps, world, dev)
+        b = ENS_BYTES_PER_CELL_TERM[prec]
+        ach = b * r["cell_terms"] / (r["run_ms"] / 1e3) / 1e9
+        Ts[prec] = r["T"]
+        summary = {"value": value, "ms_per_step": ms / steps, "iterations": r["iterations"],
+                   "tile_vecs": r["tile_vecs"], "autotune_s": r["tune_s"],
+                   "terms_per_member_run": {"median": float(np.median(r["terms"])),
+                                            "max": int(max(r["terms"]))}}
+        if prec == "fp32_bulk":
+            out.update(summary)
+            out["roofline"] = {"kernel": f"k_ens_iter<float,4,{r['tile_vecs']}>", "bound": "hbm",
+                               "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                               "traffic": None, "peak_source": f"{kind} hbm_gbs",
+                               "algorithmic_bytes_per_cell_term": b,
+                               "note": "Leja-term bytes only over the whole run: a lower bound"}
+        else:
+            out["fp64"] = summary
+            out["speedup_fp32_bulk_vs_fp64"] = summary["ms_per_step"] / out["ms_per_step"]
+        r["ens"].close()
+    num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(Ts["fp32_bulk"], Ts["fp64"]))
+    den = sum(float(np.sum(b ** 2)) for b in Ts["fp64"])
+    out["rel_l2_fp32_bulk_vs_fp64"] = float(np.sqrt(num / den))
+    return out
+
+
 def main_ensemble(args):
     import torch
 
@@ -823,8 +1069,8 @@ def main_ensemble(args):
     r32["ens"].close()
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sec, desc = time_oracle_ensemble(args.members, args.cpu_steps)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                                "sample": f"{desc} ({sec:.1f} s)"}
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{desc} ({sec:.1f} s)", "host": host_info()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -833,18 +1079,9 @@ def main_ensemble(args):
 # the adjoint workload: 128^3 channels, 60 steps, gradient of a 16-cell misfit
 # with respect to ln K and T0 (forward + checkpointed adjoint, FP32-bulk)
 # ---------------------------------------------------------------------------
-def main_adjoint(args):
-    import torch
-
-    import paper_1209_5553_gb300 as E
+def adjoint_setup(E, torch, dev, n):
     import workloads as W
-    from paper_1209_5553_gb300.autograd import MisfitModel, misfit
 
-    rank, world, local = dist_info()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    dist_init(world, "nccl")
-    n = 128 if args.n == 256 else args.n
     wl, obs, data = W.adjoint3d(n)
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     # heads for a largest face speed of 1 and (rho c) for Pe 1e3, from a GPU pressure solve
@@ -853,11 +1090,16 @@ def main_adjoint(args):
                                 tol=1e-10, maxit=200000)
     rc = W.rhoc_for_peclet(wl.peclet, float(wl.lam[0]), 1.0)
     phys = E.Physics(rc, rc, wl.head_drop / st.vmax, 0.0, wl.T_inflow, 0)
-    K, Wu = args.steps, args.warmup
+    return wl, obs, data, phys, t
+
+
+def adjoint_runs(E, torch, dev, n, K, Wu, arms):
+    """K gradient evaluations (after Wu) of the misfit for each (precision,
+    tape) arm; returns the workload and per-arm results."""
+    from paper_1209_5553_gb300.autograd import MisfitModel, misfit
+
+    wl, obs, data, phys, t = adjoint_setup(E, torch, dev, n)
     runs = {}
-    arms = [("fp32_bulk", "segment"), ("fp32_bulk", "full")]
-    if not args.no_fp64:
-        arms.append(("fp64", "segment"))
     for prec, tape in arms:
         m = MisfitModel(3, n, n, n, phys, t(wl.phi), t(wl.lam), wl.dt, wl.steps, t(obs, torch.int64),
                         t(data), precision=prec, checkpoint=10, tape=tape)
@@ -882,9 +1124,82 @@ def main_adjoint(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / K
         terms = sum(s[0] and sum(s[1:]) for s in m.schedules)
-        runs[prec if tape == "segment" else prec + "_full_tape"] = {"ms_per_gradient": ms, "L": float(L), "glnk": gl.cpu().numpy(),
-                      "gT0": gt.cpu().numpy(), "leja_terms_per_run": terms}
+        runs[prec if tape == "segment" else prec + "_full_tape"] = {
+            "ms_per_gradient": ms, "L": float(L), "glnk": gl.cpu().numpy(), "gT0": gt.cpu().numpy(),
+            "leja_terms_per_run": terms}
         m.close()
+    return wl, obs, phys, t, runs
+
+
+def adjoint_forward_terms(E, torch, wl, phys, t):
+    """The forward run's Leja terms timed on their launching stream: the
+    adjoint workload's dominant kernel (k_leja_term<float,4,3> at 128^3)."""
+    n = wl.nx
+    with E.Context(3, n, n, n, physics=phys, precision="fp32_bulk") as ctx:
+        lnk = t(wl.lnk)
+        p = t(linear_head(wl.n, wl.nx, phys.head_left, 0.0))
+        ctx.pressure_solve(lnk, None, p, tol=1e-12, maxit=200000)
+        T = t(wl.T0)
+        ctx.set_state(T, p, lnk, t(wl.phi), t(wl.lam), wl.dt)
+        opts = E.leja_opts(tol=wl.tol, time_terms=True)
+        ms, terms, degrees = 0.0, 0, []
+        for _ in range(wl.steps):
+            st = ctx.erem_step(T, wl.dt, opts=opts)
+            ms += st.t_terms_ms
+            terms += st.n_terms_timed
+            degrees += list(st.degrees[:st.substeps])
+    return ms, terms, degrees
+
+
+def adjoint_summary(E, torch, dev, world, n=128, K=2, Wu=1):
+    """The 128^3 adjoint for the default line: FP32-bulk checkpointed, with
+    the full tape, and FP64, K gradients each after Wu."""
+    wl, obs, phys, t, runs = adjoint_runs(E, torch, dev, n, K, Wu,
+                                          [("fp32_bulk", "segment"), ("fp32_bulk", "full"),
+                                           ("fp64", "segment")])
+    r, f, q = runs["fp32_bulk"], runs["fp32_bulk_full_tape"], runs["fp64"]
+    ms = max_over_ranks(r["ms_per_gradient"], world, dev)
+    peak, kind = measured_peaks()
+    tms, terms, degrees = adjoint_forward_terms(E, torch, wl, phys, t)
+    b = BYTES_PER_CELL_TERM["fp32_bulk"]
+    ach = term_bytes_per_cell(b, degrees) * wl.n / (tms / 1e3) / 1e9 if terms else None
+    rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
+    return {
+        "workload": f"adjoint3d_{n}", "cells": wl.n, "erem_steps": wl.steps, "gradients": K,
+        "warmup": Wu, "unit": UNIT, "what": "one gradient = forward run + checkpointed adjoint",
+        "value": world * wl.n * wl.steps / (ms / 1e3) / 1e6, "ms_per_gradient": ms,
+        "full_tape_ms_per_gradient": f["ms_per_gradient"],
+        "fp64": {"ms_per_gradient": q["ms_per_gradient"]},
+        "speedup_fp32_bulk_vs_fp64": q["ms_per_gradient"] / r["ms_per_gradient"],
+        "rel_l2_glnk_fp32_bulk_vs_fp64": rel(r["glnk"], q["glnk"]),
+        "rel_l2_gT0_fp32_bulk_vs_fp64": rel(r["gT0"], q["gT0"]),
+        "rel_l2_glnk_full_tape_vs_checkpointed": rel(f["glnk"], r["glnk"]),
+        "leja_terms_per_forward": r["leja_terms_per_run"],
+        "roofline": {"kernel": "k_leja_term<float,4,3>", "bound": "hbm", "achieved": ach, "peak": peak,
+                     "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,
+                     "peak_source": f"{kind} hbm_gbs",
+                     "algorithmic_bytes_per_cell": {"odd_terms": b, "even_terms": b - P_BYTES},
+                     "term_ms_avg": tms / max(terms, 1),
+                     "note": "timed over a 60-step forward run; a 128^3 term moves 109 MB, "
+                             "partly served by the 129 MB L2"},
+    }
+
+
+def main_adjoint(args):
+    import torch
+
+    import paper_1209_5553_gb300 as E
+
+    rank, world, local = dist_info()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist_init(world, "nccl")
+    n = 128 if args.n == 256 else args.n
+    K, Wu = args.steps, args.warmup
+    arms = [("fp32_bulk", "segment"), ("fp32_bulk", "full")]
+    if not args.no_fp64:
+        arms.append(("fp64", "segment"))
+    wl, obs, _, _, runs = adjoint_runs(E, torch, dev, n, K, Wu, arms)
     r = runs["fp32_bulk"]
     cell_steps = wl.n * wl.steps
     line = {

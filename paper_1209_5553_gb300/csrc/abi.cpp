@@ -439,18 +439,21 @@ struct TermTiming {
 // fused_T), P = sum_m d_m q_m, the terms launched in chunks and stopped by
 // the device test (StopParams sp) or at the forced degree.  *degree gets m;
 // *failed is set when m_max terms do not meet the test, *nonfinite when the
-// estimate left the range of the Leja precision.
+// estimate left the range of the Leja precision.  The term kernel adds the
+// products d_m q_m to P in pairs (at odd m): when the degree is even, the
+// last one is still to be added.  With fix, the caller's consumer of P adds
+// it (fix->q = q_M, or null when P is complete); without, it is added here.
 erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int S, int phi,
                         int* M_avail, int mcap, const StopParams& sp, int forced, const Opts& o,
                         TermTiming* tt, int* degree, bool* failed, bool* nonfinite,
-                        cudaStream_t s) {
+                        cudaStream_t s, PFixHost* fix = nullptr) {
   const double cg = c->cfoc / c->gam;  // the same for every substep level
-  const double d0 = dd_entry(c, S, phi).d[0];
   *failed = *nonfinite = false;
+  if (fix) *fix = PFixHost{};
   if (fused_T)  // also writes vrhs = G(T)
-    launch_step_init(c, fused_T, d0, sp, s);
+    launch_step_init(c, fused_T, sp, s);
   else
-    launch_leja_init(c, u, d0, sp, s);
+    launch_leja_init(c, u, sp, s);
   // taping (phi_1 of erem_step): the terms write q_m straight into the tape,
   // slot m of this interpolation, when the arena has room for every term
   const size_t qbytes = (size_t)c->Np * (c->prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double));
@@ -531,6 +534,11 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     }
   }
   c->last_degree = *degree;
+  if (*degree % 2 == 0) {  // q_M: the tape slot, or the ping-pong buffer of m's parity
+    const void* qM = slot0 ? (const void*)(slot0 + (size_t)*degree * qbytes) : c->q[*degree & 1];
+    if (fix) *fix = PFixHost{qM, *degree};
+    else launch_pfix(c, qM, *degree, s);
+  }
   if (slot0) c->tape_used += ((size_t)*degree + 1) * qbytes;
   return EREM_OK;
 }
@@ -566,6 +574,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
   bool nonfinite_attempt = false;  // the last failed attempt had a non-finite estimate
   int degrees[64];
   TermTiming tt;
+  PFixHost fix;  // the last product of the substep just interpolated, if P lacks it
   if (o.time_terms) EREM_TRY(ensure_events(c, mcap + 1));
   for (int a = a0; a < n_attempts; ++a) {
     const int S = replay ? o.replay[0] : (1 << a);
@@ -594,7 +603,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       int degree = 0;
       bool failed = false, nonfinite = false;
       EREM_TRY(leja_interp(c, u, (fused_T && a == a0 && k == 0) ? fused_T : nullptr, S, 1, &M_avail,
-                           mcap, sp, forced, o, &tt, &degree, &failed, &nonfinite, s));
+                           mcap, sp, forced, o, &tt, &degree, &failed, &nonfinite, s, &fix));
       if (failed) {
         nonfinite_attempt = nonfinite;
         ok = false;
@@ -603,7 +612,7 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       degrees[k] = degree;
       if (st) st->err_est = c->ctrl_h->err;
       if (k + 1 < S) {
-        launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s);
+        launch_axpy(c, c->w, c->P, delta, k == 0 ? 1 : 0, s, &fix);
         if (c->rec_ok) {  // the start of substep k+1 for the adjoint
           const size_t wb = (size_t)c->Np * sizeof(double);
           if (c->tape_used + wb <= c->tape_cap) {
@@ -635,10 +644,10 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
     // fused start: T^n is the caller's array itself, updated in place; a host
     // T (c->zc_out) is written once from T^n in Tn, where the fused kernel read it
     if (c->zc_out)
-      launch_finish(c, c->zc_out, c->Tn, S > 1 ? c->w : nullptr, c->P, delta, s, 0);
+      launch_finish(c, c->zc_out, c->Tn, S > 1 ? c->w : nullptr, c->P, delta, s, 0, &fix);
     else
       launch_finish(c, out, fused_T ? nullptr : base, S > 1 ? c->w : nullptr, c->P, delta, s,
-                    fused_T ? 1 : 0);
+                    fused_T ? 1 : 0, &fix);
     EREM_TRY(check_launch(c, "finish"));
     if (st) {
       st->substeps = S;
@@ -783,7 +792,8 @@ erem_status load_fields(erem_ctx* c, const double* p, const double* lnk, const d
 // divided differences and the adjoint's transposed copy are stale after it.
 erem_status rescale_jl(erem_ctx* c, cudaStream_t s) {
   c->jlT_valid = false;
-  launch_scale_jl(c, c->dt / c->gam, s);
+  c->jl_sc = c->dt / c->gam;
+  launch_scale_jl(c, c->jl_sc, s);
   EREM_TRY(check_launch(c, "scale"));
   c->jl_valid = true;
   c->dd_cache.clear();
@@ -1266,6 +1276,7 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   const int nc = g.dim == 3 ? 7 : 5;
   for (int k = 0; k < nc; ++k) A(&c->jc[k], np);
   if (st == EREM_OK) st = dalloc(c, &c->jl_all, (np + 128) / 128 * 128 * nc * esz);
+  if (st == EREM_OK && prec == EREM_FP32_BULK) st = dalloc(c, (void**)&c->jrow, np * sizeof(float2));
   A(&c->Tn, np); A(&c->vrhs, np); A(&c->vin, np); A(&c->w, np); A(&c->u, np); A(&c->P, np);
   for (int k = 0; k < 2; ++k)
     if (st == EREM_OK) st = dalloc(c, &c->q[k], np * esz);
@@ -1294,6 +1305,7 @@ erem_status erem_destroy(erem_ctx* c) {
   for (int k = 0; k < 7; ++k)
     if (c->jc[k]) cudaFree(c->jc[k]);
   if (c->jl_all) cudaFree(c->jl_all);
+  if (c->jrow) cudaFree(c->jrow);
   for (int k = 0; k < 2; ++k)
     if (c->q[k]) cudaFree(c->q[k]);
   for (double* p : c->kv)
@@ -1961,19 +1973,21 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
     for (int k = 1; k < S; ++k) wk[k] = (const double*)(c->tape + rec->w_off[k - 1]);
   } else {
     // G = J T^n + b (the step's first kernel), then the w_k of the substeps
-    launch_step_init(c, Td, d[0], sp, s);
+    launch_step_init(c, Td, sp, s);
     for (int k = 0; k + 1 < S; ++k) {
       const double* u = c->vrhs;
       if (k > 0) {
         launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
         u = c->u;
       }
-      launch_leja_init(c, u, d[0], sp, s);
+      launch_leja_init(c, u, sp, s);
       int qin = 0;
       for (int m = 1; m <= sched[1 + k]; ++m) {
         launch_leja_term(c, m, qin, cg, s);
         qin ^= 1;
       }
+      if (sched[1 + k] % 2 == 0)  // the last product, as erem_step's consumer adds it
+        launch_pfix(c, c->q[sched[1 + k] & 1], sched[1 + k], s);
       // the forward's own update w += delta P (k_axpy), so that these are the
       // bits erem_step produced (and an adjoint tape recorded)
       if (k > 0)
@@ -1997,7 +2011,7 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
         launch_japply_add(c, c->adj_w[k], c->vrhs, c->u, s);
         u = c->u;
       }
-      launch_leja_init(c, u, d[0], sp, s);
+      launch_leja_init(c, u, sp, s);
       EREM_CUDA(c, cudaMemcpyAsync(store, c->q[0], qbytes, cudaMemcpyDeviceToDevice, s));
       for (int m = 1; m < mk; ++m)
         launch_leja_term_ptr(c, m, store + (size_t)(m - 1) * qbytes, store + (size_t)m * qbytes, cg, s);

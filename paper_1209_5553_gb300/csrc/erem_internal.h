@@ -205,6 +205,10 @@ struct erem_ctx {
   // Leja copy of J scaled by dt / gamma, in the precision of the context,
   // interleaved per thread-vector (7 or 5 values per cell)
   void* jl_all = nullptr;
+  double jl_sc = 0;          // the factor dt / gamma of jl_all
+  // FP32-bulk: row sums r_i = sum_j J_ij of the cell form, as float pairs
+  // (hi, lo), for the difference form of G in the step's first kernel
+  float2* jrow = nullptr;
   // vectors
   double *Tn = nullptr, *vrhs = nullptr, *vin = nullptr, *w = nullptr, *u = nullptr, *P = nullptr;
   void* q[2] = {};
@@ -324,6 +328,9 @@ struct erem_ctx {
 
   // kernels launched since the current ABI call began
   mutable long long launches = 0;
+  // FP64 vector the last Leja start kernel made q_0 from (G or u): the first
+  // term starts the running sum from d_0 times it
+  mutable const double* p0 = nullptr;
 
   // timing
   std::vector<cudaEvent_t> ev;
@@ -338,8 +345,16 @@ namespace erem {
 int grid_for(const erem_ctx* c, long long items);
 
 void launch_pack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s);
+// The last product d_M q_M of a Leja sum stopped at an even degree M, which
+// the term kernel leaves out of P (it adds products in pairs at odd m); the
+// consumers below add it (q = null: P is complete).
+struct PFixHost {
+  const void* q = nullptr;  // q_M (Leja precision, padded)
+  int M = 0;
+};
 void launch_finish(const erem_ctx* c, double* out, const double* base, const double* w,
-                   const double* P, double delta, cudaStream_t s, int in_place = 0);
+                   const double* P, double delta, cudaStream_t s, int in_place = 0,
+                   const PFixHost* fix = nullptr);
 void launch_faces(const erem_ctx* c, cudaStream_t s);
 void launch_cellJ(const erem_ctx* c, cudaStream_t s);
 void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s);
@@ -349,17 +364,17 @@ void launch_inflow_forced(const erem_ctx* c, double T_in, double rate, double* b
 void launch_sumsq(const erem_ctx* c, const double* x, cudaStream_t s);  // -> ctrl->lin[K_EMB]
 void launch_japply_add(const erem_ctx* c, const double* x, const double* v, double* out,
                        cudaStream_t s);
-void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
-                      cudaStream_t s);
-void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
-                      cudaStream_t s,
+void launch_leja_init(const erem_ctx* c, const double* u, const StopParams& sp, cudaStream_t s);
+void launch_step_init(const erem_ctx* c, const double* T, const StopParams& sp, cudaStream_t s,
                       double* Tcopy = nullptr);
 int leja_term_blocks_per_sm(const erem_ctx* c);
 void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
 void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,
                           cudaStream_t s);
 void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,
-                 cudaStream_t s);
+                 cudaStream_t s, const PFixHost* fix = nullptr);
+// P += d_M q_M (dd of the current level)
+void launch_pfix(const erem_ctx* c, const void* q, int M, cudaStream_t s);
 void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,
                     const double* y, cudaStream_t s);
 

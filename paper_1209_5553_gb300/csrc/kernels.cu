@@ -72,27 +72,50 @@ __global__ void k_pack(const double* __restrict__ src, double* __restrict__ dst,
   if (bad && flags) atomicOr(flags, FLAG_NONFINITE);
 }
 
-// out[i] = base[ip] + w[ip] + delta * P[ip]  (base, w may be null); with
-// in_place the base is out[i] itself (the caller's unpadded array).
+// The last product d_M q_M of a Leja sum that stopped at an even degree M
+// (the term kernel adds products in pairs at odd m; see k_leja_term): the
+// consumers of P add it on the fly.  q = null: P is complete.
+struct PFix {
+  const void* q;      // q_M in the Leja precision, padded layout
+  int q32;            // q is FP32
+  const double* dd;   // divided differences of the substep level
+  int M;
+};
+__device__ __forceinline__ double p_full(const double* __restrict__ P, const PFix& f, int ip) {
+  double p = P[ip];
+  if (f.q) {
+    const double q = f.q32 ? f2d_exact(static_cast<const float*>(f.q)[ip])
+                           : static_cast<const double*>(f.q)[ip];
+    p = fma(f.dd[f.M], q, p);
+  }
+  return p;
+}
+
+// out[i] = (delta * P[ip] + w[ip]) + base[ip]  (base, w may be null); with
+// in_place the base is out[i] itself (the caller's unpadded array).  Every
+// operation is rounded on its own (no contraction into an FMA), so the
+// result has the same bits whichever of base or in_place supplies T^n.
 __global__ void k_finish(double* out, const double* __restrict__ base,
-                         const double* __restrict__ w, const double* __restrict__ P, double delta,
-                         int in_place, Geo g) {
+                         const double* __restrict__ w, const double* __restrict__ P, PFix f,
+                         double delta, int in_place, Geo g) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
     int ix, iy, iz, ip;
     cell_of(i, g, ix, iy, iz, ip);
-    double v = delta * P[ip];
-    if (w) v += w[ip];
-    if (base) v += base[ip];
-    if (in_place) v += out[i];
+    double v = __dmul_rn(delta, p_full(P, f, ip));
+    if (w) v = __dadd_rn(v, w[ip]);
+    if (base) v = __dadd_rn(v, base[ip]);
+    else if (in_place) v = __dadd_rn(v, out[i]);
     out[i] = v;
   }
 }
 
 // w = (first ? 0 : w) + delta * P over padded arrays
-__global__ void k_axpy(double* __restrict__ w, const double* __restrict__ P, double delta,
+__global__ void k_axpy(double* __restrict__ w, const double* __restrict__ P, PFix f, double delta,
                        int first, int Np) {
-  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
-    w[i] = first ? delta * P[i] : w[i] + delta * P[i];
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
+    const double p = p_full(P, f, i);
+    w[i] = first ? delta * p : w[i] + delta * p;
+  }
 }
 
 __global__ void k_lincomb(double* __restrict__ out, double a, const double* __restrict__ x,
@@ -287,10 +310,17 @@ __global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, P
 // Leja copy of J: (Tq)(sc * jc_k) for every padded cell, in the warp-tile
 // interleaved layout of LejaCoef (tile of T cells).
 template <typename Tq, int T>
-__global__ void k_scale_jl(JOut jc, Tq* __restrict__ out, double sc, int Np, int nc) {
+__global__ void k_scale_jl(JOut jc, Tq* __restrict__ out, double sc, int Np, int nc,
+                           float2* __restrict__ rsum) {
   for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
     const size_t base = (size_t)(i / T) * nc * T + (i % T);
     for (int k = 0; k < nc; ++k) out[base + (size_t)k * T] = (Tq)(sc * jc.c[k][i]);
+    if (rsum) {  // row sum r_i of J (FP64) as a float pair hi + lo
+      double r = 0.0;
+      for (int k = 0; k < nc; ++k) r += jc.c[k][i];
+      const float hi = (float)r;
+      rsum[i] = make_float2(hi, (float)(r - (double)hi));
+    }
   }
 }
 
@@ -415,15 +445,15 @@ __global__ void k_inflow_forced(const double* __restrict__ icap, const double* _
 // First kernel of an EREM step with the linear fluid model, where G is
 // affine in T: G = J T + b exactly (b non-zero only at the x = 0 cells).
 // One pass reads the caller's T (unpadded, left in place for the final
-// update), writes v = G(T^n) (FP64), q_0 = v in the Leja precision and
-// P_0 = d_0 v, reduces ||T^n||_inf for the error scale, and arms the
-// control block of the first substep.  This replaces the face-form G (about
-// 40 FP64 instructions per cell on GB300's slow FP64 pipe) by 8.
+// update), writes v = G(T^n) (FP64) and q_0 = v in the Leja precision,
+// reduces ||T^n||_inf for the error scale, and arms the control block of the
+// first substep (the first Leja term starts the running sum from v).  This
+// replaces the face-form G (about 40 FP64 instructions per cell on GB300's
+// slow FP64 pipe) by 7.
 template <typename Tq>
 __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
                             double* __restrict__ Tcopy, double* __restrict__ G, Tq* __restrict__ q0,
-                            double* __restrict__ P, double d0, Geo g, StopParams sp,
-                            double* part, unsigned* cnt, Ctrl* ctrl) {
+                            Geo g, StopParams sp, double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     arm_ctrl(ctrl, sp);
@@ -447,7 +477,6 @@ __global__ void k_step_init(JIn J, const double* __restrict__ b0, const double* 
     if (ix == 0) a += b0[iy + g.ny * iz];
     G[ip] = a;
     q0[ip] = (Tq)a;
-    P[ip] = d0 * a;
     if (Tcopy) Tcopy[ip] = Ti;
     bad |= !finite(a);
     tmax = fmax(tmax, fabs(Ti));
@@ -476,8 +505,7 @@ template <typename Tq, int DIM>
 __global__ void __launch_bounds__(NT)
 k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__ T,
                 double* __restrict__ Tcopy, double* __restrict__ G, Tq* __restrict__ q0,
-                double* __restrict__ P, double d0, Geo g, StopParams sp, double* part,
-                unsigned* cnt, Ctrl* ctrl) {
+                Geo g, StopParams sp, double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     arm_ctrl(ctrl, sp);
@@ -523,18 +551,15 @@ k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__
       a[v] = x;
     }
     if (ix == 0) a[0] += b0[iy + g.ny * iz];
-    double p[4];
     Tq qv[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      p[v] = d0 * a[v];
       qv[v] = (Tq)a[v];
       const unsigned long long tb_ = abs_bits(tc[v]);
       tmax = tmax > tb_ ? tmax : tb_;
       bad |= !bits_finite(tb_) | !bits_finite(abs_bits(a[v]));
     }
     stP<4>(G + i, a);
-    stP<4>(P + i, p);
     if (Tcopy) stP<4>(Tcopy + i, tc);
     if constexpr (sizeof(Tq) == 4) {
       *reinterpret_cast<float4*>(q0 + i) = make_float4(qv[0], qv[1], qv[2], qv[3]);
@@ -555,34 +580,203 @@ k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__
   }
 }
 
-// q_0 = u (in the Leja precision), P_0 = d_0 u; block 0 arms the control block.
-template <typename Tq>
-__global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0,
-                            double* __restrict__ P, double d0, int Np, StopParams sp, Ctrl* ctrl) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    arm_ctrl(ctrl, sp);
-  }
-  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
-    const double x = u[i];
-    q0[i] = (Tq)x;
-    P[i] = d0 * x;
+// x = hi + lo with hi, lo floats, from the bit fields with integer
+// instructions (the FP64 pipe of GB300 is the scarce unit here): hi is x cut
+// to its leading 24 significand bits, lo the next 23 bits (|x - hi - lo| <=
+// 2^-46 |x|), both exact.  Outside 2^-80 <= |x| < 2^128 the hardware
+// conversion gives hi and lo = 0 (zeros in particular).
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned e = (h32 >> 20) & 0x7ffu;
+  if (e - 943u <= 1150u - 943u) {
+    const unsigned sgn = h32 & 0x80000000u;
+    hi = __uint_as_float(sgn | ((e - 896u) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29));
+    // bits 28..6 of the significand as an integer r < 2^23 (exactly, through
+    // the float 2^23 + r), then r * 2^(e - 1069), a product with a power of 2
+    const float r = __uint_as_float(0x4b000000u | ((l32 & 0x1fffffffu) >> 6)) - 8388608.0f;
+    lo = __uint_as_float(sgn | ((e - 942u) << 23)) * r;
+  } else {
+    hi = __double2float_rn(x);
+    lo = 0.0f;
   }
 }
 
-// One Leja term, fused: q_m = (dt J / gamma - (c/gamma + xi_{m-1})) q_{m-1}
-// (the stencil apply), P += d_m q_m, and the partial sum of q_m^2 for the
-// error estimate; the last block runs the stopping test.  Each thread owns
-// VEC consecutive cells along x.
-template <typename Tq, int VEC, int DIM>
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// First kernel of an FP32-bulk EREM step (linear fluid model, nx a multiple
+// of 4): G = J T + b on the FP32 pipe, in the form
+//   G_i = sum_{j != i} J_ij (T_j - T_i) + (r_i T_i + b_i),   r_i = sum_j J_ij,
+// which equals J T + b exactly.  In J T the products J_ii T_i and J_ij T_j
+// nearly cancel wherever T is smooth, so G computed that way in FP32 carries
+// an error of the size of T itself; here every product is of the size of
+// the result.  Each T (FP64) is split into a float pair hi + lo by integer
+// instructions; T_j - T_i = (hi_j - hi_i) + (lo_j - lo_i) (the hi difference
+// is exact when the two are within a factor 2, i.e. wherever they nearly
+// cancel); the couplings J_ij are the FP32 Leja copy tau J / gamma times
+// gamma / tau; r_i T_i + b_i, which cancels at the Dirichlet inflow, is
+// evaluated in float-pair arithmetic (two-product by fmaf, two-sum).  G
+// keeps its float-pair value in FP64 (vrhs) and rounded to FP32 in q_0; the
+// FP64 pipe carries one addition per cell.  Also: ||T^n||_inf and the
+// finiteness checks on integer bit patterns, T^n copied when Tcopy is set,
+// the control block armed for the first substep.
+template <int DIM>
 __global__ void __launch_bounds__(NT)
-k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
-            LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi, const double* __restrict__ dd,
-            double cg, int m, double* part, unsigned* cnt, Ctrl* ctrl) {
+k_step_init_df(LejaCoef<float> cf, float jinv, const float2* __restrict__ rsum,
+               const double* __restrict__ b0, const double* __restrict__ T,
+               double* __restrict__ Tcopy, double* __restrict__ G, float* __restrict__ q0, Geo g,
+               StopParams sp, double* part, unsigned* cnt, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    arm_ctrl(ctrl, sp);
+  }
+  unsigned long long tmax = 0ULL;
+  bool bad = false;
+  const int nvec = g.Np / 4;
+  const int vrow = g.px / 4;
+  for (int t = blockIdx.x * NT + threadIdx.x; t < nvec; t += gridDim.x * NT) {
+    const int row = t / vrow;
+    const int ix = (t - row * vrow) * 4;
+    const int iy = row % g.ny;
+    const int iz = row / g.ny;
+    const int i = row * g.px + ix;
+    double tc[4];
+    ldP<4>(tc, T + i);
+    if (Tcopy) stP<4>(Tcopy + i, tc);
+    float h[4], l[4];  // the centre cells as float pairs
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const unsigned long long tb_ = abs_bits(tc[v]);
+      tmax = tmax > tb_ ? tmax : tb_;
+      bad |= !bits_finite(tb_);
+      split_f64(tc[v], h[v], l[v]);
+    }
+    const size_t off = leja_off<128>(i, cf.nc);
+    // sum_j J_ij (T_j - T_i) direction by direction, couplings of the scaled copy
+    float S[4];
+    {
+      float wh, wl, eh, el, cW[4], cE[4];
+      split_f64(ix > 0 ? T[i - 1] : 0.0, wh, wl);
+      split_f64(ix + 4 < g.px ? T[i + 4] : 0.0, eh, el);
+      ldv_stream<float, 4>(cW, cf.c[1] + off);
+      ldv_stream<float, 4>(cE, cf.c[2] + off);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float xh = v == 0 ? wh : h[v - 1], xl = v == 0 ? wl : l[v - 1];
+        const float yh = v == 3 ? eh : h[v + 1], yl = v == 3 ? el : l[v + 1];
+        S[v] = fmaf(cE[v], (yh - h[v]) + (yl - l[v]), cW[v] * ((xh - h[v]) + (xl - l[v])));
+      }
+    }
+    constexpr int NB = DIM == 3 ? 4 : 2;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {  // S, N (, B, T)
+      const int step = k < 2 ? g.px : g.plane;
+      const bool has = k == 0 ? iy > 0 : k == 1 ? iy < g.ny - 1 : k == 2 ? iz > 0 : iz < g.nz - 1;
+      double tn[4];
+      ldP<4>(tn, T + i + (has ? (k & 1 ? step : -step) : 0));
+      float cN[4];
+      ldv_stream<float, 4>(cN, cf.c[3 + k] + off);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float nh, nl;
+        split_f64(tn[v], nh, nl);
+        S[v] = fmaf(cN[v], (nh - h[v]) + (nl - l[v]), S[v]);
+      }
+    }
+    const float4 r01 = *reinterpret_cast<const float4*>(rsum + i);
+    const float4 r23 = *reinterpret_cast<const float4*>(rsum + i + 2);
+    const float rh[4] = {r01.x, r01.z, r23.x, r23.z};
+    const float rl[4] = {r01.y, r01.w, r23.y, r23.w};
+    double gv[4];
+    float qv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float Sv = S[v] * jinv;
+      // r_i T_i (+ b_i) as a float pair (p, e)
+      const float p = rh[v] * h[v];
+      float e = fmaf(rh[v], h[v], -p);
+      e = fmaf(rh[v], l[v], e);
+      e = fmaf(rl[v], h[v], e);
+      float ph = p;
+      if (v == 0 && ix == 0) {  // the x = 0 cell: + b_i
+        float bh, bl, s2;
+        split_f64(b0[iy + g.ny * iz], bh, bl);
+        two_sum(p, bh, ph, s2);
+        e += s2 + bl;
+      }
+      // G = S + (ph + e): (gr, gl) with gr the rounded value
+      float gh, g2;
+      two_sum(ph, Sv, gh, g2);
+      const float glo = g2 + e;
+      const float gr = gh + glo;
+      const float gl = glo - (gr - gh);
+      qv[v] = gr;
+      gv[v] = f2d_exact(gr) + f2d_exact(gl);
+      bad |= !isfinite(gr);
+    }
+    stP<4>(G + i, gv);
+    *reinterpret_cast<float4*>(q0 + i) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+  }
+  if (bad) atomicOr(&ctrl->flags, FLAG_NONFINITE);
+  const double bmax = block_reduce<2>(__longlong_as_double((long long)tmax), sh);
+  double vals[1] = {bmax};
+  if (publish_partials(part, cnt, vals, 1)) {
+    const double a = gather_partials<2>(part, 0, sh);
+    if (threadIdx.x == 0) {
+      ctrl->yinf = a;
+      *cnt = 0;
+    }
+  }
+}
+
+// q_0 = u (in the Leja precision); block 0 arms the control block.  The
+// first Leja term starts the running sum from d_0 u.
+template <typename Tq>
+__global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0, int Np,
+                            StopParams sp, Ctrl* ctrl) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    arm_ctrl(ctrl, sp);
+  }
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) q0[i] = (Tq)u[i];
+}
+
+// One Leja term, fused: q_m = (dt J / gamma - (c/gamma + xi_{m-1})) q_{m-1}
+// (the stencil apply), the running sum P, and the partial sum of q_m^2 for
+// the error estimate; the last block runs the stopping test.  Each thread
+// owns VEC consecutive cells along x.
+//
+// The running sum is updated every other term, when both vectors it needs
+// are in registers (q_{m-1} is the stencil's centre, q_m its result):
+//   PM = 2 (m = 1):      P = d_0 p0 + d_1 q_1   (p0: the FP64 vector q_0 was made from)
+//   PM = 1 (m odd > 1):  P += d_{m-1} q_{m-1} + d_m q_m
+//   PM = 0 (m even):     P untouched (no P traffic: 16 fewer bytes per cell)
+// The two products enter P one after the other, in the order of eq. newt,
+// so P after term m (odd) has the bits of a sum updated at every term.  A
+// substep stopped at an even degree M has P short of d_M q_M: its consumer
+// adds it (k_finish, k_axpy, k_pfix).
+//
+// In FP32-bulk the squares of a thread's values are summed in FP32 with a
+// compensated (two-sum) accumulator and enter the FP64 norm once per thread,
+// so the FP64 pipe only carries the running sum.
+template <typename Tq, int VEC, int DIM, int PM>
+__device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __restrict__ qo,
+                                               double* __restrict__ P, const double* __restrict__ p0,
+                                               const LejaCoef<Tq>& cf, const Geo& g,
+                                               const double* __restrict__ xi,
+                                               const double* __restrict__ dd, double cg, int m,
+                                               double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
   if (*(volatile int*)&ctrl->done) return;
   const Tq sh_m = (Tq)(cg + xi[m - 1]);
   const double dm = dd[m];
+  const double dm1 = dd[m - 1];
   double acc = 0.0;
+  float s_hi = 0.f, s_lo = 0.f;  // FP32-bulk: compensated sum of squares
   const int nvec = g.Np / VEC;
   const int vrow = g.px / VEC;
   for (int t = blockIdx.x * NT + threadIdx.x; t < nvec; t += gridDim.x * NT) {
@@ -612,7 +806,8 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
       ldv_stream<Tq, VEC>(cT, cf.c[6] + leja_off<32 * VEC>(i, cf.nc));
     }
     double p[VEC];
-    ldP<VEC>(p, P + i);
+    if constexpr (PM == 1) ldP<VEC>(p, P + i);
+    if constexpr (PM == 2) ldP<VEC>(p, p0 + i);
     Tq out[VEC];
     Tq sq = Tq(0);
 #pragma unroll
@@ -629,20 +824,25 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
         a = fma(cT[k], qt[k], a);
       }
       out[k] = a;
+      if constexpr (PM == 1) p[k] = fma(dm, to_f64(a), fma(dm1, to_f64(qc[k]), p[k]));
+      if constexpr (PM == 2) p[k] = fma(dm, to_f64(a), dm1 * p[k]);
       if constexpr (sizeof(Tq) == 4) {
-        // FP64 running sum; the squares of the VEC FP32 values are summed in
-        // FP32 and enter the FP64 norm accumulator once per thread-vector
-        p[k] = fma(dm, f2d_exact(a), p[k]);
         sq = fmaf(a, a, sq);
       } else {
-        p[k] = fma(dm, a, p[k]);
         acc = fma(a, a, acc);
       }
     }
-    if constexpr (sizeof(Tq) == 4) acc += (double)sq;
+    if constexpr (sizeof(Tq) == 4) {
+      // two-sum of the running FP32 sum and this vector's squares
+      const float s = s_hi + sq;
+      const float bp = s - s_hi;
+      s_lo += (s_hi - (s - bp)) + (sq - bp);
+      s_hi = s;
+    }
     stv<Tq, VEC>(qo + i, out);
-    stP<VEC>(P + i, p);
+    if constexpr (PM != 0) stP<VEC>(P + i, p);
   }
+  if constexpr (sizeof(Tq) == 4) acc = (double)s_hi + (double)s_lo;
   const double bs = block_reduce<0>(acc, sh);
   double vals[1] = {bs};
   if (publish_partials(part, cnt, vals, 1)) {
@@ -652,6 +852,35 @@ k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__
       stop_test(ctrl, m, dm, S);
     }
   }
+}
+
+// Terms m >= 2 (PM = 0 or 1), with the compiler's own register budget
+// (54-64 registers: four resident blocks of 256 threads per SM).
+template <typename Tq, int VEC, int DIM, int PM>
+__global__ void __launch_bounds__(NT)
+k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
+            LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi, const double* __restrict__ dd,
+            double cg, int m, double* part, unsigned* cnt, Ctrl* ctrl) {
+  leja_term_body<Tq, VEC, DIM, PM>(qi, qo, P, nullptr, cf, g, xi, dd, cg, m, part, cnt, ctrl);
+}
+
+// Term m = 1 (PM = 2), held to four resident blocks per SM like the others.
+template <typename Tq, int VEC, int DIM>
+__global__ void __launch_bounds__(NT, 4)
+k_leja_term1(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
+             const double* __restrict__ p0, LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi,
+             const double* __restrict__ dd, double cg, double* part, unsigned* cnt, Ctrl* ctrl) {
+  leja_term_body<Tq, VEC, DIM, 2>(qi, qo, P, p0, cf, g, xi, dd, cg, 1, part, cnt, ctrl);
+}
+
+// P += d_M q_M: the last product of a substep stopped at an even degree M
+// (the term kernel updates P at odd m only).
+template <typename Tq>
+__global__ void k_pfix(double* __restrict__ P, const Tq* __restrict__ q,
+                       const double* __restrict__ dd, int M, int Np) {
+  const double d = dd[M];
+  for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
+    P[i] = fma(d, to_f64(q[i]), P[i]);
 }
 
 __global__ void k_unpack(const double* __restrict__ src, double* __restrict__ dst, Geo g) {
@@ -2372,10 +2601,17 @@ void launch_pack(const erem_ctx* c, const double* src, double* dst, cudaStream_t
   k_pack<<<blocks_cells(c), NT, 0, s>>>(src, dst, geo_of(c), &c->ctrl->flags);
 }
 
+PFix pfix_of(const erem_ctx* c, const PFixHost* f) {
+  if (!f || !f->q) return PFix{nullptr, 0, nullptr, 0};
+  return PFix{f->q, c->prec == EREM_FP32_BULK ? 1 : 0, c->dd_dev, f->M};
+}
+
 void launch_finish(const erem_ctx* c, double* out, const double* base, const double* w,
-                   const double* P, double delta, cudaStream_t s, int in_place) {
+                   const double* P, double delta, cudaStream_t s, int in_place,
+                   const PFixHost* fix) {
   ++c->launches;
-  k_finish<<<blocks_cells(c), NT, 0, s>>>(out, base, w, P, delta, in_place, geo_of(c));
+  k_finish<<<blocks_cells(c), NT, 0, s>>>(out, base, w, P, pfix_of(c, fix), delta, in_place,
+                                          geo_of(c));
 }
 
 // the cell mobilities K / mu(T) go to P (the Leja sum, which every step
@@ -2405,9 +2641,11 @@ void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s) {
   const int nc = c->dim == 3 ? 7 : 5;
   ++c->launches;
   if (c->prec == EREM_FP32_BULK)
-    k_scale_jl<float, 128><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jl_all, sc, (int)c->Np, nc);
+    k_scale_jl<float, 128><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jl_all, sc, (int)c->Np, nc,
+                                                           c->jrow);
   else
-    k_scale_jl<double, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (double*)c->jl_all, sc, (int)c->Np, nc);
+    k_scale_jl<double, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (double*)c->jl_all, sc, (int)c->Np, nc,
+                                                           nullptr);
 }
 
 // Pointers of the interleaved Leja coefficients for kernels of vector width
@@ -2445,61 +2683,63 @@ void launch_japply_add(const erem_ctx* c, const double* x, const double* v, doub
   k_japply_add<<<blocks_cells(c), NT, 0, s>>>(jin(c), x, v, out, geo_of(c));
 }
 
-void launch_leja_init(const erem_ctx* c, const double* u, double d0, const StopParams& sp,
-                      cudaStream_t s) {
+void launch_leja_init(const erem_ctx* c, const double* u, const StopParams& sp, cudaStream_t s) {
   ++c->launches;
+  c->p0 = u;
   if (c->prec == EREM_FP32_BULK)
-    k_leja_init<float><<<blocks_padded(c), NT, 0, s>>>(u, (float*)c->q[0], c->P, d0, (int)c->Np, sp,
-                                                       c->ctrl);
+    k_leja_init<float><<<blocks_padded(c), NT, 0, s>>>(u, (float*)c->q[0], (int)c->Np, sp, c->ctrl);
   else
-    k_leja_init<double><<<blocks_padded(c), NT, 0, s>>>(u, (double*)c->q[0], c->P, d0, (int)c->Np,
-                                                        sp, c->ctrl);
+    k_leja_init<double><<<blocks_padded(c), NT, 0, s>>>(u, (double*)c->q[0], (int)c->Np, sp, c->ctrl);
 }
 
-void launch_step_init(const erem_ctx* c, const double* T, double d0, const StopParams& sp,
-                      cudaStream_t s, double* Tcopy) {
+void launch_step_init(const erem_ctx* c, const double* T, const StopParams& sp, cudaStream_t s,
+                      double* Tcopy) {
   ++c->launches;
+  c->p0 = c->vrhs;
   if (c->px == c->nx) {  // unpadded rows: four cells per thread
     const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
     const Geo g = geo_of(c);
-    if (c->prec == EREM_FP32_BULK) {
+    if (c->prec == EREM_FP32_BULK) {  // G in the difference form on the FP32 pipe
+      const LejaCoef<float> cf = leja_coef<float, 4>(c);
+      const float jinv = (float)(1.0 / c->jl_sc);
       if (c->dim == 3)
-        k_step_init_vec<float, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (float*)c->q[0], c->P,
-                                                    d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+        k_step_init_df<3><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
+                                            (float*)c->q[0], g, sp, c->red_part, c->red_cnt, c->ctrl);
       else
-        k_step_init_vec<float, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (float*)c->q[0], c->P,
-                                                    d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+        k_step_init_df<2><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
+                                            (float*)c->q[0], g, sp, c->red_part, c->red_cnt, c->ctrl);
     } else {
       if (c->dim == 3)
         k_step_init_vec<double, 3><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (double*)c->q[0],
-                                                     c->P, d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+                                                     g, sp, c->red_part, c->red_cnt, c->ctrl);
       else
         k_step_init_vec<double, 2><<<nb, NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs, (double*)c->q[0],
-                                                     c->P, d0, g, sp, c->red_part, c->red_cnt, c->ctrl);
+                                                     g, sp, c->red_part, c->red_cnt, c->ctrl);
     }
     return;
   }
   if (c->prec == EREM_FP32_BULK)
     k_step_init<float><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs,
-                                                      (float*)c->q[0], c->P, d0, geo_of(c), sp,
+                                                      (float*)c->q[0], geo_of(c), sp,
                                                       c->red_part, c->red_cnt, c->ctrl);
   else
     k_step_init<double><<<blocks_cells(c), NT, 0, s>>>(jin(c), c->b0, T, Tcopy, c->vrhs,
-                                                       (double*)c->q[0], c->P, d0, geo_of(c), sp,
+                                                       (double*)c->q[0], geo_of(c), sp,
                                                        c->red_part, c->red_cnt, c->ctrl);
 }
 
 // Resident blocks per SM of the one-term kernel of this context's precision
-// and dimension (its grid-stride grid is one full wave of them).
+// and dimension (its grid-stride grid is one full wave of them; the three
+// running-sum modes use the same registers or fewer than the first).
 int leja_term_blocks_per_sm(const erem_ctx* c) {
   int n = 0;
   cudaError_t e;
   if (c->prec == EREM_FP32_BULK)
-    e = c->dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<float, 4, 3>, NT, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<float, 4, 2>, NT, 0);
+    e = c->dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<float, 4, 3, 1>, NT, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<float, 4, 2, 1>, NT, 0);
   else
-    e = c->dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<double, 2, 3>, NT, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<double, 2, 2>, NT, 0);
+    e = c->dim == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<double, 2, 3, 1>, NT, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_leja_term<double, 2, 2, 1>, NT, 0);
   if (e != cudaSuccess || n < 1) {
     cudaGetLastError();
     n = 4;
@@ -2507,66 +2747,54 @@ int leja_term_blocks_per_sm(const erem_ctx* c) {
   return n;
 }
 
-void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
+template <typename Tq, int VEC, int DIM>
+void term_launch(const erem_ctx* c, int m, const Tq* qi, Tq* qo, double cg, cudaStream_t s) {
+  const LejaCoef<Tq> cf = leja_coef<Tq, VEC>(c);
   const Geo g = geo_of(c);
+  const int nb = std::min(grid_for(c, c->Np / VEC), c->term_grid);
+  ++c->launches;
+  if (m == 1)
+    k_leja_term1<Tq, VEC, DIM><<<nb, NT, 0, s>>>(qi, qo, c->P, c->p0, cf, g, c->xi_dev, c->dd_dev,
+                                                 cg, c->red_part, c->red_cnt, c->ctrl);
+  else if (m & 1)
+    k_leja_term<Tq, VEC, DIM, 1><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
+                                                   c->red_part, c->red_cnt, c->ctrl);
+  else
+    k_leja_term<Tq, VEC, DIM, 0><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
+                                                   c->red_part, c->red_cnt, c->ctrl);
+}
+
+// One Leja term with explicit input/output vectors (the context's ping-pong
+// pair, or the adjoint's store of Newton vectors).  The running sum is
+// updated at odd m (see k_leja_term); m = 1 starts it from c->p0, the FP64
+// vector the last Leja start kernel made q_0 from.
+void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,
+                          cudaStream_t s) {
   if (c->prec == EREM_FP32_BULK) {
-    const LejaCoef<float> cf = leja_coef<float, 4>(c);
-    const float* qi = (const float*)c->q[qin];
-    float* qo = (float*)c->q[qin ^ 1];
-    const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
-    ++c->launches;
-    if (c->dim == 3)
-      k_leja_term<float, 4, 3><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
-                                                 c->red_part, c->red_cnt, c->ctrl);
-    else
-      k_leja_term<float, 4, 2><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
-                                                 c->red_part, c->red_cnt, c->ctrl);
+    if (c->dim == 3) term_launch<float, 4, 3>(c, m, (const float*)qi, (float*)qo, cg, s);
+    else term_launch<float, 4, 2>(c, m, (const float*)qi, (float*)qo, cg, s);
   } else {
-    const LejaCoef<double> cf = leja_coef<double, 2>(c);
-    const double* qi = (const double*)c->q[qin];
-    double* qo = (double*)c->q[qin ^ 1];
-    const int nb = std::min(grid_for(c, c->Np / 2), c->term_grid);
-    ++c->launches;
-    if (c->dim == 3)
-      k_leja_term<double, 2, 3><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
-                                                  c->red_part, c->red_cnt, c->ctrl);
-    else
-      k_leja_term<double, 2, 2><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
-                                                  c->red_part, c->red_cnt, c->ctrl);
+    if (c->dim == 3) term_launch<double, 2, 3>(c, m, (const double*)qi, (double*)qo, cg, s);
+    else term_launch<double, 2, 2>(c, m, (const double*)qi, (double*)qo, cg, s);
   }
 }
 
-// One Leja term with explicit input/output vectors (the adjoint's store of
-// Newton vectors); otherwise as launch_leja_term.
-void launch_leja_term_ptr(const erem_ctx* c, int m, const void* qi, void* qo, double cg,
-                          cudaStream_t s) {
-  const Geo g = geo_of(c);
+void launch_leja_term(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
+  launch_leja_term_ptr(c, m, c->q[qin], c->q[qin ^ 1], cg, s);
+}
+
+void launch_pfix(const erem_ctx* c, const void* q, int M, cudaStream_t s) {
   ++c->launches;
-  if (c->prec == EREM_FP32_BULK) {
-    const LejaCoef<float> cf = leja_coef<float, 4>(c);
-    const int nb = std::min(grid_for(c, c->Np / 4), c->term_grid);
-    if (c->dim == 3)
-      k_leja_term<float, 4, 3><<<nb, NT, 0, s>>>((const float*)qi, (float*)qo, c->P, cf, g, c->xi_dev,
-                                                 c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
-    else
-      k_leja_term<float, 4, 2><<<nb, NT, 0, s>>>((const float*)qi, (float*)qo, c->P, cf, g, c->xi_dev,
-                                                 c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
-  } else {
-    const LejaCoef<double> cf = leja_coef<double, 2>(c);
-    const int nb = std::min(grid_for(c, c->Np / 2), c->term_grid);
-    if (c->dim == 3)
-      k_leja_term<double, 2, 3><<<nb, NT, 0, s>>>((const double*)qi, (double*)qo, c->P, cf, g, c->xi_dev,
-                                                  c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
-    else
-      k_leja_term<double, 2, 2><<<nb, NT, 0, s>>>((const double*)qi, (double*)qo, c->P, cf, g, c->xi_dev,
-                                                  c->dd_dev, cg, m, c->red_part, c->red_cnt, c->ctrl);
-  }
+  if (c->prec == EREM_FP32_BULK)
+    k_pfix<float><<<blocks_padded(c), NT, 0, s>>>(c->P, (const float*)q, c->dd_dev, M, (int)c->Np);
+  else
+    k_pfix<double><<<blocks_padded(c), NT, 0, s>>>(c->P, (const double*)q, c->dd_dev, M, (int)c->Np);
 }
 
 void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, int first,
-                 cudaStream_t s) {
+                 cudaStream_t s, const PFixHost* fix) {
   ++c->launches;
-  k_axpy<<<blocks_padded(c), NT, 0, s>>>(w, P, delta, first, (int)c->Np);
+  k_axpy<<<blocks_padded(c), NT, 0, s>>>(w, P, pfix_of(c, fix), delta, first, (int)c->Np);
 }
 
 void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,
