@@ -1147,6 +1147,7 @@ erem_status ensure_adj(erem_ctx* c, int M, int S) {
   const size_t esz = c->prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
   const int nc = c->dim == 3 ? 7 : 5;
   if (!c->jlT_all) {
+    if (c->prec == EREM_FP32_BULK) choose_adj_vec(c);
     EREM_TRY(dalloc(c, &c->jlT_all, (np + 128) / 128 * 128 * nc * esz));
     for (int k = 0; k < 2; ++k) EREM_TRY(dalloc(c, &c->adj_s[k], np * esz));
     EREM_TRY(dalloc_t(c, &c->adj_mu, np));
@@ -1263,6 +1264,7 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
     if (w >= 1) term_waves = w;
   }
   c->term_grid = std::min(c->red_blocks, term_waves * c->sm_count * leja_term_blocks_per_sm(c));
+  if (const char* e = std::getenv("EREM_TERM_PDL")) c->pdl = std::atoi(e) != 0;  // tuning override
   const size_t np = (size_t)Np, nf = (size_t)g.ny * g.nz;
   const size_t esz = prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
   erem_status st = EREM_OK;

@@ -104,6 +104,7 @@ __device__ __forceinline__ void arm_ctrl(Ctrl* c, const StopParams& sp) {
 // ---------------------------------------------------------------------------
 template <typename Tq, int VEC> struct VecT;
 template <> struct VecT<float, 4> { using V = float4; };
+template <> struct VecT<float, 2> { using V = float2; };
 template <> struct VecT<double, 2> { using V = double2; };
 
 template <typename Tq, int VEC>
@@ -157,6 +158,26 @@ __device__ __forceinline__ double f2d_exact(float f) {
   if (e == 0u || e == 0xffu) return (double)f;
   const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
   const unsigned lo = u << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// float -> double, exact, from the bit fields with integer instructions
+// only, for the single-problem kernels (the FP64 pipe of GB300 is the scarce
+// unit in the FP32-bulk sweep; the hardware conversion that f2d_exact keeps
+// for rare inputs is if-converted into one that every call executes):
+// normal numbers,
+// infinities and NaNs by widening the fields, zeros by their sign, and a
+// subnormal f through 2^24 f (an exact FP32 product, and a normal number)
+// with 24 taken off the exponent.
+__device__ __forceinline__ double f2d_fast(float f) {
+  const unsigned e0 = (__float_as_uint(f) >> 23) & 0xffu;
+  const float g = e0 == 0u ? f * 16777216.0f : f;
+  const unsigned u = __float_as_uint(g);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned E = e == 0xffu ? 0x7ffu : e + (e0 == 0u ? 872u : 896u);
+  const unsigned hi = e == 0u ? (u & 0x80000000u)
+                              : (u & 0x80000000u) | (E << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned lo = e == 0u ? 0u : u << 29;
   return __hiloint2double((int)hi, (int)lo);
 }
 
@@ -215,6 +236,11 @@ __device__ void stop_test(Ctrl* c, int m, double dm, double S) {
 template <typename Tq>
 __device__ __forceinline__ double to_f64(Tq v) {
   if constexpr (sizeof(Tq) == 4) return f2d_exact(v);
+  else return v;
+}
+template <typename Tq>
+__device__ __forceinline__ double to_f64_fast(Tq v) {
+  if constexpr (sizeof(Tq) == 4) return f2d_fast(v);
   else return v;
 }
 

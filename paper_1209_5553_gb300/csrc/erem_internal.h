@@ -190,6 +190,7 @@ struct erem_ctx {
   double hx = 1, hy = 1, hz = 1, vol = 1, ax = 1, ay = 1, az = 1;
   int device = 0, sm_count = 1, red_blocks = 1;
   int term_grid = 1;      // blocks of the one-term kernel (one resident wave)
+  bool pdl = true;        // Leja terms launched as programmatic dependents
   std::string err;
 
   // stored fields (padded, FP64)
@@ -251,7 +252,9 @@ struct erem_ctx {
   erem::KrDev* kr_host = nullptr;   // pinned
   int kr_cap = 0;                   // basis vectors allocated
   // adjoint (allocated on first use)
-  void* jlT_all = nullptr;          // Leja copy of J^T, layout of jl_all
+  void* jlT_all = nullptr;          // Leja copy of J^T (FP32: interleaved per 32 adj_vec cells)
+  int adj_vec = 4;                  // cells per thread of the FP32 Horner pass (4 or 2)
+  int adj_blocks_per_sm = 4;        // its resident blocks per SM (one wave of them)
   bool jlT_valid = false;
   void* adj_store = nullptr;        // forward Newton vectors q_0..q_{m-1} of one substep
   int adj_store_cap = 0;            // vectors adj_store holds
@@ -434,6 +437,7 @@ void launch_adj_jT_apply(const erem_ctx* c, const double* x, const double* a, do
 void launch_adj_face_pair(const erem_ctx* c, const double* y, const double* x, double scale,
                           cudaStream_t s);
 void launch_adj_start(const erem_ctx* c, const double* mu, double d, void* sbuf, cudaStream_t s);
+void choose_adj_vec(erem_ctx* c);
 void launch_adj_aux32(const erem_ctx* c, cudaStream_t s);
 void launch_adj_flush32(const erem_ctx* c, cudaStream_t s);
 void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const double* mu,

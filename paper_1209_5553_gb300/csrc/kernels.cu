@@ -84,7 +84,7 @@ struct PFix {
 __device__ __forceinline__ double p_full(const double* __restrict__ P, const PFix& f, int ip) {
   double p = P[ip];
   if (f.q) {
-    const double q = f.q32 ? f2d_exact(static_cast<const float*>(f.q)[ip])
+    const double q = f.q32 ? f2d_fast(static_cast<const float*>(f.q)[ip])
                            : static_cast<const double*>(f.q)[ip];
     p = fma(f.dd[f.M], q, p);
   }
@@ -581,25 +581,36 @@ k_step_init_vec(JIn J, const double* __restrict__ b0, const double* __restrict__
 }
 
 // x = hi + lo with hi, lo floats, from the bit fields with integer
-// instructions (the FP64 pipe of GB300 is the scarce unit here): hi is x cut
-// to its leading 24 significand bits, lo the next 23 bits (|x - hi - lo| <=
-// 2^-46 |x|), both exact.  Outside 2^-80 <= |x| < 2^128 the hardware
-// conversion gives hi and lo = 0 (zeros in particular).
+// instructions only (the FP64 pipe of GB300 is the scarce unit here): hi is
+// x cut to its leading 24 significand bits, lo the next 23 bits, both exact,
+// |x - hi - lo| <= 2^-46 |x|, for 2^-80 <= |x| < 2^128.  Below that lo is 0
+// (hi still exact down to 2^-126, the smallest normal float), magnitudes
+// under 2^-126 give hi = 0 (flushed, as FP32 arithmetic with flush-to-zero
+// would), and magnitudes of 2^128 and more give an infinite hi (a NaN stays
+// a NaN), which the caller's finiteness check reports.
 __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
   const unsigned e = (h32 >> 20) & 0x7ffu;
-  if (e - 943u <= 1150u - 943u) {
-    const unsigned sgn = h32 & 0x80000000u;
-    hi = __uint_as_float(sgn | ((e - 896u) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29));
-    // bits 28..6 of the significand as an integer r < 2^23 (exactly, through
-    // the float 2^23 + r), then r * 2^(e - 1069), a product with a power of 2
-    const float r = __uint_as_float(0x4b000000u | ((l32 & 0x1fffffffu) >> 6)) - 8388608.0f;
-    lo = __uint_as_float(sgn | ((e - 942u) << 23)) * r;
+  const unsigned sgn = h32 & 0x80000000u;
+  unsigned hb;
+  float l = 0.0f;
+  if (e - 897u <= 1150u - 897u) {
+    hb = sgn | ((e - 896u) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+    if (e >= 943u) {
+      // bits 28..6 of the significand as an integer r < 2^23 (exactly,
+      // through the float 2^23 + r), then r 2^(e - 1069), a product with a
+      // power of 2
+      const float r = __uint_as_float(0x4b000000u | ((l32 & 0x1fffffffu) >> 6)) - 8388608.0f;
+      l = __uint_as_float(sgn | ((e - 942u) << 23)) * r;
+    }
+  } else if (e < 897u) {
+    hb = sgn;
   } else {
-    hi = __double2float_rn(x);
-    lo = 0.0f;
+    hb = sgn | ((e == 0x7ffu && ((h32 & 0xfffffu) | l32)) ? 0x7fc00000u : 0x7f800000u);
   }
+  hi = __uint_as_float(hb);
+  lo = l;
 }
 
 // s + e = a + b exactly (Knuth's two-sum)
@@ -716,7 +727,7 @@ k_step_init_df(LejaCoef<float> cf, float jinv, const float2* __restrict__ rsum,
       const float gr = gh + glo;
       const float gl = glo - (gr - gh);
       qv[v] = gr;
-      gv[v] = f2d_exact(gr) + f2d_exact(gl);
+      gv[v] = f2d_fast(gr) + f2d_fast(gl);
       bad |= !isfinite(gr);
     }
     stP<4>(G + i, gv);
@@ -771,6 +782,13 @@ __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __
                                                const double* __restrict__ dd, double cg, int m,
                                                double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
+  // Launched as a programmatic dependent of the previous term: wait until
+  // that grid has completed and its writes are visible (a no-op when the
+  // launch was an ordinary one), then let the next term be scheduled: its
+  // blocks take the SM slots this grid's blocks free while its last block
+  // reduces the norm, and wait here in turn.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   if (*(volatile int*)&ctrl->done) return;
   const Tq sh_m = (Tq)(cg + xi[m - 1]);
   const double dm = dd[m];
@@ -824,13 +842,17 @@ __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __
         a = fma(cT[k], qt[k], a);
       }
       out[k] = a;
-      if constexpr (PM == 1) p[k] = fma(dm, to_f64(a), fma(dm1, to_f64(qc[k]), p[k]));
-      if constexpr (PM == 2) p[k] = fma(dm, to_f64(a), dm1 * p[k]);
       if constexpr (sizeof(Tq) == 4) {
         sq = fmaf(a, a, sq);
       } else {
         acc = fma(a, a, acc);
       }
+    }
+    // the running sum after the stencil (the coefficients are dead by now)
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      if constexpr (PM == 1) p[k] = fma(dm, to_f64_fast(out[k]), fma(dm1, to_f64_fast(qc[k]), p[k]));
+      if constexpr (PM == 2) p[k] = fma(dm, to_f64_fast(out[k]), dm1 * p[k]);
     }
     if constexpr (sizeof(Tq) == 4) {
       // two-sum of the running FP32 sum and this vector's squares
@@ -854,10 +876,10 @@ __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __
   }
 }
 
-// Terms m >= 2 (PM = 0 or 1), with the compiler's own register budget
-// (54-64 registers: four resident blocks of 256 threads per SM).
+// Terms m >= 2 (PM = 0 or 1), held to four resident blocks of 256 threads
+// per SM, the grid the launcher sizes.
 template <typename Tq, int VEC, int DIM, int PM>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
             LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi, const double* __restrict__ dd,
             double cg, int m, double* part, unsigned* cnt, Ctrl* ctrl) {
@@ -880,7 +902,7 @@ __global__ void k_pfix(double* __restrict__ P, const Tq* __restrict__ q,
                        const double* __restrict__ dd, int M, int Np) {
   const double d = dd[M];
   for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT)
-    P[i] = fma(d, to_f64(q[i]), P[i]);
+    P[i] = fma(d, to_f64_fast(q[i]), P[i]);
 }
 
 __global__ void k_unpack(const double* __restrict__ src, double* __restrict__ dst, Geo g) {
@@ -1163,16 +1185,23 @@ __global__ void k_adj_aux32(const double* __restrict__ Fx, const double* __restr
   }
 }
 
-// Four consecutive cells of one padded row per thread (px is a multiple of
-// 4, so every row starts on a 16-byte boundary): float4 loads of the vectors,
-// coefficients, capacities and face sums, scalar loads only for the x
-// neighbours beyond the four.  Pad lanes (ix >= nx) compute nothing and store 0.
-struct Row4 {
+// VEC (4 or 2) consecutive cells of one padded row per thread (px is a
+// multiple of 4, so every row starts on a 16-byte boundary): vector loads of
+// the vectors, coefficients, capacities and face sums, scalar loads only for
+// the x neighbours beyond the VEC.  Pad lanes (ix >= nx) compute nothing and
+// store 0.  The neighbour loads are unconditional, at the cell's own address
+// where the neighbour is missing (its coupling there is 0), so a thread has
+// all of them in flight at once.  The transposed coefficients are
+// interleaved per tile of 32 VEC cells (T_TILE), so a warp reads each as one
+// contiguous run.
+template <int VEC>
+struct RowV {
   int ip0, ix0, iy, iz;
 };
-__device__ __forceinline__ Row4 row4_of(int v, const Geo& g) {
-  Row4 r;
-  r.ip0 = 4 * v;
+template <int VEC>
+__device__ __forceinline__ RowV<VEC> rowv_of(int v, const Geo& g) {
+  RowV<VEC> r;
+  r.ip0 = VEC * v;
   const int row = r.ip0 / g.px;
   r.ix0 = r.ip0 - row * g.px;
   r.iy = row % g.ny;
@@ -1180,110 +1209,111 @@ __device__ __forceinline__ Row4 row4_of(int v, const Geo& g) {
   return r;
 }
 
-template <int T_TILE>
-__global__ void k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
-                               const float* __restrict__ mu, const float* __restrict__ q,
-                               const float* __restrict__ jlT, int nc, float dj, float shift,
-                               float scale, AdjFaces32 f, Geo g) {
-  const int nvec = g.Np / 4;
+template <int VEC>
+__device__ __forceinline__ void ld_flags(unsigned (&fl)[VEC], const unsigned char* p) {
+  if constexpr (VEC == 4) {
+    const uchar4 u = *reinterpret_cast<const uchar4*>(p);
+    fl[0] = u.x; fl[1] = u.y; fl[2] = u.z; fl[3] = u.w;
+  } else {
+    const uchar2 u = *reinterpret_cast<const uchar2*>(p);
+    fl[0] = u.x; fl[1] = u.y;
+  }
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(NT, 4)
+k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
+               const float* __restrict__ mu, const float* __restrict__ q,
+               const float* __restrict__ jlT, int nc, float dj, float shift, float scale,
+               AdjFaces32 f, Geo g) {
+  constexpr int T_TILE = 32 * VEC;
+  const int nvec = g.Np / VEC;
   for (int v = blockIdx.x * NT + threadIdx.x; v < nvec; v += gridDim.x * NT) {
-    const Row4 R = row4_of(v, g);
+    const RowV<VEC> R = rowv_of<VEC>(v, g);
     const int ip0 = R.ip0;
     const size_t base = (size_t)(ip0 / T_TILE) * nc * T_TILE + (ip0 % T_TILE);
-    float sc[4], a[4], cf[4], nb[4], m4[4];
-    ldv<float, 4>(sc, s_in + ip0);
-    const bool has_w = R.ix0 > 0, has_e = R.ix0 + 4 < g.nx;
-    const float sw = has_w ? s_in[ip0 - 1] : 0.0f;
-    const float se = has_e ? s_in[ip0 + 4] : 0.0f;
-    ldv<float, 4>(cf, jlT + base);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = (cf[j] - shift) * sc[j];
-    ldv<float, 4>(cf, jlT + base + T_TILE);       // west neighbour's coupling
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], j > 0 ? sc[j - 1] : sw, a[j]);
-    ldv<float, 4>(cf, jlT + base + 2 * T_TILE);   // east
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], j < 3 ? sc[j + 1] : se, a[j]);
-    float sn[4] = {0, 0, 0, 0}, st[4] = {0, 0, 0, 0};
-    if (R.iy > 0) {
-      ldv<float, 4>(cf, jlT + base + 3 * T_TILE);
-      ldv<float, 4>(nb, s_in + ip0 - g.px);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], nb[j], a[j]);
-    }
-    if (R.iy < g.ny - 1) {
-      ldv<float, 4>(cf, jlT + base + 4 * T_TILE);
-      ldv<float, 4>(sn, s_in + ip0 + g.px);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], sn[j], a[j]);
-    }
+    const bool has_w = R.ix0 > 0, has_e = R.ix0 + VEC < g.nx;
+    const bool has_s = R.iy > 0, has_n = R.iy < g.ny - 1;
+    const bool has_b = g.dim == 3 && R.iz > 0, has_t = g.dim == 3 && R.iz < g.nz - 1;
+    const int oS = has_s ? -g.px : 0, oN = has_n ? g.px : 0;
+    const int oB = has_b ? -g.plane : 0, oT = has_t ? g.plane : 0;
+    float sc[VEC], sS[VEC], sN[VEC], sB[VEC], sT[VEC], cf[7][VEC], m4[VEC];
+    ldv<float, VEC>(sc, s_in + ip0);
+    ldv<float, VEC>(sS, s_in + ip0 + oS);
+    ldv<float, VEC>(sN, s_in + ip0 + oN);
     if (g.dim == 3) {
-      if (R.iz > 0) {
-        ldv<float, 4>(cf, jlT + base + 5 * T_TILE);
-        ldv<float, 4>(nb, s_in + ip0 - g.plane);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], nb[j], a[j]);
-      }
-      if (R.iz < g.nz - 1) {
-        ldv<float, 4>(cf, jlT + base + 6 * T_TILE);
-        ldv<float, 4>(st, s_in + ip0 + g.plane);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a[j] = fmaf(cf[j], st[j], a[j]);
-      }
+      ldv<float, VEC>(sB, s_in + ip0 + oB);
+      ldv<float, VEC>(sT, s_in + ip0 + oT);
     }
-    ldv<float, 4>(m4, mu + ip0);
+    const float sw = s_in[ip0 - (has_w ? 1 : 0)];
+    const float se = s_in[ip0 + (has_e ? VEC : 0)];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a[j] = R.ix0 + j < g.nx ? fmaf(dj, m4[j], a[j]) : 0.0f;
-    stv<float, 4>(s_out + ip0, a);
+    for (int k = 0; k < 7; ++k)
+      if (k < nc) ldv<float, VEC>(cf[k], jlT + base + k * T_TILE);
+    ldv<float, VEC>(m4, mu + ip0);
+    float a[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      float x = (cf[0][j] - shift) * sc[j];
+      x = fmaf(cf[1][j], j > 0 ? sc[j - 1] : (has_w ? sw : 0.0f), x);
+      x = fmaf(cf[2][j], j < VEC - 1 ? sc[j + 1] : (has_e ? se : 0.0f), x);
+      x = fmaf(cf[3][j], sS[j], x);
+      x = fmaf(cf[4][j], sN[j], x);
+      if (g.dim == 3) {
+        x = fmaf(cf[5][j], sB[j], x);
+        x = fmaf(cf[6][j], sT[j], x);
+      }
+      a[j] = R.ix0 + j < g.nx ? fmaf(dj, m4[j], x) : 0.0f;
+    }
+    stv<float, VEC>(s_out + ip0, a);
 
     // face derivative of the pair (s_in, q_j)
-    float ic[4], x4[4], yc[4], gs[4];
-    ldv<float, 4>(ic, f.icap + ip0);
-    ldv<float, 4>(x4, q + ip0);
-    const uchar4 fl4 = *reinterpret_cast<const uchar4*>(f.up + ip0);
-    const unsigned fl[4] = {fl4.x, fl4.y, fl4.z, fl4.w};
+    float ic[VEC], x4[VEC], yc[VEC], gs[VEC], icN[VEC], xN[VEC];
+    unsigned fl[VEC];
+    ldv<float, VEC>(ic, f.icap + ip0);
+    ldv<float, VEC>(x4, q + ip0);
+    ld_flags<VEC>(fl, f.up + ip0);
+    const float ice = f.icap[ip0 + (has_e ? VEC : 0)];
+    const float qe = q[ip0 + (has_e ? VEC : 0)];
+    ldv<float, VEC>(gs, f.gx + ip0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) yc[j] = sc[j] * ic[j];
-    const float ye = has_e ? se * f.icap[ip0 + 4] : 0.0f;
-    const float qe = has_e ? q[ip0 + 4] : 0.0f;
-    ldv<float, 4>(gs, f.gx + ip0);
+    for (int j = 0; j < VEC; ++j) yc[j] = sc[j] * ic[j];
+    const float ye = has_e ? se * ice : 0.0f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < VEC; ++j) {
       const int ix = R.ix0 + j;
       if (ix < g.nx - 1) {
-        const float yr = j < 3 ? yc[j + 1] : ye;
-        const float xu = (fl[j] & 1u) ? x4[j] : (j < 3 ? x4[j + 1] : qe);
+        const float yr = j < VEC - 1 ? yc[j + 1] : ye;
+        const float xu = (fl[j] & 1u) ? x4[j] : (j < VEC - 1 ? x4[j + 1] : qe);
         gs[j] += scale * ((yr - yc[j]) * xu);
       } else if (ix == g.nx - 1) {
         gs[j] -= scale * (yc[j] * x4[j]);
       }
     }
-    stv<float, 4>(f.gx + ip0, gs);
-    if (R.iy < g.ny - 1) {
-      float icn[4], xn[4];
-      ldv<float, 4>(icn, f.icap + ip0 + g.px);
-      ldv<float, 4>(xn, q + ip0 + g.px);
-      ldv<float, 4>(gs, f.gy + ip0);
+    stv<float, VEC>(f.gx + ip0, gs);
+    if (has_n) {
+      ldv<float, VEC>(icN, f.icap + ip0 + g.px);
+      ldv<float, VEC>(xN, q + ip0 + g.px);
+      ldv<float, VEC>(gs, f.gy + ip0);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < VEC; ++j)
         if (R.ix0 + j < g.nx) {
-          const float xu = (fl[j] & 2u) ? x4[j] : xn[j];
-          gs[j] += scale * (fmaf(sn[j], icn[j], -yc[j]) * xu);
+          const float xu = (fl[j] & 2u) ? x4[j] : xN[j];
+          gs[j] += scale * (fmaf(sN[j], icN[j], -yc[j]) * xu);
         }
-      stv<float, 4>(f.gy + ip0, gs);
+      stv<float, VEC>(f.gy + ip0, gs);
     }
-    if (g.dim == 3 && R.iz < g.nz - 1) {
-      float icn[4], xn[4];
-      ldv<float, 4>(icn, f.icap + ip0 + g.plane);
-      ldv<float, 4>(xn, q + ip0 + g.plane);
-      ldv<float, 4>(gs, f.gz + ip0);
+    if (has_t) {
+      ldv<float, VEC>(icN, f.icap + ip0 + g.plane);
+      ldv<float, VEC>(xN, q + ip0 + g.plane);
+      ldv<float, VEC>(gs, f.gz + ip0);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < VEC; ++j)
         if (R.ix0 + j < g.nx) {
-          const float xu = (fl[j] & 4u) ? x4[j] : xn[j];
-          gs[j] += scale * (fmaf(st[j], icn[j], -yc[j]) * xu);
+          const float xu = (fl[j] & 4u) ? x4[j] : xN[j];
+          gs[j] += scale * (fmaf(sT[j], icN[j], -yc[j]) * xu);
         }
-      stv<float, 4>(f.gz + ip0, gs);
+      stv<float, VEC>(f.gz + ip0, gs);
     }
     if (R.ix0 == 0 && (fl[0] & 8u)) f.g0[R.iy + g.ny * R.iz] += (double)(scale * (yc[0] * x4[0]));
   }
@@ -1590,7 +1620,7 @@ __global__ void k_pc_setup(PresArr a, PcArr p, float* __restrict__ diag32, Geo g
   }
 }
 
-// One Chebyshev step, four cells of a padded row per thread (Row4).  FIRST:
+// One Chebyshev step, four cells of a padded row per thread (RowV<4>).  FIRST:
 // z_1 = D^-1 r / theta (c2 = 1/theta) and the FP32 copy of r.  Otherwise
 // z_{j+1} = z_j + c1 (z_j - z_{j-1}) + c2 (D^-1 (r + N z_j) - z_j), A = D - N.
 // LAST: also (z, r) and (z, A d) -> beta (zero on the first pass after the
@@ -1604,7 +1634,7 @@ __global__ void k_pc_sweep(PresArr a, PcArr p, const float* __restrict__ zprev,
   double rz = 0.0, zad = 0.0;
   const int nvec = g.Np / 4;
   for (int v = blockIdx.x * NT + threadIdx.x; v < nvec; v += gridDim.x * NT) {
-    const Row4 R = row4_of(v, g);
+    const RowV<4> R = rowv_of<4>(v, g);
     const int ip0 = R.ip0;
     float zn[4], di[4];
     ldv<float, 4>(di, p.dinv + ip0);
@@ -2753,15 +2783,31 @@ void term_launch(const erem_ctx* c, int m, const Tq* qi, Tq* qo, double cg, cuda
   const Geo g = geo_of(c);
   const int nb = std::min(grid_for(c, c->Np / VEC), c->term_grid);
   ++c->launches;
+  // every term after the first may start as a programmatic dependent of the
+  // one before it (the grid is one resident wave, so all of the previous
+  // grid's blocks have started when it is scheduled)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = (c->pdl && m > 1) ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   if (m == 1)
-    k_leja_term1<Tq, VEC, DIM><<<nb, NT, 0, s>>>(qi, qo, c->P, c->p0, cf, g, c->xi_dev, c->dd_dev,
-                                                 cg, c->red_part, c->red_cnt, c->ctrl);
+    cudaLaunchKernelEx(&cfg, k_leja_term1<Tq, VEC, DIM>, qi, qo, c->P, c->p0, cf, g,
+                       (const double*)c->xi_dev, (const double*)c->dd_dev, cg, c->red_part,
+                       c->red_cnt, c->ctrl);
   else if (m & 1)
-    k_leja_term<Tq, VEC, DIM, 1><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
-                                                   c->red_part, c->red_cnt, c->ctrl);
+    cudaLaunchKernelEx(&cfg, k_leja_term<Tq, VEC, DIM, 1>, qi, qo, c->P, cf, g,
+                       (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
+                       c->red_cnt, c->ctrl);
   else
-    k_leja_term<Tq, VEC, DIM, 0><<<nb, NT, 0, s>>>(qi, qo, c->P, cf, g, c->xi_dev, c->dd_dev, cg, m,
-                                                   c->red_part, c->red_cnt, c->ctrl);
+    cudaLaunchKernelEx(&cfg, k_leja_term<Tq, VEC, DIM, 0>, qi, qo, c->P, cf, g,
+                       (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
+                       c->red_cnt, c->ctrl);
 }
 
 // One Leja term with explicit input/output vectors (the context's ping-pong
@@ -3252,7 +3298,9 @@ void launch_adj_scale_jlT(const erem_ctx* c, double sc, cudaStream_t s) {
   jc.b0 = nullptr;
   const int nc = c->dim == 3 ? 7 : 5;
   ++c->launches;
-  if (c->prec == EREM_FP32_BULK)
+  if (c->prec == EREM_FP32_BULK && c->adj_vec == 2)
+    k_adj_scale_jlT<float, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jlT_all, sc, geo_of(c), nc);
+  else if (c->prec == EREM_FP32_BULK)
     k_adj_scale_jlT<float, 128><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jlT_all, sc, geo_of(c), nc);
   else
     k_adj_scale_jlT<double, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (double*)c->jlT_all, sc, geo_of(c), nc);
@@ -3289,14 +3337,42 @@ void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const d
     (void)faces;
     const AdjFaces32 f{c->adj_up, c->adj_icap32, c->adj_g32[0], c->adj_g32[1], c->adj_g32[2],
                        c->adj_g0};
-    k_adj_horner32<128><<<grid_for(c, c->Np / 4), NT, 0, s>>>(
-        (const float*)s_in, (float*)s_out, c->adj_mu32, (const float*)q, (const float*)c->jlT_all,
-        nc, (float)dj, (float)shift, (float)scale, f, geo_of(c));
+    const int vec = c->adj_vec;
+    const int nb = (int)std::min<long long>((c->Np / vec + NT - 1) / NT,
+                                            (long long)c->adj_blocks_per_sm * c->sm_count);
+    if (vec == 2)
+      k_adj_horner32<2><<<nb, NT, 0, s>>>((const float*)s_in, (float*)s_out, c->adj_mu32,
+                                          (const float*)q, (const float*)c->jlT_all, nc, (float)dj,
+                                          (float)shift, (float)scale, f, geo_of(c));
+    else
+      k_adj_horner32<4><<<nb, NT, 0, s>>>((const float*)s_in, (float*)s_out, c->adj_mu32,
+                                          (const float*)q, (const float*)c->jlT_all, nc, (float)dj,
+                                          (float)shift, (float)scale, f, geo_of(c));
   } else
     k_adj_horner<double><<<blocks_cells(c), NT, 0, s>>>((const double*)s_in, (double*)s_out, mu,
                                                         (const double*)q, (const double*)c->jlT_all,
                                                         64, nc, dj, shift, scale, faces, adj_faces(c),
                                                         geo_of(c));
+}
+
+// Cells per thread of the FP32 Horner pass, and its resident blocks per SM:
+// four cells per thread unless the grid is so small that the last round of a
+// resident wave would run mostly empty (at 128^3: 3.4 rounds of four cells,
+// 6.7 of two), then two.
+void choose_adj_vec(erem_ctx* c) {
+  int b4 = 0, b2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_adj_horner32<4>, NT, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_adj_horner32<2>, NT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    b4 = b2 = 4;
+  }
+  b4 = std::max(b4, 1);
+  b2 = std::max(b2, 1);
+  const double r4 = (double)c->Np / 4 / ((double)b4 * c->sm_count * NT);
+  const double r2 = (double)c->Np / 2 / ((double)b2 * c->sm_count * NT);
+  const double e4 = r4 / std::ceil(r4), e2 = r2 / std::ceil(r2);
+  c->adj_vec = e2 > e4 + 0.03 ? 2 : 4;
+  c->adj_blocks_per_sm = c->adj_vec == 2 ? b2 : b4;
 }
 
 void launch_adj_aux32(const erem_ctx* c, cudaStream_t s) {
