@@ -102,7 +102,8 @@ typedef struct {
   const int* replay;    /* host array [s, m_1..m_s] forcing the substep count
                            and the degrees, or NULL for the stopping rule     */
   int n_replay;         /* entries in replay (1 + s)                          */
-  int time_terms;       /* nonzero: time every Leja term with CUDA events     */
+  int time_terms;       /* nonzero: time the Leja launches with CUDA events,
+                           one pair around each chunk of launches            */
 } erem_leja_opts;
 
 typedef struct {
@@ -116,10 +117,13 @@ typedef struct {
   double flux_in;       /* pressure_solve: net Darcy inflow through x = 0     */
   double vmax;          /* pressure_solve: largest |face flux| / face area    */
   double t_ms;          /* wall time of the call, milliseconds                */
-  double t_terms_ms;    /* time_terms: summed device time of the Leja kernels */
-  int n_terms_timed;    /* time_terms: Leja terms those launches computed     */
+  double t_terms_ms;    /* time_terms: summed device time of the chunks of
+                           Leja launches (gaps between launches and launches
+                           that returned at once after the stop included)    */
+  int n_terms_timed;    /* time_terms: Leja terms those chunks computed       */
   int launches;         /* CUDA kernels this call launched                    */
-  int n_launches_timed; /* time_terms: Leja kernel launches in t_terms_ms     */
+  int n_launches_timed; /* time_terms: Leja kernel launches in t_terms_ms
+                           (those after the stop included)                   */
   int degree_phi2;      /* erem_step_forced: degree of the phi_2 interpolation */
 } erem_stats;
 

@@ -470,20 +470,23 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
   }
   int m = 1, qin = 0;
   int chunk = forced ? forced : std::max(4, c->last_degree + 2);
-  // the first term of every launch of this interpolation, in order
-  std::vector<int> launches;
+  // the terms [first, last] of every chunk of launches, in order; with
+  // time_terms a pair of events brackets each chunk (not each launch: an
+  // event between two terms would stop the next one from being scheduled
+  // while the previous one ends)
+  std::vector<std::pair<int, int>> chunks;
   while (true) {
     const int end = forced ? forced : std::min(*M_avail, m + chunk - 1);
+    if (o.time_terms) cudaEventRecord(c->ev[2 * chunks.size()], s);
     for (int mm = m; mm <= end; ++mm) {
-      if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size()], s);
       if (slot0)
         launch_leja_term_ptr(c, mm, slot0 + (size_t)(mm - 1) * qbytes, slot0 + (size_t)mm * qbytes,
                              cg, s);
       else launch_leja_term(c, mm, qin, cg, s);
-      if (o.time_terms) cudaEventRecord(c->ev[2 * launches.size() + 1], s);
-      launches.push_back(mm);
       qin ^= 1;
     }
+    if (o.time_terms) cudaEventRecord(c->ev[2 * chunks.size() + 1], s);
+    chunks.emplace_back(m, end);
     EREM_TRY(check_launch(c, "leja term"));
     EREM_TRY(read_ctrl(c, s));
     EREM_TRY(check_flags(c));
@@ -523,13 +526,17 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     chunk = 8;
   }
   if (o.time_terms && tt) {
-    for (size_t j = 0; j < launches.size(); ++j) {
-      if (launches[j] > *degree) break;  // returned at once: the test had passed
+    // a chunk's time includes its launches after the stop (they return at
+    // once) and the gaps between launches: per computed term it is an upper
+    // bound of the term kernel's own time
+    for (size_t j = 0; j < chunks.size(); ++j) {
+      const int first = chunks[j].first, last = chunks[j].second;
+      if (first > *degree) break;  // every launch returned at once
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, c->ev[2 * j], c->ev[2 * j + 1]) == cudaSuccess) {
         tt->ms += ms;
-        tt->terms += 1;
-        ++tt->launches;
+        tt->terms += std::min(last, *degree) - first + 1;
+        tt->launches += last - first + 1;
       }
     }
   }
