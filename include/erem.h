@@ -55,7 +55,7 @@ typedef enum {
   EREM_EINVAL = 1,     /* bad argument, or physically invalid input field    */
   EREM_ENOMEM = 2,     /* device or pinned host allocation failed            */
   EREM_ENOTCONV = 3,   /* Leja interpolation or linear solver did not converge */
-  EREM_ETIMEOUT = 4,   /* an iteration bound ran out (the batched loop)      */
+  EREM_ETIMEOUT = 4,   /* a pass bound ran out (a batched ensemble member)    */
   EREM_ENONFINITE = 5, /* NaN or Inf in an input or an intermediate result   */
   EREM_ECUDA = 6       /* CUDA runtime error (message in erem_last_error)    */
 } erem_status;
@@ -555,14 +555,17 @@ EREM_API int erem_phi1_divided_differences(int M, const double* xi, double c,
  * member), and one run advances every member by the same number of steps.
  *
  * On the device every member is a small state machine (G(T^n) -> Leja terms
- * with the stopping test of §4.2 -> substep bookkeeping -> T^{n+1}), and one
- * launch of the batched kernel advances every active member by one pass over
- * its own cells, so members proceed at their own Leja degrees and substep
- * counts.  Stopping, substep doubling and the end of the run are decided on
- * the device; a run is one launch of a CUDA graph whose conditional WHILE
- * node repeats the kernel until every member has finished.  The loop is
- * bounded: a run stops after steps * (sum over substep levels of
- * 2^l (m_max + 2) + 2) iterations at most (EREM_ETIMEOUT).
+ * with the stopping test of §4.2 -> substep bookkeeping -> T^{n+1}) whose
+ * phases are passes over the member's cells.  One launch runs the whole
+ * run: a persistent grid of thread-block clusters takes members from a queue
+ * (heaviest first) and each cluster runs its member through every step,
+ * with the cluster barrier between passes and the pass's reduction shared
+ * through distributed shared memory, so members proceed at their own Leja
+ * degrees and substep counts and a member's Leja vectors and coefficients
+ * stay in L2 while its cluster works on it.  Stopping, substep doubling and
+ * the end of the run are decided on the device.  A member is bounded: it
+ * stops after steps * (sum over substep levels of 2^l (m_max + 2) + 2) + 2
+ * passes at most (EREM_ETIMEOUT).
  * ------------------------------------------------------------------------ */
 typedef struct erem_ens erem_ens;
 
@@ -574,15 +577,16 @@ typedef enum { EREM_ENS_KEEP_SUBSTEPS = 0, EREM_ENS_RESTART_SUBSTEPS = 1 } erem_
 
 typedef struct {
   int substep_policy;  /* erem_ens_policy (default KEEP)                    */
-  int tile_vecs;       /* thread-vectors per thread and tile: 1, 2 or 4;
-                          0 = 2, or the value erem_ensemble_autotune chose  */
-  int blocks_per_sm;   /* 0: as many as fit (occupancy)                    */
-  int use_graph;       /* 1: one graph launch per run; 0: the host launches
-                          the kernel in batches and reads a flag between   */
+  int cluster_ctas;    /* CTAs of the cluster that runs one member: 2, 4, 8
+                          or 16; 0 = 8, or the size erem_ensemble_autotune
+                          chose                                             */
+  int max_clusters;    /* 0: as many clusters as fit on the device at once */
+  int reserved;        /* must be 0                                        */
 } erem_ens_config;
 
 typedef struct {
-  int status;          /* EREM_OK, EREM_ENOTCONV or EREM_ENONFINITE        */
+  int status;          /* EREM_OK, EREM_ENOTCONV, EREM_ENONFINITE or
+                          EREM_ETIMEOUT                                     */
   int steps_done;      /* steps of the last run this member completed     */
   int substeps;        /* substeps of its last completed step              */
   int degree_total;    /* sum of that step's degrees                       */
@@ -597,11 +601,15 @@ typedef struct {
 
 typedef struct {
   double t_ms;           /* device time of the last run (CUDA events)      */
-  long long iterations;  /* launches of the batched kernel in the last run */
+  long long passes;      /* passes over member cells in the last run, summed
+                            over members (Leja terms and the other passes) */
   long long cells;       /* sum of the members' cells                      */
   long long cell_terms;  /* sum over members of cells x Leja terms         */
   long long cell_passes; /* sum over members of cells x other passes       */
-  int tile_vecs, grid, use_graph, members_failed;
+  int cluster_ctas;      /* CTAs per cluster of the last run                */
+  int clusters;          /* clusters launched (resident at once)           */
+  int cta_threads;       /* threads per CTA                                */
+  int members_failed;
 } erem_ens_run_stats;
 
 /* Create an ensemble of n_members 2D members (grids[e].dim must be 2),
@@ -630,23 +638,29 @@ EREM_API erem_status erem_ensemble_set_temperature(erem_ens* ens, int e, const d
 /* Copy member e's current temperature into T [N_e] (device or host). */
 EREM_API erem_status erem_ensemble_get_member(erem_ens* ens, int e, double* T, void* stream);
 
-/* Leja options (as for erem_step; replay and time_terms are not accepted)
- * and batching configuration; either pointer may be NULL (defaults). */
+/* Leja options (as for erem_step; replay and time_terms are not accepted,
+ * avg_window is at most 64) and batching configuration; either pointer may
+ * be NULL (defaults). */
 EREM_API erem_status erem_ensemble_configure(erem_ens* ens, const erem_leja_opts* opts,
                                              const erem_ens_config* cfg);
 
-/* Tile-size and substep autotuner: runs probe_steps steps of the whole
- * ensemble for each tile size (1, 2, 4 thread-vectors per thread), keeps the
- * fastest, and restores every member's temperature afterwards.  Under the
- * KEEP policy each member then starts at the substep count its first probe
- * step passed with (the count erem_step would also reach, by doubling).
- * Errors as erem_ensemble_run. */
+/* Cluster-size and substep autotuner: runs probe_steps steps of the whole
+ * ensemble once to learn every member's substep level and work (the queue
+ * order), then once for each cluster size that fits the device (2, 4, 8, 16
+ * CTAs), keeps the fastest, and restores every member's temperature
+ * afterwards.  Under the KEEP policy each member then starts at the substep
+ * count its first probe step passed with (the count erem_step would also
+ * reach, by doubling).  Errors as erem_ensemble_run. */
 EREM_API erem_status erem_ensemble_autotune(erem_ens* ens, int probe_steps, void* stream);
 
-/* Advance every member by `steps` EREM steps (one graph launch).  Returns
- * when the run is complete.  A member that fails keeps the temperature of
- * the start of its failing step and stops; the call then returns the first
- * failing member's status (ENOTCONV or ENONFINITE) and
+/* Advance every member by `steps` EREM steps (one kernel launch).  Returns
+ * when the run is complete.  A member whose Leja interpolation fails (the
+ * stopping test not met within m_max terms, or a non-finite estimate: the
+ * Newton vectors left the range of the Leja precision) takes its step again
+ * at twice the substeps, up to max_doublings times.  A member that fails
+ * beyond that, or whose state is not finite, keeps the temperature of the
+ * start of its failing step and stops; the call then returns the first
+ * failing member's status (ENOTCONV, ENONFINITE or ETIMEOUT) and
  * erem_ensemble_member_stats tells which members failed.
  * Errors: EINVAL (a member without state), ENOTCONV, ENONFINITE, ETIMEOUT,
  * ECUDA. */

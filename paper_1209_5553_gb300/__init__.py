@@ -104,8 +104,8 @@ EREM_ENS_KEEP_SUBSTEPS, EREM_ENS_RESTART_SUBSTEPS = 0, 1
 
 
 class erem_ens_config(ctypes.Structure):
-    _fields_ = [("substep_policy", ctypes.c_int), ("tile_vecs", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int)]
+    _fields_ = [("substep_policy", ctypes.c_int), ("cluster_ctas", ctypes.c_int),
+                ("max_clusters", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class erem_ens_member_stats(ctypes.Structure):
@@ -121,10 +121,10 @@ class erem_ens_member_stats(ctypes.Structure):
 
 
 class erem_ens_run_stats(ctypes.Structure):
-    _fields_ = [("t_ms", ctypes.c_double), ("iterations", ctypes.c_longlong),
+    _fields_ = [("t_ms", ctypes.c_double), ("passes", ctypes.c_longlong),
                 ("cells", ctypes.c_longlong), ("cell_terms", ctypes.c_longlong),
-                ("cell_passes", ctypes.c_longlong), ("tile_vecs", ctypes.c_int),
-                ("grid", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("cell_passes", ctypes.c_longlong), ("cluster_ctas", ctypes.c_int),
+                ("clusters", ctypes.c_int), ("cta_threads", ctypes.c_int),
                 ("members_failed", ctypes.c_int)]
 
 
@@ -738,9 +738,8 @@ class Ensemble:
     def get_member(self, e, T, stream=None):
         erem_ensemble_get_member(self._h, e, self.sizes[e], T, stream)
 
-    def configure(self, opts=None, policy=EREM_ENS_KEEP_SUBSTEPS, tile_vecs=0, blocks_per_sm=0,
-                  use_graph=True):
-        cfg = erem_ens_config(int(policy), int(tile_vecs), int(blocks_per_sm), 1 if use_graph else 0)
+    def configure(self, opts=None, policy=EREM_ENS_KEEP_SUBSTEPS, cluster_ctas=0, max_clusters=0):
+        cfg = erem_ens_config(int(policy), int(cluster_ctas), int(max_clusters), 0)
         erem_ensemble_configure(self._h, opts, cfg)
 
     def autotune(self, probe_steps=1, stream=None):

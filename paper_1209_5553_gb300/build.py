@@ -20,8 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liberem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "abi.cpp", "ensemble.cpp", "leja_host.cpp", "noalloc.cu"]
-HEADERS = ["erem_internal.h", "device_common.cuh", "ensemble_kernel.cuh"]
+SOURCES = ["kernels.cu", "ensemble_cluster.cu", "abi.cpp", "ensemble.cpp", "leja_host.cpp", "noalloc.cu"]
+HEADERS = ["erem_internal.h", "device_common.cuh"]
 
 
 def _cuda_home() -> str:

@@ -65,14 +65,13 @@ struct Ctrl {
 };
 
 // ---------------------------------------------------------------------------
-// Batched ensemble of independent 2D members (ensemble.cpp, k_ens_iter).
+// Batched ensemble of independent 2D members (ensemble.cpp,
+// ensemble_cluster.cu).
 //
 // Every member runs the same EREM step as a single context, as a state
-// machine: one pass over the member's tiles per iteration of the batched
-// kernel, in the phase its state names.  The last block of a member's pass
-// advances the phase; the last block of the whole launch rebuilds the list of
-// active members when one has finished and tells the graph loop whether to go
-// on.
+// machine whose phases are the passes over the member's cells; one
+// thread-block cluster runs a member's whole run, pass after pass, with the
+// cluster barrier between passes.
 // ---------------------------------------------------------------------------
 enum : int {
   ENS_INIT = 0,   // G = J T^n + b, ||T^n||_inf, first substep's q_0 and P
@@ -82,10 +81,11 @@ enum : int {
   ENS_FINAL,      // T^{n+1} = T^n + w + delta P
   ENS_RESTART,    // substeps doubled after a failure: q_0 = G, P = d_0 G
   ENS_DONE,       // all steps of the run taken
-  ENS_FAILED      // stopped: not converged at the last level, or non-finite
+  ENS_FAILED      // stopped: not converged at the last level, non-finite, or out of passes
 };
-enum : int { ENS_OK = 0, ENS_NOTCONV = 1, ENS_NONFINITE = 2 };
+enum : int { ENS_OK = 0, ENS_NOTCONV = 1, ENS_NONFINITE = 2, ENS_TIMEOUT = 3 };
 constexpr int kEnsMaxLevels = 7;   // substeps 1, 2, .., 64
+constexpr int kEnsWin = 64;        // largest averaging window of the batched stopping test
 
 struct EnsState {
   int phase;      // ENS_*
@@ -93,7 +93,7 @@ struct EnsState {
   int sub;        // substep in progress
   int step;       // steps completed in this run
   int target;     // steps of this run
-  int status;     // ENS_OK, ENS_NOTCONV, ENS_NONFINITE
+  int status;     // ENS_OK, ENS_NOTCONV, ENS_NONFINITE, ENS_TIMEOUT
   int terms;      // Leja terms evaluated in this run, failed attempts included
   int attempts;   // failed attempts (substep doublings) in this run
   int last_S;     // substeps of the last completed step
@@ -104,38 +104,28 @@ struct EnsState {
 
 struct EnsMember {
   int nx, ny, px, Np;   // 2D geometry, padded pitch
-  int tiles;            // tiles of this member
-  int pad[3];
   const double* jc[5];  // FP64 cell form of J: D W E S N (padded)
   const double* b0;     // constant part of G at the x = 0 cells (ny)
   const void* jl;       // Leja copy of J (context precision, interleaved)
   double *T, *G, *w, *P;
   void* q[2];
-  double* part;         // kRedSlots doubles per tile
-  unsigned* cnt;        // tile ticket
-  Ctrl* ctrl;           // stopping test state
-  EnsState* st;
   const double* dd;     // kEnsMaxLevels tables of mmax + 1 divided differences
-  StopParams sp;        // delta of level 0 (= dt)
+  StopParams sp;        // tolerances, window, m_max (delta unused)
   double dt, cg;        // step, c / gamma
 };
 
-struct EnsLaunch {
-  int prec;         // EREM_FP64 or EREM_FP32_BULK
-  int U;            // thread-vectors per thread in one tile
-  int grid;         // blocks
-  int n_members;
-  int nlev;         // substep levels allowed (max_doublings + 1)
-  int mmax;         // entries per divided-difference table - 1
-  int restart;      // 1: each step starts again from one substep
-  int max_iters;    // bound on loop iterations of one run
-  const EnsMember* mem;
-  const double* xi;
-  // act[0] active members, act[1] their tiles, act[2] list stale, act[3]
-  // loop goes on; then act_member[n_members], act_start[n_members + 1]
-  int* act;
-  unsigned* gcnt;   // launch ticket
-  unsigned* iters;  // iterations taken
+// Arguments of one run of the batched kernel.
+struct EnsRun {
+  const EnsMember* mem;   // [n]
+  EnsState* st;           // [n]: level and target in, statistics out
+  const int* order;       // [n]: members in the order the clusters take them
+  unsigned* next;         // queue position (0 at launch)
+  const double* xi;       // Leja points, mmax + 1
+  int n;
+  int nlev;               // substep levels allowed (max_doublings + 1)
+  int mmax;               // entries per divided-difference table - 1
+  int restart;            // 1: each step starts again from one substep
+  long long passes_per_step;  // bound on a member's passes per step
 };
 
 // Krylov (Arnoldi) phi_1: device scalars of one basis (kernels.cu,
@@ -409,13 +399,10 @@ void launch_bicg_init(const erem_ctx* c, const double* b, double sigma, double t
                       cudaStream_t s);
 void launch_bicg_iter(const erem_ctx* c, double sigma, cudaStream_t s);
 
-// batched ensemble
-int ens_tile_cells(int prec, int U);
-int ens_blocks_per_sm(int prec, int U);
-void launch_ens_iter(const EnsLaunch& L, cudaStream_t s);
-// Graph with one conditional WHILE node whose body is the batched kernel;
-// the kernel ends the loop.
-cudaError_t build_ens_graph(const EnsLaunch& L, cudaGraph_t* graph, cudaGraphExec_t* exec);
+// batched ensemble (ensemble_cluster.cu): one cluster of cs CTAs per member
+int ens_cta_threads();
+cudaError_t ens_max_clusters(int prec, int cs, int* n);
+cudaError_t launch_ens_cluster(const EnsRun& R, int prec, int cs, int clusters, cudaStream_t s);
 void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s);
 
 // Krylov (Arnoldi, modified Gram-Schmidt) passes, FP64

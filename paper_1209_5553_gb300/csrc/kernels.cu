@@ -16,7 +16,6 @@
 
 #include "erem_internal.h"
 #include "device_common.cuh"
-#include "ensemble_kernel.cuh"
 
 namespace erem {
 namespace {
@@ -3178,79 +3177,6 @@ void launch_bicg_iter(const erem_ctx* c, double sigma, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // batched ensemble
 // ---------------------------------------------------------------------------
-int ens_tile_cells(int prec, int U) { return U * NT * (prec == EREM_FP32_BULK ? 4 : 2); }
-
-template <typename F>
-static void ens_dispatch(int prec, int U, F&& f) {
-  if (prec == EREM_FP32_BULK) {
-    if (U == 1) f(k_ens_iter<float, 4, 1>);
-    else if (U == 2) f(k_ens_iter<float, 4, 2>);
-    else f(k_ens_iter<float, 4, 4>);
-  } else {
-    if (U == 1) f(k_ens_iter<double, 2, 1>);
-    else if (U == 2) f(k_ens_iter<double, 2, 2>);
-    else f(k_ens_iter<double, 2, 4>);
-  }
-}
-
-int ens_blocks_per_sm(int prec, int U) {
-  int n = 0;
-  cudaError_t e = cudaSuccess;
-  ens_dispatch(prec, U, [&](auto kern) { e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, 0); });
-  if (e != cudaSuccess || n < 1) {
-    cudaGetLastError();
-    n = 2;
-  }
-  return n;
-}
-
-void launch_ens_iter(const EnsLaunch& L, cudaStream_t s) {
-  ens_dispatch(L.prec, L.U, [&](auto kern) { kern<<<L.grid, NT, 0, s>>>(L, 0ULL, 0); });
-}
-
-cudaError_t build_ens_graph(const EnsLaunch& L, cudaGraph_t* graph, cudaGraphExec_t* exec) {
-  *graph = nullptr;
-  *exec = nullptr;
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  if (e != cudaSuccess) return e;
-  cudaGraphConditionalHandle h;
-  // the loop condition is 1 at every launch of the graph; the kernel's last
-  // block sets it after each iteration
-  e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
-  cudaGraphNode_t node = nullptr;
-  cudaGraphNodeParams cp{};
-  if (e == cudaSuccess) {
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
-  }
-  if (e == cudaSuccess) {
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    EnsLaunch Lc = L;
-    int use = 1;
-    void* args[3] = {&Lc, &h, &use};
-    cudaKernelNodeParams kp{};
-    ens_dispatch(L.prec, L.U, [&](auto kern) { kp.func = (void*)kern; });
-    kp.gridDim = dim3(L.grid);
-    kp.blockDim = dim3(NT);
-    kp.sharedMemBytes = 0;
-    kp.kernelParams = args;
-    cudaGraphNode_t kn;
-    e = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp);
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    *exec = nullptr;
-    return e;
-  }
-  *graph = g;
-  return cudaSuccess;
-}
-
 void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream_t s) {
   ++c->launches;
   k_unpack<<<blocks_cells(c), NT, 0, s>>>(src, dst, geo_of(c));

@@ -60,7 +60,7 @@ def test_ensemble_struct_layouts_match_the_c_compiler(E, tmp_path):
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "erem.h"\n'
                    'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(erem_ens_config), '
                    'sizeof(erem_ens_member_stats), sizeof(erem_ens_run_stats), '
-                   'offsetof(erem_ens_member_stats, alpha), offsetof(erem_ens_run_stats, tile_vecs)); '
+                   'offsetof(erem_ens_member_stats, alpha), offsetof(erem_ens_run_stats, cluster_ctas)); '
                    'return 0; }\n')
     exe = tmp_path / "sizes"
     import subprocess
@@ -70,7 +70,7 @@ def test_ensemble_struct_layouts_match_the_c_compiler(E, tmp_path):
                                           check=True).stdout.split()]
     assert got == [ctypes.sizeof(E.erem_ens_config), ctypes.sizeof(E.erem_ens_member_stats),
                    ctypes.sizeof(E.erem_ens_run_stats), E.erem_ens_member_stats.alpha.offset,
-                   E.erem_ens_run_stats.tile_vecs.offset]
+                   E.erem_ens_run_stats.cluster_ctas.offset]
 
 
 def test_krylov_struct_layouts_and_defaults(E, tmp_path):

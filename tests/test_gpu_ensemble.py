@@ -1,7 +1,7 @@
 """Batched ensemble (erem_ensemble_*) against the oracle.
 
 Seven independent 2D members of different shapes (ragged widths, a 5 x 3
-grid, members that span several tiles) and two members whose first step
+grid, members that span every CTA of a cluster) and two members whose first step
 has to be split into 2 and 4 substeps and whose later steps need fewer, so
 that the two substep policies take different schedules.  Every member's
 fields come from the oracle side (workloads + the oracle's direct pressure
@@ -114,7 +114,7 @@ def test_fp64_restart_policy_matches_oracle(ref):
         T = [m[0].T0.copy() for m in members]
         for step in range(STEPS):
             rs = ens.run(1)
-            assert rs.members_failed == 0 and rs.use_graph == 1 and rs.iterations > 0
+            assert rs.members_failed == 0 and rs.clusters >= 1 and rs.passes > 0
             for k, (case, pb, traj, scheds) in enumerate(members):
                 st = ens.member_stats(k)
                 assert st.status == 0 and st.steps_done == 1
@@ -160,14 +160,15 @@ def test_fp32_bulk_matches_oracle(ref):
             assert C.rel_l2(_get(ens, k), traj[-1]) < FP32_TOL, k
 
 
-def test_tile_sizes_agree(ref):
-    # the per-cell arithmetic does not depend on the tile size; only the
+def test_cluster_sizes_agree(ref):
+    # the per-cell arithmetic does not depend on the cluster size; only the
     # order of the norm partial sums does
     E, members = ref
     runs = []
-    for tile_vecs in (1, 2, 4):
-        with _ensemble(E, members, "fp64", tile_vecs=tile_vecs) as ens:
-            assert ens.run(STEPS).tile_vecs == tile_vecs
+    for cs in (2, 4, 8, 16):
+        with _ensemble(E, members, "fp64", cluster_ctas=cs) as ens:
+            rs = ens.run(STEPS)
+            assert rs.cluster_ctas == cs and rs.members_failed == 0
             runs.append(([ens.member_stats(k).schedule for k in range(len(members))],
                          [_get(ens, k) for k in range(len(members))]))
     for sch, Ts in runs[1:]:
@@ -176,19 +177,30 @@ def test_tile_sizes_agree(ref):
             assert C.rel_l2(a, b) < 1e-14
 
 
-def test_graph_and_host_driven_loop_agree_bitwise(ref):
+def test_member_result_does_not_depend_on_the_batch(ref):
+    # a member's bits are the same alone, in the batch, with one cluster
+    # taking every member in turn, and on a second run from the same state
     E, members = ref
     out = []
-    for graph in (True, False):
-        with _ensemble(E, members, "fp32_bulk", use_graph=graph) as ens:
-            rs = ens.run(STEPS)
-            assert rs.use_graph == (1 if graph else 0)
-            out.append(([_get(ens, k) for k in range(len(members))],
-                        [ens.member_stats(k).terms for k in range(len(members))], rs.iterations))
-    (a, ta, ia), (b, tb, ib) = out
-    assert ta == tb and ia == ib
-    for x, y in zip(a, b):
-        assert np.array_equal(x, y)
+    for kw in ({}, {"max_clusters": 1}):
+        for rep in range(2):
+            with _ensemble(E, members, "fp32_bulk", **kw) as ens:
+                rs = ens.run(STEPS)
+                assert rs.members_failed == 0
+                if kw:
+                    assert rs.clusters == 1
+                out.append(([_get(ens, k) for k in range(len(members))],
+                            [ens.member_stats(k).terms for k in range(len(members))]))
+    for k in (1, 4):
+        with _ensemble(E, [members[k]], "fp32_bulk") as ens:
+            ens.run(STEPS)
+            alone = _get(ens, 0)
+            assert np.array_equal(alone, out[0][0][k]), k
+            assert ens.member_stats(0).terms == out[0][1][k]
+    for Ts, terms in out[1:]:
+        assert terms == out[0][1]
+        for x, y in zip(Ts, out[0][0]):
+            assert np.array_equal(x, y)
 
 
 def test_runs_in_pieces_equal_one_run(ref):
@@ -223,7 +235,7 @@ def test_autotune_restores_state_and_learns_substeps(ref):
         for k in range(len(members)):
             assert np.array_equal(_get(ens, k), before[k])
         rs = ens.run(1)
-        assert rs.tile_vecs in (1, 2, 4)
+        assert rs.cluster_ctas in (2, 4, 8, 16)
         for k, (case, _, traj, scheds) in enumerate(members):
             st = ens.member_stats(k)
             # started at the count doubling reached: no failed attempt
@@ -285,6 +297,33 @@ def test_fp32_estimate_overflow_splits_the_step(ref):
         st = ctx.erem_step(T, case.dt)
         assert st.substeps > 4
         assert C.rel_l2(T.cpu().numpy(), T1) < FP32_TOL
+
+
+def test_member_pass_bound_returns_timeout(ref, monkeypatch):
+    # every member is bounded in passes; with a bound of 40 passes a step
+    # (a test hook) the members whose first step needs more stop with
+    # ETIMEOUT and keep T^n, the others take their step
+    E, members = ref
+    monkeypatch.setenv("EREM_ENS_PASSES_PER_STEP", "40")
+    with _ensemble(E, members, "fp64") as ens:
+        with pytest.raises(E.EremError) as ei:
+            ens.run(1)
+        assert ei.value.status == E.EREM_ETIMEOUT
+        n_out = 0
+        for k, (case, _, traj, scheds) in enumerate(members):
+            st = ens.member_stats(k)
+            if st.status == E.EREM_ETIMEOUT:
+                n_out += 1
+                assert st.steps_done == 0 and st.terms + st.passes == 40
+                assert np.array_equal(_get(ens, k), case.T0)
+            else:
+                assert st.status == 0 and st.terms + st.passes <= 40
+                assert C.rel_l2(_get(ens, k), traj[1]) < FP64_TOL
+        assert 0 < n_out < len(members)
+    monkeypatch.delenv("EREM_ENS_PASSES_PER_STEP")
+    with _ensemble(E, members, "fp64") as ens:  # and the next ensemble runs normally
+        ens.run(1)
+        assert C.rel_l2(_get(ens, 0), members[0][2][1]) < FP64_TOL
 
 
 def test_set_temperature_restarts_from_a_saved_state(ref):
