@@ -564,7 +564,7 @@ EREM_API int erem_phi1_divided_differences(int M, const double* xi, double c,
  * degrees and substep counts and a member's Leja vectors and coefficients
  * stay in L2 while its cluster works on it.  Stopping, substep doubling and
  * the end of the run are decided on the device.  A member is bounded: it
- * stops after steps * (sum over substep levels of 2^l (m_max + 2) + 2) + 2
+ * stops after steps * (sum over substep levels of 2^l (m_max + 3) + 2) + 2
  * passes at most (EREM_ETIMEOUT).
  * ------------------------------------------------------------------------ */
 typedef struct erem_ens erem_ens;

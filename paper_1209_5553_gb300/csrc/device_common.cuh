@@ -148,27 +148,12 @@ __device__ __forceinline__ void stP(double* p, const double (&r)[VEC]) {
   for (int k = 0; k < VEC; k += 2) __stcs(reinterpret_cast<double2*>(p + k), make_double2(r[k], r[k + 1]));
 }
 
-// float -> double, exact, built from the bit fields with integer
-// instructions (the FP64 pipe of GB300 is the scarce unit in the FP32-bulk
-// sweep).  Zeros, subnormals, infinities and NaNs take the hardware
-// conversion.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  const unsigned lo = u << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // float -> double, exact, from the bit fields with integer instructions
-// only, for the single-problem kernels (the FP64 pipe of GB300 is the scarce
-// unit in the FP32-bulk sweep; the hardware conversion that f2d_exact keeps
-// for rare inputs is if-converted into one that every call executes):
-// normal numbers,
-// infinities and NaNs by widening the fields, zeros by their sign, and a
-// subnormal f through 2^24 f (an exact FP32 product, and a normal number)
-// with 24 taken off the exponent.
+// only (the FP64 pipe of GB300 is the scarce unit in the FP32-bulk sweep, and
+// a hardware conversion kept for rare inputs is if-converted into one that
+// every call executes): normal numbers, infinities and NaNs by widening the
+// fields, zeros by their sign, and a subnormal f through 2^24 f (an exact
+// FP32 product, and a normal number) with 24 taken off the exponent.
 __device__ __forceinline__ double f2d_fast(float f) {
   const unsigned e0 = (__float_as_uint(f) >> 23) & 0xffu;
   const float g = e0 == 0u ? f * 16777216.0f : f;
@@ -233,11 +218,6 @@ __device__ void stop_test(Ctrl* c, int m, double dm, double S) {
   }
 }
 
-template <typename Tq>
-__device__ __forceinline__ double to_f64(Tq v) {
-  if constexpr (sizeof(Tq) == 4) return f2d_exact(v);
-  else return v;
-}
 template <typename Tq>
 __device__ __forceinline__ double to_f64_fast(Tq v) {
   if constexpr (sizeof(Tq) == 4) return f2d_fast(v);

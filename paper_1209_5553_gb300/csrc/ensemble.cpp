@@ -150,10 +150,11 @@ erem_status build_dd(erem_ens* E, const std::vector<double>& xi, std::vector<dou
 }
 
 // Passes one step of a member may take at most: every level's substeps,
-// each with m_max terms and its start and bookkeeping passes.
+// each with m_max terms, the term pass that follows the decision, and its
+// start and bookkeeping passes.
 long long passes_per_step(const erem_ens* E) {
   long long per_step = 2;
-  for (int l = 0; l < E->nlev; ++l) per_step += (1LL << l) * (E->m_max + 2) + 2;
+  for (int l = 0; l < E->nlev; ++l) per_step += (1LL << l) * (E->m_max + 3) + 2;
   return per_step;
 }
 
