@@ -889,7 +889,7 @@ def run_ensemble(E, torch, inputs, precision, steps, warmup, dev, sample_clocks=
     tol = inputs[0][0].tol
     ens = make_ensemble(E, inputs, precision, tol)
     t_tune = time.perf_counter()
-    ens.autotune(1)
+    ens.autotune(5)  # the cluster size for a run of many steps (a 1-step probe favours large clusters)
     t_tune = time.perf_counter() - t_tune
     if warmup:
         ens.run(warmup)

@@ -648,7 +648,9 @@ EREM_API erem_status erem_ensemble_configure(erem_ens* ens, const erem_leja_opts
  * ensemble once to learn every member's substep level and work (the queue
  * order), then once for each cluster size that fits the device (2, 4, 8, 16
  * CTAs), keeps the fastest, and restores every member's temperature
- * afterwards.  Under the KEEP policy each member then starts at the substep
+ * afterwards.  The timing stands for runs of about probe_steps steps: a
+ * short run ends with its heaviest member alone, which favours large
+ * clusters, a long one is bound by throughput.  Under the KEEP policy each member then starts at the substep
  * count its first probe step passed with (the count erem_step would also
  * reach, by doubling).  Errors as erem_ensemble_run. */
 EREM_API erem_status erem_ensemble_autotune(erem_ens* ens, int probe_steps, void* stream);
