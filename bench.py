@@ -41,12 +41,18 @@ if ROOT not in sys.path:
 
 METRIC = "EREM Mcell-steps/s at 256³ FP32-bulk vs FP64 at ≤1e-5 rel err; HBM GB/s vs peak"
 UNIT = "Mcell-steps/s"
-# algorithmic bytes per cell of one Leja term (3D): 7 coefficients, q read,
-# q written, P read and written (FP64).  The running sum is updated at odd m
-# only (both products of a pair are in registers then): odd terms move these
-# bytes, even terms 16 fewer.
-BYTES_PER_CELL_TERM = {"fp32_bulk": 7 * 4 + 4 + 4 + 16, "fp64": 7 * 8 + 8 + 8 + 16}
+# algorithmic bytes per cell of one Leja term (3D): the coefficients of the
+# Leja copy of J (7 with the diagonal; 6 when the library keeps the couplings
+# only, ctx.leja_coefficients), q read, q written, P read and written
+# (FP64).  The running sum is updated at odd m only (both products of a pair
+# are in registers then): odd terms move these bytes, even terms 16 fewer.
 P_BYTES = 16
+
+
+def leja_term_bytes(precision: str, ncoef: int) -> int:
+    """Odd-term bytes per cell for a Leja copy of ncoef coefficient arrays."""
+    esz = 4 if precision == "fp32_bulk" else 8
+    return ncoef * esz + 2 * esz + P_BYTES
 
 
 def term_bytes_per_cell(full_bytes: int, degrees) -> float:
@@ -303,7 +309,7 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
     barrier(world)
     out = {"ms": ms, "degrees": degrees, "t_terms_ms": t_terms, "n_terms": n_terms,
            "n_leja": n_leja, "launches": launches, "T": T.cpu().numpy(), "clocks": clocks, "info": info,
-           "alpha": st.alpha, "beta": st.beta, "first": first}
+           "alpha": st.alpha, "beta": st.beta, "first": first, "leja_coefs": ctx.leja_coefficients}
     ctx.close()
     return out
 
@@ -591,9 +597,10 @@ def main(args):
                   capture_first=check)
     ms, value = aggregate(r32["ms"], N, K, world, dev)
     peak, peak_kind = measured_peaks()
-    b32 = BYTES_PER_CELL_TERM["fp32_bulk"]
+    b32 = leja_term_bytes("fp32_bulk", r32["leja_coefs"])
     # a Leja term moves the coefficients once and q in and out; the odd terms
-    # also read and write P: 52 B per cell for odd m, 36 B for even m
+    # also read and write P: 48 B per cell for odd m, 32 B for even m with the
+    # couplings-only copy (52 and 36 with the diagonal)
     sec_leja = r32["t_terms_ms"] / 1e3
     bpc = term_bytes_per_cell(b32, [m for s in r32["degrees"] for m in s[1:]])
     achieved = bpc * N / sec_leja / 1e9 if r32["n_terms"] else None
@@ -624,14 +631,14 @@ def main(args):
                      "timing": "CUDA events on the launching stream around each chunk of term "
                                "launches (gaps and launches after the stop included: the "
                                "per-term time is an upper bound)",
-                     "effective_gbs_at_52_bytes_per_term": effective,
+                     "effective_gbs_at_odd_term_bytes": effective,
                      "term_ms_avg": r32["t_terms_ms"] / max(r32["n_terms"], 1)},
         "setup": r32["info"],
     }
     if not args.no_fp64:
         r64 = run_gpu(E, torch, wl, "fp64", K, Wu, dev, world, capture_first=check)
         ms64, value64 = aggregate(r64["ms"], N, K, world, dev)
-        b64 = BYTES_PER_CELL_TERM["fp64"]
+        b64 = leja_term_bytes("fp64", r64["leja_coefs"])
         bpc64 = term_bytes_per_cell(b64, [m for s in r64["degrees"] for m in s[1:]])
         ach64 = bpc64 * N / (r64["t_terms_ms"] / 1e3) / 1e9 if r64["n_terms"] else None
         rel = float(np.linalg.norm(r32["T"] - r64["T"]) / np.linalg.norm(r64["T"]))
@@ -1158,7 +1165,8 @@ def adjoint_forward_terms(E, torch, wl, phys, t):
             ms += st.t_terms_ms
             terms += st.n_terms_timed
             degrees += list(st.degrees[:st.substeps])
-    return ms, terms, degrees
+        ncoef = ctx.leja_coefficients
+    return ms, terms, degrees, ncoef
 
 
 def adjoint_summary(E, torch, dev, world, n=128, K=2, Wu=1):
@@ -1170,8 +1178,8 @@ def adjoint_summary(E, torch, dev, world, n=128, K=2, Wu=1):
     r, f, q = runs["fp32_bulk"], runs["fp32_bulk_full_tape"], runs["fp64"]
     ms = max_over_ranks(r["ms_per_gradient"], world, dev)
     peak, kind = measured_peaks()
-    tms, terms, degrees = adjoint_forward_terms(E, torch, wl, phys, t)
-    b = BYTES_PER_CELL_TERM["fp32_bulk"]
+    tms, terms, degrees, ncoef = adjoint_forward_terms(E, torch, wl, phys, t)
+    b = leja_term_bytes("fp32_bulk", ncoef)
     ach = term_bytes_per_cell(b, degrees) * wl.n / (tms / 1e3) / 1e9 if terms else None
     rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
     return {

@@ -526,6 +526,17 @@ EREM_API erem_status erem_set_pressure_multigrid(erem_ctx* ctx, int nu, double o
  * Errors: EINVAL (ctx NULL; lo or hi not finite, or lo > hi). */
 EREM_API erem_status erem_hold_interval(erem_ctx* ctx, int hold, double lo, double hi);
 
+/* Coefficient arrays per cell in ctx's FP32/FP64 Leja copy of J (§4.2: the
+ * operator every Leja term applies): 5 (2D) or 7 (3D) with the diagonal;
+ * 6 for an FP32-bulk 3D context whose assembled J has every row off the
+ * x = 0 inflow plane summing to zero within 2^-28 of the row's couplings
+ * (a divergence-free Darcy flux with the linear fluid model): the term then
+ * forms sum_j J_ij (q_j - q_i) + r_i q_i with r_i kept for the x = 0 cells
+ * only, one array fewer to stream (the environment variable
+ * EREM_LEJA_DIAG=1, read at assembly, keeps the diagonal).  0 if ctx is
+ * NULL or has no state yet. */
+EREM_API int erem_leja_coefficients(const erem_ctx* ctx);
+
 /* Message of the last failing call on ctx ("" if none; a static message if
  * ctx is NULL).  The pointer stays valid until the next call on ctx. */
 EREM_API const char* erem_last_error(const erem_ctx* ctx);

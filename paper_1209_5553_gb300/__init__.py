@@ -144,6 +144,7 @@ _sigs = {
                        ctypes.POINTER(erem_stats), _P]),
     "rosm_step": (_I, [_P, _P, _P, _P, _P, _P, _D, _I, _D, _I, ctypes.POINTER(erem_stats), _P]),
     "erem_last_error": (ctypes.c_char_p, [_P]),
+    "erem_leja_coefficients": (_I, [_P]),
     "erem_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_fast_leja_points": (_I, [_I, ctypes.POINTER(_D)]),
     "erem_phi2_divided_differences": (_I, [_I, ctypes.POINTER(_D), _D, _D, ctypes.POINTER(_D)]),
@@ -621,6 +622,13 @@ class Context:
 
     def pressure_solve(self, lnk, T, p, tol=1e-10, maxit=100000, stream=None):
         return pressure_solve(self._h, self.n, lnk, T, p, tol, maxit, stream)
+
+    @property
+    def leja_coefficients(self) -> int:
+        """Coefficient arrays per cell of the Leja copy of J (7 or 5 with the
+        diagonal, 6 for a diagonal-free FP32-bulk 3D copy; 0 before any
+        state)."""
+        return int(_lib.erem_leja_coefficients(self._h))
 
     def set_state(self, T, p, lnk, phi, lam, dt, stream=None):
         erem_set_state(self._h, self.n, T, p, lnk, phi, lam, dt, stream)

@@ -769,6 +769,16 @@ erem_status assemble(erem_ctx* c, bool faces, bool rhs, cudaStream_t s) {
   EREM_TRY(check_launch(c, "assembly"));
   EREM_TRY(read_ctrl(c, s));
   EREM_TRY(check_flags(c));
+  // FP32-bulk 3D: where every row of J off the inflow plane sums to zero (a
+  // uniform temperature is transported nowhere; the discrete flux is
+  // divergence-free to far below FP32 rounding), the Leja copy keeps the
+  // couplings only and the term kernel forms sum_j J_ij (q_j - q_i) + r_i q_i
+  // with r_i stored for the x = 0 cells (EREM_LEJA_DIAG=1 keeps the diagonal)
+  {
+    const char* e = std::getenv("EREM_LEJA_DIAG");
+    const bool keep_diag = e && std::atoi(e) != 0;
+    c->jl_nodiag = c->jl_r0 && !keep_diag && c->ctrl_h->rowsum <= kRowSumNoDiag;
+  }
   set_interval(c);
   if (!std::isfinite(c->alpha) || !std::isfinite(c->beta))
     return fail(c, EREM_ENONFINITE, "non-finite spectral interval");
@@ -1286,6 +1296,8 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   for (int k = 0; k < nc; ++k) A(&c->jc[k], np);
   if (st == EREM_OK) st = dalloc(c, &c->jl_all, (np + 128) / 128 * 128 * nc * esz);
   if (st == EREM_OK && prec == EREM_FP32_BULK) st = dalloc(c, (void**)&c->jrow, np * sizeof(float2));
+  if (st == EREM_OK && prec == EREM_FP32_BULK && g.dim == 3)
+    st = dalloc(c, (void**)&c->jl_r0, nf * sizeof(float));
   A(&c->Tn, np); A(&c->vrhs, np); A(&c->vin, np); A(&c->w, np); A(&c->u, np); A(&c->P, np);
   for (int k = 0; k < 2; ++k)
     if (st == EREM_OK) st = dalloc(c, &c->q[k], np * esz);
@@ -1315,6 +1327,7 @@ erem_status erem_destroy(erem_ctx* c) {
     if (c->jc[k]) cudaFree(c->jc[k]);
   if (c->jl_all) cudaFree(c->jl_all);
   if (c->jrow) cudaFree(c->jrow);
+  if (c->jl_r0) cudaFree(c->jl_r0);
   for (int k = 0; k < 2; ++k)
     if (c->q[k]) cudaFree(c->q[k]);
   for (double* p : c->kv)
@@ -1374,6 +1387,11 @@ erem_status erem_set_physics(erem_ctx* c, const erem_physics* phys) {
   c->phys = *phys;
   c->have_state = false;  // the stored J no longer matches
   return EREM_OK;
+}
+
+int erem_leja_coefficients(const erem_ctx* c) {
+  if (!c || !c->have_state) return 0;
+  return (c->dim == 3 ? 7 : 5) - (c->jl_nodiag ? 1 : 0);
 }
 
 const char* erem_last_error(const erem_ctx* c) { return c ? c->err.c_str() : kNullCtxMsg; }

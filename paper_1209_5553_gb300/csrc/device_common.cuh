@@ -185,6 +185,10 @@ template <typename Tq>
 struct LejaCoef {
   const Tq* c[7];
   int nc;
+  // diagonal-free copy (c[0] unused): the row sum of each x = 0 cell, one per
+  // (y, z) row; every other row of J sums to zero (a uniform temperature is
+  // transported nowhere in the interior)
+  const Tq* r0;
 };
 template <int T>
 __device__ __forceinline__ size_t leja_off(int i, int nc) {

@@ -20,6 +20,7 @@ constexpr int kMaxPcDeg = 64;      // largest degree of the pressure CG's polyno
 constexpr int kDefaultPcDeg = 0;   // its default: multigrid (1 = plain Jacobi CG)
 constexpr int kMgCoarsest = 512;   // cells of the coarsest multigrid level, at most
 constexpr int kRedSlots = 4;       // reduction values per block
+constexpr double kRowSumNoDiag = 0x1p-28;  // largest relative interior row sum for a diagonal-free Leja copy
 
 // Bits of Ctrl::flags raised by the set-up kernels.
 enum : int { FLAG_NONFINITE = 1, FLAG_BAD_INPUT = 2 };
@@ -59,6 +60,7 @@ struct Ctrl {
   double yinf;     // ||T^n||_inf of the current state
   double gmin, gmax;   // Gershgorin bounds of J (before the factor dt)
   double flux_in, vmax;
+  double rowsum;   // max over cells off the x = 0 plane of |row sum of J| / sum of |off-diagonals|
   StopParams sp;
   double lin[K_NLIN];
   double e[kMaxTerms + 2];  // error estimates e_1 .. e_m of the substep
@@ -196,6 +198,8 @@ struct erem_ctx {
   // Leja copy of J scaled by dt / gamma, in the precision of the context,
   // interleaved per thread-vector (7 or 5 values per cell)
   void* jl_all = nullptr;
+  bool jl_nodiag = false;    // FP32 3D: the Leja copy holds the couplings only (diagonal implied)
+  float* jl_r0 = nullptr;    // its row sums at the x = 0 cells, one per (y, z) row
   double jl_sc = 0;          // the factor dt / gamma of jl_all
   // FP32-bulk: row sums r_i = sum_j J_ij of the cell form, as float pairs
   // (hi, lo), for the difference form of G in the step's first kernel

@@ -229,7 +229,7 @@ struct JOut {
 __global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, Phys ph,
                         double* part, unsigned* cnt, Ctrl* ctrl) {
   __shared__ double sh[NT / 32];
-  double gmin = INFINITY, gmax = -INFINITY;
+  double gmin = INFINITY, gmax = -INFINITY, rmax = 0.0;
   int bad = 0;
   const int fm = ph.fm;
   for (int i = blockIdx.x * NT + threadIdx.x; i < g.N; i += gridDim.x * NT) {
@@ -290,35 +290,48 @@ __global__ void k_cellJ(FaceIn f, const double* __restrict__ T, JOut o, Geo g, P
     bad |= !finite(D) | !finite(R);
     gmin = fmin(gmin, D - R);
     gmax = fmax(gmax, D + R);
+    if (ix > 0) {  // the row sum relative to the couplings, off the Dirichlet inflow plane
+      const double rs = fabs(D + W + E + S + Nn + B + Tt);
+      rmax = fmax(rmax, R > 0.0 ? rs / R : (rs > 0.0 ? INFINITY : 0.0));
+    }
   }
   if (bad) atomicOr(&ctrl->flags, FLAG_NONFINITE);
   const double bmin = block_reduce<1>(gmin, sh);
   const double bmax = block_reduce<2>(gmax, sh);
-  double vals[2] = {bmin, bmax};
-  if (publish_partials(part, cnt, vals, 2)) {
+  const double brs = block_reduce<2>(rmax, sh);
+  double vals[3] = {bmin, bmax, brs};
+  if (publish_partials(part, cnt, vals, 3)) {
     const double a = gather_partials<1>(part, 0, sh);
     const double b = gather_partials<2>(part, 1, sh);
+    const double r = gather_partials<2>(part, 2, sh);
     if (threadIdx.x == 0) {
       ctrl->gmin = a;
       ctrl->gmax = b;
+      ctrl->rowsum = r;
       *cnt = 0;
     }
   }
 }
 
 // Leja copy of J: (Tq)(sc * jc_k) for every padded cell, in the warp-tile
-// interleaved layout of LejaCoef (tile of T cells).
+// interleaved layout of LejaCoef (tile of T cells).  skip = 1: the couplings
+// only (the diagonal is implied by the row sums, zero off the x = 0 plane),
+// and r0[row] = (Tq)(sc * row sum) at the x = 0 cells.
 template <typename Tq, int T>
 __global__ void k_scale_jl(JOut jc, Tq* __restrict__ out, double sc, int Np, int nc,
-                           float2* __restrict__ rsum) {
+                           float2* __restrict__ rsum, int skip, Tq* __restrict__ r0, int px) {
+  const int nout = nc - skip;
   for (int i = blockIdx.x * NT + threadIdx.x; i < Np; i += gridDim.x * NT) {
-    const size_t base = (size_t)(i / T) * nc * T + (i % T);
-    for (int k = 0; k < nc; ++k) out[base + (size_t)k * T] = (Tq)(sc * jc.c[k][i]);
-    if (rsum) {  // row sum r_i of J (FP64) as a float pair hi + lo
-      double r = 0.0;
+    const size_t base = (size_t)(i / T) * nout * T + (i % T);
+    for (int k = skip; k < nc; ++k) out[base + (size_t)(k - skip) * T] = (Tq)(sc * jc.c[k][i]);
+    if (rsum || skip) {
+      double r = 0.0;  // row sum r_i of J (FP64)
       for (int k = 0; k < nc; ++k) r += jc.c[k][i];
-      const float hi = (float)r;
-      rsum[i] = make_float2(hi, (float)(r - (double)hi));
+      if (rsum) {  // as a float pair hi + lo
+        const float hi = (float)r;
+        rsum[i] = make_float2(hi, (float)(r - (double)hi));
+      }
+      if (skip && i % px == 0) r0[i / px] = (Tq)(sc * r);
     }
   }
 }
@@ -773,7 +786,7 @@ __global__ void k_leja_init(const double* __restrict__ u, Tq* __restrict__ q0, i
 // In FP32-bulk the squares of a thread's values are summed in FP32 with a
 // compensated (two-sum) accumulator and enter the FP64 norm once per thread,
 // so the FP64 pipe only carries the running sum.
-template <typename Tq, int VEC, int DIM, int PM>
+template <typename Tq, int VEC, int DIM, int PM, bool ND>
 __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __restrict__ qo,
                                                double* __restrict__ P, const double* __restrict__ p0,
                                                const LejaCoef<Tq>& cf, const Geo& g,
@@ -813,7 +826,12 @@ __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __
     const Tq ql = ix > 0 ? qi[i - 1] : Tq(0);
     const Tq qr = ix + VEC < g.px ? qi[i + VEC] : Tq(0);
     Tq cD[VEC], cW[VEC], cE[VEC], cS[VEC], cN[VEC], cB[VEC], cT[VEC];
-    ldv_stream<Tq, VEC>(cD, cf.c[0] + leja_off<32 * VEC>(i, cf.nc));
+    Tq r0 = Tq(0);  // ND: the row sum of an x = 0 cell (every other row sums to zero)
+    if constexpr (ND) {
+      if (ix == 0) r0 = cf.r0[row];
+    } else {
+      ldv_stream<Tq, VEC>(cD, cf.c[0] + leja_off<32 * VEC>(i, cf.nc));
+    }
     ldv_stream<Tq, VEC>(cW, cf.c[1] + leja_off<32 * VEC>(i, cf.nc));
     ldv_stream<Tq, VEC>(cE, cf.c[2] + leja_off<32 * VEC>(i, cf.nc));
     ldv_stream<Tq, VEC>(cS, cf.c[3] + leja_off<32 * VEC>(i, cf.nc));
@@ -831,14 +849,28 @@ __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __
     for (int k = 0; k < VEC; ++k) {
       const Tq west = k == 0 ? ql : qc[k - 1];
       const Tq east = k == VEC - 1 ? qr : qc[k + 1];
-      Tq a = (cD[k] - sh_m) * qc[k];
-      a = fma(cW[k], west, a);
-      a = fma(cE[k], east, a);
-      a = fma(cS[k], qs[k], a);
-      a = fma(cN[k], qn[k], a);
-      if (DIM == 3) {
-        a = fma(cB[k], qb[k], a);
-        a = fma(cT[k], qt[k], a);
+      Tq a;
+      if constexpr (ND) {
+        // sum_j J_ij (q_j - q_i) + (r_i - shift) q_i
+        a = ((k == 0 ? r0 : Tq(0)) - sh_m) * qc[k];
+        a = fma(cW[k], west - qc[k], a);
+        a = fma(cE[k], east - qc[k], a);
+        a = fma(cS[k], qs[k] - qc[k], a);
+        a = fma(cN[k], qn[k] - qc[k], a);
+        if (DIM == 3) {
+          a = fma(cB[k], qb[k] - qc[k], a);
+          a = fma(cT[k], qt[k] - qc[k], a);
+        }
+      } else {
+        a = (cD[k] - sh_m) * qc[k];
+        a = fma(cW[k], west, a);
+        a = fma(cE[k], east, a);
+        a = fma(cS[k], qs[k], a);
+        a = fma(cN[k], qn[k], a);
+        if (DIM == 3) {
+          a = fma(cB[k], qb[k], a);
+          a = fma(cT[k], qt[k], a);
+        }
       }
       out[k] = a;
       if constexpr (sizeof(Tq) == 4) {
@@ -877,21 +909,21 @@ __device__ __forceinline__ void leja_term_body(const Tq* __restrict__ qi, Tq* __
 
 // Terms m >= 2 (PM = 0 or 1), held to four resident blocks of 256 threads
 // per SM, the grid the launcher sizes.
-template <typename Tq, int VEC, int DIM, int PM>
+template <typename Tq, int VEC, int DIM, int PM, bool ND = false>
 __global__ void __launch_bounds__(NT, 4)
 k_leja_term(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
             LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi, const double* __restrict__ dd,
             double cg, int m, double* part, unsigned* cnt, Ctrl* ctrl) {
-  leja_term_body<Tq, VEC, DIM, PM>(qi, qo, P, nullptr, cf, g, xi, dd, cg, m, part, cnt, ctrl);
+  leja_term_body<Tq, VEC, DIM, PM, ND>(qi, qo, P, nullptr, cf, g, xi, dd, cg, m, part, cnt, ctrl);
 }
 
 // Term m = 1 (PM = 2), held to four resident blocks per SM like the others.
-template <typename Tq, int VEC, int DIM>
+template <typename Tq, int VEC, int DIM, bool ND = false>
 __global__ void __launch_bounds__(NT, 4)
 k_leja_term1(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
              const double* __restrict__ p0, LejaCoef<Tq> cf, Geo g, const double* __restrict__ xi,
              const double* __restrict__ dd, double cg, double* part, unsigned* cnt, Ctrl* ctrl) {
-  leja_term_body<Tq, VEC, DIM, 2>(qi, qo, P, p0, cf, g, xi, dd, cg, 1, part, cnt, ctrl);
+  leja_term_body<Tq, VEC, DIM, 2, ND>(qi, qo, P, p0, cf, g, xi, dd, cg, 1, part, cnt, ctrl);
 }
 
 // P += d_M q_M: the last product of a substep stopped at an even degree M
@@ -2671,10 +2703,11 @@ void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s) {
   ++c->launches;
   if (c->prec == EREM_FP32_BULK)
     k_scale_jl<float, 128><<<blocks_padded(c), NT, 0, s>>>(jc, (float*)c->jl_all, sc, (int)c->Np, nc,
-                                                           c->jrow);
+                                                           c->jrow, c->jl_nodiag ? 1 : 0, c->jl_r0,
+                                                           c->px);
   else
     k_scale_jl<double, 64><<<blocks_padded(c), NT, 0, s>>>(jc, (double*)c->jl_all, sc, (int)c->Np, nc,
-                                                           nullptr);
+                                                           nullptr, 0, nullptr, c->px);
 }
 
 // Pointers of the interleaved Leja coefficients for kernels of vector width
@@ -2682,8 +2715,18 @@ void launch_scale_jl(const erem_ctx* c, double sc, cudaStream_t s) {
 template <typename Tq, int VEC>
 LejaCoef<Tq> leja_coef(const erem_ctx* c) {
   LejaCoef<Tq> cf;
-  cf.nc = c->dim == 3 ? 7 : 5;
-  for (int k = 0; k < 7; ++k) cf.c[k] = (const Tq*)c->jl_all + (k < cf.nc ? k * 32 * VEC : 0);
+  const int nc = c->dim == 3 ? 7 : 5;
+  const Tq* base = (const Tq*)c->jl_all;
+  if (c->jl_nodiag) {  // couplings only: c[1..] from the start of the tile
+    cf.nc = nc - 1;
+    cf.c[0] = nullptr;
+    for (int k = 1; k < 7; ++k) cf.c[k] = base + (k < nc ? (k - 1) * 32 * VEC : 0);
+    cf.r0 = (const Tq*)c->jl_r0;
+  } else {
+    cf.nc = nc;
+    for (int k = 0; k < 7; ++k) cf.c[k] = base + (k < nc ? k * 32 * VEC : 0);
+    cf.r0 = nullptr;
+  }
   return cf;
 }
 
@@ -2795,6 +2838,23 @@ void term_launch(const erem_ctx* c, int m, const Tq* qi, Tq* qo, double cg, cuda
   at[0].val.programmaticStreamSerializationAllowed = (c->pdl && m > 1) ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if constexpr (sizeof(Tq) == 4 && DIM == 3) {
+    if (c->jl_nodiag) {  // the Leja copy holds the couplings only
+      if (m == 1)
+        cudaLaunchKernelEx(&cfg, k_leja_term1<Tq, VEC, DIM, true>, qi, qo, c->P, c->p0, cf, g,
+                           (const double*)c->xi_dev, (const double*)c->dd_dev, cg, c->red_part,
+                           c->red_cnt, c->ctrl);
+      else if (m & 1)
+        cudaLaunchKernelEx(&cfg, k_leja_term<Tq, VEC, DIM, 1, true>, qi, qo, c->P, cf, g,
+                           (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
+                           c->red_cnt, c->ctrl);
+      else
+        cudaLaunchKernelEx(&cfg, k_leja_term<Tq, VEC, DIM, 0, true>, qi, qo, c->P, cf, g,
+                           (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
+                           c->red_cnt, c->ctrl);
+      return;
+    }
+  }
   if (m == 1)
     cudaLaunchKernelEx(&cfg, k_leja_term1<Tq, VEC, DIM>, qi, qo, c->P, c->p0, cf, g,
                        (const double*)c->xi_dev, (const double*)c->dd_dev, cg, c->red_part,

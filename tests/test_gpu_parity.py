@@ -171,6 +171,49 @@ def test_erem_steps_3d(E, name, make):
         assert C.rel_l2(got - case.T0, T_ref - case.T0) < inc_tol, prec
 
 
+@pytest.mark.parametrize("name,make", CASES_3D, ids=[c[0] for c in CASES_3D])
+def test_diagonal_free_leja_copy(E, name, make, monkeypatch):
+    # FP32-bulk 3D with a divergence-free Darcy flux: the Leja copy keeps the
+    # couplings only (6 arrays) and the term forms sum_j J_ij (q_j - q_i) +
+    # r_i q_i; against the oracle as every FP32-bulk step, and against the
+    # copy with the diagonal (EREM_LEJA_DIAG=1) to FP32 rounding
+    case = make()
+    steps = 2
+    T_ref, _ = _oracle_run(case, steps)
+    out = {}
+    for keep in ("0", "1"):
+        monkeypatch.setenv("EREM_LEJA_DIAG", keep)
+        with _ctx(E, case, "fp32_bulk") as ctx:
+            T = _t(case.T0)
+            for k in range(steps):
+                fields = (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam)) if k == 0 else (None,) * 4
+                ctx.erem_step(T, case.dt, *fields)
+            out[keep] = (ctx.leja_coefficients, T.cpu().numpy())
+    assert out["0"][0] == 6 and out["1"][0] == 7
+    for ncoef, got in out.values():
+        assert C.rel_l2(got, T_ref) < FP32_TOL, ncoef
+        assert C.rel_l2(got - case.T0, T_ref - case.T0) < FP32_TOL, ncoef
+    assert C.rel_l2(out["0"][1] - case.T0, out["1"][1] - case.T0) < FP32_TOL
+
+
+def test_leja_copy_keeps_the_diagonal_for_a_divergent_flux(E, monkeypatch):
+    # a pressure that is not the steady solution (the linear head) leaves the
+    # interior rows of J with nonzero sums: the copy keeps the diagonal, and
+    # the step still matches the oracle on the same pressure
+    monkeypatch.delenv("EREM_LEJA_DIAG", raising=False)
+    case = C.random_case(3, 17, 13, 11, seed=9)
+    g = case.grid
+    x = (np.arange(g.nx) + 0.5) / g.nx
+    case.p = np.broadcast_to(1.0 - x, (g.nz, g.ny, g.nx)).reshape(-1).copy()
+    T_ref, _ = _oracle_run(case, 1)
+    with _ctx(E, case, "fp32_bulk") as ctx:
+        T = _t(case.T0)
+        ctx.erem_step(T, case.dt, _t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam))
+        assert ctx.leja_coefficients == 7
+        got = T.cpu().numpy()
+    assert C.rel_l2(got - case.T0, T_ref - case.T0) < FP32_TOL
+
+
 def test_erem_nonlinear_fluid_reassembles_every_step(E):
     case = C.random_case(2, 24, 18, seed=7, fluid_model=1)
     steps = 3
