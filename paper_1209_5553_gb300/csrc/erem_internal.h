@@ -247,7 +247,7 @@ struct erem_ctx {
   int kr_cap = 0;                   // basis vectors allocated
   // adjoint (allocated on first use)
   void* jlT_all = nullptr;          // Leja copy of J^T (FP32: interleaved per 32 adj_vec cells)
-  int adj_vec = 4;                  // cells per thread of the FP32 Horner pass (4 or 2)
+  int adj_vec = 2;                  // cells per thread of the FP32 Horner pass
   int adj_blocks_per_sm = 4;        // its resident blocks per SM (one wave of them)
   bool jlT_valid = false;
   void* adj_store = nullptr;        // forward Newton vectors q_0..q_{m-1} of one substep

@@ -1216,10 +1216,10 @@ __global__ void k_adj_aux32(const double* __restrict__ Fx, const double* __restr
   }
 }
 
-// VEC (4 or 2) consecutive cells of one padded row per thread (px is a
-// multiple of 4, so every row starts on a 16-byte boundary): vector loads of
-// the vectors, coefficients, capacities and face sums, scalar loads only for
-// the x neighbours beyond the VEC.  Pad lanes (ix >= nx) compute nothing and
+// VEC consecutive cells of one padded row per thread (px is a multiple of
+// 4, so every row starts on a 16-byte boundary): vector loads of the
+// vectors, coefficients, capacities and face sums, scalar loads only for the
+// x neighbours beyond the VEC.  Pad lanes (ix >= nx) compute nothing and
 // store 0.  The neighbour loads are unconditional, at the cell's own address
 // where the neighbour is missing (its coupling there is 0), so a thread has
 // all of them in flight at once.  The transposed coefficients are
@@ -1259,6 +1259,11 @@ k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
                AdjFaces32 f, Geo g) {
   constexpr int T_TILE = 32 * VEC;
   const int nvec = g.Np / VEC;
+  const float* __restrict__ icap = f.icap;
+  const unsigned char* __restrict__ up = f.up;
+  float* __restrict__ gxp = f.gx;
+  float* __restrict__ gyp = f.gy;
+  float* __restrict__ gzp = f.gz;
   for (int v = blockIdx.x * NT + threadIdx.x; v < nvec; v += gridDim.x * NT) {
     const RowV<VEC> R = rowv_of<VEC>(v, g);
     const int ip0 = R.ip0;
@@ -1268,6 +1273,9 @@ k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
     const bool has_b = g.dim == 3 && R.iz > 0, has_t = g.dim == 3 && R.iz < g.nz - 1;
     const int oS = has_s ? -g.px : 0, oN = has_n ? g.px : 0;
     const int oB = has_b ? -g.plane : 0, oT = has_t ? g.plane : 0;
+    const int oE = has_e ? VEC : 0;
+    // every load of the vector first (the face-sum inputs do not depend on
+    // the stencil), so that one round trip to memory covers them all
     float sc[VEC], sS[VEC], sN[VEC], sB[VEC], sT[VEC], cf[7][VEC], m4[VEC];
     ldv<float, VEC>(sc, s_in + ip0);
     ldv<float, VEC>(sS, s_in + ip0 + oS);
@@ -1277,11 +1285,28 @@ k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
       ldv<float, VEC>(sT, s_in + ip0 + oT);
     }
     const float sw = s_in[ip0 - (has_w ? 1 : 0)];
-    const float se = s_in[ip0 + (has_e ? VEC : 0)];
+    const float se = s_in[ip0 + oE];
 #pragma unroll
     for (int k = 0; k < 7; ++k)
       if (k < nc) ldv<float, VEC>(cf[k], jlT + base + k * T_TILE);
     ldv<float, VEC>(m4, mu + ip0);
+    float ic[VEC], x4[VEC], gsx[VEC], icN[VEC], xN[VEC], gsy[VEC], icT[VEC], xT[VEC], gsz[VEC];
+    unsigned fl[VEC];
+    ldv<float, VEC>(ic, icap + ip0);
+    ldv<float, VEC>(x4, q + ip0);
+    ld_flags<VEC>(fl, up + ip0);
+    const float ice = icap[ip0 + oE];
+    const float qe = q[ip0 + oE];
+    ldv<float, VEC>(gsx, gxp + ip0);
+    ldv<float, VEC>(icN, icap + ip0 + oN);
+    ldv<float, VEC>(xN, q + ip0 + oN);
+    ldv<float, VEC>(gsy, gyp + ip0);
+    if (g.dim == 3) {
+      ldv<float, VEC>(icT, icap + ip0 + oT);
+      ldv<float, VEC>(xT, q + ip0 + oT);
+      ldv<float, VEC>(gsz, gzp + ip0);
+    }
+
     float a[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
@@ -1299,14 +1324,7 @@ k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
     stv<float, VEC>(s_out + ip0, a);
 
     // face derivative of the pair (s_in, q_j)
-    float ic[VEC], x4[VEC], yc[VEC], gs[VEC], icN[VEC], xN[VEC];
-    unsigned fl[VEC];
-    ldv<float, VEC>(ic, f.icap + ip0);
-    ldv<float, VEC>(x4, q + ip0);
-    ld_flags<VEC>(fl, f.up + ip0);
-    const float ice = f.icap[ip0 + (has_e ? VEC : 0)];
-    const float qe = q[ip0 + (has_e ? VEC : 0)];
-    ldv<float, VEC>(gs, f.gx + ip0);
+    float yc[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) yc[j] = sc[j] * ic[j];
     const float ye = has_e ? se * ice : 0.0f;
@@ -1316,35 +1334,29 @@ k_adj_horner32(const float* __restrict__ s_in, float* __restrict__ s_out,
       if (ix < g.nx - 1) {
         const float yr = j < VEC - 1 ? yc[j + 1] : ye;
         const float xu = (fl[j] & 1u) ? x4[j] : (j < VEC - 1 ? x4[j + 1] : qe);
-        gs[j] += scale * ((yr - yc[j]) * xu);
+        gsx[j] += scale * ((yr - yc[j]) * xu);
       } else if (ix == g.nx - 1) {
-        gs[j] -= scale * (yc[j] * x4[j]);
+        gsx[j] -= scale * (yc[j] * x4[j]);
       }
     }
-    stv<float, VEC>(f.gx + ip0, gs);
+    stv<float, VEC>(gxp + ip0, gsx);
     if (has_n) {
-      ldv<float, VEC>(icN, f.icap + ip0 + g.px);
-      ldv<float, VEC>(xN, q + ip0 + g.px);
-      ldv<float, VEC>(gs, f.gy + ip0);
 #pragma unroll
       for (int j = 0; j < VEC; ++j)
         if (R.ix0 + j < g.nx) {
           const float xu = (fl[j] & 2u) ? x4[j] : xN[j];
-          gs[j] += scale * (fmaf(sN[j], icN[j], -yc[j]) * xu);
+          gsy[j] += scale * (fmaf(sN[j], icN[j], -yc[j]) * xu);
         }
-      stv<float, VEC>(f.gy + ip0, gs);
+      stv<float, VEC>(gyp + ip0, gsy);
     }
     if (has_t) {
-      ldv<float, VEC>(icN, f.icap + ip0 + g.plane);
-      ldv<float, VEC>(xN, q + ip0 + g.plane);
-      ldv<float, VEC>(gs, f.gz + ip0);
 #pragma unroll
       for (int j = 0; j < VEC; ++j)
         if (R.ix0 + j < g.nx) {
-          const float xu = (fl[j] & 4u) ? x4[j] : xN[j];
-          gs[j] += scale * (fmaf(sT[j], icN[j], -yc[j]) * xu);
+          const float xu = (fl[j] & 4u) ? x4[j] : xT[j];
+          gsz[j] += scale * (fmaf(sT[j], icT[j], -yc[j]) * xu);
         }
-      stv<float, VEC>(f.gz + ip0, gs);
+      stv<float, VEC>(gzp + ip0, gsz);
     }
     if (R.ix0 == 0 && (fl[0] & 8u)) f.g0[R.iy + g.ny * R.iz] += (double)(scale * (yc[0] * x4[0]));
   }
@@ -3326,14 +3338,9 @@ void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const d
     const int vec = c->adj_vec;
     const int nb = (int)std::min<long long>((c->Np / vec + NT - 1) / NT,
                                             (long long)c->adj_blocks_per_sm * c->sm_count);
-    if (vec == 2)
-      k_adj_horner32<2><<<nb, NT, 0, s>>>((const float*)s_in, (float*)s_out, c->adj_mu32,
-                                          (const float*)q, (const float*)c->jlT_all, nc, (float)dj,
-                                          (float)shift, (float)scale, f, geo_of(c));
-    else
-      k_adj_horner32<4><<<nb, NT, 0, s>>>((const float*)s_in, (float*)s_out, c->adj_mu32,
-                                          (const float*)q, (const float*)c->jlT_all, nc, (float)dj,
-                                          (float)shift, (float)scale, f, geo_of(c));
+    k_adj_horner32<2><<<nb, NT, 0, s>>>((const float*)s_in, (float*)s_out, c->adj_mu32,
+                                        (const float*)q, (const float*)c->jlT_all, nc, (float)dj,
+                                        (float)shift, (float)scale, f, geo_of(c));
   } else
     k_adj_horner<double><<<blocks_cells(c), NT, 0, s>>>((const double*)s_in, (double*)s_out, mu,
                                                         (const double*)q, (const double*)c->jlT_all,
@@ -3341,24 +3348,17 @@ void launch_adj_horner(const erem_ctx* c, const void* s_in, void* s_out, const d
                                                         geo_of(c));
 }
 
-// Cells per thread of the FP32 Horner pass, and its resident blocks per SM:
-// four cells per thread unless the grid is so small that the last round of a
-// resident wave would run mostly empty (at 128^3: 3.4 rounds of four cells,
-// 6.7 of two), then two.
+// Cells per thread of the FP32 Horner pass (two: with every load of a
+// vector issued before its arithmetic, four cells would not fit the register
+// budget) and its resident blocks per SM.
 void choose_adj_vec(erem_ctx* c) {
-  int b4 = 0, b2 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_adj_horner32<4>, NT, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_adj_horner32<2>, NT, 0) != cudaSuccess) {
+  int b2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_adj_horner32<2>, NT, 0) != cudaSuccess) {
     cudaGetLastError();
-    b4 = b2 = 4;
+    b2 = 4;
   }
-  b4 = std::max(b4, 1);
-  b2 = std::max(b2, 1);
-  const double r4 = (double)c->Np / 4 / ((double)b4 * c->sm_count * NT);
-  const double r2 = (double)c->Np / 2 / ((double)b2 * c->sm_count * NT);
-  const double e4 = r4 / std::ceil(r4), e2 = r2 / std::ceil(r2);
-  c->adj_vec = e2 > e4 + 0.03 ? 2 : 4;
-  c->adj_blocks_per_sm = c->adj_vec == 2 ? b2 : b4;
+  c->adj_vec = 2;
+  c->adj_blocks_per_sm = std::max(b2, 1);
 }
 
 void launch_adj_aux32(const erem_ctx* c, cudaStream_t s) {
