@@ -308,22 +308,27 @@ void focal_map(erem_ctx* c) {
 int dd_key(int S, int phi) { return 8 * S + phi; }
 DDEntry& dd_entry(erem_ctx* c, int S, int phi = 1) { return c->dd_cache[dd_key(S, phi)]; }
 
-erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1) {
+erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1,
+                       bool take_spec = true) {
   DDEntry& e = dd_entry(c, S, phi);
   const int key = dd_key(S, phi);
   const double cc = c->cfoc / S, gg = c->gam / S;
   if (e.M < M || e.c != cc || e.gamma != gg) {
     e.c = cc;
     e.gamma = gg;
-    if (c->dd_spec.valid() && c->spec_key == key && c->spec_kind == c->leja_kind &&
-        c->spec_M >= M && c->spec_c == cc && c->spec_g == gg) {
-      // computed ahead on the host thread (the same function of the same inputs)
-      e.d = c->dd_spec.get();
-      e.M = c->spec_M;
+    erem_ctx::DDSpec* sp = nullptr;
+    for (auto& x : c->dd_spec)
+      if (take_spec && x.f.valid() && x.key == key && x.kind == c->leja_kind && x.M >= M &&
+          x.c == cc && x.g == gg)
+        sp = &x;
+    if (sp) {
+      // computed ahead on host threads (the same function of the same inputs)
+      e.d = sp->f.get();
+      e.M = sp->M;
     } else {
       e.M = M;
       e.d.assign(M + 1, 0.0);
-      if (divided_differences_phi(phi, M, c->xi_host.data(), cc, gg, e.d.data()) != 0)
+      if (divided_differences_phi(phi, M, c->xi_host.data(), cc, gg, e.d.data(), kDdThreads) != 0)
         e.d.clear();
     }
     if (e.d.empty()) {
@@ -347,33 +352,42 @@ erem_status prepare_dd(erem_ctx* c, int S, int M, cudaStream_t s, int phi = 1) {
   return EREM_OK;
 }
 
-// Start the phi_1 table of substep level S (M + 1 entries) on a host thread;
-// prepare_dd takes it if that level is reached with the same interval.
+// Start the phi_1 table of substep level S (M + 1 entries) on host threads;
+// prepare_dd takes it if that level is reached with the same interval.  Two
+// tables may be under way; a third waits for the older one.
 void speculate_dd(erem_ctx* c, int S, int M) {
   const int key = dd_key(S, 1);
   const double cc = c->cfoc / S, gg = c->gam / S;
   const DDEntry& e = dd_entry(c, S, 1);
   if (e.M >= M && e.c == cc && e.gamma == gg) return;  // cached
-  if (c->dd_spec.valid() && c->spec_key == key && c->spec_kind == c->leja_kind &&
-      c->spec_M >= M && c->spec_c == cc && c->spec_g == gg)
-    return;  // already under way
-  if (c->dd_spec.valid()) c->dd_spec.wait();  // one table at a time
+  for (auto& x : c->dd_spec)
+    if (x.f.valid() && x.key == key && x.kind == c->leja_kind && x.M >= M && x.c == cc && x.g == gg)
+      return;  // already under way
+  erem_ctx::DDSpec* slot = nullptr;
+  for (auto& x : c->dd_spec)
+    if (!x.f.valid()) slot = &x;
+  if (!slot) {  // both busy: reuse the older one
+    slot = &c->dd_spec[0];
+    slot->f.wait();
+    std::swap(c->dd_spec[0], c->dd_spec[1]);
+    slot = &c->dd_spec[1];
+  }
   std::vector<double> xi(c->xi_host.begin(), c->xi_host.begin() + M + 1);
   try {
-    c->dd_spec = std::async(std::launch::async, [xi = std::move(xi), M, cc, gg]() {
+    slot->f = std::async(std::launch::async, [xi = std::move(xi), M, cc, gg]() {
       std::vector<double> d(M + 1, 0.0);
-      if (divided_differences_phi(1, M, xi.data(), cc, gg, d.data()) != 0) d.clear();
+      if (divided_differences_phi(1, M, xi.data(), cc, gg, d.data(), kDdThreads) != 0) d.clear();
       return d;
     });
   } catch (...) {  // no thread: prepare_dd computes the table itself
-    c->dd_spec = std::future<std::vector<double>>();
+    slot->f = std::future<std::vector<double>>();
     return;
   }
-  c->spec_key = key;
-  c->spec_kind = c->leja_kind;
-  c->spec_M = M;
-  c->spec_c = cc;
-  c->spec_g = gg;
+  slot->key = key;
+  slot->kind = c->leja_kind;
+  slot->M = M;
+  slot->c = cc;
+  slot->g = gg;
 }
 
 struct Opts {
@@ -592,9 +606,21 @@ erem_status run_phi1(erem_ctx* c, const double* src, const double* base, double*
       c->rec.w_off.clear();
       c->rec_ok = true;
     }
-    // a short table first; the full one when a substep needs more terms
-    int M_avail = replay ? mcap : std::min(mcap, std::max(48, 2 * c->last_degree + 8));
-    EREM_TRY(prepare_dd(c, S, M_avail, s));
+    // a short table first; the full one when a substep needs more terms.  A
+    // table not cached yet starts at kDdShort terms, computed here, while
+    // host threads compute the full one (m_max terms) for the chunk loop to
+    // take when the substep runs past the short one
+    int M_avail = replay ? mcap : std::min(mcap, std::max(kDdShort, 2 * c->last_degree + 8));
+    bool short_first = false;
+    if (!replay && M_avail > kDdShort) {
+      const DDEntry& e = dd_entry(c, S, 1);
+      if (!(e.M >= M_avail && e.c == c->cfoc / S && e.gamma == c->gam / S)) {
+        speculate_dd(c, S, mcap);
+        M_avail = kDdShort;
+        short_first = true;
+      }
+    }
+    EREM_TRY(prepare_dd(c, S, M_avail, s, 1, !short_first));
     // the last step needed more substeps: the next level's table is computed
     // on the host while this level's terms run
     if (!replay && a + 1 < n_attempts && c->last_S > S) speculate_dd(c, 2 * S, mcap);

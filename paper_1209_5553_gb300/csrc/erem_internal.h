@@ -165,6 +165,9 @@ struct SmgLevel {
   float* x[3] = {};
 };
 
+constexpr int kDdShort = 48;    // divided differences of a level's first table
+constexpr int kDdThreads = 8;   // host threads of a divided-difference table
+
 struct DDEntry {
   double c = 0, gamma = 0;
   int M = -1;
@@ -306,11 +309,15 @@ struct erem_ctx {
   int dd_tag_S = -1, dd_tag_M = -1;
   std::vector<double> xi_host;
   std::map<int, erem::DDEntry> dd_cache;  // substep count -> table
-  // the phi_1 table of the next substep level, computed on a host thread
-  // while the GPU runs the current level (when the last step needed it)
-  std::future<std::vector<double>> dd_spec;
-  int spec_key = -1, spec_kind = -1, spec_M = -1;
-  double spec_c = 0, spec_g = 0;
+  // phi_1 tables computed on host threads while the GPU runs terms: the
+  // full table of the level being interpolated (its first terms use a short
+  // one), and the next level's when the last step needed it
+  struct DDSpec {
+    std::future<std::vector<double>> f;
+    int key = -1, kind = -1, M = -1;
+    double c = 0, g = 0;
+  };
+  DDSpec dd_spec[2];
   int last_S = 1;   // substeps of the last erem_step
   int substep_start = 0;   // EREM_SUBSTEPS_FROM_ONE or EREM_SUBSTEPS_FROM_LAST
 
@@ -445,7 +452,8 @@ void launch_adj_lnk(const erem_ctx* c, double* out, cudaStream_t s);
 void expm_small(int n, const double* A, double* E);
 
 // host scalar side (leja_host.cpp)
-int divided_differences_phi(int kphi, int M, const double* xi, double c, double gamma, double* d);
+int divided_differences_phi(int kphi, int M, const double* xi, double c, double gamma, double* d,
+                            int threads = 1);
 void leja_table(int M, std::vector<double>* out);
 void fast_leja_table(int M, std::vector<double>* out);
 int divided_differences(int M, const double* xi, double c, double gamma, double* d);

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <limits>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "erem_internal.h"
@@ -159,14 +161,48 @@ void leja_table(int M, std::vector<double>* out) {
 // 16 rows per squaring level (n / 2^s <= 16), and its exponential is taken
 // from 64 Taylor terms built by repeated right-multiplication with the
 // bidiagonal matrix (each power is banded).  Every entry of exp(W / 2^s) is
-// non-negative (W has a non-negative off-diagonal), so the squarings
-// add terms of one sign and keep relative accuracy even for the tiny
-// entries far below the diagonal.
+// non-negative (W has a non-negative off-diagonal), so the squarings and
+// the products with a non-negative vector add terms of one sign and keep
+// relative accuracy even for the tiny entries far below the diagonal.
+// Only column 0 of exp(W) is needed: k squarings make F = exp(W / 2^s)^(2^k)
+// and 2^(s-k) - 1 products F v, from v = F e_0, finish it, with k chosen
+// to minimise the operations (k n^3 / 6 against n^2 / 2 per product).
 //
 // phi_2 (and phi_k) the same way: phi_k(z) = exp[0, .., 0, z] with k zeros,
 // so the diagonal starts with k zeros, the subdiagonal with k ones, and the
 // entry (j+k, 0) is the divided difference d_j of phi_k.
-int divided_differences_phi(int kphi, int M, const double* xi, double c, double gamma, double* d) {
+//
+// threads > 1: the rows of the Taylor sum and of every squaring are shared
+// out among that many host threads (row i to thread i mod threads), which
+// meet at a barrier between squarings; the split between squarings and
+// products follows the number of threads asked for, and every entry sums its
+// terms in the same order, so a given thread count gives the same bits
+// however many threads could be started.
+namespace {
+
+// Sense-counting barrier for a team of host threads.
+class SpinBarrier {
+ public:
+  void set(int n) { n_ = n; }
+  void wait() {
+    const int g = gen_.load(std::memory_order_acquire);
+    if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+      count_.store(0, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_acq_rel);
+    } else {
+      while (gen_.load(std::memory_order_acquire) == g) std::this_thread::yield();
+    }
+  }
+
+ private:
+  int n_ = 1;
+  std::atomic<int> count_{0}, gen_{0};
+};
+
+}  // namespace
+
+int divided_differences_phi(int kphi, int M, const double* xi, double c, double gamma, double* d,
+                            int threads) {
   if (kphi < 1 || kphi > 4 || M < 0 || !xi || !d || !std::isfinite(c) || !std::isfinite(gamma) ||
       gamma <= 0.0)
     return -1;
@@ -183,57 +219,107 @@ int divided_differences_phi(int kphi, int M, const double* xi, double c, double 
   while ((double)n / std::ldexp(1.0, s) > 16.0) ++s;
   const double scale = std::ldexp(1.0, -s);
   for (int k = 0; k < n; ++k) { diag[k] *= scale; sub[k] *= scale; }
-
-  // E = sum_{k=0}^{64} B^k / k!, lower triangular, row-major n x n.
-  std::vector<double> E((size_t)n * n, 0.0), Tk((size_t)n * n, 0.0), Tn((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) { E[(size_t)i * n + i] = 1.0; Tk[(size_t)i * n + i] = 1.0; }
-  const int K = 64;
-  for (int k = 0; k < K; ++k) {
-    const int band = std::min(k, n - 1);       // Tk is zero below band k
-    const int nb = std::min(k + 1, n - 1);
-    const double inv = 1.0 / (double)(k + 1);
-    for (int i = 0; i < n; ++i) {
-      const int j0 = std::max(0, i - nb);
-      for (int j = j0; j <= i; ++j) {
-        // (Tk B)(i, j) = Tk(i, j) B(j, j) + Tk(i, j+1) B(j+1, j)
-        double v = 0.0;
-        if (i - j <= band) v += Tk[(size_t)i * n + j] * diag[j];
-        if (j + 1 <= i && i - (j + 1) <= band) v += Tk[(size_t)i * n + j + 1] * sub[j + 1];
-        Tn[(size_t)i * n + j] = v * inv;
+  const int T_want = std::max(1, std::min(threads, n / 24));
+  std::vector<double> E((size_t)n * n, 0.0), Ta((size_t)n * n, 0.0), Tb((size_t)n * n, 0.0);
+  std::vector<double> va(n, 0.0), vb(n, 0.0);
+  for (int i = 0; i < n; ++i) { E[(size_t)i * n + i] = 1.0; Ta[(size_t)i * n + i] = 1.0; }
+  SpinBarrier bar;
+  // squarings k (shared by the team), then 2^(s-k) - 1 matrix-vector
+  // products (one thread), k minimising the operations per thread of the
+  // team asked for (not of the team started: the bits depend on k only)
+  int ksq = s;
+  {
+    double best = 1e300;
+    for (int k = std::max(0, s - 24); k <= s; ++k) {
+      const double cost =
+          k * (double)n * n * n / (6.0 * T_want) + (std::ldexp(1.0, s - k) - 1.0) * n * n / 2.0;
+      if (cost < best) {
+        best = cost;
+        ksq = k;
       }
     }
-    std::swap(Tk, Tn);
-    for (int i = 0; i < n; ++i)
-      for (int j = std::max(0, i - nb); j <= i; ++j) E[(size_t)i * n + j] += Tk[(size_t)i * n + j];
   }
-  // s - 1 full squarings of the lower triangle, the last one only for column 0.
-  // Row form: row i of E E is sum_l E(i, l) (row l of E), rows read
-  // contiguously; each entry still sums its products in increasing l.
-  std::vector<double> F((size_t)n * n, 0.0);
-  for (int sq = 0; sq + 1 < s; ++sq) {
-    for (int i = 0; i < n; ++i) {
-      double* __restrict__ Fi = &F[(size_t)i * n];
-      const double* __restrict__ Ei = &E[(size_t)i * n];
-      for (int j = 0; j <= i; ++j) Fi[j] = 0.0;
-      for (int l = 0; l <= i; ++l) {
-        const double a = Ei[l];
-        const double* __restrict__ El = &E[(size_t)l * n];
+  auto team = [&](int t, int T) {
+    // E = sum_{k=0}^{64} B^k / k!, lower triangular, row-major n x n; row i
+    // of every power needs only row i of the one before, so each thread runs
+    // all terms on its own rows
+    const int K = 64;
+    for (int i = t; i < n; i += T) {
+      double* __restrict__ Tk = Ta.data() + (size_t)i * n;
+      double* __restrict__ Tn = Tb.data() + (size_t)i * n;
+      double* __restrict__ Ei = E.data() + (size_t)i * n;
+      for (int k = 0; k < K; ++k) {
+        const int band = std::min(k, n - 1);       // Tk is zero below band k
+        const int nb = std::min(k + 1, n - 1);
+        const double inv = 1.0 / (double)(k + 1);
+        const int j0 = std::max(0, i - nb);
+        for (int j = j0; j <= i; ++j) {
+          // (Tk B)(i, j) = Tk(i, j) B(j, j) + Tk(i, j+1) B(j+1, j)
+          double v = 0.0;
+          if (i - j <= band) v += Tk[j] * diag[j];
+          if (j + 1 <= i && i - (j + 1) <= band) v += Tk[j + 1] * sub[j + 1];
+          Tn[j] = v * inv;
+        }
+        for (int j = j0; j <= i; ++j) Ei[j] += Tn[j];
+        std::swap(Tk, Tn);
+      }
+    }
+    bar.wait();
+    // squarings of the lower triangle (row i of A A is sum_l A(i, l) (row
+    // l of A); each entry sums in increasing l)
+    double* A = E.data();
+    double* F = Ta.data();
+    for (int sq = 0; sq < ksq; ++sq) {
+      for (int i = t; i < n; i += T) {
+        double* __restrict__ Fi = F + (size_t)i * n;
+        const double* __restrict__ Ai = A + (size_t)i * n;
+        for (int j = 0; j <= i; ++j) Fi[j] = 0.0;
+        for (int l = 0; l <= i; ++l) {
+          const double a = Ai[l];
+          const double* __restrict__ Al = A + (size_t)l * n;
 #pragma GCC ivdep
-        for (int j = 0; j <= l; ++j) Fi[j] += a * El[j];
+          for (int j = 0; j <= l; ++j) Fi[j] += a * Al[j];
+        }
       }
+      std::swap(A, F);
+      bar.wait();
     }
-    std::swap(E, F);
-  }
-  for (int j = 0; j <= M; ++j) {
-    const int i = j + kphi;
-    if (s == 0) {
-      d[j] = E[(size_t)i * n];
-    } else {
-      double acc = 0.0;
-      for (int l = 0; l <= i; ++l) acc += E[(size_t)i * n + l] * E[(size_t)l * n];
-      d[j] = acc;
+    if (t != 0) return;
+    // v = A e_0, then v = A v
+    double* v = va.data();
+    double* w = vb.data();
+    for (int i = 0; i < n; ++i) v[i] = A[(size_t)i * n];
+    const long long nprod = (1LL << (s - ksq)) - 1;
+    for (long long r = 0; r < nprod; ++r) {
+      for (int i = 0; i < n; ++i) {
+        const double* __restrict__ Ai = A + (size_t)i * n;
+        double acc = 0.0;
+        for (int l = 0; l <= i; ++l) acc += Ai[l] * v[l];
+        w[i] = acc;
+      }
+      std::swap(v, w);
+    }
+    for (int j = 0; j <= M; ++j) d[j] = v[j + kphi];
+  };
+  // the helpers wait for the size of the team that could be started
+  std::atomic<int> go{0};
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T_want; ++t) {
+    try {
+      pool.emplace_back([&, t]() {
+        int T;
+        while ((T = go.load(std::memory_order_acquire)) == 0) std::this_thread::yield();
+        team(t, T);
+      });
+    } catch (...) {  // fewer threads than asked for: the team is smaller
+      break;
     }
   }
+  const int T = (int)pool.size() + 1;
+  bar.set(T);
+  go.store(T, std::memory_order_release);
+  team(0, T);
+  for (auto& th : pool) th.join();
   return 0;
 }
 
