@@ -648,7 +648,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // FP64 pipe carries one addition per cell.  Also: ||T^n||_inf and the
 // finiteness checks on integer bit patterns, T^n copied when Tcopy is set,
 // the control block armed for the first substep.
-template <int DIM>
+template <int DIM, bool ND = false>
 __global__ void __launch_bounds__(NT)
 k_step_init_df(LejaCoef<float> cf, float jinv, const float2* __restrict__ rsum,
                const double* __restrict__ b0, const double* __restrict__ T,
@@ -711,20 +711,33 @@ k_step_init_df(LejaCoef<float> cf, float jinv, const float2* __restrict__ rsum,
         S[v] = fmaf(cN[v], (nh - h[v]) + (nl - l[v]), S[v]);
       }
     }
-    const float4 r01 = *reinterpret_cast<const float4*>(rsum + i);
-    const float4 r23 = *reinterpret_cast<const float4*>(rsum + i + 2);
-    const float rh[4] = {r01.x, r01.z, r23.x, r23.z};
-    const float rl[4] = {r01.y, r01.w, r23.y, r23.w};
+    // the row sums: every cell's, or (ND: the rows of J sum to zero off the
+    // x = 0 plane) the x = 0 cell's only
+    float rh[4], rl[4];
+    if constexpr (ND) {
+      const float2 r0 = ix == 0 ? rsum[i] : make_float2(0.f, 0.f);
+      rh[0] = r0.x;
+      rl[0] = r0.y;
+      rh[1] = rh[2] = rh[3] = rl[1] = rl[2] = rl[3] = 0.f;
+    } else {
+      const float4 r01 = *reinterpret_cast<const float4*>(rsum + i);
+      const float4 r23 = *reinterpret_cast<const float4*>(rsum + i + 2);
+      rh[0] = r01.x; rh[1] = r01.z; rh[2] = r23.x; rh[3] = r23.z;
+      rl[0] = r01.y; rl[1] = r01.w; rl[2] = r23.y; rl[3] = r23.w;
+    }
     double gv[4];
     float qv[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const float Sv = S[v] * jinv;
       // r_i T_i (+ b_i) as a float pair (p, e)
-      const float p = rh[v] * h[v];
-      float e = fmaf(rh[v], h[v], -p);
-      e = fmaf(rh[v], l[v], e);
-      e = fmaf(rl[v], h[v], e);
+      float p = 0.f, e = 0.f;
+      if (!ND || v == 0) {
+        p = rh[v] * h[v];
+        e = fmaf(rh[v], h[v], -p);
+        e = fmaf(rh[v], l[v], e);
+        e = fmaf(rl[v], h[v], e);
+      }
       float ph = p;
       if (v == 0 && ix == 0) {  // the x = 0 cell: + b_i
         float bh, bl, s2;
@@ -2786,7 +2799,11 @@ void launch_step_init(const erem_ctx* c, const double* T, const StopParams& sp, 
     if (c->prec == EREM_FP32_BULK) {  // G in the difference form on the FP32 pipe
       const LejaCoef<float> cf = leja_coef<float, 4>(c);
       const float jinv = (float)(1.0 / c->jl_sc);
-      if (c->dim == 3)
+      if (c->dim == 3 && c->jl_nodiag)
+        k_step_init_df<3, true><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
+                                                  (float*)c->q[0], g, sp, c->red_part, c->red_cnt,
+                                                  c->ctrl);
+      else if (c->dim == 3)
         k_step_init_df<3><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
                                             (float*)c->q[0], g, sp, c->red_part, c->red_cnt, c->ctrl);
       else
