@@ -762,6 +762,7 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     out = {"ms": e0.elapsed_time(e1), "cg_iters_per_step": float(np.mean(cg_it)),
            "stage_iters_per_step": float(np.mean(lin_it)),
            "leja_terms_per_step": float(np.mean(degrees)), "launches": launches,
+           "leja_coefs": ctx.leja_coefficients,
            "T": T.cpu().numpy(), "rhoc": rc, "t_terms_ms": t_terms, "n_terms": n_terms,
            "degrees": [m for sc in scheds for m in sc]}
     ctx.close()
@@ -783,7 +784,7 @@ def coupled_summary(E, torch, dev, world, K, Wu):
         runs[key] = r
     h, d, q = runs["erem_fp32_bulk"], runs["erem_fp64"], runs["ros2_fp64"]
     peak, kind = measured_peaks()
-    b = ENS_BYTES_PER_CELL_TERM["fp32_bulk"]  # 2D: 5 coefficients, q in/out, P in/out
+    b = leja_term_bytes("fp32_bulk", h["leja_coefs"])  # 2D: the copy's coefficients, q in/out, P in/out
     bpc = term_bytes_per_cell(b, h["degrees"])
     ach = bpc * wl.n / (h["t_terms_ms"] / 1e3) / 1e9 if h["n_terms"] else None
     rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
@@ -865,6 +866,14 @@ def main_coupled(args):
 ENS_BYTES_PER_CELL_TERM = {"fp32_bulk": 5 * 4 + 4 + 4 + 16, "fp64": 5 * 8 + 8 + 8 + 16}
 
 
+def ensemble_term_bytes(prec, r):
+    """Algorithmic bytes of the run's Leja terms: per member, cells x terms x
+    (its Leja copy's coefficient arrays, q in and out, P in and out)."""
+    esz = 4 if prec == "fp32_bulk" else 8
+    return sum(n * t * (nc * esz + 2 * esz + P_BYTES)
+               for n, t, nc in zip(r["sizes"], r["terms"], r["leja_coefs"]))
+
+
 def ensemble_inputs(E, torch, dev, members):
     """Member fields, GPU pressure solves and heat capacities (Pe = 50 from
     each member's Darcy inflow), as host arrays."""
@@ -922,6 +931,7 @@ def run_ensemble(E, torch, inputs, precision, steps, warmup, dev, sample_clocks=
            "clusters": rs.clusters, "cta_threads": rs.cta_threads, "clocks": clocks, "T": T,
            "tune_s": t_tune,
            "terms": [s.terms for s in stats], "substeps": [s.substeps for s in stats],
+           "leja_coefs": [s.leja_coefficients for s in stats], "sizes": list(ens.sizes),
            "failed": rs.members_failed, "ens": ens}
     return out
 
@@ -987,8 +997,9 @@ def ensemble_summary(E, torch, dev, world, Wu, members=512, steps=30):
     for prec in ("fp32_bulk", "fp64"):
         r = run_ensemble(E, torch, inputs, prec, steps, Wu, dev)
         ms, value = aggregate(r["ms"], cells, steps, world, dev)
-        b = ENS_BYTES_PER_CELL_TERM[prec]
-        ach = b * r["cell_terms"] / (r["run_ms"] / 1e3) / 1e9
+        tb = ensemble_term_bytes(prec, r)
+        b = tb / max(r["cell_terms"], 1)
+        ach = tb / (r["run_ms"] / 1e3) / 1e9
         Ts[prec] = r["T"]
         summary = {"value": value, "ms_per_step": ms / steps, "member_passes": r["passes"],
                    "cluster_ctas": r["cluster_ctas"], "clusters": r["clusters"],
@@ -1031,8 +1042,9 @@ def main_ensemble(args):
     r32 = run_ensemble(E, torch, inputs, "fp32_bulk", K, Wu, dev, sample_clocks=(rank == 0))
     ms, value = aggregate(r32["ms"], cells, K, world, dev)
     peak, peak_kind = measured_peaks()
-    b32 = ENS_BYTES_PER_CELL_TERM["fp32_bulk"]
-    achieved = b32 * r32["cell_terms"] / (r32["run_ms"] / 1e3) / 1e9
+    tb32 = ensemble_term_bytes("fp32_bulk", r32)
+    b32 = tb32 / max(r32["cell_terms"], 1)
+    achieved = tb32 / (r32["run_ms"] / 1e3) / 1e9
     line = {
         "metric": "ensemble EREM Mcell-steps/s (512 independent 2D members, 64^2..512^2, FP32-bulk)",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wu,
@@ -1073,7 +1085,7 @@ def main_ensemble(args):
         num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(r32["T"], r64["T"]))
         den = sum(float(np.sum(b ** 2)) for b in r64["T"])
         line["fp64"] = {"value": value64, "ms_per_step": ms64 / K, "cluster_ctas": r64["cluster_ctas"],
-                        "achieved_gbs": ENS_BYTES_PER_CELL_TERM["fp64"] * r64["cell_terms"]
+                        "achieved_gbs": ensemble_term_bytes("fp64", r64)
                         / (r64["run_ms"] / 1e3) / 1e9}
         line["speedup_fp32_bulk_vs_fp64"] = ms64 / ms
         line["rel_l2_fp32_bulk_vs_fp64"] = float(np.sqrt(num / den))

@@ -526,11 +526,11 @@ EREM_API erem_status erem_set_pressure_multigrid(erem_ctx* ctx, int nu, double o
  * Errors: EINVAL (ctx NULL; lo or hi not finite, or lo > hi). */
 EREM_API erem_status erem_hold_interval(erem_ctx* ctx, int hold, double lo, double hi);
 
-/* Coefficient arrays per cell in ctx's FP32/FP64 Leja copy of J (§4.2: the
- * operator every Leja term applies): 5 (2D) or 7 (3D) with the diagonal;
- * 6 for an FP32-bulk 3D context whose assembled J has every row off the
- * x = 0 inflow plane summing to zero within 2^-28 of the row's couplings
- * (a divergence-free Darcy flux with the linear fluid model): the term then
+/* Coefficient arrays per cell in ctx's Leja copy of J (§4.2: the operator
+ * every Leja term applies): 5 (2D) or 7 (3D) with the diagonal; 4 or 6 for
+ * an FP32-bulk context whose assembled J has every row off the x = 0 inflow
+ * plane summing to zero within 2^-28 of the row's couplings (a
+ * divergence-free Darcy flux with the linear fluid model): the term then
  * forms sum_j J_ij (q_j - q_i) + r_i q_i with r_i kept for the x = 0 cells
  * only, one array fewer to stream (the environment variable
  * EREM_LEJA_DIAG=1, read at assembly, keeps the diagonal).  0 if ctx is
@@ -606,7 +606,9 @@ typedef struct {
                           attempts included)                               */
   int passes;          /* other passes over its cells in the last run      */
   int attempts;        /* failed attempts (substep doublings) in the run   */
-  int pad;
+  int leja_coefficients; /* arrays per cell of its Leja copy of J (as
+                          erem_leja_coefficients: 5, or 4 without the
+                          diagonal)                                          */
   double alpha, beta;  /* Gershgorin interval of dt*J                      */
 } erem_ens_member_stats;
 

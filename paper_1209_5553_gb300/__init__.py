@@ -112,7 +112,8 @@ class erem_ens_member_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int),
                 ("substeps", ctypes.c_int), ("degree_total", ctypes.c_int),
                 ("degrees", ctypes.c_int * 64), ("terms", ctypes.c_int),
-                ("passes", ctypes.c_int), ("attempts", ctypes.c_int), ("pad", ctypes.c_int),
+                ("passes", ctypes.c_int), ("attempts", ctypes.c_int),
+                ("leja_coefficients", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
 
     @property

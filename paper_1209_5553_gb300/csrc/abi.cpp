@@ -795,7 +795,7 @@ erem_status assemble(erem_ctx* c, bool faces, bool rhs, cudaStream_t s) {
   EREM_TRY(check_launch(c, "assembly"));
   EREM_TRY(read_ctrl(c, s));
   EREM_TRY(check_flags(c));
-  // FP32-bulk 3D: where every row of J off the inflow plane sums to zero (a
+  // FP32-bulk: where every row of J off the inflow plane sums to zero (a
   // uniform temperature is transported nowhere; the discrete flux is
   // divergence-free to far below FP32 rounding), the Leja copy keeps the
   // couplings only and the term kernel forms sum_j J_ij (q_j - q_i) + r_i q_i
@@ -1322,7 +1322,7 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   for (int k = 0; k < nc; ++k) A(&c->jc[k], np);
   if (st == EREM_OK) st = dalloc(c, &c->jl_all, (np + 128) / 128 * 128 * nc * esz);
   if (st == EREM_OK && prec == EREM_FP32_BULK) st = dalloc(c, (void**)&c->jrow, np * sizeof(float2));
-  if (st == EREM_OK && prec == EREM_FP32_BULK && g.dim == 3)
+  if (st == EREM_OK && prec == EREM_FP32_BULK)
     st = dalloc(c, (void**)&c->jl_r0, nf * sizeof(float));
   A(&c->Tn, np); A(&c->vrhs, np); A(&c->vin, np); A(&c->w, np); A(&c->u, np); A(&c->P, np);
   for (int k = 0; k < 2; ++k)

@@ -197,6 +197,7 @@ erem_status build(erem_ens* E) {
     for (int k = 0; k < 5; ++k) m.jc[k] = c->jc[k];
     m.b0 = c->b0;
     m.jl = c->jl_all;
+    m.r0 = c->jl_nodiag ? c->jl_r0 : nullptr;
     m.T = c->Tn;
     m.G = c->vrhs;
     m.w = c->w;
@@ -568,6 +569,7 @@ erem_status erem_ensemble_member_stats(const erem_ens* E, int e, erem_ens_member
   std::memset(out, 0, sizeof(*out));
   out->alpha = E->ctx[e]->alpha;
   out->beta = E->ctx[e]->beta;
+  out->leja_coefficients = erem_leja_coefficients(E->ctx[e]);
   if (E->last.empty()) return EREM_OK;
   const EnsState& st = E->last[e];
   out->status = st.phase != ENS_FAILED       ? EREM_OK

@@ -284,7 +284,7 @@ __device__ PassDesc ens_control(EnsCtl& c, const EnsMember& M, const EnsRun R, c
 // One Leja term over the thread's vectors: q_m = ((J_l - shift) q_{m-1}) and,
 // from m = 2, P += d_{m-1} q_{m-1}; returns the thread's sum of q_m^2.  Kept
 // out of line so that the hot loop has the register budget to itself.
-template <typename Tq, int VEC>
+template <typename Tq, int VEC, bool ND>
 __device__ __noinline__ double ens_term_pass(const EnsMember& M, const PassDesc& d, int g0, int G) {
   double r0 = 0.0;
   const int nvec = M.Np / VEC;
@@ -307,10 +307,20 @@ __device__ __noinline__ double ens_term_pass(const EnsMember& M, const PassDesc&
     ldv_l2<Tq, VEC>(qn, qi + i + (row < M.ny - 1 ? M.px : 0));
     const Tq ql = ix > 0 ? __ldcg(qi + i - 1) : Tq(0);
     const Tq qr = ix + VEC < M.px ? __ldcg(qi + i + VEC) : Tq(0);
+    // the Leja copy: D W E S N, or (ND) W E S N with the diagonal implied by
+    // the row sums, zero off the x = 0 column
     Tq c[5][VEC];
-    const size_t off = leja_off<32 * VEC>(i, 5);
+    Tq rsum = Tq(0);  // ND: the row sum of an x = 0 cell
+    if constexpr (ND) {
+      const size_t off = leja_off<32 * VEC>(i, 4);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) ldv<Tq, VEC>(c[k], jl + k * 32 * VEC + off);
+      for (int k = 1; k < 5; ++k) ldv<Tq, VEC>(c[k], jl + (k - 1) * 32 * VEC + off);
+      if (ix == 0) rsum = (Tq)M.r0[row];
+    } else {
+      const size_t off = leja_off<32 * VEC>(i, 5);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ldv<Tq, VEC>(c[k], jl + k * 32 * VEC + off);
+    }
     double p[VEC];
     if (addP) ld2<VEC>(p, P + i);
     Tq out[VEC];
@@ -319,11 +329,20 @@ __device__ __noinline__ double ens_term_pass(const EnsMember& M, const PassDesc&
     for (int k = 0; k < VEC; ++k) {
       const Tq west = k == 0 ? ql : qc[k - 1];
       const Tq east = k == VEC - 1 ? qr : qc[k + 1];
-      Tq a = (c[0][k] - shm) * qc[k];
-      a = fma(c[1][k], west, a);
-      a = fma(c[2][k], east, a);
-      a = fma(c[3][k], qs[k], a);
-      a = fma(c[4][k], qn[k], a);
+      Tq a;
+      if constexpr (ND) {  // sum_j J_ij (q_j - q_i) + (r_i - shift) q_i
+        a = ((k == 0 ? rsum : Tq(0)) - shm) * qc[k];
+        a = fma(c[1][k], west - qc[k], a);
+        a = fma(c[2][k], east - qc[k], a);
+        a = fma(c[3][k], qs[k] - qc[k], a);
+        a = fma(c[4][k], qn[k] - qc[k], a);
+      } else {
+        a = (c[0][k] - shm) * qc[k];
+        a = fma(c[1][k], west, a);
+        a = fma(c[2][k], east, a);
+        a = fma(c[3][k], qs[k], a);
+        a = fma(c[4][k], qn[k], a);
+      }
       out[k] = a;
     }
     stv<Tq, VEC>(qo + i, out);
@@ -413,7 +432,8 @@ __global__ void __launch_bounds__(kEnsThreads, 2) k_ens_cluster(EnsRun R) {
         double r0 = 0.0;
         bool bad = false;
         if (d.phase == ENS_TERM) {
-          r0 = ens_term_pass<Tq, VEC>(M, d, g0, G);
+          r0 = M.r0 ? ens_term_pass<Tq, VEC, true>(M, d, g0, G)
+                    : ens_term_pass<Tq, VEC, false>(M, d, g0, G);
         } else if (d.phase == ENS_INIT || d.phase == ENS_SUBSTART) {
           // INIT: G = J T^n + b, q_0 = G, P = d_0 G.  SUBSTART: q_0 = G + J w.
           const double* x = d.phase == ENS_INIT ? M.T : M.w;

@@ -109,6 +109,7 @@ struct EnsMember {
   const double* jc[5];  // FP64 cell form of J: D W E S N (padded)
   const double* b0;     // constant part of G at the x = 0 cells (ny)
   const void* jl;       // Leja copy of J (context precision, interleaved)
+  const float* r0;      // diagonal-free FP32 copy: the x = 0 row sums (else nullptr)
   double *T, *G, *w, *P;
   void* q[2];
   const double* dd;     // kEnsMaxLevels tables of mmax + 1 divided differences

@@ -2806,6 +2806,10 @@ void launch_step_init(const erem_ctx* c, const double* T, const StopParams& sp, 
       else if (c->dim == 3)
         k_step_init_df<3><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
                                             (float*)c->q[0], g, sp, c->red_part, c->red_cnt, c->ctrl);
+      else if (c->jl_nodiag)
+        k_step_init_df<2, true><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
+                                                  (float*)c->q[0], g, sp, c->red_part, c->red_cnt,
+                                                  c->ctrl);
       else
         k_step_init_df<2><<<nb, NT, 0, s>>>(cf, jinv, c->jrow, c->b0, T, Tcopy, c->vrhs,
                                             (float*)c->q[0], g, sp, c->red_part, c->red_cnt, c->ctrl);
@@ -2867,7 +2871,7 @@ void term_launch(const erem_ctx* c, int m, const Tq* qi, Tq* qo, double cg, cuda
   at[0].val.programmaticStreamSerializationAllowed = (c->pdl && m > 1) ? 1 : 0;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if constexpr (sizeof(Tq) == 4 && DIM == 3) {
+  if constexpr (sizeof(Tq) == 4) {
     if (c->jl_nodiag) {  // the Leja copy holds the couplings only
       if (m == 1)
         cudaLaunchKernelEx(&cfg, k_leja_term1<Tq, VEC, DIM, true>, qi, qo, c->P, c->p0, cf, g,

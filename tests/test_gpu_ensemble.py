@@ -153,11 +153,16 @@ def test_fp64_keep_policy_matches_oracle_replay(ref):
 
 
 def test_fp32_bulk_matches_oracle(ref):
+    # the members' fluxes are divergence-free (the oracle's direct pressure
+    # solves), so their FP32 Leja copies hold the couplings only
     E, members = ref
     with _ensemble(E, members, "fp32_bulk", policy=E.EREM_ENS_KEEP_SUBSTEPS) as ens:
         ens.run(STEPS)
         for k, (case, _, traj, _) in enumerate(members):
+            assert ens.member_stats(k).leja_coefficients == 4, k
             assert C.rel_l2(_get(ens, k), traj[-1]) < FP32_TOL, k
+    with _ensemble(E, members[:1], "fp64") as ens:
+        assert ens.member_stats(0).leja_coefficients == 5
 
 
 def test_cluster_sizes_agree(ref):
