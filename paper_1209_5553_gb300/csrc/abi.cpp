@@ -482,20 +482,25 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
       c->rec_ok = false;
     }
   }
+  // small grids, untaped: each launch takes the stopping test of the term
+  // before it (k_leja_term_lag), so the launch after the stopping term is
+  // needed too: it completes P
+  const int lag = (c->term_lag && !slot0) ? 1 : 0;
   int m = 1, qin = 0;
-  int chunk = forced ? forced : std::max(4, c->last_degree + 2);
+  int chunk = forced ? forced + lag : std::max(4, c->last_degree + 2 + lag);
   // the terms [first, last] of every chunk of launches, in order; with
   // time_terms a pair of events brackets each chunk (not each launch: an
   // event between two terms would stop the next one from being scheduled
   // while the previous one ends)
   std::vector<std::pair<int, int>> chunks;
   while (true) {
-    const int end = forced ? forced : std::min(*M_avail, m + chunk - 1);
+    const int end = forced ? forced + lag : std::min(*M_avail + lag, m + chunk - 1);
     if (o.time_terms) cudaEventRecord(c->ev[2 * chunks.size()], s);
     for (int mm = m; mm <= end; ++mm) {
       if (slot0)
         launch_leja_term_ptr(c, mm, slot0 + (size_t)(mm - 1) * qbytes, slot0 + (size_t)mm * qbytes,
                              cg, s);
+      else if (lag) launch_leja_term_lag(c, mm, qin, cg, s);
       else launch_leja_term(c, mm, qin, cg, s);
       qin ^= 1;
     }
@@ -520,11 +525,11 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
       *degree = h.degree;
       break;
     }
-    if (h.fail || end >= o.m_max) {
+    if (h.fail || end >= o.m_max + lag) {
       *failed = true;
       return EREM_OK;
     }
-    if (end >= *M_avail) {  // table exhausted below m_max: extend it
+    if (end >= *M_avail + lag) {  // table exhausted below m_max: extend it
       *M_avail = mcap;
       EREM_TRY(prepare_dd(c, S, *M_avail, s, phi));
       if (slot0 && c->tape_used + ((size_t)mcap + 1) * qbytes > c->tape_cap) {
@@ -555,7 +560,7 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
     }
   }
   c->last_degree = *degree;
-  if (*degree % 2 == 0) {  // q_M: the tape slot, or the ping-pong buffer of m's parity
+  if (!lag && *degree % 2 == 0) {  // q_M: the tape slot, or the ping-pong buffer of m's parity
     const void* qM = slot0 ? (const void*)(slot0 + (size_t)*degree * qbytes) : c->q[*degree & 1];
     if (fix) *fix = PFixHost{qM, *degree};
     else launch_pfix(c, qM, *degree, s);
@@ -1308,6 +1313,8 @@ erem_status erem_create(const erem_grid* grid, const erem_physics* phys, erem_pr
   }
   c->term_grid = std::min(c->red_blocks, term_waves * c->sm_count * leja_term_blocks_per_sm(c));
   if (const char* e = std::getenv("EREM_TERM_PDL")) c->pdl = std::atoi(e) != 0;  // tuning override
+  c->term_lag = Np <= kLagCells;
+  if (const char* e = std::getenv("EREM_TERM_LAG")) c->term_lag = std::atoi(e) != 0;  // override
   const size_t np = (size_t)Np, nf = (size_t)g.ny * g.nz;
   const size_t esz = prec == EREM_FP32_BULK ? sizeof(float) : sizeof(double);
   erem_status st = EREM_OK;

@@ -95,6 +95,7 @@ __device__ __forceinline__ void arm_ctrl(Ctrl* c, const StopParams& sp) {
   c->fail = 0;
   c->nonfinite = 0;
   c->m_last = 0;
+  c->stop_m = 0x3fffffff;
   c->err = 0.0;
   c->sp = sp;
 }

@@ -56,6 +56,8 @@ struct Ctrl {
   int lin_done;    // linear solver converged (or broke down)
   int lin_it;      // linear solver iterations
   int lin_break;   // linear solver breakdown
+  int stop_m;      // lagged Leja terms: the term the test stopped at (large while running)
+  int pad_ctrl;
   double err;      // mean error estimate at the last term
   double yinf;     // ||T^n||_inf of the current state
   double gmin, gmax;   // Gershgorin bounds of J (before the factor dt)
@@ -168,6 +170,7 @@ struct SmgLevel {
 
 constexpr int kDdShort = 48;    // divided differences of a level's first table
 constexpr int kDdThreads = 8;   // host threads of a divided-difference table
+constexpr long long kLagCells = 4500000;  // padded cells below which Leja terms run lagged
 
 struct DDEntry {
   double c = 0, gamma = 0;
@@ -187,6 +190,7 @@ struct erem_ctx {
   int device = 0, sm_count = 1, red_blocks = 1;
   int term_grid = 1;      // blocks of the one-term kernel (one resident wave)
   bool pdl = true;        // Leja terms launched as programmatic dependents
+  bool term_lag = false;  // small grids: each term's test taken by the next launch (k_leja_term_lag)
   std::string err;
 
   // stored fields (padded, FP64)
@@ -380,6 +384,10 @@ void launch_axpy(const erem_ctx* c, double* w, const double* P, double delta, in
                  cudaStream_t s, const PFixHost* fix = nullptr);
 // P += d_M q_M (dd of the current level)
 void launch_pfix(const erem_ctx* c, const void* q, int M, cudaStream_t s);
+// Lagged form for small grids: launch m tests term m - 1 (block 0) while the
+// other blocks compute term m and add d_{m-1} q_{m-1} to P; m = 1 starts P
+// = d_0 p0.  The launch after the stopping term completes P.
+void launch_leja_term_lag(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s);
 void launch_lincomb(const erem_ctx* c, double* out, double a, const double* x, double b,
                     const double* y, cudaStream_t s);
 

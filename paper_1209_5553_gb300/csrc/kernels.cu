@@ -939,6 +939,131 @@ k_leja_term1(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict_
   leja_term_body<Tq, VEC, DIM, 2, ND>(qi, qo, P, p0, cf, g, xi, dd, cg, 1, part, cnt, ctrl);
 }
 
+// Lagged Leja term m for small grids, where the last block's gather of the
+// partial sums and the stopping test would be a large part of a term.  Block
+// 0 does no sweep: it sums the partials of term m - 1 in block order and takes
+// its stopping test, while blocks 1.. compute q_m = ((J - c) / gamma - xi_{m-1})
+// q_{m-1}, add d_{m-1} q_{m-1} to P (m = 1: P = d_0 p0) and publish their
+// partials of ||q_m||^2 (slot m & 1 of each block).  P thus receives the
+// products one launch after the paired form and in the same order, so both
+// leave the same P for the same degree; the launch after the stopping term
+// completes P and its own q is not used.  A launch returns at once when the
+// test stopped at least two terms before it (ctrl->stop_m, written by block 0
+// of the launch after the stopping term, never acted on by that launch).
+template <typename Tq, int VEC, int DIM, bool ND>
+__global__ void __launch_bounds__(NT, 4)
+k_leja_term_lag(const Tq* __restrict__ qi, Tq* __restrict__ qo, double* __restrict__ P,
+                const double* __restrict__ p0, LejaCoef<Tq> cf, Geo g,
+                const double* __restrict__ xi, const double* __restrict__ dd, double cg, int m,
+                double* part, Ctrl* ctrl) {
+  __shared__ double sh[NT / 32];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+  if (m >= *(volatile int*)&ctrl->stop_m + 2) return;
+  if (blockIdx.x == 0) {
+    if (m >= 2) {  // the stopping test of term m - 1
+      double v = 0.0;
+      for (int b = 1 + threadIdx.x; b < (int)gridDim.x; b += NT)
+        v += __ldcg(part + (size_t)b * kRedSlots + ((m - 1) & 1));
+      const double S = block_reduce<0>(v, sh);
+      if (threadIdx.x == 0) {
+        stop_test(ctrl, m - 1, dd[m - 1], S);
+        if (ctrl->done) ctrl->stop_m = m - 1;
+      }
+    }
+    return;
+  }
+  const Tq sh_m = (Tq)(cg + xi[m - 1]);
+  const double dprev = m >= 2 ? dd[m - 1] : 0.0;
+  const double d0 = dd[0];
+  float s_hi = 0.f, s_lo = 0.f;  // FP32-bulk: compensated sum of squares
+  double acc = 0.0;
+  const int nvec = g.Np / VEC;
+  const int vrow = g.px / VEC;
+  const int G = (gridDim.x - 1) * NT;
+  for (int t = (blockIdx.x - 1) * NT + threadIdx.x; t < nvec; t += G) {
+    const int row = t / vrow;
+    const int ix = (t - row * vrow) * VEC;
+    const int iy = row % g.ny;
+    const int iz = row / g.ny;
+    const int i = row * g.px + ix;
+    Tq qc[VEC], qs[VEC], qn[VEC], qb[VEC], qt[VEC];
+    ldv<Tq, VEC>(qc, qi + i);
+    ldv<Tq, VEC>(qs, qi + i - (iy > 0 ? g.px : 0));
+    ldv<Tq, VEC>(qn, qi + i + (iy < g.ny - 1 ? g.px : 0));
+    if (DIM == 3) {
+      ldv<Tq, VEC>(qb, qi + i - (iz > 0 ? g.plane : 0));
+      ldv<Tq, VEC>(qt, qi + i + (iz < g.nz - 1 ? g.plane : 0));
+    }
+    const Tq ql = ix > 0 ? qi[i - 1] : Tq(0);
+    const Tq qr = ix + VEC < g.px ? qi[i + VEC] : Tq(0);
+    Tq cD[VEC], cW[VEC], cE[VEC], cS[VEC], cN[VEC], cB[VEC], cT[VEC];
+    Tq r0 = Tq(0);
+    if constexpr (ND) {
+      if (ix == 0) r0 = cf.r0[row];
+    } else {
+      ldv_stream<Tq, VEC>(cD, cf.c[0] + leja_off<32 * VEC>(i, cf.nc));
+    }
+    ldv_stream<Tq, VEC>(cW, cf.c[1] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cE, cf.c[2] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cS, cf.c[3] + leja_off<32 * VEC>(i, cf.nc));
+    ldv_stream<Tq, VEC>(cN, cf.c[4] + leja_off<32 * VEC>(i, cf.nc));
+    if (DIM == 3) {
+      ldv_stream<Tq, VEC>(cB, cf.c[5] + leja_off<32 * VEC>(i, cf.nc));
+      ldv_stream<Tq, VEC>(cT, cf.c[6] + leja_off<32 * VEC>(i, cf.nc));
+    }
+    double p[VEC];
+    if (m == 1) ldP<VEC>(p, p0 + i);
+    else ldP<VEC>(p, P + i);
+    Tq out[VEC];
+    Tq sq = Tq(0);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const Tq west = k == 0 ? ql : qc[k - 1];
+      const Tq east = k == VEC - 1 ? qr : qc[k + 1];
+      Tq a;
+      if constexpr (ND) {
+        a = ((k == 0 ? r0 : Tq(0)) - sh_m) * qc[k];
+        a = fma(cW[k], west - qc[k], a);
+        a = fma(cE[k], east - qc[k], a);
+        a = fma(cS[k], qs[k] - qc[k], a);
+        a = fma(cN[k], qn[k] - qc[k], a);
+        if (DIM == 3) {
+          a = fma(cB[k], qb[k] - qc[k], a);
+          a = fma(cT[k], qt[k] - qc[k], a);
+        }
+      } else {
+        a = (cD[k] - sh_m) * qc[k];
+        a = fma(cW[k], west, a);
+        a = fma(cE[k], east, a);
+        a = fma(cS[k], qs[k], a);
+        a = fma(cN[k], qn[k], a);
+        if (DIM == 3) {
+          a = fma(cB[k], qb[k], a);
+          a = fma(cT[k], qt[k], a);
+        }
+      }
+      out[k] = a;
+      if constexpr (sizeof(Tq) == 4) sq = fmaf(a, a, sq);
+      else acc = fma(a, a, acc);
+    }
+#pragma unroll
+    for (int k = 0; k < VEC; ++k)
+      p[k] = m == 1 ? d0 * p[k] : fma(dprev, to_f64_fast(qc[k]), p[k]);
+    if constexpr (sizeof(Tq) == 4) {
+      const float s = s_hi + sq;
+      const float bp = s - s_hi;
+      s_lo += (s_hi - (s - bp)) + (sq - bp);
+      s_hi = s;
+    }
+    stv<Tq, VEC>(qo + i, out);
+    stP<VEC>(P + i, p);
+  }
+  if constexpr (sizeof(Tq) == 4) acc = (double)s_hi + (double)s_lo;
+  const double bs = block_reduce<0>(acc, sh);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.x * kRedSlots + (m & 1)] = bs;
+}
+
 // P += d_M q_M: the last product of a substep stopped at an even degree M
 // (the term kernel updates P at odd m only).
 template <typename Tq>
@@ -2900,6 +3025,47 @@ void term_launch(const erem_ctx* c, int m, const Tq* qi, Tq* qo, double cg, cuda
     cudaLaunchKernelEx(&cfg, k_leja_term<Tq, VEC, DIM, 0>, qi, qo, c->P, cf, g,
                        (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
                        c->red_cnt, c->ctrl);
+}
+
+template <typename Tq, int VEC, int DIM>
+void term_launch_lag(const erem_ctx* c, int m, const Tq* qi, Tq* qo, double cg, cudaStream_t s) {
+  const LejaCoef<Tq> cf = leja_coef<Tq, VEC>(c);
+  const Geo g = geo_of(c);
+  const int nb = std::min(grid_for(c, c->Np / VEC) + 1, c->term_grid);
+  ++c->launches;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(std::max(nb, 2));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = (c->pdl && m > 1) ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if constexpr (sizeof(Tq) == 4) {
+    if (c->jl_nodiag) {
+      cudaLaunchKernelEx(&cfg, k_leja_term_lag<Tq, VEC, DIM, true>, qi, qo, c->P, c->p0, cf, g,
+                         (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
+                         c->ctrl);
+      return;
+    }
+  }
+  cudaLaunchKernelEx(&cfg, k_leja_term_lag<Tq, VEC, DIM, false>, qi, qo, c->P, c->p0, cf, g,
+                     (const double*)c->xi_dev, (const double*)c->dd_dev, cg, m, c->red_part,
+                     c->ctrl);
+}
+
+void launch_leja_term_lag(const erem_ctx* c, int m, int qin, double cg, cudaStream_t s) {
+  const void* qi = c->q[qin];
+  void* qo = c->q[qin ^ 1];
+  if (c->prec == EREM_FP32_BULK) {
+    if (c->dim == 3) term_launch_lag<float, 4, 3>(c, m, (const float*)qi, (float*)qo, cg, s);
+    else term_launch_lag<float, 4, 2>(c, m, (const float*)qi, (float*)qo, cg, s);
+  } else {
+    if (c->dim == 3) term_launch_lag<double, 2, 3>(c, m, (const double*)qi, (double*)qo, cg, s);
+    else term_launch_lag<double, 2, 2>(c, m, (const double*)qi, (double*)qo, cg, s);
+  }
 }
 
 // One Leja term with explicit input/output vectors (the context's ping-pong

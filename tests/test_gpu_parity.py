@@ -199,6 +199,31 @@ def test_diagonal_free_leja_copy(E, name, make, monkeypatch):
     assert C.rel_l2(out["0"][1] - case.T0, out["1"][1] - case.T0) < FP32_TOL
 
 
+@pytest.mark.parametrize("name,make", [CASES_2D[0], CASES_2D[1], CASES_2D[2], CASES_3D[1], CASES_3D[2]],
+                         ids=["heat2d_64", "ragged_65x67", "tiny_5x3", "box_24x20x9", "channels_32"])
+def test_lagged_terms_match_the_paired_form(E, name, make, monkeypatch):
+    # small grids take each term's stopping test in the next launch (block 0)
+    # and add d_{m-1} q_{m-1} to P one launch late: the same schedules and,
+    # up to the order of the partial sums, the same steps as one test per
+    # launch with the paired running sum (EREM_TERM_LAG=0)
+    case = make()
+    steps = 2
+    for prec in ("fp64", "fp32_bulk"):
+        out = {}
+        for lag in ("0", "1"):
+            monkeypatch.setenv("EREM_TERM_LAG", lag)
+            with _ctx(E, case, prec) as ctx:
+                T = _t(case.T0)
+                scheds = []
+                for k in range(steps):
+                    fields = (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam)) if k == 0 else (None,) * 4
+                    scheds.append(ctx.erem_step(T, case.dt, *fields).schedule)
+                out[lag] = (scheds, T.cpu().numpy())
+        assert out["0"][0] == out["1"][0], prec
+        tol = 1e-13 if prec == "fp64" else 1e-6
+        assert C.rel_l2(out["1"][1] - case.T0, out["0"][1] - case.T0) < tol, prec
+
+
 def test_leja_copy_keeps_the_diagonal_for_a_divergent_flux(E, monkeypatch):
     # a pressure that is not the steady solution (the linear head) leaves the
     # interior rows of J with nonzero sums: the copy keeps the diagonal, and
