@@ -55,13 +55,14 @@ def leja_term_bytes(precision: str, ncoef: int) -> int:
     return ncoef * esz + 2 * esz + P_BYTES
 
 
-def term_bytes_per_cell(full_bytes: int, degrees) -> float:
+def term_bytes_per_cell(full_bytes: int, degrees, lagged: bool = False) -> float:
     """Algorithmic bytes per cell of all Leja terms of substeps with these
     degrees: the odd terms (which update P) move full_bytes, the even ones
-    full_bytes - 16."""
+    full_bytes - 16; in the lagged form of small grids every term updates P
+    and moves full_bytes."""
     total = 0
     for m in degrees:
-        odd = (m + 1) // 2
+        odd = m if lagged else (m + 1) // 2
         total += odd * full_bytes + (m - odd) * (full_bytes - P_BYTES)
     return float(total)
 FALLBACK_HBM_GBS = 6800.0
@@ -302,6 +303,7 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
         n_terms += st.n_terms_timed
         n_leja += st.n_launches_timed
         launches += st.launches
+        lagged = bool(st.terms_lagged)
     t1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
@@ -309,7 +311,8 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
     barrier(world)
     out = {"ms": ms, "degrees": degrees, "t_terms_ms": t_terms, "n_terms": n_terms,
            "n_leja": n_leja, "launches": launches, "T": T.cpu().numpy(), "clocks": clocks, "info": info,
-           "alpha": st.alpha, "beta": st.beta, "first": first, "leja_coefs": ctx.leja_coefficients}
+           "alpha": st.alpha, "beta": st.beta, "first": first, "leja_coefs": ctx.leja_coefficients,
+           "lagged": lagged}
     ctx.close()
     return out
 
@@ -602,7 +605,7 @@ def main(args):
     # also read and write P: 48 B per cell for odd m, 32 B for even m with the
     # couplings-only copy (52 and 36 with the diagonal)
     sec_leja = r32["t_terms_ms"] / 1e3
-    bpc = term_bytes_per_cell(b32, [m for s in r32["degrees"] for m in s[1:]])
+    bpc = term_bytes_per_cell(b32, [m for s in r32["degrees"] for m in s[1:]], r32["lagged"])
     achieved = bpc * N / sec_leja / 1e9 if r32["n_terms"] else None
     effective = b32 * N * r32["n_terms"] / sec_leja / 1e9 if r32["n_terms"] else None
     traffic = recorded_traffic("fp32_bulk", N)
@@ -639,7 +642,7 @@ def main(args):
         r64 = run_gpu(E, torch, wl, "fp64", K, Wu, dev, world, capture_first=check)
         ms64, value64 = aggregate(r64["ms"], N, K, world, dev)
         b64 = leja_term_bytes("fp64", r64["leja_coefs"])
-        bpc64 = term_bytes_per_cell(b64, [m for s in r64["degrees"] for m in s[1:]])
+        bpc64 = term_bytes_per_cell(b64, [m for s in r64["degrees"] for m in s[1:]], r64["lagged"])
         ach64 = bpc64 * N / (r64["t_terms_ms"] / 1e3) / 1e9 if r64["n_terms"] else None
         rel = float(np.linalg.norm(r32["T"] - r64["T"]) / np.linalg.norm(r64["T"]))
         line["fp64"] = {"value": value64, "ms_per_step": ms64 / K,
@@ -757,12 +760,13 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
         launches += s1.launches + s2.launches
         t_terms += s2.t_terms_ms
         n_terms += s2.n_terms_timed
+        lagged = bool(s2.terms_lagged)
     e1.record(stream)
     torch.cuda.synchronize()
     out = {"ms": e0.elapsed_time(e1), "cg_iters_per_step": float(np.mean(cg_it)),
            "stage_iters_per_step": float(np.mean(lin_it)),
            "leja_terms_per_step": float(np.mean(degrees)), "launches": launches,
-           "leja_coefs": ctx.leja_coefficients,
+           "leja_coefs": ctx.leja_coefficients, "lagged": lagged,
            "T": T.cpu().numpy(), "rhoc": rc, "t_terms_ms": t_terms, "n_terms": n_terms,
            "degrees": [m for sc in scheds for m in sc]}
     ctx.close()
@@ -785,7 +789,8 @@ def coupled_summary(E, torch, dev, world, K, Wu):
     h, d, q = runs["erem_fp32_bulk"], runs["erem_fp64"], runs["ros2_fp64"]
     peak, kind = measured_peaks()
     b = leja_term_bytes("fp32_bulk", h["leja_coefs"])  # 2D: the copy's coefficients, q in/out, P in/out
-    bpc = term_bytes_per_cell(b, h["degrees"])
+    h_lag = h["lagged"]
+    bpc = term_bytes_per_cell(b, h["degrees"], h_lag)
     ach = bpc * wl.n / (h["t_terms_ms"] / 1e3) / 1e9 if h["n_terms"] else None
     rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
     return {
@@ -803,7 +808,9 @@ def coupled_summary(E, torch, dev, world, K, Wu):
         "roofline": {"kernel": "k_leja_term<float,4,2>", "bound": "hbm", "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,
                      "peak_source": f"{kind} hbm_gbs",
-                     "algorithmic_bytes_per_cell": {"odd_terms": b, "even_terms": b - P_BYTES},
+                     "algorithmic_bytes_per_cell": {"odd_terms": b,
+                                                   "even_terms": b if h_lag else b - P_BYTES},
+                     "terms_lagged": h_lag,
                      "term_ms_avg": h["t_terms_ms"] / max(h["n_terms"], 1),
                      "note": "the 1024^2 term's working set (about 50 MB) stays in L2, so the "
                              "achieved rate is not an HBM figure"},
@@ -1177,8 +1184,9 @@ def adjoint_forward_terms(E, torch, wl, phys, t):
             ms += st.t_terms_ms
             terms += st.n_terms_timed
             degrees += list(st.degrees[:st.substeps])
+            lagged = bool(st.terms_lagged)
         ncoef = ctx.leja_coefficients
-    return ms, terms, degrees, ncoef
+    return ms, terms, degrees, ncoef, lagged
 
 
 def adjoint_summary(E, torch, dev, world, n=128, K=2, Wu=1):
@@ -1190,9 +1198,10 @@ def adjoint_summary(E, torch, dev, world, n=128, K=2, Wu=1):
     r, f, q = runs["fp32_bulk"], runs["fp32_bulk_full_tape"], runs["fp64"]
     ms = max_over_ranks(r["ms_per_gradient"], world, dev)
     peak, kind = measured_peaks()
-    tms, terms, degrees, ncoef = adjoint_forward_terms(E, torch, wl, phys, t)
+    tms, terms, degrees, ncoef, lagged = adjoint_forward_terms(E, torch, wl, phys, t)
     b = leja_term_bytes("fp32_bulk", ncoef)
-    ach = term_bytes_per_cell(b, degrees) * wl.n / (tms / 1e3) / 1e9 if terms else None
+    h_lag = lagged
+    ach = term_bytes_per_cell(b, degrees, lagged) * wl.n / (tms / 1e3) / 1e9 if terms else None
     rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
     return {
         "workload": f"adjoint3d_{n}", "cells": wl.n, "erem_steps": wl.steps, "gradients": K,
@@ -1208,7 +1217,9 @@ def adjoint_summary(E, torch, dev, world, n=128, K=2, Wu=1):
         "roofline": {"kernel": "k_leja_term<float,4,3>", "bound": "hbm", "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,
                      "peak_source": f"{kind} hbm_gbs",
-                     "algorithmic_bytes_per_cell": {"odd_terms": b, "even_terms": b - P_BYTES},
+                     "algorithmic_bytes_per_cell": {"odd_terms": b,
+                                                   "even_terms": b if h_lag else b - P_BYTES},
+                     "terms_lagged": h_lag,
                      "term_ms_avg": tms / max(terms, 1),
                      "note": "timed over a 60-step forward run; a 128^3 term moves 109 MB, "
                              "partly served by the 129 MB L2"},

@@ -125,6 +125,9 @@ typedef struct {
   int n_launches_timed; /* time_terms: Leja kernel launches in t_terms_ms
                            (those after the stop included)                   */
   int degree_phi2;      /* erem_step_forced: degree of the phi_2 interpolation */
+  int terms_lagged;     /* 1: the Leja terms of this call took each stopping
+                           test in the next launch (small grids, untaped):
+                           the running sum was updated at every term         */
 } erem_stats;
 
 typedef struct erem_ctx erem_ctx;

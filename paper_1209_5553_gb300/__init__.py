@@ -64,7 +64,8 @@ class erem_stats(ctypes.Structure):
                 ("flux_in", ctypes.c_double), ("vmax", ctypes.c_double),
                 ("t_ms", ctypes.c_double), ("t_terms_ms", ctypes.c_double),
                 ("n_terms_timed", ctypes.c_int), ("launches", ctypes.c_int),
-                ("n_launches_timed", ctypes.c_int), ("degree_phi2", ctypes.c_int)]
+                ("n_launches_timed", ctypes.c_int), ("degree_phi2", ctypes.c_int),
+                ("terms_lagged", ctypes.c_int)]
 
     @property
     def schedule(self):

@@ -486,6 +486,7 @@ erem_status leja_interp(erem_ctx* c, const double* u, const double* fused_T, int
   // before it (k_leja_term_lag), so the launch after the stopping term is
   // needed too: it completes P
   const int lag = (c->term_lag && !slot0) ? 1 : 0;
+  if (lag) c->last_lag = true;
   int m = 1, qin = 0;
   int chunk = forced ? forced + lag : std::max(4, c->last_degree + 2 + lag);
   // the terms [first, last] of every chunk of launches, in order; with
@@ -1434,6 +1435,7 @@ erem_status pressure_solve(erem_ctx* c, const double* lnk, const double* T, doub
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   if (!lnk || !p) return fail(c, EREM_EINVAL, "lnk and p must not be NULL");
   if (!(tol > 0.0) || maxit < 0) return fail(c, EREM_EINVAL, "tol must be > 0 and maxit >= 0");
@@ -1460,6 +1462,7 @@ erem_status pressure_solve(erem_ctx* c, const double* lnk, const double* T, doub
     st->vmax = c->ctrl_h->vmax;
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
+    st->terms_lagged = c->last_lag ? 1 : 0;
   }
   if (h.lin_break && !(h.lin[K_RR] <= h.lin[K_TOL2]))
     return fail(c, EREM_ENOTCONV, "CG breakdown (matrix not positive definite?)");
@@ -1485,6 +1488,7 @@ erem_status phi1_apply(erem_ctx* c, const double* v, double* out, const erem_lej
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   if (!c->have_state || !c->jl_valid) return fail(c, EREM_EINVAL, "phi1_apply before erem_set_state");
   if (!v || !out) return fail(c, EREM_EINVAL, "NULL vector");
@@ -1501,6 +1505,7 @@ erem_status phi1_apply(erem_ctx* c, const double* v, double* out, const erem_lej
   if (st) {
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
+    st->terms_lagged = c->last_lag ? 1 : 0;
   }
   return EREM_OK;
 }
@@ -1511,6 +1516,7 @@ erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   Opts o;
   EREM_TRY(parse_opts(c, opts, &o));
@@ -1559,6 +1565,7 @@ erem_status erem_step(erem_ctx* c, double* T, const double* p, const double* lnk
   if (st) {
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
+    st->terms_lagged = c->last_lag ? 1 : 0;
   }
   return EREM_OK;
 }
@@ -1570,6 +1577,7 @@ erem_status erem_step_forced(erem_ctx* c, double* T, double dt, double T_in, dou
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   if (c->phys.fluid_model != 0)
     return fail(c, EREM_EINVAL, "erem_step_forced needs fluid_model 0 (G affine in T_in)");
@@ -1607,6 +1615,7 @@ erem_status erem_step_forced(erem_ctx* c, double* T, double dt, double T_in, dou
   if (st) {
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
+    st->terms_lagged = c->last_lag ? 1 : 0;
   }
   return EREM_OK;
 }
@@ -1617,6 +1626,7 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   if (scheme != EREM_ROSM1 && scheme != EREM_ROSM_HALF && scheme != EREM_ROS2 &&
       scheme != EREM_ROS3P)
@@ -1716,6 +1726,7 @@ erem_status rosm_step(erem_ctx* c, double* T, const double* p, const double* lnk
     st->err_est = embedded ? std::sqrt(c->ctrl_h->lin[K_EMB] / (double)c->N) : 0.0;
     st->t_ms = now_ms() - t0;
     st->launches = (int)c->launches;
+    st->terms_lagged = c->last_lag ? 1 : 0;
   }
   return EREM_OK;
 }
@@ -1837,6 +1848,7 @@ erem_status phi1_apply_krylov(erem_ctx* c, const double* v, double* out, const e
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   if (!c->have_state) return fail(c, EREM_EINVAL, "phi1_apply_krylov before erem_set_state");
   if (!v || !out) return fail(c, EREM_EINVAL, "NULL vector");
@@ -1865,6 +1877,7 @@ erem_status erem_step_krylov(erem_ctx* c, double* T, const double* p, const doub
   if (!c) return EREM_EINVAL;
   const double t0 = now_ms();
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   KrOpts o;
   EREM_TRY(parse_kr_opts(c, opts, &o));
@@ -1983,6 +1996,7 @@ erem_status erem_adjoint_step(erem_ctx* c, const double* T, double* lam, const i
                               int ns, void* stream) {
   if (!c) return EREM_EINVAL;
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   EREM_TRY(adj_check(c));
   if (!T || !lam || !sched) return fail(c, EREM_EINVAL, "NULL argument");
@@ -2105,6 +2119,7 @@ erem_status erem_adjoint_lnk(erem_ctx* c, const double* lnk, double* glnk, doubl
                              erem_stats* st, void* stream) {
   if (!c) return EREM_EINVAL;
   c->launches = 0;
+  c->last_lag = false;
   cudaStream_t s = (cudaStream_t)stream;
   EREM_TRY(adj_check(c));
   if (!c->adj_gx) return fail(c, EREM_EINVAL, "erem_adjoint_lnk before erem_adjoint_begin");
@@ -2126,6 +2141,7 @@ erem_status erem_adjoint_lnk(erem_ctx* c, const double* lnk, double* glnk, doubl
     st->lin_iters = h.lin_it;
     st->lin_resid = h.lin[K_BB] > 0 ? std::sqrt(h.lin[K_RR] / h.lin[K_BB]) : 0.0;
     st->launches = (int)c->launches;
+    st->terms_lagged = c->last_lag ? 1 : 0;
   }
   if (h.lin_break && !(h.lin[K_RR] <= h.lin[K_TOL2]))
     return fail(c, EREM_ENOTCONV, "adjoint pressure CG breakdown");

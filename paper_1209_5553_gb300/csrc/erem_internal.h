@@ -191,6 +191,7 @@ struct erem_ctx {
   int term_grid = 1;      // blocks of the one-term kernel (one resident wave)
   bool pdl = true;        // Leja terms launched as programmatic dependents
   bool term_lag = false;  // small grids: each term's test taken by the next launch (k_leja_term_lag)
+  mutable bool last_lag = false;  // the current call ran lagged terms
   std::string err;
 
   // stored fields (padded, FP64)

@@ -217,7 +217,9 @@ def test_lagged_terms_match_the_paired_form(E, name, make, monkeypatch):
                 scheds = []
                 for k in range(steps):
                     fields = (_t(case.p), _t(case.lnk), _t(case.phi), _t(case.lam)) if k == 0 else (None,) * 4
-                    scheds.append(ctx.erem_step(T, case.dt, *fields).schedule)
+                    st = ctx.erem_step(T, case.dt, *fields)
+                    assert st.terms_lagged == int(lag)
+                    scheds.append(st.schedule)
                 out[lag] = (scheds, T.cpu().numpy())
         assert out["0"][0] == out["1"][0], prec
         tol = 1e-13 if prec == "fp64" else 1e-6
