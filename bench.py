@@ -285,7 +285,9 @@ def run_gpu(E, torch, wl, precision, steps, warmup, dev, world, sample_clocks=Fa
     if capture_first:  # the first step from T^0, untimed, for the oracle check
         st = ctx.erem_step(T, wl.dt, opts=opts)
         first = {"T": T.cpu().numpy(), "schedule": st.schedule}
-    for _ in range(warmup):
+    # the captured step is the first warm-up step, so that every arm ends on
+    # the same state and the cross-arm differences compare the same steps
+    for _ in range(warmup - (1 if first is not None else 0)):
         ctx.erem_step(T, wl.dt, opts=opts)
     torch.cuda.synchronize()
     barrier(world)

@@ -1103,6 +1103,7 @@ void kr_phi1_hbar(const KrDev& K, int k, double delta, std::vector<double>* out)
 erem_status run_krylov(erem_ctx* c, const double* src, const KrOpts& o, erem_krylov_stats* st,
                        cudaStream_t s) {
   EREM_TRY(ensure_kr(c, o.m));
+  c->kr_pass = 0;  // the same sweep directions on every call
   EREM_TRY(read_ctrl(c, s));
   EREM_TRY(check_flags(c));
   const double tau = c->dt;

@@ -254,6 +254,7 @@ struct erem_ctx {
   erem::KrDev* kr_dev = nullptr;
   erem::KrDev* kr_host = nullptr;   // pinned
   int kr_cap = 0;                   // basis vectors allocated
+  mutable unsigned kr_pass = 0;     // Krylov passes launched (their direction alternates)
   // adjoint (allocated on first use)
   void* jlT_all = nullptr;          // Leja copy of J^T (FP32: interleaved per 32 adj_vec cells)
   int adj_vec = 2;                  // cells per thread of the FP32 Horner pass

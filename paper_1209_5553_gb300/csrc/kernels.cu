@@ -1097,12 +1097,20 @@ __device__ __forceinline__ void kr_cell(int ip, const Geo& g, int& ix, int& iy, 
   iz = row / g.ny;
 }
 
+// Consecutive passes sweep the cells in opposite directions (rev = 1: from
+// the last cell down), so that a pass starts on the cells whose vectors the
+// previous pass left in L2.
+__device__ __forceinline__ int kr_index(int idx, int Np, int rev) { return rev ? Np - 1 - idx : idx; }
+
 // beta = ||r||_2, arms the breakdown flag
 __global__ void k_kr_norm0(const double* __restrict__ r, Geo g, double btol, double* part,
-                           unsigned* cnt, KrDev* K) {
+                           unsigned* cnt, KrDev* K, int rev) {
   __shared__ double sh[NT / 32];
   double acc = 0.0;
-  for (int ip = blockIdx.x * NT + threadIdx.x; ip < g.Np; ip += gridDim.x * NT) acc = fma(r[ip], r[ip], acc);
+  for (int idx = blockIdx.x * NT + threadIdx.x; idx < g.Np; idx += gridDim.x * NT) {
+    const int ip = kr_index(idx, g.Np, rev);
+    acc = fma(r[ip], r[ip], acc);
+  }
   double vals[1] = {block_reduce<0>(acc, sh)};
   if (publish_partials(part, cnt, vals, 1)) {
     const double s = gather_partials<0>(part, 0, sh);
@@ -1119,26 +1127,21 @@ __global__ void k_kr_norm0(const double* __restrict__ r, Geo g, double btol, dou
 // mode 0: the partial dot w_out . v_0 -> H(0, j); mode 1: ||w_out||_2 -> avnorm.
 __global__ void k_kr_matvec(JIn J, const double* __restrict__ w_in, double* __restrict__ v_out,
                             double* __restrict__ w_out, const double* __restrict__ v0, Geo g, int j,
-                            int mode, double* part, unsigned* cnt, KrDev* K) {
+                            int mode, double* part, unsigned* cnt, KrDev* K, int rev) {
   __shared__ double sh[NT / 32];
   if (*(volatile int*)&K->breakdown >= 0) return;
   const double h = j == 0 ? K->beta : K->H[j * kKrMax + (j - 1)];
   const double s = 1.0 / h;
   double acc = 0.0;
-  for (int ip = blockIdx.x * NT + threadIdx.x; ip < g.Np; ip += gridDim.x * NT) {
+  for (int idx = blockIdx.x * NT + threadIdx.x; idx < g.Np; idx += gridDim.x * NT) {
+    const int ip = kr_index(idx, g.Np, rev);
     int ix, iy, iz;
     kr_cell(ip, g, ix, iy, iz);
     const double vc = s * w_in[ip];
     v_out[ip] = vc;
-    double a = J.c[0][ip] * vc;
-    if (ix > 0) a += J.c[1][ip] * (s * w_in[ip - 1]);
-    if (ix < g.nx - 1) a += J.c[2][ip] * (s * w_in[ip + 1]);
-    if (iy > 0) a += J.c[3][ip] * (s * w_in[ip - g.px]);
-    if (iy < g.ny - 1) a += J.c[4][ip] * (s * w_in[ip + g.px]);
-    if (g.dim == 3) {
-      if (iz > 0) a += J.c[5][ip] * (s * w_in[ip - g.plane]);
-      if (iz < g.nz - 1) a += J.c[6][ip] * (s * w_in[ip + g.plane]);
-    }
+    // J v_j = s (J w_in): one scaling of the sum instead of one per operand
+    // (ten FP64 operations per cell instead of fifteen)
+    const double a = s * japply_cell(J, w_in, ip, ix, iy, iz, g);
     w_out[ip] = a;
     acc = fma(a, mode == 0 ? (j == 0 ? vc : v0[ip]) : a, acc);
   }
@@ -1157,12 +1160,13 @@ __global__ void k_kr_matvec(JIn J, const double* __restrict__ w_in, double* __re
 // the last pass ||w||_2 -> h_{j+1,j} (and the breakdown test).
 __global__ void k_kr_orth(double* __restrict__ w, const double* __restrict__ vprev,
                           const double* __restrict__ vi, Geo g, int i, int j, int last,
-                          double* part, unsigned* cnt, KrDev* K) {
+                          double* part, unsigned* cnt, KrDev* K, int rev) {
   __shared__ double sh[NT / 32];
   if (*(volatile int*)&K->breakdown >= 0) return;
   const double h = K->H[(i - 1) * kKrMax + j];
   double acc = 0.0;
-  for (int ip = blockIdx.x * NT + threadIdx.x; ip < g.Np; ip += gridDim.x * NT) {
+  for (int idx = blockIdx.x * NT + threadIdx.x; idx < g.Np; idx += gridDim.x * NT) {
+    const int ip = kr_index(idx, g.Np, rev);
     const double x = w[ip] - h * vprev[ip];
     w[ip] = x;
     acc = fma(x, last ? x : vi[ip], acc);
@@ -1184,8 +1188,9 @@ __global__ void k_kr_orth(double* __restrict__ w, const double* __restrict__ vpr
 }
 
 // y += sum_i coef_i v_i
-__global__ void k_kr_combine(double* __restrict__ y, KrComb cb, int Np) {
-  for (int ip = blockIdx.x * NT + threadIdx.x; ip < Np; ip += gridDim.x * NT) {
+__global__ void k_kr_combine(double* __restrict__ y, KrComb cb, int Np, int rev) {
+  for (int idx = blockIdx.x * NT + threadIdx.x; idx < Np; idx += gridDim.x * NT) {
+    const int ip = kr_index(idx, Np, rev);
     double a = y[ip];
     for (int k = 0; k < cb.n; ++k) a = fma(cb.coef[k], cb.v[k][ip], a);
     y[ip] = a;
@@ -3445,28 +3450,32 @@ void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream
 // ---------------------------------------------------------------------------
 // Krylov
 // ---------------------------------------------------------------------------
+// the direction of the next Krylov pass: alternating
+int kr_dir(const erem_ctx* c) { return (int)(c->kr_pass++ & 1u); }
+
 void launch_kr_norm0(const erem_ctx* c, const double* r, double btol, cudaStream_t s) {
   ++c->launches;
-  k_kr_norm0<<<blocks_padded(c), NT, 0, s>>>(r, geo_of(c), btol, c->red_part, c->red_cnt, c->kr_dev);
+  k_kr_norm0<<<blocks_padded(c), NT, 0, s>>>(r, geo_of(c), btol, c->red_part, c->red_cnt, c->kr_dev,
+                                             kr_dir(c));
 }
 
 void launch_kr_matvec(const erem_ctx* c, const double* w_in, double* v_out, double* w_out, int j,
                       int mode, cudaStream_t s) {
   ++c->launches;
   k_kr_matvec<<<blocks_padded(c), NT, 0, s>>>(jin(c), w_in, v_out, w_out, c->kr_V[0], geo_of(c), j,
-                                              mode, c->red_part, c->red_cnt, c->kr_dev);
+                                              mode, c->red_part, c->red_cnt, c->kr_dev, kr_dir(c));
 }
 
 void launch_kr_orth(const erem_ctx* c, double* w, const double* vprev, const double* vi, int i,
                     int j, int last, cudaStream_t s) {
   ++c->launches;
   k_kr_orth<<<blocks_padded(c), NT, 0, s>>>(w, vprev, vi, geo_of(c), i, j, last, c->red_part,
-                                            c->red_cnt, c->kr_dev);
+                                            c->red_cnt, c->kr_dev, kr_dir(c));
 }
 
 void launch_kr_combine(const erem_ctx* c, double* y, const KrComb& cb, cudaStream_t s) {
   ++c->launches;
-  k_kr_combine<<<blocks_padded(c), NT, 0, s>>>(y, cb, (int)c->Np);
+  k_kr_combine<<<blocks_padded(c), NT, 0, s>>>(y, cb, (int)c->Np, kr_dir(c));
 }
 
 
