@@ -3451,7 +3451,7 @@ void launch_unpack(const erem_ctx* c, const double* src, double* dst, cudaStream
 // Krylov
 // ---------------------------------------------------------------------------
 // the direction of the next Krylov pass: alternating
-int kr_dir(const erem_ctx* c) { return (int)(c->kr_pass++ & 1u); }
+static int kr_dir(const erem_ctx* c) { return (int)(c->kr_pass++ & 1u); }
 
 void launch_kr_norm0(const erem_ctx* c, const double* r, double btol, cudaStream_t s) {
   ++c->launches;
