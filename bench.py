@@ -32,6 +32,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import types
 
 import numpy as np
 
@@ -93,8 +94,8 @@ def parse_args():
     ap.add_argument("--members", type=int, default=512, help="ensemble members")
     ap.add_argument("--arms", default="all",
                     help="coupled2d: comma-separated subset of erem_fp32_bulk, erem_fp64, ros2_fp64, "
-                         "ros3p_fp64, erem_strang_fp32_bulk, erem_from_last_fp32_bulk (the line "
-                         "needs erem_fp32_bulk); adjoint: subset of fp32_full_tape, fp64 (the "
+                         "ros3p_fp64, erem_strang_fp32_bulk, erem_from_last_fp32_bulk, and the "
+                         "opt-in ros2_adaptive_fp64 (the line needs erem_fp32_bulk); adjoint: subset of fp32_full_tape, fp64 (the "
                          "checkpointed FP32-bulk arm always runs)")
     return ap.parse_args()
 
@@ -730,6 +731,7 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     opts = E.leja_opts(tol=wl.tol, time_terms=True)
     stream = torch.cuda.current_stream()
     T_p = T.clone()  # the temperature p was solved at
+    ada = {"h0": wl.dt, "accepted": [], "rejected": []}
 
     def step():
         if scheme == "strang":
@@ -741,6 +743,20 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
         s1 = ctx.pressure_solve(lnk, T, p, tol=1e-10, maxit=200000)
         if scheme == "erem":
             s2 = ctx.erem_step(T, wl.dt, p, lnk, phi, lam, opts=opts)
+        elif scheme in ("ros2_adaptive", "ros3p_adaptive"):
+            # the heat step over dt by embedded-ROS error control (tolerances of
+            # the EREM arms), starting from the previous step's longest
+            # accepted length
+            code = E.EREM_ROS3P if scheme == "ros3p_adaptive" else E.EREM_ROS2
+            ctx.set_state(T, p, lnk, phi, lam, wl.dt)
+            a, dts = ctx.rosm_integrate(T, wl.dt, ada["h0"], code, wl.tol, wl.tol, lin_tol=1e-10,
+                                        maxit=20000)
+            ada["h0"] = min(wl.dt, a.dt_max)
+            ada["accepted"].append(a.accepted)
+            ada["rejected"].append(a.rejected)
+            s2 = types.SimpleNamespace(lin_iters=a.lin_iters, degree_total=0, degrees=[],
+                                       substeps=0, launches=a.launches, t_terms_ms=0.0,
+                                       n_terms_timed=0, terms_lagged=0)
         else:
             code = E.EREM_ROS3P if scheme == "ros3p" else E.EREM_ROS2
             s2 = ctx.rosm_step(T, wl.dt, code, p, lnk, phi, lam, lin_tol=1e-10, maxit=20000)
@@ -771,6 +787,9 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
            "leja_coefs": ctx.leja_coefficients, "lagged": lagged,
            "T": T.cpu().numpy(), "rhoc": rc, "t_terms_ms": t_terms, "n_terms": n_terms,
            "degrees": [m for sc in scheds for m in sc]}
+    if ada["accepted"]:
+        out["ros_steps_per_step"] = float(np.mean(ada["accepted"][-steps:]))
+        out["ros_rejections_per_step"] = float(np.mean(ada["rejected"][-steps:]))
     ctx.close()
     return out
 
@@ -836,10 +855,12 @@ def main_coupled(args):
     arms = (("erem_fp32_bulk", "erem", "fp32_bulk"), ("erem_fp64", "erem", "fp64"),
             ("ros2_fp64", "ros2", "fp64"), ("ros3p_fp64", "ros3p", "fp64"),
             ("erem_strang_fp32_bulk", "strang", "fp32_bulk"),
-            ("erem_from_last_fp32_bulk", "erem_from_last", "fp32_bulk"))
+            ("erem_from_last_fp32_bulk", "erem_from_last", "fp32_bulk"),
+            ("ros2_adaptive_fp64", "ros2_adaptive", "fp64"))
+    opt_in = {"ros2_adaptive_fp64"}  # not part of "all": many short ROS steps per coupled step
     want = None if args.arms == "all" else set(args.arms.split(",")) | {"erem_fp32_bulk"}
     for key, scheme, prec in arms:
-        if want is not None and key not in want:
+        if (want is None and key in opt_in) or (want is not None and key not in want):
             continue
         r = run_coupled(E, torch, wl, scheme, prec, K, Wu, dev)
         ms, value = aggregate(r["ms"], wl.n, K, world, dev)
@@ -860,7 +881,8 @@ def main_coupled(args):
                      "cg_iters_per_step": r["cg_iters_per_step"],
                      "stage_iters_per_step": r["stage_iters_per_step"],
                      "leja_terms_per_step": r["leja_terms_per_step"],
-                     "rel_l2_vs_erem_fp64": float(np.linalg.norm(r["T"] - ref) / np.linalg.norm(ref))}
+                     "rel_l2_vs_erem_fp64": float(np.linalg.norm(r["T"] - ref) / np.linalg.norm(ref)),
+                     **{q: r[q] for q in ("ros_steps_per_step", "ros_rejections_per_step") if q in r}}
                  for k, r in runs.items()},
     }
     if rank == 0:
