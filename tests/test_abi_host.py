@@ -134,7 +134,10 @@ def test_null_context_error_message(E):
 
 
 def test_create_rejects_bad_grids_without_touching_the_gpu(E):
-    for dims in [(4, 8, 8, 1), (2, 0, 8, 1), (2, 8, 8, 3), (3, 8, 8, 0)]:
+    # bad dimensions, empty extents, and grids whose padded cell count reaches
+    # the 32-bit cell index (46344^2 in 2D, 1290^3 in 3D)
+    for dims in [(4, 8, 8, 1), (2, 0, 8, 1), (2, 8, 8, 3), (3, 8, 8, 0), (2, 46344, 46344, 1),
+                 (3, 1290, 1290, 1290)]:
         g = E.erem_grid(*dims, 1.0, 1.0, 1.0)
         with pytest.raises(E.EremError) as ei:
             E.erem_create(g, E.Physics().c(), E.EREM_FP64)
