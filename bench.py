@@ -960,7 +960,7 @@ def run_ensemble(E, torch, inputs, precision, steps, warmup, dev, sample_clocks=
     out = {"ms": ms, "run_ms": rs.t_ms, "passes": rs.passes, "cells": rs.cells,
            "cell_terms": rs.cell_terms, "cell_passes": rs.cell_passes, "cluster_ctas": rs.cluster_ctas,
            "clusters": rs.clusters, "cta_threads": rs.cta_threads, "clocks": clocks, "T": T,
-           "tune_s": t_tune,
+           "tune_s": t_tune, "graph": rs.graph,
            "terms": [s.terms for s in stats], "substeps": [s.substeps for s in stats],
            "leja_coefs": [s.leja_coefficients for s in stats], "sizes": list(ens.sizes),
            "failed": rs.members_failed, "ens": ens}
@@ -1034,7 +1034,7 @@ def ensemble_summary(E, torch, dev, world, Wu, members=512, steps=30):
         Ts[prec] = r["T"]
         summary = {"value": value, "ms_per_step": ms / steps, "member_passes": r["passes"],
                    "cluster_ctas": r["cluster_ctas"], "clusters": r["clusters"],
-                   "autotune_s": r["tune_s"],
+                   "cuda_graph": bool(r["graph"]), "autotune_s": r["tune_s"],
                    "terms_per_member_run": {"median": float(np.median(r["terms"])),
                                             "max": int(max(r["terms"]))}}
         if prec == "fp32_bulk":
@@ -1085,6 +1085,7 @@ def main_ensemble(args):
                    "sizes": "n ~ U{64..512} (seeded), sigma ~ U[0.5, 2.5], Pe 50, dt 0.05, tol 1e-6",
                    "substep_policy": "keep (autotuned start)", "cluster_ctas": r32["cluster_ctas"],
                    "clusters": r32["clusters"], "cta_threads": r32["cta_threads"],
+                   "cuda_graph": bool(r32["graph"]),
                    "l2": "all members 1.9 GB of Leja working set (> L2); one member's (at most "
                          "9.4 MB) stays L2-resident while its cluster runs it",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -626,6 +626,10 @@ typedef struct {
   int clusters;          /* clusters launched (resident at once)           */
   int cta_threads;       /* threads per CTA                                */
   int members_failed;
+  int graph;             /* 1: the run was replayed from its captured CUDA
+                            graph (uploads, the launch, the read-back);
+                            0: launched directly (capture unavailable)     */
+  int reserved;
 } erem_ens_run_stats;
 
 /* Create an ensemble of n_members 2D members (grids[e].dim must be 2),
@@ -671,7 +675,12 @@ EREM_API erem_status erem_ensemble_configure(erem_ens* ens, const erem_leja_opts
  * reach, by doubling).  Errors as erem_ensemble_run. */
 EREM_API erem_status erem_ensemble_autotune(erem_ens* ens, int probe_steps, void* stream);
 
-/* Advance every member by `steps` EREM steps (one kernel launch).  Returns
+/* Advance every member by `steps` EREM steps (one kernel launch).  The run
+ * (the member states and queue order uploaded from pinned host memory, the
+ * persistent launch, the states read back) is captured once as a CUDA graph
+ * per run configuration (the members' tables, the options, the cluster
+ * shape) and replayed on `stream`; where capture is not available it is
+ * launched directly (erem_ensemble_run_stats.graph tells which).  Returns
  * when the run is complete.  A member whose Leja interpolation fails (the
  * stopping test not met within m_max terms, or a non-finite estimate: the
  * Newton vectors left the range of the Leja precision) takes its step again

@@ -127,7 +127,7 @@ class erem_ens_run_stats(ctypes.Structure):
                 ("cells", ctypes.c_longlong), ("cell_terms", ctypes.c_longlong),
                 ("cell_passes", ctypes.c_longlong), ("cluster_ctas", ctypes.c_int),
                 ("clusters", ctypes.c_int), ("cta_threads", ctypes.c_int),
-                ("members_failed", ctypes.c_int)]
+                ("members_failed", ctypes.c_int), ("graph", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

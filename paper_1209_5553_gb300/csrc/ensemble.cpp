@@ -56,6 +56,14 @@ struct erem_ens {
   double* stage_d = nullptr;        // host-pointer staging (largest member)
   cudaEvent_t ev[2] = {nullptr, nullptr};
 
+  // the run as a CUDA graph (state and queue upload, the persistent launch,
+  // state read-back), captured once per run descriptor and cluster shape
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t run_exec = nullptr;
+  EnsRun run_key{};
+  int key_cs = 0, key_clusters = 0;
+  bool graph_ok = true;             // false after a failed capture: direct launches
+
   // statistics of the last run
   erem_ens_run_stats rs{};
   std::vector<EnsState> last;
@@ -92,7 +100,13 @@ erem_status ens_alloc(erem_ens* E, T** p, size_t count) {
   return EREM_OK;
 }
 
+void drop_graph(erem_ens* E) {
+  if (E->run_exec) cudaGraphExecDestroy(E->run_exec);
+  E->run_exec = nullptr;
+}
+
 void release_tables(erem_ens* E) {
+  drop_graph(E);
   void* dp[] = {E->mem_d, E->st_d, E->dd_d, E->xi_d, E->order_d, E->next_d};
   for (void* p : dp)
     if (p) cudaFree(p);
@@ -244,6 +258,59 @@ double member_weight(const erem_ens* E, int e) {
   return rate * ((double)c->Np + 16384.0);
 }
 
+bool same_run(const EnsRun& a, const EnsRun& b) {
+  return a.mem == b.mem && a.st == b.st && a.order == b.order && a.next == b.next && a.xi == b.xi &&
+         a.n == b.n && a.nlev == b.nlev && a.mmax == b.mmax && a.restart == b.restart &&
+         a.passes_per_step == b.passes_per_step;
+}
+
+// The device work of a run, in stream order: the member states and the queue
+// order up from pinned host memory, the queue position reset, the persistent
+// launch, the states back.  The copies read and write the pinned buffers when
+// they execute, so one capture serves every run with the same descriptor.
+cudaError_t enqueue_run(erem_ens* E, const EnsRun& R, int cs, int clusters, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(E->st_d, E->st_h, sizeof(EnsState) * E->n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(E->order_d, E->order_h, sizeof(int) * E->n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E->next_d, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = launch_ens_cluster(R, E->prec, cs, clusters, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(E->st_h, E->st_d, sizeof(EnsState) * E->n, cudaMemcpyDeviceToHost, s);
+  return e;
+}
+
+// Capture the run on the ensemble's own stream (a legacy default stream
+// cannot be captured) and instantiate it; on any failure the ensemble keeps
+// to direct launches.
+void capture_run(erem_ens* E, const EnsRun& R, int cs, int clusters) {
+  if (!E->cap_stream && cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    E->cap_stream = nullptr;
+    E->graph_ok = false;
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    E->graph_ok = false;
+    return;
+  }
+  const cudaError_t e = enqueue_run(E, R, cs, clusters, E->cap_stream);
+  const cudaError_t ee = cudaStreamEndCapture(E->cap_stream, &g);
+  cudaGraphExec_t x = nullptr;
+  if (e != cudaSuccess || ee != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    E->graph_ok = false;
+    return;
+  }
+  cudaGraphDestroy(g);
+  E->run_exec = x;
+  E->run_key = R;
+  E->key_cs = cs;
+  E->key_clusters = clusters;
+}
+
 // One run: every member advances `steps` steps, one launch of the batched
 // kernel.  A member whose Leja estimate became non-finite (the Newton
 // vectors or their squares left the range of the Leja precision) or whose
@@ -281,13 +348,18 @@ erem_status run(erem_ens* E, int steps, cudaStream_t s) {
     const long long b = std::atoll(v);
     if (b >= 1) R.passes_per_step = b;
   }
-  ENS_CUDA(E, cudaMemcpyAsync(E->st_d, E->st_h, sizeof(EnsState) * E->n, cudaMemcpyHostToDevice, s));
-  ENS_CUDA(E, cudaMemcpyAsync(E->order_d, E->order_h, sizeof(int) * E->n, cudaMemcpyHostToDevice, s));
-  ENS_CUDA(E, cudaMemsetAsync(E->next_d, 0, sizeof(unsigned), s));
+  if (E->graph_ok) {
+    if (E->run_exec && !(same_run(R, E->run_key) && cs == E->key_cs && clusters == E->key_clusters))
+      drop_graph(E);
+    if (!E->run_exec) capture_run(E, R, cs, clusters);
+  }
+  // the events bracket the whole run: copies, queue reset and the launch
   ENS_CUDA(E, cudaEventRecord(E->ev[0], s));
-  ENS_CUDA(E, launch_ens_cluster(R, E->prec, cs, clusters, s));
+  if (E->run_exec)
+    ENS_CUDA(E, cudaGraphLaunch(E->run_exec, s));
+  else
+    ENS_CUDA(E, enqueue_run(E, R, cs, clusters, s));
   ENS_CUDA(E, cudaEventRecord(E->ev[1], s));
-  ENS_CUDA(E, cudaMemcpyAsync(E->st_h, E->st_d, sizeof(EnsState) * E->n, cudaMemcpyDeviceToHost, s));
   ENS_CUDA(E, cudaStreamSynchronize(s));
   float t = 0.f;
   ENS_CUDA(E, cudaEventElapsedTime(&t, E->ev[0], E->ev[1]));
@@ -298,6 +370,7 @@ erem_status run(erem_ens* E, int steps, cudaStream_t s) {
   r.cluster_ctas = cs;
   r.clusters = clusters;
   r.cta_threads = ens_cta_threads();
+  r.graph = E->run_exec ? 1 : 0;
   E->last.assign(E->st_h, E->st_h + E->n);
   int first_fail = -1;
   for (int e = 0; e < E->n; ++e) {
@@ -369,6 +442,7 @@ erem_status erem_ensemble_create(int n_members, const erem_grid* grids, const er
   if (cudaMalloc((void**)&E->stage_d, sizeof(double) * maxN) != cudaSuccess) return bail(EREM_ENOMEM);
   if (cudaEventCreate(&E->ev[0]) != cudaSuccess || cudaEventCreate(&E->ev[1]) != cudaSuccess)
     return bail(EREM_ECUDA);
+  if (const char* v = std::getenv("EREM_ENS_GRAPH")) E->graph_ok = std::atoi(v) != 0;  // 0: direct launches
   *out = E;
   return EREM_OK;
 }
@@ -382,6 +456,7 @@ erem_status erem_ensemble_destroy(erem_ens* E) {
   if (E->stage_d) cudaFree(E->stage_d);
   for (cudaEvent_t ev : E->ev)
     if (ev) cudaEventDestroy(ev);
+  if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
   delete E;
   return EREM_OK;
 }

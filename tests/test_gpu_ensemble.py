@@ -211,11 +211,32 @@ def test_member_result_does_not_depend_on_the_batch(ref):
 def test_runs_in_pieces_equal_one_run(ref):
     E, members = ref
     with _ensemble(E, members, "fp32_bulk") as one, _ensemble(E, members, "fp32_bulk") as three:
-        one.run(STEPS)
+        assert one.run(STEPS).graph == 1
         for _ in range(STEPS):
-            three.run(1)
+            assert three.run(1).graph == 1  # the first run captures, the others replay
         for k in range(len(members)):
             assert np.array_equal(_get(one, k), _get(three, k))
+
+
+def test_graph_replay_equals_direct_launches(ref, monkeypatch):
+    # the captured run (uploads, the persistent launch, the read-back) gives
+    # the bits of the same operations launched directly, over several runs and
+    # a change of cluster shape (a new capture)
+    E, members = ref
+    out = {}
+    for graph in ("1", "0"):
+        monkeypatch.setenv("EREM_ENS_GRAPH", graph)
+        res = []
+        with _ensemble(E, members, "fp32_bulk", cluster_ctas=4) as ens:
+            for cs in (4, 4, 2):
+                ens.configure(policy=E.EREM_ENS_RESTART_SUBSTEPS, cluster_ctas=cs)
+                rs = ens.run(1)
+                assert rs.graph == int(graph) and rs.cluster_ctas == cs and rs.members_failed == 0
+                res.append([_get(ens, k) for k in range(len(members))])
+        out[graph] = res
+    for a, b in zip(out["1"], out["0"]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
 
 
 def test_matches_single_context_steps(ref):
