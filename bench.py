@@ -685,7 +685,7 @@ def main(args):
     if not args.no_extra:
         # the other workloads, each with its own value, step time, dominant
         # kernel's roofline and FP32-bulk/FP64 ratio
-        line["coupled2d"] = coupled_summary(E, torch, dev, world, K, Wu)
+        line["coupled2d"] = coupled_summary(E, torch, dev, world, K, Wu, check=check)
         line["ensemble"] = ensemble_summary(E, torch, dev, world, Wu)
         line["adjoint"] = adjoint_summary(E, torch, dev, world)
     if check:
@@ -713,7 +713,7 @@ def main(args):
 # the 1024^2 coupled workload: per step, the steady pressure at T^n (warm
 # started CG, FP64), then one heat step (EREM FP32-bulk / FP64, or ROS2)
 # ---------------------------------------------------------------------------
-def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
+def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev, capture_first=False):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
     import workloads as W
 
@@ -762,8 +762,11 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
             s2 = ctx.rosm_step(T, wl.dt, code, p, lnk, phi, lam, lin_tol=1e-10, maxit=20000)
         return s1, s2
 
-    for _ in range(warmup):
-        step()
+    first = None
+    for k in range(warmup):
+        _, s2 = step()
+        if capture_first and k == 0:  # the first step from T^0 (a warm-up step), for the oracle check
+            first = {"T": T.cpu().numpy(), "schedule": s2.schedule}
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -786,7 +789,7 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
            "leja_terms_per_step": float(np.mean(degrees)), "launches": launches,
            "leja_coefs": ctx.leja_coefficients, "lagged": lagged,
            "T": T.cpu().numpy(), "rhoc": rc, "t_terms_ms": t_terms, "n_terms": n_terms,
-           "degrees": [m for sc in scheds for m in sc]}
+           "degrees": [m for sc in scheds for m in sc], "first": first}
     if ada["accepted"]:
         out["ros_steps_per_step"] = float(np.mean(ada["accepted"][-steps:]))
         out["ros_rejections_per_step"] = float(np.mean(ada["rejected"][-steps:]))
@@ -794,16 +797,47 @@ def run_coupled(E, torch, wl, scheme, precision, steps, warmup, dev):
     return out
 
 
-def coupled_summary(E, torch, dev, world, K, Wu):
+def oracle_coupled_check(wl, rc, firsts):
+    """Relative L2 errors of the GPU's first coupled steps from T^0 against
+    one oracle sequential step (§3.2: steady pressure at T^0 by a sparse
+    direct solve, Darcy fluxes at T^0, one EREM heat step with the
+    T-dependent fluid laws; FP64), with the heat capacity the GPU run took
+    from its own pressure solve."""
+    from oracle import fv, timestep as ts
+    from oracle.leja import LejaOptions
+
+    t = time.perf_counter()
+    g = fv.Grid(2, wl.nx, wl.ny)
+    ph = fv.Physics(rc, rc, wl.head_drop, 0.0, wl.T_inflow, 1)
+    T0 = wl.T0
+    T1, _, res = ts.sequential_step(g, ph, wl.lnk, wl.phi, wl.lam, T0.copy(), None, wl.dt,
+                                    opts=LejaOptions(tol_a=wl.tol, tol_r=wl.tol))
+    sec = time.perf_counter() - t
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out = {"oracle_schedule": res.schedule, "oracle_s": sec,
+           "what": "one coupled step from T^0 (pressure, then the heat step); relative L2 of the "
+                   "state T^1 and of the increment T^1 - T^0 against the FP64 oracle",
+           "note": "the GPU's pressure is its CG to 1e-10, the oracle's a direct solve: the FP64 "
+                   "arm's difference is that of the pressure (with the oracle's pressure the "
+                   "parity tests hold 1e-11)"}
+    for key, f in firsts.items():
+        if f is not None:
+            out[key] = {"rel_l2_state": rel(f["T"], T1), "rel_l2_increment": rel(f["T"] - T0, T1 - T0),
+                        "schedule": f["schedule"]}
+    return out
+
+
+def coupled_summary(E, torch, dev, world, K, Wu, check=False):
     """The 1024^2 coupled workload for the default line: EREM FP32-bulk and
-    FP64 and ROS2 (FP64), K steps each after Wu warm-up steps."""
+    FP64 and ROS2 (FP64), K steps each after Wu warm-up steps; with check,
+    the first EREM steps against one oracle step."""
     import workloads as W
 
     wl = W.coupled2d(1024)
     runs = {}
     for key, scheme, prec in (("erem_fp32_bulk", "erem", "fp32_bulk"), ("erem_fp64", "erem", "fp64"),
                               ("ros2_fp64", "ros2", "fp64")):
-        r = run_coupled(E, torch, wl, scheme, prec, K, Wu, dev)
+        r = run_coupled(E, torch, wl, scheme, prec, K, Wu, dev, capture_first=check and scheme == "erem")
         ms, value = aggregate(r["ms"], wl.n, K, world, dev)
         r.update(ms=ms, value=value)
         runs[key] = r
@@ -814,7 +848,7 @@ def coupled_summary(E, torch, dev, world, K, Wu):
     bpc = term_bytes_per_cell(b, h["degrees"], h_lag)
     ach = bpc * wl.n / (h["t_terms_ms"] / 1e3) / 1e9 if h["n_terms"] else None
     rel = lambda a, b_: float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
-    return {
+    out = {
         "workload": "coupled2d_1024", "cells": wl.n, "steps": K, "warmup": Wu, "unit": UNIT,
         "value": h["value"], "ms_per_step": h["ms"] / K,
         "what": "per step: steady FP64 pressure CG at T^n (multigrid-preconditioned, to 1e-10), "
@@ -836,6 +870,10 @@ def coupled_summary(E, torch, dev, world, K, Wu):
                      "note": "the 1024^2 term's working set (about 50 MB) stays in L2, so the "
                              "achieved rate is not an HBM figure"},
     }
+    if check and h["first"] is not None:
+        out["rel_l2_vs_oracle"] = oracle_coupled_check(
+            wl, h["rhoc"], {"fp32_bulk": h["first"], "fp64": d["first"]})
+    return out
 
 
 def main_coupled(args):
